@@ -1,0 +1,305 @@
+"""Seeded synthetic workloads shaped like the examples of Zhao & Choo (Sec. 5).
+
+This module lays out material points, material fields, boundary masks and load
+schedules, and nothing else: it holds no arithmetic of the method (no Lame
+conversion, no stabilization parameter, no mass).  Both the CUDA path and the
+CPU oracle consume what it returns, so it is the only module they share.
+
+Every workload is synthetic.  The paper's examples use no dataset; the shapes,
+sizes and distributions below follow the example set-ups (Terzaghi column,
+strip footing, 3D consolidation block) with seeded random fields where the
+workload asks for heterogeneity.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional, Tuple
+
+import numpy as np
+
+ORIG, GIMP = 0, 1
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    shape: int                      # ORIG or GIMP
+    ncell: Tuple[int, int, int]
+    origin: Tuple[float, float, float]
+    h: float
+    # material points (input order = caller's particle ids)
+    x: np.ndarray                   # (n, d)
+    vol: np.ndarray                 # (n,)
+    lp: np.ndarray                  # (n, d) GIMP half lengths
+    p0: np.ndarray                  # (n,)
+    v0: Optional[np.ndarray]        # (n, d) or None
+    E: np.ndarray                   # (n,)
+    nu: np.ndarray                  # (n,)
+    k: np.ndarray                   # (n,) intrinsic permeability, m^2
+    surf_id: np.ndarray             # (n,) int32, -1 = interior
+    surf_normal: np.ndarray         # (n, d)
+    surf_area: np.ndarray           # (n,)
+    trac_full: np.ndarray           # (n_surf, d) traction at full load
+    # mixture and fluid
+    rho_s: float = 2500.0
+    rho_f: float = 1000.0
+    phi0: float = 0.33
+    mu_f: float = 1.0e-3
+    alpha_vis: float = 0.0
+    g: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    # time integration and stabilization
+    dynamic: bool = False
+    beta: float = 0.3025
+    gamma: float = 0.6
+    stabilize: bool = True
+    tau_scale: float = 1.0
+    dt: float = 1.0
+    nsteps: int = 1
+    ramp_time: float = 0.0          # load scale min(t / ramp_time, 1); 0 = applied at once
+    # Dirichlet data per grid node
+    u_fixed: np.ndarray = field(default=None)   # (nnodes, d) uint8
+    u_value: np.ndarray = field(default=None)   # (nnodes, d) increment over a step
+    p_fixed: np.ndarray = field(default=None)   # (nnodes,) uint8
+    p_value: np.ndarray = field(default=None)   # (nnodes,)
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def n_surf(self) -> int:
+        return int(self.trac_full.shape[0])
+
+    @property
+    def nn(self) -> Tuple[int, ...]:
+        return tuple(self.ncell[k] + 1 for k in range(self.dim))
+
+    @property
+    def nnodes(self) -> int:
+        return int(np.prod(self.nn))
+
+    def load_scale(self, t: float) -> float:
+        if self.ramp_time <= 0.0:
+            return 1.0
+        return min(t / self.ramp_time, 1.0)
+
+    def traction(self, t: float) -> np.ndarray:
+        return np.ascontiguousarray(self.load_scale(t) * self.trac_full)
+
+
+# --------------------------------------------------------------------------
+# building blocks
+# --------------------------------------------------------------------------
+def lattice(dim, body_cells, h, ppc_axis, origin=(0.0, 0.0, 0.0), cell_offset=(0, 0, 0)):
+    """Material points at the regular sub-cell centres of `body_cells` cells."""
+    axes = []
+    for k in range(dim):
+        c = np.arange(cell_offset[k], cell_offset[k] + body_cells[k])
+        s = (np.arange(ppc_axis) + 0.5) / ppc_axis
+        axes.append(((c[:, None] + s[None, :]).reshape(-1)) * h + origin[k])
+    mesh = np.meshgrid(*axes, indexing="ij")
+    # Fortran order: x index fastest, then y, then z
+    x = np.stack([m.reshape(-1, order="F") for m in mesh], axis=1)
+    n = x.shape[0]
+    vol = np.full(n, h ** dim / ppc_axis ** dim)
+    lp = np.full((n, dim), 0.5 * h / ppc_axis)
+    return np.ascontiguousarray(x), vol, lp
+
+
+def node_coords(dim, ncell):
+    nn = [ncell[k] + 1 for k in range(dim)]
+    idx = np.indices(nn[::-1]).reshape(dim, -1)[::-1]  # idx[0] fastest
+    return idx.T  # (nnodes, dim) integer node coordinates
+
+
+def empty_bcs(dim, ncell):
+    nnodes = int(np.prod([ncell[k] + 1 for k in range(dim)]))
+    return (np.zeros((nnodes, dim), np.uint8), np.zeros((nnodes, dim)),
+            np.zeros(nnodes, np.uint8), np.zeros(nnodes))
+
+
+def _surface(x, top_axis, top_value, h, ppc_axis, select):
+    """Top-row material points (upper sub-row) for which select(x) holds."""
+    y = x[:, top_axis]
+    top = np.abs(y - (top_value - 0.5 * h / ppc_axis)) < 1e-9 * max(1.0, abs(top_value))
+    return np.nonzero(top & select(x))[0]
+
+
+def _finish(dim, x, surf_idx, normal_axis, area, trac_vec):
+    n = x.shape[0]
+    surf_id = np.full(n, -1, np.int32)
+    surf_id[surf_idx] = np.arange(len(surf_idx), dtype=np.int32)
+    surf_normal = np.zeros((n, dim))
+    surf_normal[surf_idx, normal_axis] = 1.0
+    surf_area = np.zeros(n)
+    surf_area[surf_idx] = area
+    trac = np.tile(np.asarray(trac_vec, float)[None, :dim], (len(surf_idx), 1))
+    return surf_id, surf_normal, surf_area, np.ascontiguousarray(trac)
+
+
+def _perm(rng, n):
+    return rng.permutation(n) if rng is not None else np.arange(n)
+
+
+# --------------------------------------------------------------------------
+# the workloads
+# --------------------------------------------------------------------------
+def terzaghi_column(ncell_y=40, ncell_x=4, h=0.25, E=10e6, nu=0.3, k=1e-10, mu_f=1e-3,
+                    load=10e3, dt=1.0, nsteps=10, ppc_axis=(2, 2), stabilize=True,
+                    tau_scale=1.0, shape=ORIG, name="terzaghi-4x40"):
+    """2D plane-strain consolidation column (Sec. 5.1 set-up): drained loaded top,
+    impermeable rollers on the sides, fixed impermeable bottom, no gravity."""
+    dim = 2
+    ncell = (ncell_x, ncell_y, 0)
+    px, py = ppc_axis
+    axes = [((np.arange(ncell_x)[:, None] + (np.arange(px) + 0.5)[None, :] / px).reshape(-1)) * h,
+            ((np.arange(ncell_y)[:, None] + (np.arange(py) + 0.5)[None, :] / py).reshape(-1)) * h]
+    X, Y = np.meshgrid(axes[0], axes[1], indexing="xy")
+    x = np.ascontiguousarray(np.stack([X.reshape(-1), Y.reshape(-1)], axis=1))
+    n = x.shape[0]
+    vol = np.full(n, h * h / (px * py))
+    lp = np.ascontiguousarray(np.tile([0.5 * h / px, 0.5 * h / py], (n, 1)))
+    H = ncell_y * h
+    top = np.nonzero(np.abs(x[:, 1] - (H - 0.5 * h / py)) < 1e-9 * H)[0]
+    surf_id, surf_normal, surf_area, trac = _finish(dim, x, top, 1, h / px, (0.0, -load))
+    uf, uv, pf, pv = empty_bcs(dim, ncell)
+    nc = node_coords(dim, ncell)
+    uf[nc[:, 0] == 0, 0] = 1
+    uf[nc[:, 0] == ncell_x, 0] = 1
+    uf[nc[:, 1] == 0, :] = 1
+    pf[nc[:, 1] == ncell_y] = 1
+    return Workload(name=name, dim=dim, shape=shape, ncell=ncell, origin=(0.0, 0.0, 0.0), h=h,
+                    x=x, vol=vol, lp=lp, p0=np.zeros(n), v0=None,
+                    E=np.full(n, E), nu=np.full(n, nu), k=np.full(n, k),
+                    surf_id=surf_id, surf_normal=surf_normal, surf_area=surf_area, trac_full=trac,
+                    mu_f=mu_f, dynamic=False, stabilize=stabilize, tau_scale=tau_scale,
+                    dt=dt, nsteps=nsteps, u_fixed=uf, u_value=uv, p_fixed=pf, p_value=pv)
+
+
+def paper_terzaghi(n_elem=40, stabilize=True, tau_scale=1.0, shape=ORIG):
+    """Sec. 5.1 verification column: K = 1 MPa, nu = 0.25, c_v = 1.8e-5 m^2/s,
+    H = 1 m, w = 1 kPa, dt = 0.1 s, one step, 2 material points per element
+    (one column of elements, points stacked vertically)."""
+    K, nu = 1.0e6, 0.25
+    G = 3.0 * K * (1.0 - 2.0 * nu) / (2.0 * (1.0 + nu))
+    E = 2.0 * G * (1.0 + nu)
+    M = K + 4.0 * G / 3.0
+    mu_f = 1.0e-3
+    k = 1.8e-5 / M * mu_f          # c_v = M k / mu_f
+    h = 1.0 / n_elem
+    return terzaghi_column(ncell_y=n_elem, ncell_x=1, h=h, E=E, nu=nu, k=k, mu_f=mu_f,
+                           load=1.0e3, dt=0.1, nsteps=1, ppc_axis=(1, 2), stabilize=stabilize,
+                           tau_scale=tau_scale, shape=shape, name=f"paper-terzaghi-{n_elem}")
+
+
+def strip_footing(body=(200, 100), pad=2, h=0.1, seed=2, ppc_axis=2, E0=20e6, nu=0.3, k=1e-14,
+                  w_max=200e3, ramp=0.1, dt=1e-3, nsteps=200, half_width=1.0,
+                  shape=GIMP, dynamic=True, alpha_vis=0.04, name=None):
+    """2D plane-strain dynamic strip footing (Sec. 5.2 shape): a block with empty
+    padding rows above the surface, a rigid strip of half width 1 m at the top
+    centre loaded by a linear ramp, drained top outside the strip, fixed bottom,
+    rollers on the sides; lognormal stiffness field E = E0 exp(0.05 Z)."""
+    rng = np.random.default_rng(seed)
+    dim = 2
+    ncell = (body[0], body[1] + pad, 0)
+    x, vol, lp = lattice(dim, body, h, ppc_axis)
+    n = x.shape[0]
+    E = E0 * np.exp(0.05 * rng.standard_normal(n))
+    W, H = body[0] * h, body[1] * h
+    xc = 0.5 * W
+    top = _surface(x, 1, H, h, ppc_axis, lambda q: np.abs(q[:, 0] - xc) <= half_width + 1e-12)
+    surf_id, surf_normal, surf_area, trac = _finish(dim, x, top, 1, h / ppc_axis, (0.0, -w_max))
+    uf, uv, pf, pv = empty_bcs(dim, ncell)
+    nc = node_coords(dim, ncell)
+    uf[nc[:, 1] == 0, :] = 1
+    uf[nc[:, 0] == 0, 0] = 1
+    uf[nc[:, 0] == ncell[0], 0] = 1
+    strip = int(round(half_width / h))
+    mid = body[0] // 2
+    drained = (nc[:, 1] == body[1]) & ((nc[:, 0] < mid - strip) | (nc[:, 0] > mid + strip))
+    pf[drained] = 1
+    return Workload(name=name or f"footing-{body[0]}x{body[1]}", dim=dim, shape=shape, ncell=ncell,
+                    origin=(0.0, 0.0, 0.0), h=h, x=x, vol=vol, lp=lp, p0=np.zeros(n),
+                    v0=np.zeros((n, dim)), E=E, nu=np.full(n, nu), k=np.full(n, k),
+                    surf_id=surf_id, surf_normal=surf_normal, surf_area=surf_area, trac_full=trac,
+                    alpha_vis=alpha_vis if dynamic else 0.0, dynamic=dynamic, dt=dt,
+                    nsteps=nsteps, ramp_time=ramp, u_fixed=uf, u_value=uv, p_fixed=pf, p_value=pv)
+
+
+def consolidation_block(body=(64, 64, 32), pad=1, h=0.1, seed=3, ppc_axis=2, E=10e6, nu=0.3,
+                        logk=(-13.0, -11.0), load=50e3, patch_half=1.0, dt=5.0, nsteps=20,
+                        shape=GIMP, name=None):
+    """3D quasi-static consolidation block: per-point permeability log-uniform,
+    surface load on a central square patch, drained top, fixed bottom, rollers."""
+    rng = np.random.default_rng(seed)
+    dim = 3
+    ncell = (body[0], body[1], body[2] + pad)
+    x, vol, lp = lattice(dim, body, h, ppc_axis)
+    n = x.shape[0]
+    k = 10.0 ** rng.uniform(logk[0], logk[1], n)
+    cx, cy, H = 0.5 * body[0] * h, 0.5 * body[1] * h, body[2] * h
+    top = _surface(x, 2, H, h, ppc_axis,
+                   lambda q: (np.abs(q[:, 0] - cx) <= patch_half + 1e-12)
+                   & (np.abs(q[:, 1] - cy) <= patch_half + 1e-12))
+    surf_id, surf_normal, surf_area, trac = _finish(dim, x, top, 2, (h / ppc_axis) ** 2,
+                                                    (0.0, 0.0, -load))
+    uf, uv, pf, pv = empty_bcs(dim, ncell)
+    nc = node_coords(dim, ncell)
+    uf[nc[:, 2] == 0, :] = 1
+    uf[(nc[:, 0] == 0) | (nc[:, 0] == ncell[0]), 0] = 1
+    uf[(nc[:, 1] == 0) | (nc[:, 1] == ncell[1]), 1] = 1
+    pf[nc[:, 2] == body[2]] = 1
+    return Workload(name=name or "block-{}x{}x{}".format(*body), dim=dim, shape=shape,
+                    ncell=ncell, origin=(0.0, 0.0, 0.0), h=h, x=x, vol=vol, lp=lp,
+                    p0=np.zeros(n), v0=None, E=np.full(n, E), nu=np.full(n, nu), k=k,
+                    surf_id=surf_id, surf_normal=surf_normal, surf_area=surf_area,
+                    trac_full=trac, dynamic=False, dt=dt, nsteps=nsteps,
+                    u_fixed=uf, u_value=uv, p_fixed=pf, p_value=pv)
+
+
+def jittered(w: Workload, seed: int, frac: float = 0.15, shuffle: bool = True,
+             E_spread: float = 0.2, logk_spread: float = 1.0) -> Workload:
+    """A copy of `w` whose points are displaced by up to `frac` of their spacing
+    (so GIMP domains straddle cell faces), whose E and k are perturbed, and whose
+    input order is shuffled: the parity workloads."""
+    rng = np.random.default_rng(seed)
+    n, d = w.x.shape
+    spacing = 2.0 * w.lp
+    x = w.x + frac * spacing * rng.uniform(-1.0, 1.0, (n, d))
+    E = w.E * np.exp(E_spread * rng.standard_normal(n))
+    k = w.k * 10.0 ** (logk_spread * rng.uniform(-1.0, 1.0, n))
+    p0 = 1e3 * rng.standard_normal(n)
+    perm = _perm(rng, n) if shuffle else np.arange(n)
+    surf_id = w.surf_id[perm]
+
+    def take(a):
+        return None if a is None else np.ascontiguousarray(a[perm])
+
+    v0 = None if w.v0 is None else np.ascontiguousarray(0.01 * rng.standard_normal((n, d)))
+    return replace(w, name=w.name + f"-jit{seed}", x=take(x), vol=take(w.vol), lp=take(w.lp),
+                   p0=take(p0), v0=take(v0) if v0 is not None else None, E=take(E), nu=take(w.nu),
+                   k=take(k), surf_id=np.ascontiguousarray(surf_id),
+                   surf_normal=take(w.surf_normal), surf_area=take(w.surf_area))
+
+
+def small_footing(seed=7, shape=GIMP, dynamic=True, body=(24, 12), pad=2, h=0.25, dt=2e-3,
+                  k=1e-12, jitter=0.15):
+    """A footing a few tiles wide with jittered, shuffled points: parity case."""
+    w = strip_footing(body=body, pad=pad, h=h, seed=seed, k=k, w_max=100e3, ramp=4 * dt, dt=dt,
+                      nsteps=4, half_width=1.0, shape=shape, dynamic=dynamic,
+                      alpha_vis=0.04 if dynamic else 0.0, name=f"small-footing-{body[0]}x{body[1]}")
+    return jittered(w, seed + 100, frac=jitter) if jitter > 0 else w
+
+
+def small_block(seed=11, shape=GIMP, body=(6, 5, 4), pad=1, h=0.25, dt=1.0, jitter=0.15):
+    w = consolidation_block(body=body, pad=pad, h=h, seed=seed, patch_half=0.25, dt=dt, nsteps=3,
+                            shape=shape, name="small-block-{}x{}x{}".format(*body))
+    return jittered(w, seed + 100, frac=jitter) if jitter > 0 else w
+
+
+CONFIGS = {
+    "terzaghi": lambda: terzaghi_column(),
+    "footing": lambda: strip_footing(),
+    "block3d": lambda: consolidation_block(),
+}
