@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of the stabilized implicit u-p MPM load step on GB300.
+
+One "step" is one load step of the whole hot path (bin + sort, shape
+functions, Stage-1 P2G, sparsity, Newton with residual / Jacobian assembly and
+FGMRES to the paper's 1e-8 residual test, G2P + convection) on the 2D dynamic
+strip footing: 200 x 100 cells at h = 0.1 m (+2 empty rows), 80,000 points,
+GIMP, Newmark, k = 1e-14 m^2, seeded lognormal stiffness, strip load ramped to
+200 kPa over 0.1 s, dt = 1e-3 s.  Inputs are synthetic (seeded), resident in
+HBM for `value`; `e2e` goes through the C-ABI with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank steps its own
+independent replica of the problem ("replicas only": the path has no exchange
+step at this size); value = all ranks' particle updates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "implicit u–p MPM steps/s and particle-updates/s at 1e-8 residual, FP64 vs mixed"
+UNIT = "particle-updates/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="footing")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", default="spmv,orth,jacobian,point,residual,precond",
+                    help="kernel classes timed with CUDA events")
+    return ap.parse_args()
+
+
+def make_workload(name):
+    from paper_1905_00671_gb300 import inputs as I
+
+    if name == "footing":
+        return I.strip_footing()
+    if name == "terzaghi":
+        return I.terzaghi_column()
+    if name == "block3d":
+        return I.consolidation_block()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(w):
+    return {"workload": f"{w.name}: 2D plane-strain dynamic strip footing" if w.dim == 2 and w.dynamic
+            else w.name,
+            "grid_cells": list(w.ncell[:w.dim]), "h_m": w.h, "points": w.n,
+            "shape": "GIMP" if w.shape == 1 else "original MPM",
+            "scheme": "Newmark" if w.dynamic else "quasi-static implicit Euler",
+            "dt_s": w.dt, "newton_rtol": 1e-8, "krylov_rtol": 1e-8,
+            "l2": "flushed between timed steps (512 MiB write)"}
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("mpm_solver.cu", "mpm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1905_00671_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    summary was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    src = kernel_source_hash()
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == src:
+            return float(parts[3])
+    return None
+
+
+def spmv_bytes(nnodes, nnzb, nb):
+    """Algorithmic bytes of one block-CSR SpMV: values + column indices + row
+    pointers, x read once, y written once."""
+    return nnzb * (nb * nb * 8 + 4) + (nnodes + 1) * 4 + 2 * nnodes * nb * 8
+
+
+# --------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_1905_00671_gb300 import build as B
+    from paper_1905_00671_gb300 import mpm
+
+    torch.cuda.set_device(local_rank)
+    if not B.up_to_date():
+        B.build()
+    mpm.load()
+    w = make_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    prof_bits = 0
+    for k in args.profile.split(","):
+        if k:
+            prof_bits |= 1 << mpm.PROF[k]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident throughput
+    sim = mpm.Simulation(w, stream=stream.cuda_stream, profile=prof_bits)
+    for _ in range(args.warmup):
+        sim.step(resident=True)
+    barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    newton = krylov = launches = 0
+    prof_ms = {k: 0.0 for k in mpm.PROF}
+    prof_n = {k: 0 for k in mpm.PROF}
+    nnzb = []
+    for i in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps (not timed)
+        ev0[i].record(stream)
+        st = sim.step(resident=True)
+        ev1[i].record(stream)
+        newton += st["newton_iters"]
+        krylov += st["krylov_total"]
+        launches += st["kernel_launches"]
+        nnzb.append(st["nnzb"])
+        for k in mpm.PROF:
+            prof_ms[k] += st["prof_ms"][k]
+            prof_n[k] += st["prof_launches"][k]
+    barrier()
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    t_local = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t_local, op=torch.distributed.ReduceOp.MAX)
+    total_ms = float(t_local.item())
+    sim.close()
+
+    # ---- end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        n, d = w.n, w.dim
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        trac_h = pin((max(w.n_surf, 1), d))
+        outs = {"x": pin((n, d)), "u": pin((n, d)), "p": pin(n)}
+        sim2 = mpm.Simulation(w, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            trac_h[:w.n_surf] = w.traction(sim2.t + w.dt)
+            sim2.step(traction=trac_h[:w.n_surf])
+        barrier()
+        e2e_s = 0.0
+        import ctypes as C
+        o = mpm.mpm_particles_out(x=outs["x"].ctypes.data_as(C.c_void_p),
+                                  u=outs["u"].ctypes.data_as(C.c_void_p),
+                                  p=outs["p"].ctypes.data_as(C.c_void_p))
+        for i in range(args.steps):
+            flush.zero_()
+            trac_h[:w.n_surf] = w.traction(sim2.t + w.dt)   # the step's input, in pinned memory
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim2.step(traction=trac_h[:w.n_surf])          # H2D copy of the loads inside
+            rc = sim2.lib.mpm_read(sim2.ctx, C.byref(o))    # D2H of the step's result
+            e2e_s += time.perf_counter() - t0
+            if rc != 0:
+                raise RuntimeError("mpm_read failed")
+        barrier()
+        sim2.close()
+        te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(te.item())
+        e2e = {"value": world * w.n * args.steps / e2e_total, "unit": UNIT,
+               "h2d_bytes_per_step": int(w.n_surf * d * 8),
+               "d2h_bytes_per_step": int(n * (2 * d + 1) * 8),
+               "steps_per_s": world * args.steps / e2e_total}
+
+    # ---- roofline of the dominant kernel class (live CUDA-event times)
+    peaks, peak_src = measured_peaks()
+    shares = {k: prof_ms[k] for k in prof_ms if prof_n[k] > 0}
+    dominant = max(shares, key=shares.get) if shares else None
+    roofline = None
+    if "spmv" in shares and prof_n["spmv"] > 0:
+        nb = w.dim + 1
+        avg_nnzb = sum(nnzb) / len(nnzb)
+        bytes_launch = spmv_bytes(w.nnodes, avg_nnzb, nb)
+        avg_ms = prof_ms["spmv"] / prof_n["spmv"]
+        ach = bytes_launch / (avg_ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roofline = {"kernel": "k_bsr_spmv", "bound": "hbm", "achieved": round(ach, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                    "traffic": ncu_traffic("k_bsr_spmv"), "algorithmic_bytes": int(bytes_launch),
+                    "avg_launch_us": round(avg_ms * 1e3, 3), "peak_source": peak_src + " hbm_gbs",
+                    "dominant_class": dominant,
+                    "class_ms_per_step": {k: round(v / args.steps, 3) for k, v in shares.items()},
+                    "class_launches_per_step": {k: prof_n[k] / args.steps for k in shares}}
+
+    value = world * w.n * args.steps / (total_ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
+            "steps_per_s": world * args.steps / (total_ms * 1e-3),
+            "newton_iters_per_step": newton / args.steps, "krylov_iters_per_step": krylov / args.steps,
+            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e}
+    return line, w
+
+
+# --------------------------------------------------------------- oracle
+def oracle_sample_step(w, dt):
+    from oracle import oracle as O
+
+    o = O.Oracle(w, newton_rtol=1e-8)
+    t0 = time.perf_counter()
+    info = o.step(dt)
+    return time.perf_counter() - t0, info.newton_iters
+
+
+def reference_sample():
+    """A bounded piece of the footing workload for the oracle: same h, material,
+    loading and time step, 140 x 70 cells of body (39,200 points)."""
+    from paper_1905_00671_gb300 import inputs as I
+
+    return I.strip_footing(body=(140, 70), seed=2)
+
+
+def run_cpu_baseline(w):
+    sec, its = oracle_sample_step(w, w.dt)
+    return {"value": w.n / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one load step (t = 0 -> dt, {its} Newton iterations) of the full "
+                      f"{w.n}-point footing, C loops + SuperLU, single thread",
+            "seconds": round(sec, 2)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = make_workload(args.workload)
+    s = reference_sample()
+    secs = []
+    for i in range(args.warmup + args.steps):
+        sec, _ = oracle_sample_step(s, s.dt)
+        if i >= args.warmup:
+            secs.append(sec)
+    total = sum(secs)
+    value = s.n * args.steps / total
+    sample = (f"each step: one oracle load step of a {s.ncell[0]}x{s.ncell[1] - 2}-cell, "
+              f"{s.n}-point piece of the footing (same h, material, load, dt)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": dict(workload_config(w), parallelism="cpu"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line, w = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = run_cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

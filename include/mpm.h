@@ -1,0 +1,245 @@
+/*
+ * mpm.h -- C-ABI of the GB300 stabilized implicit u-p material point method.
+ *
+ * The method is the one of Zhao & Choo, "Stabilized material point methods for
+ * coupled large deformation and fluid flow in porous materials" (arXiv
+ * 1905.00671): a fully implicit MPM for a fluid-saturated mixture with nodal
+ * unknowns [u, p] (equal-order linear interpolation, Sec. 3.1), stabilized by
+ * polynomial pressure projection (PPP, Sec. 4.2) and solved by Newton (Sec.
+ * 3.4).  Everything behind these calls runs as CUDA kernels on one GPU.
+ *
+ * The calls follow the paper's statement of the problem (Sec. 2.4): given the
+ * Dirichlet data u^, p^, the Neumann data t^, q^ and the initial fields u0 = 0,
+ * p0, find u and p.  mpm_create takes the material points (the initial
+ * configuration), the material and the permeability; mpm_step advances one
+ * load step (Stages 1-4 of Sec. 3.1) with the current loads and boundary
+ * conditions; mpm_read returns the material point state.
+ *
+ * Conventions (all calls)
+ *   - SI units.  Tension positive, pore pressure positive in compression
+ *     (Eq. darcy-law and the effective stress of Sec. 2.2).
+ *   - dim = 2 is plane strain, dim = 3 is 3D.  Per-point vectors are stored
+ *     point-major: x[i*dim + k].  Tensors are row-major dim x dim.
+ *   - Grid nodes are numbered i + (nx+1)*(j + (ny+1)*k) with nx = ncell[0], ...
+ *     Nodal unknowns are interleaved [u_x, u_y, (u_z), p] per node.
+ *   - Every pointer argument is a HOST pointer unless stated otherwise; the
+ *     library copies what it needs and never keeps a caller pointer.
+ *   - Return value: MPM_OK (0) or a negative MPM_ERR_* code.  After an error
+ *     mpm_last_error(ctx) describes it.  A failed mpm_step leaves the state at
+ *     the last completed step.  No call throws.
+ *   - A context is used by one host thread at a time.
+ */
+#ifndef UPMPM_MPM_H
+#define UPMPM_MPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MPM_OK = 0,
+  MPM_ERR_BAD_ARG = -1,          /* invalid argument or size */
+  MPM_ERR_OUT_OF_GRID = -2,      /* a material point centre left the background grid */
+  MPM_ERR_NEGATIVE_J = -3,       /* det F <= 0 at some material point */
+  MPM_ERR_NONFINITE = -4,        /* NaN / Inf in the residual */
+  MPM_ERR_NEWTON_DIVERGED = -5,  /* Newton hit its iteration cap */
+  MPM_ERR_KRYLOV_STAGNATED = -6, /* the Krylov solver hit its iteration cap */
+  MPM_ERR_TIMEOUT = -7,          /* reserved for bounded device-side waits */
+  MPM_ERR_CUDA = -8,             /* a CUDA runtime call failed */
+  MPM_ERR_NO_MEMORY = -9         /* device allocation failed */
+};
+
+enum { MPM_SHAPE_ORIG = 0, MPM_SHAPE_GIMP = 1 };     /* Sec. 3.1: FE basis or GIMP basis */
+enum { MPM_QUASISTATIC = 0, MPM_NEWMARK = 1 };       /* Sec. 3.2: implicit Euler or Newmark */
+enum { MPM_FP64 = 0, MPM_MIXED = 1 };
+
+/* Kernel classes that mpm_options.profile can time with CUDA events (bit k of
+ * the mask selects class k; mpm_stats.prof_ms[k] / prof_launches[k]). */
+enum {
+  MPM_PROF_SPMV = 0,      /* block-CSR SpMV inside the Krylov solver */
+  MPM_PROF_JACOBIAN = 1,  /* Jacobian block assembly */
+  MPM_PROF_RESIDUAL = 2,  /* residual assembly */
+  MPM_PROF_POINT = 3,     /* per-point kinematics / stress / flux evaluation */
+  MPM_PROF_ORTH = 4,      /* Gram-Schmidt kernels of FGMRES */
+  MPM_PROF_P2G = 5,       /* Stage-1 P2G */
+  MPM_PROF_G2P = 6,       /* Stages 3-4 update */
+  MPM_PROF_PRECOND = 7,   /* preconditioner application */
+  MPM_PROF_COUNT = 8
+};
+
+typedef struct mpm_ctx mpm_ctx;
+
+/* Structured background grid, fixed for the whole run (Sec. 3.5: "fixed
+ * background mesh").  Square (cubic) cells of size h. */
+typedef struct {
+  int32_t dim;        /* 2 or 3 */
+  int32_t ncell[3];   /* cells per axis; ncell[2] ignored for dim = 2 */
+  double origin[3];
+  double h;
+} mpm_grid;
+
+/* Material points at t = 0 (u0 = 0 there).  n points; arrays of length n or
+ * n*dim.  lp are the half lengths of the GIMP domains (Eq. gimp-basis); they
+ * also place the surface points of Neumann data (x + lp.n).  surf_id maps a
+ * point to its entry in the load arrays of mpm_loads (-1: interior point). */
+typedef struct {
+  int64_t n;
+  const double *x;            /* n*dim positions */
+  const double *vol;          /* n volumes */
+  const double *lp;           /* n*dim GIMP half lengths (0 < lp < h) */
+  const double *p0;           /* n initial pore pressures, NULL = 0 */
+  const double *v0;           /* n*dim initial velocities (Newmark), NULL = 0 */
+  const int32_t *surf_id;     /* n, -1 = interior; NULL = no surface points */
+  const double *surf_normal;  /* n*dim outward unit normals (surface points) */
+  const double *surf_area;    /* n boundary measure carried by each surface point */
+  int32_t n_surf;             /* number of surface entries */
+} mpm_particles;
+
+/* Mixture of incompressible constituents (Sec. 2.1), compressible
+ * neo-Hookean skeleton (Kirchhoff effective stress G(b - 1) + lambda ln J 1),
+ * Kelvin viscous stress (Sec. 2.2, Newmark only), Darcy flow with mobility
+ * k / mu_f (Eq. darcy-law). */
+typedef struct {
+  const double *E;            /* n Young's moduli */
+  const double *nu;           /* n Poisson ratios */
+  double rho_s, rho_f;        /* intrinsic densities */
+  double phi0;                /* initial porosity */
+  double mu_f;                /* fluid dynamic viscosity */
+  double alpha_vis;           /* Kelvin damping parameter */
+  double g[3];                /* gravity */
+} mpm_material;
+
+typedef struct {
+  int32_t shape;              /* MPM_SHAPE_ORIG / MPM_SHAPE_GIMP */
+  int32_t scheme;             /* MPM_QUASISTATIC / MPM_NEWMARK */
+  double beta, gamma;         /* Newmark parameters (Sec. 3.2: 0.3025, 0.6) */
+  int32_t stabilize;          /* PPP on (1) / off (0), Eq. stab-term-ppp */
+  double tau_scale;           /* tau = tau_scale / (2 G), Eq. tau-white */
+  int32_t precision;          /* MPM_FP64 (MPM_MIXED reserved) */
+  double newton_rtol;         /* ||R^k|| / ||R^0|| test of Eq. newton-tolerance */
+  int32_t newton_max;         /* Newton iteration cap */
+  double newton_stag;         /* > 0: accept the round-off floor once
+                                 ||R^{k-1}|| <= newton_stag ||R^0|| and R^k fails
+                                 to halve it; 0 disables */
+  double krylov_rtol;         /* linear solve to rtol of the scaled residual */
+  int32_t krylov_restart;     /* FGMRES restart length (<= 64) */
+  int32_t krylov_max;         /* total Krylov iterations per Newton iteration */
+  int32_t profile;            /* bit mask of MPM_PROF_* classes timed with CUDA
+                                 events on the work stream (0 = none) */
+  void *stream;               /* cudaStream_t for all work; NULL = default stream */
+} mpm_options;
+
+/* Neumann data of one step: traction t^ per surface entry (n_surf*dim), and
+ * optionally the normal flux q^ (n_surf).  traction == NULL keeps the traction
+ * uploaded by the previous step; the applied traction is scale * traction. */
+typedef struct {
+  const double *traction;
+  const double *flux;
+  double scale;
+} mpm_loads;
+
+/* Dirichlet data per grid node (Sec. 2.4).  u_fixed/u_value are nnodes*dim,
+ * p_fixed/p_value are nnodes.  u_value is the prescribed displacement
+ * increment over the step (the grid is reset every step), p_value the
+ * prescribed pore pressure at t_{n+1}.  bcs == NULL keeps the previous data. */
+typedef struct {
+  const uint8_t *u_fixed;
+  const double *u_value;
+  const uint8_t *p_fixed;
+  const double *p_value;
+} mpm_bcs;
+
+/* Caller-owned host buffers, in the caller's original point order; any
+ * pointer may be NULL to skip that field. */
+typedef struct {
+  double *x, *u, *p;          /* n*dim, n*dim, n */
+  double *v, *a;              /* n*dim (Newmark state) */
+  double *F;                  /* n*dim*dim */
+  double *V;                  /* n current volumes */
+  double *lp;                 /* n*dim GIMP half lengths */
+  double *pd, *pdd;           /* n, dp/dt and d2p/dt2 (Newmark) */
+} mpm_particles_out;
+
+#define MPM_MAX_NEWTON 64
+
+typedef struct {
+  int32_t newton_iters;                    /* of the last step */
+  int32_t krylov_iters[MPM_MAX_NEWTON];    /* per Newton iteration of the last step */
+  double res_norm[MPM_MAX_NEWTON + 1];     /* ||R^k|| of the last step */
+  int32_t krylov_total;                    /* sum over the last step */
+  int64_t steps;                           /* completed steps */
+  double t;                                /* time reached */
+  int64_t nnzb;                            /* blocks of the last Jacobian */
+  int64_t kernel_launches;                 /* kernels launched by the last step */
+  double prof_ms[MPM_PROF_COUNT];          /* device time of the profiled classes, last step */
+  int64_t prof_launches[MPM_PROF_COUNT];   /* launches of the profiled classes, last step */
+} mpm_stats;
+
+/* Fills *o with the defaults: GIMP, quasi-static, beta 0.3025, gamma 0.6,
+ * PPP on with tau_W, FP64, Newton rtol 1e-8 (Eq. newton-tolerance), 25
+ * iterations, Krylov rtol 1e-8, restart 30, 3000 iterations. */
+void mpm_default_options(mpm_options *o);
+
+/* Creates a context and uploads the problem (Sec. 2.4 "given u0, p0"): the
+ * points, per-point E, nu and intrinsic permeability k (permeability, n
+ * values, m^2).  Allocates all device memory the run needs except what
+ * depends on the evolving sparsity.  *out receives the context, or NULL on
+ * error (the code says why). */
+int mpm_create(const mpm_grid *grid, const mpm_particles *particles, const mpm_material *material,
+               const double *permeability, const mpm_options *options, mpm_ctx **out);
+
+/* One load step t_n -> t_n + dt (Sec. 3.1 Stages 1-4): bin the points, map
+ * their state to the nodes (Eq. map-from-particles-to-nodes), Newton on the
+ * stabilized system (Eq. jacobian-system-stabilized-ppp) with the FGMRES
+ * linear solver, then update and convect the points (Sec. 3.5).  loads and
+ * bcs may be NULL (keep the previous ones).  Blocks until the step is done. */
+int mpm_step(mpm_ctx *ctx, double dt, const mpm_loads *loads, const mpm_bcs *bcs);
+
+/* Copies the point state into caller-owned host buffers (original order). */
+int mpm_read(const mpm_ctx *ctx, mpm_particles_out *out);
+
+int mpm_get_stats(const mpm_ctx *ctx, mpm_stats *stats);
+
+/* Human-readable description of the last error on ctx (never NULL). */
+const char *mpm_last_error(const mpm_ctx *ctx);
+
+/* Frees the context and all its device memory.  NULL is a no-op. */
+void mpm_destroy(mpm_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Inspection entry points.  They expose the intermediate results of one step
+ * so that each stage can be compared with an independent implementation.
+ * ---------------------------------------------------------------------- */
+
+/* Cell of every point (original order) and the cell-sorted order (original
+ * point ids sorted by (cell, id)) of the current state.  cell: n int32,
+ * order: n int64. */
+int mpm_debug_bin(mpm_ctx *ctx, int32_t *cell, int64_t *order);
+
+/* Runs Stage 1 and the sparsity build for a step of size dt from the current
+ * state, without solving; the inspection calls below then refer to it. */
+int mpm_debug_prepare(mpm_ctx *ctx, double dt, const mpm_loads *loads, const mpm_bcs *bcs);
+
+/* Block-CSR sparsity of the prepared step: nnodes+1 row pointers, then the
+ * block column indices (ascending per row).  Returns the number of blocks, or
+ * a negative code; with col_idx == NULL only the count is returned. */
+int64_t mpm_debug_pattern(mpm_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, int64_t cap);
+
+/* Lumped nodal mass M (nnodes) and Stage-1 nodal pressure P_n (nnodes) of the
+ * prepared step. */
+int mpm_debug_nodal(mpm_ctx *ctx, double *M, double *Pn);
+
+/* Residual R(X) (nnodes*(dim+1)) and the Jacobian block values (nnzb blocks of
+ * (dim+1)^2, row-major, in the pattern's order) at the nodal unknowns X
+ * (nnodes*(dim+1), node-interleaved [dU, P]) for the prepared step, exactly as
+ * the residual/Jacobian kernels produce them before Dirichlet elimination
+ * (apply_bc = 0) or after it (apply_bc = 1).  Jv may be NULL. */
+int mpm_debug_eval(mpm_ctx *ctx, const double *X, double *R, double *Jv, int32_t apply_bc);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UPMPM_MPM_H */

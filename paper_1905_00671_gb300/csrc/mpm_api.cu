@@ -1,0 +1,673 @@
+// mpm_api.cu -- the C-ABI of include/mpm.h and the host driver of one load
+// step (Sec. 3.1 Stages 1-4, Newton of Sec. 3.4).  The host only sequences
+// kernel launches and reads back one scalar per Newton / Krylov iteration;
+// every arithmetic step of the method runs in the kernels of this library.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "mpm_internal.cuh"
+
+namespace upmpm {
+
+DevView Ctx::view() const {
+  DevView v{};
+  v.n = n;
+  v.pf = pf;
+  v.pid = pid;
+  v.surf = surf;
+  v.cell = cell;
+  v.cell_start = cell_start;
+  v.sh_first = sh_first;
+  v.sh_cnt = sh_cnt;
+  v.sh_S = sh_S;
+  v.sh_dS = sh_dS;
+  v.sh_S0 = sh_S0;
+  v.m = m;
+  v.rec = rec;
+  v.M = M;
+  v.Pn = Pn;
+  v.vn = vn;
+  v.an = an;
+  v.pdn = pdn;
+  v.pddn = pddn;
+  v.fixed = fixed;
+  v.u_fixed = u_fixed;
+  v.u_value = u_value;
+  v.p_fixed = p_fixed;
+  v.p_value = p_value;
+  v.trac = trac;
+  v.flux = has_flux ? flux : nullptr;
+  v.err = err;
+  return v;
+}
+
+int check_cuda(Ctx &c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return MPM_OK;
+  c.last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return MPM_ERR_CUDA;
+}
+
+int read_dev_err(Ctx &c) {
+  cudaMemcpyAsync(c.h_err, c.err, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+  cudaError_t e = cudaStreamSynchronize(c.st);
+  if (e != cudaSuccess) return check_cuda(c, e, "kernel execution");
+  const int f = *c.h_err;
+  if (!f) return MPM_OK;
+  cudaMemsetAsync(c.err, 0, sizeof(int), c.st);
+  if (f & DE_OUT_OF_GRID) {
+    c.last_error = "a material point centre left the background grid";
+    return MPM_ERR_OUT_OF_GRID;
+  }
+  if (f & DE_NEG_J) {
+    c.last_error = "non-positive Jacobian det F at a material point";
+    return MPM_ERR_NEGATIVE_J;
+  }
+  if (f & DE_SUPPORT) {
+    c.last_error = "GIMP half length outside (0, h) or support wider than 4 nodes";
+    return MPM_ERR_BAD_ARG;
+  }
+  if (f & DE_SINGULAR) {
+    c.last_error = "singular diagonal block in the block-Jacobi preconditioner";
+    return MPM_ERR_NONFINITE;
+  }
+  c.last_error = "device error flag";
+  return MPM_ERR_CUDA;
+}
+
+void prof_begin(Ctx &c, int kind) {
+  if (!((c.opt.profile >> kind) & 1)) return;
+  if ((size_t)(2 * c.ev_used + 2) > c.ev.size()) {
+    if (c.ev.size() >= (1u << 15)) prof_collect(c);  // bounded pool: drain it
+    while ((size_t)(2 * c.ev_used + 2) > c.ev.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      c.ev.push_back(e);
+    }
+    c.ev_kind.resize(c.ev.size() / 2);
+  }
+  cudaEventRecord(c.ev[2 * c.ev_used], c.st);
+}
+
+void prof_end(Ctx &c, int kind) {
+  if (!((c.opt.profile >> kind) & 1)) return;
+  if ((size_t)(2 * c.ev_used + 2) > c.ev.size()) return;
+  cudaEventRecord(c.ev[2 * c.ev_used + 1], c.st);
+  c.ev_kind[c.ev_used] = kind;
+  ++c.ev_used;
+}
+
+void prof_collect(Ctx &c) {
+  if (c.ev_used == 0) return;
+  cudaStreamSynchronize(c.st);
+  for (int i = 0; i < c.ev_used; ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c.ev[2 * i], c.ev[2 * i + 1]) == cudaSuccess) {
+      c.stats.prof_ms[c.ev_kind[i]] += ms;
+      c.stats.prof_launches[c.ev_kind[i]] += 1;
+    }
+  }
+  c.ev_used = 0;
+}
+
+namespace {
+
+constexpr int TPB = 256;
+inline int nblk(int64_t n) { return (int)((n + TPB - 1) / TPB); }
+
+// Lame constants from (E, nu), mobility, PPP parameter tau_W = 1 / (2 G)
+// (Eq. tau-white) scaled by tau_scale, and the initial state of every field.
+template <int D>
+__global__ void k_init(int64_t n, double *pf, const double *__restrict__ x, const double *__restrict__ vol,
+                       const double *__restrict__ lp, const double *__restrict__ p0,
+                       const double *__restrict__ v0, const double *__restrict__ E,
+                       const double *__restrict__ nu, const double *__restrict__ k,
+                       const double *__restrict__ sn, const double *__restrict__ sa, double mu_f,
+                       double tau_scale, int stabilize, int64_t *pid) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  for (int f = 0; f < PF_COUNT; ++f) pf[f * n + p] = 0.0;
+  for (int i = 0; i < D; ++i) {
+    pf[(PF_X + i) * n + p] = x[p * D + i];
+    pf[(PF_LP + i) * n + p] = lp[p * D + i];
+    pf[(PF_LP0 + i) * n + p] = lp[p * D + i];
+    pf[(PF_F + i * D + i) * n + p] = 1.0;
+    if (v0) pf[(PF_VEL + i) * n + p] = v0[p * D + i];
+    if (sn) pf[(PF_SN + i) * n + p] = sn[p * D + i];
+  }
+  pf[PF_V * n + p] = vol[p];
+  pf[PF_P * n + p] = p0 ? p0[p] : 0.0;
+  const double e = E[p], v = nu[p];
+  const double lam = e * v / ((1.0 + v) * (1.0 - 2.0 * v));
+  const double G = e / (2.0 * (1.0 + v));
+  pf[PF_LAM * n + p] = lam;
+  pf[PF_G * n + p] = G;
+  pf[PF_KAP * n + p] = k[p] / mu_f;
+  pf[PF_TAU * n + p] = stabilize ? tau_scale / (2.0 * G) : 0.0;
+  pf[PF_SA * n + p] = sa ? sa[p] : 0.0;
+  pid[p] = p;
+}
+
+__global__ void k_scale_trac(int64_t m, const double *__restrict__ raw, double s, double *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) out[i] = s * raw[i];
+}
+
+// gather field f (comps components) into original point order
+__global__ void k_read_field(int64_t n, const double *__restrict__ pf, int f0, int comps,
+                             const int64_t *__restrict__ pid, double *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t o = pid[i];
+  for (int c = 0; c < comps; ++c) out[o * comps + c] = pf[(int64_t)(f0 + c) * n + i];
+}
+
+__global__ void k_read_cells(int64_t n, const int32_t *__restrict__ cell, const int64_t *__restrict__ pid,
+                             int32_t *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[pid[i]] = cell[i];
+}
+
+template <typename T>
+int dalloc(Ctx &c, T **p, int64_t count) {
+  if (count <= 0) count = 1;
+  if (cudaMalloc((void **)p, sizeof(T) * (size_t)count) != cudaSuccess) {
+    c.last_error = "device allocation failed";
+    return MPM_ERR_NO_MEMORY;
+  }
+  return MPM_OK;
+}
+
+int upload_loads(Ctx &c, const mpm_loads *L) {
+  if (!L) return MPM_OK;
+  const int64_t m = (int64_t)c.n_surf * c.d;
+  if (L->traction && m > 0)
+    if (cudaMemcpyAsync(c.trac_raw, L->traction, sizeof(double) * m, cudaMemcpyHostToDevice, c.st))
+      return check_cuda(c, cudaGetLastError(), "upload traction");
+  if (L->flux && c.n_surf > 0) {
+    cudaMemcpyAsync(c.flux, L->flux, sizeof(double) * c.n_surf, cudaMemcpyHostToDevice, c.st);
+    c.has_flux = 1;
+  }
+  c.trac_scale = L->scale;
+  if (m > 0) {
+    k_scale_trac<<<nblk(m), TPB, 0, c.st>>>(m, c.trac_raw, c.trac_scale, c.trac);
+    UPMPM_LAUNCH(c);
+  }
+  return check_cuda(c, cudaGetLastError(), "loads");
+}
+
+int upload_bcs(Ctx &c, const mpm_bcs *B) {
+  if (!B) return MPM_OK;
+  const int64_t nn = c.g.nnodes;
+  cudaStream_t s = c.st;
+  if (B->u_fixed) cudaMemcpyAsync(c.u_fixed, B->u_fixed, nn * c.d, cudaMemcpyHostToDevice, s);
+  if (B->u_value) cudaMemcpyAsync(c.u_value, B->u_value, sizeof(double) * nn * c.d, cudaMemcpyHostToDevice, s);
+  if (B->p_fixed) cudaMemcpyAsync(c.p_fixed, B->p_fixed, nn, cudaMemcpyHostToDevice, s);
+  if (B->p_value) cudaMemcpyAsync(c.p_value, B->p_value, sizeof(double) * nn, cudaMemcpyHostToDevice, s);
+  return check_cuda(c, cudaGetLastError(), "bcs");
+}
+
+// Stage 1 and everything fixed over the Newton loop of one step.
+int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
+  if (!(dt > 0.0) || !isfinite(dt)) {
+    c.last_error = "dt must be positive and finite";
+    return MPM_ERR_BAD_ARG;
+  }
+  int rc = upload_loads(c, L);
+  if (!rc) rc = upload_bcs(c, B);
+  if (rc) return rc;
+  c.s.dt = dt;
+  rc = run_binning(c);
+  if (rc) return rc;
+  run_shape(c);
+  run_mass(c);
+  rc = read_dev_err(c);
+  if (rc) return rc;
+  run_p2g(c);
+  rc = run_pattern(c);
+  if (rc) return rc;
+  run_initial_guess(c);
+  rc = read_dev_err(c);
+  if (rc) return rc;
+  c.prepared = true;
+  return MPM_OK;
+}
+
+int eval_residual(Ctx &c, double *rnorm) {
+  run_point_eval(c, c.X);
+  int rc = read_dev_err(c);
+  if (rc) return rc;
+  run_residual(c, c.X, c.R, 1);
+  *rnorm = run_norm(c, c.R);
+  if (!isfinite(*rnorm)) {
+    c.last_error = "non-finite residual";
+    return MPM_ERR_NONFINITE;
+  }
+  return MPM_OK;
+}
+
+int newton(Ctx &c) {
+  mpm_stats &st = c.stats;
+  st.newton_iters = 0;
+  st.krylov_total = 0;
+  double rk;
+  int rc = eval_residual(c, &rk);
+  if (rc) return rc;
+  const double r0 = rk;
+  st.res_norm[0] = r0;
+  double prev = r0;
+  int k = 0;
+  while (true) {
+    if (r0 == 0.0 || rk <= c.opt.newton_rtol * r0) break;
+    if (c.opt.newton_stag > 0.0 && k >= 2 && prev <= c.opt.newton_stag * r0 && rk > 0.5 * prev) break;
+    if (k >= c.opt.newton_max || k >= MPM_MAX_NEWTON) {
+      c.last_error = "Newton did not reach the residual tolerance";
+      return MPM_ERR_NEWTON_DIVERGED;
+    }
+    run_jacobian(c, 1);
+    run_scale_system(c, c.rhs, c.R);
+    run_block_jacobi(c);
+    rc = read_dev_err(c);
+    if (rc) return rc;
+    int its = 0;
+    rc = run_fgmres(c, c.rhs, c.dX, c.opt.krylov_rtol, c.opt.krylov_max, &its);
+    st.krylov_iters[k] = its;
+    st.krylov_total += its;
+    if (rc) {
+      if (rc == MPM_ERR_KRYLOV_STAGNATED) c.last_error = "FGMRES hit its iteration cap";
+      else if (rc == MPM_ERR_NONFINITE) c.last_error = "non-finite value in FGMRES";
+      return rc;
+    }
+    run_unscale_add(c, c.X, c.dX);
+    prev = rk;
+    rc = eval_residual(c, &rk);
+    if (rc) return rc;
+    ++k;
+    st.res_norm[k] = rk;
+    st.newton_iters = k;
+  }
+  return MPM_OK;
+}
+
+int do_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
+  c.launches = 0;
+  c.ev_used = 0;
+  for (int k = 0; k < MPM_PROF_COUNT; ++k) {
+    c.stats.prof_ms[k] = 0.0;
+    c.stats.prof_launches[k] = 0;
+  }
+  int rc = prepare_step(c, dt, L, B);
+  if (rc) return rc;
+  rc = newton(c);
+  if (rc) return rc;
+  run_g2p(c);
+  rc = read_dev_err(c);
+  if (rc) return rc;
+  prof_collect(c);
+  c.prepared = false;
+  c.t += dt;
+  c.steps += 1;
+  c.stats.steps = c.steps;
+  c.stats.t = c.t;
+  c.stats.nnzb = c.nnzb;
+  c.stats.kernel_launches = c.launches;
+  return MPM_OK;
+}
+
+void free_all(Ctx &c) {
+  for (cudaEvent_t e : c.ev) cudaEventDestroy(e);
+  c.ev.clear();
+  void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
+                  c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS,
+                  c.sh_S0, c.m, c.rec, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.fixed, c.u_fixed,
+                  c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
+                  c.row_ptr, c.row_of, c.col, c.row_mask, c.val, c.dscale, c.dinv, c.X, c.R, c.dX,
+                  c.rhs, c.w, c.V, c.Z, c.H, c.gvec, c.cs, c.sn, c.yv, c.hcol, c.part, c.scal,
+                  c.scan_tmp};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (c.h_err) cudaFreeHost(c.h_err);
+  if (c.h_scalar) cudaFreeHost(c.h_scalar);
+}
+
+}  // namespace
+}  // namespace upmpm
+
+using namespace upmpm;
+
+struct mpm_ctx {
+  Ctx c;
+};
+
+extern "C" {
+
+void mpm_default_options(mpm_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->shape = MPM_SHAPE_GIMP;
+  o->scheme = MPM_QUASISTATIC;
+  o->beta = 0.3025;
+  o->gamma = 0.6;
+  o->stabilize = 1;
+  o->tau_scale = 1.0;
+  o->precision = MPM_FP64;
+  o->newton_rtol = 1e-8;
+  o->newton_max = 25;
+  o->newton_stag = 0.0;
+  o->krylov_rtol = 1e-8;
+  o->krylov_restart = 30;
+  o->krylov_max = 3000;
+  o->stream = nullptr;
+}
+
+int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material *mat,
+               const double *permeability, const mpm_options *opt, mpm_ctx **out) {
+  if (!out) return MPM_ERR_BAD_ARG;
+  *out = nullptr;
+  if (!grid || !P || !mat || !permeability || !opt) return MPM_ERR_BAD_ARG;
+  if (grid->dim != 2 && grid->dim != 3) return MPM_ERR_BAD_ARG;
+  if (!(grid->h > 0.0) || P->n <= 0 || !P->x || !P->vol || !P->lp || !mat->E || !mat->nu)
+    return MPM_ERR_BAD_ARG;
+  for (int k = 0; k < grid->dim; ++k)
+    if (grid->ncell[k] < 1) return MPM_ERR_BAD_ARG;
+  if (P->n > INT32_MAX / 2) return MPM_ERR_BAD_ARG;
+  if (opt->krylov_restart < 1 || opt->krylov_restart > 63) return MPM_ERR_BAD_ARG;
+  if (P->n_surf < 0 || (P->n_surf > 0 && (!P->surf_id || !P->surf_normal || !P->surf_area)))
+    return MPM_ERR_BAD_ARG;
+  if (!(mat->mu_f > 0.0)) return MPM_ERR_BAD_ARG;
+  // every surface id must address an entry of the load arrays
+  if (P->surf_id)
+    for (int64_t i = 0; i < P->n; ++i)
+      if (P->surf_id[i] < -1 || P->surf_id[i] >= P->n_surf) return MPM_ERR_BAD_ARG;
+
+  mpm_ctx *h = new (std::nothrow) mpm_ctx();
+  if (!h) return MPM_ERR_NO_MEMORY;
+  Ctx &c = h->c;
+  c.opt = *opt;
+  c.st = (cudaStream_t)opt->stream;
+  c.d = grid->dim;
+  c.nb = c.d + 1;
+  c.shape = opt->shape;
+  c.dyn = opt->scheme == MPM_NEWMARK;
+  c.stabilize = opt->stabilize;
+  c.tau_scale = opt->tau_scale;
+  c.precision = opt->precision;
+  c.m_restart = opt->krylov_restart;
+  GridP &g = c.g;
+  g.d = c.d;
+  g.nnodes = 1;
+  g.ncells = 1;
+  for (int k = 0; k < 3; ++k) {
+    const bool used = k < c.d;
+    g.nc[k] = used ? grid->ncell[k] : 1;
+    g.nn[k] = used ? grid->ncell[k] + 1 : 1;
+    g.org[k] = used ? grid->origin[k] : 0.0;
+    g.nnodes *= g.nn[k];
+    g.ncells *= g.nc[k];
+  }
+  g.h = grid->h;
+  if (g.nnodes > INT32_MAX / 16) {
+    delete h;
+    return MPM_ERR_BAD_ARG;
+  }
+  StepP &s = c.s;
+  s.beta = opt->beta;
+  s.gamma = opt->gamma;
+  s.rho_f = mat->rho_f;
+  s.rho_s = mat->rho_s;
+  s.phi0 = mat->phi0;
+  s.alpha_vis = c.dyn ? mat->alpha_vis : 0.0;
+  for (int k = 0; k < 3; ++k) s.g[k] = k < c.d ? mat->g[k] : 0.0;
+  c.n = P->n;
+  c.n_surf = P->n_surf;
+
+  const int64_t n = c.n, nn = g.nnodes, nc = g.ncells, N = (int64_t)c.nb * nn;
+  const int d = c.d, nb = c.nb, m = c.m_restart;
+  int rc = MPM_OK;
+  auto A = [&](auto **p, int64_t cnt) {
+    if (!rc) rc = dalloc(c, p, cnt);
+  };
+  A(&c.pf, PF_COUNT * n);
+  A(&c.pf_alt, PF_COUNT * n);
+  A(&c.pid, n);
+  A(&c.pid_alt, n);
+  A(&c.surf, n);
+  A(&c.surf_alt, n);
+  A(&c.cell, n);
+  A(&c.cell_tmp, n);
+  A(&c.cell_start, nc + 1);
+  A(&c.cell_cursor, nc + 1);
+  A(&c.perm, n);
+  A(&c.sh_first, 3 * n);
+  A(&c.sh_cnt, n);
+  A(&c.sh_S, 3 * MAXS * n);
+  A(&c.sh_dS, 3 * MAXS * n);
+  A(&c.sh_S0, 3 * MAXS * n);
+  A(&c.m, n);
+  A(&c.rec, RC_COUNT * n);
+  A(&c.M, nn);
+  A(&c.Pn, nn);
+  A(&c.vn, d * nn);
+  A(&c.an, d * nn);
+  A(&c.pdn, nn);
+  A(&c.pddn, nn);
+  A(&c.fixed, N);
+  A(&c.u_fixed, d * nn);
+  A(&c.p_fixed, nn);
+  A(&c.u_value, d * nn);
+  A(&c.p_value, nn);
+  A(&c.trac, (int64_t)c.n_surf * d);
+  A(&c.trac_raw, (int64_t)c.n_surf * d);
+  A(&c.flux, c.n_surf);
+  A(&c.err, 1);
+  A(&c.row_nnz, nn + 1);
+  A(&c.row_ptr, nn + 1);
+  A(&c.row_mask, nn * 6);
+  A(&c.dscale, N);
+  A(&c.dinv, nn * nb * nb);
+  A(&c.X, N);
+  A(&c.R, N);
+  A(&c.dX, N);
+  A(&c.rhs, N);
+  A(&c.w, std::max<int64_t>(N, 9 * n));
+  A(&c.V, (int64_t)(m + 1) * N);
+  A(&c.Z, (int64_t)m * N);
+  A(&c.H, (int64_t)(m + 1) * m);
+  A(&c.gvec, m + 1);
+  A(&c.cs, m);
+  A(&c.sn, m);
+  A(&c.yv, m);
+  A(&c.hcol, 128);
+  A(&c.part, 304 * 64);
+  A(&c.scal, 8);
+  c.scan_cap = 4096;
+  A(&c.scan_tmp, c.scan_cap);
+  if (!rc && cudaHostAlloc((void **)&c.h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess)
+    rc = MPM_ERR_NO_MEMORY;
+  if (!rc && cudaHostAlloc((void **)&c.h_scalar, 8 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+    rc = MPM_ERR_NO_MEMORY;
+  if (rc) {
+    free_all(c);
+    delete h;
+    return rc;
+  }
+  cudaMemsetAsync(c.err, 0, sizeof(int), c.st);
+  cudaMemsetAsync(c.row_nnz, 0, sizeof(int32_t) * (nn + 1), c.st);  // [nn] stays 0 for the scan
+  cudaMemsetAsync(c.u_fixed, 0, d * nn, c.st);
+  cudaMemsetAsync(c.p_fixed, 0, nn, c.st);
+  cudaMemsetAsync(c.u_value, 0, sizeof(double) * d * nn, c.st);
+  cudaMemsetAsync(c.p_value, 0, sizeof(double) * nn, c.st);
+  cudaMemsetAsync(c.vn, 0, sizeof(double) * d * nn, c.st);
+  cudaMemsetAsync(c.an, 0, sizeof(double) * d * nn, c.st);
+  cudaMemsetAsync(c.pdn, 0, sizeof(double) * nn, c.st);
+  cudaMemsetAsync(c.pddn, 0, sizeof(double) * nn, c.st);
+  if (c.n_surf > 0) {
+    cudaMemsetAsync(c.trac, 0, sizeof(double) * c.n_surf * d, c.st);
+    cudaMemsetAsync(c.trac_raw, 0, sizeof(double) * c.n_surf * d, c.st);
+  }
+
+  // stage the inputs on the device (temporary buffers), then initialise
+  double *tmp = nullptr;
+  const int64_t tcount = n * (4 * d + 7);
+  rc = dalloc(c, &tmp, tcount);
+  if (rc) {
+    free_all(c);
+    delete h;
+    return rc;
+  }
+  double *dx = tmp, *dvol = dx + n * d, *dlp = dvol + n, *dp0 = dlp + n * d, *dv0 = dp0 + n,
+         *dE = dv0 + n * d, *dnu = dE + n, *dk = dnu + n, *dsn = dk + n, *dsa = dsn + n * d;
+  auto H2D = [&](double *dst, const double *src, int64_t cnt) {
+    if (src) cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyHostToDevice, c.st);
+  };
+  H2D(dx, P->x, n * d);
+  H2D(dvol, P->vol, n);
+  H2D(dlp, P->lp, n * d);
+  H2D(dp0, P->p0, n);
+  H2D(dv0, P->v0, n * d);
+  H2D(dE, mat->E, n);
+  H2D(dnu, mat->nu, n);
+  H2D(dk, permeability, n);
+  H2D(dsn, P->surf_normal, n * d);
+  H2D(dsa, P->surf_area, n);
+  if (P->surf_id)
+    cudaMemcpyAsync(c.surf, P->surf_id, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c.st);
+  else
+    cudaMemsetAsync(c.surf, 0xff, sizeof(int32_t) * n, c.st);
+  if (d == 2)
+    k_init<2><<<nblk(n), TPB, 0, c.st>>>(n, c.pf, dx, dvol, dlp, P->p0 ? dp0 : nullptr,
+                                          P->v0 ? dv0 : nullptr, dE, dnu, dk,
+                                          P->surf_normal ? dsn : nullptr, P->surf_area ? dsa : nullptr,
+                                          mat->mu_f, c.tau_scale, c.stabilize, c.pid);
+  else
+    k_init<3><<<nblk(n), TPB, 0, c.st>>>(n, c.pf, dx, dvol, dlp, P->p0 ? dp0 : nullptr,
+                                          P->v0 ? dv0 : nullptr, dE, dnu, dk,
+                                          P->surf_normal ? dsn : nullptr, P->surf_area ? dsa : nullptr,
+                                          mat->mu_f, c.tau_scale, c.stabilize, c.pid);
+  cudaError_t e = cudaStreamSynchronize(c.st);
+  cudaFree(tmp);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    rc = check_cuda(c, e, "create");
+    free_all(c);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return MPM_OK;
+}
+
+int mpm_step(mpm_ctx *h, double dt, const mpm_loads *loads, const mpm_bcs *bcs) {
+  if (!h) return MPM_ERR_BAD_ARG;
+  return do_step(h->c, dt, loads, bcs);
+}
+
+int mpm_read(const mpm_ctx *hc, mpm_particles_out *o) {
+  if (!hc || !o) return MPM_ERR_BAD_ARG;
+  Ctx &c = const_cast<mpm_ctx *>(hc)->c;
+  const int64_t n = c.n;
+  const int d = c.d;
+  struct Item {
+    double *dst;
+    int f0, comps;
+  } items[] = {{o->x, PF_X, d}, {o->u, PF_U, d}, {o->p, PF_P, 1}, {o->v, PF_VEL, d},
+               {o->a, PF_ACC, d}, {o->F, PF_F, d * d}, {o->V, PF_V, 1}, {o->lp, PF_LP, d},
+               {o->pd, PF_PD, 1}, {o->pdd, PF_PDD, 1}};
+  for (const Item &it : items) {
+    if (!it.dst) continue;
+    k_read_field<<<nblk(n), TPB, 0, c.st>>>(n, c.pf, it.f0, it.comps, c.pid, c.w);
+    cudaMemcpyAsync(it.dst, c.w, sizeof(double) * n * it.comps, cudaMemcpyDeviceToHost, c.st);
+    cudaError_t e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return check_cuda(c, e, "read");
+  }
+  return check_cuda(c, cudaGetLastError(), "read");
+}
+
+int mpm_get_stats(const mpm_ctx *h, mpm_stats *s) {
+  if (!h || !s) return MPM_ERR_BAD_ARG;
+  *s = h->c.stats;
+  return MPM_OK;
+}
+
+const char *mpm_last_error(const mpm_ctx *h) {
+  if (!h) return "null context";
+  return h->c.last_error.c_str();
+}
+
+void mpm_destroy(mpm_ctx *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->c.st);
+  free_all(h->c);
+  delete h;
+}
+
+int mpm_debug_bin(mpm_ctx *h, int32_t *cell, int64_t *order) {
+  if (!h || !cell || !order) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  int rc = run_binning(c);
+  if (rc) return rc;
+  int32_t *tmp = reinterpret_cast<int32_t *>(c.w);
+  k_read_cells<<<nblk(c.n), TPB, 0, c.st>>>(c.n, c.cell, c.pid, tmp);
+  cudaMemcpyAsync(cell, tmp, sizeof(int32_t) * c.n, cudaMemcpyDeviceToHost, c.st);
+  cudaMemcpyAsync(order, c.pid, sizeof(int64_t) * c.n, cudaMemcpyDeviceToHost, c.st);
+  return check_cuda(c, cudaStreamSynchronize(c.st), "debug_bin");
+}
+
+int mpm_debug_prepare(mpm_ctx *h, double dt, const mpm_loads *loads, const mpm_bcs *bcs) {
+  if (!h) return MPM_ERR_BAD_ARG;
+  return prepare_step(h->c, dt, loads, bcs);
+}
+
+int64_t mpm_debug_pattern(mpm_ctx *h, int64_t *row_ptr, int32_t *col_idx, int64_t cap) {
+  if (!h || !row_ptr) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  const int64_t nn = c.g.nnodes;
+  int32_t *tmp = new (std::nothrow) int32_t[nn + 1];
+  if (!tmp) return MPM_ERR_NO_MEMORY;
+  cudaMemcpyAsync(tmp, c.row_ptr, sizeof(int32_t) * (nn + 1), cudaMemcpyDeviceToHost, c.st);
+  cudaError_t e = cudaStreamSynchronize(c.st);
+  for (int64_t i = 0; i <= nn; ++i) row_ptr[i] = tmp[i];
+  delete[] tmp;
+  if (e != cudaSuccess) return check_cuda(c, e, "debug_pattern");
+  if (col_idx) {
+    if (cap < c.nnzb) return MPM_ERR_BAD_ARG;
+    cudaMemcpyAsync(col_idx, c.col, sizeof(int32_t) * c.nnzb, cudaMemcpyDeviceToHost, c.st);
+    e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return check_cuda(c, e, "debug_pattern");
+  }
+  return c.nnzb;
+}
+
+int mpm_debug_nodal(mpm_ctx *h, double *M, double *Pn) {
+  if (!h) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  if (M) cudaMemcpyAsync(M, c.M, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
+  if (Pn) cudaMemcpyAsync(Pn, c.Pn, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
+  return check_cuda(c, cudaStreamSynchronize(c.st), "debug_nodal");
+}
+
+int mpm_debug_eval(mpm_ctx *h, const double *X, double *R, double *Jv, int32_t apply_bc) {
+  if (!h || !X || !R) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  const int64_t N = c.N();
+  cudaMemcpyAsync(c.dX, X, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
+  run_point_eval(c, c.dX);
+  int rc = read_dev_err(c);
+  if (rc) return rc;
+  run_residual(c, c.dX, c.R, apply_bc);
+  cudaMemcpyAsync(R, c.R, sizeof(double) * N, cudaMemcpyDeviceToHost, c.st);
+  if (Jv) {
+    run_jacobian(c, apply_bc);
+    cudaMemcpyAsync(Jv, c.val, sizeof(double) * c.nnzb * c.nb * c.nb, cudaMemcpyDeviceToHost, c.st);
+  }
+  return check_cuda(c, cudaStreamSynchronize(c.st), "debug_eval");
+}
+
+}  // extern "C"

@@ -1,0 +1,546 @@
+// mpm_assemble.cu -- Stage 2 evaluation of the discrete equations:
+//   sparsity of the block Jacobian (node b couples with node a iff one point
+//   has both in its support),
+//   per-point kinematics, Kirchhoff stress, Darcy flux and PPP terms of the
+//   current Newton iterate (Sec. 3.3 pull-back to t_n),
+//   residual R = [R_mom; R_mass + R_stab] (Eqs. residual-momentum,
+//   residual-mass, stab-term-ppp) gathered per node row,
+//   Jacobian blocks [A B1; B2 C + C_stab] (Eq. jacobian-system-stabilized-ppp)
+//   gathered per block, with the Newmark linearization of Eq.
+//   newmark-linearization and delta ln J = div u for the quasi-static form.
+//
+// Design: gather, not scatter.  Points are cell-sorted, so the points that
+// can touch node a live in a small box of cells around it.  The residual is
+// computed by one thread per node row and each Jacobian block by one thread,
+// each summing its points in a fixed order: no floating-point atomics, results
+// are deterministic, and every (point, a, b) block term is computed exactly
+// once.  Per-point quantities that do not depend on (a, b) are computed once
+// per Newton iterate by k_point_eval and stored as structure-of-arrays
+// records.
+#include <math.h>
+
+#include "mpm_internal.cuh"
+
+namespace upmpm {
+
+namespace {
+
+constexpr int TPB = 256;
+inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
+
+constexpr int MASKW = 6;  // 64-bit words for 7^3 = 343 offsets in [-3, 3]^3
+
+// Support box of point q along each axis, and whether node coordinate ac lies in
+// it (off = slot of that node).
+template <int D>
+__device__ inline bool in_box(const DevView &v, int64_t q, const int ac[3], int off[3]) {
+  const int64_t n = v.n;
+  const int packed = v.sh_cnt[q];
+  off[0] = off[1] = off[2] = 0;
+  for (int k = 0; k < D; ++k) {
+    const int o = ac[k] - v.sh_first[k * n + q];
+    if (o < 0 || o >= unpack_cnt(packed, k)) return false;
+    off[k] = o;
+  }
+  return true;
+}
+
+// S_a, S0_a and the t_n-gradient Gn_a of the node at slots off of point q.
+template <int D>
+__device__ inline void node_basis(const DevView &v, int64_t q, const int off[3], double &S,
+                                  double &S0, double Gn[3]) {
+  const int64_t n = v.n;
+  double s[3] = {1.0, 1.0, 1.0}, ds[3] = {0.0, 0.0, 0.0}, s0[3] = {1.0, 1.0, 1.0};
+  for (int k = 0; k < D; ++k) {
+    s[k] = v.sh_S[(k * MAXS + off[k]) * n + q];
+    ds[k] = v.sh_dS[(k * MAXS + off[k]) * n + q];
+    s0[k] = v.sh_S0[(k * MAXS + off[k]) * n + q];
+  }
+  S = s[0] * s[1] * s[2];
+  S0 = s0[0] * s0[1] * s0[2];
+  Gn[0] = ds[0] * s[1] * s[2];
+  Gn[1] = s[0] * ds[1] * s[2];
+  Gn[2] = s[0] * s[1] * ds[2];
+}
+
+// g = Gn . dF^{-1}
+template <int D>
+__device__ inline void spatial_grad(const DevView &v, int64_t q, const double Gn[3], double g[3]) {
+  const int64_t n = v.n;
+  for (int j = 0; j < D; ++j) {
+    double s = 0.0;
+    for (int k = 0; k < D; ++k) s += Gn[k] * v.rec[(RC_FINV + k * D + j) * n + q];
+    g[j] = s;
+  }
+}
+
+// ---------------------------------------------------------------- pattern
+template <int D, bool GIMP>
+__global__ void k_pattern_count(GridP g, DevView v, uint64_t *__restrict__ mask,
+                                int32_t *__restrict__ row_nnz) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  int ac[3];
+  node_coords(g, a, ac);
+  uint64_t mk[MASKW] = {0, 0, 0, 0, 0, 0};
+  {  // self coupling
+    const int bit = 3 + 7 * (D > 1 ? 3 : 0) + 49 * (D > 2 ? 3 : 0);
+    mk[bit >> 6] |= 1ull << (bit & 63);
+  }
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) cand_range<GIMP>(ac[k], g.nc[k], lo[k], hi[k]);
+  const int64_t n = v.n;
+  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
+    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
+      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
+        const int64_t cid = cell_index(g, c0, c1, c2);
+        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
+          int off[3];
+          if (!in_box<D>(v, q, ac, off)) continue;
+          const int packed = v.sh_cnt[q];
+          int ob[3] = {0, 0, 0}, oe[3] = {0, 0, 0};
+          for (int k = 0; k < D; ++k) {
+            ob[k] = v.sh_first[k * n + q] - ac[k];
+            oe[k] = ob[k] + unpack_cnt(packed, k) - 1;
+          }
+          for (int o2 = ob[2]; o2 <= oe[2]; ++o2)
+            for (int o1 = ob[1]; o1 <= oe[1]; ++o1)
+              for (int o0 = ob[0]; o0 <= oe[0]; ++o0) {
+                const int bit = (o0 + 3) + 7 * (D > 1 ? o1 + 3 : 0) + 49 * (D > 2 ? o2 + 3 : 0);
+                mk[bit >> 6] |= 1ull << (bit & 63);
+              }
+        }
+      }
+  int cnt = 0;
+  for (int w = 0; w < MASKW; ++w) {
+    mask[a * MASKW + w] = mk[w];
+    cnt += __popcll(mk[w]);
+  }
+  row_nnz[a] = cnt;
+}
+
+// Offsets in ascending bit order are ascending node indices (the z offset is
+// most significant, then y, then x), so each row's columns come out sorted.
+template <int D>
+__global__ void k_pattern_fill(GridP g, const uint64_t *__restrict__ mask,
+                               const int32_t *__restrict__ row_ptr, int32_t *__restrict__ col,
+                               int32_t *__restrict__ row_of) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  int ac[3];
+  node_coords(g, a, ac);
+  int32_t pos = row_ptr[a];
+  for (int w = 0; w < MASKW; ++w) {
+    uint64_t mk = mask[a * MASKW + w];
+    while (mk) {
+      const int bit = w * 64 + __ffsll((long long)mk) - 1;
+      mk &= mk - 1;
+      const int o0 = bit % 7 - 3, o1 = (bit / 7) % 7 - 3, o2 = bit / 49 - 3;
+      const int bc[3] = {ac[0] + o0, ac[1] + (D > 1 ? o1 : 0), ac[2] + (D > 2 ? o2 : 0)};
+      col[pos] = (int32_t)node_index(g, bc);
+      row_of[pos] = (int32_t)a;
+      ++pos;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- Dirichlet
+// Fixed DOFs: Dirichlet data, and every DOF of an inactive node (no mass).
+// Initial Newton guess: dU = prescribed increment or 0, P = p^ or P_n.
+template <int D>
+__global__ void k_initial_guess(GridP g, DevView v, double *__restrict__ X) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  constexpr int NB = D + 1;
+  const bool inactive = !(v.M[a] > 0.0);
+  for (int k = 0; k < D; ++k) {
+    const bool uf = v.u_fixed[a * D + k] != 0;
+    v.fixed[a * NB + k] = (inactive || uf) ? 1 : 0;
+    X[a * NB + k] = inactive ? 0.0 : (uf ? v.u_value[a * D + k] : 0.0);
+  }
+  const bool pfx = v.p_fixed[a] != 0;
+  v.fixed[a * NB + D] = (inactive || pfx) ? 1 : 0;
+  X[a * NB + D] = inactive ? 0.0 : (pfx ? v.p_value[a] : v.Pn[a]);
+}
+
+// ---------------------------------------------------------------- points
+template <int D, bool DYN>
+__global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restrict__ X) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = v.n;
+  if (p >= n) return;
+  constexpr int NB = D + 1;
+  const int64_t nn = g.nnodes;
+  const double dt = s.dt, b = s.beta, gm = s.gamma;
+  const int packed = v.sh_cnt[p];
+  int f[3], cn[3];
+  for (int k = 0; k < 3; ++k) {
+    f[k] = v.sh_first[k * n + p];
+    cn[k] = unpack_cnt(packed, k);
+  }
+  double dF[9] = {0}, gPn[3] = {0, 0, 0}, gVn[9] = {0}, ah[3] = {0, 0, 0};
+  double ph = 0.0, pdev = 0.0;
+  for (int k = 0; k < D; ++k) dF[k * D + k] = 1.0;
+  for (int s2 = 0; s2 < cn[2]; ++s2)
+    for (int s1 = 0; s1 < cn[1]; ++s1)
+      for (int s0 = 0; s0 < cn[0]; ++s0) {
+        const int off[3] = {s0, s1, s2};
+        double Sa, S0a, Gn[3];
+        node_basis<D>(v, p, off, Sa, S0a, Gn);
+        const int nc3[3] = {f[0] + s0, f[1] + s1, f[2] + s2};
+        const int64_t a = node_index(g, nc3);
+        const double P = X[a * NB + D];
+        for (int i = 0; i < D; ++i) {
+          const double dU = X[a * NB + i];
+          for (int k = 0; k < D; ++k) dF[i * D + k] += dU * Gn[k];
+        }
+        ph += Sa * P;
+        for (int k = 0; k < D; ++k) gPn[k] += P * Gn[k];
+        if (DYN) {
+          for (int i = 0; i < D; ++i) {
+            const double dU = X[a * NB + i];
+            const double vn = v.vn[i * nn + a], an = v.an[i * nn + a];
+            const double aa = dU / (b * dt * dt) - vn / (b * dt) + (1.0 - 1.0 / (2.0 * b)) * an;
+            const double va = gm / (b * dt) * dU + (1.0 - gm / b) * vn + (1.0 - gm / (2.0 * b)) * dt * an;
+            ah[i] += Sa * aa;
+            for (int k = 0; k < D; ++k) gVn[i * D + k] += va * Gn[k];
+          }
+          const double pda = gm / (b * dt) * (P - v.Pn[a]) + (1.0 - gm / b) * v.pdn[a] +
+                             (1.0 - gm / (2.0 * b)) * dt * v.pddn[a];
+          pdev += (Sa - S0a) * pda;
+        } else {
+          pdev += (Sa - S0a) * (P - v.Pn[a]) / dt;
+        }
+      }
+  const double dJ = det_d<D>(dF);
+  if (!(dJ > 0.0)) {
+    atomicOr(v.err, DE_NEG_J);
+    return;
+  }
+  double fi[9], Fn[9], F[9], bl[9];
+  inv_d<D>(dF, fi);
+  const double *pf = v.pf;
+  for (int i = 0; i < D * D; ++i) Fn[i] = pf[(PF_F + i) * n + p];
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < D; ++k) acc += dF[i * D + k] * Fn[k * D + j];
+      F[i * D + j] = acc;
+    }
+  const double Jn = det_d<D>(Fn), J = det_d<D>(F);
+  if (!(J > 0.0)) {
+    atomicOr(v.err, DE_NEG_J);
+    return;
+  }
+  const double lnJ = log(J);
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < D; ++k) acc += F[i * D + k] * F[j * D + k];
+      bl[i * D + j] = acc;
+    }
+  const double lam = pf[PF_LAM * n + p], G = pf[PF_G * n + p];
+  const double Vn = pf[PF_V * n + p], kap = pf[PF_KAP * n + p], tau = pf[PF_TAU * n + p];
+  const double mu_p = G - lam * lnJ;
+  const double vol = dJ * Vn;
+  double *rec = v.rec;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      rec[(RC_FINV + i * D + j) * n + p] = fi[i * D + j];
+      rec[(RC_TAU + i * D + j) * n + p] = G * (bl[i * D + j] - (i == j ? 1.0 : 0.0)) + (i == j ? lam * lnJ : 0.0);
+    }
+  double gp[3] = {0, 0, 0}, gv[9] = {0};
+  for (int j = 0; j < D; ++j) {
+    double acc = 0.0;
+    for (int k = 0; k < D; ++k) acc += gPn[k] * fi[k * D + j];
+    gp[j] = acc;
+  }
+  double divv;
+  if (DYN) {
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < D; ++k) acc += gVn[i * D + k] * fi[k * D + j];
+        gv[i * D + j] = acc;
+      }
+    divv = 0.0;
+    for (int i = 0; i < D; ++i) divv += gv[i * D + i];
+    double trD = divv;
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        rec[(RC_GV + i * D + j) * n + p] = gv[i * D + j];
+        const double Dij = 0.5 * (gv[i * D + j] + gv[j * D + i]);
+        rec[(RC_SVIS + i * D + j) * n + p] =
+            s.alpha_vis * ((i == j ? lam * trD : 0.0) + 2.0 * mu_p * Dij);
+      }
+  } else {
+    divv = log(dJ) / dt;
+  }
+  const double m = v.m[p];
+  for (int j = 0; j < D; ++j) {
+    rec[(RC_GP + j) * n + p] = gp[j];
+    rec[(RC_W + j) * n + p] = gp[j] - s.rho_f * (s.g[j] - ah[j]);
+    rec[(RC_FRC + j) * n + p] = m * (s.g[j] - ah[j]);
+  }
+  rec[RC_CS * n + p] = Vn / Jn;
+  rec[RC_VOL * n + p] = vol;
+  rec[RC_PH * n + p] = ph;
+  rec[RC_MUP * n + p] = mu_p;
+  rec[RC_LAM * n + p] = lam;
+  rec[RC_KV * n + p] = vol * kap;
+  rec[RC_CST * n + p] = (DYN ? tau * gm / (b * dt) : tau / dt) * Vn;
+  rec[RC_RST * n + p] = tau * Vn * pdev;
+  rec[RC_DIVV * n + p] = vol * divv;
+  rec[RC_B2 * n + p] = DYN ? vol * (gm / (b * dt) + divv) : vol * (1.0 + log(dJ)) / dt;
+  rec[RC_MS * n + p] = DYN ? m / (b * dt * dt) : 0.0;
+}
+
+// ---------------------------------------------------------------- residual
+template <int D, bool GIMP, bool DYN>
+__global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply_bc) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  constexpr int NB = D + 1;
+  const int64_t n = v.n;
+  int ac[3];
+  node_coords(g, a, ac);
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) cand_range<GIMP>(ac[k], g.nc[k], lo[k], hi[k]);
+  double r[NB];
+  for (int i = 0; i < NB; ++i) r[i] = 0.0;
+  const double *rec = v.rec;
+  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
+    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
+      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
+        const int64_t cid = cell_index(g, c0, c1, c2);
+        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
+          int off[3];
+          if (!in_box<D>(v, q, ac, off)) continue;
+          double Sa, S0a, Gn[3], ga[3];
+          node_basis<D>(v, q, off, Sa, S0a, Gn);
+          spatial_grad<D>(v, q, Gn, ga);
+          const double cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
+          for (int i = 0; i < D; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < D; ++j) {
+              double sij = rec[(RC_TAU + i * D + j) * n + q];
+              if (DYN) sij += rec[(RC_SVIS + i * D + j) * n + q];
+              acc -= cs * ga[j] * sij;
+            }
+            acc += vol * ga[i] * ph;
+            acc += Sa * rec[(RC_FRC + i) * n + q];
+            r[i] += acc;
+          }
+          double gw = 0.0;
+          for (int j = 0; j < D; ++j) gw += ga[j] * rec[(RC_W + j) * n + q];
+          r[D] += Sa * rec[RC_DIVV * n + q] + rec[RC_KV * n + q] * gw + (Sa - S0a) * rec[RC_RST * n + q];
+          const int32_t e = v.surf[q];
+          if (e >= 0) {  // Neumann data at the surface point x + lp.n (hat basis)
+            double Ny = 1.0;
+            for (int k = 0; k < D; ++k) {
+              const double y = v.pf[(PF_X + k) * n + q] + v.pf[(PF_LP + k) * n + q] * v.pf[(PF_SN + k) * n + q];
+              const double t = 1.0 - fabs((y - g.org[k]) / g.h - (double)ac[k]);
+              Ny *= t > 0.0 ? t : 0.0;
+            }
+            const double A = v.pf[PF_SA * n + q];
+            for (int i = 0; i < D; ++i) r[i] += Ny * v.trac[(int64_t)e * D + i] * A;
+            if (v.flux) r[D] -= Ny * v.flux[e] * A;
+          }
+        }
+      }
+  for (int i = 0; i < NB; ++i) {
+    const bool fx = apply_bc && v.fixed[a * NB + i];
+    R[a * NB + i] = fx ? 0.0 : r[i];
+  }
+}
+
+// ---------------------------------------------------------------- Jacobian
+template <int D, bool GIMP, bool DYN>
+__global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restrict__ row_of,
+                           const int32_t *__restrict__ col, int64_t nnzb, double *__restrict__ val,
+                           int apply_bc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  constexpr int NB = D + 1;
+  const int64_t n = v.n;
+  const int64_t a = row_of[e], bn = col[e];
+  int ac[3], bc[3];
+  node_coords(g, a, ac);
+  node_coords(g, bn, bc);
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) {
+    int l1, h1, l2, h2;
+    cand_range<GIMP>(ac[k], g.nc[k], l1, h1);
+    cand_range<GIMP>(bc[k], g.nc[k], l2, h2);
+    lo[k] = max(l1, l2);
+    hi[k] = min(h1, h2);
+  }
+  double B[NB * NB];
+  for (int i = 0; i < NB * NB; ++i) B[i] = 0.0;
+  const double *rec = v.rec;
+  const double cvis = DYN ? s.alpha_vis * s.gamma / (s.beta * s.dt) : 0.0;
+  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
+    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
+      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
+        const int64_t cid = cell_index(g, c0, c1, c2);
+        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
+          int oa[3], ob[3];
+          if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
+          double Sa, S0a, Gna[3], Sb, S0b, Gnb[3], ga[3], gb[3];
+          node_basis<D>(v, q, oa, Sa, S0a, Gna);
+          node_basis<D>(v, q, ob, Sb, S0b, Gnb);
+          spatial_grad<D>(v, q, Gna, ga);
+          spatial_grad<D>(v, q, Gnb, gb);
+          const double cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
+          const double mu = rec[RC_MUP * n + q], lam = rec[RC_LAM * n + q], kv = rec[RC_KV * n + q];
+          double gab = 0.0, gtg = 0.0, gaw = 0.0, gbw = 0.0;
+          for (int j = 0; j < D; ++j) {
+            gab += ga[j] * gb[j];
+            const double wj = rec[(RC_W + j) * n + q];
+            gaw += ga[j] * wj;
+            gbw += gb[j] * wj;
+            for (int l = 0; l < D; ++l) gtg += ga[j] * rec[(RC_TAU + j * D + l) * n + q] * gb[l];
+          }
+          const double ms = DYN ? rec[RC_MS * n + q] * Sa * Sb : 0.0;
+          for (int i = 0; i < D; ++i)
+            for (int k = 0; k < D; ++k) {
+              const double dik = i == k ? 1.0 : 0.0;
+              const double sym = mu * (dik * gab + ga[k] * gb[i]);
+              double A = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
+              A += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
+              if (DYN) {
+                A -= cs * cvis * (lam * ga[i] * gb[k] + sym);
+                A -= dik * ms;
+              }
+              B[i * NB + k] += A;
+            }
+          for (int i = 0; i < D; ++i) B[i * NB + D] += vol * ga[i] * Sb;
+          const double b2 = rec[RC_B2 * n + q];
+          for (int k = 0; k < D; ++k) {
+            double t = Sa * b2 * gb[k];
+            if (DYN) {
+              double gbgv = 0.0;
+              for (int j = 0; j < D; ++j) gbgv += gb[j] * rec[(RC_GV + j * D + k) * n + q];
+              t -= vol * Sa * gbgv;
+            }
+            t += kv * (gb[k] * gaw - ga[k] * gbw - rec[(RC_GP + k) * n + q] * gab);
+            B[D * NB + k] += t;
+          }
+          B[D * NB + D] += kv * gab + rec[RC_CST * n + q] * (Sa - S0a) * (Sb - S0b);
+        }
+      }
+  if (apply_bc) {
+    constexpr int NBc = NB;
+    for (int i = 0; i < NBc; ++i) {
+      const bool fr = v.fixed[a * NBc + i] != 0;
+      for (int k = 0; k < NBc; ++k) {
+        const bool fc = v.fixed[bn * NBc + k] != 0;
+        if (fr || fc) B[i * NBc + k] = (a == bn && i == k) ? 1.0 : 0.0;
+      }
+    }
+  }
+  double *out = val + e * (NB * NB);
+  for (int i = 0; i < NB * NB; ++i) out[i] = B[i];
+}
+
+}  // namespace
+
+// ============================================================== launchers
+int run_pattern(Ctx &c) {
+  const DevView v = c.view();
+  const int nbk = nblk(c.g.nnodes, 128);
+  const bool gimp = c.shape == MPM_SHAPE_GIMP;
+  if (c.d == 2) {
+    if (gimp) k_pattern_count<2, true><<<nbk, 128, 0, c.st>>>(c.g, v, c.row_mask, c.row_nnz);
+    else k_pattern_count<2, false><<<nbk, 128, 0, c.st>>>(c.g, v, c.row_mask, c.row_nnz);
+  } else {
+    if (gimp) k_pattern_count<3, true><<<nbk, 128, 0, c.st>>>(c.g, v, c.row_mask, c.row_nnz);
+    else k_pattern_count<3, false><<<nbk, 128, 0, c.st>>>(c.g, v, c.row_mask, c.row_nnz);
+  }
+  UPMPM_LAUNCH(c);
+  const int64_t nnzb = scan_exclusive(c, c.row_nnz, c.row_ptr, c.g.nnodes + 1);
+  if (nnzb < 0) return MPM_ERR_CUDA;
+  if (nnzb > c.nnzb_cap) {
+    const int64_t cap = nnzb + nnzb / 4 + 1024;
+    cudaFree(c.col);
+    cudaFree(c.row_of);
+    cudaFree(c.val);
+    c.col = c.row_of = nullptr;
+    c.val = nullptr;
+    if (cudaMalloc(&c.col, sizeof(int32_t) * cap) != cudaSuccess ||
+        cudaMalloc(&c.row_of, sizeof(int32_t) * cap) != cudaSuccess ||
+        cudaMalloc(&c.val, sizeof(double) * cap * c.nb * c.nb) != cudaSuccess) {
+      c.nnzb_cap = 0;
+      c.last_error = "device allocation of the block-CSR matrix failed";
+      return MPM_ERR_NO_MEMORY;
+    }
+    c.nnzb_cap = cap;
+  }
+  c.nnzb = nnzb;
+  if (c.d == 2) k_pattern_fill<2><<<nbk, 128, 0, c.st>>>(c.g, c.row_mask, c.row_ptr, c.col, c.row_of);
+  else k_pattern_fill<3><<<nbk, 128, 0, c.st>>>(c.g, c.row_mask, c.row_ptr, c.col, c.row_of);
+  UPMPM_LAUNCH(c);
+  return check_cuda(c, cudaGetLastError(), "pattern");
+}
+
+void run_initial_guess(Ctx &c) {
+  const DevView v = c.view();
+  if (c.d == 2) k_initial_guess<2><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, v, c.X);
+  else k_initial_guess<3><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, v, c.X);
+  UPMPM_LAUNCH(c);
+}
+
+void run_point_eval(Ctx &c, const double *X) {
+  prof_begin(c, MPM_PROF_POINT);
+  const DevView v = c.view();
+  const int nbk = nblk(c.n);
+  if (c.d == 2) {
+    if (c.dyn) k_point_eval<2, true><<<nbk, TPB, 0, c.st>>>(c.g, c.s, v, X);
+    else k_point_eval<2, false><<<nbk, TPB, 0, c.st>>>(c.g, c.s, v, X);
+  } else {
+    if (c.dyn) k_point_eval<3, true><<<nbk, TPB, 0, c.st>>>(c.g, c.s, v, X);
+    else k_point_eval<3, false><<<nbk, TPB, 0, c.st>>>(c.g, c.s, v, X);
+  }
+  UPMPM_LAUNCH(c);
+  prof_end(c, MPM_PROF_POINT);
+}
+
+void run_residual(Ctx &c, const double *X, double *R, int apply_bc) {
+  (void)X;
+  prof_begin(c, MPM_PROF_RESIDUAL);
+  const DevView v = c.view();
+  const int nbk = nblk(c.g.nnodes, 128);
+  const bool gimp = c.shape == MPM_SHAPE_GIMP;
+#define RES(D, G, Y) k_residual<D, G, Y><<<nbk, 128, 0, c.st>>>(c.g, v, R, apply_bc)
+  if (c.d == 2) {
+    if (gimp) { if (c.dyn) RES(2, true, true); else RES(2, true, false); }
+    else { if (c.dyn) RES(2, false, true); else RES(2, false, false); }
+  } else {
+    if (gimp) { if (c.dyn) RES(3, true, true); else RES(3, true, false); }
+    else { if (c.dyn) RES(3, false, true); else RES(3, false, false); }
+  }
+#undef RES
+  UPMPM_LAUNCH(c);
+  prof_end(c, MPM_PROF_RESIDUAL);
+}
+
+void run_jacobian(Ctx &c, int apply_bc) {
+  prof_begin(c, MPM_PROF_JACOBIAN);
+  const DevView v = c.view();
+  const int nbk = nblk(c.nnzb, 128);
+  const bool gimp = c.shape == MPM_SHAPE_GIMP;
+#define JAC(D, G, Y) \
+  k_jacobian<D, G, Y><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, c.row_of, c.col, c.nnzb, c.val, apply_bc)
+  if (c.d == 2) {
+    if (gimp) { if (c.dyn) JAC(2, true, true); else JAC(2, true, false); }
+    else { if (c.dyn) JAC(2, false, true); else JAC(2, false, false); }
+  } else {
+    if (gimp) { if (c.dyn) JAC(3, true, true); else JAC(3, true, false); }
+    else { if (c.dyn) JAC(3, false, true); else JAC(3, false, false); }
+  }
+#undef JAC
+  UPMPM_LAUNCH(c);
+  prof_end(c, MPM_PROF_JACOBIAN);
+}
+
+}  // namespace upmpm

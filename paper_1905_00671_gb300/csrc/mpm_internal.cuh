@@ -1,0 +1,274 @@
+// mpm_internal.cuh -- data layout, context and device helpers shared by the
+// CUDA translation units of the u-p MPM library (not part of the public ABI).
+//
+// Layout in HBM (all structure-of-arrays, field-major, so that a warp reading
+// one field of 32 consecutive material points issues one coalesced load):
+//   particles  pf[PF_*][n]   FP64 state, cell-sorted at the start of each step
+//   shape      sh_first[k][n], sh_cnt[n] (packed per-axis node counts),
+//              sh_S/sh_dS/sh_S0[k*4+s][n]  1D basis values per axis and slot
+//   records    rec[RC_*][n]  per-point quantities of the current Newton
+//                            iterate (kinematics, stress, flux, stabilization)
+//   nodes      nodal fields [field][nnodes]; unknowns X node-interleaved
+//              [dU_x, dU_y, (dU_z), P] per node, like the block-CSR blocks
+//   matrix     block-CSR: row_ptr[nnodes+1], col[nnzb], val[nnzb][nb][nb]
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mpm.h"
+
+namespace upmpm {
+
+constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
+
+// ---- particle fields ------------------------------------------------------
+enum PField {
+  PF_X = 0,        // 3
+  PF_U = 3,        // 3
+  PF_F = 6,        // 9, row-major d x d in the first d*d entries
+  PF_V = 15,       // current volume (at t_n)
+  PF_LP = 16,      // 3 GIMP half lengths
+  PF_LP0 = 19,     // 3 initial half lengths
+  PF_P = 22,       // pore pressure
+  PF_VEL = 23,     // 3 velocity
+  PF_ACC = 26,     // 3 acceleration
+  PF_PD = 29,      // dp/dt
+  PF_PDD = 30,     // d2p/dt2
+  PF_LAM = 31,     // Lame lambda
+  PF_G = 32,       // shear modulus
+  PF_KAP = 33,     // mobility k / mu_f
+  PF_TAU = 34,     // PPP parameter (0 when unstabilized)
+  PF_SN = 35,      // 3 surface normal
+  PF_SA = 38,      // surface measure
+  PF_COUNT = 39
+};
+
+// ---- per-point records of one Newton iterate -------------------------------
+enum RField {
+  RC_FINV = 0,     // 9  dF^{-1}
+  RC_TAU = 9,      // 9  Kirchhoff effective stress tau'
+  RC_SVIS = 18,    // 9  alpha (lambda trD 1 + 2 mu' D)   (Newmark)
+  RC_GV = 27,      // 9  spatial velocity gradient        (Newmark)
+  RC_GP = 36,      // 3  grad p
+  RC_W = 39,       // 3  grad p - rho_f (g - a)
+  RC_FRC = 42,     // 3  m (g - a)
+  RC_CS = 45,      // V_n / J_n
+  RC_VOL = 46,     // dJ V_n
+  RC_PH = 47,      // p^h
+  RC_MUP = 48,     // G - lambda ln J
+  RC_LAM = 49,     // lambda
+  RC_KV = 50,      // kappa * vol
+  RC_CST = 51,     // C_stab factor * V_n
+  RC_RST = 52,     // tau V_n (pdot - Pi pdot)
+  RC_DIVV = 53,    // vol * div v
+  RC_B2 = 54,      // B2 divergence coefficient
+  RC_MS = 55,      // m (inertia Jacobian)
+  RC_COUNT = 56
+};
+
+// error bits raised by kernels (read back at synchronisation points)
+enum DevErr : int { DE_OUT_OF_GRID = 1, DE_NEG_J = 2, DE_SUPPORT = 4, DE_SINGULAR = 8 };
+
+struct GridP {
+  int d;
+  int nc[3];   // cells per axis (1 for unused axes)
+  int nn[3];   // nodes per axis (1 for unused axes)
+  double org[3];
+  double h;
+  int64_t nnodes, ncells;
+};
+
+struct StepP {
+  double dt, beta, gamma, rho_f, alpha_vis;
+  double g[3];
+  double phi0, rho_s;
+};
+
+// all device pointers the kernels need, passed by value
+struct DevView {
+  int64_t n;
+  double *pf;               // PF_COUNT * n
+  int64_t *pid;             // original ids
+  int32_t *surf;            // surface entry or -1
+  int32_t *cell;            // cell of each point (current order)
+  int32_t *cell_start;      // ncells + 1
+  int32_t *sh_first;        // 3 * n
+  int32_t *sh_cnt;          // n, counts packed 4 bits per axis
+  double *sh_S, *sh_dS, *sh_S0;  // 12 * n each
+  double *m;                // n mixture mass of the step
+  double *rec;              // RC_COUNT * n
+  // nodes
+  double *M, *Pn, *vn, *an, *pdn, *pddn;  // vn/an: d * nnodes (field-major)
+  uint8_t *fixed;           // nb * nnodes, node-interleaved
+  uint8_t *u_fixed;         // d * nnodes node-interleaved
+  double *u_value;          // d * nnodes
+  uint8_t *p_fixed;         // nnodes
+  double *p_value;          // nnodes
+  double *trac;             // n_surf * d (already scaled)
+  double *flux;             // n_surf or null
+  int *err;                 // device error word
+};
+
+// ---- host-side context ----------------------------------------------------
+struct Ctx {
+  GridP g{};
+  StepP s{};
+  int d = 2, nb = 3;
+  int shape = MPM_SHAPE_GIMP, dyn = 0, stabilize = 1, precision = MPM_FP64;
+  double tau_scale = 1.0;
+  mpm_options opt{};
+  cudaStream_t st = nullptr;
+  int64_t n = 0;
+  int32_t n_surf = 0;
+  double t = 0.0;
+  int64_t steps = 0;
+  std::string last_error;
+  mpm_stats stats{};
+  int64_t launches = 0;
+
+  // device buffers
+  double *pf = nullptr, *pf_alt = nullptr;
+  int64_t *pid = nullptr, *pid_alt = nullptr;
+  int32_t *surf = nullptr, *surf_alt = nullptr;
+  int32_t *cell = nullptr, *cell_tmp = nullptr, *cell_start = nullptr, *cell_cursor = nullptr;
+  int32_t *perm = nullptr;
+  int32_t *sh_first = nullptr, *sh_cnt = nullptr;
+  double *sh_S = nullptr, *sh_dS = nullptr, *sh_S0 = nullptr;
+  double *m = nullptr, *rec = nullptr;
+  double *M = nullptr, *Pn = nullptr, *vn = nullptr, *an = nullptr, *pdn = nullptr, *pddn = nullptr;
+  uint8_t *fixed = nullptr, *u_fixed = nullptr, *p_fixed = nullptr;
+  double *u_value = nullptr, *p_value = nullptr, *trac = nullptr, *trac_raw = nullptr, *flux = nullptr;
+  int has_flux = 0;
+  double trac_scale = 1.0;
+  int *err = nullptr;
+  int *h_err = nullptr;                  // pinned
+  double *h_scalar = nullptr;            // pinned scratch for scalars read by the host
+
+  // sparsity + matrix
+  int32_t *row_nnz = nullptr, *row_ptr = nullptr, *row_of = nullptr, *col = nullptr;
+  uint64_t *row_mask = nullptr;          // per node, 6 words (7^d offsets)
+  int64_t nnzb = 0, nnzb_cap = 0;
+  double *val = nullptr;                 // nnzb_cap * nb * nb
+  double *dscale = nullptr;              // nb * nnodes diagonal scaling
+  double *dinv = nullptr;                // nnodes * nb * nb block-Jacobi inverse
+
+  // vectors (length nb * nnodes)
+  double *X = nullptr, *R = nullptr, *dX = nullptr, *rhs = nullptr, *w = nullptr;
+  // FGMRES workspace
+  int m_restart = 30;
+  double *V = nullptr, *Z = nullptr;     // (m+1) and m vectors
+  double *H = nullptr, *gvec = nullptr, *cs = nullptr, *sn = nullptr, *yv = nullptr;
+  double *hcol = nullptr, *part = nullptr, *scal = nullptr;
+  int nparts = 0;
+
+  // scan scratch
+  int32_t *scan_tmp = nullptr;
+  int64_t scan_cap = 0;
+
+  bool prepared = false;
+
+  // CUDA-event timing of selected kernel classes (opt.profile bit mask)
+  std::vector<cudaEvent_t> ev;           // start/stop pairs
+  std::vector<int> ev_kind;
+  int ev_used = 0;
+
+  DevView view() const;
+  int64_t N() const { return (int64_t)nb * g.nnodes; }
+};
+
+// ---- launchers (implemented in the .cu files) -----------------------------
+// particles: binning, shape, Stage 1, Stage 3/4
+int run_binning(Ctx &c);                          // keys, counting sort, (cell, id) order, permute
+void run_shape(Ctx &c);
+void run_mass(Ctx &c);
+void run_p2g(Ctx &c);
+void run_g2p(Ctx &c);
+// assembly
+int run_pattern(Ctx &c);                          // builds row_ptr / col / row_of
+void run_initial_guess(Ctx &c);
+void run_point_eval(Ctx &c, const double *X);
+void run_residual(Ctx &c, const double *X, double *R, int apply_bc);
+void run_jacobian(Ctx &c, int apply_bc);
+// linear algebra
+void run_scale_system(Ctx &c, double *rhs_out, const double *R);  // scales val, rhs = -D R
+void run_block_jacobi(Ctx &c);
+int run_fgmres(Ctx &c, const double *b, double *x, double rtol, int maxit, int *iters);
+double run_norm(Ctx &c, const double *x);          // synchronises
+void run_axpy(Ctx &c, double *y, double a, const double *x, int64_t n);
+void run_unscale_add(Ctx &c, double *X, const double *xhat);  // X += D xhat
+
+// scan: out[i] = sum_{j<i} in[j]; returns the total (synchronises)
+int64_t scan_exclusive(Ctx &c, const int32_t *in, int32_t *out, int64_t n);
+
+// helpers
+int check_cuda(Ctx &c, cudaError_t e, const char *what);
+int read_dev_err(Ctx &c);   // synchronises; returns MPM_ERR_* or 0
+
+#define UPMPM_LAUNCH(ctx) ((ctx).launches++)
+
+// Event timing of kernel class `kind` around the launches between begin/end.
+void prof_begin(Ctx &c, int kind);
+void prof_end(Ctx &c, int kind);
+void prof_collect(Ctx &c);   // synchronises; adds elapsed times into stats
+
+// ---- device helpers -------------------------------------------------------
+__host__ __device__ inline int unpack_cnt(int packed, int k) { return (packed >> (4 * k)) & 15; }
+
+template <int D>
+__device__ inline double det_d(const double *A) {
+  if (D == 2) return A[0] * A[3] - A[1] * A[2];
+  return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+         A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+
+template <int D>
+__device__ inline void inv_d(const double *A, double *B) {
+  const double det = det_d<D>(A);
+  if (D == 2) {
+    B[0] = A[3] / det;
+    B[1] = -A[1] / det;
+    B[2] = -A[2] / det;
+    B[3] = A[0] / det;
+  } else {
+    B[0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    B[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    B[2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    B[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+    B[4] = (A[0] * A[8] - A[2] * A[6]) / det;
+    B[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    B[6] = (A[3] * A[7] - A[4] * A[6]) / det;
+    B[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    B[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  }
+}
+
+// node / cell coordinates
+__host__ __device__ inline void node_coords(const GridP &g, int64_t a, int c[3]) {
+  c[0] = (int)(a % g.nn[0]);
+  int64_t r = a / g.nn[0];
+  c[1] = (int)(r % g.nn[1]);
+  c[2] = (int)(r / g.nn[1]);
+}
+__host__ __device__ inline int64_t node_index(const GridP &g, const int c[3]) {
+  return c[0] + (int64_t)g.nn[0] * (c[1] + (int64_t)g.nn[1] * c[2]);
+}
+__host__ __device__ inline int64_t cell_index(const GridP &g, int c0, int c1, int c2) {
+  return c0 + (int64_t)g.nc[0] * (c1 + (int64_t)g.nc[1] * c2);
+}
+
+// Candidate cells holding points whose support may contain node coordinate a
+// along one axis: a point in cell c has support within [c-1, c+2] (GIMP,
+// half length < h) or [c, c+1] (original MPM).
+template <bool GIMP>
+__device__ inline void cand_range(int a, int nc, int &lo, int &hi) {
+  lo = GIMP ? a - 2 : a - 1;
+  hi = GIMP ? a + 1 : a;
+  if (lo < 0) lo = 0;
+  if (hi > nc - 1) hi = nc - 1;
+}
+
+}  // namespace upmpm

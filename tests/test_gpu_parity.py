@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Bars (spec tolerances): binning order and block sparsity bit-exact;
+Stage-1 nodal values, residual and Jacobian entry-wise to 1e-11 relative to
+each block type's largest entry; whole steps to 1e-10 relative (max abs
+difference over the largest magnitude of each field) with both sides solved to
+their round-off floor.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1905_00671_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(newton_rtol=1e-13, newton_stag=1e-6, newton_max=12)
+GPU_TIGHT = dict(TIGHT, krylov_rtol=1e-13, krylov_max=20000)
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_00671_gb300 import mpm as m
+
+    m.load()
+    return m
+
+
+def rel(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / scale
+
+
+CASES = {
+    "footing2d-gimp-newmark": lambda: I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25),
+    "footing2d-orig-newmark": lambda: I.small_footing(seed=8, shape=I.ORIG, body=(20, 10), pad=2),
+    "footing2d-gimp-qs": lambda: I.small_footing(seed=9, dynamic=False, body=(20, 10), pad=2,
+                                                 dt=1.0),
+    "block3d-gimp-qs": lambda: I.small_block(seed=11, body=(6, 5, 4)),
+    "block3d-orig-qs": lambda: I.small_block(seed=12, shape=I.ORIG, body=(5, 4, 4)),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_binning_bit_exact(mpm, name):
+    w = CASES[name]()
+    sim = mpm.Simulation(w)
+    cell, order = sim.debug_bin()
+    g = O.grid_struct(w.dim, w.shape, w.ncell, w.origin, w.h)
+    ocell, oorder = O.binning(g, w.x)
+    np.testing.assert_array_equal(cell, ocell)
+    np.testing.assert_array_equal(order, oorder)
+    sim.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_stage1_pattern_residual_jacobian(mpm, name):
+    w = CASES[name]()
+    sim = mpm.Simulation(w)
+    sim.debug_prepare()
+    orc = O.Oracle(w)
+    prep = orc.prepare(w.dt)
+    # sparsity: bit-exact
+    row_ptr, col = sim.debug_pattern()
+    np.testing.assert_array_equal(row_ptr, prep["row_ptr"])
+    np.testing.assert_array_equal(col, prep["col"])
+    # Stage 1
+    M, Pn = sim.debug_nodal()
+    assert rel(M, prep["M"]) <= 1e-13
+    np.testing.assert_array_equal(M > 0, prep["M"] > 0)
+    assert rel(Pn, prep["nodal"]["P"]) <= 1e-12
+    # residual and Jacobian at a perturbed iterate, before Dirichlet elimination
+    rng = np.random.default_rng(0)
+    nb = w.dim + 1
+    X = orc.initial_guess(prep).reshape(-1, nb)
+    X[:, :w.dim] += 1e-4 * rng.standard_normal((orc.nn, w.dim))
+    X[:, w.dim] += 1e3 * rng.standard_normal(orc.nn)
+    X = X.reshape(-1)
+    Ro, Jo = orc.eval(prep, X, w.traction(w.dt))
+    Rg, Jg = sim.debug_eval(X, nnzb=len(col), apply_bc=False)
+    for r in range(nb):
+        assert rel(Rg[r::nb], Ro[r::nb]) <= 1e-11, ("R", r)
+    Jo = Jo.reshape(-1, nb, nb)
+    Jg = Jg.reshape(-1, nb, nb)
+    for r in range(nb):
+        for c in range(nb):
+            assert rel(Jg[:, r, c], Jo[:, r, c]) <= 1e-11, ("J", r, c)
+    sim.close()
+
+
+STEP_CASES = {
+    "footing2d-gimp-newmark": (CASES["footing2d-gimp-newmark"], 4),
+    "footing2d-orig-newmark": (CASES["footing2d-orig-newmark"], 3),
+    "footing2d-gimp-qs": (CASES["footing2d-gimp-qs"], 3),
+    "terzaghi-4x40": (lambda: I.terzaghi_column(), 10),
+    "block3d-gimp-qs": (CASES["block3d-gimp-qs"], 2),
+}
+
+
+@pytest.mark.parametrize("name", list(STEP_CASES))
+def test_step_trajectory_parity(mpm, name):
+    make, nsteps = STEP_CASES[name]
+    w = make()
+    sim = mpm.Simulation(w, **GPU_TIGHT)
+    orc = O.Oracle(w, **TIGHT)
+    fields = ("x", "u", "p", "F", "V", "lp") + (("v", "a", "pd", "pdd") if w.dynamic else ())
+    for s in range(nsteps):
+        sim.step()
+        orc.step()
+        got = sim.read(fields)
+        ref = orc.state()
+        for k in fields:
+            r = ref[k].reshape(got[k].shape)
+            if k in ("x", "F", "V", "lp"):   # compare the change over the run, not the offset
+                base = {"x": w.x, "F": np.tile(np.eye(w.dim).reshape(-1), (w.n, 1)),
+                        "V": w.vol, "lp": w.lp}[k].reshape(got[k].shape)
+                err = rel(got[k] - base, r - base)
+            else:
+                err = rel(got[k], r)
+            assert err <= 1e-10, (name, s, k, err)
+    sim.close()
+
+
+def test_full_size_footing_first_step(mpm):
+    """200 x 100 footing, 80,000 points, GIMP + Newmark, one step at full size."""
+    w = I.strip_footing()
+    sim = mpm.Simulation(w, **GPU_TIGHT)
+    orc = O.Oracle(w, **TIGHT)
+    sim.step()
+    orc.step()
+    got = sim.read(("u", "p", "v"))
+    ref = orc.state()
+    for k in ("u", "p", "v"):
+        assert rel(got[k], ref[k].reshape(got[k].shape)) <= 1e-10, k
+    sim.close()
+
+
+# ---------------------------------------------------------------- failures
+def test_point_out_of_grid_is_reported(mpm):
+    w = I.small_footing(seed=3, body=(8, 4), pad=1, jitter=0.0)
+    x = w.x.copy()
+    x[5, 0] = -0.01
+    w = replace(w, x=x)
+    sim = mpm.Simulation(w)
+    with pytest.raises(mpm.MPMError) as e:
+        sim.step()
+    assert e.value.code == -2
+    sim.close()
+
+
+def test_newton_cap_is_reported_and_state_kept(mpm):
+    w = I.small_footing(seed=3, body=(8, 4), pad=1)
+    sim = mpm.Simulation(w, newton_max=1, newton_rtol=1e-14)
+    before = sim.read(("x", "p"))
+    with pytest.raises(mpm.MPMError) as e:
+        sim.step()
+    assert e.value.code == -5
+    after = sim.read(("x", "p"))
+    np.testing.assert_array_equal(before["x"], after["x"])
+    np.testing.assert_array_equal(before["p"], after["p"])
+    sim.close()
+
+
+def test_krylov_cap_is_reported(mpm):
+    w = I.small_footing(seed=3, body=(8, 4), pad=1)
+    sim = mpm.Simulation(w, krylov_max=1, krylov_rtol=1e-14)
+    with pytest.raises(mpm.MPMError) as e:
+        sim.step()
+    assert e.value.code == -6
+    sim.close()
+
+
+def test_bad_arguments_are_rejected(mpm):
+    import ctypes as C
+
+    w = I.small_footing(seed=3, body=(8, 4), pad=1)
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(w, krylov_restart=100)
+    assert e.value.code == -1
+    bad = replace(w, surf_id=np.where(w.surf_id >= 0, w.surf_id + 1000, -1).astype(np.int32))
+    with pytest.raises(mpm.MPMError):
+        mpm.Simulation(bad)
+    sim = mpm.Simulation(w)
+    assert sim.lib.mpm_step(sim.ctx, C.c_double(-1.0), None, None) == -1
+    sim.close()
+
+
+def test_deterministic_across_runs(mpm):
+    w = CASES["footing2d-gimp-newmark"]()
+    outs = []
+    for _ in range(2):
+        sim = mpm.Simulation(w)
+        sim.step()
+        sim.step()
+        outs.append(sim.read(("x", "p", "v")))
+        sim.close()
+    for k in ("x", "p", "v"):
+        np.testing.assert_array_equal(outs[0][k], outs[1][k])
