@@ -55,6 +55,12 @@ enum { MPM_SHAPE_ORIG = 0, MPM_SHAPE_GIMP = 1 };     /* Sec. 3.1: FE basis or GI
 enum { MPM_QUASISTATIC = 0, MPM_NEWMARK = 1 };       /* Sec. 3.2: implicit Euler or Newmark */
 enum { MPM_FP64 = 0, MPM_MIXED = 1 };
 
+/* Preconditioner of the FGMRES solve of the Newton system: node-block Jacobi,
+ * or the Schur-complement block preconditioner of Sec. 3.4 with geometric
+ * multigrid V-cycles for the displacement block and the pressure Schur
+ * complement (default). */
+enum { MPM_PRECOND_BLOCK_JACOBI = 0, MPM_PRECOND_SCHUR_MG = 1 };
+
 /* Kernel classes that mpm_options.profile can time with CUDA events (bit k of
  * the mask selects class k; mpm_stats.prof_ms[k] / prof_launches[k]). */
 enum {
@@ -124,8 +130,14 @@ typedef struct {
                                  ||R^{k-1}|| <= newton_stag ||R^0|| and R^k fails
                                  to halve it; 0 disables */
   double krylov_rtol;         /* linear solve to rtol of the scaled residual */
-  int32_t krylov_restart;     /* FGMRES restart length (<= 64) */
+  int32_t krylov_restart;     /* FGMRES restart length (<= 128) */
   int32_t krylov_max;         /* total Krylov iterations per Newton iteration */
+  int32_t precond;            /* MPM_PRECOND_* */
+  double min_volume_fraction; /* a node is active iff sum_p S_ip V_p / h^dim exceeds
+                                 this (default 1e-4; 0 = any positive volume).  An
+                                 inactive node is removed from the bases of the
+                                 points whose support holds it, and those bases
+                                 are renormalised over their other nodes. */
   int32_t profile;            /* bit mask of MPM_PROF_* classes timed with CUDA
                                  events on the work stream (0 = none) */
   void *stream;               /* cudaStream_t for all work; NULL = default stream */
@@ -179,7 +191,8 @@ typedef struct {
 
 /* Fills *o with the defaults: GIMP, quasi-static, beta 0.3025, gamma 0.6,
  * PPP on with tau_W, FP64, Newton rtol 1e-8 (Eq. newton-tolerance), 25
- * iterations, Krylov rtol 1e-8, restart 30, 3000 iterations. */
+ * iterations, Krylov rtol 1e-8, restart 120, 3000 iterations, Schur-complement
+ * multigrid preconditioner. */
 void mpm_default_options(mpm_options *o);
 
 /* Creates a context and uploads the problem (Sec. 2.4 "given u0, p0"): the
@@ -227,9 +240,10 @@ int mpm_debug_prepare(mpm_ctx *ctx, double dt, const mpm_loads *loads, const mpm
  * a negative code; with col_idx == NULL only the count is returned. */
 int64_t mpm_debug_pattern(mpm_ctx *ctx, int64_t *row_ptr, int32_t *col_idx, int64_t cap);
 
-/* Lumped nodal mass M (nnodes) and Stage-1 nodal pressure P_n (nnodes) of the
- * prepared step. */
-int mpm_debug_nodal(mpm_ctx *ctx, double *M, double *Pn);
+/* Lumped nodal mass M, Stage-1 nodal pressure P_n and nodal volume fraction
+ * phi = sum_p S_ip V_p / h^dim (each nnodes; any may be NULL) of the prepared
+ * step. */
+int mpm_debug_nodal(mpm_ctx *ctx, double *M, double *Pn, double *phi);
 
 /* Residual R(X) (nnodes*(dim+1)) and the Jacobian block values (nnzb blocks of
  * (dim+1)^2, row-major, in the pattern's order) at the nodal unknowns X
@@ -237,6 +251,12 @@ int mpm_debug_nodal(mpm_ctx *ctx, double *M, double *Pn);
  * the residual/Jacobian kernels produce them before Dirichlet elimination
  * (apply_bc = 0) or after it (apply_bc = 1).  Jv may be NULL. */
 int mpm_debug_eval(mpm_ctx *ctx, const double *X, double *R, double *Jv, int32_t apply_bc);
+
+/* z = M^{-1} v for the preconditioner the Krylov solver would use at the
+ * iterate X of the prepared step: the Jacobian (after Dirichlet elimination)
+ * is assembled at X, scaled symmetrically by D = |diag J|^{-1/2}, and M^{-1}
+ * is the preconditioner of that scaled system.  X, v, z: nnodes*(dim+1). */
+int mpm_debug_precond(mpm_ctx *ctx, const double *X, const double *v, double *z);
 
 #ifdef __cplusplus
 }

@@ -193,7 +193,8 @@ class StepInfo:
 class Oracle:
     """State of one problem, stepped on the CPU in FP64."""
 
-    def __init__(self, w, newton_rtol=1e-8, newton_max=25, newton_stag=0.0):
+    def __init__(self, w, newton_rtol=1e-8, newton_max=25, newton_stag=0.0,
+                 min_volume_fraction=1e-4):
         self.w = w
         d = w.dim
         self.d = d
@@ -223,6 +224,7 @@ class Oracle:
         self.newton_rtol = newton_rtol
         self.newton_max = newton_max
         self.newton_stag = newton_stag
+        self.phi_min = min_volume_fraction
         self.u_fixed = np.asarray(w.u_fixed, np.uint8).copy()
         self.u_value = np.asarray(w.u_value, float).copy()
         self.p_fixed = np.asarray(w.p_fixed, np.uint8).copy()
@@ -266,6 +268,9 @@ class Oracle:
         if self.w.dynamic:
             fld += [self.v, self.a, self.pd[:, None], self.pdd[:, None]]
         M, out = p2g(self.g, first, count, S, m, np.concatenate(fld, axis=1))
+        # nodal volume fraction sum_p S_ip V_p / h^d (activity of the node)
+        Mv, _ = p2g(self.g, first, count, S, self.V, np.zeros(self.n))
+        phi = Mv / self.w.h ** d
         Pn = np.ascontiguousarray(out[:, 0])
         nodal = {"P": Pn}
         if self.w.dynamic:
@@ -274,8 +279,10 @@ class Oracle:
             nodal["pd"] = np.ascontiguousarray(out[:, 1 + 2 * d])
             nodal["pdd"] = np.ascontiguousarray(out[:, 2 + 2 * d])
         row_ptr, col = pattern(self.g, first, count)
-        return dict(first=first, count=count, S=S, dS=dS, S0=S0, m=m, M=M, nodal=nodal,
-                    row_ptr=row_ptr, col=col, dt=dt)
+        active = (M > 0.0) & (phi > self.phi_min)
+        return dict(first=first, count=count, S=S, dS=dS, S0=S0, m=m, M=M, phi=phi,
+                    active=active, active_u8=np.ascontiguousarray(active.astype(np.uint8)),
+                    nodal=nodal, row_ptr=row_ptr, col=col, dt=dt)
 
     def _nodal_struct(self, nodal):
         nd = _Nodal()
@@ -301,18 +308,20 @@ class Oracle:
         flx = None if flux is None else np.ascontiguousarray(flux, float)
         rc = lib().orc_eval(C.byref(self.g), C.byref(sp), C.byref(pp), _p(prep["first"]),
                             _p(prep["count"]), _p(prep["S"]), _p(prep["dS"]), _p(prep["S0"]),
-                            C.byref(nd), _p(trac), _p(flx), _p(X), _p(prep["row_ptr"]),
-                            _p(prep["col"]), _p(R), _p(Jv))
+                            _p(prep["active_u8"]), C.byref(nd), _p(trac), _p(flx), _p(X),
+                            _p(prep["row_ptr"]), _p(prep["col"]), _p(R), _p(Jv))
         _check(rc, "eval")
         return R, Jv
 
     def fixed_dofs(self, prep):
-        """Dirichlet DOFs plus every DOF of an inactive node (lumped mass 0)."""
+        """Dirichlet DOFs plus every DOF of an inactive node: a node whose
+        volume fraction sum_p S_ip V_p / h^d is at most the threshold (the
+        minimum-mass rule of GIMP codes)."""
         d, nb = self.d, self.d + 1
         fixed = np.zeros((self.nn, nb), bool)
         fixed[:, :d] = self.u_fixed.astype(bool)
         fixed[:, d] = self.p_fixed.astype(bool)
-        fixed[prep["M"] <= 0.0, :] = True
+        fixed[~prep["active"], :] = True
         return fixed.reshape(-1)
 
     def initial_guess(self, prep):
@@ -323,7 +332,7 @@ class Oracle:
         X[:, :d][uf] = self.u_value[uf]
         pf = self.p_fixed.astype(bool)
         X[pf, d] = self.p_value[pf]
-        X[prep["M"] <= 0.0, :] = 0.0
+        X[~prep["active"], :] = 0.0
         return X.reshape(-1)
 
     def jacobian_matrix(self, prep, Jv, fixed):
@@ -383,7 +392,8 @@ class Oracle:
         sp = self._step_struct(prep["dt"])
         nd = self._nodal_struct(prep["nodal"])
         rc = lib().orc_g2p(C.byref(self.g), C.byref(sp), C.c_int64(self.n), _p(prep["first"]),
-                           _p(prep["count"]), _p(prep["S"]), _p(prep["dS"]), C.byref(nd),
+                           _p(prep["count"]), _p(prep["S"]), _p(prep["dS"]), _p(prep["S0"]),
+                           _p(prep["active_u8"]), C.byref(nd),
                            _p(np.ascontiguousarray(X)), _p(self.x), _p(self.u), _p(self.F),
                            _p(self.V), _p(self.lp), _p(self.lp0), _p(self.p), _p(self.v),
                            _p(self.a), _p(self.pd), _p(self.pdd))

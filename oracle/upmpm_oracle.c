@@ -179,6 +179,16 @@ typedef struct {
   int ax[MAXS * MAXS * MAXS][MAXD];    /* node index per axis */
 } support;
 
+/* Nodes of the point's support box with their S, S0 and t_n gradient.  When
+ * `active` is given and some box node is inactive (its volume fraction is at
+ * or below the threshold), that node is removed from this point's basis and
+ * the rest is renormalised so that constants stay exactly reproduced:
+ *   S'_a = S_a / sum S,  grad S'_a = (grad S_a - S'_a grad sum S) / sum S,
+ *   S0'_a = S0_a / sum S0   (sums over the active box nodes). */
+static void build_support_active(const orc_grid *g, int64_t p, const int32_t *first,
+                                 const int32_t *count, const double *S, const double *dS,
+                                 const double *S0, const uint8_t *active, support *sp);
+
 static void build_support(const orc_grid *g, int64_t p, const int32_t *first, const int32_t *count,
                           const double *S, const double *dS, const double *S0, support *sp) {
   const int d = g->dim;
@@ -209,6 +219,36 @@ static void build_support(const orc_grid *g, int64_t p, const int32_t *first, co
           sp->ax[q][k] = idx[k];
         }
       }
+}
+
+static void build_support_active(const orc_grid *g, int64_t p, const int32_t *first,
+                                 const int32_t *count, const double *S, const double *dS,
+                                 const double *S0, const uint8_t *active, support *sp) {
+  build_support(g, p, first, count, S, dS, S0, sp);
+  if (!active) return;
+  int any = 0;
+  for (int q = 0; q < sp->ns; ++q)
+    if (!active[sp->node[q]]) any = 1;
+  if (!any) return;
+  const int d = g->dim;
+  double sum = 0.0, sum0 = 0.0, gsum[MAXD] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < sp->ns; ++q) {
+    if (!active[sp->node[q]]) continue;
+    sum += sp->S[q];
+    sum0 += sp->S0[q];
+    for (int k = 0; k < d; ++k) gsum[k] += sp->Gn[q][k];
+  }
+  for (int q = 0; q < sp->ns; ++q) {
+    if (!active[sp->node[q]]) {
+      sp->S[q] = sp->S0[q] = 0.0;
+      for (int k = 0; k < d; ++k) sp->Gn[q][k] = 0.0;
+      continue;
+    }
+    const double Sr = sp->S[q] / sum;
+    for (int k = 0; k < d; ++k) sp->Gn[q][k] = (sp->Gn[q][k] - Sr * gsum[k]) / sum;
+    sp->S[q] = Sr;
+    sp->S0[q] = sp->S0[q] / sum0;
+  }
 }
 
 /* ------------------------------------------------------------------------
@@ -374,8 +414,8 @@ static void newmark_node(const orc_step *sp, int d, const orc_nodal *nd, int64_t
  * ---------------------------------------------------------------------- */
 int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
              const int32_t *first, const int32_t *count, const double *S, const double *dS,
-             const double *S0, const orc_nodal *nd, const double *trac, const double *flux,
-             const double *X, const int64_t *row_ptr, const int32_t *col_idx,
+             const double *S0, const uint8_t *active, const orc_nodal *nd, const double *trac,
+             const double *flux, const double *X, const int64_t *row_ptr, const int32_t *col_idx,
              double *R, double *Jv) {
   const int d = g->dim, nb = d + 1, nb2 = nb * nb;
   const int64_t nn = orc_nnodes(g);
@@ -388,7 +428,7 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
   support *su = (support *)malloc(sizeof(support));
   int rc = ORC_OK;
   for (int64_t p = 0; p < pp->n; ++p) {
-    build_support(g, p, first, count, S, dS, S0, su);
+    build_support_active(g, p, first, count, S, dS, S0, active, su);
     const int ns = su->ns;
     /* relative deformation gradient dF = 1 + sum dU_b (x) Gn_b */
     double dF[9] = {0}, f[9], Fn[9], F[9] = {0}, bL[9] = {0};
@@ -629,14 +669,15 @@ void orc_stretch_diag(int32_t d, const double *F, double *Udiag) {
  * V = dJ Vn, GIMP half lengths from the right stretch.
  * ---------------------------------------------------------------------- */
 int orc_g2p(const orc_grid *g, const orc_step *sp, int64_t n, const int32_t *first,
-            const int32_t *count, const double *S, const double *dS, const orc_nodal *nd,
-            const double *X, double *x, double *u, double *F, double *V, double *lp,
-            const double *lp0, double *p, double *v, double *a, double *pd, double *pdd) {
+            const int32_t *count, const double *S, const double *dS, const double *S0,
+            const uint8_t *active, const orc_nodal *nd, const double *X, double *x, double *u,
+            double *F, double *V, double *lp, const double *lp0, double *p, double *v, double *a,
+            double *pd, double *pdd) {
   const int d = g->dim, nb = d + 1;
   support *su = (support *)malloc(sizeof(support));
   int rc = ORC_OK;
   for (int64_t q0 = 0; q0 < n; ++q0) {
-    build_support(g, q0, first, count, S, dS, S, su);
+    build_support_active(g, q0, first, count, S, dS, S0, active, su);
     double dF[9] = {0}, du[3] = {0, 0, 0}, ph = 0.0;
     for (int i = 0; i < d; ++i) dF[i * d + i] = 1.0;
     for (int q = 0; q < su->ns; ++q) {

@@ -88,16 +88,19 @@ int orc_p2g(const orc_grid *g, int64_t n, const int32_t *first, const int32_t *c
             const double *S, const double *m, int32_t nf, const double *fld,
             double *M, double *out);
 
+/* active (nnodes, may be NULL): nodes with active == 0 are removed from the
+ * bases of the points whose support box holds them, which are renormalised. */
 int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
              const int32_t *first, const int32_t *count, const double *S, const double *dS,
-             const double *S0, const orc_nodal *nd, const double *trac, const double *flux,
-             const double *X, const int64_t *row_ptr, const int32_t *col_idx,
+             const double *S0, const uint8_t *active, const orc_nodal *nd, const double *trac,
+             const double *flux, const double *X, const int64_t *row_ptr, const int32_t *col_idx,
              double *R, double *Jv);
 
 int orc_g2p(const orc_grid *g, const orc_step *sp, int64_t n, const int32_t *first,
-            const int32_t *count, const double *S, const double *dS, const orc_nodal *nd,
-            const double *X, double *x, double *u, double *F, double *V, double *lp,
-            const double *lp0, double *p, double *v, double *a, double *pd, double *pdd);
+            const int32_t *count, const double *S, const double *dS, const double *S0,
+            const uint8_t *active, const orc_nodal *nd, const double *X, double *x, double *u,
+            double *F, double *V, double *lp, const double *lp0, double *p, double *v, double *a,
+            double *pd, double *pdd);
 
 /* Right stretch U = (F^T F)^{1/2} diagonal by Jacobi eigen-iteration. */
 void orc_stretch_diag(int32_t d, const double *F, double *Udiag);

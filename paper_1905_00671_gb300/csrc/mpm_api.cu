@@ -34,6 +34,9 @@ DevView Ctx::view() const {
   v.an = an;
   v.pdn = pdn;
   v.pddn = pddn;
+  v.phi = phi;
+  v.act = act;
+  v.sh_nrm = sh_nrm;
   v.fixed = fixed;
   v.u_fixed = u_fixed;
   v.u_value = u_value;
@@ -231,6 +234,7 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   rc = run_pattern(c);
   if (rc) return rc;
   run_initial_guess(c);
+  run_renorm(c);
   rc = read_dev_err(c);
   if (rc) return rc;
   c.prepared = true;
@@ -269,8 +273,14 @@ int newton(Ctx &c) {
       return MPM_ERR_NEWTON_DIVERGED;
     }
     run_jacobian(c, 1);
-    run_scale_system(c, c.rhs, c.R);
-    run_block_jacobi(c);
+    if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
+      rc = schur_setup(c);  // on the unscaled blocks
+      if (rc) return rc;
+      run_scale_system(c, c.rhs, c.R);
+    } else {
+      run_scale_system(c, c.rhs, c.R);
+      run_block_jacobi(c);
+    }
     rc = read_dev_err(c);
     if (rc) return rc;
     int its = 0;
@@ -321,9 +331,10 @@ int do_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
 void free_all(Ctx &c) {
   for (cudaEvent_t e : c.ev) cudaEventDestroy(e);
   c.ev.clear();
+  schur_free(c);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
                   c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS,
-                  c.sh_S0, c.m, c.rec, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.fixed, c.u_fixed,
+                  c.sh_S0, c.m, c.rec, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.val, c.dscale, c.dinv, c.X, c.R, c.dX,
                   c.rhs, c.w, c.V, c.Z, c.H, c.gvec, c.cs, c.sn, c.yv, c.hcol, c.part, c.scal,
@@ -359,8 +370,11 @@ void mpm_default_options(mpm_options *o) {
   o->newton_max = 25;
   o->newton_stag = 0.0;
   o->krylov_rtol = 1e-8;
-  o->krylov_restart = 30;
+  o->krylov_restart = 120;
   o->krylov_max = 3000;
+  o->precond = MPM_PRECOND_SCHUR_MG;
+  o->min_volume_fraction = 1e-4;
+  o->profile = 0;
   o->stream = nullptr;
 }
 
@@ -375,10 +389,13 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   for (int k = 0; k < grid->dim; ++k)
     if (grid->ncell[k] < 1) return MPM_ERR_BAD_ARG;
   if (P->n > INT32_MAX / 2) return MPM_ERR_BAD_ARG;
-  if (opt->krylov_restart < 1 || opt->krylov_restart > 63) return MPM_ERR_BAD_ARG;
+  if (opt->krylov_restart < 1 || opt->krylov_restart > 128) return MPM_ERR_BAD_ARG;
+  if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
+    return MPM_ERR_BAD_ARG;
   if (P->n_surf < 0 || (P->n_surf > 0 && (!P->surf_id || !P->surf_normal || !P->surf_area)))
     return MPM_ERR_BAD_ARG;
   if (!(mat->mu_f > 0.0)) return MPM_ERR_BAD_ARG;
+  if (!(opt->min_volume_fraction >= 0.0)) return MPM_ERR_BAD_ARG;
   // every surface id must address an entry of the load arrays
   if (P->surf_id)
     for (int64_t i = 0; i < P->n; ++i)
@@ -421,6 +438,7 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   s.rho_s = mat->rho_s;
   s.phi0 = mat->phi0;
   s.alpha_vis = c.dyn ? mat->alpha_vis : 0.0;
+  s.phi_min = opt->min_volume_fraction;
   for (int k = 0; k < 3; ++k) s.g[k] = k < c.d ? mat->g[k] : 0.0;
   c.n = P->n;
   c.n_surf = P->n_surf;
@@ -455,6 +473,9 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   A(&c.an, d * nn);
   A(&c.pdn, nn);
   A(&c.pddn, nn);
+  A(&c.phi, nn);
+  A(&c.act, nn);
+  A(&c.sh_nrm, 5 * n);
   A(&c.fixed, N);
   A(&c.u_fixed, d * nn);
   A(&c.p_fixed, nn);
@@ -481,11 +502,12 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   A(&c.cs, m);
   A(&c.sn, m);
   A(&c.yv, m);
-  A(&c.hcol, 128);
-  A(&c.part, 304 * 64);
+  A(&c.hcol, 2 * 129);
+  A(&c.part, 304 * 129);
   A(&c.scal, 8);
   c.scan_cap = 4096;
   A(&c.scan_tmp, c.scan_cap);
+  if (!rc && c.opt.precond == MPM_PRECOND_SCHUR_MG) rc = schur_alloc(c);
   if (!rc && cudaHostAlloc((void **)&c.h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess)
     rc = MPM_ERR_NO_MEMORY;
   if (!rc && cudaHostAlloc((void **)&c.h_scalar, 8 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
@@ -643,12 +665,13 @@ int64_t mpm_debug_pattern(mpm_ctx *h, int64_t *row_ptr, int32_t *col_idx, int64_
   return c.nnzb;
 }
 
-int mpm_debug_nodal(mpm_ctx *h, double *M, double *Pn) {
+int mpm_debug_nodal(mpm_ctx *h, double *M, double *Pn, double *phi) {
   if (!h) return MPM_ERR_BAD_ARG;
   Ctx &c = h->c;
   if (!c.prepared) return MPM_ERR_BAD_ARG;
   if (M) cudaMemcpyAsync(M, c.M, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
   if (Pn) cudaMemcpyAsync(Pn, c.Pn, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
+  if (phi) cudaMemcpyAsync(phi, c.phi, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
   return check_cuda(c, cudaStreamSynchronize(c.st), "debug_nodal");
 }
 
@@ -668,6 +691,31 @@ int mpm_debug_eval(mpm_ctx *h, const double *X, double *R, double *Jv, int32_t a
     cudaMemcpyAsync(Jv, c.val, sizeof(double) * c.nnzb * c.nb * c.nb, cudaMemcpyDeviceToHost, c.st);
   }
   return check_cuda(c, cudaStreamSynchronize(c.st), "debug_eval");
+}
+
+int mpm_debug_precond(mpm_ctx *h, const double *X, const double *v, double *z) {
+  if (!h || !X || !v || !z) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  const int64_t N = c.N();
+  cudaMemcpyAsync(c.X, X, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
+  run_point_eval(c, c.X);
+  int rc = read_dev_err(c);
+  if (rc) return rc;
+  run_residual(c, c.X, c.R, 1);
+  run_jacobian(c, 1);
+  if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
+    rc = schur_setup(c);
+    if (rc) return rc;
+    run_scale_system(c, c.rhs, c.R);
+  } else {
+    run_scale_system(c, c.rhs, c.R);
+    run_block_jacobi(c);
+  }
+  cudaMemcpyAsync(c.w, v, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
+  run_precond(c, c.w, c.dX);
+  cudaMemcpyAsync(z, c.dX, sizeof(double) * N, cudaMemcpyDeviceToHost, c.st);
+  return check_cuda(c, cudaStreamSynchronize(c.st), "debug_precond");
 }
 
 }  // extern "C"

@@ -45,24 +45,6 @@ __device__ inline bool in_box(const DevView &v, int64_t q, const int ac[3], int 
   return true;
 }
 
-// S_a, S0_a and the t_n-gradient Gn_a of the node at slots off of point q.
-template <int D>
-__device__ inline void node_basis(const DevView &v, int64_t q, const int off[3], double &S,
-                                  double &S0, double Gn[3]) {
-  const int64_t n = v.n;
-  double s[3] = {1.0, 1.0, 1.0}, ds[3] = {0.0, 0.0, 0.0}, s0[3] = {1.0, 1.0, 1.0};
-  for (int k = 0; k < D; ++k) {
-    s[k] = v.sh_S[(k * MAXS + off[k]) * n + q];
-    ds[k] = v.sh_dS[(k * MAXS + off[k]) * n + q];
-    s0[k] = v.sh_S0[(k * MAXS + off[k]) * n + q];
-  }
-  S = s[0] * s[1] * s[2];
-  S0 = s0[0] * s0[1] * s0[2];
-  Gn[0] = ds[0] * s[1] * s[2];
-  Gn[1] = s[0] * ds[1] * s[2];
-  Gn[2] = s[0] * s[1] * ds[2];
-}
-
 // g = Gn . dF^{-1}
 template <int D>
 __device__ inline void spatial_grad(const DevView &v, int64_t q, const double Gn[3], double g[3]) {
@@ -145,14 +127,18 @@ __global__ void k_pattern_fill(GridP g, const uint64_t *__restrict__ mask,
 }
 
 // ---------------------------------------------------------------- Dirichlet
-// Fixed DOFs: Dirichlet data, and every DOF of an inactive node (no mass).
+// Fixed DOFs: Dirichlet data, and every DOF of an inactive node, i.e. a node
+// whose volume fraction sum_p S_ip V_p / h^d does not exceed phi_min (a
+// support reached only by a sliver of a GIMP domain carries no stiffness,
+// mass or storage worth an unknown and would leave the system near-singular).
 // Initial Newton guess: dU = prescribed increment or 0, P = p^ or P_n.
 template <int D>
-__global__ void k_initial_guess(GridP g, DevView v, double *__restrict__ X) {
+__global__ void k_initial_guess(GridP g, double phi_min, DevView v, double *__restrict__ X) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= g.nnodes) return;
   constexpr int NB = D + 1;
-  const bool inactive = !(v.M[a] > 0.0);
+  const bool inactive = !(v.M[a] > 0.0) || !(v.phi[a] > phi_min);
+  v.act[a] = inactive ? 0 : 1;
   for (int k = 0; k < D; ++k) {
     const bool uf = v.u_fixed[a * D + k] != 0;
     v.fixed[a * NB + k] = (inactive || uf) ? 1 : 0;
@@ -161,6 +147,52 @@ __global__ void k_initial_guess(GridP g, DevView v, double *__restrict__ X) {
   const bool pfx = v.p_fixed[a] != 0;
   v.fixed[a * NB + D] = (inactive || pfx) ? 1 : 0;
   X[a * NB + D] = inactive ? 0.0 : (pfx ? v.p_value[a] : v.Pn[a]);
+}
+
+// Points whose support box holds an inactive node get their basis
+// renormalised over the active box nodes (see basis_at).
+template <int D>
+__global__ void k_renorm(GridP g, DevView v) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = v.n;
+  if (p >= n) return;
+  int packed = v.sh_cnt[p] & ~RENORM_BIT;
+  int f[3], cn[3];
+  for (int k = 0; k < 3; ++k) {
+    f[k] = v.sh_first[k * n + p];
+    cn[k] = unpack_cnt(packed, k);
+  }
+  bool any = false;
+  double sum = 0.0, sum0 = 0.0, gs[3] = {0.0, 0.0, 0.0};
+  for (int s2 = 0; s2 < cn[2]; ++s2)
+    for (int s1 = 0; s1 < cn[1]; ++s1)
+      for (int s0 = 0; s0 < cn[0]; ++s0) {
+        const int nc3[3] = {f[0] + s0, f[1] + s1, f[2] + s2};
+        const int64_t a = node_index(g, nc3);
+        if (!v.act[a]) {
+          any = true;
+          continue;
+        }
+        double s[3] = {1.0, 1.0, 1.0}, ds[3] = {0.0, 0.0, 0.0}, z[3] = {1.0, 1.0, 1.0};
+        const int sl[3] = {s0, s1, s2};
+        for (int k = 0; k < D; ++k) {
+          s[k] = v.sh_S[(k * MAXS + sl[k]) * n + p];
+          ds[k] = v.sh_dS[(k * MAXS + sl[k]) * n + p];
+          z[k] = v.sh_S0[(k * MAXS + sl[k]) * n + p];
+        }
+        sum += s[0] * s[1] * s[2];
+        sum0 += z[0] * z[1] * z[2];
+        gs[0] += ds[0] * s[1] * s[2];
+        gs[1] += s[0] * ds[1] * s[2];
+        gs[2] += s[0] * s[1] * ds[2];
+      }
+  if (any) {
+    v.sh_nrm[0 * n + p] = 1.0 / sum;
+    for (int k = 0; k < 3; ++k) v.sh_nrm[(1 + k) * n + p] = gs[k];
+    v.sh_nrm[4 * n + p] = 1.0 / sum0;
+    packed |= RENORM_BIT;
+  }
+  v.sh_cnt[p] = packed;
 }
 
 // ---------------------------------------------------------------- points
@@ -185,10 +217,10 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
     for (int s1 = 0; s1 < cn[1]; ++s1)
       for (int s0 = 0; s0 < cn[0]; ++s0) {
         const int off[3] = {s0, s1, s2};
-        double Sa, S0a, Gn[3];
-        node_basis<D>(v, p, off, Sa, S0a, Gn);
         const int nc3[3] = {f[0] + s0, f[1] + s1, f[2] + s2};
         const int64_t a = node_index(g, nc3);
+        double Sa, S0a, Gn[3];
+        basis_at<D>(v, p, off, a, Sa, S0a, Gn);
         const double P = X[a * NB + D];
         for (int i = 0; i < D; ++i) {
           const double dU = X[a * NB + i];
@@ -317,7 +349,7 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
           int off[3];
           if (!in_box<D>(v, q, ac, off)) continue;
           double Sa, S0a, Gn[3], ga[3];
-          node_basis<D>(v, q, off, Sa, S0a, Gn);
+          basis_at<D>(v, q, off, a, Sa, S0a, Gn);
           spatial_grad<D>(v, q, Gn, ga);
           const double cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
           for (int i = 0; i < D; ++i) {
@@ -387,8 +419,8 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restric
           int oa[3], ob[3];
           if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
           double Sa, S0a, Gna[3], Sb, S0b, Gnb[3], ga[3], gb[3];
-          node_basis<D>(v, q, oa, Sa, S0a, Gna);
-          node_basis<D>(v, q, ob, Sb, S0b, Gnb);
+          basis_at<D>(v, q, oa, a, Sa, S0a, Gna);
+          basis_at<D>(v, q, ob, bn, Sb, S0b, Gnb);
           spatial_grad<D>(v, q, Gna, ga);
           spatial_grad<D>(v, q, Gnb, gb);
           const double cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
@@ -485,8 +517,15 @@ int run_pattern(Ctx &c) {
 
 void run_initial_guess(Ctx &c) {
   const DevView v = c.view();
-  if (c.d == 2) k_initial_guess<2><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, v, c.X);
-  else k_initial_guess<3><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, v, c.X);
+  if (c.d == 2) k_initial_guess<2><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, c.s.phi_min, v, c.X);
+  else k_initial_guess<3><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, c.s.phi_min, v, c.X);
+  UPMPM_LAUNCH(c);
+}
+
+void run_renorm(Ctx &c) {
+  const DevView v = c.view();
+  if (c.d == 2) k_renorm<2><<<nblk(c.n), TPB, 0, c.st>>>(c.g, v);
+  else k_renorm<3><<<nblk(c.n), TPB, 0, c.st>>>(c.g, v);
   UPMPM_LAUNCH(c);
 }
 

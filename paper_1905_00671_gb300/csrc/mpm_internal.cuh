@@ -23,6 +23,8 @@
 
 namespace upmpm {
 
+struct MGHier;
+
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
 
 // ---- particle fields ------------------------------------------------------
@@ -86,6 +88,7 @@ struct StepP {
   double dt, beta, gamma, rho_f, alpha_vis;
   double g[3];
   double phi0, rho_s;
+  double phi_min;  // minimum nodal volume fraction of an active node
 };
 
 // all device pointers the kernels need, passed by value
@@ -103,6 +106,9 @@ struct DevView {
   double *rec;              // RC_COUNT * n
   // nodes
   double *M, *Pn, *vn, *an, *pdn, *pddn;  // vn/an: d * nnodes (field-major)
+  double *phi;              // nodal volume fraction sum_p S V_p / h^d
+  uint8_t *act;             // node active (mass > 0 and phi > phi_min)
+  double *sh_nrm;           // 5 * n: 1/sum S, grad sum S (3), 1/sum S0 over active box nodes
   uint8_t *fixed;           // nb * nnodes, node-interleaved
   uint8_t *u_fixed;         // d * nnodes node-interleaved
   double *u_value;          // d * nnodes
@@ -140,6 +146,9 @@ struct Ctx {
   double *sh_S = nullptr, *sh_dS = nullptr, *sh_S0 = nullptr;
   double *m = nullptr, *rec = nullptr;
   double *M = nullptr, *Pn = nullptr, *vn = nullptr, *an = nullptr, *pdn = nullptr, *pddn = nullptr;
+  double *phi = nullptr;
+  uint8_t *act = nullptr;
+  double *sh_nrm = nullptr;
   uint8_t *fixed = nullptr, *u_fixed = nullptr, *p_fixed = nullptr;
   double *u_value = nullptr, *p_value = nullptr, *trac = nullptr, *trac_raw = nullptr, *flux = nullptr;
   int has_flux = 0;
@@ -165,6 +174,12 @@ struct Ctx {
   double *hcol = nullptr, *part = nullptr, *scal = nullptr;
   int nparts = 0;
 
+  // Schur-complement block preconditioner (mpm_mg.cu)
+  MGHier *mgA = nullptr, *mgS = nullptr;
+  double *Aval = nullptr, *Sval = nullptr, *DAinv = nullptr;
+  double *vu = nullptr, *wu = nullptr, *zu = nullptr, *vp = nullptr, *zp = nullptr;
+  int64_t sub_cap = 0;
+
   // scan scratch
   int32_t *scan_tmp = nullptr;
   int64_t scan_cap = 0;
@@ -189,7 +204,8 @@ void run_p2g(Ctx &c);
 void run_g2p(Ctx &c);
 // assembly
 int run_pattern(Ctx &c);                          // builds row_ptr / col / row_of
-void run_initial_guess(Ctx &c);
+void run_initial_guess(Ctx &c);   // also sets the active flags
+void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
 void run_point_eval(Ctx &c, const double *X);
 void run_residual(Ctx &c, const double *X, double *R, int apply_bc);
 void run_jacobian(Ctx &c, int apply_bc);
@@ -197,9 +213,16 @@ void run_jacobian(Ctx &c, int apply_bc);
 void run_scale_system(Ctx &c, double *rhs_out, const double *R);  // scales val, rhs = -D R
 void run_block_jacobi(Ctx &c);
 int run_fgmres(Ctx &c, const double *b, double *x, double rtol, int maxit, int *iters);
+void run_precond(Ctx &c, const double *v, double *z);  // z = M^{-1} v (scaled system)
 double run_norm(Ctx &c, const double *x);          // synchronises
 void run_axpy(Ctx &c, double *y, double a, const double *x, int64_t n);
 void run_unscale_add(Ctx &c, double *X, const double *xhat);  // X += D xhat
+
+// Schur-complement multigrid preconditioner
+int schur_alloc(Ctx &c);
+void schur_free(Ctx &c);
+int schur_setup(Ctx &c);                               // after run_scale_system
+void schur_apply(Ctx &c, const double *v, double *z);  // z = M^{-1} v
 
 // scan: out[i] = sum_{j<i} in[j]; returns the total (synchronises)
 int64_t scan_exclusive(Ctx &c, const int32_t *in, int32_t *out, int64_t n);
@@ -217,6 +240,7 @@ void prof_collect(Ctx &c);   // synchronises; adds elapsed times into stats
 
 // ---- device helpers -------------------------------------------------------
 __host__ __device__ inline int unpack_cnt(int packed, int k) { return (packed >> (4 * k)) & 15; }
+constexpr int RENORM_BIT = 1 << 15;  // in sh_cnt: the point's basis is renormalised
 
 template <int D>
 __device__ inline double det_d(const double *A) {
@@ -243,6 +267,38 @@ __device__ inline void inv_d(const double *A, double *B) {
     B[6] = (A[3] * A[7] - A[4] * A[6]) / det;
     B[7] = (A[1] * A[6] - A[0] * A[7]) / det;
     B[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+  }
+}
+
+// S_a, S0_a and the t_n-gradient Gn_a of box node a (slots off) of point q.
+// Nodes that are inactive are removed from the point's basis, which is then
+// renormalised over its active box nodes (constants stay exactly reproduced):
+//   S' = S / sum S,  Gn' = (Gn - S' grad sum S) / sum S,  S0' = S0 / sum S0.
+template <int D>
+__device__ inline void basis_at(const DevView &v, int64_t q, const int off[3], int64_t a, double &S,
+                                double &S0, double Gn[3]) {
+  const int64_t n = v.n;
+  double s[3] = {1.0, 1.0, 1.0}, ds[3] = {0.0, 0.0, 0.0}, s0[3] = {1.0, 1.0, 1.0};
+  for (int k = 0; k < D; ++k) {
+    s[k] = v.sh_S[(k * MAXS + off[k]) * n + q];
+    ds[k] = v.sh_dS[(k * MAXS + off[k]) * n + q];
+    s0[k] = v.sh_S0[(k * MAXS + off[k]) * n + q];
+  }
+  S = s[0] * s[1] * s[2];
+  S0 = s0[0] * s0[1] * s0[2];
+  Gn[0] = ds[0] * s[1] * s[2];
+  Gn[1] = s[0] * ds[1] * s[2];
+  Gn[2] = s[0] * s[1] * ds[2];
+  if (v.sh_cnt[q] & RENORM_BIT) {
+    if (!v.act[a]) {
+      S = S0 = 0.0;
+      Gn[0] = Gn[1] = Gn[2] = 0.0;
+      return;
+    }
+    const double sinv = v.sh_nrm[0 * n + q];
+    S *= sinv;
+    for (int k = 0; k < D; ++k) Gn[k] = (Gn[k] - S * v.sh_nrm[(1 + k) * n + q]) * sinv;
+    S0 *= v.sh_nrm[4 * n + q];
   }
 }
 

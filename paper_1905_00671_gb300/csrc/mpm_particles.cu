@@ -202,7 +202,7 @@ __global__ void k_p2g(GridP g, DevView v) {
   node_coords(g, a, ac);
   int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   for (int k = 0; k < D; ++k) cand_range<GIMP>(ac[k], g.nc[k], lo[k], hi[k]);
-  double Msum = 0.0, mp = 0.0, mv[3] = {0, 0, 0}, ma[3] = {0, 0, 0}, mpd = 0.0, mpdd = 0.0;
+  double Msum = 0.0, Vsum = 0.0, mp = 0.0, mv[3] = {0, 0, 0}, ma[3] = {0, 0, 0}, mpd = 0.0, mpdd = 0.0;
   for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
     for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
       for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
@@ -223,6 +223,7 @@ __global__ void k_p2g(GridP g, DevView v) {
           if (!in) continue;
           const double w = S * v.m[q];
           Msum += w;
+          Vsum += S * v.pf[PF_V * n + q];
           mp += w * v.pf[PF_P * n + q];
           if (DYN) {
             for (int k = 0; k < D; ++k) {
@@ -236,6 +237,9 @@ __global__ void k_p2g(GridP g, DevView v) {
       }
   const int64_t nn = g.nnodes;
   v.M[a] = Msum;
+  double hd = g.h;
+  for (int k = 1; k < D; ++k) hd *= g.h;
+  v.phi[a] = Vsum / hd;
   const double inv = Msum > 0.0 ? 1.0 / Msum : 0.0;
   v.Pn[a] = mp * inv;
   if (DYN) {
@@ -322,18 +326,10 @@ __global__ void k_g2p(GridP g, StepP s, DevView v, const double *__restrict__ X)
     for (int s1 = 0; s1 < cn[1]; ++s1)
       for (int s0 = 0; s0 < cn[0]; ++s0) {
         const int sl[3] = {s0, s1, s2};
-        double Sv[3], dSv[3];
-        for (int k = 0; k < 3; ++k) {
-          Sv[k] = v.sh_S[(k * MAXS + sl[k]) * n + p];
-          dSv[k] = v.sh_dS[(k * MAXS + sl[k]) * n + p];
-        }
-        const double Sa = Sv[0] * Sv[1] * Sv[2];
-        double Gn[3];
-        Gn[0] = dSv[0] * Sv[1] * Sv[2];
-        Gn[1] = Sv[0] * dSv[1] * Sv[2];
-        Gn[2] = Sv[0] * Sv[1] * dSv[2];
         const int nc3[3] = {f[0] + s0, f[1] + s1, f[2] + s2};
         const int64_t a = node_index(g, nc3);
+        double Sa, S0a, Gn[3];
+        basis_at<D>(v, p, sl, a, Sa, S0a, Gn);
         for (int i = 0; i < D; ++i) {
           const double dU = X[a * NB + i];
           du[i] += Sa * dU;

@@ -20,6 +20,7 @@ namespace {
 
 constexpr int TPB = 256;
 constexpr int NPART = 304;  // partial sums per reduction (2 x 152 SMs)
+constexpr int PSTR = 129;   // stride of the per-block partial sums (restart <= 128)
 inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
 
 __device__ inline double block_sum(double v) {
@@ -291,7 +292,7 @@ __global__ void k_multidot_partial(const double *__restrict__ V, int cnt, const 
          k += (int64_t)gridDim.x * blockDim.x)
       acc += vi[k] * w[k];
     acc = block_sum(acc);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * 64 + i] = acc;
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = acc;
   }
 }
 
@@ -301,7 +302,7 @@ __global__ void k_multidot_reduce(const double *__restrict__ part, int np, int c
   const int i = blockIdx.x;
   if (i >= cnt) return;
   double acc = 0.0;
-  for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * 64 + i];
+  for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * PSTR + i];
   acc = block_sum(acc);
   if (threadIdx.x == 0) h[i] = acc;
 }
@@ -322,7 +323,7 @@ __global__ void k_orth_update(double *__restrict__ w, const double *__restrict__
          k += (int64_t)gridDim.x * blockDim.x)
       acc += w[k] * w[k];
     acc = block_sum(acc);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * 64] = acc;
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR] = acc;
   } else {
     for (int i = 0; i < cnt; ++i) {
       double acc = 0.0;
@@ -330,7 +331,7 @@ __global__ void k_orth_update(double *__restrict__ w, const double *__restrict__
            k += (int64_t)gridDim.x * blockDim.x)
         acc += V[(int64_t)i * n + k] * w[k];
       acc = block_sum(acc);
-      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * 64 + i] = acc;
+      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = acc;
     }
   }
 }
@@ -343,11 +344,11 @@ __global__ void k_arnoldi_finish(const double *__restrict__ part, int np, int j,
                                  double *__restrict__ H, double *__restrict__ g, double *__restrict__ cs,
                                  double *__restrict__ sn, double *__restrict__ scal) {
   double acc = 0.0;
-  for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * 64];
+  for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * PSTR];
   acc = block_sum(acc);
   if (threadIdx.x != 0) return;
   const double hn = sqrt(acc);
-  double col[65];
+  double col[PSTR];
   for (int i = 0; i <= j; ++i) col[i] = h1[i] + h2[i];
   for (int i = 0; i < j; ++i) {
     const double t = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -411,9 +412,13 @@ void spmv(Ctx &c, const double *x, double *y) {
 template <int NB>
 void precond(Ctx &c, const double *x, double *y) {
   prof_begin(c, MPM_PROF_PRECOND);
-  k_bj_apply<NB><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g.nnodes, c.dinv, x, y);
+  if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
+    schur_apply(c, x, y);
+  } else {
+    k_bj_apply<NB><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g.nnodes, c.dinv, x, y);
+    UPMPM_LAUNCH(c);
+  }
   prof_end(c, MPM_PROF_PRECOND);
-  UPMPM_LAUNCH(c);
 }
 
 double read_scalar(Ctx &c, const double *dptr) {
@@ -428,7 +433,7 @@ int fgmres_impl(Ctx &c, const double *b, double *x, double rtol, int maxit, int 
   const int m = c.m_restart;
   const int gN = nblk(N);
   double *w = c.w;
-  double *h1 = c.hcol, *h2 = c.hcol + 64;
+  double *h1 = c.hcol, *h2 = c.hcol + PSTR;
   cudaMemsetAsync(x, 0, sizeof(double) * N, c.st);
   // beta = ||b||, V_0 = b / beta
   k_dot_partial<<<NPART, TPB, 0, c.st>>>(b, b, N, c.part);
@@ -546,6 +551,11 @@ void run_block_jacobi(Ctx &c) {
   else
     k_block_jacobi<4><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dinv, c.err);
   UPMPM_LAUNCH(c);
+}
+
+void run_precond(Ctx &c, const double *v, double *z) {
+  if (c.nb == 3) precond<3>(c, v, z);
+  else precond<4>(c, v, z);
 }
 
 int run_fgmres(Ctx &c, const double *b, double *x, double rtol, int maxit, int *iters) {

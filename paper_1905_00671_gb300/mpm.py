@@ -21,13 +21,14 @@ ERRORS = {-1: "MPM_ERR_BAD_ARG", -2: "MPM_ERR_OUT_OF_GRID", -3: "MPM_ERR_NEGATIV
 MPM_SHAPE_ORIG, MPM_SHAPE_GIMP = 0, 1
 MPM_QUASISTATIC, MPM_NEWMARK = 0, 1
 MPM_FP64, MPM_MIXED = 0, 1
+MPM_PRECOND_BLOCK_JACOBI, MPM_PRECOND_SCHUR_MG = 0, 1
 MPM_MAX_NEWTON = 64
 PROF = {"spmv": 0, "jacobian": 1, "residual": 2, "point": 3, "orth": 4, "p2g": 5, "g2p": 6,
         "precond": 7}
 
 EXPORTED = ["mpm_default_options", "mpm_create", "mpm_step", "mpm_read", "mpm_get_stats",
             "mpm_last_error", "mpm_destroy", "mpm_debug_bin", "mpm_debug_prepare",
-            "mpm_debug_pattern", "mpm_debug_nodal", "mpm_debug_eval"]
+            "mpm_debug_pattern", "mpm_debug_nodal", "mpm_debug_eval", "mpm_debug_precond"]
 
 
 class MPMError(RuntimeError):
@@ -58,7 +59,8 @@ class mpm_options(C.Structure):
                 ("gamma", C.c_double), ("stabilize", C.c_int32), ("tau_scale", C.c_double),
                 ("precision", C.c_int32), ("newton_rtol", C.c_double), ("newton_max", C.c_int32),
                 ("newton_stag", C.c_double), ("krylov_rtol", C.c_double),
-                ("krylov_restart", C.c_int32), ("krylov_max", C.c_int32), ("profile", C.c_int32),
+                ("krylov_restart", C.c_int32), ("krylov_max", C.c_int32), ("precond", C.c_int32),
+                ("min_volume_fraction", C.c_double), ("profile", C.c_int32),
                 ("stream", C.c_void_p)]
 
 
@@ -117,8 +119,9 @@ def load(build_if_missing: bool = False):
     lib.mpm_debug_prepare.argtypes = [P, C.c_double, C.POINTER(mpm_loads), C.POINTER(mpm_bcs)]
     lib.mpm_debug_pattern.argtypes = [P, P, P, C.c_int64]
     lib.mpm_debug_pattern.restype = C.c_int64
-    lib.mpm_debug_nodal.argtypes = [P, P, P]
+    lib.mpm_debug_nodal.argtypes = [P, P, P, P]
     lib.mpm_debug_eval.argtypes = [P, P, P, P, C.c_int32]
+    lib.mpm_debug_precond.argtypes = [P, P, P, P]
     _lib = lib
     return lib
 
@@ -285,10 +288,9 @@ class Simulation:
 
     def debug_nodal(self):
         nn = self.w.nnodes
-        M = np.zeros(nn)
-        Pn = np.zeros(nn)
-        self._check(self.lib.mpm_debug_nodal(self.ctx, _p(M), _p(Pn)), "mpm_debug_nodal")
-        return M, Pn
+        M, Pn, phi = np.zeros(nn), np.zeros(nn), np.zeros(nn)
+        self._check(self.lib.mpm_debug_nodal(self.ctx, _p(M), _p(Pn), _p(phi)), "mpm_debug_nodal")
+        return M, Pn, phi
 
     def debug_eval(self, X, nnzb=None, apply_bc=False):
         nb = self.w.dim + 1
@@ -298,6 +300,13 @@ class Simulation:
         self._check(self.lib.mpm_debug_eval(self.ctx, _p(X), _p(R), _p(Jv), int(apply_bc)),
                     "mpm_debug_eval")
         return R, Jv
+
+    def debug_precond(self, X, v):
+        X = _f64(X).reshape(-1)
+        v = _f64(v).reshape(-1)
+        z = np.zeros_like(v)
+        self._check(self.lib.mpm_debug_precond(self.ctx, _p(X), _p(v), _p(z)), "mpm_debug_precond")
+        return z
 
     def close(self):
         if getattr(self, "ctx", None):

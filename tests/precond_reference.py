@@ -1,0 +1,133 @@
+"""Numpy/scipy restatement of the library's Newton-system preconditioner, for
+testing the CUDA implementation element by element (test infrastructure; the
+preconditioner is a solver choice, not part of the paper's method, so its
+reference is a restatement of the same algorithm, not an oracle).
+
+Algorithm (as in the library):
+  * scaled system  D J D,  D_ii = |J_ii|^{-1/2} (1 where J_ii = 0);
+  * blocks of the unscaled J: A (u-u), B1 (u-p), B2 (p-u), C (p-p);
+  * S = C - B2 diag_blocks(A)^{-1} B1 kept on the block sparsity of J, the
+    dropped part of every row added to its diagonal;
+  * z_p = V(S) v_p,  z_u = V(A) (v_u - B1 z_p), preconditioner of the scaled
+    system  z = D^{-1} M^{-1} (D^{-1} v);
+  * V-cycle: factor-2 vertex coarsening per axis ((n + 1) // 2 nodes) while
+    min(n) > 3 and nodes > 32, bilinear P (rows of Dirichlet / inactive DOFs
+    zeroed on the finest level), Galerkin P^T A P, damped block Jacobi
+    (omega 0.6, 2 + 2 sweeps, first sweep from zero), 40 sweeps on the
+    coarsest level.
+"""
+import numpy as np
+import scipy.sparse as sps
+
+OMEGA, PRE, POST, COARSE = 0.6, 2, 2, 40
+
+
+def prolong_1d(nf):
+    nc = (nf + 1) // 2
+    rows, cols, vals = [], [], []
+    for a in range(nf):
+        if a % 2 == 0:
+            rows.append(a); cols.append(a // 2); vals.append(1.0)
+        else:
+            rows.append(a); cols.append((a - 1) // 2); vals.append(0.5)
+            if (a + 1) // 2 < nc:
+                rows.append(a); cols.append((a + 1) // 2); vals.append(0.5)
+    return sps.csr_matrix((vals, (rows, cols)), shape=(nf, nc)), nc
+
+
+def block_inv(A, B):
+    n = A.shape[0] // B
+    A = A.tocsr()
+    out = []
+    for a in range(n):
+        M = A[a * B:(a + 1) * B, a * B:(a + 1) * B].toarray()
+        try:
+            inv = np.linalg.inv(M)
+            if not np.all(np.isfinite(inv)):
+                raise np.linalg.LinAlgError
+        except np.linalg.LinAlgError:
+            inv = np.eye(B)
+        out.append(sps.csr_matrix(inv))
+    return sps.block_diag(out, format="csr")
+
+
+def hierarchy(A, nn, dim, B, free):
+    levels = []
+    cur = A.tocsr()
+    nnc = list(nn)
+    first = True
+    while True:
+        lev = {"A": cur, "Dinv": block_inv(cur, B)}
+        levels.append(lev)
+        if min(nnc[:dim]) <= 3 or int(np.prod(nnc)) <= 32 or len(levels) >= 15:
+            break
+        Ps, new = [], []
+        for k in range(dim):
+            P1, c = prolong_1d(nnc[k])
+            Ps.append(P1)
+            new.append(c)
+        P = Ps[0]
+        for k in range(1, dim):
+            P = sps.kron(Ps[k], P)          # x index fastest
+        P = sps.kron(P, sps.eye(B)).tocsr()
+        if first:
+            P = (sps.diags(free.astype(float)) @ P).tocsr()
+            first = False
+        lev["P"] = P
+        cur = (P.T @ cur @ P).tocsr()
+        nnc = new + list(nnc[dim:])
+    return levels
+
+
+def vcycle(levels, b, l=0):
+    A, Dinv = levels[l]["A"], levels[l]["Dinv"]
+    if l == len(levels) - 1:
+        x = OMEGA * (Dinv @ b)
+        for _ in range(COARSE - 1):
+            x = x + OMEGA * (Dinv @ (b - A @ x))
+        return x
+    x = OMEGA * (Dinv @ b)
+    for _ in range(PRE - 1):
+        x = x + OMEGA * (Dinv @ (b - A @ x))
+    P = levels[l]["P"]
+    x = x + P @ vcycle(levels, P.T @ (b - A @ x), l + 1)
+    for _ in range(POST):
+        x = x + OMEGA * (Dinv @ (b - A @ x))
+    return x
+
+
+class SchurMG:
+    """Preconditioner of D J D for the unscaled block-CSR Jacobian J (after
+    Dirichlet elimination) with sparsity (row_ptr, col) and fixed-DOF mask."""
+
+    def __init__(self, J, row_ptr, col, fixed, nn, dim):
+        nb = dim + 1
+        J = J.tocsr()
+        N = J.shape[0]
+        nnod = N // nb
+        d = np.abs(J.diagonal())
+        self.D = np.where(d > 0, 1.0 / np.sqrt(np.where(d > 0, d, 1.0)), 1.0)
+        iu = np.array([a * nb + k for a in range(nnod) for k in range(dim)])
+        ip = np.arange(nnod) * nb + dim
+        self.iu, self.ip = iu, ip
+        A = J[iu][:, iu].tocsr()
+        self.B1 = J[iu][:, ip].tocsr()
+        B2 = J[ip][:, iu].tocsr()
+        C = J[ip][:, ip].tocsr()
+        prod = (B2 @ block_inv(A, dim) @ self.B1).tocsr()
+        rows = np.repeat(np.arange(nnod), np.diff(row_ptr))
+        pat = sps.csr_matrix((np.ones(len(col)), (rows, col)), shape=(nnod, nnod))
+        kept = prod.multiply(pat).tocsr()
+        lump = np.asarray(prod.sum(axis=1)).ravel() - np.asarray(kept.sum(axis=1)).ravel()
+        S = (C - kept - sps.diags(lump)).tocsr()
+        self.LA = hierarchy(A, nn, dim, dim, ~fixed[iu])
+        self.LS = hierarchy(S, nn, dim, 1, ~fixed[ip])
+
+    def apply(self, v):
+        vv = v / self.D
+        zp = vcycle(self.LS, vv[self.ip])
+        zu = vcycle(self.LA, vv[self.iu] - self.B1 @ zp)
+        z = np.zeros_like(v)
+        z[self.iu] = zu
+        z[self.ip] = zp
+        return z / self.D

@@ -71,9 +71,11 @@ def test_stage1_pattern_residual_jacobian(mpm, name):
     np.testing.assert_array_equal(row_ptr, prep["row_ptr"])
     np.testing.assert_array_equal(col, prep["col"])
     # Stage 1
-    M, Pn = sim.debug_nodal()
+    M, Pn, phi = sim.debug_nodal()
     assert rel(M, prep["M"]) <= 1e-13
+    assert rel(phi, prep["phi"]) <= 1e-13
     np.testing.assert_array_equal(M > 0, prep["M"] > 0)
+    np.testing.assert_array_equal((M > 0) & (phi > 1e-4), prep["active"])
     assert rel(Pn, prep["nodal"]["P"]) <= 1e-12
     # residual and Jacobian at a perturbed iterate, before Dirichlet elimination
     rng = np.random.default_rng(0)
@@ -181,7 +183,7 @@ def test_bad_arguments_are_rejected(mpm):
 
     w = I.small_footing(seed=3, body=(8, 4), pad=1)
     with pytest.raises(mpm.MPMError) as e:
-        mpm.Simulation(w, krylov_restart=100)
+        mpm.Simulation(w, krylov_restart=200)
     assert e.value.code == -1
     bad = replace(w, surf_id=np.where(w.surf_id >= 0, w.surf_id + 1000, -1).astype(np.int32))
     with pytest.raises(mpm.MPMError):

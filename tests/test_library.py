@@ -39,7 +39,8 @@ def test_default_options_without_gpu(lib):
     from paper_1905_00671_gb300 import mpm
 
     o = mpm.default_options()
-    assert o.shape == mpm.MPM_SHAPE_GIMP and o.newton_rtol == 1e-8 and o.krylov_restart == 30
+    assert o.shape == mpm.MPM_SHAPE_GIMP and o.newton_rtol == 1e-8 and o.krylov_restart == 120
+    assert o.precond == mpm.MPM_PRECOND_SCHUR_MG
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
