@@ -48,7 +48,8 @@ enum {
   MPM_ERR_KRYLOV_STAGNATED = -6, /* the Krylov solver hit its iteration cap */
   MPM_ERR_TIMEOUT = -7,          /* reserved for bounded device-side waits */
   MPM_ERR_CUDA = -8,             /* a CUDA runtime call failed */
-  MPM_ERR_NO_MEMORY = -9         /* device allocation failed */
+  MPM_ERR_NO_MEMORY = -9,        /* device allocation failed */
+  MPM_ERR_TOO_LARGE = -10        /* size beyond the fixed scratch of mpm_bin_noalloc */
 };
 
 enum { MPM_SHAPE_ORIG = 0, MPM_SHAPE_GIMP = 1 };     /* Sec. 3.1: FE basis or GIMP basis */
@@ -257,6 +258,30 @@ int mpm_debug_eval(mpm_ctx *ctx, const double *X, double *R, double *Jv, int32_t
  * is assembled at X, scaled symmetrically by D = |diag J|^{-1/2}, and M^{-1}
  * is the preconditioner of that scaled system.  X, v, z: nnodes*(dim+1). */
 int mpm_debug_precond(mpm_ctx *ctx, const double *X, const double *v, double *z);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free binning.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory where they bin points
+ * (a solver inside a host application that owns all device memory through its
+ * own pool, or a latency-critical loop that cannot afford the implicit device
+ * synchronisation of cudaMalloc / cudaFree).
+ *
+ * Computes, like the binning inside mpm_step, the cell of every point
+ * (floor((x - origin) / h) per axis, linear id x-fastest) and the points
+ * ordered by (cell, index), without allocating: x_dev (n*dim doubles,
+ * point-major), cell_dev (n int32) and order_dev (n int64) are DEVICE pointers
+ * owned by the caller; stream is a cudaStream_t (NULL = default stream).  The
+ * per-cell counters live in a fixed device array of this library (about 3 MiB
+ * on every GPU that loads it, held until exit), so the grid may have at most
+ * 262,144 cells; larger grids return MPM_ERR_TOO_LARGE.  A point outside the
+ * grid returns MPM_ERR_OUT_OF_GRID (cell_dev then holds -1 for it and
+ * order_dev is not written).  The call returns when the work is done.  The
+ * first call on a device looks up the array's device address and should come
+ * before any stream capture.  All calls on a device share the array and the
+ * call clears what it needs at zero; calls that overlap on the GPU race on it
+ * and must be ordered by the caller. */
+int mpm_bin_noalloc(const mpm_grid *grid, int64_t n, const double *x_dev, int32_t *cell_dev,
+                    int64_t *order_dev, void *stream);
 
 #ifdef __cplusplus
 }

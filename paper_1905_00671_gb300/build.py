@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libupmpm.so")
-UNITS = ["mpm_particles", "mpm_assemble", "mpm_solver", "mpm_mg", "mpm_api"]
+UNITS = ["mpm_particles", "mpm_assemble", "mpm_solver", "mpm_mg", "mpm_api", "mpm_noalloc"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
