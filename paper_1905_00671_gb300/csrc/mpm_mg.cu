@@ -109,49 +109,56 @@ __global__ void k_diag_inv_A(int64_t nnodes, const int32_t *__restrict__ row_ptr
 }
 
 // S row a on J's sparsity: S_ab = C_ab - sum_c B2_ac DAinv_c B1_cb; the part of
-// the product falling outside the sparsity is added to S_aa.
+// the product falling outside the sparsity is added to S_aa.  LN lanes per row.
 template <int D>
 __global__ void k_schur_rows(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                              const int32_t *__restrict__ col, const double *__restrict__ J,
                              const double *__restrict__ DAinv, double *__restrict__ S) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= nnodes) return;
-  constexpr int NB = D + 1;
-  const int r0 = row_ptr[a], r1 = row_ptr[a + 1];
+  constexpr int NB = D + 1, LN = D == 2 ? 8 : 16;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < nnodes;
   double total = 0.0, kept = 0.0;
-  int diag = -1;
-  // full product row sum: sum_c (B2_ac DAinv_c) . (sum_b B1_cb)
-  for (int ec = r0; ec < r1; ++ec) {
-    const int c = col[ec];
-    double w[D];  // B2_ac DAinv_c
-    for (int k = 0; k < D; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < D; ++i) s += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
-      w[k] = s;
-    }
-    double rs[D] = {0};
-    for (int eb = row_ptr[c]; eb < row_ptr[c + 1]; ++eb)
-      for (int k = 0; k < D; ++k) rs[k] += J[(int64_t)eb * NB * NB + k * NB + D];
-    for (int k = 0; k < D; ++k) total += w[k] * rs[k];
-  }
-  for (int eb = r0; eb < r1; ++eb) {
-    const int b = col[eb];
-    if (b == a) diag = eb;
-    double prod = 0.0;
-    for (int ec = r0; ec < r1; ++ec) {
+  int mydiag = -1;
+  if (valid) {
+    const int r0 = row_ptr[a], r1 = row_ptr[a + 1];
+    // full product row sum: sum_c (B2_ac DAinv_c) . (sum_b B1_cb)
+    for (int ec = r0 + lane; ec < r1; ec += LN) {
       const int c = col[ec];
-      const int e_cb = find_col(col, row_ptr[c], row_ptr[c + 1], b);
-      if (e_cb < 0) continue;
+      double rs[D];
+      for (int k = 0; k < D; ++k) rs[k] = 0.0;
+      for (int eb = row_ptr[c]; eb < row_ptr[c + 1]; ++eb)
+        for (int k = 0; k < D; ++k) rs[k] += J[(int64_t)eb * NB * NB + k * NB + D];
       for (int k = 0; k < D; ++k) {
-        double s = 0.0;
-        for (int i = 0; i < D; ++i) s += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
-        prod += s * J[(int64_t)e_cb * NB * NB + k * NB + D];
+        double w = 0.0;
+        for (int i = 0; i < D; ++i) w += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
+        total += w * rs[k];
       }
     }
-    kept += prod;
-    S[eb] = J[(int64_t)eb * NB * NB + D * NB + D] - prod;
+    for (int eb = r0 + lane; eb < r1; eb += LN) {
+      const int b = col[eb];
+      if (b == a) mydiag = eb;
+      double prod = 0.0;
+      for (int ec = r0; ec < r1; ++ec) {
+        const int c = col[ec];
+        const int e_cb = find_col(col, row_ptr[c], row_ptr[c + 1], b);
+        if (e_cb < 0) continue;
+        for (int k = 0; k < D; ++k) {
+          double w = 0.0;
+          for (int i = 0; i < D; ++i) w += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
+          prod += w * J[(int64_t)e_cb * NB * NB + k * NB + D];
+        }
+      }
+      kept += prod;
+      S[eb] = J[(int64_t)eb * NB * NB + D * NB + D] - prod;
+    }
   }
-  if (diag >= 0) S[diag] -= (total - kept);
+  for (int o = LN / 2; o > 0; o >>= 1) {
+    total += __shfl_xor_sync(0xffffffffu, total, o);
+    kept += __shfl_xor_sync(0xffffffffu, kept, o);
+  }
+  if (mydiag >= 0) S[mydiag] -= (total - kept);
 }
 
 // ------------------------------------------------------------ Schur apply
@@ -173,17 +180,25 @@ __global__ void k_b1_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ col, const double *__restrict__ Js,
                             const double *__restrict__ dsc, const double *__restrict__ zp,
                             const double *__restrict__ vu, double *__restrict__ wu) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= nnodes) return;
-  constexpr int NB = D + 1;
+  constexpr int NB = D + 1, LN = D == 2 ? 8 : 16;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < nnodes;
   double acc[D];
-  for (int k = 0; k < D; ++k) acc[k] = vu[a * D + k];
-  for (int e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
-    const int64_t b = col[e];
-    const double z = zp[b] / dsc[b * NB + D];
-    for (int k = 0; k < D; ++k) acc[k] -= Js[(int64_t)e * NB * NB + k * NB + D] * z / dsc[a * NB + k];
+  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  if (valid) {
+    const int e1 = row_ptr[a + 1];
+    for (int e = row_ptr[a] + lane; e < e1; e += LN) {
+      const int64_t b = col[e];
+      const double z = zp[b] / dsc[b * NB + D];
+      for (int k = 0; k < D; ++k) acc[k] = fma(Js[(int64_t)e * NB * NB + k * NB + D], z, acc[k]);
+    }
   }
-  for (int k = 0; k < D; ++k) wu[a * D + k] = acc[k];
+  for (int o = LN / 2; o > 0; o >>= 1)
+    for (int k = 0; k < D; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if (!valid || lane != 0) return;
+  for (int k = 0; k < D; ++k) wu[a * D + k] = vu[a * D + k] - acc[k] / dsc[a * NB + k];
 }
 
 template <int D>
@@ -212,19 +227,27 @@ __device__ inline double free_w(const LevelDev &L, int64_t a, int i) {
   return (L.fixed && L.fixed[a * L.mstride + L.moff + i]) ? 0.0 : 1.0;
 }
 
-// A_ab x_b summed over row a (block B), either block-CSR or stencil storage.
-template <int B, int D, bool ST>
-__device__ inline void row_apply(const LevelDev &L, int64_t a, const double *__restrict__ x, double acc[B]) {
-  for (int i = 0; i < B; ++i) acc[i] = 0.0;
+// Lanes per row of the row kernels (a row is one node: up to 49 blocks of the
+// fine block-CSR in 2D, 5^d slots of a coarse stencil).
+template <int D>
+struct LN_ {
+  static constexpr int v = D == 2 ? 8 : 16;
+};
+
+// Partial sum over the blocks of row a handled by `lane` (of LN lanes):
+// acc += A_ab x_b, one FMA per matrix value.
+template <int B, int D, bool ST, int LN>
+__device__ inline void row_partial(const LevelDev &L, int64_t a, int lane, const double *__restrict__ x,
+                                   double acc[B]) {
   if (!ST) {
-    for (int e = L.row_ptr[a]; e < L.row_ptr[a + 1]; ++e) {
+    const int e1 = L.row_ptr[a + 1];
+    for (int e = L.row_ptr[a] + lane; e < e1; e += LN) {
       const int64_t b = L.col[e];
       const double *blk = L.val + (int64_t)e * B * B;
-      for (int i = 0; i < B; ++i) {
-        double s = 0.0;
-        for (int j = 0; j < B; ++j) s += blk[i * B + j] * x[b * B + j];
-        acc[i] += s;
-      }
+      double xb[B];
+      for (int j = 0; j < B; ++j) xb[j] = x[b * B + j];
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) acc[i] = fma(blk[i * B + j], xb[j], acc[i]);
     }
   } else {
     int ac[3];
@@ -233,19 +256,24 @@ __device__ inline void row_apply(const LevelDev &L, int64_t a, const double *__r
     ac[2] = (int)(a / ((int64_t)L.nn[0] * L.nn[1]));
     constexpr int NS = NS_<D>::v;
     const double *base = L.sval + a * NS * B * B;
-    for (int s = 0; s < NS; ++s) {
+    for (int s = lane; s < NS; s += LN) {
       const int o0 = s % 5 - 2, o1 = (s / 5) % 5 - 2, o2 = D == 3 ? s / 25 - 2 : 0;
       const int b0 = ac[0] + o0, b1 = ac[1] + o1, b2 = ac[2] + o2;
       if (b0 < 0 || b0 >= L.nn[0] || b1 < 0 || b1 >= L.nn[1] || b2 < 0 || b2 >= L.nn[2]) continue;
       const int64_t b = b0 + (int64_t)L.nn[0] * (b1 + (int64_t)L.nn[1] * b2);
       const double *blk = base + s * B * B;
-      for (int i = 0; i < B; ++i) {
-        double t = 0.0;
-        for (int j = 0; j < B; ++j) t += blk[i * B + j] * x[b * B + j];
-        acc[i] += t;
-      }
+      double xb[B];
+      for (int j = 0; j < B; ++j) xb[j] = x[b * B + j];
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) acc[i] = fma(blk[i * B + j], xb[j], acc[i]);
     }
   }
+}
+
+template <int B, int LN>
+__device__ inline void lane_reduce(double acc[B]) {
+  for (int o = LN / 2; o > 0; o >>= 1)
+    for (int i = 0; i < B; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
 }
 
 template <int B, int D, bool ST>
@@ -276,22 +304,25 @@ __global__ void k_mg_dinv(LevelDev L, int *err) {
 }
 
 // One damped block-Jacobi sweep: xo = xi + w Dinv (b - A xi); zero_init: xi = 0.
+// LN lanes per row.
 template <int B, int D, bool ST>
 __global__ void k_mg_smooth(LevelDev L, const double *__restrict__ xi, double *__restrict__ xo,
                             const double *__restrict__ b, double omega, int zero_init) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= L.nnodes) return;
+  constexpr int LN = LN_<D>::v;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < L.nnodes;
+  double ax[B];
+  for (int i = 0; i < B; ++i) ax[i] = 0.0;
+  if (valid && !zero_init) row_partial<B, D, ST, LN>(L, a, lane, xi, ax);
+  lane_reduce<B, LN>(ax);
+  if (!valid || lane != 0) return;
   double r[B];
-  if (zero_init) {
-    for (int i = 0; i < B; ++i) r[i] = b[a * B + i];
-  } else {
-    double ax[B];
-    row_apply<B, D, ST>(L, a, xi, ax);
-    for (int i = 0; i < B; ++i) r[i] = b[a * B + i] - ax[i];
-  }
+  for (int i = 0; i < B; ++i) r[i] = b[a * B + i] - ax[i];
   for (int i = 0; i < B; ++i) {
     double s = 0.0;
-    for (int j = 0; j < B; ++j) s += L.dinv[a * B * B + i * B + j] * r[j];
+    for (int j = 0; j < B; ++j) s = fma(L.dinv[a * B * B + i * B + j], r[j], s);
     xo[a * B + i] = (zero_init ? 0.0 : xi[a * B + i]) + omega * s;
   }
 }
@@ -299,11 +330,108 @@ __global__ void k_mg_smooth(LevelDev L, const double *__restrict__ xi, double *_
 template <int B, int D, bool ST>
 __global__ void k_mg_resid(LevelDev L, const double *__restrict__ x, const double *__restrict__ b,
                            double *__restrict__ r) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= L.nnodes) return;
+  constexpr int LN = LN_<D>::v;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < L.nnodes;
   double ax[B];
-  row_apply<B, D, ST>(L, a, x, ax);
+  for (int i = 0; i < B; ++i) ax[i] = 0.0;
+  if (valid) row_partial<B, D, ST, LN>(L, a, lane, x, ax);
+  lane_reduce<B, LN>(ax);
+  if (!valid || lane != 0) return;
   for (int i = 0; i < B; ++i) r[a * B + i] = b[a * B + i] - ax[i];
+}
+
+// ---- coarsest level: exact solve with a dense inverse built at set-up
+// Dense copy of the coarsest operator (n = nnodes * B unknowns).
+template <int B, int D, bool ST>
+__global__ void k_dense_fill(LevelDev L, double *__restrict__ Ad) {
+  const int64_t n = L.nnodes * B;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int64_t ri = t / n, ci = t % n;
+  const int64_t a = ri / B, b = ci / B;
+  const int i = (int)(ri % B), j = (int)(ci % B);
+  double v = 0.0;
+  if (!ST) {
+    const int e = find_col(L.col, L.row_ptr[a], L.row_ptr[a + 1], (int)b);
+    if (e >= 0) v = L.val[(int64_t)e * B * B + i * B + j];
+  } else {
+    int ac[3], bc[3];
+    ac[0] = (int)(a % L.nn[0]); ac[1] = (int)((a / L.nn[0]) % L.nn[1]); ac[2] = (int)(a / ((int64_t)L.nn[0] * L.nn[1]));
+    bc[0] = (int)(b % L.nn[0]); bc[1] = (int)((b / L.nn[0]) % L.nn[1]); bc[2] = (int)(b / ((int64_t)L.nn[0] * L.nn[1]));
+    const int o0 = bc[0] - ac[0], o1 = bc[1] - ac[1], o2 = bc[2] - ac[2];
+    if (o0 >= -2 && o0 <= 2 && o1 >= -2 && o1 <= 2 && o2 >= -2 && o2 <= 2) {
+      constexpr int NS = NS_<D>::v;
+      const int sl = (o0 + 2) + 5 * (o1 + 2) + (D == 3 ? 25 * (o2 + 2) : 0);
+      v = L.sval[(a * NS + sl) * B * B + i * B + j];
+    }
+  }
+  Ad[t] = v;
+}
+
+// In-place Gauss-Jordan inverse of the dense n x n matrix Ad into Ai (one
+// block).  Rows with no usable pivot (singular directions) get a zero row in
+// the inverse, so the coarse correction leaves them alone.
+__global__ void k_dense_invert(int n, double *__restrict__ Ad, double *__restrict__ Ai) {
+  __shared__ int piv;
+  __shared__ double pval;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ai[t] = (t / n == t % n) ? 1.0 : 0.0;
+  double amax = 0.0;
+  for (int t = 0; t < n * n; ++t) amax = fmax(amax, fabs(Ad[t]));
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int p = k;
+      double best = fabs(Ad[k * n + k]);
+      for (int i = k + 1; i < n; ++i)
+        if (fabs(Ad[i * n + k]) > best) { best = fabs(Ad[i * n + k]); p = i; }
+      piv = best > 1e-14 * amax ? p : -1;
+      pval = piv >= 0 ? Ad[p * n + k] : 0.0;
+    }
+    __syncthreads();
+    if (piv < 0) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        Ad[k * n + j] = 0.0;
+        Ai[k * n + j] = 0.0;
+      }
+      continue;
+    }
+    if (piv != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double t1 = Ad[k * n + j]; Ad[k * n + j] = Ad[piv * n + j]; Ad[piv * n + j] = t1;
+        t1 = Ai[k * n + j]; Ai[k * n + j] = Ai[piv * n + j]; Ai[piv * n + j] = t1;
+      }
+    __syncthreads();
+    const double inv = 1.0 / pval;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      Ad[k * n + j] *= inv;
+      Ai[k * n + j] *= inv;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = t / n, j = t % n;
+      if (i == k) continue;
+      const double f = Ad[i * n + k];
+      if (f == 0.0) continue;
+      if (j != k) Ad[i * n + j] -= f * Ad[k * n + j];
+      Ai[i * n + j] -= f * Ai[k * n + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) Ad[i * n + k] = 0.0;
+  }
+}
+
+// x = Ai b
+__global__ void k_dense_apply(int n, const double *__restrict__ Ai, const double *__restrict__ b,
+                              double *__restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = 0; j < n; ++j) s = fma(Ai[(int64_t)i * n + j], b[j], s);
+  x[i] = s;
 }
 
 // weight of coarse node I for fine node a along one axis
@@ -438,6 +566,8 @@ struct MGHier {
   int B = 1, nlev = 0;
   LevelDev L[16];
   double *x[16], *x2[16], *b[16], *r[16];
+  double *Ad = nullptr, *Ai = nullptr;  // dense coarsest operator and its inverse
+  int ncoarse = 0;                       // unknowns of the coarsest level
 };
 
 namespace {
@@ -459,12 +589,19 @@ void mg_setup_t(Ctx &c, MGHier &H) {
     }
     UPMPM_LAUNCH(c);
   }
+  // coarsest level: dense inverse
+  LevelDev &Lc = H.L[H.nlev - 1];
+  const int64_t n = H.ncoarse;
+  if (H.nlev == 1) k_dense_fill<B, D, false><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
+  else k_dense_fill<B, D, true><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
+  k_dense_invert<<<1, 256, 0, c.st>>>((int)n, H.Ad, H.Ai);
+  c.launches += 2;
 }
 
 template <int B, int D>
 void smooth(Ctx &c, MGHier &H, int l, int sweeps, double omega, bool zero_first) {
   LevelDev &L = H.L[l];
-  const int nbk = nblk(L.nnodes);
+  const int nbk = nblk(L.nnodes * LN_<D>::v);
   for (int s = 0; s < sweeps; ++s) {
     const bool z = zero_first && s == 0;
     if (l == 0) k_mg_smooth<B, D, false><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], omega, z);
@@ -478,15 +615,17 @@ template <int B, int D>
 void vcycle_t(Ctx &c, MGHier &H, int l) {
   const double omega = 0.6;
   const int pre = 2, post = 2;
-  if (l == H.nlev - 1) {
-    smooth<B, D>(c, H, l, 40, omega, true);
+  if (l == H.nlev - 1) {  // exact solve on the coarsest grid
+    k_dense_apply<<<nblk(H.ncoarse, 64), 64, 0, c.st>>>(H.ncoarse, H.Ai, H.b[l], H.x[l]);
+    UPMPM_LAUNCH(c);
     return;
   }
   smooth<B, D>(c, H, l, pre, omega, true);
   LevelDev &L = H.L[l];
   const int nbk = nblk(L.nnodes);
-  if (l == 0) k_mg_resid<B, D, false><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
-  else k_mg_resid<B, D, true><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  const int nbr = nblk(L.nnodes * LN_<D>::v);
+  if (l == 0) k_mg_resid<B, D, false><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  else k_mg_resid<B, D, true><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
   k_mg_restrict<B, D><<<nblk(H.L[l + 1].nnodes), TPB, 0, c.st>>>(L, H.L[l + 1], H.r[l], H.b[l + 1]);
   c.launches += 2;
   vcycle_t<B, D>(c, H, l + 1);
@@ -525,14 +664,23 @@ int mg_alloc(Ctx &c, MGHier &H, int B) {
     ++l;
     int mn = 1 << 30;
     for (int k = 0; k < D; ++k) mn = nn[k] < mn ? nn[k] : mn;
-    if (mn <= 3 || L.nnodes <= 32 || l >= 15) break;
+    // the coarsest level is solved exactly: stop at <= 64 nodes or a 2-node axis
+    if (mn <= 2 || L.nnodes <= 64 || l >= 15) break;
     for (int k = 0; k < D; ++k) nn[k] = (nn[k] + 1) / 2;
   }
   H.nlev = l;
+  H.ncoarse = (int)(H.L[l - 1].nnodes * B);
+  if (H.ncoarse > 1024) return MPM_ERR_BAD_ARG;
+  if (cudaMalloc(&H.Ad, sizeof(double) * H.ncoarse * H.ncoarse) ||
+      cudaMalloc(&H.Ai, sizeof(double) * H.ncoarse * H.ncoarse))
+    return MPM_ERR_NO_MEMORY;
   return MPM_OK;
 }
 
 void mg_free(MGHier &H) {
+  cudaFree(H.Ad);
+  cudaFree(H.Ai);
+  H.Ad = H.Ai = nullptr;
   for (int l = 0; l < H.nlev; ++l) {
     cudaFree(H.L[l].dinv);
     cudaFree(H.L[l].sval);
@@ -626,11 +774,11 @@ int schur_setup(Ctx &c) {
   if (d == 2) {
     k_extract_A<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, c.val, c.Aval);
     k_diag_inv_A<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.Aval, c.DAinv);
-    k_schur_rows<2><<<nblk(nn, 128), 128, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.DAinv, c.Sval);
+    k_schur_rows<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.DAinv, c.Sval);
   } else {
     k_extract_A<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, c.val, c.Aval);
     k_diag_inv_A<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.Aval, c.DAinv);
-    k_schur_rows<3><<<nblk(nn, 128), 128, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.DAinv, c.Sval);
+    k_schur_rows<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.DAinv, c.Sval);
   }
   c.launches += 3;
   mg_setup(c, *c.mgA, c.row_ptr, c.col, c.Aval, 0);
@@ -646,8 +794,10 @@ void schur_apply(Ctx &c, const double *v, double *z) {
   else k_split<3><<<nbk, TPB, 0, c.st>>>(nn, v, c.dscale, c.vu, c.vp);
   UPMPM_LAUNCH(c);
   mg_vcycle(c, *c.mgS, c.vp, c.zp);
-  if (c.d == 2) k_b1_update<2><<<nbk, TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dscale, c.zp, c.vu, c.wu);
-  else k_b1_update<3><<<nbk, TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dscale, c.zp, c.vu, c.wu);
+  if (c.d == 2)
+    k_b1_update<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dscale, c.zp, c.vu, c.wu);
+  else
+    k_b1_update<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dscale, c.zp, c.vu, c.wu);
   UPMPM_LAUNCH(c);
   mg_vcycle(c, *c.mgA, c.wu, c.zu);
   if (c.d == 2) k_merge<2><<<nbk, TPB, 0, c.st>>>(nn, c.zu, c.zp, c.dscale, z);

@@ -254,31 +254,43 @@ __global__ void k_bj_apply(int64_t nnodes, const double *__restrict__ dinv, cons
 }
 
 // ---------------------------------------------------------------- SpMV
-// One warp per block row: lanes stride over the row's NB*NB*nblocks values
-// (coalesced), each lane keeps NB partial sums, butterfly-reduced at the end.
-template <int NB>
+// LN lanes per block row; each lane takes whole NB x NB blocks (72 / 128
+// contiguous bytes, so the lanes of a row read one contiguous span), does one
+// FMA per matrix value, and the row's NB sums are reduced across the lanes.
+// (The FP64 pipe of GB300 is narrow, so the kernel spends exactly one FP64
+// instruction per stored value.)
+template <int NB, int LN>
 __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, const double *__restrict__ val,
                            const double *__restrict__ x, double *__restrict__ y) {
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= nnodes) return;
-  const int64_t b0 = (int64_t)row_ptr[row] * NB * NB, b1 = (int64_t)row_ptr[row + 1] * NB * NB;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = row < nnodes;
   double acc[NB];
-  for (int r = 0; r < NB; ++r) acc[r] = 0.0;
-  for (int64_t t = b0 + lane; t < b1; t += 32) {
-    const int64_t e = t / (NB * NB);
-    const int rc = (int)(t - e * NB * NB);
-    const int r = rc / NB, cc = rc % NB;
-    const double prod = __ldg(&val[t]) * __ldg(&x[(int64_t)__ldg(&col[e]) * NB + cc]);
 #pragma unroll
-    for (int q = 0; q < NB; ++q) acc[q] += (q == r) ? prod : 0.0;
+  for (int r = 0; r < NB; ++r) acc[r] = 0.0;
+  if (valid) {
+    const int e1 = row_ptr[row + 1];
+    for (int e = row_ptr[row] + lane; e < e1; e += LN) {
+      const double *blk = val + (int64_t)e * NB * NB;
+      const double *xb = x + (int64_t)__ldg(&col[e]) * NB;
+      double xv[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) xv[c] = __ldg(&xb[c]);
+#pragma unroll
+      for (int r = 0; r < NB; ++r)
+#pragma unroll
+        for (int c = 0; c < NB; ++c) acc[r] = fma(__ldg(&blk[r * NB + c]), xv[c], acc[r]);
+    }
   }
 #pragma unroll
-  for (int q = 0; q < NB; ++q)
-    for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-  if (lane == 0)
-    for (int q = 0; q < NB; ++q) y[row * NB + q] = acc[q];
+  for (int o = LN / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < NB; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  if (valid && lane == 0)
+#pragma unroll
+    for (int r = 0; r < NB; ++r) y[row * NB + r] = acc[r];
 }
 
 // ---------------------------------------------------------------- FGMRES
@@ -402,9 +414,10 @@ __global__ void k_update_x(double *__restrict__ x, const double *__restrict__ Z,
 
 template <int NB>
 void spmv(Ctx &c, const double *x, double *y) {
-  const int64_t threads = c.g.nnodes * 32;
+  constexpr int LN = NB == 3 ? 8 : 16;
+  const int64_t threads = c.g.nnodes * LN;
   prof_begin(c, MPM_PROF_SPMV);
-  k_bsr_spmv<NB><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, c.val, x, y);
+  k_bsr_spmv<NB, LN><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, c.val, x, y);
   prof_end(c, MPM_PROF_SPMV);
   UPMPM_LAUNCH(c);
 }

@@ -11,15 +11,15 @@ Algorithm (as in the library):
   * z_p = V(S) v_p,  z_u = V(A) (v_u - B1 z_p), preconditioner of the scaled
     system  z = D^{-1} M^{-1} (D^{-1} v);
   * V-cycle: factor-2 vertex coarsening per axis ((n + 1) // 2 nodes) while
-    min(n) > 3 and nodes > 32, bilinear P (rows of Dirichlet / inactive DOFs
-    zeroed on the finest level), Galerkin P^T A P, damped block Jacobi
-    (omega 0.6, 2 + 2 sweeps, first sweep from zero), 40 sweeps on the
-    coarsest level.
+    every axis has more than 2 nodes and the level more than 64 nodes,
+    bilinear P (rows of Dirichlet / inactive DOFs zeroed on the finest level),
+    Galerkin P^T A P, damped block Jacobi (omega 0.6, 2 + 2 sweeps, first
+    sweep from zero), exact solve on the coarsest level.
 """
 import numpy as np
 import scipy.sparse as sps
 
-OMEGA, PRE, POST, COARSE = 0.6, 2, 2, 40
+OMEGA, PRE, POST = 0.6, 2, 2
 
 
 def prolong_1d(nf):
@@ -59,7 +59,7 @@ def hierarchy(A, nn, dim, B, free):
     while True:
         lev = {"A": cur, "Dinv": block_inv(cur, B)}
         levels.append(lev)
-        if min(nnc[:dim]) <= 3 or int(np.prod(nnc)) <= 32 or len(levels) >= 15:
+        if min(nnc[:dim]) <= 2 or int(np.prod(nnc)) <= 64 or len(levels) >= 15:
             break
         Ps, new = [], []
         for k in range(dim):
@@ -82,10 +82,7 @@ def hierarchy(A, nn, dim, B, free):
 def vcycle(levels, b, l=0):
     A, Dinv = levels[l]["A"], levels[l]["Dinv"]
     if l == len(levels) - 1:
-        x = OMEGA * (Dinv @ b)
-        for _ in range(COARSE - 1):
-            x = x + OMEGA * (Dinv @ (b - A @ x))
-        return x
+        return np.linalg.solve(A.toarray(), b)
     x = OMEGA * (Dinv @ b)
     for _ in range(PRE - 1):
         x = x + OMEGA * (Dinv @ (b - A @ x))
