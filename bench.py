@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--workload", default="footing")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--profile", default="spmv,orth,jacobian,point,residual,precond",
                     help="kernel classes timed with CUDA events")
     return ap.parse_args()
@@ -218,6 +219,46 @@ def run_ours(args, rank, world, local_rank):
     total_ms = float(t_local.item())
     sim.close()
 
+    final64 = None
+
+    # ---- mixed precision (FP32 Jacobian / preconditioner / Krylov in the FP64
+    # Newton loop): same steps, same timing rules, error against the FP64 run
+    mixed = None
+    if not args.no_mixed:
+        sim_m = mpm.Simulation(w, stream=stream.cuda_stream, precision=mpm.MPM_MIXED,
+                               newton_max=60)
+        sim_r = mpm.Simulation(w, stream=stream.cuda_stream)   # FP64 twin for the error
+        for _ in range(args.warmup):
+            sim_m.step(resident=True)
+            sim_r.step(resident=True)
+        barrier()
+        ms = 0.0
+        newton_m = krylov_m = 0
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            st = sim_m.step(resident=True)
+            ev1[i].record(stream)
+            newton_m += st["newton_iters"]
+            krylov_m += st["krylov_total"]
+            sim_r.step(resident=True)
+            torch.cuda.synchronize()
+            ms += ev0[i].elapsed_time(ev1[i])
+        barrier()
+        a, b = sim_m.read(("u", "p")), sim_r.read(("u", "p"))
+        errs = {k: float(np.abs(a[k] - b[k]).max() / max(np.abs(b[k]).max(), 1e-300)) for k in a}
+        tm = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(tm, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tm.item())
+        mixed = {"value": world * w.n * args.steps / (ms * 1e-3), "unit": UNIT,
+                 "ms_per_step": ms / args.steps, "dtype": "f32 solve / f64 Newton residual",
+                 "newton_iters_per_step": newton_m / args.steps,
+                 "krylov_iters_per_step": krylov_m / args.steps,
+                 "rel_error_vs_fp64": errs}
+        sim_m.close()
+        sim_r.close()
+
     # ---- end to end through the C-ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -283,7 +324,8 @@ def run_ours(args, rank, world, local_rank):
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "steps_per_s": world * args.steps / (total_ms * 1e-3),
             "newton_iters_per_step": newton / args.steps, "krylov_iters_per_step": krylov / args.steps,
-            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e}
+            "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e,
+            "mixed": mixed}
     return line, w
 
 

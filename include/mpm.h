@@ -124,7 +124,12 @@ typedef struct {
   double beta, gamma;         /* Newmark parameters (Sec. 3.2: 0.3025, 0.6) */
   int32_t stabilize;          /* PPP on (1) / off (0), Eq. stab-term-ppp */
   double tau_scale;           /* tau = tau_scale / (2 G), Eq. tau-white */
-  int32_t precision;          /* MPM_FP64 (MPM_MIXED reserved) */
+  int32_t precision;          /* MPM_FP64, or MPM_MIXED: Jacobian values, scaling,
+                                 preconditioner and Krylov vectors in FP32 inside the
+                                 FP64 Newton loop (residual, kinematics, det F,
+                                 ln J and point updates stay FP64); the Krylov
+                                 solve then stops at max(krylov_rtol, 1e-6) or its
+                                 cap, as an inexact Newton step */
   double newton_rtol;         /* ||R^k|| / ||R^0|| test of Eq. newton-tolerance */
   int32_t newton_max;         /* Newton iteration cap */
   double newton_stag;         /* > 0: accept the round-off floor once

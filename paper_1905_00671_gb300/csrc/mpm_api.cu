@@ -232,6 +232,8 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   if (rc) return rc;
   run_p2g(c);
   rc = run_pattern(c);
+  if (!rc) rc = linsys_reserve<double>(c, c.L64);
+  if (!rc && c.have32) rc = linsys_reserve<float>(c, c.L32);
   if (rc) return rc;
   run_initial_guess(c);
   run_renorm(c);
@@ -254,6 +256,37 @@ int eval_residual(Ctx &c, double *rnorm) {
   return MPM_OK;
 }
 
+// One Newton correction: assemble J (precision T), build the preconditioner
+// on the unscaled blocks, scale, FGMRES, X += D x.  In the mixed mode a Krylov
+// solve that stops at its iteration cap is an inexact Newton step: the FP64
+// residual test of the Newton loop decides convergence.
+template <typename T>
+int newton_correction(Ctx &c, LinSys<T> &S, int *its) {
+  run_jacobian<T>(c, S.val, 1);
+  int rc;
+  if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
+    rc = schur_setup<T>(c, S);  // on the unscaled blocks
+    if (rc) return rc;
+    run_scale_system<T>(c, S, c.R);
+  } else {
+    run_scale_system<T>(c, S, c.R);
+    run_block_jacobi<T>(c, S);
+  }
+  rc = read_dev_err(c);
+  if (rc) return rc;
+  const bool inexact = sizeof(T) < sizeof(double);
+  const double rtol = inexact ? fmax(c.opt.krylov_rtol, 1e-6) : c.opt.krylov_rtol;
+  rc = run_fgmres<T>(c, S, rtol, c.opt.krylov_max, its);
+  if (rc == MPM_ERR_KRYLOV_STAGNATED && inexact) rc = MPM_OK;
+  if (rc) {
+    if (rc == MPM_ERR_KRYLOV_STAGNATED) c.last_error = "FGMRES hit its iteration cap";
+    else if (rc == MPM_ERR_NONFINITE) c.last_error = "non-finite value in FGMRES";
+    return rc;
+  }
+  run_unscale_add<T>(c, S, c.X);
+  return MPM_OK;
+}
+
 int newton(Ctx &c) {
   mpm_stats &st = c.stats;
   st.newton_iters = 0;
@@ -272,27 +305,11 @@ int newton(Ctx &c) {
       c.last_error = "Newton did not reach the residual tolerance";
       return MPM_ERR_NEWTON_DIVERGED;
     }
-    run_jacobian(c, 1);
-    if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
-      rc = schur_setup(c);  // on the unscaled blocks
-      if (rc) return rc;
-      run_scale_system(c, c.rhs, c.R);
-    } else {
-      run_scale_system(c, c.rhs, c.R);
-      run_block_jacobi(c);
-    }
-    rc = read_dev_err(c);
-    if (rc) return rc;
     int its = 0;
-    rc = run_fgmres(c, c.rhs, c.dX, c.opt.krylov_rtol, c.opt.krylov_max, &its);
+    rc = c.have32 ? newton_correction<float>(c, c.L32, &its) : newton_correction<double>(c, c.L64, &its);
     st.krylov_iters[k] = its;
     st.krylov_total += its;
-    if (rc) {
-      if (rc == MPM_ERR_KRYLOV_STAGNATED) c.last_error = "FGMRES hit its iteration cap";
-      else if (rc == MPM_ERR_NONFINITE) c.last_error = "non-finite value in FGMRES";
-      return rc;
-    }
-    run_unscale_add(c, c.X, c.dX);
+    if (rc) return rc;
     prev = rk;
     rc = eval_residual(c, &rk);
     if (rc) return rc;
@@ -331,14 +348,14 @@ int do_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
 void free_all(Ctx &c) {
   for (cudaEvent_t e : c.ev) cudaEventDestroy(e);
   c.ev.clear();
-  schur_free(c);
+  linsys_free<double>(c.L64);
+  linsys_free<float>(c.L32);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
                   c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS,
                   c.sh_S0, c.m, c.rec, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
-                  c.row_ptr, c.row_of, c.col, c.row_mask, c.val, c.dscale, c.dinv, c.X, c.R, c.dX,
-                  c.rhs, c.w, c.V, c.Z, c.H, c.gvec, c.cs, c.sn, c.yv, c.hcol, c.part, c.scal,
-                  c.scan_tmp};
+                  c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
+                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.h_err) cudaFreeHost(c.h_err);
@@ -392,6 +409,7 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   if (opt->krylov_restart < 1 || opt->krylov_restart > 128) return MPM_ERR_BAD_ARG;
   if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
     return MPM_ERR_BAD_ARG;
+  if (opt->precision != MPM_FP64 && opt->precision != MPM_MIXED) return MPM_ERR_BAD_ARG;
   if (P->n_surf < 0 || (P->n_surf > 0 && (!P->surf_id || !P->surf_normal || !P->surf_area)))
     return MPM_ERR_BAD_ARG;
   if (!(mat->mu_f > 0.0)) return MPM_ERR_BAD_ARG;
@@ -488,15 +506,10 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   A(&c.row_nnz, nn + 1);
   A(&c.row_ptr, nn + 1);
   A(&c.row_mask, nn * 6);
-  A(&c.dscale, N);
-  A(&c.dinv, nn * nb * nb);
   A(&c.X, N);
   A(&c.R, N);
   A(&c.dX, N);
-  A(&c.rhs, N);
-  A(&c.w, std::max<int64_t>(N, 9 * n));
-  A(&c.V, (int64_t)(m + 1) * N);
-  A(&c.Z, (int64_t)m * N);
+  A(&c.stage, std::max<int64_t>(N, 9 * n));
   A(&c.H, (int64_t)(m + 1) * m);
   A(&c.gvec, m + 1);
   A(&c.cs, m);
@@ -507,7 +520,9 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   A(&c.scal, 8);
   c.scan_cap = 4096;
   A(&c.scan_tmp, c.scan_cap);
-  if (!rc && c.opt.precond == MPM_PRECOND_SCHUR_MG) rc = schur_alloc(c);
+  c.have32 = c.precision == MPM_MIXED;
+  if (!rc) rc = linsys_alloc<double>(c, c.L64, !c.have32);
+  if (!rc && c.have32) rc = linsys_alloc<float>(c, c.L32, true);
   if (!rc && cudaHostAlloc((void **)&c.h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess)
     rc = MPM_ERR_NO_MEMORY;
   if (!rc && cudaHostAlloc((void **)&c.h_scalar, 8 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
@@ -601,8 +616,8 @@ int mpm_read(const mpm_ctx *hc, mpm_particles_out *o) {
                {o->pd, PF_PD, 1}, {o->pdd, PF_PDD, 1}};
   for (const Item &it : items) {
     if (!it.dst) continue;
-    k_read_field<<<nblk(n), TPB, 0, c.st>>>(n, c.pf, it.f0, it.comps, c.pid, c.w);
-    cudaMemcpyAsync(it.dst, c.w, sizeof(double) * n * it.comps, cudaMemcpyDeviceToHost, c.st);
+    k_read_field<<<nblk(n), TPB, 0, c.st>>>(n, c.pf, it.f0, it.comps, c.pid, c.stage);
+    cudaMemcpyAsync(it.dst, c.stage, sizeof(double) * n * it.comps, cudaMemcpyDeviceToHost, c.st);
     cudaError_t e = cudaStreamSynchronize(c.st);
     if (e != cudaSuccess) return check_cuda(c, e, "read");
   }
@@ -632,7 +647,7 @@ int mpm_debug_bin(mpm_ctx *h, int32_t *cell, int64_t *order) {
   Ctx &c = h->c;
   int rc = run_binning(c);
   if (rc) return rc;
-  int32_t *tmp = reinterpret_cast<int32_t *>(c.w);
+  int32_t *tmp = reinterpret_cast<int32_t *>(c.stage);
   k_read_cells<<<nblk(c.n), TPB, 0, c.st>>>(c.n, c.cell, c.pid, tmp);
   cudaMemcpyAsync(cell, tmp, sizeof(int32_t) * c.n, cudaMemcpyDeviceToHost, c.st);
   cudaMemcpyAsync(order, c.pid, sizeof(int64_t) * c.n, cudaMemcpyDeviceToHost, c.st);
@@ -687,8 +702,8 @@ int mpm_debug_eval(mpm_ctx *h, const double *X, double *R, double *Jv, int32_t a
   run_residual(c, c.dX, c.R, apply_bc);
   cudaMemcpyAsync(R, c.R, sizeof(double) * N, cudaMemcpyDeviceToHost, c.st);
   if (Jv) {
-    run_jacobian(c, apply_bc);
-    cudaMemcpyAsync(Jv, c.val, sizeof(double) * c.nnzb * c.nb * c.nb, cudaMemcpyDeviceToHost, c.st);
+    run_jacobian<double>(c, c.L64.val, apply_bc);
+    cudaMemcpyAsync(Jv, c.L64.val, sizeof(double) * c.nnzb * c.nb * c.nb, cudaMemcpyDeviceToHost, c.st);
   }
   return check_cuda(c, cudaStreamSynchronize(c.st), "debug_eval");
 }
@@ -703,18 +718,19 @@ int mpm_debug_precond(mpm_ctx *h, const double *X, const double *v, double *z) {
   int rc = read_dev_err(c);
   if (rc) return rc;
   run_residual(c, c.X, c.R, 1);
-  run_jacobian(c, 1);
+  LinSys<double> &S = c.L64;
+  run_jacobian<double>(c, S.val, 1);
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
-    rc = schur_setup(c);
+    rc = schur_setup<double>(c, S);
     if (rc) return rc;
-    run_scale_system(c, c.rhs, c.R);
+    run_scale_system<double>(c, S, c.R);
   } else {
-    run_scale_system(c, c.rhs, c.R);
-    run_block_jacobi(c);
+    run_scale_system<double>(c, S, c.R);
+    run_block_jacobi<double>(c, S);
   }
-  cudaMemcpyAsync(c.w, v, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
-  run_precond(c, c.w, c.dX);
-  cudaMemcpyAsync(z, c.dX, sizeof(double) * N, cudaMemcpyDeviceToHost, c.st);
+  cudaMemcpyAsync(S.w, v, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
+  run_precond<double>(c, S, S.w, S.x);
+  cudaMemcpyAsync(z, S.x, sizeof(double) * N, cudaMemcpyDeviceToHost, c.st);
   return check_cuda(c, cudaStreamSynchronize(c.st), "debug_precond");
 }
 

@@ -387,9 +387,11 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
 }
 
 // ---------------------------------------------------------------- Jacobian
-template <int D, bool GIMP, bool DYN>
+// Block values are written in precision T (FP64, or FP32 for the mixed-
+// precision Krylov solve); the sums are formed in FP64 from the FP64 records.
+template <int D, bool GIMP, bool DYN, typename T>
 __global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restrict__ row_of,
-                           const int32_t *__restrict__ col, int64_t nnzb, double *__restrict__ val,
+                           const int32_t *__restrict__ col, int64_t nnzb, T *__restrict__ val,
                            int apply_bc) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nnzb) return;
@@ -471,8 +473,8 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restric
       }
     }
   }
-  double *out = val + e * (NB * NB);
-  for (int i = 0; i < NB * NB; ++i) out[i] = B[i];
+  T *out = val + e * (NB * NB);
+  for (int i = 0; i < NB * NB; ++i) out[i] = (T)B[i];
 }
 
 }  // namespace
@@ -496,12 +498,9 @@ int run_pattern(Ctx &c) {
     const int64_t cap = nnzb + nnzb / 4 + 1024;
     cudaFree(c.col);
     cudaFree(c.row_of);
-    cudaFree(c.val);
     c.col = c.row_of = nullptr;
-    c.val = nullptr;
     if (cudaMalloc(&c.col, sizeof(int32_t) * cap) != cudaSuccess ||
-        cudaMalloc(&c.row_of, sizeof(int32_t) * cap) != cudaSuccess ||
-        cudaMalloc(&c.val, sizeof(double) * cap * c.nb * c.nb) != cudaSuccess) {
+        cudaMalloc(&c.row_of, sizeof(int32_t) * cap) != cudaSuccess) {
       c.nnzb_cap = 0;
       c.last_error = "device allocation of the block-CSR matrix failed";
       return MPM_ERR_NO_MEMORY;
@@ -563,13 +562,14 @@ void run_residual(Ctx &c, const double *X, double *R, int apply_bc) {
   prof_end(c, MPM_PROF_RESIDUAL);
 }
 
-void run_jacobian(Ctx &c, int apply_bc) {
+template <typename T>
+void run_jacobian(Ctx &c, T *val, int apply_bc) {
   prof_begin(c, MPM_PROF_JACOBIAN);
   const DevView v = c.view();
   const int nbk = nblk(c.nnzb, 128);
   const bool gimp = c.shape == MPM_SHAPE_GIMP;
 #define JAC(D, G, Y) \
-  k_jacobian<D, G, Y><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, c.row_of, c.col, c.nnzb, c.val, apply_bc)
+  k_jacobian<D, G, Y, T><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, c.row_of, c.col, c.nnzb, val, apply_bc)
   if (c.d == 2) {
     if (gimp) { if (c.dyn) JAC(2, true, true); else JAC(2, true, false); }
     else { if (c.dyn) JAC(2, false, true); else JAC(2, false, false); }
@@ -581,5 +581,8 @@ void run_jacobian(Ctx &c, int apply_bc) {
   UPMPM_LAUNCH(c);
   prof_end(c, MPM_PROF_JACOBIAN);
 }
+
+template void run_jacobian<double>(Ctx &, double *, int);
+template void run_jacobian<float>(Ctx &, float *, int);
 
 }  // namespace upmpm

@@ -23,7 +23,25 @@
 
 namespace upmpm {
 
+template <typename T>
 struct MGHier;
+
+// The scaled Newton system D J D y = -D R and its solver workspace in the
+// precision T of the Krylov solve (FP64, or FP32 in the mixed mode).
+template <typename T>
+struct LinSys {
+  T *val = nullptr;            // nnzb_cap * nb * nb block values (scaled in place)
+  int64_t cap = 0;             // blocks val can hold
+  T *dscale = nullptr;         // nb * nnodes, D = |diag J|^{-1/2}
+  T *dinv = nullptr;           // nnodes * nb * nb block-Jacobi inverse
+  T *rhs = nullptr, *x = nullptr, *w = nullptr;  // N each
+  T *V = nullptr, *Z = nullptr;                  // (m + 1) * N and m * N
+  // Schur-complement multigrid preconditioner (mpm_mg.cu)
+  MGHier<T> *mgA = nullptr, *mgS = nullptr;
+  T *Aval = nullptr, *Sval = nullptr, *DAinv = nullptr;
+  T *vu = nullptr, *wu = nullptr, *zu = nullptr, *vp = nullptr, *zp = nullptr;
+  int64_t sub_cap = 0;
+};
 
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
 
@@ -161,24 +179,17 @@ struct Ctx {
   int32_t *row_nnz = nullptr, *row_ptr = nullptr, *row_of = nullptr, *col = nullptr;
   uint64_t *row_mask = nullptr;          // per node, 6 words (7^d offsets)
   int64_t nnzb = 0, nnzb_cap = 0;
-  double *val = nullptr;                 // nnzb_cap * nb * nb
-  double *dscale = nullptr;              // nb * nnodes diagonal scaling
-  double *dinv = nullptr;                // nnodes * nb * nb block-Jacobi inverse
 
-  // vectors (length nb * nnodes)
-  double *X = nullptr, *R = nullptr, *dX = nullptr, *rhs = nullptr, *w = nullptr;
-  // FGMRES workspace
+  // Newton vectors (FP64, length nb * nnodes) and read-back staging
+  double *X = nullptr, *R = nullptr, *dX = nullptr, *stage = nullptr;
+  // Krylov solve: FP64 system always (debug calls, FP64 mode), FP32 system in
+  // the mixed mode; Hessenberg / Givens / reduction scratch in FP64
   int m_restart = 30;
-  double *V = nullptr, *Z = nullptr;     // (m+1) and m vectors
+  LinSys<double> L64;
+  LinSys<float> L32;
+  bool have32 = false;
   double *H = nullptr, *gvec = nullptr, *cs = nullptr, *sn = nullptr, *yv = nullptr;
   double *hcol = nullptr, *part = nullptr, *scal = nullptr;
-  int nparts = 0;
-
-  // Schur-complement block preconditioner (mpm_mg.cu)
-  MGHier *mgA = nullptr, *mgS = nullptr;
-  double *Aval = nullptr, *Sval = nullptr, *DAinv = nullptr;
-  double *vu = nullptr, *wu = nullptr, *zu = nullptr, *vp = nullptr, *zp = nullptr;
-  int64_t sub_cap = 0;
 
   // scan scratch
   int32_t *scan_tmp = nullptr;
@@ -208,21 +219,36 @@ void run_initial_guess(Ctx &c);   // also sets the active flags
 void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
 void run_point_eval(Ctx &c, const double *X);
 void run_residual(Ctx &c, const double *X, double *R, int apply_bc);
-void run_jacobian(Ctx &c, int apply_bc);
+template <typename T>
+void run_jacobian(Ctx &c, T *val, int apply_bc);  // block values in precision T
 // linear algebra
-void run_scale_system(Ctx &c, double *rhs_out, const double *R);  // scales val, rhs = -D R
-void run_block_jacobi(Ctx &c);
-int run_fgmres(Ctx &c, const double *b, double *x, double rtol, int maxit, int *iters);
-void run_precond(Ctx &c, const double *v, double *z);  // z = M^{-1} v (scaled system)
+template <typename T>
+int linsys_alloc(Ctx &c, LinSys<T> &S, bool krylov);  // vectors; matrix on demand
+template <typename T>
+void linsys_free(LinSys<T> &S);
+template <typename T>
+int linsys_reserve(Ctx &c, LinSys<T> &S);           // val for nnzb_cap blocks
+template <typename T>
+void run_scale_system(Ctx &c, LinSys<T> &S, const double *R);  // scales val, rhs = -D R
+template <typename T>
+void run_block_jacobi(Ctx &c, LinSys<T> &S);
+template <typename T>
+int run_fgmres(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters);  // S.x from S.rhs
+template <typename T>
+void run_precond(Ctx &c, LinSys<T> &S, const T *v, T *z);  // z = M^{-1} v (scaled system)
+template <typename T>
+void run_unscale_add(Ctx &c, const LinSys<T> &S, double *X);  // X += D x
 double run_norm(Ctx &c, const double *x);          // synchronises
-void run_axpy(Ctx &c, double *y, double a, const double *x, int64_t n);
-void run_unscale_add(Ctx &c, double *X, const double *xhat);  // X += D xhat
 
 // Schur-complement multigrid preconditioner
-int schur_alloc(Ctx &c);
-void schur_free(Ctx &c);
-int schur_setup(Ctx &c);                               // after run_scale_system
-void schur_apply(Ctx &c, const double *v, double *z);  // z = M^{-1} v
+template <typename T>
+int schur_alloc(Ctx &c, LinSys<T> &S);
+template <typename T>
+void schur_free(LinSys<T> &S);
+template <typename T>
+int schur_setup(Ctx &c, LinSys<T> &S);                 // before run_scale_system (unscaled val)
+template <typename T>
+void schur_apply(Ctx &c, LinSys<T> &S, const T *v, T *z);  // z = M^{-1} v
 
 // scan: out[i] = sum_{j<i} in[j]; returns the total (synchronises)
 int64_t scan_exclusive(Ctx &c, const int32_t *in, int32_t *out, int64_t n);

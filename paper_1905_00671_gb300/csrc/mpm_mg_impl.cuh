@@ -1,0 +1,794 @@
+// mpm_mg_impl.cuh -- precision-generic body of mpm_mg.cu (included twice, with
+// MG_REAL = double / float and MG_NS naming the namespace of that precision).
+
+namespace MG_NS {
+using real = MG_REAL;
+
+
+constexpr int TPB = 256;
+inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
+
+template <int D>
+struct NS_ {
+  static constexpr int v = D == 2 ? 25 : 125;
+};
+
+__host__ __device__ inline int slot_of(int o0, int o1, int o2) {
+  return (o0 + 2) + 5 * (o1 + 2) + 25 * (o2 + 2);
+}
+
+// Small dense inverse with partial pivoting (B <= 4); identity on failure.
+template <int B>
+__device__ inline bool invert_small(real A[B][B], real Inv[B][B]) {
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) Inv[i][j] = i == j ? 1.0 : 0.0;
+  for (int k = 0; k < B; ++k) {
+    int piv = k;
+    real best = fabs(A[k][k]);
+    for (int i = k + 1; i < B; ++i)
+      if (fabs(A[i][k]) > best) { best = fabs(A[i][k]); piv = i; }
+    if (!(best > 1e-300)) {
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) Inv[i][j] = i == j ? 1.0 : 0.0;
+      return false;
+    }
+    if (piv != k)
+      for (int j = 0; j < B; ++j) {
+        real t = A[k][j]; A[k][j] = A[piv][j]; A[piv][j] = t;
+        t = Inv[k][j]; Inv[k][j] = Inv[piv][j]; Inv[piv][j] = t;
+      }
+    const real inv = 1.0 / A[k][k];
+    for (int j = 0; j < B; ++j) { A[k][j] *= inv; Inv[k][j] *= inv; }
+    for (int i = 0; i < B; ++i) {
+      if (i == k) continue;
+      const real f = A[i][k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < B; ++j) { A[i][j] -= f * A[k][j]; Inv[i][j] -= f * Inv[k][j]; }
+    }
+  }
+  return true;
+}
+
+__device__ inline int find_col(const int32_t *__restrict__ col, int lo, int hi, int key) {
+  hi -= 1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const int c = col[mid];
+    if (c == key) return mid;
+    if (c < key) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------ block split
+template <int D>
+__global__ void k_extract_A(int64_t nnzb, const real *__restrict__ J, real *__restrict__ A) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  constexpr int NB = D + 1;
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) A[e * D * D + i * D + k] = J[e * NB * NB + i * NB + k];
+}
+
+template <int D>
+__global__ void k_diag_inv_A(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const real *__restrict__ A,
+                             real *__restrict__ DAinv) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nnodes) return;
+  const int e = find_col(col, row_ptr[a], row_ptr[a + 1], (int)a);
+  real M[D][D], Inv[D][D];
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) M[i][k] = e >= 0 ? A[(int64_t)e * D * D + i * D + k] : (i == k);
+  invert_small<D>(M, Inv);
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) DAinv[a * D * D + i * D + k] = Inv[i][k];
+}
+
+// S row a on J's sparsity: S_ab = C_ab - sum_c B2_ac DAinv_c B1_cb; the part of
+// the product falling outside the sparsity is added to S_aa.  LN lanes per row.
+template <int D>
+__global__ void k_schur_rows(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const real *__restrict__ J,
+                             const real *__restrict__ DAinv, real *__restrict__ S) {
+  constexpr int NB = D + 1, LN = D == 2 ? 8 : 16;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < nnodes;
+  real total = 0.0, kept = 0.0;
+  int mydiag = -1;
+  if (valid) {
+    const int r0 = row_ptr[a], r1 = row_ptr[a + 1];
+    // full product row sum: sum_c (B2_ac DAinv_c) . (sum_b B1_cb)
+    for (int ec = r0 + lane; ec < r1; ec += LN) {
+      const int c = col[ec];
+      real rs[D];
+      for (int k = 0; k < D; ++k) rs[k] = 0.0;
+      for (int eb = row_ptr[c]; eb < row_ptr[c + 1]; ++eb)
+        for (int k = 0; k < D; ++k) rs[k] += J[(int64_t)eb * NB * NB + k * NB + D];
+      for (int k = 0; k < D; ++k) {
+        real w = 0.0;
+        for (int i = 0; i < D; ++i) w += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
+        total += w * rs[k];
+      }
+    }
+    for (int eb = r0 + lane; eb < r1; eb += LN) {
+      const int b = col[eb];
+      if (b == a) mydiag = eb;
+      real prod = 0.0;
+      for (int ec = r0; ec < r1; ++ec) {
+        const int c = col[ec];
+        const int e_cb = find_col(col, row_ptr[c], row_ptr[c + 1], b);
+        if (e_cb < 0) continue;
+        for (int k = 0; k < D; ++k) {
+          real w = 0.0;
+          for (int i = 0; i < D; ++i) w += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
+          prod += w * J[(int64_t)e_cb * NB * NB + k * NB + D];
+        }
+      }
+      kept += prod;
+      S[eb] = J[(int64_t)eb * NB * NB + D * NB + D] - prod;
+    }
+  }
+  for (int o = LN / 2; o > 0; o >>= 1) {
+    total += __shfl_xor_sync(0xffffffffu, total, o);
+    kept += __shfl_xor_sync(0xffffffffu, kept, o);
+  }
+  if (mydiag >= 0) S[mydiag] -= (total - kept);
+}
+
+// ------------------------------------------------------------ Schur apply
+// The Krylov solver works on D J D (D = dsc); the blocks below are the
+// unscaled physical ones, so the preconditioner of D J D is D^-1 M^-1 D^-1.
+template <int D>
+__global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsc,
+                        real *__restrict__ vu, real *__restrict__ vp) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nnodes) return;
+  for (int k = 0; k < D; ++k) vu[a * D + k] = v[a * (D + 1) + k] / dsc[a * (D + 1) + k];
+  vp[a] = v[a * (D + 1) + D] / dsc[a * (D + 1) + D];
+}
+
+// w_u = v_u - B1 z_p with the unscaled B1 (column D of the u rows of the
+// scaled J divided by the two scale factors)
+template <int D>
+__global__ void k_b1_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                            const int32_t *__restrict__ col, const real *__restrict__ Js,
+                            const real *__restrict__ dsc, const real *__restrict__ zp,
+                            const real *__restrict__ vu, real *__restrict__ wu) {
+  constexpr int NB = D + 1, LN = D == 2 ? 8 : 16;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < nnodes;
+  real acc[D];
+  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  if (valid) {
+    const int e1 = row_ptr[a + 1];
+    for (int e = row_ptr[a] + lane; e < e1; e += LN) {
+      const int64_t b = col[e];
+      const real z = zp[b] / dsc[b * NB + D];
+      for (int k = 0; k < D; ++k) acc[k] = fma(Js[(int64_t)e * NB * NB + k * NB + D], z, acc[k]);
+    }
+  }
+  for (int o = LN / 2; o > 0; o >>= 1)
+    for (int k = 0; k < D; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if (!valid || lane != 0) return;
+  for (int k = 0; k < D; ++k) wu[a * D + k] = vu[a * D + k] - acc[k] / dsc[a * NB + k];
+}
+
+template <int D>
+__global__ void k_merge(int64_t nnodes, const real *__restrict__ zu, const real *__restrict__ zp,
+                        const real *__restrict__ dsc, real *__restrict__ z) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nnodes) return;
+  for (int k = 0; k < D; ++k) z[a * (D + 1) + k] = zu[a * D + k] / dsc[a * (D + 1) + k];
+  z[a * (D + 1) + D] = zp[a] / dsc[a * (D + 1) + D];
+}
+
+// ------------------------------------------------------------ multigrid
+struct LevelDev {
+  int nn[3];
+  int64_t nnodes;
+  const int32_t *row_ptr, *col;  // level 0 only
+  const real *val;              // level 0: block-CSR values
+  real *sval;                   // coarse levels: dense 5^d stencil values
+  real *dinv;
+  // level 0 only: Dirichlet / inactive DOFs are left out of the transfers
+  const uint8_t *fixed;           // fixed[a * mstride + moff + i] != 0: DOF fixed
+  int mstride, moff;
+};
+
+__device__ inline real free_w(const LevelDev &L, int64_t a, int i) {
+  return (L.fixed && L.fixed[a * L.mstride + L.moff + i]) ? 0.0 : 1.0;
+}
+
+// Lanes per row of the row kernels (a row is one node: up to 49 blocks of the
+// fine block-CSR in 2D, 5^d slots of a coarse stencil).
+template <int D>
+struct LN_ {
+  static constexpr int v = D == 2 ? 8 : 16;
+};
+
+// Partial sum over the blocks of row a handled by `lane` (of LN lanes):
+// acc += A_ab x_b, one FMA per matrix value.
+template <int B, int D, bool ST, int LN>
+__device__ inline void row_partial(const LevelDev &L, int64_t a, int lane, const real *__restrict__ x,
+                                   real acc[B]) {
+  if (!ST) {
+    const int e1 = L.row_ptr[a + 1];
+    for (int e = L.row_ptr[a] + lane; e < e1; e += LN) {
+      const int64_t b = L.col[e];
+      const real *blk = L.val + (int64_t)e * B * B;
+      real xb[B];
+      for (int j = 0; j < B; ++j) xb[j] = x[b * B + j];
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) acc[i] = fma(blk[i * B + j], xb[j], acc[i]);
+    }
+  } else {
+    int ac[3];
+    ac[0] = (int)(a % L.nn[0]);
+    ac[1] = (int)((a / L.nn[0]) % L.nn[1]);
+    ac[2] = (int)(a / ((int64_t)L.nn[0] * L.nn[1]));
+    constexpr int NS = NS_<D>::v;
+    const real *base = L.sval + a * NS * B * B;
+    for (int s = lane; s < NS; s += LN) {
+      const int o0 = s % 5 - 2, o1 = (s / 5) % 5 - 2, o2 = D == 3 ? s / 25 - 2 : 0;
+      const int b0 = ac[0] + o0, b1 = ac[1] + o1, b2 = ac[2] + o2;
+      if (b0 < 0 || b0 >= L.nn[0] || b1 < 0 || b1 >= L.nn[1] || b2 < 0 || b2 >= L.nn[2]) continue;
+      const int64_t b = b0 + (int64_t)L.nn[0] * (b1 + (int64_t)L.nn[1] * b2);
+      const real *blk = base + s * B * B;
+      real xb[B];
+      for (int j = 0; j < B; ++j) xb[j] = x[b * B + j];
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) acc[i] = fma(blk[i * B + j], xb[j], acc[i]);
+    }
+  }
+}
+
+template <int B, int LN>
+__device__ inline void lane_reduce(real acc[B]) {
+  for (int o = LN / 2; o > 0; o >>= 1)
+    for (int i = 0; i < B; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+}
+
+template <int B, int D, bool ST>
+__global__ void k_mg_dinv(LevelDev L, int *err) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= L.nnodes) return;
+  real M[B][B], Inv[B][B];
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) M[i][j] = (i == j) ? 1.0 : 0.0;
+  if (!ST) {
+    const int e = find_col(L.col, L.row_ptr[a], L.row_ptr[a + 1], (int)a);
+    if (e >= 0)
+      for (int i = 0; i < B; ++i)
+        for (int j = 0; j < B; ++j) M[i][j] = L.val[(int64_t)e * B * B + i * B + j];
+  } else {
+    constexpr int NS = NS_<D>::v;
+    const int s = D == 2 ? 12 : 62;  // centre slot of the 5^d stencil
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) M[i][j] = L.sval[(a * NS + s) * B * B + i * B + j];
+  }
+  if (!invert_small<B>(M, Inv)) {
+    // an all-zero diagonal block (e.g. a node without coupling) acts as identity
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < B; ++j) Inv[i][j] = i == j ? 1.0 : 0.0;
+  }
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) L.dinv[a * B * B + i * B + j] = Inv[i][j];
+}
+
+// One damped block-Jacobi sweep: xo = xi + w Dinv (b - A xi); zero_init: xi = 0.
+// LN lanes per row.
+template <int B, int D, bool ST>
+__global__ void k_mg_smooth(LevelDev L, const real *__restrict__ xi, real *__restrict__ xo,
+                            const real *__restrict__ b, real omega, int zero_init) {
+  constexpr int LN = LN_<D>::v;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < L.nnodes;
+  real ax[B];
+  for (int i = 0; i < B; ++i) ax[i] = 0.0;
+  if (valid && !zero_init) row_partial<B, D, ST, LN>(L, a, lane, xi, ax);
+  lane_reduce<B, LN>(ax);
+  if (!valid || lane != 0) return;
+  real r[B];
+  for (int i = 0; i < B; ++i) r[i] = b[a * B + i] - ax[i];
+  for (int i = 0; i < B; ++i) {
+    real s = 0.0;
+    for (int j = 0; j < B; ++j) s = fma(L.dinv[a * B * B + i * B + j], r[j], s);
+    xo[a * B + i] = (zero_init ? 0.0 : xi[a * B + i]) + omega * s;
+  }
+}
+
+template <int B, int D, bool ST>
+__global__ void k_mg_resid(LevelDev L, const real *__restrict__ x, const real *__restrict__ b,
+                           real *__restrict__ r) {
+  constexpr int LN = LN_<D>::v;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < L.nnodes;
+  real ax[B];
+  for (int i = 0; i < B; ++i) ax[i] = 0.0;
+  if (valid) row_partial<B, D, ST, LN>(L, a, lane, x, ax);
+  lane_reduce<B, LN>(ax);
+  if (!valid || lane != 0) return;
+  for (int i = 0; i < B; ++i) r[a * B + i] = b[a * B + i] - ax[i];
+}
+
+// ---- coarsest level: exact solve with a dense inverse built at set-up
+// Dense copy of the coarsest operator (n = nnodes * B unknowns).
+template <int B, int D, bool ST>
+__global__ void k_dense_fill(LevelDev L, real *__restrict__ Ad) {
+  const int64_t n = L.nnodes * B;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int64_t ri = t / n, ci = t % n;
+  const int64_t a = ri / B, b = ci / B;
+  const int i = (int)(ri % B), j = (int)(ci % B);
+  real v = 0.0;
+  if (!ST) {
+    const int e = find_col(L.col, L.row_ptr[a], L.row_ptr[a + 1], (int)b);
+    if (e >= 0) v = L.val[(int64_t)e * B * B + i * B + j];
+  } else {
+    int ac[3], bc[3];
+    ac[0] = (int)(a % L.nn[0]); ac[1] = (int)((a / L.nn[0]) % L.nn[1]); ac[2] = (int)(a / ((int64_t)L.nn[0] * L.nn[1]));
+    bc[0] = (int)(b % L.nn[0]); bc[1] = (int)((b / L.nn[0]) % L.nn[1]); bc[2] = (int)(b / ((int64_t)L.nn[0] * L.nn[1]));
+    const int o0 = bc[0] - ac[0], o1 = bc[1] - ac[1], o2 = bc[2] - ac[2];
+    if (o0 >= -2 && o0 <= 2 && o1 >= -2 && o1 <= 2 && o2 >= -2 && o2 <= 2) {
+      constexpr int NS = NS_<D>::v;
+      const int sl = (o0 + 2) + 5 * (o1 + 2) + (D == 3 ? 25 * (o2 + 2) : 0);
+      v = L.sval[(a * NS + sl) * B * B + i * B + j];
+    }
+  }
+  Ad[t] = v;
+}
+
+// In-place Gauss-Jordan inverse of the dense n x n matrix Ad into Ai (one
+// block).  Rows with no usable pivot (singular directions) get a zero row in
+// the inverse, so the coarse correction leaves them alone.
+__global__ void k_dense_invert(int n, real *__restrict__ Ad, real *__restrict__ Ai) {
+  __shared__ int piv;
+  __shared__ real pval;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ai[t] = (t / n == t % n) ? 1.0 : 0.0;
+  real amax = 0.0;
+  for (int t = 0; t < n * n; ++t) amax = fmax(amax, fabs(Ad[t]));
+  for (int k = 0; k < n; ++k) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int p = k;
+      real best = fabs(Ad[k * n + k]);
+      for (int i = k + 1; i < n; ++i)
+        if (fabs(Ad[i * n + k]) > best) { best = fabs(Ad[i * n + k]); p = i; }
+      piv = best > 1e-14 * amax ? p : -1;
+      pval = piv >= 0 ? Ad[p * n + k] : 0.0;
+    }
+    __syncthreads();
+    if (piv < 0) {
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        Ad[k * n + j] = 0.0;
+        Ai[k * n + j] = 0.0;
+      }
+      continue;
+    }
+    if (piv != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        real t1 = Ad[k * n + j]; Ad[k * n + j] = Ad[piv * n + j]; Ad[piv * n + j] = t1;
+        t1 = Ai[k * n + j]; Ai[k * n + j] = Ai[piv * n + j]; Ai[piv * n + j] = t1;
+      }
+    __syncthreads();
+    const real inv = 1.0 / pval;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      Ad[k * n + j] *= inv;
+      Ai[k * n + j] *= inv;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = t / n, j = t % n;
+      if (i == k) continue;
+      const real f = Ad[i * n + k];
+      if (f == 0.0) continue;
+      if (j != k) Ad[i * n + j] -= f * Ad[k * n + j];
+      Ai[i * n + j] -= f * Ai[k * n + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) Ad[i * n + k] = 0.0;
+  }
+}
+
+// x = Ai b
+__global__ void k_dense_apply(int n, const real *__restrict__ Ai, const real *__restrict__ b,
+                              real *__restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  real s = 0.0;
+  for (int j = 0; j < n; ++j) s = fma(Ai[(int64_t)i * n + j], b[j], s);
+  x[i] = s;
+}
+
+// weight of coarse node I for fine node a along one axis
+__device__ inline real pw(int a, int I) {
+  const int dlt = a - 2 * I;
+  return dlt == 0 ? 1.0 : ((dlt == 1 || dlt == -1) ? 0.5 : 0.0);
+}
+
+// b_c(I) = sum_a P_aI r_a over the fine nodes within one fine cell of 2I
+template <int B, int D>
+__global__ void k_mg_restrict(LevelDev F, LevelDev Cl, const real *__restrict__ rf,
+                              real *__restrict__ bc) {
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= Cl.nnodes) return;
+  int Ic[3];
+  Ic[0] = (int)(I % Cl.nn[0]);
+  Ic[1] = (int)((I / Cl.nn[0]) % Cl.nn[1]);
+  Ic[2] = (int)(I / ((int64_t)Cl.nn[0] * Cl.nn[1]));
+  real acc[B];
+  for (int i = 0; i < B; ++i) acc[i] = 0.0;
+  const int lo2 = D == 3 ? -1 : 0, hi2 = D == 3 ? 1 : 0;
+  for (int d2 = lo2; d2 <= hi2; ++d2)
+    for (int d1 = -1; d1 <= 1; ++d1)
+      for (int d0 = -1; d0 <= 1; ++d0) {
+        const int a0 = 2 * Ic[0] + d0, a1 = 2 * Ic[1] + d1, a2 = D == 3 ? 2 * Ic[2] + d2 : 0;
+        if (a0 < 0 || a0 >= F.nn[0] || a1 < 0 || a1 >= F.nn[1] || a2 < 0 || a2 >= F.nn[2]) continue;
+        const real wgt = pw(a0, Ic[0]) * pw(a1, Ic[1]) * (D == 3 ? pw(a2, Ic[2]) : 1.0);
+        const int64_t a = a0 + (int64_t)F.nn[0] * (a1 + (int64_t)F.nn[1] * a2);
+        for (int i = 0; i < B; ++i) acc[i] += wgt * free_w(F, a, i) * rf[a * B + i];
+      }
+  for (int i = 0; i < B; ++i) bc[I * B + i] = acc[i];
+}
+
+// x_f(a) += sum_I P_aI x_c(I)
+template <int B, int D>
+__global__ void k_mg_prolong(LevelDev F, LevelDev Cl, real *__restrict__ xf,
+                             const real *__restrict__ xc) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= F.nnodes) return;
+  int ac[3];
+  ac[0] = (int)(a % F.nn[0]);
+  ac[1] = (int)((a / F.nn[0]) % F.nn[1]);
+  ac[2] = (int)(a / ((int64_t)F.nn[0] * F.nn[1]));
+  real acc[B];
+  for (int i = 0; i < B; ++i) acc[i] = 0.0;
+  int lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = ac[k] / 2;
+    hi[k] = (ac[k] + 1) / 2;
+    if (hi[k] >= Cl.nn[k]) hi[k] = Cl.nn[k] - 1;
+  }
+  for (int I2 = lo[2]; I2 <= hi[2]; ++I2)
+    for (int I1 = lo[1]; I1 <= hi[1]; ++I1)
+      for (int I0 = lo[0]; I0 <= hi[0]; ++I0) {
+        const real wgt = pw(ac[0], I0) * pw(ac[1], I1) * (D == 3 ? pw(ac[2], I2) : 1.0);
+        if (wgt == 0.0) continue;
+        const int64_t I = I0 + (int64_t)Cl.nn[0] * (I1 + (int64_t)Cl.nn[1] * I2);
+        for (int i = 0; i < B; ++i) acc[i] += wgt * xc[I * B + i];
+      }
+  for (int i = 0; i < B; ++i) xf[a * B + i] += free_w(F, a, i) * acc[i];
+}
+
+// Galerkin coarse operator: one thread per (coarse node I, stencil slot).
+template <int B, int D, bool FST>
+__global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
+  constexpr int NS = NS_<D>::v;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= Cl.nnodes * NS) return;
+  const int64_t I = t / NS;
+  const int s = (int)(t % NS);
+  const int o0 = s % 5 - 2, o1 = (s / 5) % 5 - 2, o2 = D == 3 ? s / 25 - 2 : 0;
+  int Ic[3], Jc[3];
+  Ic[0] = (int)(I % Cl.nn[0]);
+  Ic[1] = (int)((I / Cl.nn[0]) % Cl.nn[1]);
+  Ic[2] = (int)(I / ((int64_t)Cl.nn[0] * Cl.nn[1]));
+  Jc[0] = Ic[0] + o0;
+  Jc[1] = Ic[1] + o1;
+  Jc[2] = Ic[2] + o2;
+  real acc[B * B];
+  for (int i = 0; i < B * B; ++i) acc[i] = 0.0;
+  const bool Jin = Jc[0] >= 0 && Jc[0] < Cl.nn[0] && Jc[1] >= 0 && Jc[1] < Cl.nn[1] && Jc[2] >= 0 &&
+                   Jc[2] < Cl.nn[2];
+  if (Jin) {
+    const int lo2 = D == 3 ? -1 : 0, hi2 = D == 3 ? 1 : 0;
+    for (int a2 = lo2; a2 <= hi2; ++a2)
+      for (int a1 = -1; a1 <= 1; ++a1)
+        for (int a0 = -1; a0 <= 1; ++a0) {
+          const int fa[3] = {2 * Ic[0] + a0, 2 * Ic[1] + a1, D == 3 ? 2 * Ic[2] + a2 : 0};
+          if (fa[0] < 0 || fa[0] >= F.nn[0] || fa[1] < 0 || fa[1] >= F.nn[1] || fa[2] < 0 || fa[2] >= F.nn[2])
+            continue;
+          const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
+          const int64_t a = fa[0] + (int64_t)F.nn[0] * (fa[1] + (int64_t)F.nn[1] * fa[2]);
+          for (int b2 = lo2; b2 <= hi2; ++b2)
+            for (int b1 = -1; b1 <= 1; ++b1)
+              for (int b0 = -1; b0 <= 1; ++b0) {
+                const int fb[3] = {2 * Jc[0] + b0, 2 * Jc[1] + b1, D == 3 ? 2 * Jc[2] + b2 : 0};
+                if (fb[0] < 0 || fb[0] >= F.nn[0] || fb[1] < 0 || fb[1] >= F.nn[1] || fb[2] < 0 ||
+                    fb[2] >= F.nn[2])
+                  continue;
+                const real wb = pw(fb[0], Jc[0]) * pw(fb[1], Jc[1]) * (D == 3 ? pw(fb[2], Jc[2]) : 1.0);
+                const real *blk = nullptr;
+                if (!FST) {
+                  const int64_t b = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
+                  const int e = find_col(F.col, F.row_ptr[a], F.row_ptr[a + 1], (int)b);
+                  if (e < 0) continue;
+                  blk = F.val + (int64_t)e * B * B;
+                } else {
+                  const int d0 = fb[0] - fa[0], d1 = fb[1] - fa[1], d2 = fb[2] - fa[2];
+                  if (d0 < -2 || d0 > 2 || d1 < -2 || d1 > 2 || d2 < -2 || d2 > 2) continue;
+                  const int sl = (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0);
+                  blk = F.sval + (a * NS + sl) * B * B;
+                }
+                const real w = wa * wb;
+                if (!FST) {
+                  const int64_t b = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
+                  for (int i = 0; i < B; ++i)
+                    for (int j = 0; j < B; ++j)
+                      acc[i * B + j] += w * free_w(F, a, i) * free_w(F, b, j) * blk[i * B + j];
+                } else {
+                  for (int i = 0; i < B * B; ++i) acc[i] += w * blk[i];
+                }
+              }
+        }
+  }
+  for (int i = 0; i < B * B; ++i) Cl.sval[t * B * B + i] = acc[i];
+}
+
+}  // namespace MG_NS
+
+// ============================================================== hierarchy
+template <>
+struct MGHier<MG_REAL> {
+  int B = 1, nlev = 0;
+  MG_NS::LevelDev L[16];
+  MG_REAL *x[16], *x2[16], *b[16], *r[16];
+  MG_REAL *Ad = nullptr, *Ai = nullptr;  // dense coarsest operator and its inverse
+  int ncoarse = 0;                       // unknowns of the coarsest level
+};
+
+namespace MG_NS {
+
+template <int B, int D>
+void mg_setup_t(Ctx &c, MGHier<real> &H) {
+  for (int l = 0; l < H.nlev; ++l) {
+    LevelDev &L = H.L[l];
+    const int nbk = nblk(L.nnodes);
+    if (l > 0) {
+      constexpr int NS = NS_<D>::v;
+      const int g2 = nblk(L.nnodes * NS);
+      if (l == 1) k_mg_rap<B, D, false><<<g2, TPB, 0, c.st>>>(H.L[0], L);
+      else k_mg_rap<B, D, true><<<g2, TPB, 0, c.st>>>(H.L[l - 1], L);
+      UPMPM_LAUNCH(c);
+      k_mg_dinv<B, D, true><<<nbk, TPB, 0, c.st>>>(L, c.err);
+    } else {
+      k_mg_dinv<B, D, false><<<nbk, TPB, 0, c.st>>>(L, c.err);
+    }
+    UPMPM_LAUNCH(c);
+  }
+  // coarsest level: dense inverse
+  LevelDev &Lc = H.L[H.nlev - 1];
+  const int64_t n = H.ncoarse;
+  if (H.nlev == 1) k_dense_fill<B, D, false><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
+  else k_dense_fill<B, D, true><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
+  k_dense_invert<<<1, 256, 0, c.st>>>((int)n, H.Ad, H.Ai);
+  c.launches += 2;
+}
+
+template <int B, int D>
+void smooth(Ctx &c, MGHier<real> &H, int l, int sweeps, real omega, bool zero_first) {
+  LevelDev &L = H.L[l];
+  const int nbk = nblk(L.nnodes * LN_<D>::v);
+  for (int s = 0; s < sweeps; ++s) {
+    const bool z = zero_first && s == 0;
+    if (l == 0) k_mg_smooth<B, D, false><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], omega, z);
+    else k_mg_smooth<B, D, true><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], omega, z);
+    UPMPM_LAUNCH(c);
+    std::swap(H.x[l], H.x2[l]);
+  }
+}
+
+template <int B, int D>
+void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
+  const real omega = 0.6;
+  const int pre = 2, post = 2;
+  if (l == H.nlev - 1) {  // exact solve on the coarsest grid
+    k_dense_apply<<<nblk(H.ncoarse, 64), 64, 0, c.st>>>(H.ncoarse, H.Ai, H.b[l], H.x[l]);
+    UPMPM_LAUNCH(c);
+    return;
+  }
+  smooth<B, D>(c, H, l, pre, omega, true);
+  LevelDev &L = H.L[l];
+  const int nbk = nblk(L.nnodes);
+  const int nbr = nblk(L.nnodes * LN_<D>::v);
+  if (l == 0) k_mg_resid<B, D, false><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  else k_mg_resid<B, D, true><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  k_mg_restrict<B, D><<<nblk(H.L[l + 1].nnodes), TPB, 0, c.st>>>(L, H.L[l + 1], H.r[l], H.b[l + 1]);
+  c.launches += 2;
+  vcycle_t<B, D>(c, H, l + 1);
+  k_mg_prolong<B, D><<<nbk, TPB, 0, c.st>>>(L, H.L[l + 1], H.x[l], H.x[l + 1]);
+  UPMPM_LAUNCH(c);
+  smooth<B, D>(c, H, l, post, omega, false);
+}
+
+
+// Allocate a hierarchy for block size B over the grid's node lattice; level 0
+// refers to a block-CSR operator given at setup.
+int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
+  H.B = B;
+  const int D = c.d;
+  const int NS = D == 2 ? 25 : 125;
+  int nn[3] = {c.g.nn[0], c.g.nn[1], c.g.nn[2]};
+  int l = 0;
+  while (true) {
+    LevelDev &L = H.L[l];
+    for (int k = 0; k < 3; ++k) L.nn[k] = nn[k];
+    L.nnodes = (int64_t)nn[0] * nn[1] * nn[2];
+    L.row_ptr = nullptr;
+    L.col = nullptr;
+    L.val = nullptr;
+    L.sval = nullptr;
+    L.fixed = nullptr;
+    L.mstride = 1;
+    L.moff = 0;
+    const int64_t vb = L.nnodes * B;
+    if (cudaMalloc(&L.dinv, sizeof(real) * L.nnodes * B * B) ||
+        cudaMalloc(&H.x[l], sizeof(real) * vb) || cudaMalloc(&H.x2[l], sizeof(real) * vb) ||
+        cudaMalloc(&H.b[l], sizeof(real) * vb) || cudaMalloc(&H.r[l], sizeof(real) * vb))
+      return MPM_ERR_NO_MEMORY;
+    if (l > 0 && cudaMalloc(&L.sval, sizeof(real) * L.nnodes * NS * B * B)) return MPM_ERR_NO_MEMORY;
+    ++l;
+    int mn = 1 << 30;
+    for (int k = 0; k < D; ++k) mn = nn[k] < mn ? nn[k] : mn;
+    // the coarsest level is solved exactly: stop at <= 64 nodes or a 2-node axis
+    if (mn <= 2 || L.nnodes <= 64 || l >= 15) break;
+    for (int k = 0; k < D; ++k) nn[k] = (nn[k] + 1) / 2;
+  }
+  H.nlev = l;
+  H.ncoarse = (int)(H.L[l - 1].nnodes * B);
+  if (H.ncoarse > 1024) return MPM_ERR_BAD_ARG;
+  if (cudaMalloc(&H.Ad, sizeof(real) * H.ncoarse * H.ncoarse) ||
+      cudaMalloc(&H.Ai, sizeof(real) * H.ncoarse * H.ncoarse))
+    return MPM_ERR_NO_MEMORY;
+  return MPM_OK;
+}
+
+void mg_free(MGHier<real> &H) {
+  cudaFree(H.Ad);
+  cudaFree(H.Ai);
+  H.Ad = H.Ai = nullptr;
+  for (int l = 0; l < H.nlev; ++l) {
+    cudaFree(H.L[l].dinv);
+    cudaFree(H.L[l].sval);
+    cudaFree(H.x[l]);
+    cudaFree(H.x2[l]);
+    cudaFree(H.b[l]);
+    cudaFree(H.r[l]);
+  }
+  H.nlev = 0;
+}
+
+void mg_setup(Ctx &c, MGHier<real> &H, const int32_t *row_ptr, const int32_t *col, const real *val,
+              int moff) {
+  H.L[0].row_ptr = row_ptr;
+  H.L[0].col = col;
+  H.L[0].val = val;
+  H.L[0].fixed = c.fixed;
+  H.L[0].mstride = c.nb;
+  H.L[0].moff = moff;
+  if (c.d == 2) {
+    if (H.B == 1) mg_setup_t<1, 2>(c, H);
+    else mg_setup_t<2, 2>(c, H);
+  } else {
+    if (H.B == 1) mg_setup_t<1, 3>(c, H);
+    else mg_setup_t<3, 3>(c, H);
+  }
+}
+
+// x = V-cycle(b) on the level-0 vectors of H (b copied in, x copied out)
+void mg_vcycle(Ctx &c, MGHier<real> &H, const real *b, real *x) {
+  const int64_t n0 = H.L[0].nnodes * H.B;
+  cudaMemcpyAsync(H.b[0], b, sizeof(real) * n0, cudaMemcpyDeviceToDevice, c.st);
+  if (c.d == 2) {
+    if (H.B == 1) vcycle_t<1, 2>(c, H, 0);
+    else vcycle_t<2, 2>(c, H, 0);
+  } else {
+    if (H.B == 1) vcycle_t<1, 3>(c, H, 0);
+    else vcycle_t<3, 3>(c, H, 0);
+  }
+  cudaMemcpyAsync(x, H.x[0], sizeof(real) * n0, cudaMemcpyDeviceToDevice, c.st);
+}
+
+}  // namespace MG_NS
+
+// ============================================================== Schur
+template <>
+int schur_alloc<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
+  using namespace MG_NS;
+  const int64_t nn = c.g.nnodes;
+  const int d = c.d;
+  if (!S.mgA) S.mgA = new MGHier<MG_REAL>();
+  if (!S.mgS) S.mgS = new MGHier<MG_REAL>();
+  int rc = mg_alloc(c, *S.mgA, d);
+  if (!rc) rc = mg_alloc(c, *S.mgS, 1);
+  if (rc) return rc;
+  if (cudaMalloc(&S.DAinv, sizeof(real) * nn * d * d) || cudaMalloc(&S.vu, sizeof(real) * nn * d) ||
+      cudaMalloc(&S.wu, sizeof(real) * nn * d) || cudaMalloc(&S.zu, sizeof(real) * nn * d) ||
+      cudaMalloc(&S.vp, sizeof(real) * nn) || cudaMalloc(&S.zp, sizeof(real) * nn))
+    return MPM_ERR_NO_MEMORY;
+  return MPM_OK;
+}
+
+template <>
+void schur_free<MG_REAL>(LinSys<MG_REAL> &S) {
+  using namespace MG_NS;
+  if (S.mgA) { mg_free(*S.mgA); delete S.mgA; S.mgA = nullptr; }
+  if (S.mgS) { mg_free(*S.mgS); delete S.mgS; S.mgS = nullptr; }
+  cudaFree(S.Aval);
+  cudaFree(S.Sval);
+  cudaFree(S.DAinv);
+  cudaFree(S.vu);
+  cudaFree(S.wu);
+  cudaFree(S.zu);
+  cudaFree(S.vp);
+  cudaFree(S.zp);
+  S.Aval = S.Sval = S.DAinv = S.vu = S.wu = S.zu = S.vp = S.zp = nullptr;
+  S.sub_cap = 0;
+}
+
+// Split the unscaled Jacobian (after Dirichlet elimination) into A and S and
+// build both hierarchies.
+template <>
+int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
+  using namespace MG_NS;
+  const int64_t nn = c.g.nnodes, nnzb = c.nnzb;
+  const int d = c.d;
+  if (nnzb > S.sub_cap) {
+    cudaFree(S.Aval);
+    cudaFree(S.Sval);
+    S.Aval = S.Sval = nullptr;
+    const int64_t cap = c.nnzb_cap;
+    if (cudaMalloc(&S.Aval, sizeof(real) * cap * d * d) || cudaMalloc(&S.Sval, sizeof(real) * cap)) {
+      S.sub_cap = 0;
+      c.last_error = "device allocation of the block preconditioner failed";
+      return MPM_ERR_NO_MEMORY;
+    }
+    S.sub_cap = cap;
+  }
+  if (d == 2) {
+    k_extract_A<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
+    k_diag_inv_A<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.DAinv);
+    k_schur_rows<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.DAinv, S.Sval);
+  } else {
+    k_extract_A<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
+    k_diag_inv_A<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.DAinv);
+    k_schur_rows<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.DAinv, S.Sval);
+  }
+  c.launches += 3;
+  mg_setup(c, *S.mgA, c.row_ptr, c.col, S.Aval, 0);
+  mg_setup(c, *S.mgS, c.row_ptr, c.col, S.Sval, d);
+  return check_cuda(c, cudaGetLastError(), "schur setup");
+}
+
+// z = M^{-1} v (block upper triangular, multigrid sub-solves)
+template <>
+void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
+  using namespace MG_NS;
+  const int64_t nn = c.g.nnodes;
+  const int nbk = nblk(nn);
+  if (c.d == 2) k_split<2><<<nbk, TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, S.vp);
+  else k_split<3><<<nbk, TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, S.vp);
+  UPMPM_LAUNCH(c);
+  mg_vcycle(c, *S.mgS, S.vp, S.zp);
+  if (c.d == 2)
+    k_b1_update<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.zp, S.vu, S.wu);
+  else
+    k_b1_update<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.zp, S.vu, S.wu);
+  UPMPM_LAUNCH(c);
+  mg_vcycle(c, *S.mgA, S.wu, S.zu);
+  if (c.d == 2) k_merge<2><<<nbk, TPB, 0, c.st>>>(nn, S.zu, S.zp, S.dscale, z);
+  else k_merge<3><<<nbk, TPB, 0, c.st>>>(nn, S.zu, S.zp, S.dscale, z);
+  UPMPM_LAUNCH(c);
+}
+

@@ -1,15 +1,16 @@
 // mpm_solver.cu -- linear algebra of the Newton step (Eq. jacobian-system-
 // stabilized-ppp):  J dX = -R  on the block-CSR Jacobian.
 //
-// The system is first scaled symmetrically, D J D y = -D R with
-// D_ii = |J_ii|^{-1/2}, which brings the momentum rows (stiffness ~ 1e7) and
-// the mass rows (~ 1e-7) to unit diagonal, so that the Krylov residual norm
-// weighs both balance laws; then right-preconditioned restarted FGMRES with
-// classical Gram-Schmidt applied twice (CGS2) and node-block Jacobi
-// preconditioning solves it.  The Givens rotations and the Hessenberg system
-// live in device memory; the host reads one scalar per iteration.
-// All reductions use a fixed grid and a fixed tree, so results are
-// deterministic.  Plain FP64 HBM-bound kernels, no tensor cores (sparse work).
+// The system is scaled symmetrically, D J D y = -D R with D_ii = |J_ii|^{-1/2},
+// which brings the momentum rows (stiffness ~ 1e7) and the mass rows (~ 1e-7)
+// to unit diagonal so that the Krylov residual weighs both balance laws; then
+// right-preconditioned restarted FGMRES with classical Gram-Schmidt applied
+// twice (CGS2) solves it.  The Hessenberg matrix and the Givens rotations live
+// in device memory (FP64); the host reads one scalar per iteration.  Vectors
+// and matrix values are in the precision T of the solve: FP64, or FP32 in the
+// mixed mode (the Newton residual around it stays FP64).  Reductions use a
+// fixed grid and tree (deterministic) and sum each thread's part in T before
+// the FP64 block sum.  No tensor cores: the work is sparse.
 #include <math.h>
 
 #include "mpm_internal.cuh"
@@ -83,8 +84,7 @@ __global__ void k_scan_blocks(const int32_t *__restrict__ in, int32_t *__restric
 }
 
 __global__ void k_scan_top(int32_t *__restrict__ blk, int nb) {
-  // one block; nb <= SCAN_CHUNK
-  const int base = threadIdx.x * SCAN_I;
+  const int base = threadIdx.x * SCAN_I;  // one block; nb <= SCAN_CHUNK
   int v[SCAN_I], s = 0;
   for (int i = 0; i < SCAN_I; ++i) {
     v[i] = (base + i < nb) ? blk[base + i] : 0;
@@ -110,14 +110,15 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int64_t n, const int32_t *
 }
 
 // ---------------------------------------------------------------- vectors
-__global__ void k_dot_partial(const double *__restrict__ x, const double *__restrict__ y, int64_t n,
+template <typename T>
+__global__ void k_dot_partial(const T *__restrict__ x, const T *__restrict__ y, int64_t n,
                               double *__restrict__ part) {
-  double acc = 0.0;
+  T acc = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     acc += x[i] * y[i];
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __global__ void k_reduce(const double *__restrict__ part, int np, double *__restrict__ out) {
@@ -127,47 +128,48 @@ __global__ void k_reduce(const double *__restrict__ part, int np, double *__rest
   if (threadIdx.x == 0) out[0] = acc;
 }
 
-__global__ void k_axpy(double *__restrict__ y, double a, const double *__restrict__ x, int64_t n) {
+template <typename T>
+__global__ void k_scale_copy(T *__restrict__ y, const T *__restrict__ x, const double *s, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] += a * x[i];
+  if (i < n) y[i] = x[i] * (T)s[0];
 }
 
-__global__ void k_scale_copy(double *__restrict__ y, const double *__restrict__ x, const double *s,
-                             int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = x[i] * s[0];
-}
-
-// y = b - y
-__global__ void k_residual_vec(double *__restrict__ y, const double *__restrict__ b, int64_t n) {
+template <typename T>
+__global__ void k_residual_vec(T *__restrict__ y, const T *__restrict__ b, int64_t n) {  // y = b - y
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = b[i] - y[i];
 }
 
 // ---------------------------------------------------------------- scaling
-template <int NB>
-__global__ void k_diag_scale(int64_t nnodes, const int32_t *__restrict__ row_ptr,
-                             const int32_t *__restrict__ col, const double *__restrict__ val,
-                             double *__restrict__ dsc) {
-  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (a >= nnodes) return;
-  int lo = row_ptr[a], hi = row_ptr[a + 1] - 1, e = -1;
+__device__ inline int find_diag(const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                                int64_t a) {
+  int lo = row_ptr[a], hi = row_ptr[a + 1] - 1;
   while (lo <= hi) {
     const int mid = (lo + hi) >> 1;
     const int cm = col[mid];
-    if (cm == a) { e = mid; break; }
+    if (cm == a) return mid;
     if (cm < a) lo = mid + 1; else hi = mid - 1;
   }
+  return -1;
+}
+
+template <int NB, typename T>
+__global__ void k_diag_scale(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const T *__restrict__ val,
+                             T *__restrict__ dsc) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nnodes) return;
+  const int e = find_diag(row_ptr, col, a);
   for (int r = 0; r < NB; ++r) {
-    const double d = e >= 0 ? fabs(val[(int64_t)e * NB * NB + r * NB + r]) : 0.0;
-    dsc[a * NB + r] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+    const double d = e >= 0 ? fabs((double)val[(int64_t)e * NB * NB + r * NB + r]) : 0.0;
+    dsc[a * NB + r] = (T)(d > 0.0 ? 1.0 / sqrt(d) : 1.0);
   }
 }
 
-template <int NB>
+template <int NB, typename T>
 __global__ void k_scale_matrix(int64_t nnzb, const int32_t *__restrict__ row_of,
-                               const int32_t *__restrict__ col, double *__restrict__ val,
-                               const double *__restrict__ dsc) {
+                               const int32_t *__restrict__ col, T *__restrict__ val,
+                               const T *__restrict__ dsc) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nnzb * NB * NB) return;
   const int64_t e = t / (NB * NB);
@@ -176,40 +178,35 @@ __global__ void k_scale_matrix(int64_t nnzb, const int32_t *__restrict__ row_of,
   val[t] *= dsc[(int64_t)row_of[e] * NB + r] * dsc[(int64_t)col[e] * NB + cc];
 }
 
-__global__ void k_scale_rhs(int64_t n, const double *__restrict__ R, const double *__restrict__ dsc,
-                            double *__restrict__ rhs) {
+template <typename T>
+__global__ void k_scale_rhs(int64_t n, const double *__restrict__ R, const T *__restrict__ dsc,
+                            T *__restrict__ rhs) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) rhs[i] = -dsc[i] * R[i];
+  if (i < n) rhs[i] = (T)(-(double)dsc[i] * R[i]);
 }
 
-__global__ void k_unscale_add(int64_t n, double *__restrict__ X, const double *__restrict__ dsc,
-                              const double *__restrict__ y) {
+template <typename T>
+__global__ void k_unscale_add(int64_t n, double *__restrict__ X, const T *__restrict__ dsc,
+                              const T *__restrict__ y) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) X[i] += dsc[i] * y[i];
+  if (i < n) X[i] += (double)dsc[i] * (double)y[i];
 }
 
 // ---------------------------------------------------------------- block Jacobi
-template <int NB>
+template <int NB, typename T>
 __global__ void k_block_jacobi(int64_t nnodes, const int32_t *__restrict__ row_ptr,
-                               const int32_t *__restrict__ col, const double *__restrict__ val,
-                               double *__restrict__ dinv, int *err) {
+                               const int32_t *__restrict__ col, const T *__restrict__ val,
+                               T *__restrict__ dinv, int *err) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
-  int lo = row_ptr[a], hi = row_ptr[a + 1] - 1, e = -1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const int cm = col[mid];
-    if (cm == a) { e = mid; break; }
-    if (cm < a) lo = mid + 1; else hi = mid - 1;
-  }
+  const int e = find_diag(row_ptr, col, a);
   double A[NB][NB], B[NB][NB];
   for (int i = 0; i < NB; ++i)
     for (int j = 0; j < NB; ++j) {
-      A[i][j] = e >= 0 ? val[(int64_t)e * NB * NB + i * NB + j] : (i == j ? 1.0 : 0.0);
+      A[i][j] = e >= 0 ? (double)val[(int64_t)e * NB * NB + i * NB + j] : (i == j ? 1.0 : 0.0);
       B[i][j] = i == j ? 1.0 : 0.0;
     }
-  // Gauss-Jordan with partial pivoting
-  bool ok = true;
+  bool ok = true;  // Gauss-Jordan with partial pivoting
   for (int k = 0; k < NB; ++k) {
     int piv = k;
     double best = fabs(A[k][k]);
@@ -236,46 +233,45 @@ __global__ void k_block_jacobi(int64_t nnodes, const int32_t *__restrict__ row_p
       for (int j = 0; j < NB; ++j) B[i][j] = i == j ? 1.0 : 0.0;
   }
   for (int i = 0; i < NB; ++i)
-    for (int j = 0; j < NB; ++j) dinv[a * NB * NB + i * NB + j] = B[i][j];
+    for (int j = 0; j < NB; ++j) dinv[a * NB * NB + i * NB + j] = (T)B[i][j];
 }
 
-template <int NB>
-__global__ void k_bj_apply(int64_t nnodes, const double *__restrict__ dinv, const double *__restrict__ x,
-                           double *__restrict__ y) {
+template <int NB, typename T>
+__global__ void k_bj_apply(int64_t nnodes, const T *__restrict__ dinv, const T *__restrict__ x,
+                           T *__restrict__ y) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
-  double xv[NB];
+  T xv[NB];
   for (int j = 0; j < NB; ++j) xv[j] = x[a * NB + j];
   for (int i = 0; i < NB; ++i) {
-    double s = 0.0;
+    T s = 0;
     for (int j = 0; j < NB; ++j) s += dinv[a * NB * NB + i * NB + j] * xv[j];
     y[a * NB + i] = s;
   }
 }
 
 // ---------------------------------------------------------------- SpMV
-// LN lanes per block row; each lane takes whole NB x NB blocks (72 / 128
-// contiguous bytes, so the lanes of a row read one contiguous span), does one
-// FMA per matrix value, and the row's NB sums are reduced across the lanes.
-// (The FP64 pipe of GB300 is narrow, so the kernel spends exactly one FP64
-// instruction per stored value.)
-template <int NB, int LN>
+// LN lanes per block row; each lane takes whole NB x NB blocks (the lanes of a
+// row read one contiguous span), one FMA per stored value (GB300's FP64 pipe
+// is narrow, so an FP64 SpMV spends exactly one FP64 instruction per value),
+// and the row's NB sums are reduced across the lanes.
+template <int NB, int LN, typename T>
 __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
-                           const int32_t *__restrict__ col, const double *__restrict__ val,
-                           const double *__restrict__ x, double *__restrict__ y) {
+                           const int32_t *__restrict__ col, const T *__restrict__ val,
+                           const T *__restrict__ x, T *__restrict__ y) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = t / LN;
   const int lane = (int)(t % LN);
   const bool valid = row < nnodes;
-  double acc[NB];
+  T acc[NB];
 #pragma unroll
-  for (int r = 0; r < NB; ++r) acc[r] = 0.0;
+  for (int r = 0; r < NB; ++r) acc[r] = 0;
   if (valid) {
     const int e1 = row_ptr[row + 1];
     for (int e = row_ptr[row] + lane; e < e1; e += LN) {
-      const double *blk = val + (int64_t)e * NB * NB;
-      const double *xb = x + (int64_t)__ldg(&col[e]) * NB;
-      double xv[NB];
+      const T *blk = val + (int64_t)e * NB * NB;
+      const T *xb = x + (int64_t)__ldg(&col[e]) * NB;
+      T xv[NB];
 #pragma unroll
       for (int c = 0; c < NB; ++c) xv[c] = __ldg(&xb[c]);
 #pragma unroll
@@ -295,23 +291,23 @@ __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
 
 // ---------------------------------------------------------------- FGMRES
 // partial dots of w against V_0..V_{cnt-1}
-__global__ void k_multidot_partial(const double *__restrict__ V, int cnt, const double *__restrict__ w,
+template <typename T>
+__global__ void k_multidot_partial(const T *__restrict__ V, int cnt, const T *__restrict__ w,
                                    int64_t n, double *__restrict__ part) {
   for (int i = 0; i < cnt; ++i) {
-    const double *vi = V + (int64_t)i * n;
-    double acc = 0.0;
+    const T *vi = V + (int64_t)i * n;
+    T acc = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x)
       acc += vi[k] * w[k];
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = acc;
+    const double s = block_sum((double)acc);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = s;
   }
 }
 
 __global__ void k_multidot_reduce(const double *__restrict__ part, int np, int cnt,
                                   double *__restrict__ h) {
-  // one block per coefficient
-  const int i = blockIdx.x;
+  const int i = blockIdx.x;  // one block per coefficient
   if (i >= cnt) return;
   double acc = 0.0;
   for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * PSTR + i];
@@ -321,29 +317,30 @@ __global__ void k_multidot_reduce(const double *__restrict__ part, int np, int c
 
 // w -= sum_i h_i V_i over the thread's elements, then partial dots of the
 // updated w against V_i (second Gram-Schmidt pass) or with itself (norm).
-__global__ void k_orth_update(double *__restrict__ w, const double *__restrict__ V, const double *h,
-                              int cnt, int64_t n, double *__restrict__ part, int want_norm) {
+template <typename T>
+__global__ void k_orth_update(T *__restrict__ w, const T *__restrict__ V, const double *h, int cnt,
+                              int64_t n, double *__restrict__ part, int want_norm) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    double s = w[k];
-    for (int i = 0; i < cnt; ++i) s -= h[i] * V[(int64_t)i * n + k];
+    T s = w[k];
+    for (int i = 0; i < cnt; ++i) s -= (T)h[i] * V[(int64_t)i * n + k];
     w[k] = s;
   }
   if (want_norm) {
-    double acc = 0.0;
+    T acc = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x)
       acc += w[k] * w[k];
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR] = acc;
+    const double s = block_sum((double)acc);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR] = s;
   } else {
     for (int i = 0; i < cnt; ++i) {
-      double acc = 0.0;
+      T acc = 0;
       for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
            k += (int64_t)gridDim.x * blockDim.x)
         acc += V[(int64_t)i * n + k] * w[k];
-      acc = block_sum(acc);
-      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = acc;
+      const double s = block_sum((double)acc);
+      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = s;
     }
   }
 }
@@ -403,32 +400,32 @@ __global__ void k_backsolve(const double *__restrict__ H, const double *__restri
   }
 }
 
-__global__ void k_update_x(double *__restrict__ x, const double *__restrict__ Z, const double *y, int jc,
-                           int64_t n) {
+template <typename T>
+__global__ void k_update_x(T *__restrict__ x, const T *__restrict__ Z, const double *y, int jc, int64_t n) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
-  double s = x[k];
-  for (int i = 0; i < jc; ++i) s += y[i] * Z[(int64_t)i * n + k];
+  T s = x[k];
+  for (int i = 0; i < jc; ++i) s += (T)y[i] * Z[(int64_t)i * n + k];
   x[k] = s;
 }
 
-template <int NB>
-void spmv(Ctx &c, const double *x, double *y) {
+template <int NB, typename T>
+void spmv(Ctx &c, const LinSys<T> &S, const T *x, T *y) {
   constexpr int LN = NB == 3 ? 8 : 16;
   const int64_t threads = c.g.nnodes * LN;
   prof_begin(c, MPM_PROF_SPMV);
-  k_bsr_spmv<NB, LN><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, c.val, x, y);
+  k_bsr_spmv<NB, LN, T><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, S.val, x, y);
   prof_end(c, MPM_PROF_SPMV);
   UPMPM_LAUNCH(c);
 }
 
-template <int NB>
-void precond(Ctx &c, const double *x, double *y) {
+template <int NB, typename T>
+void precond(Ctx &c, LinSys<T> &S, const T *x, T *y) {
   prof_begin(c, MPM_PROF_PRECOND);
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
-    schur_apply(c, x, y);
+    schur_apply<T>(c, S, x, y);
   } else {
-    k_bj_apply<NB><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g.nnodes, c.dinv, x, y);
+    k_bj_apply<NB, T><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g.nnodes, S.dinv, x, y);
     UPMPM_LAUNCH(c);
   }
   prof_end(c, MPM_PROF_PRECOND);
@@ -440,19 +437,20 @@ double read_scalar(Ctx &c, const double *dptr) {
   return c.h_scalar[0];
 }
 
-template <int NB>
-int fgmres_impl(Ctx &c, const double *b, double *x, double rtol, int maxit, int *iters) {
+template <int NB, typename T>
+int fgmres_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
   const int64_t N = c.N();
   const int m = c.m_restart;
   const int gN = nblk(N);
-  double *w = c.w;
+  const T *b = S.rhs;
+  T *x = S.x, *w = S.w;
   double *h1 = c.hcol, *h2 = c.hcol + PSTR;
-  cudaMemsetAsync(x, 0, sizeof(double) * N, c.st);
+  cudaMemsetAsync(x, 0, sizeof(T) * N, c.st);
   // beta = ||b||, V_0 = b / beta
-  k_dot_partial<<<NPART, TPB, 0, c.st>>>(b, b, N, c.part);
+  k_dot_partial<T><<<NPART, TPB, 0, c.st>>>(b, b, N, c.part);
   k_reduce<<<1, TPB, 0, c.st>>>(c.part, NPART, c.scal + 2);
   k_gmres_init<<<1, 32, 0, c.st>>>(c.gvec, m, c.scal + 2, c.scal);
-  k_scale_copy<<<gN, TPB, 0, c.st>>>(c.V, b, c.scal + 1, N);
+  k_scale_copy<T><<<gN, TPB, 0, c.st>>>(S.V, b, c.scal + 1, N);
   c.launches += 4;
   const double beta0 = read_scalar(c, c.scal);
   *iters = 0;
@@ -464,18 +462,18 @@ int fgmres_impl(Ctx &c, const double *b, double *x, double rtol, int maxit, int 
   while (true) {
     int jc = 0;
     for (int j = 0; j < m; ++j) {
-      double *Vj = c.V + (int64_t)j * N, *Zj = c.Z + (int64_t)j * N, *Vn = c.V + (int64_t)(j + 1) * N;
-      precond<NB>(c, Vj, Zj);
-      spmv<NB>(c, Zj, w);
+      T *Vj = S.V + (int64_t)j * N, *Zj = S.Z + (int64_t)j * N, *Vn = S.V + (int64_t)(j + 1) * N;
+      precond<NB, T>(c, S, Vj, Zj);
+      spmv<NB, T>(c, S, Zj, w);
       prof_begin(c, MPM_PROF_ORTH);
-      k_multidot_partial<<<NPART, TPB, 0, c.st>>>(c.V, j + 1, w, N, c.part);
+      k_multidot_partial<T><<<NPART, TPB, 0, c.st>>>(S.V, j + 1, w, N, c.part);
       k_multidot_reduce<<<j + 1, TPB, 0, c.st>>>(c.part, NPART, j + 1, h1);
-      k_orth_update<<<NPART, TPB, 0, c.st>>>(w, c.V, h1, j + 1, N, c.part, 0);
+      k_orth_update<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h1, j + 1, N, c.part, 0);
       k_multidot_reduce<<<j + 1, TPB, 0, c.st>>>(c.part, NPART, j + 1, h2);
-      k_orth_update<<<NPART, TPB, 0, c.st>>>(w, c.V, h2, j + 1, N, c.part, 1);
+      k_orth_update<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h2, j + 1, N, c.part, 1);
       prof_end(c, MPM_PROF_ORTH);
       k_arnoldi_finish<<<1, TPB, 0, c.st>>>(c.part, NPART, j, m, h1, h2, c.H, c.gvec, c.cs, c.sn, c.scal);
-      k_scale_copy<<<gN, TPB, 0, c.st>>>(Vn, w, c.scal + 1, N);
+      k_scale_copy<T><<<gN, TPB, 0, c.st>>>(Vn, w, c.scal + 1, N);
       c.launches += 7;
       ++total;
       jc = j + 1;
@@ -488,17 +486,17 @@ int fgmres_impl(Ctx &c, const double *b, double *x, double rtol, int maxit, int 
       if (total >= maxit) break;
     }
     k_backsolve<<<1, 32, 0, c.st>>>(c.H, c.gvec, jc, m, c.yv);
-    k_update_x<<<gN, TPB, 0, c.st>>>(x, c.Z, c.yv, jc, N);
+    k_update_x<T><<<gN, TPB, 0, c.st>>>(x, S.Z, c.yv, jc, N);
     c.launches += 2;
     if (converged || total >= maxit) break;
-    // restart from the true residual r = b - A M^{-1}... in right
-    // preconditioning x is already in the unpreconditioned space: r = b - A x
-    spmv<NB>(c, x, w);
-    k_residual_vec<<<gN, TPB, 0, c.st>>>(w, b, N);
-    k_dot_partial<<<NPART, TPB, 0, c.st>>>(w, w, N, c.part);
+    // restart from the true residual r = b - A x (right preconditioning: x is
+    // already in the unpreconditioned space)
+    spmv<NB, T>(c, S, x, w);
+    k_residual_vec<T><<<gN, TPB, 0, c.st>>>(w, b, N);
+    k_dot_partial<T><<<NPART, TPB, 0, c.st>>>(w, w, N, c.part);
     k_reduce<<<1, TPB, 0, c.st>>>(c.part, NPART, c.scal + 2);
     k_gmres_init<<<1, 32, 0, c.st>>>(c.gvec, m, c.scal + 2, c.scal);
-    k_scale_copy<<<gN, TPB, 0, c.st>>>(c.V, w, c.scal + 1, N);
+    k_scale_copy<T><<<gN, TPB, 0, c.st>>>(S.V, w, c.scal + 1, N);
     c.launches += 5;
     const double br = read_scalar(c, c.scal);
     if (br <= target) {
@@ -509,6 +507,12 @@ int fgmres_impl(Ctx &c, const double *b, double *x, double rtol, int maxit, int 
   *iters = total;
   if (check_cuda(c, cudaGetLastError(), "fgmres")) return MPM_ERR_CUDA;
   return converged ? MPM_OK : MPM_ERR_KRYLOV_STAGNATED;
+}
+
+template <typename T>
+int dmalloc(T **p, int64_t n) {
+  return cudaMalloc((void **)p, sizeof(T) * (size_t)(n > 0 ? n : 1)) == cudaSuccess ? MPM_OK
+                                                                                     : MPM_ERR_NO_MEMORY;
 }
 
 }  // namespace
@@ -528,52 +532,110 @@ int64_t scan_exclusive(Ctx &c, const int32_t *in, int32_t *out, int64_t n) {
 }
 
 double run_norm(Ctx &c, const double *x) {
-  k_dot_partial<<<NPART, TPB, 0, c.st>>>(x, x, c.N(), c.part);
+  k_dot_partial<double><<<NPART, TPB, 0, c.st>>>(x, x, c.N(), c.part);
   k_reduce<<<1, TPB, 0, c.st>>>(c.part, NPART, c.scal + 3);
   c.launches += 2;
   return sqrt(read_scalar(c, c.scal + 3));
 }
 
-void run_axpy(Ctx &c, double *y, double a, const double *x, int64_t n) {
-  k_axpy<<<nblk(n), TPB, 0, c.st>>>(y, a, x, n);
-  UPMPM_LAUNCH(c);
+template <typename T>
+int linsys_alloc(Ctx &c, LinSys<T> &S, bool krylov) {
+  const int64_t nn = c.g.nnodes, N = c.N();
+  const int nb = c.nb, m = c.m_restart;
+  int rc = MPM_OK;
+  auto A = [&](T **p, int64_t n) {
+    if (!rc) rc = dmalloc(p, n);
+  };
+  A(&S.dscale, N);
+  A(&S.dinv, nn * nb * nb);
+  A(&S.rhs, N);
+  A(&S.x, N);
+  A(&S.w, N);
+  if (krylov) {
+    A(&S.V, (int64_t)(m + 1) * N);
+    A(&S.Z, (int64_t)m * N);
+  }
+  if (!rc && c.opt.precond == MPM_PRECOND_SCHUR_MG) rc = schur_alloc<T>(c, S);
+  return rc;
 }
 
-void run_scale_system(Ctx &c, double *rhs_out, const double *R) {
+template <typename T>
+void linsys_free(LinSys<T> &S) {
+  schur_free<T>(S);
+  T *ptrs[] = {S.val, S.dscale, S.dinv, S.rhs, S.x, S.w, S.V, S.Z};
+  for (T *p : ptrs)
+    if (p) cudaFree(p);
+  S.val = S.dscale = S.dinv = S.rhs = S.x = S.w = S.V = S.Z = nullptr;
+  S.cap = 0;
+}
+
+template <typename T>
+int linsys_reserve(Ctx &c, LinSys<T> &S) {
+  if (S.cap >= c.nnzb_cap && S.val) return MPM_OK;
+  if (S.val) cudaFree(S.val);
+  S.val = nullptr;
+  S.cap = 0;
+  if (dmalloc(&S.val, c.nnzb_cap * c.nb * c.nb)) {
+    c.last_error = "device allocation of the block-CSR values failed";
+    return MPM_ERR_NO_MEMORY;
+  }
+  S.cap = c.nnzb_cap;
+  return MPM_OK;
+}
+
+template <typename T>
+void run_scale_system(Ctx &c, LinSys<T> &S, const double *R) {
   const int64_t nn = c.g.nnodes;
   if (c.nb == 3) {
-    k_diag_scale<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dscale);
-    k_scale_matrix<3><<<nblk(c.nnzb * 9), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, c.val, c.dscale);
+    k_diag_scale<3, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale);
+    k_scale_matrix<3, T><<<nblk(c.nnzb * 9), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
   } else {
-    k_diag_scale<4><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dscale);
-    k_scale_matrix<4><<<nblk(c.nnzb * 16), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, c.val, c.dscale);
+    k_diag_scale<4, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale);
+    k_scale_matrix<4, T><<<nblk(c.nnzb * 16), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
   }
-  k_scale_rhs<<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), R, c.dscale, rhs_out);
+  k_scale_rhs<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), R, S.dscale, S.rhs);
   c.launches += 3;
 }
 
-void run_unscale_add(Ctx &c, double *X, const double *xhat) {
-  k_unscale_add<<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), X, c.dscale, xhat);
+template <typename T>
+void run_unscale_add(Ctx &c, const LinSys<T> &S, double *X) {
+  k_unscale_add<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), X, S.dscale, S.x);
   UPMPM_LAUNCH(c);
 }
 
-void run_block_jacobi(Ctx &c) {
+template <typename T>
+void run_block_jacobi(Ctx &c, LinSys<T> &S) {
   const int64_t nn = c.g.nnodes;
   if (c.nb == 3)
-    k_block_jacobi<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dinv, c.err);
+    k_block_jacobi<3, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dinv, c.err);
   else
-    k_block_jacobi<4><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, c.val, c.dinv, c.err);
+    k_block_jacobi<4, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dinv, c.err);
   UPMPM_LAUNCH(c);
 }
 
-void run_precond(Ctx &c, const double *v, double *z) {
-  if (c.nb == 3) precond<3>(c, v, z);
-  else precond<4>(c, v, z);
+template <typename T>
+void run_precond(Ctx &c, LinSys<T> &S, const T *v, T *z) {
+  if (c.nb == 3) precond<3, T>(c, S, v, z);
+  else precond<4, T>(c, S, v, z);
 }
 
-int run_fgmres(Ctx &c, const double *b, double *x, double rtol, int maxit, int *iters) {
-  if (c.nb == 3) return fgmres_impl<3>(c, b, x, rtol, maxit, iters);
-  return fgmres_impl<4>(c, b, x, rtol, maxit, iters);
+template <typename T>
+int run_fgmres(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
+  if (c.nb == 3) return fgmres_impl<3, T>(c, S, rtol, maxit, iters);
+  return fgmres_impl<4, T>(c, S, rtol, maxit, iters);
 }
+
+#define UPMPM_INST(T)                                                               \
+  template int linsys_alloc<T>(Ctx &, LinSys<T> &, bool);                           \
+  template void linsys_free<T>(LinSys<T> &);                                        \
+  template int linsys_reserve<T>(Ctx &, LinSys<T> &);                               \
+  template void run_scale_system<T>(Ctx &, LinSys<T> &, const double *);            \
+  template void run_unscale_add<T>(Ctx &, const LinSys<T> &, double *);             \
+  template void run_block_jacobi<T>(Ctx &, LinSys<T> &);                            \
+  template void run_precond<T>(Ctx &, LinSys<T> &, const T *, T *);                 \
+  template int run_fgmres<T>(Ctx &, LinSys<T> &, double, int, int *);
+UPMPM_INST(double)
+UPMPM_INST(float)
+#undef UPMPM_INST
 
 }  // namespace upmpm
