@@ -173,7 +173,10 @@ def run_ours(args, rank, world, local_rank):
         B.build()
     mpm.load()
     w = make_workload(args.workload)
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the library launches on it (CUDA-graph capture needs a
+    # non-default stream) and the timing events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     prof_bits = 0
     for k in args.profile.split(","):
         if k:

@@ -37,6 +37,11 @@ DevView Ctx::view() const {
   v.phi = phi;
   v.act = act;
   v.sh_nrm = sh_nrm;
+  v.sh_Sf = sh_Sf;
+  v.sh_dSf = sh_dSf;
+  v.sh_S0f = sh_S0f;
+  v.sh_nrmf = sh_nrmf;
+  v.recf = recf;
   v.fixed = fixed;
   v.u_fixed = u_fixed;
   v.u_value = u_value;
@@ -82,7 +87,7 @@ int read_dev_err(Ctx &c) {
 }
 
 void prof_begin(Ctx &c, int kind) {
-  if (!((c.opt.profile >> kind) & 1)) return;
+  if (!((c.opt.profile >> kind) & 1) || c.capturing) return;
   if ((size_t)(2 * c.ev_used + 2) > c.ev.size()) {
     if (c.ev.size() >= (1u << 15)) prof_collect(c);  // bounded pool: drain it
     while ((size_t)(2 * c.ev_used + 2) > c.ev.size()) {
@@ -96,7 +101,7 @@ void prof_begin(Ctx &c, int kind) {
 }
 
 void prof_end(Ctx &c, int kind) {
-  if (!((c.opt.profile >> kind) & 1)) return;
+  if (!((c.opt.profile >> kind) & 1) || c.capturing) return;
   if ((size_t)(2 * c.ev_used + 2) > c.ev.size()) return;
   cudaEventRecord(c.ev[2 * c.ev_used + 1], c.st);
   c.ev_kind[c.ev_used] = kind;
@@ -350,6 +355,9 @@ void free_all(Ctx &c) {
   c.ev.clear();
   linsys_free<double>(c.L64);
   linsys_free<float>(c.L32);
+  float *fptrs[] = {c.sh_Sf, c.sh_dSf, c.sh_S0f, c.sh_nrmf, c.recf};
+  for (float *p : fptrs)
+    if (p) cudaFree(p);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
                   c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS,
                   c.sh_S0, c.m, c.rec, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.sh_nrm, c.fixed, c.u_fixed,
@@ -360,6 +368,8 @@ void free_all(Ctx &c) {
     if (p) cudaFree(p);
   if (c.h_err) cudaFreeHost(c.h_err);
   if (c.h_scalar) cudaFreeHost(c.h_scalar);
+  if (c.own_stream && c.st) cudaStreamDestroy(c.st);
+  c.st = nullptr;
 }
 
 }  // namespace
@@ -424,6 +434,15 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   Ctx &c = h->c;
   c.opt = *opt;
   c.st = (cudaStream_t)opt->stream;
+  if (!c.st) {
+    // a stream of our own (blocking, so it stays ordered with the legacy
+    // default stream); needed for CUDA graph capture
+    if (cudaStreamCreate(&c.st) != cudaSuccess) {
+      delete h;
+      return MPM_ERR_CUDA;
+    }
+    c.own_stream = true;
+  }
   c.d = grid->dim;
   c.nb = c.d + 1;
   c.shape = opt->shape;
@@ -521,6 +540,16 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   c.scan_cap = 4096;
   A(&c.scan_tmp, c.scan_cap);
   c.have32 = c.precision == MPM_MIXED;
+  if (c.have32) {
+    auto F = [&](float **p, int64_t cnt) {
+      if (!rc && cudaMalloc((void **)p, sizeof(float) * cnt) != cudaSuccess) rc = MPM_ERR_NO_MEMORY;
+    };
+    F(&c.sh_Sf, 3 * MAXS * n);
+    F(&c.sh_dSf, 3 * MAXS * n);
+    F(&c.sh_S0f, 3 * MAXS * n);
+    F(&c.sh_nrmf, 5 * n);
+    F(&c.recf, RC_COUNT * n);
+  }
   if (!rc) rc = linsys_alloc<double>(c, c.L64, !c.have32);
   if (!rc && c.have32) rc = linsys_alloc<float>(c, c.L32, true);
   if (!rc && cudaHostAlloc((void **)&c.h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess)

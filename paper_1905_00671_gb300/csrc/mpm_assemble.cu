@@ -190,6 +190,8 @@ __global__ void k_renorm(GridP g, DevView v) {
     v.sh_nrm[0 * n + p] = 1.0 / sum;
     for (int k = 0; k < 3; ++k) v.sh_nrm[(1 + k) * n + p] = gs[k];
     v.sh_nrm[4 * n + p] = 1.0 / sum0;
+    if (v.sh_nrmf)
+      for (int k = 0; k < 5; ++k) v.sh_nrmf[k * n + p] = (float)v.sh_nrm[k * n + p];
     packed |= RENORM_BIT;
   }
   v.sh_cnt[p] = packed;
@@ -325,6 +327,8 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
   rec[RC_DIVV * n + p] = vol * divv;
   rec[RC_B2 * n + p] = DYN ? vol * (gm / (b * dt) + divv) : vol * (1.0 + log(dJ)) / dt;
   rec[RC_MS * n + p] = DYN ? m / (b * dt * dt) : 0.0;
+  if (v.recf)
+    for (int f = 0; f < RC_COUNT; ++f) v.recf[f * n + p] = (float)rec[f * n + p];
 }
 
 // ---------------------------------------------------------------- residual
@@ -387,12 +391,12 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
 }
 
 // ---------------------------------------------------------------- Jacobian
-// Block values are written in precision T (FP64, or FP32 for the mixed-
-// precision Krylov solve); the sums are formed in FP64 from the FP64 records.
-template <int D, bool GIMP, bool DYN, typename T>
-__global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restrict__ row_of,
-                           const int32_t *__restrict__ col, int64_t nnzb, T *__restrict__ val,
-                           int apply_bc) {
+// Block values are written in precision T and computed in precision R: FP64
+// from the FP64 records, or FP32 from their FP32 copies in the mixed mode.
+template <int D, bool GIMP, bool DYN, typename T, typename R>
+__global__ void k_jacobian(GridP g, StepP s, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
+                           const int32_t *__restrict__ row_of, const int32_t *__restrict__ col,
+                           int64_t nnzb, T *__restrict__ val, int apply_bc) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nnzb) return;
   constexpr int NB = D + 1;
@@ -409,10 +413,9 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restric
     lo[k] = max(l1, l2);
     hi[k] = min(h1, h2);
   }
-  double B[NB * NB];
-  for (int i = 0; i < NB * NB; ++i) B[i] = 0.0;
-  const double *rec = v.rec;
-  const double cvis = DYN ? s.alpha_vis * s.gamma / (s.beta * s.dt) : 0.0;
+  R B[NB * NB];
+  for (int i = 0; i < NB * NB; ++i) B[i] = 0;
+  const R cvis = DYN ? (R)(s.alpha_vis * s.gamma / (s.beta * s.dt)) : R(0);
   for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
     for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
       for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
@@ -420,27 +423,35 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restric
         for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
           int oa[3], ob[3];
           if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
-          double Sa, S0a, Gna[3], Sb, S0b, Gnb[3], ga[3], gb[3];
-          basis_at<D>(v, q, oa, a, Sa, S0a, Gna);
-          basis_at<D>(v, q, ob, bn, Sb, S0b, Gnb);
-          spatial_grad<D>(v, q, Gna, ga);
-          spatial_grad<D>(v, q, Gnb, gb);
-          const double cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
-          const double mu = rec[RC_MUP * n + q], lam = rec[RC_LAM * n + q], kv = rec[RC_KV * n + q];
-          double gab = 0.0, gtg = 0.0, gaw = 0.0, gbw = 0.0;
+          R Sa, S0a, Gna[3], Sb, S0b, Gnb[3], ga[3], gb[3];
+          basis_at_t<D, R>(BA, q, oa, a, Sa, S0a, Gna);
+          basis_at_t<D, R>(BA, q, ob, bn, Sb, S0b, Gnb);
+          for (int j = 0; j < D; ++j) {
+            R sa = 0, sb = 0;
+            for (int k = 0; k < D; ++k) {
+              const R fkj = rec[(RC_FINV + k * D + j) * n + q];
+              sa += Gna[k] * fkj;
+              sb += Gnb[k] * fkj;
+            }
+            ga[j] = sa;
+            gb[j] = sb;
+          }
+          const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
+          const R mu = rec[RC_MUP * n + q], lam = rec[RC_LAM * n + q], kv = rec[RC_KV * n + q];
+          R gab = 0, gtg = 0, gaw = 0, gbw = 0;
           for (int j = 0; j < D; ++j) {
             gab += ga[j] * gb[j];
-            const double wj = rec[(RC_W + j) * n + q];
+            const R wj = rec[(RC_W + j) * n + q];
             gaw += ga[j] * wj;
             gbw += gb[j] * wj;
             for (int l = 0; l < D; ++l) gtg += ga[j] * rec[(RC_TAU + j * D + l) * n + q] * gb[l];
           }
-          const double ms = DYN ? rec[RC_MS * n + q] * Sa * Sb : 0.0;
+          const R ms = DYN ? rec[RC_MS * n + q] * Sa * Sb : R(0);
           for (int i = 0; i < D; ++i)
             for (int k = 0; k < D; ++k) {
-              const double dik = i == k ? 1.0 : 0.0;
-              const double sym = mu * (dik * gab + ga[k] * gb[i]);
-              double A = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
+              const R dik = i == k ? R(1) : R(0);
+              const R sym = mu * (dik * gab + ga[k] * gb[i]);
+              R A = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
               A += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
               if (DYN) {
                 A -= cs * cvis * (lam * ga[i] * gb[k] + sym);
@@ -449,11 +460,11 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restric
               B[i * NB + k] += A;
             }
           for (int i = 0; i < D; ++i) B[i * NB + D] += vol * ga[i] * Sb;
-          const double b2 = rec[RC_B2 * n + q];
+          const R b2 = rec[RC_B2 * n + q];
           for (int k = 0; k < D; ++k) {
-            double t = Sa * b2 * gb[k];
+            R t = Sa * b2 * gb[k];
             if (DYN) {
-              double gbgv = 0.0;
+              R gbgv = 0;
               for (int j = 0; j < D; ++j) gbgv += gb[j] * rec[(RC_GV + j * D + k) * n + q];
               t -= vol * Sa * gbgv;
             }
@@ -469,7 +480,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const int32_t *__restric
       const bool fr = v.fixed[a * NBc + i] != 0;
       for (int k = 0; k < NBc; ++k) {
         const bool fc = v.fixed[bn * NBc + k] != 0;
-        if (fr || fc) B[i * NBc + k] = (a == bn && i == k) ? 1.0 : 0.0;
+        if (fr || fc) B[i * NBc + k] = (a == bn && i == k) ? R(1) : R(0);
       }
     }
   }
@@ -568,8 +579,22 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
   const DevView v = c.view();
   const int nbk = nblk(c.nnzb, 128);
   const bool gimp = c.shape == MPM_SHAPE_GIMP;
+  // FP32 values are computed in FP32 from the FP32 copies; FP64 in FP64
+  using R = T;
+  BasisArrays<R> BA;
+  BA.n = c.n;
+  BA.cnt = c.sh_cnt;
+  BA.act = c.act;
+  const R *rec;
+  if constexpr (sizeof(T) == sizeof(double)) {
+    BA.S = (const R *)c.sh_S; BA.dS = (const R *)c.sh_dS; BA.S0 = (const R *)c.sh_S0;
+    BA.nrm = (const R *)c.sh_nrm; rec = (const R *)c.rec;
+  } else {
+    BA.S = (const R *)c.sh_Sf; BA.dS = (const R *)c.sh_dSf; BA.S0 = (const R *)c.sh_S0f;
+    BA.nrm = (const R *)c.sh_nrmf; rec = (const R *)c.recf;
+  }
 #define JAC(D, G, Y) \
-  k_jacobian<D, G, Y, T><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, c.row_of, c.col, c.nnzb, val, apply_bc)
+  k_jacobian<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_of, c.col, c.nnzb, val, apply_bc)
   if (c.d == 2) {
     if (gimp) { if (c.dyn) JAC(2, true, true); else JAC(2, true, false); }
     else { if (c.dyn) JAC(2, false, true); else JAC(2, false, false); }

@@ -41,6 +41,12 @@ struct LinSys {
   T *Aval = nullptr, *Sval = nullptr, *DAinv = nullptr;
   T *vu = nullptr, *wu = nullptr, *zu = nullptr, *vp = nullptr, *zp = nullptr;
   int64_t sub_cap = 0;
+  // the preconditioner application captured as a CUDA graph (input gin,
+  // output gout); valid while the matrix buffers it reads stay in place
+  T *gin = nullptr, *gout = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void *gkey_col = nullptr, *gkey_val = nullptr;
+  int64_t gkernels = 0;
 };
 
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
@@ -127,6 +133,8 @@ struct DevView {
   double *phi;              // nodal volume fraction sum_p S V_p / h^d
   uint8_t *act;             // node active (mass > 0 and phi > phi_min)
   double *sh_nrm;           // 5 * n: 1/sum S, grad sum S (3), 1/sum S0 over active box nodes
+  // FP32 copies written in the mixed mode for the FP32 Jacobian (else null)
+  float *sh_Sf, *sh_dSf, *sh_S0f, *sh_nrmf, *recf;
   uint8_t *fixed;           // nb * nnodes, node-interleaved
   uint8_t *u_fixed;         // d * nnodes node-interleaved
   double *u_value;          // d * nnodes
@@ -146,6 +154,8 @@ struct Ctx {
   double tau_scale = 1.0;
   mpm_options opt{};
   cudaStream_t st = nullptr;
+  bool own_stream = false;   // created by the context (no stream was given)
+  bool capturing = false;    // a CUDA graph capture is in progress on st
   int64_t n = 0;
   int32_t n_surf = 0;
   double t = 0.0;
@@ -167,6 +177,7 @@ struct Ctx {
   double *phi = nullptr;
   uint8_t *act = nullptr;
   double *sh_nrm = nullptr;
+  float *sh_Sf = nullptr, *sh_dSf = nullptr, *sh_S0f = nullptr, *sh_nrmf = nullptr, *recf = nullptr;
   uint8_t *fixed = nullptr, *u_fixed = nullptr, *p_fixed = nullptr;
   double *u_value = nullptr, *p_value = nullptr, *trac = nullptr, *trac_raw = nullptr, *flux = nullptr;
   int has_flux = 0;
@@ -325,6 +336,43 @@ __device__ inline void basis_at(const DevView &v, int64_t q, const int off[3], i
     S *= sinv;
     for (int k = 0; k < D; ++k) Gn[k] = (Gn[k] - S * v.sh_nrm[(1 + k) * n + q]) * sinv;
     S0 *= v.sh_nrm[4 * n + q];
+  }
+}
+
+// The same basis from arrays of type R (FP64 or the FP32 copies).
+template <typename R>
+struct BasisArrays {
+  int64_t n;
+  const int32_t *cnt;
+  const uint8_t *act;
+  const R *S, *dS, *S0, *nrm;
+};
+
+template <int D, typename R>
+__device__ inline void basis_at_t(const BasisArrays<R> &B, int64_t q, const int off[3], int64_t a, R &S,
+                                  R &S0, R Gn[3]) {
+  const int64_t n = B.n;
+  R s[3] = {1, 1, 1}, ds[3] = {0, 0, 0}, s0[3] = {1, 1, 1};
+  for (int k = 0; k < D; ++k) {
+    s[k] = B.S[(k * MAXS + off[k]) * n + q];
+    ds[k] = B.dS[(k * MAXS + off[k]) * n + q];
+    s0[k] = B.S0[(k * MAXS + off[k]) * n + q];
+  }
+  S = s[0] * s[1] * s[2];
+  S0 = s0[0] * s0[1] * s0[2];
+  Gn[0] = ds[0] * s[1] * s[2];
+  Gn[1] = s[0] * ds[1] * s[2];
+  Gn[2] = s[0] * s[1] * ds[2];
+  if (B.cnt[q] & RENORM_BIT) {
+    if (!B.act[a]) {
+      S = S0 = 0;
+      Gn[0] = Gn[1] = Gn[2] = 0;
+      return;
+    }
+    const R sinv = B.nrm[0 * n + q];
+    S *= sinv;
+    for (int k = 0; k < D; ++k) Gn[k] = (Gn[k] - S * B.nrm[(1 + k) * n + q]) * sinv;
+    S0 *= B.nrm[4 * n + q];
   }
 }
 

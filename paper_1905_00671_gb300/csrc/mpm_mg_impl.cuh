@@ -713,6 +713,8 @@ int schur_alloc<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   int rc = mg_alloc(c, *S.mgA, d);
   if (!rc) rc = mg_alloc(c, *S.mgS, 1);
   if (rc) return rc;
+  if (cudaMalloc(&S.gin, sizeof(real) * nn * (d + 1)) || cudaMalloc(&S.gout, sizeof(real) * nn * (d + 1)))
+    return MPM_ERR_NO_MEMORY;
   if (cudaMalloc(&S.DAinv, sizeof(real) * nn * d * d) || cudaMalloc(&S.vu, sizeof(real) * nn * d) ||
       cudaMalloc(&S.wu, sizeof(real) * nn * d) || cudaMalloc(&S.zu, sizeof(real) * nn * d) ||
       cudaMalloc(&S.vp, sizeof(real) * nn) || cudaMalloc(&S.zp, sizeof(real) * nn))
@@ -733,7 +735,12 @@ void schur_free<MG_REAL>(LinSys<MG_REAL> &S) {
   cudaFree(S.zu);
   cudaFree(S.vp);
   cudaFree(S.zp);
-  S.Aval = S.Sval = S.DAinv = S.vu = S.wu = S.zu = S.vp = S.zp = nullptr;
+  cudaFree(S.gin);
+  cudaFree(S.gout);
+  if (S.gexec) cudaGraphExecDestroy(S.gexec);
+  S.gexec = nullptr;
+  S.gkey_col = S.gkey_val = nullptr;
+  S.Aval = S.Sval = S.DAinv = S.vu = S.wu = S.zu = S.vp = S.zp = S.gin = S.gout = nullptr;
   S.sub_cap = 0;
 }
 
@@ -772,9 +779,8 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
 }
 
 // z = M^{-1} v (block upper triangular, multigrid sub-solves)
-template <>
-void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
-  using namespace MG_NS;
+namespace MG_NS {
+void schur_apply_body(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
   const int64_t nn = c.g.nnodes;
   const int nbk = nblk(nn);
   if (c.d == 2) k_split<2><<<nbk, TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, S.vp);
@@ -791,4 +797,47 @@ void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL 
   else k_merge<3><<<nbk, TPB, 0, c.st>>>(nn, S.zu, S.zp, S.dscale, z);
   UPMPM_LAUNCH(c);
 }
+}  // namespace MG_NS
 
+// The application is a fixed sequence of ~100 small kernels on fixed buffers:
+// it is captured once into a CUDA graph (re-captured only when the matrix
+// buffers it reads move) and replayed, with the input and output copied in and
+// out of the graph's own buffers.
+template <>
+void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
+  using namespace MG_NS;
+  const int64_t N = c.N();
+  if (c.capturing) {  // nested inside another capture: plain launches
+    schur_apply_body(c, S, v, z);
+    return;
+  }
+  if (!S.gexec || S.gkey_col != c.col || S.gkey_val != S.val) {
+    if (S.gexec) cudaGraphExecDestroy(S.gexec);
+    S.gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    const int64_t before = c.launches;
+    bool ok = cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      c.capturing = true;
+      schur_apply_body(c, S, S.gin, S.gout);
+      c.capturing = false;
+      ok = cudaStreamEndCapture(c.st, &graph) == cudaSuccess && graph;
+    }
+    if (ok) ok = cudaGraphInstantiate(&S.gexec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    S.gkernels = c.launches - before;
+    c.launches = before;
+    if (!ok) {  // capture unavailable: launch directly
+      cudaGetLastError();
+      S.gexec = nullptr;
+      schur_apply_body(c, S, v, z);
+      return;
+    }
+    S.gkey_col = c.col;
+    S.gkey_val = S.val;
+  }
+  cudaMemcpyAsync(S.gin, v, sizeof(MG_REAL) * N, cudaMemcpyDeviceToDevice, c.st);
+  cudaGraphLaunch(S.gexec, c.st);
+  cudaMemcpyAsync(z, S.gout, sizeof(MG_REAL) * N, cudaMemcpyDeviceToDevice, c.st);
+  c.launches += S.gkernels;
+}

@@ -99,6 +99,7 @@ template <int D, bool GIMP>
 __global__ void k_shape(GridP g, int64_t n, const double *__restrict__ pf,
                         int32_t *__restrict__ first, int32_t *__restrict__ cnt_packed,
                         double *__restrict__ S, double *__restrict__ dS, double *__restrict__ S0,
+                        float *__restrict__ Sf, float *__restrict__ dSf, float *__restrict__ S0f,
                         int *err) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
@@ -169,6 +170,11 @@ __global__ void k_shape(GridP g, int64_t n, const double *__restrict__ pf,
       S[(k * MAXS + q) * n + p] = s[q];
       dS[(k * MAXS + q) * n + p] = ds[q];
       S0[(k * MAXS + q) * n + p] = s0[q];
+      if (Sf) {
+        Sf[(k * MAXS + q) * n + p] = (float)s[q];
+        dSf[(k * MAXS + q) * n + p] = (float)ds[q];
+        S0f[(k * MAXS + q) * n + p] = (float)s0[q];
+      }
     }
   }
   cnt_packed[p] = packed;
@@ -421,14 +427,14 @@ void run_shape(Ctx &c) {
   const int nbk = nblk(n);
   if (c.d == 2) {
     if (c.shape == MPM_SHAPE_GIMP)
-      k_shape<2, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.err);
+      k_shape<2, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
     else
-      k_shape<2, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.err);
+      k_shape<2, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
   } else {
     if (c.shape == MPM_SHAPE_GIMP)
-      k_shape<3, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.err);
+      k_shape<3, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
     else
-      k_shape<3, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.err);
+      k_shape<3, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
   }
   UPMPM_LAUNCH(c);
 }
