@@ -160,6 +160,22 @@ def spmv_bytes(nnodes, nnzb, nb):
     return nnzb * (nb * nb * 8 + 4) + (nnodes + 1) * 4 + 2 * nnodes * nb * 8
 
 
+def nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
 # --------------------------------------------------------------- our arm
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -203,9 +219,11 @@ def run_ours(args, rank, world, local_rank):
     nnzb = []
     for i in range(args.steps):
         flush.zero_()                       # evict L2 between timed steps (not timed)
+        nvtx_push("timed")                  # lets a profiler select the timed steps
         ev0[i].record(stream)
         st = sim.step(resident=True)
         ev1[i].record(stream)
+        nvtx_pop()
         newton += st["newton_iters"]
         krylov += st["krylov_total"]
         launches += st["kernel_launches"]

@@ -38,7 +38,7 @@ struct LinSys {
   T *V = nullptr, *Z = nullptr;                  // (m + 1) * N and m * N
   // Schur-complement multigrid preconditioner (mpm_mg.cu)
   MGHier<T> *mgA = nullptr, *mgS = nullptr;
-  T *Aval = nullptr, *Sval = nullptr, *DAinv = nullptr;
+  T *Aval = nullptr, *Sval = nullptr, *DAinv = nullptr, *B1c = nullptr;
   T *vu = nullptr, *wu = nullptr, *zu = nullptr, *vp = nullptr, *zp = nullptr;
   int64_t sub_cap = 0;
   // the preconditioner application captured as a CUDA graph (input gin,

@@ -150,32 +150,40 @@ __global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *
   vp[a] = v[a * (D + 1) + D] / dsc[a * (D + 1) + D];
 }
 
-// w_u = v_u - B1 z_p with the unscaled B1 (column D of the u rows of the
-// scaled J divided by the two scale factors)
+// Compact unscaled B1 (column D of the u rows of the unscaled J): D values
+// per block instead of the whole (D+1)^2 block.
 template <int D>
-__global__ void k_b1_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
-                            const int32_t *__restrict__ col, const real *__restrict__ Js,
-                            const real *__restrict__ dsc, const real *__restrict__ zp,
-                            const real *__restrict__ vu, real *__restrict__ wu) {
-  constexpr int NB = D + 1, LN = D == 2 ? 8 : 16;
+__global__ void k_extract_B1(int64_t nnzb, const real *__restrict__ J, real *__restrict__ B1) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  constexpr int NB = D + 1;
+  for (int k = 0; k < D; ++k) B1[e * D + k] = J[e * NB * NB + k * NB + D];
+}
+
+// w_u = v_u - B1 z_p with the compact unscaled B1
+template <int D>
+__global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const real *__restrict__ B1,
+                             const real *__restrict__ zp, const real *__restrict__ vu,
+                             real *__restrict__ wu) {
+  constexpr int LN = D == 2 ? 8 : 16;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = t / LN;
   const int lane = (int)(t % LN);
   const bool valid = a < nnodes;
   real acc[D];
-  for (int k = 0; k < D; ++k) acc[k] = 0.0;
+  for (int k = 0; k < D; ++k) acc[k] = 0;
   if (valid) {
     const int e1 = row_ptr[a + 1];
     for (int e = row_ptr[a] + lane; e < e1; e += LN) {
-      const int64_t b = col[e];
-      const real z = zp[b] / dsc[b * NB + D];
-      for (int k = 0; k < D; ++k) acc[k] = fma(Js[(int64_t)e * NB * NB + k * NB + D], z, acc[k]);
+      const real z = zp[col[e]];
+      for (int k = 0; k < D; ++k) acc[k] = fma(B1[(int64_t)e * D + k], z, acc[k]);
     }
   }
   for (int o = LN / 2; o > 0; o >>= 1)
     for (int k = 0; k < D; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
   if (!valid || lane != 0) return;
-  for (int k = 0; k < D; ++k) wu[a * D + k] = vu[a * D + k] - acc[k] / dsc[a * NB + k];
+  for (int k = 0; k < D; ++k) wu[a * D + k] = vu[a * D + k] - acc[k];
 }
 
 template <int D>
@@ -354,25 +362,49 @@ __global__ void k_dense_fill(LevelDev L, real *__restrict__ Ad) {
 __global__ void k_dense_invert(int n, real *__restrict__ Ad, real *__restrict__ Ai) {
   __shared__ int piv;
   __shared__ real pval;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ai[t] = (t / n == t % n) ? 1.0 : 0.0;
-  real amax = 0.0;
-  for (int t = 0; t < n * n; ++t) amax = fmax(amax, fabs(Ad[t]));
+  __shared__ real red_v[32];
+  __shared__ int red_i[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ai[t] = (t / n == t % n) ? real(1) : real(0);
+  // largest magnitude (parallel), for the singular-pivot threshold
+  real amax = 0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) amax = fmax(amax, fabs(Ad[t]));
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if (lane == 0) red_v[wid] = amax;
+  __syncthreads();
+  amax = 0;
+  for (int i = 0; i < nw; ++i) amax = fmax(amax, red_v[i]);
+  __syncthreads();
   for (int k = 0; k < n; ++k) {
+    // pivot: largest |Ad[i][k]| for i >= k (warp-parallel argmax)
+    real best = -1;
+    int bi = k;
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+      const real v = fabs(Ad[i * n + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const real ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { red_v[wid] = best; red_i[wid] = bi; }
     __syncthreads();
     if (threadIdx.x == 0) {
+      real b = -1;
       int p = k;
-      real best = fabs(Ad[k * n + k]);
-      for (int i = k + 1; i < n; ++i)
-        if (fabs(Ad[i * n + k]) > best) { best = fabs(Ad[i * n + k]); p = i; }
-      piv = best > 1e-14 * amax ? p : -1;
-      pval = piv >= 0 ? Ad[p * n + k] : 0.0;
+      for (int i = 0; i < nw; ++i)
+        if (red_v[i] > b || (red_v[i] == b && red_i[i] < p)) { b = red_v[i]; p = red_i[i]; }
+      piv = b > real(1e-14) * amax ? p : -1;
+      pval = piv >= 0 ? Ad[p * n + k] : real(0);
     }
     __syncthreads();
     if (piv < 0) {
       for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        Ad[k * n + j] = 0.0;
-        Ai[k * n + j] = 0.0;
+        Ad[k * n + j] = 0;
+        Ai[k * n + j] = 0;
       }
+      __syncthreads();
       continue;
     }
     if (piv != k)
@@ -381,7 +413,7 @@ __global__ void k_dense_invert(int n, real *__restrict__ Ad, real *__restrict__ 
         t1 = Ai[k * n + j]; Ai[k * n + j] = Ai[piv * n + j]; Ai[piv * n + j] = t1;
       }
     __syncthreads();
-    const real inv = 1.0 / pval;
+    const real inv = real(1) / pval;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       Ad[k * n + j] *= inv;
       Ai[k * n + j] *= inv;
@@ -391,13 +423,14 @@ __global__ void k_dense_invert(int n, real *__restrict__ Ad, real *__restrict__ 
       const int i = t / n, j = t % n;
       if (i == k) continue;
       const real f = Ad[i * n + k];
-      if (f == 0.0) continue;
+      if (f == real(0)) continue;
       if (j != k) Ad[i * n + j] -= f * Ad[k * n + j];
       Ai[i * n + j] -= f * Ai[k * n + j];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x)
-      if (i != k) Ad[i * n + k] = 0.0;
+      if (i != k) Ad[i * n + k] = 0;
+    __syncthreads();
   }
 }
 
@@ -729,6 +762,8 @@ void schur_free<MG_REAL>(LinSys<MG_REAL> &S) {
   if (S.mgS) { mg_free(*S.mgS); delete S.mgS; S.mgS = nullptr; }
   cudaFree(S.Aval);
   cudaFree(S.Sval);
+  cudaFree(S.B1c);
+  S.B1c = nullptr;
   cudaFree(S.DAinv);
   cudaFree(S.vu);
   cudaFree(S.wu);
@@ -754,9 +789,11 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   if (nnzb > S.sub_cap) {
     cudaFree(S.Aval);
     cudaFree(S.Sval);
-    S.Aval = S.Sval = nullptr;
+    cudaFree(S.B1c);
+    S.Aval = S.Sval = S.B1c = nullptr;
     const int64_t cap = c.nnzb_cap;
-    if (cudaMalloc(&S.Aval, sizeof(real) * cap * d * d) || cudaMalloc(&S.Sval, sizeof(real) * cap)) {
+    if (cudaMalloc(&S.Aval, sizeof(real) * cap * d * d) || cudaMalloc(&S.Sval, sizeof(real) * cap) ||
+        cudaMalloc(&S.B1c, sizeof(real) * cap * d)) {
       S.sub_cap = 0;
       c.last_error = "device allocation of the block preconditioner failed";
       return MPM_ERR_NO_MEMORY;
@@ -765,10 +802,12 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   }
   if (d == 2) {
     k_extract_A<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
+    k_extract_B1<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B1c);
     k_diag_inv_A<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.DAinv);
     k_schur_rows<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.DAinv, S.Sval);
   } else {
     k_extract_A<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
+    k_extract_B1<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B1c);
     k_diag_inv_A<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.DAinv);
     k_schur_rows<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.DAinv, S.Sval);
   }
@@ -788,9 +827,9 @@ void schur_apply_body(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) 
   UPMPM_LAUNCH(c);
   mg_vcycle(c, *S.mgS, S.vp, S.zp);
   if (c.d == 2)
-    k_b1_update<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.zp, S.vu, S.wu);
+    k_b1c_update<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, S.zp, S.vu, S.wu);
   else
-    k_b1_update<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.zp, S.vu, S.wu);
+    k_b1c_update<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, S.zp, S.vu, S.wu);
   UPMPM_LAUNCH(c);
   mg_vcycle(c, *S.mgA, S.wu, S.zu);
   if (c.d == 2) k_merge<2><<<nbk, TPB, 0, c.st>>>(nn, S.zu, S.zp, S.dscale, z);
