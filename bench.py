@@ -130,9 +130,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCE = {"k_bsr_spmv": "mpm_solver.cu", "k_jacobian": "mpm_assemble.cu"}
+
+
+def kernel_source_hash(kernel):
+    """Hash of the sources a kernel is built from (its file and the shared
+    header): a committed ncu figure counts only for the source it was taken on."""
     h = hashlib.sha256()
-    for f in ("mpm_solver.cu", "mpm_internal.cuh"):
+    for f in (KERNEL_SOURCE[kernel], "mpm_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1905_00671_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -146,12 +151,22 @@ def ncu_traffic(kernel):
         lines = open(path).read().splitlines()
     except OSError:
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel)
     for ln in lines:
         parts = ln.split()
         if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == src:
             return float(parts[3])
     return None
+
+
+# Algorithmic FP64 flops of the Jacobian assembly (Eqs. jacobian-system-
+# stabilized-ppp, newmark-linearization as evaluated per point): F per
+# (point, a, b) term and G per (point, node) term, counted by hand from the
+# formula with the per-(point, node) vectors (g_a = F^-T grad S_a, tau g_a,
+# g_a.w, g_a.grad v, S_a - S0_a) formed once: {(dim, dynamic): (F, G)}.
+JAC_FLOPS = {(2, False): (83, 25), (2, True): (105, 33), (3, False): (158, 53), (3, True): (202, 71)}
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 
 
 def spmv_bytes(nnodes, nnzb, nb):
@@ -217,6 +232,7 @@ def run_ours(args, rank, world, local_rank):
     prof_ms = {k: 0.0 for k in mpm.PROF}
     prof_n = {k: 0 for k in mpm.PROF}
     nnzb = []
+    terms = []
     for i in range(args.steps):
         flush.zero_()                       # evict L2 between timed steps (not timed)
         nvtx_push("timed")                  # lets a profiler select the timed steps
@@ -228,6 +244,7 @@ def run_ours(args, rank, world, local_rank):
         krylov += st["krylov_total"]
         launches += st["kernel_launches"]
         nnzb.append(st["nnzb"])
+        terms.append((st["jac_terms"], st["jac_point_nodes"]))
         for k in mpm.PROF:
             prof_ms[k] += st["prof_ms"][k]
             prof_n[k] += st["prof_launches"][k]
@@ -247,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
     mixed = None
     if not args.no_mixed:
         sim_m = mpm.Simulation(w, stream=stream.cuda_stream, precision=mpm.MPM_MIXED,
-                               newton_max=60)
+                               newton_max=60, profile=prof_bits)
         sim_r = mpm.Simulation(w, stream=stream.cuda_stream)   # FP64 twin for the error
         for _ in range(args.warmup):
             sim_m.step(resident=True)
@@ -255,13 +272,18 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         ms = 0.0
         newton_m = krylov_m = 0
+        prof_m = {k: 0.0 for k in mpm.PROF}
         for i in range(args.steps):
             flush.zero_()
+            nvtx_push("timed_mixed")
             ev0[i].record(stream)
             st = sim_m.step(resident=True)
             ev1[i].record(stream)
+            nvtx_pop()
             newton_m += st["newton_iters"]
             krylov_m += st["krylov_total"]
+            for k in mpm.PROF:
+                prof_m[k] += st["prof_ms"][k]
             sim_r.step(resident=True)
             torch.cuda.synchronize()
             ms += ev0[i].elapsed_time(ev1[i])
@@ -276,6 +298,7 @@ def run_ours(args, rank, world, local_rank):
                  "ms_per_step": ms / args.steps, "dtype": "f32 solve / f64 Newton residual",
                  "newton_iters_per_step": newton_m / args.steps,
                  "krylov_iters_per_step": krylov_m / args.steps,
+                 "class_ms_per_step": {k: round(v / args.steps, 3) for k, v in prof_m.items() if v > 0},
                  "rel_error_vs_fp64": errs}
         sim_m.close()
         sim_r.close()
@@ -318,11 +341,29 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(n * (2 * d + 1) * 8),
                "steps_per_s": world * args.steps / e2e_total}
 
-    # ---- roofline of the dominant kernel class (live CUDA-event times)
+    # ---- roofline of the dominant kernel (the Jacobian assembly: the largest
+    # single kernel of the step, bound by GB300's FP64 pipe) with the SpMV
+    # beside it (HBM and FP64 fractions); live CUDA-event times on the
+    # library's stream
     peaks, peak_src = measured_peaks()
     shares = {k: prof_ms[k] for k in prof_ms if prof_n[k] > 0}
     dominant = max(shares, key=shares.get) if shares else None
     roofline = None
+    if prof_n.get("jacobian", 0) > 0:
+        F, G = JAC_FLOPS[(w.dim, w.dynamic)]
+        flops = sum(F * t + G * pn for t, pn in terms) / len(terms)   # per assembly
+        avg_ms = prof_ms["jacobian"] / prof_n["jacobian"]
+        ach = flops / (avg_ms * 1e-3) / 1e12
+        roofline = {"kernel": "k_jacobian", "bound": "alu", "achieved": round(ach, 4),
+                    "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+                    "frac": round(ach / FP64_PEAK_TFLOPS, 4),
+                    "traffic": ncu_traffic("k_jacobian"),
+                    "peak_source": "FP64 from unit counts and clocks (152 SMs x 2 FMA/clk x 2070 MHz)",
+                    "algorithmic_flops": int(flops), "jac_terms": int(sum(t for t, _ in terms) / len(terms)),
+                    "avg_launch_us": round(avg_ms * 1e3, 3),
+                    "dominant_class": dominant,
+                    "class_ms_per_step": {k: round(v / args.steps, 3) for k, v in shares.items()},
+                    "class_launches_per_step": {k: prof_n[k] / args.steps for k in shares}}
     if "spmv" in shares and prof_n["spmv"] > 0:
         nb = w.dim + 1
         avg_nnzb = sum(nnzb) / len(nnzb)
@@ -330,13 +371,16 @@ def run_ours(args, rank, world, local_rank):
         avg_ms = prof_ms["spmv"] / prof_n["spmv"]
         ach = bytes_launch / (avg_ms * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])
-        roofline = {"kernel": "k_bsr_spmv", "bound": "hbm", "achieved": round(ach, 1),
-                    "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                    "traffic": ncu_traffic("k_bsr_spmv"), "algorithmic_bytes": int(bytes_launch),
-                    "avg_launch_us": round(avg_ms * 1e3, 3), "peak_source": peak_src + " hbm_gbs",
-                    "dominant_class": dominant,
-                    "class_ms_per_step": {k: round(v / args.steps, 3) for k, v in shares.items()},
-                    "class_launches_per_step": {k: prof_n[k] / args.steps for k in shares}}
+        fl = 2 * avg_nnzb * nb * nb / (avg_ms * 1e-3) / 1e12
+        spmv = {"kernel": "k_bsr_spmv", "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic("k_bsr_spmv"),
+                "algorithmic_bytes": int(bytes_launch), "avg_launch_us": round(avg_ms * 1e3, 3),
+                "peak_source": peak_src + " hbm_gbs",
+                "fp64_tflops": round(fl, 4), "fp64_frac": round(fl / FP64_PEAK_TFLOPS, 4)}
+        if roofline is None:
+            roofline = spmv
+        else:
+            roofline["spmv"] = spmv
 
     value = world * w.n * args.steps / (total_ms * 1e-3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

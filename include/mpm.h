@@ -193,6 +193,9 @@ typedef struct {
   int64_t kernel_launches;                 /* kernels launched by the last step */
   double prof_ms[MPM_PROF_COUNT];          /* device time of the profiled classes, last step */
   int64_t prof_launches[MPM_PROF_COUNT];   /* launches of the profiled classes, last step */
+  int64_t jac_terms;        /* (point, a, b) terms of one Jacobian assembly of the last step:
+                               sum over points of n_p^2, n_p = active nodes of the point's support */
+  int64_t jac_point_nodes;  /* sum over points of n_p */
 } mpm_stats;
 
 /* Fills *o with the defaults: GIMP, quasi-static, beta 0.3025, gamma 0.6,

@@ -242,6 +242,7 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   if (rc) return rc;
   run_initial_guess(c);
   run_renorm(c);
+  run_count_terms(c);
   rc = read_dev_err(c);
   if (rc) return rc;
   c.prepared = true;
@@ -337,8 +338,11 @@ int do_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   rc = newton(c);
   if (rc) return rc;
   run_g2p(c);
-  rc = read_dev_err(c);
+  cudaMemcpyAsync(c.h_terms, c.terms, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.st);
+  rc = read_dev_err(c);  // synchronises the stream
   if (rc) return rc;
+  c.stats.jac_terms = (int64_t)c.h_terms[0];
+  c.stats.jac_point_nodes = (int64_t)c.h_terms[1];
   prof_collect(c);
   c.prepared = false;
   c.t += dt;
@@ -363,11 +367,12 @@ void free_all(Ctx &c) {
                   c.sh_S0, c.m, c.rec, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
-                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp};
+                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp, c.terms};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.h_err) cudaFreeHost(c.h_err);
   if (c.h_scalar) cudaFreeHost(c.h_scalar);
+  if (c.h_terms) cudaFreeHost(c.h_terms);
   if (c.own_stream && c.st) cudaStreamDestroy(c.st);
   c.st = nullptr;
 }
@@ -555,6 +560,10 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   if (!rc && cudaHostAlloc((void **)&c.h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess)
     rc = MPM_ERR_NO_MEMORY;
   if (!rc && cudaHostAlloc((void **)&c.h_scalar, 8 * sizeof(double), cudaHostAllocDefault) != cudaSuccess)
+    rc = MPM_ERR_NO_MEMORY;
+  if (!rc && (cudaMalloc((void **)&c.terms, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+              cudaHostAlloc((void **)&c.h_terms, 2 * sizeof(unsigned long long), cudaHostAllocDefault) !=
+                  cudaSuccess))
     rc = MPM_ERR_NO_MEMORY;
   if (rc) {
     free_all(c);

@@ -28,7 +28,7 @@ namespace {
 constexpr int TPB = 256;
 inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
 
-constexpr int MASKW = 6;  // 64-bit words for 7^3 = 343 offsets in [-3, 3]^3
+constexpr int MASKW = PATTERN_MASK_WORDS;  // 7^3 = 343 offsets in [-3, 3]^3
 
 // Support box of point q along each axis, and whether node coordinate ac lies in
 // it (off = slot of that node).
@@ -151,6 +151,38 @@ __global__ void k_initial_guess(GridP g, double phi_min, DevView v, double *__re
 
 // Points whose support box holds an inactive node get their basis
 // renormalised over the active box nodes (see basis_at).
+// Work count of the Jacobian assembly: n_p active nodes in point p's support
+// give n_p^2 (point, a, b) terms and n_p (point, node) terms.
+template <int D>
+__global__ void k_count_terms(GridP g, DevView v, unsigned long long *__restrict__ terms) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = v.n;
+  unsigned long long np = 0;
+  if (p < n) {
+    const int packed = v.sh_cnt[p] & ~RENORM_BIT;
+    int f[3], cn[3];
+    for (int k = 0; k < 3; ++k) {
+      f[k] = v.sh_first[k * n + p];
+      cn[k] = unpack_cnt(packed, k);
+    }
+    for (int s2 = 0; s2 < cn[2]; ++s2)
+      for (int s1 = 0; s1 < cn[1]; ++s1)
+        for (int s0 = 0; s0 < cn[0]; ++s0) {
+          const int nc3[3] = {f[0] + s0, f[1] + s1, f[2] + s2};
+          np += v.act[node_index(g, nc3)] ? 1 : 0;
+        }
+  }
+  unsigned long long sq = np * np;
+  for (int o = 16; o > 0; o >>= 1) {
+    np += __shfl_xor_sync(0xffffffffu, np, o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&terms[0], sq);
+    atomicAdd(&terms[1], np);
+  }
+}
+
 template <int D>
 __global__ void k_renorm(GridP g, DevView v) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -393,15 +425,35 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
 // ---------------------------------------------------------------- Jacobian
 // Block values are written in precision T and computed in precision R: FP64
 // from the FP64 records, or FP32 from their FP32 copies in the mixed mode.
+// One thread per block (a, b), mapped offset-major: thread t takes coupling
+// offset slot s = t / nnodes (b - a in [-3, 3]^d) of row a = t % nnodes, so the
+// 32 lanes of a warp hold the same offset in 32 consecutive rows and walk the
+// same number of candidate cells; a slot absent from the row's pattern exits.
+template <int D>
+__device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
+                                        int64_t a, int s) {
+  const uint64_t *mk = mask + a * MASKW;
+  const int w = s >> 6;
+  const uint64_t word = mk[w];
+  if (!((word >> (s & 63)) & 1ull)) return -1;
+  int before = __popcll(word & ((1ull << (s & 63)) - 1ull));
+  for (int i = 0; i < w; ++i) before += __popcll(mk[i]);
+  return (int64_t)row_ptr[a] + before;
+}
+
 template <int D, bool GIMP, bool DYN, typename T, typename R>
 __global__ void k_jacobian(GridP g, StepP s, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
-                           const int32_t *__restrict__ row_of, const int32_t *__restrict__ col,
-                           int64_t nnzb, T *__restrict__ val, int apply_bc) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (e >= nnzb) return;
+                           const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
+                           const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  constexpr int NSLOT = D == 2 ? 49 : 343;
+  if (t >= NSLOT * g.nnodes) return;
+  const int64_t a = t % g.nnodes;
+  const int64_t e = block_of_slot<D>(mask, row_ptr, a, (int)(t / g.nnodes));
+  if (e < 0) return;
   constexpr int NB = D + 1;
   const int64_t n = v.n;
-  const int64_t a = row_of[e], bn = col[e];
+  const int64_t bn = col[e];
   int ac[3], bc[3];
   node_coords(g, a, ac);
   node_coords(g, bn, bc);
@@ -532,6 +584,14 @@ void run_initial_guess(Ctx &c) {
   UPMPM_LAUNCH(c);
 }
 
+void run_count_terms(Ctx &c) {
+  const DevView v = c.view();
+  cudaMemsetAsync(c.terms, 0, 2 * sizeof(unsigned long long), c.st);
+  if (c.d == 2) k_count_terms<2><<<nblk(c.n), TPB, 0, c.st>>>(c.g, v, c.terms);
+  else k_count_terms<3><<<nblk(c.n), TPB, 0, c.st>>>(c.g, v, c.terms);
+  UPMPM_LAUNCH(c);
+}
+
 void run_renorm(Ctx &c) {
   const DevView v = c.view();
   if (c.d == 2) k_renorm<2><<<nblk(c.n), TPB, 0, c.st>>>(c.g, v);
@@ -577,7 +637,7 @@ template <typename T>
 void run_jacobian(Ctx &c, T *val, int apply_bc) {
   prof_begin(c, MPM_PROF_JACOBIAN);
   const DevView v = c.view();
-  const int nbk = nblk(c.nnzb, 128);
+  const int nbk = nblk((c.d == 2 ? 49 : 343) * c.g.nnodes, 128);
   const bool gimp = c.shape == MPM_SHAPE_GIMP;
   // FP32 values are computed in FP32 from the FP32 copies; FP64 in FP64
   using R = T;
@@ -594,7 +654,7 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
     BA.nrm = (const R *)c.sh_nrmf; rec = (const R *)c.recf;
   }
 #define JAC(D, G, Y) \
-  k_jacobian<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_of, c.col, c.nnzb, val, apply_bc)
+  k_jacobian<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask, c.row_ptr, c.col, val, apply_bc)
   if (c.d == 2) {
     if (gimp) { if (c.dyn) JAC(2, true, true); else JAC(2, true, false); }
     else { if (c.dyn) JAC(2, false, true); else JAC(2, false, false); }

@@ -39,15 +39,24 @@ struct LinSys {
   // Schur-complement multigrid preconditioner (mpm_mg.cu)
   MGHier<T> *mgA = nullptr, *mgS = nullptr;
   T *Aval = nullptr, *Sval = nullptr, *DAinv = nullptr, *B1c = nullptr;
-  T *vu = nullptr, *wu = nullptr, *zu = nullptr, *vp = nullptr, *zp = nullptr;
+  T *W = nullptr;      // B2_ac diag(A)_c^{-1} per block (d values), Schur set-up
+  T *B1rs = nullptr;   // per node: sum over its row of the B1 blocks (d values)
+  T *vu = nullptr;
   int64_t sub_cap = 0;
-  // the preconditioner application captured as a CUDA graph (input gin,
-  // output gout); valid while the matrix buffers it reads stay in place
-  T *gin = nullptr, *gout = nullptr;
+  // The multigrid part of the preconditioner application (both V-cycles and
+  // the B1 update between them) captured as a CUDA graph; valid while the
+  // matrix buffers it reads stay in place.  The graph reads the S-cycle's
+  // level-0 rhs and first iterate from g_bs0 / g_xs0 and leaves the results
+  // in g_zp / g_zu (the hierarchies' vector buffers at capture time).
   cudaGraphExec_t gexec = nullptr;
+  T *g_xs0 = nullptr, *g_zp = nullptr, *g_zu = nullptr;
   const void *gkey_col = nullptr, *gkey_val = nullptr;
   int64_t gkernels = 0;
 };
+
+// 64-bit words of the per-node coupling mask of the block sparsity: bit
+// (o0 + 3) + 7 (o1 + 3) + 49 (o2 + 3) is set iff node a + o couples with a.
+constexpr int PATTERN_MASK_WORDS = 6;
 
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
 
@@ -185,6 +194,8 @@ struct Ctx {
   int *err = nullptr;
   int *h_err = nullptr;                  // pinned
   double *h_scalar = nullptr;            // pinned scratch for scalars read by the host
+  unsigned long long *terms = nullptr;   // device: Jacobian term counts (n_p^2, n_p sums)
+  unsigned long long *h_terms = nullptr; // pinned copy
 
   // sparsity + matrix
   int32_t *row_nnz = nullptr, *row_ptr = nullptr, *row_of = nullptr, *col = nullptr;
@@ -228,6 +239,7 @@ void run_g2p(Ctx &c);
 int run_pattern(Ctx &c);                          // builds row_ptr / col / row_of
 void run_initial_guess(Ctx &c);   // also sets the active flags
 void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
+void run_count_terms(Ctx &c);     // Jacobian term counts into c.terms (device)
 void run_point_eval(Ctx &c, const double *X);
 void run_residual(Ctx &c, const double *X, double *R, int apply_bc);
 template <typename T>

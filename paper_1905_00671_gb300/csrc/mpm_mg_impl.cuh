@@ -70,12 +70,38 @@ __global__ void k_extract_A(int64_t nnzb, const real *__restrict__ J, real *__re
     for (int k = 0; k < D; ++k) A[e * D * D + i * D + k] = J[e * NB * NB + i * NB + k];
 }
 
+// Block of row a coupling with node a + o, from the per-node coupling mask of
+// the block sparsity (columns of a row are in mask-bit order); -1 if absent.
+template <int D>
+__device__ inline int mask_block(const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
+                                 int a, int o0, int o1, int o2) {
+  if (o0 < -3 || o0 > 3 || o1 < -3 || o1 > 3 || (D == 3 && (o2 < -3 || o2 > 3))) return -1;
+  const int sl = (o0 + 3) + 7 * (o1 + 3) + (D == 3 ? 49 * (o2 + 3) : 0);
+  const uint64_t *mk = mask + (int64_t)a * PATTERN_MASK_WORDS;
+  const int w = sl >> 6;
+  const uint64_t word = mk[w];
+  if (!((word >> (sl & 63)) & 1ull)) return -1;
+  int before = __popcll(word & ((1ull << (sl & 63)) - 1ull));
+  for (int i = 0; i < w; ++i) before += __popcll(mk[i]);
+  return row_ptr[a] + before;
+}
+
+__device__ inline void grid_xyz(const int nn0, const int nn1, int a, int c[3]) {
+  const int r = a / nn0;
+  c[0] = a - r * nn0;
+  c[1] = r % nn1;
+  c[2] = r / nn1;
+}
+
+// diag(A)_a^{-1} and the row sum of the B1 blocks of row a
 template <int D>
 __global__ void k_diag_inv_A(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                              const int32_t *__restrict__ col, const real *__restrict__ A,
-                             real *__restrict__ DAinv) {
+                             const real *__restrict__ J, real *__restrict__ DAinv,
+                             real *__restrict__ B1rs) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
+  constexpr int NB = D + 1;
   const int e = find_col(col, row_ptr[a], row_ptr[a + 1], (int)a);
   real M[D][D], Inv[D][D];
   for (int i = 0; i < D; ++i)
@@ -83,71 +109,96 @@ __global__ void k_diag_inv_A(int64_t nnodes, const int32_t *__restrict__ row_ptr
   invert_small<D>(M, Inv);
   for (int i = 0; i < D; ++i)
     for (int k = 0; k < D; ++k) DAinv[a * D * D + i * D + k] = Inv[i][k];
+  real rs[D];
+  for (int k = 0; k < D; ++k) rs[k] = 0.0;
+  for (int eb = row_ptr[a]; eb < row_ptr[a + 1]; ++eb)
+    for (int k = 0; k < D; ++k) rs[k] += J[(int64_t)eb * NB * NB + k * NB + D];
+  for (int k = 0; k < D; ++k) B1rs[a * D + k] = rs[k];
 }
 
-// S row a on J's sparsity: S_ab = C_ab - sum_c B2_ac DAinv_c B1_cb; the part of
-// the product falling outside the sparsity is added to S_aa.  LN lanes per row.
+// W_ac = B2_ac diag(A)_c^{-1} (a 1 x D row per block)
 template <int D>
-__global__ void k_schur_rows(int64_t nnodes, const int32_t *__restrict__ row_ptr,
-                             const int32_t *__restrict__ col, const real *__restrict__ J,
-                             const real *__restrict__ DAinv, real *__restrict__ S) {
-  constexpr int NB = D + 1, LN = D == 2 ? 8 : 16;
+__global__ void k_schur_w(int64_t nnzb, const int32_t *__restrict__ col, const real *__restrict__ J,
+                          const real *__restrict__ DAinv, real *__restrict__ W) {
+  const int64_t ec = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ec >= nnzb) return;
+  constexpr int NB = D + 1;
+  const int64_t c = col[ec];
+  for (int k = 0; k < D; ++k) {
+    real w = 0.0;
+    for (int i = 0; i < D; ++i) w += J[ec * NB * NB + D * NB + i] * DAinv[c * D * D + i * D + k];
+    W[ec * D + k] = w;
+  }
+}
+
+// S_ab = C_ab - sum_c W_ac B1_cb on J's sparsity, one thread per block (a, b),
+// offset-major (thread t: offset slot t / nnodes of row t % nnodes) so that a
+// warp's lanes share the offset; (c, b) is found from c's coupling mask.
+template <int D>
+__global__ void k_schur_rows(int nn0, int nn1, int64_t nnodes, const uint64_t *__restrict__ mask,
+                             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+                             const real *__restrict__ J, const real *__restrict__ W,
+                             real *__restrict__ S) {
+  constexpr int NB = D + 1, NSL = D == 2 ? 49 : 343;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t a = t / LN;
-  const int lane = (int)(t % LN);
-  const bool valid = a < nnodes;
+  if (t >= NSL * nnodes) return;
+  const int a = (int)(t % nnodes);
+  const int sl = (int)(t / nnodes);
+  const int o0 = sl % 7 - 3, o1 = (sl / 7) % 7 - 3, o2 = D == 3 ? sl / 49 - 3 : 0;
+  const int eb = mask_block<D>(mask, row_ptr, a, o0, o1, o2);
+  if (eb < 0) return;
+  int ac[3];
+  grid_xyz(nn0, nn1, a, ac);
+  const int b0 = ac[0] + o0, b1 = ac[1] + o1, b2 = ac[2] + o2;
+  real prod = 0.0;
+  const int r1 = row_ptr[a + 1];
+  for (int ec = row_ptr[a]; ec < r1; ++ec) {
+    const int cn = col[ec];
+    int cc[3];
+    grid_xyz(nn0, nn1, cn, cc);
+    const int e_cb = mask_block<D>(mask, row_ptr, cn, b0 - cc[0], b1 - cc[1], b2 - cc[2]);
+    if (e_cb < 0) continue;
+    for (int k = 0; k < D; ++k) prod += W[(int64_t)ec * D + k] * J[(int64_t)e_cb * NB * NB + k * NB + D];
+  }
+  S[eb] = J[(int64_t)eb * NB * NB + D * NB + D] - prod;
+}
+
+// The part of row a's full product sum_c W_ac (sum_b B1_cb) that fell outside
+// the sparsity is added to S_aa.
+template <int D>
+__global__ void k_schur_lump(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const real *__restrict__ J,
+                             const real *__restrict__ W, const real *__restrict__ B1rs,
+                             real *__restrict__ S) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nnodes) return;
+  constexpr int NB = D + 1;
   real total = 0.0, kept = 0.0;
-  int mydiag = -1;
-  if (valid) {
-    const int r0 = row_ptr[a], r1 = row_ptr[a + 1];
-    // full product row sum: sum_c (B2_ac DAinv_c) . (sum_b B1_cb)
-    for (int ec = r0 + lane; ec < r1; ec += LN) {
-      const int c = col[ec];
-      real rs[D];
-      for (int k = 0; k < D; ++k) rs[k] = 0.0;
-      for (int eb = row_ptr[c]; eb < row_ptr[c + 1]; ++eb)
-        for (int k = 0; k < D; ++k) rs[k] += J[(int64_t)eb * NB * NB + k * NB + D];
-      for (int k = 0; k < D; ++k) {
-        real w = 0.0;
-        for (int i = 0; i < D; ++i) w += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
-        total += w * rs[k];
-      }
-    }
-    for (int eb = r0 + lane; eb < r1; eb += LN) {
-      const int b = col[eb];
-      if (b == a) mydiag = eb;
-      real prod = 0.0;
-      for (int ec = r0; ec < r1; ++ec) {
-        const int c = col[ec];
-        const int e_cb = find_col(col, row_ptr[c], row_ptr[c + 1], b);
-        if (e_cb < 0) continue;
-        for (int k = 0; k < D; ++k) {
-          real w = 0.0;
-          for (int i = 0; i < D; ++i) w += J[(int64_t)ec * NB * NB + D * NB + i] * DAinv[(int64_t)c * D * D + i * D + k];
-          prod += w * J[(int64_t)e_cb * NB * NB + k * NB + D];
-        }
-      }
-      kept += prod;
-      S[eb] = J[(int64_t)eb * NB * NB + D * NB + D] - prod;
-    }
+  int diag = -1;
+  for (int e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
+    const int cn = col[e];
+    if (cn == a) diag = e;
+    for (int k = 0; k < D; ++k) total += W[(int64_t)e * D + k] * B1rs[(int64_t)cn * D + k];
+    kept += J[(int64_t)e * NB * NB + D * NB + D] - S[e];
   }
-  for (int o = LN / 2; o > 0; o >>= 1) {
-    total += __shfl_xor_sync(0xffffffffu, total, o);
-    kept += __shfl_xor_sync(0xffffffffu, kept, o);
-  }
-  if (mydiag >= 0) S[mydiag] -= (total - kept);
+  if (diag >= 0) S[diag] -= (total - kept);
 }
 
 // ------------------------------------------------------------ Schur apply
 // The Krylov solver works on D J D (D = dsc); the blocks below are the
 // unscaled physical ones, so the preconditioner of D J D is D^-1 M^-1 D^-1.
+// v_u, v_p of the unscaled system; v_p is the S-cycle's level-0 rhs, whose
+// first smoothing sweep from zero (x = omega Dinv b, pointwise) is done here.
 template <int D>
 __global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsc,
-                        real *__restrict__ vu, real *__restrict__ vp) {
+                        real *__restrict__ vu, real *__restrict__ bs0, real *__restrict__ xs0,
+                        const real *__restrict__ dinvs0, real omega) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
   for (int k = 0; k < D; ++k) vu[a * D + k] = v[a * (D + 1) + k] / dsc[a * (D + 1) + k];
-  vp[a] = v[a * (D + 1) + D] / dsc[a * (D + 1) + D];
+  const real vp = v[a * (D + 1) + D] / dsc[a * (D + 1) + D];
+  bs0[a] = vp;
+  xs0[a] = omega * (dinvs0[a] * vp);
 }
 
 // Compact unscaled B1 (column D of the u rows of the unscaled J): D values
@@ -160,12 +211,14 @@ __global__ void k_extract_B1(int64_t nnzb, const real *__restrict__ J, real *__r
   for (int k = 0; k < D; ++k) B1[e * D + k] = J[e * NB * NB + k * NB + D];
 }
 
-// w_u = v_u - B1 z_p with the compact unscaled B1
+// w_u = v_u - B1 z_p with the compact unscaled B1: the A-cycle's level-0 rhs,
+// with its first smoothing sweep from zero (x = omega Dinv w_u).
 template <int D>
 __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                              const int32_t *__restrict__ col, const real *__restrict__ B1,
                              const real *__restrict__ zp, const real *__restrict__ vu,
-                             real *__restrict__ wu) {
+                             real *__restrict__ ba0, real *__restrict__ xa0,
+                             const real *__restrict__ dinva0, real omega) {
   constexpr int LN = D == 2 ? 8 : 16;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = t / LN;
@@ -183,7 +236,16 @@ __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr
   for (int o = LN / 2; o > 0; o >>= 1)
     for (int k = 0; k < D; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
   if (!valid || lane != 0) return;
-  for (int k = 0; k < D; ++k) wu[a * D + k] = vu[a * D + k] - acc[k];
+  real w[D];
+  for (int k = 0; k < D; ++k) {
+    w[k] = vu[a * D + k] - acc[k];
+    ba0[a * D + k] = w[k];
+  }
+  for (int i = 0; i < D; ++i) {
+    real s = 0.0;
+    for (int j = 0; j < D; ++j) s = fma(dinva0[a * D * D + i * D + j], w[j], s);
+    xa0[a * D + i] = omega * s;
+  }
 }
 
 template <int D>
@@ -206,6 +268,7 @@ struct LevelDev {
   // level 0 only: Dirichlet / inactive DOFs are left out of the transfers
   const uint8_t *fixed;           // fixed[a * mstride + moff + i] != 0: DOF fixed
   int mstride, moff;
+  const uint64_t *mask;           // level 0 only: coupling mask of the block sparsity
 };
 
 __device__ inline real free_w(const LevelDev &L, int64_t a, int i) {
@@ -236,16 +299,16 @@ __device__ inline void row_partial(const LevelDev &L, int64_t a, int lane, const
     }
   } else {
     int ac[3];
-    ac[0] = (int)(a % L.nn[0]);
-    ac[1] = (int)((a / L.nn[0]) % L.nn[1]);
-    ac[2] = (int)(a / ((int64_t)L.nn[0] * L.nn[1]));
+    grid_xyz(L.nn[0], L.nn[1], (int)a, ac);
     constexpr int NS = NS_<D>::v;
     const real *base = L.sval + a * NS * B * B;
-    for (int s = lane; s < NS; s += LN) {
+#pragma unroll
+    for (int k = 0; k < (NS + LN - 1) / LN; ++k) {
+      const int s = lane + k * LN;
       const int o0 = s % 5 - 2, o1 = (s / 5) % 5 - 2, o2 = D == 3 ? s / 25 - 2 : 0;
       const int b0 = ac[0] + o0, b1 = ac[1] + o1, b2 = ac[2] + o2;
-      if (b0 < 0 || b0 >= L.nn[0] || b1 < 0 || b1 >= L.nn[1] || b2 < 0 || b2 >= L.nn[2]) continue;
-      const int64_t b = b0 + (int64_t)L.nn[0] * (b1 + (int64_t)L.nn[1] * b2);
+      if (s >= NS || b0 < 0 || b0 >= L.nn[0] || b1 < 0 || b1 >= L.nn[1] || b2 < 0 || b2 >= L.nn[2]) continue;
+      const int64_t b = b0 + L.nn[0] * (b1 + L.nn[1] * b2);
       const real *blk = base + s * B * B;
       real xb[B];
       for (int j = 0; j < B; ++j) xb[j] = x[b * B + j];
@@ -359,11 +422,20 @@ __global__ void k_dense_fill(LevelDev L, real *__restrict__ Ad) {
 // In-place Gauss-Jordan inverse of the dense n x n matrix Ad into Ai (one
 // block).  Rows with no usable pivot (singular directions) get a zero row in
 // the inverse, so the coarse correction leaves them alone.
-__global__ void k_dense_invert(int n, real *__restrict__ Ad, real *__restrict__ Ai) {
+// With smem set, both matrices are worked on in dynamic shared memory
+// (2 n^2 values) and the inverse is copied out at the end.
+__global__ void k_dense_invert(int n, real *__restrict__ Adg, real *__restrict__ Aig, int smem) {
   __shared__ int piv;
   __shared__ real pval;
   __shared__ real red_v[32];
   __shared__ int red_i[32];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  real *Ad = Adg, *Ai = Aig;
+  if (smem) {
+    Ad = reinterpret_cast<real *>(dyn_smem);
+    Ai = Ad + n * n;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ad[t] = Adg[t];
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ai[t] = (t / n == t % n) ? real(1) : real(0);
   // largest magnitude (parallel), for the singular-pivot threshold
@@ -432,7 +504,12 @@ __global__ void k_dense_invert(int n, real *__restrict__ Ad, real *__restrict__ 
       if (i != k) Ad[i * n + k] = 0;
     __syncthreads();
   }
+  if (smem)
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Aig[t] = Ai[t];
 }
+
+// largest coarsest system whose inverse is built in shared memory
+constexpr int DENSE_SMEM_MAX_N = 80;
 
 // x = Ai b
 __global__ void k_dense_apply(int n, const real *__restrict__ Ai, const real *__restrict__ b,
@@ -450,16 +527,16 @@ __device__ inline real pw(int a, int I) {
   return dlt == 0 ? 1.0 : ((dlt == 1 || dlt == -1) ? 0.5 : 0.0);
 }
 
-// b_c(I) = sum_a P_aI r_a over the fine nodes within one fine cell of 2I
+// b_c(I) = sum_a P_aI r_a over the fine nodes within one fine cell of 2I; if
+// xc is given, also the coarse level's first smoothing sweep from zero,
+// x_c = omega Dinv_c b_c.
 template <int B, int D>
 __global__ void k_mg_restrict(LevelDev F, LevelDev Cl, const real *__restrict__ rf,
-                              real *__restrict__ bc) {
+                              real *__restrict__ bc, real *__restrict__ xc, real omega) {
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= Cl.nnodes) return;
   int Ic[3];
-  Ic[0] = (int)(I % Cl.nn[0]);
-  Ic[1] = (int)((I / Cl.nn[0]) % Cl.nn[1]);
-  Ic[2] = (int)(I / ((int64_t)Cl.nn[0] * Cl.nn[1]));
+  grid_xyz(Cl.nn[0], Cl.nn[1], (int)I, Ic);
   real acc[B];
   for (int i = 0; i < B; ++i) acc[i] = 0.0;
   const int lo2 = D == 3 ? -1 : 0, hi2 = D == 3 ? 1 : 0;
@@ -473,6 +550,40 @@ __global__ void k_mg_restrict(LevelDev F, LevelDev Cl, const real *__restrict__ 
         for (int i = 0; i < B; ++i) acc[i] += wgt * free_w(F, a, i) * rf[a * B + i];
       }
   for (int i = 0; i < B; ++i) bc[I * B + i] = acc[i];
+  if (xc)
+    for (int i = 0; i < B; ++i) {
+      real s = 0.0;
+      for (int j = 0; j < B; ++j) s = fma(Cl.dinv[I * B * B + i * B + j], acc[j], s);
+      xc[I * B + i] = omega * s;
+    }
+}
+
+// (P x_c)(a) at fine node a from its 2^d candidate coarse parents: per axis
+// I = a/2 (weight 1 if a is even, 1/2 if odd) and I + 1 (weight 1/2 if a is
+// odd and I + 1 exists, else 0, with its index clamped), so all loads are
+// issued without branches.
+template <int B, int D>
+__device__ inline void prolong_at(const LevelDev &Cl, const real *__restrict__ xc, const int ac[3],
+                                  real out[B]) {
+  int i0[3], i1[3];
+  real w0[3], w1[3];
+  for (int k = 0; k < 3; ++k) {
+    const int odd = ac[k] & 1;
+    i0[k] = ac[k] >> 1;
+    const bool up = odd && i0[k] + 1 < Cl.nn[k];
+    i1[k] = up ? i0[k] + 1 : i0[k];
+    w0[k] = odd ? 0.5 : 1.0;
+    w1[k] = up ? 0.5 : 0.0;
+  }
+  for (int i = 0; i < B; ++i) out[i] = 0.0;
+#pragma unroll
+  for (int cmb = 0; cmb < (1 << D); ++cmb) {
+    const int s0 = cmb & 1, s1 = (cmb >> 1) & 1, s2 = (cmb >> 2) & 1;
+    const real wgt = (s0 ? w1[0] : w0[0]) * (s1 ? w1[1] : w0[1]) * (D == 3 ? (s2 ? w1[2] : w0[2]) : 1.0);
+    const int64_t I = (s0 ? i1[0] : i0[0]) +
+                      (int64_t)Cl.nn[0] * ((s1 ? i1[1] : i0[1]) + (int64_t)Cl.nn[1] * (D == 3 ? (s2 ? i1[2] : i0[2]) : 0));
+    for (int i = 0; i < B; ++i) out[i] = fma(wgt, xc[I * B + i], out[i]);
+  }
 }
 
 // x_f(a) += sum_I P_aI x_c(I)
@@ -482,25 +593,9 @@ __global__ void k_mg_prolong(LevelDev F, LevelDev Cl, real *__restrict__ xf,
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= F.nnodes) return;
   int ac[3];
-  ac[0] = (int)(a % F.nn[0]);
-  ac[1] = (int)((a / F.nn[0]) % F.nn[1]);
-  ac[2] = (int)(a / ((int64_t)F.nn[0] * F.nn[1]));
+  grid_xyz(F.nn[0], F.nn[1], (int)a, ac);
   real acc[B];
-  for (int i = 0; i < B; ++i) acc[i] = 0.0;
-  int lo[3], hi[3];
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = ac[k] / 2;
-    hi[k] = (ac[k] + 1) / 2;
-    if (hi[k] >= Cl.nn[k]) hi[k] = Cl.nn[k] - 1;
-  }
-  for (int I2 = lo[2]; I2 <= hi[2]; ++I2)
-    for (int I1 = lo[1]; I1 <= hi[1]; ++I1)
-      for (int I0 = lo[0]; I0 <= hi[0]; ++I0) {
-        const real wgt = pw(ac[0], I0) * pw(ac[1], I1) * (D == 3 ? pw(ac[2], I2) : 1.0);
-        if (wgt == 0.0) continue;
-        const int64_t I = I0 + (int64_t)Cl.nn[0] * (I1 + (int64_t)Cl.nn[1] * I2);
-        for (int i = 0; i < B; ++i) acc[i] += wgt * xc[I * B + i];
-      }
+  prolong_at<B, D>(Cl, xc, ac, acc);
   for (int i = 0; i < B; ++i) xf[a * B + i] += free_w(F, a, i) * acc[i];
 }
 
@@ -514,9 +609,7 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
   const int s = (int)(t % NS);
   const int o0 = s % 5 - 2, o1 = (s / 5) % 5 - 2, o2 = D == 3 ? s / 25 - 2 : 0;
   int Ic[3], Jc[3];
-  Ic[0] = (int)(I % Cl.nn[0]);
-  Ic[1] = (int)((I / Cl.nn[0]) % Cl.nn[1]);
-  Ic[2] = (int)(I / ((int64_t)Cl.nn[0] * Cl.nn[1]));
+  grid_xyz(Cl.nn[0], Cl.nn[1], (int)I, Ic);
   Jc[0] = Ic[0] + o0;
   Jc[1] = Ic[1] + o1;
   Jc[2] = Ic[2] + o2;
@@ -544,8 +637,8 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
                 const real wb = pw(fb[0], Jc[0]) * pw(fb[1], Jc[1]) * (D == 3 ? pw(fb[2], Jc[2]) : 1.0);
                 const real *blk = nullptr;
                 if (!FST) {
-                  const int64_t b = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
-                  const int e = find_col(F.col, F.row_ptr[a], F.row_ptr[a + 1], (int)b);
+                  const int e = mask_block<D>(F.mask, F.row_ptr, (int)a, fb[0] - fa[0], fb[1] - fa[1],
+                                              fb[2] - fa[2]);
                   if (e < 0) continue;
                   blk = F.val + (int64_t)e * B * B;
                 } else {
@@ -605,46 +698,51 @@ void mg_setup_t(Ctx &c, MGHier<real> &H) {
   const int64_t n = H.ncoarse;
   if (H.nlev == 1) k_dense_fill<B, D, false><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
   else k_dense_fill<B, D, true><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
-  k_dense_invert<<<1, 256, 0, c.st>>>((int)n, H.Ad, H.Ai);
+  const int smem = n <= DENSE_SMEM_MAX_N;
+  const size_t bytes = smem ? sizeof(real) * 2 * n * n : 0;
+  if (smem && bytes > 48 * 1024)
+    cudaFuncSetAttribute(k_dense_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  k_dense_invert<<<1, 512, bytes, c.st>>>((int)n, H.Ad, H.Ai, smem);
   c.launches += 2;
 }
 
+constexpr real MG_OMEGA = 0.6;
+
+// one damped block-Jacobi sweep on level l: x <- x + omega Dinv (b - A x)
 template <int B, int D>
-void smooth(Ctx &c, MGHier<real> &H, int l, int sweeps, real omega, bool zero_first) {
+void sweep(Ctx &c, MGHier<real> &H, int l) {
   LevelDev &L = H.L[l];
   const int nbk = nblk(L.nnodes * LN_<D>::v);
-  for (int s = 0; s < sweeps; ++s) {
-    const bool z = zero_first && s == 0;
-    if (l == 0) k_mg_smooth<B, D, false><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], omega, z);
-    else k_mg_smooth<B, D, true><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], omega, z);
-    UPMPM_LAUNCH(c);
-    std::swap(H.x[l], H.x2[l]);
-  }
+  if (l == 0) k_mg_smooth<B, D, false><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+  else k_mg_smooth<B, D, true><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+  UPMPM_LAUNCH(c);
+  std::swap(H.x[l], H.x2[l]);
 }
 
+// V(2,2)-cycle on level l.  On entry b[l] holds the rhs and x[l] the first
+// pre-smoothing sweep from zero (omega Dinv b, pointwise), done by the kernel
+// that produced b[l]; on return x[l] holds the result.
 template <int B, int D>
 void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
-  const real omega = 0.6;
-  const int pre = 2, post = 2;
   if (l == H.nlev - 1) {  // exact solve on the coarsest grid
     k_dense_apply<<<nblk(H.ncoarse, 64), 64, 0, c.st>>>(H.ncoarse, H.Ai, H.b[l], H.x[l]);
     UPMPM_LAUNCH(c);
     return;
   }
-  smooth<B, D>(c, H, l, pre, omega, true);
-  LevelDev &L = H.L[l];
-  const int nbk = nblk(L.nnodes);
+  LevelDev &L = H.L[l], &Ln = H.L[l + 1];
+  real *xn_first = l + 1 == H.nlev - 1 ? nullptr : H.x[l + 1];
+  sweep<B, D>(c, H, l);  // second pre-smoothing sweep
   const int nbr = nblk(L.nnodes * LN_<D>::v);
   if (l == 0) k_mg_resid<B, D, false><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
   else k_mg_resid<B, D, true><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
-  k_mg_restrict<B, D><<<nblk(H.L[l + 1].nnodes), TPB, 0, c.st>>>(L, H.L[l + 1], H.r[l], H.b[l + 1]);
+  k_mg_restrict<B, D><<<nblk(Ln.nnodes), TPB, 0, c.st>>>(L, Ln, H.r[l], H.b[l + 1], xn_first, MG_OMEGA);
   c.launches += 2;
   vcycle_t<B, D>(c, H, l + 1);
-  k_mg_prolong<B, D><<<nbk, TPB, 0, c.st>>>(L, H.L[l + 1], H.x[l], H.x[l + 1]);
+  k_mg_prolong<B, D><<<nblk(L.nnodes), TPB, 0, c.st>>>(L, Ln, H.x[l], H.x[l + 1]);
   UPMPM_LAUNCH(c);
-  smooth<B, D>(c, H, l, post, omega, false);
+  sweep<B, D>(c, H, l);  // first post-smoothing sweep
+  sweep<B, D>(c, H, l);  // second post-smoothing sweep
 }
-
 
 // Allocate a hierarchy for block size B over the grid's node lattice; level 0
 // refers to a block-CSR operator given at setup.
@@ -663,6 +761,7 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
     L.val = nullptr;
     L.sval = nullptr;
     L.fixed = nullptr;
+    L.mask = nullptr;
     L.mstride = 1;
     L.moff = 0;
     const int64_t vb = L.nnodes * B;
@@ -710,6 +809,7 @@ void mg_setup(Ctx &c, MGHier<real> &H, const int32_t *row_ptr, const int32_t *co
   H.L[0].fixed = c.fixed;
   H.L[0].mstride = c.nb;
   H.L[0].moff = moff;
+  H.L[0].mask = c.row_mask;
   if (c.d == 2) {
     if (H.B == 1) mg_setup_t<1, 2>(c, H);
     else mg_setup_t<2, 2>(c, H);
@@ -719,10 +819,9 @@ void mg_setup(Ctx &c, MGHier<real> &H, const int32_t *row_ptr, const int32_t *co
   }
 }
 
-// x = V-cycle(b) on the level-0 vectors of H (b copied in, x copied out)
-void mg_vcycle(Ctx &c, MGHier<real> &H, const real *b, real *x) {
-  const int64_t n0 = H.L[0].nnodes * H.B;
-  cudaMemcpyAsync(H.b[0], b, sizeof(real) * n0, cudaMemcpyDeviceToDevice, c.st);
+// V-cycle on H's level-0 vectors (b[0] and the first sweep in x[0] set by the
+// caller); the result is left in x[0].
+void mg_vcycle(Ctx &c, MGHier<real> &H) {
   if (c.d == 2) {
     if (H.B == 1) vcycle_t<1, 2>(c, H, 0);
     else vcycle_t<2, 2>(c, H, 0);
@@ -730,7 +829,6 @@ void mg_vcycle(Ctx &c, MGHier<real> &H, const real *b, real *x) {
     if (H.B == 1) vcycle_t<1, 3>(c, H, 0);
     else vcycle_t<3, 3>(c, H, 0);
   }
-  cudaMemcpyAsync(x, H.x[0], sizeof(real) * n0, cudaMemcpyDeviceToDevice, c.st);
 }
 
 }  // namespace MG_NS
@@ -746,11 +844,8 @@ int schur_alloc<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   int rc = mg_alloc(c, *S.mgA, d);
   if (!rc) rc = mg_alloc(c, *S.mgS, 1);
   if (rc) return rc;
-  if (cudaMalloc(&S.gin, sizeof(real) * nn * (d + 1)) || cudaMalloc(&S.gout, sizeof(real) * nn * (d + 1)))
-    return MPM_ERR_NO_MEMORY;
   if (cudaMalloc(&S.DAinv, sizeof(real) * nn * d * d) || cudaMalloc(&S.vu, sizeof(real) * nn * d) ||
-      cudaMalloc(&S.wu, sizeof(real) * nn * d) || cudaMalloc(&S.zu, sizeof(real) * nn * d) ||
-      cudaMalloc(&S.vp, sizeof(real) * nn) || cudaMalloc(&S.zp, sizeof(real) * nn))
+      cudaMalloc(&S.B1rs, sizeof(real) * nn * d))
     return MPM_ERR_NO_MEMORY;
   return MPM_OK;
 }
@@ -760,22 +855,13 @@ void schur_free<MG_REAL>(LinSys<MG_REAL> &S) {
   using namespace MG_NS;
   if (S.mgA) { mg_free(*S.mgA); delete S.mgA; S.mgA = nullptr; }
   if (S.mgS) { mg_free(*S.mgS); delete S.mgS; S.mgS = nullptr; }
-  cudaFree(S.Aval);
-  cudaFree(S.Sval);
-  cudaFree(S.B1c);
-  S.B1c = nullptr;
-  cudaFree(S.DAinv);
-  cudaFree(S.vu);
-  cudaFree(S.wu);
-  cudaFree(S.zu);
-  cudaFree(S.vp);
-  cudaFree(S.zp);
-  cudaFree(S.gin);
-  cudaFree(S.gout);
+  MG_REAL *ptrs[] = {S.Aval, S.Sval, S.B1c, S.W, S.B1rs, S.DAinv, S.vu};
+  for (MG_REAL *p : ptrs) cudaFree(p);
+  S.Aval = S.Sval = S.B1c = S.W = S.B1rs = S.DAinv = S.vu = nullptr;
   if (S.gexec) cudaGraphExecDestroy(S.gexec);
   S.gexec = nullptr;
   S.gkey_col = S.gkey_val = nullptr;
-  S.Aval = S.Sval = S.DAinv = S.vu = S.wu = S.zu = S.vp = S.zp = S.gin = S.gout = nullptr;
+  S.g_xs0 = S.g_zp = S.g_zu = nullptr;
   S.sub_cap = 0;
 }
 
@@ -787,78 +873,93 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   const int64_t nn = c.g.nnodes, nnzb = c.nnzb;
   const int d = c.d;
   if (nnzb > S.sub_cap) {
-    cudaFree(S.Aval);
-    cudaFree(S.Sval);
-    cudaFree(S.B1c);
-    S.Aval = S.Sval = S.B1c = nullptr;
+    MG_REAL *ptrs[] = {S.Aval, S.Sval, S.B1c, S.W};
+    for (MG_REAL *p : ptrs) cudaFree(p);
+    S.Aval = S.Sval = S.B1c = S.W = nullptr;
     const int64_t cap = c.nnzb_cap;
     if (cudaMalloc(&S.Aval, sizeof(real) * cap * d * d) || cudaMalloc(&S.Sval, sizeof(real) * cap) ||
-        cudaMalloc(&S.B1c, sizeof(real) * cap * d)) {
+        cudaMalloc(&S.B1c, sizeof(real) * cap * d) || cudaMalloc(&S.W, sizeof(real) * cap * d)) {
       S.sub_cap = 0;
       c.last_error = "device allocation of the block preconditioner failed";
       return MPM_ERR_NO_MEMORY;
     }
     S.sub_cap = cap;
   }
+  const int nsl = d == 2 ? 49 : 343;
   if (d == 2) {
     k_extract_A<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
     k_extract_B1<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B1c);
-    k_diag_inv_A<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.DAinv);
-    k_schur_rows<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.DAinv, S.Sval);
+    k_diag_inv_A<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.val, S.DAinv, S.B1rs);
+    k_schur_w<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, c.col, S.val, S.DAinv, S.W);
+    k_schur_rows<2><<<nblk(nsl * nn), TPB, 0, c.st>>>(c.g.nn[0], c.g.nn[1], nn, c.row_mask, c.row_ptr, c.col,
+                                                      S.val, S.W, S.Sval);
+    k_schur_lump<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.W, S.B1rs, S.Sval);
   } else {
     k_extract_A<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
     k_extract_B1<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B1c);
-    k_diag_inv_A<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.DAinv);
-    k_schur_rows<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.DAinv, S.Sval);
+    k_diag_inv_A<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.val, S.DAinv, S.B1rs);
+    k_schur_w<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, c.col, S.val, S.DAinv, S.W);
+    k_schur_rows<3><<<nblk(nsl * nn), TPB, 0, c.st>>>(c.g.nn[0], c.g.nn[1], nn, c.row_mask, c.row_ptr, c.col,
+                                                      S.val, S.W, S.Sval);
+    k_schur_lump<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.W, S.B1rs, S.Sval);
   }
-  c.launches += 3;
+  c.launches += 6;
   mg_setup(c, *S.mgA, c.row_ptr, c.col, S.Aval, 0);
   mg_setup(c, *S.mgS, c.row_ptr, c.col, S.Sval, d);
   return check_cuda(c, cudaGetLastError(), "schur setup");
 }
 
-// z = M^{-1} v (block upper triangular, multigrid sub-solves)
+// z = M^{-1} v (block upper triangular, multigrid sub-solves) in three parts:
+// split (v -> v_u and the S-cycle's rhs), the multigrid core (S-cycle, B1
+// update, A-cycle), merge (-> z).
 namespace MG_NS {
-void schur_apply_body(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
+void schur_split(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *xs0) {
   const int64_t nn = c.g.nnodes;
-  const int nbk = nblk(nn);
-  if (c.d == 2) k_split<2><<<nbk, TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, S.vp);
-  else k_split<3><<<nbk, TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, S.vp);
+  MGHier<real> &HS = *S.mgS;
+  if (c.d == 2) k_split<2><<<nblk(nn), TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
+  else k_split<3><<<nblk(nn), TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
   UPMPM_LAUNCH(c);
-  mg_vcycle(c, *S.mgS, S.vp, S.zp);
+}
+
+void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
+  const int64_t nn = c.g.nnodes;
+  MGHier<real> &HS = *S.mgS, &HA = *S.mgA;
+  mg_vcycle(c, HS);
   if (c.d == 2)
-    k_b1c_update<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, S.zp, S.vu, S.wu);
+    k_b1c_update<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
+                                                     HA.x[0], HA.L[0].dinv, MG_OMEGA);
   else
-    k_b1c_update<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, S.zp, S.vu, S.wu);
+    k_b1c_update<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
+                                                      HA.x[0], HA.L[0].dinv, MG_OMEGA);
   UPMPM_LAUNCH(c);
-  mg_vcycle(c, *S.mgA, S.wu, S.zu);
-  if (c.d == 2) k_merge<2><<<nbk, TPB, 0, c.st>>>(nn, S.zu, S.zp, S.dscale, z);
-  else k_merge<3><<<nbk, TPB, 0, c.st>>>(nn, S.zu, S.zp, S.dscale, z);
+  mg_vcycle(c, HA);
+}
+
+void schur_merge(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *zu, const MG_REAL *zp, MG_REAL *z) {
+  const int64_t nn = c.g.nnodes;
+  if (c.d == 2) k_merge<2><<<nblk(nn), TPB, 0, c.st>>>(nn, zu, zp, S.dscale, z);
+  else k_merge<3><<<nblk(nn), TPB, 0, c.st>>>(nn, zu, zp, S.dscale, z);
   UPMPM_LAUNCH(c);
 }
 }  // namespace MG_NS
 
-// The application is a fixed sequence of ~100 small kernels on fixed buffers:
-// it is captured once into a CUDA graph (re-captured only when the matrix
-// buffers it reads move) and replayed, with the input and output copied in and
-// out of the graph's own buffers.
+// The multigrid core is a fixed sequence of small kernels on fixed buffers: it
+// is captured once into a CUDA graph (re-captured only when the matrix buffers
+// it reads move) and replayed between the split and merge kernels, which take
+// the caller's v and z.
 template <>
 void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
   using namespace MG_NS;
-  const int64_t N = c.N();
-  if (c.capturing) {  // nested inside another capture: plain launches
-    schur_apply_body(c, S, v, z);
-    return;
-  }
-  if (!S.gexec || S.gkey_col != c.col || S.gkey_val != S.val) {
+  if (!c.capturing && (!S.gexec || S.gkey_col != c.col || S.gkey_val != S.val)) {
     if (S.gexec) cudaGraphExecDestroy(S.gexec);
     S.gexec = nullptr;
     cudaGraph_t graph = nullptr;
     const int64_t before = c.launches;
+    MG_REAL *xs0 = S.mgS->x[0];
     bool ok = cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       c.capturing = true;
-      schur_apply_body(c, S, S.gin, S.gout);
+      schur_core(c, S);
       c.capturing = false;
       ok = cudaStreamEndCapture(c.st, &graph) == cudaSuccess && graph;
     }
@@ -866,17 +967,25 @@ void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL 
     if (graph) cudaGraphDestroy(graph);
     S.gkernels = c.launches - before;
     c.launches = before;
-    if (!ok) {  // capture unavailable: launch directly
+    if (ok) {
+      S.g_xs0 = xs0;
+      S.g_zp = S.mgS->x[0];
+      S.g_zu = S.mgA->x[0];
+      S.gkey_col = c.col;
+      S.gkey_val = S.val;
+    } else {  // capture unavailable: launch directly from now on
       cudaGetLastError();
       S.gexec = nullptr;
-      schur_apply_body(c, S, v, z);
-      return;
     }
-    S.gkey_col = c.col;
-    S.gkey_val = S.val;
   }
-  cudaMemcpyAsync(S.gin, v, sizeof(MG_REAL) * N, cudaMemcpyDeviceToDevice, c.st);
-  cudaGraphLaunch(S.gexec, c.st);
-  cudaMemcpyAsync(z, S.gout, sizeof(MG_REAL) * N, cudaMemcpyDeviceToDevice, c.st);
-  c.launches += S.gkernels;
+  if (S.gexec && !c.capturing) {
+    schur_split(c, S, v, S.g_xs0);
+    cudaGraphLaunch(S.gexec, c.st);
+    c.launches += S.gkernels;
+    schur_merge(c, S, S.g_zu, S.g_zp, z);
+    return;
+  }
+  schur_split(c, S, v, S.mgS->x[0]);
+  schur_core(c, S);
+  schur_merge(c, S, S.mgA->x[0], S.mgS->x[0], z);
 }

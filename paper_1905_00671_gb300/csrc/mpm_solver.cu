@@ -251,42 +251,28 @@ __global__ void k_bj_apply(int64_t nnodes, const T *__restrict__ dinv, const T *
 }
 
 // ---------------------------------------------------------------- SpMV
-// LN lanes per block row; each lane takes whole NB x NB blocks (the lanes of a
-// row read one contiguous span), one FMA per stored value (GB300's FP64 pipe
-// is narrow, so an FP64 SpMV spends exactly one FP64 instruction per value),
-// and the row's NB sums are reduced across the lanes.
-template <int NB, int LN, typename T>
+// NB threads per block row, thread r computing y_r of its row: it walks the
+// row's blocks in order and spends one FMA per stored value of block row r
+// (GB300's FP64 pipe is narrow: an FP64 SpMV should issue exactly one FP64
+// instruction per value, with all lanes busy and no cross-lane reduction).
+template <int NB, typename T>
 __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, const T *__restrict__ val,
                            const T *__restrict__ x, T *__restrict__ y) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = t / LN;
-  const int lane = (int)(t % LN);
-  const bool valid = row < nnodes;
-  T acc[NB];
+  const int64_t row = t / NB;
+  const int r = (int)(t - row * NB);
+  if (row >= nnodes) return;
+  T acc = 0;
+  const int e1 = row_ptr[row + 1];
+#pragma unroll 4
+  for (int e = row_ptr[row]; e < e1; ++e) {
+    const T *blk = val + (int64_t)e * NB * NB + r * NB;
+    const T *xb = x + (int64_t)__ldg(&col[e]) * NB;
 #pragma unroll
-  for (int r = 0; r < NB; ++r) acc[r] = 0;
-  if (valid) {
-    const int e1 = row_ptr[row + 1];
-    for (int e = row_ptr[row] + lane; e < e1; e += LN) {
-      const T *blk = val + (int64_t)e * NB * NB;
-      const T *xb = x + (int64_t)__ldg(&col[e]) * NB;
-      T xv[NB];
-#pragma unroll
-      for (int c = 0; c < NB; ++c) xv[c] = __ldg(&xb[c]);
-#pragma unroll
-      for (int r = 0; r < NB; ++r)
-#pragma unroll
-        for (int c = 0; c < NB; ++c) acc[r] = fma(__ldg(&blk[r * NB + c]), xv[c], acc[r]);
-    }
+    for (int c = 0; c < NB; ++c) acc = fma(__ldg(&blk[c]), __ldg(&xb[c]), acc);
   }
-#pragma unroll
-  for (int o = LN / 2; o > 0; o >>= 1)
-#pragma unroll
-    for (int r = 0; r < NB; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-  if (valid && lane == 0)
-#pragma unroll
-    for (int r = 0; r < NB; ++r) y[row * NB + r] = acc[r];
+  y[row * NB + r] = acc;
 }
 
 // ---------------------------------------------------------------- FGMRES
@@ -411,10 +397,9 @@ __global__ void k_update_x(T *__restrict__ x, const T *__restrict__ Z, const dou
 
 template <int NB, typename T>
 void spmv(Ctx &c, const LinSys<T> &S, const T *x, T *y) {
-  constexpr int LN = NB == 3 ? 8 : 16;
-  const int64_t threads = c.g.nnodes * LN;
+  const int64_t threads = c.g.nnodes * NB;
   prof_begin(c, MPM_PROF_SPMV);
-  k_bsr_spmv<NB, LN, T><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, S.val, x, y);
+  k_bsr_spmv<NB, T><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, S.val, x, y);
   prof_end(c, MPM_PROF_SPMV);
   UPMPM_LAUNCH(c);
 }

@@ -82,7 +82,8 @@ class mpm_stats(C.Structure):
                 ("res_norm", C.c_double * (MPM_MAX_NEWTON + 1)), ("krylov_total", C.c_int32),
                 ("steps", C.c_int64), ("t", C.c_double), ("nnzb", C.c_int64),
                 ("kernel_launches", C.c_int64), ("prof_ms", C.c_double * 8),
-                ("prof_launches", C.c_int64 * 8)]
+                ("prof_launches", C.c_int64 * 8), ("jac_terms", C.c_int64),
+                ("jac_point_nodes", C.c_int64)]
 
 
 _lib = None
@@ -255,7 +256,8 @@ class Simulation:
                 "res_norm": list(s.res_norm[:k + 1]), "krylov_total": s.krylov_total,
                 "steps": s.steps, "t": s.t, "nnzb": s.nnzb, "kernel_launches": s.kernel_launches,
                 "prof_ms": {k: s.prof_ms[i] for k, i in PROF.items()},
-                "prof_launches": {k: s.prof_launches[i] for k, i in PROF.items()}}
+                "prof_launches": {k: s.prof_launches[i] for k, i in PROF.items()},
+                "jac_terms": s.jac_terms, "jac_point_nodes": s.jac_point_nodes}
 
     # -- inspection
     def debug_bin(self):
