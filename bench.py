@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--precond-lag", type=int, default=2,
+                    help="Newton iterations served by one preconditioner set-up")
     ap.add_argument("--profile", default="spmv,orth,jacobian,point,residual,precond",
                     help="kernel classes timed with CUDA events")
     return ap.parse_args()
@@ -220,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     # ---- device-resident throughput
-    sim = mpm.Simulation(w, stream=stream.cuda_stream, profile=prof_bits)
+    sim = mpm.Simulation(w, stream=stream.cuda_stream, profile=prof_bits, precond_lag=args.precond_lag)
     for _ in range(args.warmup):
         sim.step(resident=True)
     barrier()
@@ -264,7 +266,7 @@ def run_ours(args, rank, world, local_rank):
     mixed = None
     if not args.no_mixed:
         sim_m = mpm.Simulation(w, stream=stream.cuda_stream, precision=mpm.MPM_MIXED,
-                               newton_max=60, profile=prof_bits)
+                               newton_max=60, profile=prof_bits, precond_lag=args.precond_lag)
         sim_r = mpm.Simulation(w, stream=stream.cuda_stream)   # FP64 twin for the error
         for _ in range(args.warmup):
             sim_m.step(resident=True)

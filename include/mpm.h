@@ -146,6 +146,13 @@ typedef struct {
                                  are renormalised over their other nodes. */
   int32_t profile;            /* bit mask of MPM_PROF_* classes timed with CUDA
                                  events on the work stream (0 = none) */
+  int32_t precond_lag;        /* Newton iterations of a step served by one set-up of
+                                 the Schur/multigrid preconditioner (default 2; 1 =
+                                 rebuilt for every Newton iteration; k > 1: rebuilt
+                                 at iterations 0, k, 2k, ... of each step and reused
+                                 in between, with the current diagonal scaling).
+                                 Changes Krylov iteration counts only: the Newton
+                                 test is on the exact residual. */
   void *stream;               /* cudaStream_t for all work; NULL = default stream */
 } mpm_options;
 
@@ -201,7 +208,7 @@ typedef struct {
 /* Fills *o with the defaults: GIMP, quasi-static, beta 0.3025, gamma 0.6,
  * PPP on with tau_W, FP64, Newton rtol 1e-8 (Eq. newton-tolerance), 25
  * iterations, Krylov rtol 1e-8, restart 120, 3000 iterations, Schur-complement
- * multigrid preconditioner. */
+ * multigrid preconditioner set up once per two Newton iterations. */
 void mpm_default_options(mpm_options *o);
 
 /* Creates a context and uploads the problem (Sec. 2.4 "given u0, p0"): the

@@ -267,12 +267,15 @@ int eval_residual(Ctx &c, double *rnorm) {
 // solve that stops at its iteration cap is an inexact Newton step: the FP64
 // residual test of the Newton loop decides convergence.
 template <typename T>
-int newton_correction(Ctx &c, LinSys<T> &S, int *its) {
+int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
   run_jacobian<T>(c, S.val, 1);
   int rc;
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
-    rc = schur_setup<T>(c, S);  // on the unscaled blocks
-    if (rc) return rc;
+    const int lag = c.opt.precond_lag > 1 ? c.opt.precond_lag : 1;
+    if (k % lag == 0) {
+      rc = schur_setup<T>(c, S);  // on the unscaled blocks
+      if (rc) return rc;
+    }
     run_scale_system<T>(c, S, c.R);
   } else {
     run_scale_system<T>(c, S, c.R);
@@ -312,7 +315,7 @@ int newton(Ctx &c) {
       return MPM_ERR_NEWTON_DIVERGED;
     }
     int its = 0;
-    rc = c.have32 ? newton_correction<float>(c, c.L32, &its) : newton_correction<double>(c, c.L64, &its);
+    rc = c.have32 ? newton_correction<float>(c, c.L32, k, &its) : newton_correction<double>(c, c.L64, k, &its);
     st.krylov_iters[k] = its;
     st.krylov_total += its;
     if (rc) return rc;
@@ -364,7 +367,7 @@ void free_all(Ctx &c) {
     if (p) cudaFree(p);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
                   c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS,
-                  c.sh_S0, c.m, c.rec, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.sh_nrm, c.fixed, c.u_fixed,
+                  c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
                   c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp, c.terms};
@@ -407,6 +410,7 @@ void mpm_default_options(mpm_options *o) {
   o->precond = MPM_PRECOND_SCHUR_MG;
   o->min_volume_fraction = 1e-4;
   o->profile = 0;
+  o->precond_lag = 2;
   o->stream = nullptr;
 }
 
@@ -422,6 +426,7 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
     if (grid->ncell[k] < 1) return MPM_ERR_BAD_ARG;
   if (P->n > INT32_MAX / 2) return MPM_ERR_BAD_ARG;
   if (opt->krylov_restart < 1 || opt->krylov_restart > 128) return MPM_ERR_BAD_ARG;
+  if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON) return MPM_ERR_BAD_ARG;
   if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
     return MPM_ERR_BAD_ARG;
   if (opt->precision != MPM_FP64 && opt->precision != MPM_MIXED) return MPM_ERR_BAD_ARG;
@@ -438,6 +443,12 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   if (!h) return MPM_ERR_NO_MEMORY;
   Ctx &c = h->c;
   c.opt = *opt;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      c.nsm = nsm;
+  }
   c.st = (cudaStream_t)opt->stream;
   if (!c.st) {
     // a stream of our own (blocking, so it stays ordered with the legacy
@@ -509,6 +520,7 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   A(&c.sh_S0, 3 * MAXS * n);
   A(&c.m, n);
   A(&c.rec, RC_COUNT * n);
+  A(&c.pn, (int64_t)pn_nslot(c.d) * PN_NPF * n);
   A(&c.M, nn);
   A(&c.Pn, nn);
   A(&c.vn, d * nn);

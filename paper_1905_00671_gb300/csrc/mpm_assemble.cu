@@ -441,8 +441,161 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
   return (int64_t)row_ptr[a] + before;
 }
 
+// Per (point q, support slot) the node vectors the Jacobian terms are built
+// from, formed once per assembly instead of once per (q, a, b) term:
+//   g_a = F^{-T} grad_n S_a (the spatial gradient), S_a, S_a - S0_a,
+//   (g_a tau')_l, g_a . w, and (Newmark) (g_a grad v)_k,
+// at offsets 0, D, D+1, D+2, 2D+2, 2D+3; the last slot holds the point's
+// coefficients cs, vol, p^h, G - lambda ln J, lambda, kappa vol, m, b2,
+// C_stab factor, grad p.
+template <int D, bool DYN, typename R>
+__global__ void k_point_nodes(GridP g, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
+                              R *__restrict__ pn) {
+  constexpr int NSL = pn_nslot(D);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = v.n;
+  if (t >= n * NSL) return;
+  const int64_t q = t / NSL;
+  const int s = (int)(t - q * NSL);
+  R *out = pn + t * PN_NPF;
+  if (s == NSL - 1) {
+    out[0] = rec[RC_CS * n + q];
+    out[1] = rec[RC_VOL * n + q];
+    out[2] = rec[RC_PH * n + q];
+    out[3] = rec[RC_MUP * n + q];
+    out[4] = rec[RC_LAM * n + q];
+    out[5] = rec[RC_KV * n + q];
+    out[6] = DYN ? rec[RC_MS * n + q] : R(0);
+    out[7] = rec[RC_B2 * n + q];
+    out[8] = rec[RC_CST * n + q];
+    for (int k = 0; k < D; ++k) out[9 + k] = rec[(RC_GP + k) * n + q];
+    return;
+  }
+  const int off[3] = {s % MAXS, (s / MAXS) % MAXS, s / (MAXS * MAXS)};
+  const int packed = v.sh_cnt[q];
+  for (int k = 0; k < 3; ++k)
+    if (off[k] >= (k < D ? unpack_cnt(packed, k) : 1)) return;
+  int nc[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) nc[k] = v.sh_first[k * n + q] + off[k];
+  const int64_t a = node_index(g, nc);
+  R Sa, S0a, Gn[3], gs[3];
+  basis_at_t<D, R>(BA, q, off, a, Sa, S0a, Gn);
+  for (int j = 0; j < D; ++j) {
+    R sj = 0;
+    for (int k = 0; k < D; ++k) sj += Gn[k] * rec[(RC_FINV + k * D + j) * n + q];
+    gs[j] = sj;
+  }
+  for (int j = 0; j < D; ++j) out[j] = gs[j];
+  out[D] = Sa;
+  out[D + 1] = Sa - S0a;
+  R gw = 0;
+  for (int l = 0; l < D; ++l) {
+    R tl = 0;
+    for (int j = 0; j < D; ++j) tl += gs[j] * rec[(RC_TAU + j * D + l) * n + q];
+    out[D + 2 + l] = tl;
+    gw += gs[l] * rec[(RC_W + l) * n + q];
+  }
+  out[2 * D + 2] = gw;
+  if (DYN)
+    for (int k = 0; k < D; ++k) {
+      R gv = 0;
+      for (int j = 0; j < D; ++j) gv += gs[j] * rec[(RC_GV + j * D + k) * n + q];
+      out[2 * D + 3 + k] = gv;
+    }
+}
+
 template <int D, bool GIMP, bool DYN, typename T, typename R>
-__global__ void k_jacobian(GridP g, StepP s, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
+__global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn,
+                           const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
+                           const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  constexpr int NSLOT = D == 2 ? 49 : 343;
+  constexpr int NSL = pn_nslot(D);
+  if (t >= NSLOT * g.nnodes) return;
+  const int64_t a = t % g.nnodes;
+  const int64_t e = block_of_slot<D>(mask, row_ptr, a, (int)(t / g.nnodes));
+  if (e < 0) return;
+  constexpr int NB = D + 1;
+  const int64_t bn = col[e];
+  int ac[3], bc[3];
+  node_coords(g, a, ac);
+  node_coords(g, bn, bc);
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) {
+    int l1, h1, l2, h2;
+    cand_range<GIMP>(ac[k], g.nc[k], l1, h1);
+    cand_range<GIMP>(bc[k], g.nc[k], l2, h2);
+    lo[k] = max(l1, l2);
+    hi[k] = min(h1, h2);
+  }
+  R B[NB * NB];
+  for (int i = 0; i < NB * NB; ++i) B[i] = 0;
+  const R cvis = DYN ? (R)(s.alpha_vis * s.gamma / (s.beta * s.dt)) : R(0);
+  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
+    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
+      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
+        const int64_t cid = cell_index(g, c0, c1, c2);
+        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
+          int oa[3], ob[3];
+          if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
+          const R *P = pn + (int64_t)q * NSL * PN_NPF;
+          const R *pa = P + (oa[0] + MAXS * (oa[1] + MAXS * oa[2])) * PN_NPF;
+          const R *pb = P + (ob[0] + MAXS * (ob[1] + MAXS * ob[2])) * PN_NPF;
+          const R *pp = P + (NSL - 1) * PN_NPF;
+          R ga[3], gb[3];
+          for (int j = 0; j < D; ++j) {
+            ga[j] = pa[j];
+            gb[j] = pb[j];
+          }
+          const R Sa = pa[D], Sb = pb[D], Sta = pa[D + 1], Stb = pb[D + 1];
+          const R gaw = pa[2 * D + 2], gbw = pb[2 * D + 2];
+          const R cs = pp[0], vol = pp[1], ph = pp[2], mu = pp[3], lam = pp[4], kv = pp[5];
+          R gab = 0, gtg = 0;
+          for (int j = 0; j < D; ++j) {
+            gab += ga[j] * gb[j];
+            gtg += pa[D + 2 + j] * gb[j];
+          }
+          const R ms = DYN ? pp[6] * Sa * Sb : R(0);
+          for (int i = 0; i < D; ++i)
+            for (int k = 0; k < D; ++k) {
+              const R dik = i == k ? R(1) : R(0);
+              const R sym = mu * (dik * gab + ga[k] * gb[i]);
+              R A = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
+              A += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
+              if (DYN) {
+                A -= cs * cvis * (lam * ga[i] * gb[k] + sym);
+                A -= dik * ms;
+              }
+              B[i * NB + k] += A;
+            }
+          for (int i = 0; i < D; ++i) B[i * NB + D] += vol * ga[i] * Sb;
+          const R b2 = pp[7];
+          for (int k = 0; k < D; ++k) {
+            R tk = Sa * b2 * gb[k];
+            if (DYN) tk -= vol * Sa * pb[2 * D + 3 + k];
+            tk += kv * (gb[k] * gaw - ga[k] * gbw - pp[9 + k] * gab);
+            B[D * NB + k] += tk;
+          }
+          B[D * NB + D] += kv * gab + pp[8] * Sta * Stb;
+        }
+      }
+  if (apply_bc) {
+    for (int i = 0; i < NB; ++i) {
+      const bool fr = v.fixed[a * NB + i] != 0;
+      for (int k = 0; k < NB; ++k) {
+        const bool fc = v.fixed[bn * NB + k] != 0;
+        if (fr || fc) B[i * NB + k] = (a == bn && i == k) ? R(1) : R(0);
+      }
+    }
+  }
+  T *out = val + e * (NB * NB);
+  for (int i = 0; i < NB * NB; ++i) out[i] = (T)B[i];
+}
+
+// FP32 variant (mixed mode): the node vectors are recomputed per term from the
+// FP32 basis and records; with FP32 arithmetic plentiful this beats staging.
+template <int D, bool GIMP, bool DYN, typename T, typename R>
+__global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -653,8 +806,29 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
     BA.S = (const R *)c.sh_Sf; BA.dS = (const R *)c.sh_dSf; BA.S0 = (const R *)c.sh_S0f;
     BA.nrm = (const R *)c.sh_nrmf; rec = (const R *)c.recf;
   }
-#define JAC(D, G, Y) \
-  k_jacobian<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask, c.row_ptr, c.col, val, apply_bc)
+  // FP64: stage the per-(point, node) vectors, then assemble; FP32: direct
+  constexpr bool staged = sizeof(R) == sizeof(double);
+  R *pn = (R *)c.pn;
+  if (staged) {
+    const int npb = nblk((int64_t)pn_nslot(c.d) * c.n, TPB);
+    if (c.d == 2) {
+      if (c.dyn) k_point_nodes<2, true, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
+      else k_point_nodes<2, false, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
+    } else {
+      if (c.dyn) k_point_nodes<3, true, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
+      else k_point_nodes<3, false, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
+    }
+    UPMPM_LAUNCH(c);
+  }
+#define JAC(D, G, Y)                                                                                         \
+  do {                                                                                                       \
+    if (staged)                                                                                              \
+      k_jacobian<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr, c.col, val,   \
+                                                       apply_bc);                                            \
+    else                                                                                                     \
+      k_jacobian_direct<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask, c.row_ptr,   \
+                                                              c.col, val, apply_bc);                         \
+  } while (0)
   if (c.d == 2) {
     if (gimp) { if (c.dyn) JAC(2, true, true); else JAC(2, true, false); }
     else { if (c.dyn) JAC(2, false, true); else JAC(2, false, false); }

@@ -59,6 +59,10 @@ struct LinSys {
 constexpr int PATTERN_MASK_WORDS = 6;
 
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
+// Jacobian staging: per point, one record per support slot (MAXS^d) and one
+// for the point's own coefficients, PN_NPF values each.
+constexpr int PN_NPF = 12;
+__host__ __device__ constexpr int pn_nslot(int d) { return (d == 2 ? MAXS * MAXS : MAXS * MAXS * MAXS) + 1; }
 
 // ---- particle fields ------------------------------------------------------
 enum PField {
@@ -164,6 +168,7 @@ struct Ctx {
   mpm_options opt{};
   cudaStream_t st = nullptr;
   bool own_stream = false;   // created by the context (no stream was given)
+  int nsm = 152;             // SMs of the context's device
   bool capturing = false;    // a CUDA graph capture is in progress on st
   int64_t n = 0;
   int32_t n_surf = 0;
@@ -195,6 +200,9 @@ struct Ctx {
   int *h_err = nullptr;                  // pinned
   double *h_scalar = nullptr;            // pinned scratch for scalars read by the host
   unsigned long long *terms = nullptr;   // device: Jacobian term counts (n_p^2, n_p sums)
+  // per-(point, support node) vectors of the FP64 Jacobian (pn_nslot(d)
+  // records of PN_NPF values per point)
+  double *pn = nullptr;
   unsigned long long *h_terms = nullptr; // pinned copy
 
   // sparsity + matrix

@@ -8,6 +8,19 @@ using real = MG_REAL;
 constexpr int TPB = 256;
 inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
 
+// Block size for a launch of `threads` threads: the largest of 256, 128, 64, 32
+// that still gives two blocks per SM, so that small multigrid levels spread
+// over the whole GPU (one SM's FP64 pipe is narrow; a level's rows packed into
+// a few 256-thread blocks would run on a few SMs).
+struct Geom {
+  int blocks, tpb;
+};
+inline Geom geom(const Ctx &c, int64_t threads) {
+  int t = 256;
+  while (t > 32 && threads < (int64_t)t * 2 * c.nsm) t >>= 1;
+  return {nblk(threads > 0 ? threads : 1, t), t};
+}
+
 template <int D>
 struct NS_ {
   static constexpr int v = D == 2 ? 25 : 125;
@@ -422,9 +435,19 @@ __global__ void k_dense_fill(LevelDev L, real *__restrict__ Ad) {
 // In-place Gauss-Jordan inverse of the dense n x n matrix Ad into Ai (one
 // block).  Rows with no usable pivot (singular directions) get a zero row in
 // the inverse, so the coarse correction leaves them alone.
-// With smem set, both matrices are worked on in dynamic shared memory
-// (2 n^2 values) and the inverse is copied out at the end.
-__global__ void k_dense_invert(int n, real *__restrict__ Adg, real *__restrict__ Aig, int smem) {
+// Block j inverts job j (the coarsest operators of the two hierarchies are
+// inverted side by side).  With smem set, both matrices are worked on in
+// dynamic shared memory (2 n^2 values) and the inverse is copied out at the end.
+struct DenseJob {
+  int n;
+  real *Ad, *Ai;
+};
+
+__global__ void k_dense_invert(DenseJob j0, DenseJob j1, int smem) {
+  const DenseJob job = blockIdx.x == 0 ? j0 : j1;
+  const int n = job.n;
+  real *__restrict__ Adg = job.Ad;
+  real *__restrict__ Aig = job.Ai;
   __shared__ int piv;
   __shared__ real pval;
   __shared__ real red_v[32];
@@ -491,13 +514,16 @@ __global__ void k_dense_invert(int n, real *__restrict__ Adg, real *__restrict__
       Ai[k * n + j] *= inv;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      const int i = t / n, j = t % n;
+    // columns < k of Ad are already reduced (zero in the pivot row), column k
+    // is cleared below: update Ad's columns > k and all of Ai
+    const int wa = n - k - 1, wt = wa + n;
+    for (int t = threadIdx.x; t < n * wt; t += blockDim.x) {
+      const int i = t / wt, jj = t - i * wt;
       if (i == k) continue;
       const real f = Ad[i * n + k];
       if (f == real(0)) continue;
-      if (j != k) Ad[i * n + j] -= f * Ad[k * n + j];
-      Ai[i * n + j] -= f * Ai[k * n + j];
+      if (jj < wa) Ad[i * n + k + 1 + jj] -= f * Ad[k * n + k + 1 + jj];
+      else Ai[i * n + jj - wa] -= f * Ai[k * n + jj - wa];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -512,13 +538,16 @@ __global__ void k_dense_invert(int n, real *__restrict__ Adg, real *__restrict__
 constexpr int DENSE_SMEM_MAX_N = 80;
 
 // x = Ai b
+// one warp per row i; lanes split the row and reduce
 __global__ void k_dense_apply(int n, const real *__restrict__ Ai, const real *__restrict__ b,
                               real *__restrict__ x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   real s = 0.0;
-  for (int j = 0; j < n; ++j) s = fma(Ai[(int64_t)i * n + j], b[j], s);
-  x[i] = s;
+  if (i < n)
+    for (int j = lane; j < n; j += 32) s = fma(Ai[(int64_t)i * n + j], b[j], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (i < n && lane == 0) x[i] = s;
 }
 
 // weight of coarse node I for fine node a along one axis
@@ -650,11 +679,13 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
                 const real w = wa * wb;
                 if (!FST) {
                   const int64_t b = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
-                  for (int i = 0; i < B; ++i)
+                  for (int i = 0; i < B; ++i) {
+                    if (free_w(F, a, i) == 0.0) continue;
                     for (int j = 0; j < B; ++j)
-                      acc[i * B + j] += w * free_w(F, a, i) * free_w(F, b, j) * blk[i * B + j];
+                      if (free_w(F, b, j) != 0.0) acc[i * B + j] = fma(w, blk[i * B + j], acc[i * B + j]);
+                  }
                 } else {
-                  for (int i = 0; i < B * B; ++i) acc[i] += w * blk[i];
+                  for (int i = 0; i < B * B; ++i) acc[i] = fma(w, blk[i], acc[i]);
                 }
               }
         }
@@ -698,12 +729,19 @@ void mg_setup_t(Ctx &c, MGHier<real> &H) {
   const int64_t n = H.ncoarse;
   if (H.nlev == 1) k_dense_fill<B, D, false><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
   else k_dense_fill<B, D, true><<<nblk(n * n), TPB, 0, c.st>>>(Lc, H.Ad);
-  const int smem = n <= DENSE_SMEM_MAX_N;
-  const size_t bytes = smem ? sizeof(real) * 2 * n * n : 0;
+  UPMPM_LAUNCH(c);
+}
+
+// Inverses of the coarsest operators of two hierarchies, in one launch.
+void dense_invert_pair(Ctx &c, MGHier<real> &H0, MGHier<real> &H1) {
+  const int nmax = H0.ncoarse > H1.ncoarse ? H0.ncoarse : H1.ncoarse;
+  const int smem = nmax <= DENSE_SMEM_MAX_N;
+  const size_t bytes = smem ? sizeof(real) * 2 * nmax * nmax : 0;
   if (smem && bytes > 48 * 1024)
     cudaFuncSetAttribute(k_dense_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_dense_invert<<<1, 512, bytes, c.st>>>((int)n, H.Ad, H.Ai, smem);
-  c.launches += 2;
+  k_dense_invert<<<2, 512, bytes, c.st>>>(DenseJob{H0.ncoarse, H0.Ad, H0.Ai},
+                                          DenseJob{H1.ncoarse, H1.Ad, H1.Ai}, smem);
+  UPMPM_LAUNCH(c);
 }
 
 constexpr real MG_OMEGA = 0.6;
@@ -712,9 +750,9 @@ constexpr real MG_OMEGA = 0.6;
 template <int B, int D>
 void sweep(Ctx &c, MGHier<real> &H, int l) {
   LevelDev &L = H.L[l];
-  const int nbk = nblk(L.nnodes * LN_<D>::v);
-  if (l == 0) k_mg_smooth<B, D, false><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
-  else k_mg_smooth<B, D, true><<<nbk, TPB, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+  const Geom g = geom(c, L.nnodes * LN_<D>::v);
+  if (l == 0) k_mg_smooth<B, D, false><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+  else k_mg_smooth<B, D, true><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
   UPMPM_LAUNCH(c);
   std::swap(H.x[l], H.x2[l]);
 }
@@ -725,20 +763,21 @@ void sweep(Ctx &c, MGHier<real> &H, int l) {
 template <int B, int D>
 void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
   if (l == H.nlev - 1) {  // exact solve on the coarsest grid
-    k_dense_apply<<<nblk(H.ncoarse, 64), 64, 0, c.st>>>(H.ncoarse, H.Ai, H.b[l], H.x[l]);
+    const Geom g = geom(c, (int64_t)H.ncoarse * 32);
+    k_dense_apply<<<g.blocks, g.tpb, 0, c.st>>>(H.ncoarse, H.Ai, H.b[l], H.x[l]);
     UPMPM_LAUNCH(c);
     return;
   }
   LevelDev &L = H.L[l], &Ln = H.L[l + 1];
   real *xn_first = l + 1 == H.nlev - 1 ? nullptr : H.x[l + 1];
   sweep<B, D>(c, H, l);  // second pre-smoothing sweep
-  const int nbr = nblk(L.nnodes * LN_<D>::v);
-  if (l == 0) k_mg_resid<B, D, false><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
-  else k_mg_resid<B, D, true><<<nbr, TPB, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
-  k_mg_restrict<B, D><<<nblk(Ln.nnodes), TPB, 0, c.st>>>(L, Ln, H.r[l], H.b[l + 1], xn_first, MG_OMEGA);
+  const Geom gr = geom(c, L.nnodes * LN_<D>::v), gc = geom(c, Ln.nnodes), gf = geom(c, L.nnodes);
+  if (l == 0) k_mg_resid<B, D, false><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  else k_mg_resid<B, D, true><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  k_mg_restrict<B, D><<<gc.blocks, gc.tpb, 0, c.st>>>(L, Ln, H.r[l], H.b[l + 1], xn_first, MG_OMEGA);
   c.launches += 2;
   vcycle_t<B, D>(c, H, l + 1);
-  k_mg_prolong<B, D><<<nblk(L.nnodes), TPB, 0, c.st>>>(L, Ln, H.x[l], H.x[l + 1]);
+  k_mg_prolong<B, D><<<gf.blocks, gf.tpb, 0, c.st>>>(L, Ln, H.x[l], H.x[l + 1]);
   UPMPM_LAUNCH(c);
   sweep<B, D>(c, H, l);  // first post-smoothing sweep
   sweep<B, D>(c, H, l);  // second post-smoothing sweep
@@ -906,6 +945,7 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   c.launches += 6;
   mg_setup(c, *S.mgA, c.row_ptr, c.col, S.Aval, 0);
   mg_setup(c, *S.mgS, c.row_ptr, c.col, S.Sval, d);
+  dense_invert_pair(c, *S.mgA, *S.mgS);
   return check_cuda(c, cudaGetLastError(), "schur setup");
 }
 
@@ -916,8 +956,9 @@ namespace MG_NS {
 void schur_split(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *xs0) {
   const int64_t nn = c.g.nnodes;
   MGHier<real> &HS = *S.mgS;
-  if (c.d == 2) k_split<2><<<nblk(nn), TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
-  else k_split<3><<<nblk(nn), TPB, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
+  const Geom g = geom(c, nn);
+  if (c.d == 2) k_split<2><<<g.blocks, g.tpb, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
+  else k_split<3><<<g.blocks, g.tpb, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
   UPMPM_LAUNCH(c);
 }
 
@@ -925,20 +966,22 @@ void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
   const int64_t nn = c.g.nnodes;
   MGHier<real> &HS = *S.mgS, &HA = *S.mgA;
   mg_vcycle(c, HS);
+  const Geom g = geom(c, nn * (c.d == 2 ? 8 : 16));
   if (c.d == 2)
-    k_b1c_update<2><<<nblk(nn * 8), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
-                                                     HA.x[0], HA.L[0].dinv, MG_OMEGA);
+    k_b1c_update<2><<<g.blocks, g.tpb, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
+                                                   HA.x[0], HA.L[0].dinv, MG_OMEGA);
   else
-    k_b1c_update<3><<<nblk(nn * 16), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
-                                                      HA.x[0], HA.L[0].dinv, MG_OMEGA);
+    k_b1c_update<3><<<g.blocks, g.tpb, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
+                                                   HA.x[0], HA.L[0].dinv, MG_OMEGA);
   UPMPM_LAUNCH(c);
   mg_vcycle(c, HA);
 }
 
 void schur_merge(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *zu, const MG_REAL *zp, MG_REAL *z) {
   const int64_t nn = c.g.nnodes;
-  if (c.d == 2) k_merge<2><<<nblk(nn), TPB, 0, c.st>>>(nn, zu, zp, S.dscale, z);
-  else k_merge<3><<<nblk(nn), TPB, 0, c.st>>>(nn, zu, zp, S.dscale, z);
+  const Geom g = geom(c, nn);
+  if (c.d == 2) k_merge<2><<<g.blocks, g.tpb, 0, c.st>>>(nn, zu, zp, S.dscale, z);
+  else k_merge<3><<<g.blocks, g.tpb, 0, c.st>>>(nn, zu, zp, S.dscale, z);
   UPMPM_LAUNCH(c);
 }
 }  // namespace MG_NS

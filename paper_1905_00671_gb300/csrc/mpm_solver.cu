@@ -251,28 +251,35 @@ __global__ void k_bj_apply(int64_t nnodes, const T *__restrict__ dinv, const T *
 }
 
 // ---------------------------------------------------------------- SpMV
-// NB threads per block row, thread r computing y_r of its row: it walks the
-// row's blocks in order and spends one FMA per stored value of block row r
-// (GB300's FP64 pipe is narrow: an FP64 SpMV should issue exactly one FP64
-// instruction per value, with all lanes busy and no cross-lane reduction).
-template <int NB, typename T>
+// SPL * NB threads per block row: the SPL lanes of output r of a row split the
+// row's blocks (lane l takes blocks l, l + SPL, ...) and spend one FMA per
+// stored value of block row r; one shuffle sum per output joins them.
+// (GB300's FP64 pipe is narrow: an FP64 SpMV should issue one FP64
+// instruction per value with all lanes busy; the SPL-fold split gives the SM
+// enough warps to cover the load latency.)
+template <int NB, int SPL, typename T>
 __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, const T *__restrict__ val,
                            const T *__restrict__ x, T *__restrict__ y) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = t / NB;
-  const int r = (int)(t - row * NB);
-  if (row >= nnodes) return;
+  const int64_t o = t / SPL;
+  const int part = (int)(t - o * SPL);
+  const int64_t row = o / NB;
+  const int r = (int)(o - row * NB);
   T acc = 0;
-  const int e1 = row_ptr[row + 1];
+  if (row < nnodes) {
+    const int e1 = row_ptr[row + 1];
 #pragma unroll 4
-  for (int e = row_ptr[row]; e < e1; ++e) {
-    const T *blk = val + (int64_t)e * NB * NB + r * NB;
-    const T *xb = x + (int64_t)__ldg(&col[e]) * NB;
+    for (int e = row_ptr[row] + part; e < e1; e += SPL) {
+      const T *blk = val + (int64_t)e * NB * NB + r * NB;
+      const T *xb = x + (int64_t)__ldg(&col[e]) * NB;
 #pragma unroll
-    for (int c = 0; c < NB; ++c) acc = fma(__ldg(&blk[c]), __ldg(&xb[c]), acc);
+      for (int c = 0; c < NB; ++c) acc = fma(__ldg(&blk[c]), __ldg(&xb[c]), acc);
+    }
   }
-  y[row * NB + r] = acc;
+#pragma unroll
+  for (int s = SPL / 2; s > 0; s >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, s);
+  if (row < nnodes && part == 0) y[row * NB + r] = acc;
 }
 
 // ---------------------------------------------------------------- FGMRES
@@ -397,9 +404,10 @@ __global__ void k_update_x(T *__restrict__ x, const T *__restrict__ Z, const dou
 
 template <int NB, typename T>
 void spmv(Ctx &c, const LinSys<T> &S, const T *x, T *y) {
-  const int64_t threads = c.g.nnodes * NB;
+  constexpr int SPL = NB == 3 ? 2 : 4;  // 25 (2D) / 125 (3D) blocks per GIMP row
+  const int64_t threads = c.g.nnodes * NB * SPL;
   prof_begin(c, MPM_PROF_SPMV);
-  k_bsr_spmv<NB, T><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, S.val, x, y);
+  k_bsr_spmv<NB, SPL, T><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, S.val, x, y);
   prof_end(c, MPM_PROF_SPMV);
   UPMPM_LAUNCH(c);
 }

@@ -61,7 +61,7 @@ class mpm_options(C.Structure):
                 ("newton_stag", C.c_double), ("krylov_rtol", C.c_double),
                 ("krylov_restart", C.c_int32), ("krylov_max", C.c_int32), ("precond", C.c_int32),
                 ("min_volume_fraction", C.c_double), ("profile", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("precond_lag", C.c_int32), ("stream", C.c_void_p)]
 
 
 class mpm_loads(C.Structure):

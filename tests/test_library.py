@@ -40,6 +40,7 @@ def test_default_options_without_gpu(lib):
 
     o = mpm.default_options()
     assert o.shape == mpm.MPM_SHAPE_GIMP and o.newton_rtol == 1e-8 and o.krylov_restart == 120
+    assert o.precond_lag == 2
     assert o.precond == mpm.MPM_PRECOND_SCHUR_MG
 
 
