@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-sample", type=int, default=4)
     ap.add_argument("--precond-lag", type=int, default=2,
                     help="Newton iterations served by one preconditioner set-up")
     ap.add_argument("--profile", default="spmv,orth,jacobian,point,residual,precond",
@@ -445,6 +447,108 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# --------------------------------------------------------------- batched instances
+def run_batch(args, rank, world, local_rank):
+    """Batched stepping of many independent instances (256 uneven 2D problems,
+    Terzaghi-type and footing-type alternating): the two kinds (different
+    shape functions, time scheme and step) are two batched contexts; one timed
+    step advances every instance once, in mixed precision and in FP64.  Beside
+    it, a sample of the instances stepped one at a time in FP64 (each its own
+    context), extrapolated to all instances by kind."""
+    import numpy as np
+    import torch
+
+    from paper_1905_00671_gb300 import build as B
+    from paper_1905_00671_gb300 import inputs as I
+    from paper_1905_00671_gb300 import mpm
+
+    torch.cuda.set_device(local_rank)
+    if not B.up_to_date():
+        B.build()
+    mpm.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ws = I.batch_instances(count=args.batch_count, seed=5)
+    kinds = {"terzaghi": [w for w in ws if w.name.startswith("terzaghi")],
+             "footing": [w for w in ws if w.name.startswith("footing")]}
+    npts = sum(w.n for w in ws)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(precision):
+        bs = [mpm.Batch(v, stream=stream.cuda_stream, precision=precision, newton_max=60)
+              for v in kinds.values() if v]
+        for _ in range(args.warmup):
+            for b in bs:
+                b.step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ms = 0.0
+        newton = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0.record(stream)
+            for b in bs:
+                newton.append(b.step()["newton_iters"])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        out = [b.read(("u", "p")) for b in bs]
+        for b in bs:
+            b.close()
+        return ms, newton, out
+
+    ms_mixed, newton_mixed, res_mixed = timed(mpm.MPM_MIXED)
+    ms_fp64, newton_fp64, res_fp64 = timed(mpm.MPM_FP64)
+    # one at a time, FP64: a sample of each kind, same number of steps
+    sample = {k: v[:args.batch_sample] for k, v in kinds.items() if v}
+    per_kind_ms = {}
+    errs = []
+    for ki, (k, v) in enumerate(sample.items()):
+        tot = 0.0
+        for j, w in enumerate(v):
+            sim = mpm.Simulation(w, stream=stream.cuda_stream, newton_max=60)
+            for _ in range(args.warmup):
+                sim.step(resident=True)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            for _ in range(args.steps):
+                e0.record(stream)
+                sim.step(resident=True)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            ref = sim.read(("u", "p"))
+            kidx = list(kinds).index(k)
+            got = res_mixed[kidx][j]
+            errs.append(max(float(np.abs(got[f] - ref[f]).max() / max(np.abs(ref[f]).max(), 1e-300))
+                            for f in ("u", "p")))
+            sim.close()
+        per_kind_ms[k] = tot / len(v)          # per instance, all timed steps
+    one_ms = sum(per_kind_ms[k] * len(kinds[k]) for k in per_kind_ms)
+    value = npts * args.steps / (ms_mixed * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_mixed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 solve / f64 Newton residual",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"batch-{len(ws)}: independent 2D instances 16-128 x 32-64 cells, "
+                                   "Terzaghi-type (original MPM, quasi-static, dt 1 s) and footing-type "
+                                   "(GIMP, Newmark, dt 1e-3 s) alternating, 2x2 points per cell",
+                       "instances": len(ws), "points": npts, "contexts": len(sample),
+                       "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas x1"},
+            "newton_iters_per_context_step": float(np.mean(newton_mixed)),
+            "fp64_batched": {"value": npts * args.steps / (ms_fp64 * 1e-3), "unit": UNIT,
+                             "ms_per_step": ms_fp64 / args.steps,
+                             "newton_iters_per_context_step": float(np.mean(newton_fp64))},
+            "one_by_one_fp64": {"value": npts * args.steps / (one_ms * 1e-3), "unit": UNIT,
+                                "ms_per_step": one_ms / args.steps,
+                                "sample": f"{sum(len(v) for v in sample.values())} instances stepped alone "
+                                          "(first of each kind), extrapolated per kind to all instances",
+                                "max_rel_error_of_batched_mixed": max(errs) if errs else None}}
+    return line
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -460,6 +564,11 @@ def main():
 
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
+    if args.workload == "batch":
+        line = run_batch(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     line, w = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:

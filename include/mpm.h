@@ -62,6 +62,17 @@ enum { MPM_FP64 = 0, MPM_MIXED = 1 };
  * complement (default). */
 enum { MPM_PRECOND_BLOCK_JACOBI = 0, MPM_PRECOND_SCHUR_MG = 1 };
 
+/* Approximation of the pressure Schur complement S = C - B2 A^{-1} B1 inside
+ * the Schur preconditioner.  DIAG_A: C - B2 diag(A)^{-1} B1 kept on the
+ * Jacobian's sparsity (fill lumped to the diagonal); good when A is dominated
+ * by the Newmark mass term.  FIXED_STRESS: C plus the lumped pressure mass
+ * sum_p S_ip b2_p vol_p / (cs_p K_p) on the diagonal, K = lambda + 2 (G -
+ * lambda ln J) / dim the drained bulk modulus (the volumetric part of A
+ * replaced by its bulk stiffness); robust in the quasi-static, near-undrained
+ * limit.  AUTO (default): FIXED_STRESS for quasi-static steps, DIAG_A for
+ * Newmark. */
+enum { MPM_SCHUR_AUTO = 0, MPM_SCHUR_DIAG_A = 1, MPM_SCHUR_FIXED_STRESS = 2 };
+
 /* Kernel classes that mpm_options.profile can time with CUDA events (bit k of
  * the mask selects class k; mpm_stats.prof_ms[k] / prof_launches[k]). */
 enum {
@@ -153,6 +164,7 @@ typedef struct {
                                  in between, with the current diagonal scaling).
                                  Changes Krylov iteration counts only: the Newton
                                  test is on the exact residual. */
+  int32_t schur_approx;       /* MPM_SCHUR_* (default AUTO) */
   void *stream;               /* cudaStream_t for all work; NULL = default stream */
 } mpm_options;
 
@@ -229,6 +241,15 @@ int mpm_step(mpm_ctx *ctx, double dt, const mpm_loads *loads, const mpm_bcs *bcs
 /* Copies the point state into caller-owned host buffers (original order). */
 int mpm_read(const mpm_ctx *ctx, mpm_particles_out *out);
 
+/* Checkpoint / resume.  All state that persists between steps lives on the
+ * material points (the grid is reset every step, Sec. 3.5), so a checkpoint
+ * is mpm_read of every field of mpm_particles_out.  mpm_restore writes such a
+ * state (caller's original point order) back into a context created with the
+ * same initial configuration, and sets its time and step count; stepping on
+ * with the same loads and boundary conditions then repeats the original run.
+ * NULL fields are left as they are. */
+int mpm_restore(mpm_ctx *ctx, const mpm_particles_out *state, double t, int64_t steps);
+
 int mpm_get_stats(const mpm_ctx *ctx, mpm_stats *stats);
 
 /* Human-readable description of the last error on ctx (never NULL). */
@@ -236,6 +257,45 @@ const char *mpm_last_error(const mpm_ctx *ctx);
 
 /* Frees the context and all its device memory.  NULL is a no-op. */
 void mpm_destroy(mpm_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Batched instances.  The paper steps one problem at a time; these calls step
+ * many independent problems together (same dim, cell size h, options, time
+ * step and material constants rho_s, rho_f, phi0, mu_f, alpha_vis, g; each
+ * with its own grid, points, per-point E, nu and permeability, loads and
+ * boundary conditions).  The instance grids are laid out on one background
+ * grid of the context, at least MPM_BATCH_GAP empty cells apart, so every
+ * kernel of a step runs once over all instances.  Each point keeps the
+ * coordinates of its own grid and its GIMP domain is clipped by its own grid
+ * (Sec. 3.1 as for a single problem), so no support reaches another instance:
+ * the instances never couple through the discrete equations.  Newton
+ * continues until every instance meets the residual test of
+ * Eq. newton-tolerance on its own residual; the FGMRES solve and its
+ * preconditioner act on all instances at once.
+ * ---------------------------------------------------------------------- */
+#define MPM_BATCH_GAP 2
+
+/* Layout of count instance grids on one background grid (no GPU needed):
+ * offsets[3*i + k] = cell offset of instance i along axis k (the instance's
+ * node (a, b, c) becomes node (a, b, c) + offset); ncell = cells per axis of
+ * the background grid.  Instances are placed on shelves of width about
+ * sqrt(total area), tallest first; all grids must share dim and h. */
+int mpm_batch_pack(int32_t count, const mpm_grid *grids, int32_t *offsets, int32_t *ncell);
+
+/* Creates a context holding count instances (arrays of count entries;
+ * permeability[i] has particles[i].n values).  mpm_read then returns the
+ * points of all instances in order (instance 0's points first, each in its
+ * instance's original order and coordinates); mpm_get_stats reports the
+ * whole batch. */
+int mpm_create_batch(int32_t count, const mpm_grid *grids, const mpm_particles *particles,
+                     const mpm_material *materials, const double *const *permeability,
+                     const mpm_options *options, mpm_ctx **out);
+
+/* One load step of every instance.  loads / bcs: count entries each (or NULL
+ * to keep all previous data); inside an entry, a NULL array keeps that
+ * instance's previous values.  Node arrays of bcs[i] refer to instance i's own
+ * grid numbering. */
+int mpm_step_batch(mpm_ctx *ctx, double dt, const mpm_loads *loads, const mpm_bcs *bcs);
 
 /* ------------------------------------------------------------------------
  * Inspection entry points.  They expose the intermediate results of one step

@@ -50,6 +50,7 @@ DevView Ctx::view() const {
   v.trac = trac;
   v.flux = has_flux ? flux : nullptr;
   v.err = err;
+  v.inst = inst;
   return v;
 }
 
@@ -134,7 +135,7 @@ __global__ void k_init(int64_t n, double *pf, const double *__restrict__ x, cons
                        const double *__restrict__ v0, const double *__restrict__ E,
                        const double *__restrict__ nu, const double *__restrict__ k,
                        const double *__restrict__ sn, const double *__restrict__ sa, double mu_f,
-                       double tau_scale, int stabilize, int64_t *pid) {
+                       double tau_scale, int stabilize, int64_t *pid, const int32_t *__restrict__ pinst) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   for (int f = 0; f < PF_COUNT; ++f) pf[f * n + p] = 0.0;
@@ -156,7 +157,31 @@ __global__ void k_init(int64_t n, double *pf, const double *__restrict__ x, cons
   pf[PF_KAP * n + p] = k[p] / mu_f;
   pf[PF_TAU * n + p] = stabilize ? tau_scale / (2.0 * G) : 0.0;
   pf[PF_SA * n + p] = sa ? sa[p] : 0.0;
+  pf[PF_INST * n + p] = pinst ? (double)pinst[p] : 0.0;
   pid[p] = p;
+}
+
+// Per-instance squared residual norms: block i sums R^2 over the nodes of
+// instance i's grid (a fixed order, so the sums are run-to-run identical).
+__global__ void k_inst_norm(GridP g, int nb, const InstDev *__restrict__ inst, const double *__restrict__ R,
+                            double *__restrict__ out) {
+  __shared__ double part[256];
+  const InstDev I = inst[blockIdx.x];
+  const int64_t m0 = I.nc[0] + 1, m1 = g.d > 1 ? I.nc[1] + 1 : 1, m2 = g.d > 2 ? I.nc[2] + 1 : 1;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < m0 * m1 * m2; t += blockDim.x) {
+    const int64_t i0 = t % m0, i1 = (t / m0) % m1, i2 = t / (m0 * m1);
+    const int c3[3] = {(int)i0 + I.off[0], (int)i1 + I.off[1], (int)i2 + I.off[2]};
+    const int64_t a = node_index(g, c3);
+    for (int k = 0; k < nb; ++k) acc += R[a * nb + k] * R[a * nb + k];
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = part[0];
 }
 
 __global__ void k_scale_trac(int64_t m, const double *__restrict__ raw, double s, double *__restrict__ out) {
@@ -171,6 +196,15 @@ __global__ void k_read_field(int64_t n, const double *__restrict__ pf, int f0, i
   if (i >= n) return;
   const int64_t o = pid[i];
   for (int c = 0; c < comps; ++c) out[o * comps + c] = pf[(int64_t)(f0 + c) * n + i];
+}
+
+// scatter field f (comps components) from original point order
+__global__ void k_write_field(int64_t n, double *__restrict__ pf, int f0, int comps,
+                              const int64_t *__restrict__ pid, const double *__restrict__ in) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t o = pid[i];
+  for (int c = 0; c < comps; ++c) pf[(int64_t)(f0 + c) * n + i] = in[o * comps + c];
 }
 
 __global__ void k_read_cells(int64_t n, const int32_t *__restrict__ cell, const int64_t *__restrict__ pid,
@@ -254,7 +288,12 @@ int eval_residual(Ctx &c, double *rnorm) {
   int rc = read_dev_err(c);
   if (rc) return rc;
   run_residual(c, c.X, c.R, 1);
-  *rnorm = run_norm(c, c.R);
+  if (c.ninst > 1) {  // per-instance norms (h_inorm) for the Newton test
+    k_inst_norm<<<c.ninst, 256, 0, c.st>>>(c.g, c.nb, c.inst, c.R, c.inorm);
+    UPMPM_LAUNCH(c);
+    cudaMemcpyAsync(c.h_inorm, c.inorm, sizeof(double) * c.ninst, cudaMemcpyDeviceToHost, c.st);
+  }
+  *rnorm = run_norm(c, c.R);  // synchronises
   if (!isfinite(*rnorm)) {
     c.last_error = "non-finite residual";
     return MPM_ERR_NONFINITE;
@@ -281,6 +320,18 @@ int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
     run_scale_system<T>(c, S, c.R);
     run_block_jacobi<T>(c, S);
   }
+  // batched instances: each instance's right-hand side is weighted by the
+  // inverse of its residual norm, so that the one relative Krylov tolerance
+  // applies to every instance alike (the system is block diagonal over the
+  // instances: the weighted solution is the weighted exact one)
+  if (c.ninst > 1) {
+    for (int i = 0; i < c.ninst; ++i) {
+      const double r = sqrt(c.h_inorm[i]);
+      c.h_iw[i] = r > 0.0 ? 1.0 / r : 1.0;
+    }
+    cudaMemcpyAsync(c.iw, c.h_iw, sizeof(double) * c.ninst, cudaMemcpyHostToDevice, c.st);
+    run_inst_weight<T>(c, S.rhs, 0);
+  }
   rc = read_dev_err(c);
   if (rc) return rc;
   const bool inexact = sizeof(T) < sizeof(double);
@@ -292,6 +343,7 @@ int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
     else if (rc == MPM_ERR_NONFINITE) c.last_error = "non-finite value in FGMRES";
     return rc;
   }
+  if (c.ninst > 1) run_inst_weight<T>(c, S.x, 1);
   run_unscale_add<T>(c, S, c.X);
   return MPM_OK;
 }
@@ -306,10 +358,34 @@ int newton(Ctx &c) {
   const double r0 = rk;
   st.res_norm[0] = r0;
   double prev = r0;
+  // batched contexts: every instance meets its own test (on its own norms);
+  // an instance that has met it stays accepted while the others iterate
+  const int ni = c.ninst;
+  std::vector<double> ri0, riprev, ri;
+  std::vector<char> accepted;
+  if (ni > 1) {
+    ri.resize(ni);
+    for (int i = 0; i < ni; ++i) ri[i] = sqrt(c.h_inorm[i]);
+    ri0 = ri;
+    riprev = ri;
+    accepted.assign(ni, 0);
+  }
+  auto done = [&](double r, double rp, double rz, int kk) {
+    if (rz == 0.0 || r <= c.opt.newton_rtol * rz) return true;
+    return c.opt.newton_stag > 0.0 && kk >= 2 && rp <= c.opt.newton_stag * rz && r > 0.5 * rp;
+  };
   int k = 0;
   while (true) {
-    if (r0 == 0.0 || rk <= c.opt.newton_rtol * r0) break;
-    if (c.opt.newton_stag > 0.0 && k >= 2 && prev <= c.opt.newton_stag * r0 && rk > 0.5 * prev) break;
+    if (ni > 1) {
+      bool all = true;
+      for (int i = 0; i < ni; ++i) {
+        if (!accepted[i] && done(ri[i], riprev[i], ri0[i], k)) accepted[i] = 1;
+        all = all && accepted[i];
+      }
+      if (all) break;
+    } else if (done(rk, prev, r0, k)) {
+      break;
+    }
     if (k >= c.opt.newton_max || k >= MPM_MAX_NEWTON) {
       c.last_error = "Newton did not reach the residual tolerance";
       return MPM_ERR_NEWTON_DIVERGED;
@@ -322,6 +398,10 @@ int newton(Ctx &c) {
     prev = rk;
     rc = eval_residual(c, &rk);
     if (rc) return rc;
+    if (ni > 1) {
+      riprev = ri;
+      for (int i = 0; i < ni; ++i) ri[i] = sqrt(c.h_inorm[i]);
+    }
     ++k;
     st.res_norm[k] = rk;
     st.newton_iters = k;
@@ -367,12 +447,14 @@ void free_all(Ctx &c) {
     if (p) cudaFree(p);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
                   c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS,
-                  c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.sh_nrm, c.fixed, c.u_fixed,
+                  c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.fsd, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
-                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp, c.terms};
+                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp, c.terms, c.inst, c.inorm, c.iw, c.node_inst};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+  if (c.h_inorm) cudaFreeHost(c.h_inorm);
+  if (c.h_iw) cudaFreeHost(c.h_iw);
   if (c.h_err) cudaFreeHost(c.h_err);
   if (c.h_scalar) cudaFreeHost(c.h_scalar);
   if (c.h_terms) cudaFreeHost(c.h_terms);
@@ -389,33 +471,16 @@ struct mpm_ctx {
   Ctx c;
 };
 
-extern "C" {
+namespace upmpm {
+namespace {
 
-void mpm_default_options(mpm_options *o) {
-  if (!o) return;
-  memset(o, 0, sizeof(*o));
-  o->shape = MPM_SHAPE_GIMP;
-  o->scheme = MPM_QUASISTATIC;
-  o->beta = 0.3025;
-  o->gamma = 0.6;
-  o->stabilize = 1;
-  o->tau_scale = 1.0;
-  o->precision = MPM_FP64;
-  o->newton_rtol = 1e-8;
-  o->newton_max = 25;
-  o->newton_stag = 0.0;
-  o->krylov_rtol = 1e-8;
-  o->krylov_restart = 120;
-  o->krylov_max = 3000;
-  o->precond = MPM_PRECOND_SCHUR_MG;
-  o->min_volume_fraction = 1e-4;
-  o->profile = 0;
-  o->precond_lag = 2;
-  o->stream = nullptr;
-}
-
-int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material *mat,
-               const double *permeability, const mpm_options *opt, mpm_ctx **out) {
+// The context of one or several instances: grid is the background grid of the
+// context, P / mat / permeability the points of all instances (instance-major,
+// each in its own grid's coordinates), insts the instance table and pinst the
+// instance of every point (NULL: all instance 0).
+int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material *mat,
+                const double *permeability, const mpm_options *opt, const std::vector<InstDev> &insts,
+                const int32_t *pinst, mpm_ctx **out) {
   if (!out) return MPM_ERR_BAD_ARG;
   *out = nullptr;
   if (!grid || !P || !mat || !permeability || !opt) return MPM_ERR_BAD_ARG;
@@ -427,6 +492,7 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   if (P->n > INT32_MAX / 2) return MPM_ERR_BAD_ARG;
   if (opt->krylov_restart < 1 || opt->krylov_restart > 128) return MPM_ERR_BAD_ARG;
   if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON) return MPM_ERR_BAD_ARG;
+  if (opt->schur_approx < MPM_SCHUR_AUTO || opt->schur_approx > MPM_SCHUR_FIXED_STRESS) return MPM_ERR_BAD_ARG;
   if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
     return MPM_ERR_BAD_ARG;
   if (opt->precision != MPM_FP64 && opt->precision != MPM_MIXED) return MPM_ERR_BAD_ARG;
@@ -495,6 +561,8 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   for (int k = 0; k < 3; ++k) s.g[k] = k < c.d ? mat->g[k] : 0.0;
   c.n = P->n;
   c.n_surf = P->n_surf;
+  c.ninst = (int)insts.size();
+  c.inst_h = insts;
 
   const int64_t n = c.n, nn = g.nnodes, nc = g.ncells, N = (int64_t)c.nb * nn;
   const int d = c.d, nb = c.nb, m = c.m_restart;
@@ -529,6 +597,7 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   A(&c.pddn, nn);
   A(&c.phi, nn);
   A(&c.act, nn);
+  A(&c.fsd, nn);
   A(&c.sh_nrm, 5 * n);
   A(&c.fixed, N);
   A(&c.u_fixed, d * nn);
@@ -577,10 +646,31 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
               cudaHostAlloc((void **)&c.h_terms, 2 * sizeof(unsigned long long), cudaHostAllocDefault) !=
                   cudaSuccess))
     rc = MPM_ERR_NO_MEMORY;
+  A(&c.inst, c.ninst);
+  A(&c.inorm, c.ninst);
+  A(&c.iw, c.ninst);
+  A(&c.node_inst, nn);
+  if (!rc && (cudaHostAlloc((void **)&c.h_inorm, sizeof(double) * c.ninst, cudaHostAllocDefault) != cudaSuccess ||
+              cudaHostAlloc((void **)&c.h_iw, sizeof(double) * c.ninst, cudaHostAllocDefault) != cudaSuccess))
+    rc = MPM_ERR_NO_MEMORY;
   if (rc) {
     free_all(c);
     delete h;
     return rc;
+  }
+  cudaMemcpyAsync(c.inst, c.inst_h.data(), sizeof(InstDev) * c.ninst, cudaMemcpyHostToDevice, c.st);
+  {  // instance of every node (node boxes of the instances; -1 between them)
+    std::vector<int32_t> ni(nn, -1);
+    for (int i = 0; i < c.ninst; ++i) {
+      const InstDev &I = c.inst_h[i];
+      const int64_t m0 = I.nc[0] + 1, m1 = d > 1 ? I.nc[1] + 1 : 1, m2 = d > 2 ? I.nc[2] + 1 : 1;
+      for (int64_t t = 0; t < m0 * m1 * m2; ++t) {
+        const int64_t i0 = t % m0, i1 = (t / m0) % m1, i2 = t / (m0 * m1);
+        ni[(i0 + I.off[0]) + (int64_t)g.nn[0] * ((i1 + I.off[1]) + (int64_t)g.nn[1] * (i2 + I.off[2]))] = i;
+      }
+    }
+    cudaMemcpyAsync(c.node_inst, ni.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice, c.st);
+    cudaStreamSynchronize(c.st);  // ni is a host temporary
   }
   cudaMemsetAsync(c.err, 0, sizeof(int), c.st);
   cudaMemsetAsync(c.row_nnz, 0, sizeof(int32_t) * (nn + 1), c.st);  // [nn] stays 0 for the scan
@@ -599,7 +689,7 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
 
   // stage the inputs on the device (temporary buffers), then initialise
   double *tmp = nullptr;
-  const int64_t tcount = n * (4 * d + 7);
+  const int64_t tcount = n * (4 * d + 7) + (n + 1) / 2;  // + instance ids (int32)
   rc = dalloc(c, &tmp, tcount);
   if (rc) {
     free_all(c);
@@ -621,6 +711,8 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   H2D(dk, permeability, n);
   H2D(dsn, P->surf_normal, n * d);
   H2D(dsa, P->surf_area, n);
+  int32_t *dinst = reinterpret_cast<int32_t *>(dsa + n);
+  if (pinst) cudaMemcpyAsync(dinst, pinst, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c.st);
   if (P->surf_id)
     cudaMemcpyAsync(c.surf, P->surf_id, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c.st);
   else
@@ -629,12 +721,14 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
     k_init<2><<<nblk(n), TPB, 0, c.st>>>(n, c.pf, dx, dvol, dlp, P->p0 ? dp0 : nullptr,
                                           P->v0 ? dv0 : nullptr, dE, dnu, dk,
                                           P->surf_normal ? dsn : nullptr, P->surf_area ? dsa : nullptr,
-                                          mat->mu_f, c.tau_scale, c.stabilize, c.pid);
+                                          mat->mu_f, c.tau_scale, c.stabilize, c.pid,
+                                          pinst ? dinst : nullptr);
   else
     k_init<3><<<nblk(n), TPB, 0, c.st>>>(n, c.pf, dx, dvol, dlp, P->p0 ? dp0 : nullptr,
                                           P->v0 ? dv0 : nullptr, dE, dnu, dk,
                                           P->surf_normal ? dsn : nullptr, P->surf_area ? dsa : nullptr,
-                                          mat->mu_f, c.tau_scale, c.stabilize, c.pid);
+                                          mat->mu_f, c.tau_scale, c.stabilize, c.pid,
+                                          pinst ? dinst : nullptr);
   cudaError_t e = cudaStreamSynchronize(c.st);
   cudaFree(tmp);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -646,6 +740,252 @@ int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material 
   }
   *out = h;
   return MPM_OK;
+}
+
+}  // namespace
+}  // namespace upmpm
+
+
+extern "C" {
+
+void mpm_default_options(mpm_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->shape = MPM_SHAPE_GIMP;
+  o->scheme = MPM_QUASISTATIC;
+  o->beta = 0.3025;
+  o->gamma = 0.6;
+  o->stabilize = 1;
+  o->tau_scale = 1.0;
+  o->precision = MPM_FP64;
+  o->newton_rtol = 1e-8;
+  o->newton_max = 25;
+  o->newton_stag = 0.0;
+  o->krylov_rtol = 1e-8;
+  o->krylov_restart = 120;
+  o->krylov_max = 3000;
+  o->precond = MPM_PRECOND_SCHUR_MG;
+  o->min_volume_fraction = 1e-4;
+  o->profile = 0;
+  o->precond_lag = 2;
+  o->schur_approx = MPM_SCHUR_AUTO;
+  o->stream = nullptr;
+}
+
+int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material *mat,
+               const double *permeability, const mpm_options *opt, mpm_ctx **out) {
+  if (!out) return MPM_ERR_BAD_ARG;
+  *out = nullptr;
+  if (!grid) return MPM_ERR_BAD_ARG;
+  InstDev one{};
+  for (int k = 0; k < 3; ++k) {
+    const bool used = k < grid->dim;
+    one.org[k] = used ? grid->origin[k] : 0.0;
+    one.off[k] = 0;
+    one.nc[k] = used ? grid->ncell[k] : 1;
+  }
+  return create_impl(grid, P, mat, permeability, opt, std::vector<InstDev>{one}, nullptr, out);
+}
+
+// ---- batched instances
+int mpm_batch_pack(int32_t count, const mpm_grid *grids, int32_t *offsets, int32_t *ncell) {
+  if (count < 1 || !grids || !offsets || !ncell) return MPM_ERR_BAD_ARG;
+  const int d = grids[0].dim;
+  if (d != 2 && d != 3) return MPM_ERR_BAD_ARG;
+  double area = 0.0;
+  int32_t wmax = 0, zmax = 1;
+  for (int i = 0; i < count; ++i) {
+    const mpm_grid &g = grids[i];
+    if (g.dim != d || !(g.h > 0.0) || g.h != grids[0].h) return MPM_ERR_BAD_ARG;
+    for (int k = 0; k < d; ++k)
+      if (g.ncell[k] < 1 || g.ncell[k] > (1 << 20)) return MPM_ERR_BAD_ARG;
+    area += (double)(g.ncell[0] + MPM_BATCH_GAP) * (double)(g.ncell[1] + MPM_BATCH_GAP);
+    wmax = std::max(wmax, g.ncell[0]);
+    if (d == 3) zmax = std::max(zmax, g.ncell[2]);
+  }
+  // shelves of width W ~ sqrt(total area): tallest instances first, left to
+  // right, at least MPM_BATCH_GAP empty cells between neighbours
+  const int64_t W = std::max<int64_t>((int64_t)ceil(sqrt(area)), wmax);
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (grids[a].ncell[1] != grids[b].ncell[1]) return grids[a].ncell[1] > grids[b].ncell[1];
+    return grids[a].ncell[0] > grids[b].ncell[0];
+  });
+  int64_t x = 0, y = 0, shelf = 0, xmax = 0;
+  for (int i : order) {
+    const int64_t nx = grids[i].ncell[0], ny = grids[i].ncell[1];
+    if (x > 0 && x + nx > W) {
+      y += shelf + MPM_BATCH_GAP;
+      x = 0;
+      shelf = 0;
+    }
+    offsets[3 * i + 0] = (int32_t)x;
+    offsets[3 * i + 1] = (int32_t)y;
+    offsets[3 * i + 2] = 0;
+    xmax = std::max(xmax, x + nx);
+    x += nx + MPM_BATCH_GAP;
+    shelf = std::max(shelf, ny);
+  }
+  const int64_t ny_all = y + shelf;
+  if (xmax > INT32_MAX / 4 || ny_all > INT32_MAX / 4) return MPM_ERR_BAD_ARG;
+  ncell[0] = (int32_t)xmax;
+  ncell[1] = (int32_t)ny_all;
+  ncell[2] = d == 3 ? zmax : 1;
+  return MPM_OK;
+}
+
+int mpm_create_batch(int32_t count, const mpm_grid *grids, const mpm_particles *parts,
+                     const mpm_material *mats, const double *const *permeability, const mpm_options *opt,
+                     mpm_ctx **out) {
+  if (!out) return MPM_ERR_BAD_ARG;
+  *out = nullptr;
+  if (count < 1 || !grids || !parts || !mats || !permeability || !opt) return MPM_ERR_BAD_ARG;
+  std::vector<int32_t> offs(3 * (size_t)count);
+  mpm_grid big{};
+  int rc = mpm_batch_pack(count, grids, offs.data(), big.ncell);
+  if (rc) return rc;
+  const int d = grids[0].dim;
+  big.dim = d;
+  big.h = grids[0].h;
+  // the material constants are shared; E, nu and k are per point
+  const mpm_material &m0 = mats[0];
+  for (int i = 1; i < count; ++i) {
+    const mpm_material &m = mats[i];
+    if (m.rho_s != m0.rho_s || m.rho_f != m0.rho_f || m.phi0 != m0.phi0 || m.mu_f != m0.mu_f ||
+        m.alpha_vis != m0.alpha_vis || m.g[0] != m0.g[0] || m.g[1] != m0.g[1] || m.g[2] != m0.g[2])
+      return MPM_ERR_BAD_ARG;
+  }
+  int64_t n = 0;
+  int32_t nsurf = 0;
+  bool any_p0 = false, any_v0 = false, any_surf = false;
+  for (int i = 0; i < count; ++i) {
+    const mpm_particles &P = parts[i];
+    if (P.n <= 0 || !P.x || !P.vol || !P.lp || !mats[i].E || !mats[i].nu || !permeability[i])
+      return MPM_ERR_BAD_ARG;
+    if (P.n_surf < 0 || (P.n_surf > 0 && (!P.surf_id || !P.surf_normal || !P.surf_area)))
+      return MPM_ERR_BAD_ARG;
+    if (P.surf_id)
+      for (int64_t j = 0; j < P.n; ++j)
+        if (P.surf_id[j] < -1 || P.surf_id[j] >= P.n_surf) return MPM_ERR_BAD_ARG;
+    n += P.n;
+    nsurf += P.n_surf;
+    any_p0 |= P.p0 != nullptr;
+    any_v0 |= P.v0 != nullptr;
+    any_surf |= P.n_surf > 0;
+  }
+  if (n > INT32_MAX / 2) return MPM_ERR_BAD_ARG;
+  std::vector<double> x(n * d), vol(n), lp(n * d), p0(any_p0 ? n : 0), v0(any_v0 ? n * d : 0), E(n), nu(n), k(n),
+      sn(any_surf ? n * d : 0), sa(any_surf ? n : 0);
+  std::vector<int32_t> sid(n, -1), pinst(n);
+  std::vector<InstDev> insts(count);
+  int64_t at = 0;
+  int32_t sbase = 0;
+  for (int i = 0; i < count; ++i) {
+    const mpm_particles &P = parts[i];
+    const int64_t ni = P.n;
+    std::copy(P.x, P.x + ni * d, x.begin() + at * d);
+    std::copy(P.vol, P.vol + ni, vol.begin() + at);
+    std::copy(P.lp, P.lp + ni * d, lp.begin() + at * d);
+    if (P.p0) std::copy(P.p0, P.p0 + ni, p0.begin() + at);
+    if (P.v0) std::copy(P.v0, P.v0 + ni * d, v0.begin() + at * d);
+    std::copy(mats[i].E, mats[i].E + ni, E.begin() + at);
+    std::copy(mats[i].nu, mats[i].nu + ni, nu.begin() + at);
+    std::copy(permeability[i], permeability[i] + ni, k.begin() + at);
+    if (P.n_surf > 0) {
+      std::copy(P.surf_normal, P.surf_normal + ni * d, sn.begin() + at * d);
+      std::copy(P.surf_area, P.surf_area + ni, sa.begin() + at);
+      for (int64_t j = 0; j < ni; ++j) sid[at + j] = P.surf_id[j] < 0 ? -1 : P.surf_id[j] + sbase;
+    }
+    std::fill(pinst.begin() + at, pinst.begin() + at + ni, i);
+    InstDev &I = insts[i];
+    for (int a = 0; a < 3; ++a) {
+      const bool used = a < d;
+      I.org[a] = used ? grids[i].origin[a] : 0.0;
+      I.off[a] = used ? offs[3 * i + a] : 0;
+      I.nc[a] = used ? grids[i].ncell[a] : 1;
+    }
+    at += ni;
+    sbase += P.n_surf;
+  }
+  mpm_particles all{};
+  all.n = n;
+  all.x = x.data();
+  all.vol = vol.data();
+  all.lp = lp.data();
+  all.p0 = any_p0 ? p0.data() : nullptr;
+  all.v0 = any_v0 ? v0.data() : nullptr;
+  all.surf_id = any_surf ? sid.data() : nullptr;
+  all.surf_normal = any_surf ? sn.data() : nullptr;
+  all.surf_area = any_surf ? sa.data() : nullptr;
+  all.n_surf = nsurf;
+  mpm_material mat = m0;
+  mat.E = E.data();
+  mat.nu = nu.data();
+  rc = create_impl(&big, &all, &mat, k.data(), opt, insts, pinst.data(), out);
+  if (rc) return rc;
+  Ctx &c = (*out)->c;
+  const int64_t nn = c.g.nnodes;
+  for (int i = 0; i < count; ++i) {
+    c.inst_n.push_back(parts[i].n);
+    c.inst_nsurf.push_back(parts[i].n_surf);
+  }
+  c.b_trac.assign((size_t)nsurf * d, 0.0);
+  c.b_flux.assign(nsurf, 0.0);
+  c.b_ufix.assign((size_t)nn * d, 0);
+  c.b_uval.assign((size_t)nn * d, 0.0);
+  c.b_pfix.assign(nn, 0);
+  c.b_pval.assign(nn, 0.0);
+  return MPM_OK;
+}
+
+int mpm_step_batch(mpm_ctx *h, double dt, const mpm_loads *loads, const mpm_bcs *bcs) {
+  if (!h) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  const int d = c.d, ni = c.ninst;
+  if ((int)c.inst_n.size() != ni) return MPM_ERR_BAD_ARG;  // not a batched context
+  mpm_loads L{};
+  if (loads) {
+    int64_t sb = 0;
+    for (int i = 0; i < ni; ++i) {
+      const int64_t ns = c.inst_nsurf[i];
+      const mpm_loads &li = loads[i];
+      if (li.traction)
+        for (int64_t j = 0; j < ns * d; ++j) c.b_trac[sb * d + j] = li.scale * li.traction[j];
+      if (li.flux) {
+        for (int64_t j = 0; j < ns; ++j) c.b_flux[sb + j] = li.flux[j];
+        c.b_has_flux = true;
+      }
+      sb += ns;
+    }
+    L.traction = c.b_trac.data();
+    L.flux = c.b_has_flux ? c.b_flux.data() : nullptr;
+    L.scale = 1.0;
+  }
+  mpm_bcs B{};
+  if (bcs) {
+    const GridP &g = c.g;
+    for (int i = 0; i < ni; ++i) {
+      const InstDev &I = c.inst_h[i];
+      const mpm_bcs &bi = bcs[i];
+      const int64_t m0 = I.nc[0] + 1, m1 = d > 1 ? I.nc[1] + 1 : 1, m2 = d > 2 ? I.nc[2] + 1 : 1;
+      for (int64_t t = 0; t < m0 * m1 * m2; ++t) {
+        const int64_t i0 = t % m0, i1 = (t / m0) % m1, i2 = t / (m0 * m1);
+        const int64_t a = (i0 + I.off[0]) + (int64_t)g.nn[0] * ((i1 + I.off[1]) + (int64_t)g.nn[1] * (i2 + I.off[2]));
+        for (int k = 0; k < d; ++k) {
+          if (bi.u_fixed) c.b_ufix[a * d + k] = bi.u_fixed[t * d + k];
+          if (bi.u_value) c.b_uval[a * d + k] = bi.u_value[t * d + k];
+        }
+        if (bi.p_fixed) c.b_pfix[a] = bi.p_fixed[t];
+        if (bi.p_value) c.b_pval[a] = bi.p_value[t];
+      }
+    }
+    B.u_fixed = c.b_ufix.data();
+    B.u_value = c.b_uval.data();
+    B.p_fixed = c.b_pfix.data();
+    B.p_value = c.b_pval.data();
+  }
+  return do_step(c, dt, loads ? &L : nullptr, bcs ? &B : nullptr);
 }
 
 int mpm_step(mpm_ctx *h, double dt, const mpm_loads *loads, const mpm_bcs *bcs) {
@@ -672,6 +1012,32 @@ int mpm_read(const mpm_ctx *hc, mpm_particles_out *o) {
     if (e != cudaSuccess) return check_cuda(c, e, "read");
   }
   return check_cuda(c, cudaGetLastError(), "read");
+}
+
+int mpm_restore(mpm_ctx *h, const mpm_particles_out *st, double t, int64_t steps) {
+  if (!h || !st || !(t >= 0.0) || steps < 0) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  const int64_t n = c.n;
+  const int d = c.d;
+  struct Item {
+    const double *src;
+    int f0, comps;
+  } items[] = {{st->x, PF_X, d}, {st->u, PF_U, d}, {st->p, PF_P, 1}, {st->v, PF_VEL, d},
+               {st->a, PF_ACC, d}, {st->F, PF_F, d * d}, {st->V, PF_V, 1}, {st->lp, PF_LP, d},
+               {st->pd, PF_PD, 1}, {st->pdd, PF_PDD, 1}};
+  for (const Item &it : items) {
+    if (!it.src) continue;
+    cudaMemcpyAsync(c.stage, it.src, sizeof(double) * n * it.comps, cudaMemcpyHostToDevice, c.st);
+    k_write_field<<<nblk(n), TPB, 0, c.st>>>(n, c.pf, it.f0, it.comps, c.pid, c.stage);
+    cudaError_t e = cudaStreamSynchronize(c.st);
+    if (e != cudaSuccess) return check_cuda(c, e, "restore");
+  }
+  c.t = t;
+  c.steps = steps;
+  c.stats.t = t;
+  c.stats.steps = steps;
+  c.prepared = false;
+  return check_cuda(c, cudaGetLastError(), "restore");
 }
 
 int mpm_get_stats(const mpm_ctx *h, mpm_stats *s) {

@@ -151,6 +151,37 @@ __global__ void k_initial_guess(GridP g, double phi_min, DevView v, double *__re
 
 // Points whose support box holds an inactive node get their basis
 // renormalised over the active box nodes (see basis_at).
+// Fixed-stress term of the pressure Schur complement, lumped per node:
+// fsd_a = sum_p S_ap b2_p vol_p / (cs_p K_p), K = lambda + 2 (G - lambda ln J) / d
+// (the drained bulk modulus of the current records).  Node-centric gather in
+// (cell, id) order.
+template <int D, bool GIMP>
+__global__ void k_fs_diag(GridP g, DevView v, double *__restrict__ out) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= g.nnodes) return;
+  const int64_t n = v.n;
+  int ac[3];
+  node_coords(g, a, ac);
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) cand_range<GIMP>(ac[k], g.nc[k], lo[k], hi[k]);
+  const double *rec = v.rec;
+  double acc = 0.0;
+  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
+    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
+      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
+        const int64_t cid = cell_index(g, c0, c1, c2);
+        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
+          int off[3];
+          if (!in_box<D>(v, q, ac, off)) continue;
+          double Sa, S0a, Gn[3];
+          basis_at<D>(v, q, off, a, Sa, S0a, Gn);
+          const double K = rec[RC_LAM * n + q] + 2.0 * rec[RC_MUP * n + q] / D;
+          acc += Sa * rec[RC_B2 * n + q] * rec[RC_VOL * n + q] / (rec[RC_CS * n + q] * K);
+        }
+      }
+  out[a] = acc;
+}
+
 // Work count of the Jacobian assembly: n_p active nodes in point p's support
 // give n_p^2 (point, a, b) terms and n_p (point, node) terms.
 template <int D>
@@ -404,10 +435,11 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
           r[D] += Sa * rec[RC_DIVV * n + q] + rec[RC_KV * n + q] * gw + (Sa - S0a) * rec[RC_RST * n + q];
           const int32_t e = v.surf[q];
           if (e >= 0) {  // Neumann data at the surface point x + lp.n (hat basis)
+            const InstDev &I = v.inst[(int)v.pf[PF_INST * n + q]];
             double Ny = 1.0;
             for (int k = 0; k < D; ++k) {
               const double y = v.pf[(PF_X + k) * n + q] + v.pf[(PF_LP + k) * n + q] * v.pf[(PF_SN + k) * n + q];
-              const double t = 1.0 - fabs((y - g.org[k]) / g.h - (double)ac[k]);
+              const double t = 1.0 - fabs((y - I.org[k]) / g.h - (double)(ac[k] - I.off[k]));
               Ny *= t > 0.0 ? t : 0.0;
             }
             const double A = v.pf[PF_SA * n + q];
@@ -734,6 +766,20 @@ void run_initial_guess(Ctx &c) {
   const DevView v = c.view();
   if (c.d == 2) k_initial_guess<2><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, c.s.phi_min, v, c.X);
   else k_initial_guess<3><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g, c.s.phi_min, v, c.X);
+  UPMPM_LAUNCH(c);
+}
+
+void run_fs_diag(Ctx &c) {
+  const DevView v = c.view();
+  const int nbk = nblk(c.g.nnodes, 128);
+  const bool gimp = c.shape == MPM_SHAPE_GIMP;
+  if (c.d == 2) {
+    if (gimp) k_fs_diag<2, true><<<nbk, 128, 0, c.st>>>(c.g, v, c.fsd);
+    else k_fs_diag<2, false><<<nbk, 128, 0, c.st>>>(c.g, v, c.fsd);
+  } else {
+    if (gimp) k_fs_diag<3, true><<<nbk, 128, 0, c.st>>>(c.g, v, c.fsd);
+    else k_fs_diag<3, false><<<nbk, 128, 0, c.st>>>(c.g, v, c.fsd);
+  }
   UPMPM_LAUNCH(c);
 }
 

@@ -83,7 +83,18 @@ enum PField {
   PF_TAU = 34,     // PPP parameter (0 when unstabilized)
   PF_SN = 35,      // 3 surface normal
   PF_SA = 38,      // surface measure
-  PF_COUNT = 39
+  PF_INST = 39,    // instance of a batched context (0 otherwise)
+  PF_COUNT = 40
+};
+
+// One problem instance of a context.  Its points keep the coordinates of its
+// own grid (origin org, ncell nc); on the context's background grid that grid
+// starts at cell / node offset off.  A single-instance context has one entry
+// (its own grid, off = 0).
+struct InstDev {
+  double org[3];
+  int off[3];
+  int nc[3];
 };
 
 // ---- per-point records of one Newton iterate -------------------------------
@@ -156,6 +167,7 @@ struct DevView {
   double *trac;             // n_surf * d (already scaled)
   double *flux;             // n_surf or null
   int *err;                 // device error word
+  const InstDev *inst;      // instance table
 };
 
 // ---- host-side context ----------------------------------------------------
@@ -169,6 +181,24 @@ struct Ctx {
   cudaStream_t st = nullptr;
   bool own_stream = false;   // created by the context (no stream was given)
   int nsm = 152;             // SMs of the context's device
+  double *fsd = nullptr;     // nnodes: lumped fixed-stress term of the pressure Schur complement
+  bool fixed_stress() const {
+    return opt.schur_approx == MPM_SCHUR_FIXED_STRESS || (opt.schur_approx == MPM_SCHUR_AUTO && !dyn);
+  }
+  // instances (batched contexts hold several; see mpm_create_batch)
+  int ninst = 1;
+  InstDev *inst = nullptr;             // device table
+  std::vector<InstDev> inst_h;         // host copy
+  std::vector<int64_t> inst_n, inst_nsurf;
+  // batched contexts: host copies of the combined loads and Dirichlet data,
+  // so that an instance whose entry is NULL keeps its previous values
+  std::vector<double> b_trac, b_flux, b_uval, b_pval;
+  std::vector<uint8_t> b_ufix, b_pfix;
+  bool b_has_flux = false;
+  double *inorm = nullptr;             // device: per-instance squared residual norms
+  double *h_inorm = nullptr;           // pinned copy
+  int32_t *node_inst = nullptr;        // device: instance of every node (-1: between instances)
+  double *iw = nullptr, *h_iw = nullptr;  // per-instance weights of the Krylov right-hand side
   bool capturing = false;    // a CUDA graph capture is in progress on st
   int64_t n = 0;
   int32_t n_surf = 0;
@@ -248,6 +278,7 @@ int run_pattern(Ctx &c);                          // builds row_ptr / col / row_
 void run_initial_guess(Ctx &c);   // also sets the active flags
 void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
 void run_count_terms(Ctx &c);     // Jacobian term counts into c.terms (device)
+void run_fs_diag(Ctx &c);         // c.fsd = sum_p S_ip b2 vol / (cs K) (current records)
 void run_point_eval(Ctx &c, const double *X);
 void run_residual(Ctx &c, const double *X, double *R, int apply_bc);
 template <typename T>
@@ -269,6 +300,8 @@ template <typename T>
 void run_precond(Ctx &c, LinSys<T> &S, const T *v, T *z);  // z = M^{-1} v (scaled system)
 template <typename T>
 void run_unscale_add(Ctx &c, const LinSys<T> &S, double *X);  // X += D x
+template <typename T>
+void run_inst_weight(Ctx &c, T *v, int divide);  // batched: v *= (or /=) instance weight per node
 double run_norm(Ctx &c, const double *x);          // synchronises
 
 // Schur-complement multigrid preconditioner

@@ -176,6 +176,24 @@ __global__ void k_schur_rows(int nn0, int nn1, int64_t nnodes, const uint64_t *_
   S[eb] = J[(int64_t)eb * NB * NB + D * NB + D] - prod;
 }
 
+// Fixed-stress approximation: S_ab = C_ab, plus the lumped fixed-stress term
+// on the diagonal of free pressure rows.
+template <int D>
+__global__ void k_schur_fs(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                           const int32_t *__restrict__ col, const real *__restrict__ J,
+                           const double *__restrict__ fsd, const uint8_t *__restrict__ fixed,
+                           real *__restrict__ S) {
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nnodes) return;
+  constexpr int NB = D + 1;
+  const bool free_p = !fixed[a * NB + D];
+  for (int e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
+    real v = J[(int64_t)e * NB * NB + D * NB + D];
+    if (col[e] == a && free_p) v += (real)fsd[a];
+    S[e] = v;
+  }
+}
+
 // The part of row a's full product sum_c W_ac (sum_b B1_cb) that fell outside
 // the sparsity is added to S_aa.
 template <int D>
@@ -282,6 +300,10 @@ struct LevelDev {
   const uint8_t *fixed;           // fixed[a * mstride + moff + i] != 0: DOF fixed
   int mstride, moff;
   const uint64_t *mask;           // level 0 only: coupling mask of the block sparsity
+  // instance of every node (-1 between instances): the transfers connect a
+  // fine and a coarse node only within one instance, so the hierarchy of a
+  // batched context never mixes instances (a single instance: all 0)
+  const int32_t *inst;
 };
 
 __device__ inline real free_w(const LevelDev &L, int64_t a, int i) {
@@ -576,6 +598,7 @@ __global__ void k_mg_restrict(LevelDev F, LevelDev Cl, const real *__restrict__ 
         if (a0 < 0 || a0 >= F.nn[0] || a1 < 0 || a1 >= F.nn[1] || a2 < 0 || a2 >= F.nn[2]) continue;
         const real wgt = pw(a0, Ic[0]) * pw(a1, Ic[1]) * (D == 3 ? pw(a2, Ic[2]) : 1.0);
         const int64_t a = a0 + (int64_t)F.nn[0] * (a1 + (int64_t)F.nn[1] * a2);
+        if (F.inst[a] != Cl.inst[I]) continue;
         for (int i = 0; i < B; ++i) acc[i] += wgt * free_w(F, a, i) * rf[a * B + i];
       }
   for (int i = 0; i < B; ++i) bc[I * B + i] = acc[i];
@@ -593,7 +616,7 @@ __global__ void k_mg_restrict(LevelDev F, LevelDev Cl, const real *__restrict__ 
 // issued without branches.
 template <int B, int D>
 __device__ inline void prolong_at(const LevelDev &Cl, const real *__restrict__ xc, const int ac[3],
-                                  real out[B]) {
+                                  int inst_a, real out[B]) {
   int i0[3], i1[3];
   real w0[3], w1[3];
   for (int k = 0; k < 3; ++k) {
@@ -611,7 +634,8 @@ __device__ inline void prolong_at(const LevelDev &Cl, const real *__restrict__ x
     const real wgt = (s0 ? w1[0] : w0[0]) * (s1 ? w1[1] : w0[1]) * (D == 3 ? (s2 ? w1[2] : w0[2]) : 1.0);
     const int64_t I = (s0 ? i1[0] : i0[0]) +
                       (int64_t)Cl.nn[0] * ((s1 ? i1[1] : i0[1]) + (int64_t)Cl.nn[1] * (D == 3 ? (s2 ? i1[2] : i0[2]) : 0));
-    for (int i = 0; i < B; ++i) out[i] = fma(wgt, xc[I * B + i], out[i]);
+    const real w = Cl.inst[I] == inst_a ? wgt : real(0);
+    for (int i = 0; i < B; ++i) out[i] = fma(w, xc[I * B + i], out[i]);
   }
 }
 
@@ -624,7 +648,7 @@ __global__ void k_mg_prolong(LevelDev F, LevelDev Cl, real *__restrict__ xf,
   int ac[3];
   grid_xyz(F.nn[0], F.nn[1], (int)a, ac);
   real acc[B];
-  prolong_at<B, D>(Cl, xc, ac, acc);
+  prolong_at<B, D>(Cl, xc, ac, F.inst[a], acc);
   for (int i = 0; i < B; ++i) xf[a * B + i] += free_w(F, a, i) * acc[i];
 }
 
@@ -647,6 +671,7 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
   const bool Jin = Jc[0] >= 0 && Jc[0] < Cl.nn[0] && Jc[1] >= 0 && Jc[1] < Cl.nn[1] && Jc[2] >= 0 &&
                    Jc[2] < Cl.nn[2];
   if (Jin) {
+    const int64_t Jn = Jc[0] + (int64_t)Cl.nn[0] * (Jc[1] + (int64_t)Cl.nn[1] * Jc[2]);
     const int lo2 = D == 3 ? -1 : 0, hi2 = D == 3 ? 1 : 0;
     for (int a2 = lo2; a2 <= hi2; ++a2)
       for (int a1 = -1; a1 <= 1; ++a1)
@@ -656,6 +681,7 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
             continue;
           const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
           const int64_t a = fa[0] + (int64_t)F.nn[0] * (fa[1] + (int64_t)F.nn[1] * fa[2]);
+          if (F.inst[a] != Cl.inst[I]) continue;
           for (int b2 = lo2; b2 <= hi2; ++b2)
             for (int b1 = -1; b1 <= 1; ++b1)
               for (int b0 = -1; b0 <= 1; ++b0) {
@@ -664,6 +690,10 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
                     fb[2] >= F.nn[2])
                   continue;
                 const real wb = pw(fb[0], Jc[0]) * pw(fb[1], Jc[1]) * (D == 3 ? pw(fb[2], Jc[2]) : 1.0);
+                {
+                  const int64_t bq = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
+                  if (F.inst[bq] != Cl.inst[Jn]) continue;
+                }
                 const real *blk = nullptr;
                 if (!FST) {
                   const int e = mask_block<D>(F.mask, F.row_ptr, (int)a, fb[0] - fa[0], fb[1] - fa[1],
@@ -790,6 +820,17 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
   const int D = c.d;
   const int NS = D == 2 ? 25 : 125;
   int nn[3] = {c.g.nn[0], c.g.nn[1], c.g.nn[2]};
+  // instance of every node of the current level (host); level l + 1 takes
+  // the instance of the fine node at the same place (2I)
+  std::vector<int32_t> imap((size_t)nn[0] * nn[1] * nn[2], -1), inext;
+  for (size_t i = 0; i < c.inst_h.size(); ++i) {
+    const InstDev &I = c.inst_h[i];
+    const int64_t m0 = I.nc[0] + 1, m1 = D > 1 ? I.nc[1] + 1 : 1, m2 = D > 2 ? I.nc[2] + 1 : 1;
+    for (int64_t t = 0; t < m0 * m1 * m2; ++t) {
+      const int64_t i0 = t % m0, i1 = (t / m0) % m1, i2 = t / (m0 * m1);
+      imap[(i0 + I.off[0]) + (int64_t)nn[0] * ((i1 + I.off[1]) + (int64_t)nn[1] * (i2 + I.off[2]))] = (int32_t)i;
+    }
+  }
   int l = 0;
   while (true) {
     LevelDev &L = H.L[l];
@@ -809,12 +850,26 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
         cudaMalloc(&H.b[l], sizeof(real) * vb) || cudaMalloc(&H.r[l], sizeof(real) * vb))
       return MPM_ERR_NO_MEMORY;
     if (l > 0 && cudaMalloc(&L.sval, sizeof(real) * L.nnodes * NS * B * B)) return MPM_ERR_NO_MEMORY;
+    int32_t *dinst = nullptr;
+    if (cudaMalloc(&dinst, sizeof(int32_t) * L.nnodes) != cudaSuccess) return MPM_ERR_NO_MEMORY;
+    cudaMemcpy(dinst, imap.data(), sizeof(int32_t) * L.nnodes, cudaMemcpyHostToDevice);
+    L.inst = dinst;
     ++l;
     int mn = 1 << 30;
     for (int k = 0; k < D; ++k) mn = nn[k] < mn ? nn[k] : mn;
     // the coarsest level is solved exactly: stop at <= 64 nodes or a 2-node axis
     if (mn <= 2 || L.nnodes <= 64 || l >= 15) break;
-    for (int k = 0; k < D; ++k) nn[k] = (nn[k] + 1) / 2;
+    int nc[3] = {nn[0], nn[1], nn[2]};
+    for (int k = 0; k < D; ++k) nc[k] = (nn[k] + 1) / 2;
+    inext.assign((size_t)nc[0] * nc[1] * nc[2], -1);
+    for (int64_t I2 = 0; I2 < nc[2]; ++I2)
+      for (int64_t I1 = 0; I1 < nc[1]; ++I1)
+        for (int64_t I0 = 0; I0 < nc[0]; ++I0) {
+          const int64_t f0 = 2 * I0, f1 = D > 1 ? 2 * I1 : I1, f2 = D > 2 ? 2 * I2 : I2;
+          inext[I0 + nc[0] * (I1 + nc[1] * I2)] = imap[f0 + nn[0] * (f1 + nn[1] * f2)];
+        }
+    imap.swap(inext);
+    for (int k = 0; k < 3; ++k) nn[k] = nc[k];
   }
   H.nlev = l;
   H.ncoarse = (int)(H.L[l - 1].nnodes * B);
@@ -830,6 +885,8 @@ void mg_free(MGHier<real> &H) {
   cudaFree(H.Ai);
   H.Ad = H.Ai = nullptr;
   for (int l = 0; l < H.nlev; ++l) {
+    cudaFree(const_cast<int32_t *>(H.L[l].inst));
+    H.L[l].inst = nullptr;
     cudaFree(H.L[l].dinv);
     cudaFree(H.L[l].sval);
     cudaFree(H.x[l]);
@@ -912,6 +969,10 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   const int64_t nn = c.g.nnodes, nnzb = c.nnzb;
   const int d = c.d;
   if (nnzb > S.sub_cap) {
+    // the captured graph reads these buffers (B1c, and Aval / Sval through
+    // the finest multigrid level): drop it, it is re-captured on next use
+    if (S.gexec) cudaGraphExecDestroy(S.gexec);
+    S.gexec = nullptr;
     MG_REAL *ptrs[] = {S.Aval, S.Sval, S.B1c, S.W};
     for (MG_REAL *p : ptrs) cudaFree(p);
     S.Aval = S.Sval = S.B1c = S.W = nullptr;
@@ -925,7 +986,19 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
     S.sub_cap = cap;
   }
   const int nsl = d == 2 ? 49 : 343;
-  if (d == 2) {
+  if (c.fixed_stress()) {
+    run_fs_diag(c);
+    if (d == 2) {
+      k_extract_A<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
+      k_extract_B1<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B1c);
+      k_schur_fs<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, c.fsd, c.fixed, S.Sval);
+    } else {
+      k_extract_A<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
+      k_extract_B1<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B1c);
+      k_schur_fs<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, c.fsd, c.fixed, S.Sval);
+    }
+    c.launches += 3;
+  } else if (d == 2) {
     k_extract_A<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.Aval);
     k_extract_B1<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B1c);
     k_diag_inv_A<2><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.Aval, S.val, S.DAinv, S.B1rs);
@@ -942,7 +1015,7 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
                                                       S.val, S.W, S.Sval);
     k_schur_lump<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.W, S.B1rs, S.Sval);
   }
-  c.launches += 6;
+  if (!c.fixed_stress()) c.launches += 6;
   mg_setup(c, *S.mgA, c.row_ptr, c.col, S.Aval, 0);
   mg_setup(c, *S.mgS, c.row_ptr, c.col, S.Sval, d);
   dense_invert_pair(c, *S.mgA, *S.mgS);
@@ -987,9 +1060,11 @@ void schur_merge(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *zu, const MG_REAL *z
 }  // namespace MG_NS
 
 // The multigrid core is a fixed sequence of small kernels on fixed buffers: it
-// is captured once into a CUDA graph (re-captured only when the matrix buffers
-// it reads move) and replayed between the split and merge kernels, which take
-// the caller's v and z.
+// is captured once into a CUDA graph and replayed between the split and merge
+// kernels, which take the caller's v and z.  It is re-captured when a buffer
+// it reads moves: the block columns (key below) or the Schur / multigrid
+// matrices (schur_setup drops the graph when it reallocates them; a freed and
+// reallocated buffer may come back at another address while col does not).
 template <>
 void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
   using namespace MG_NS;

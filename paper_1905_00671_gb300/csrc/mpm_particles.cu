@@ -24,21 +24,24 @@ inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
 // Cell of the point centre: floor((x - origin) / h) per axis with IEEE
 // round-to-nearest subtract and divide (no contraction), so the key is
 // bit-identical to any IEEE implementation of the same expression.
+// The cell is taken on the point's own instance grid (its origin and extent)
+// and shifted by the instance's offset on the context's background grid.
 template <int D>
-__global__ void k_bin_keys(GridP g, int64_t n, const double *__restrict__ pf,
+__global__ void k_bin_keys(GridP g, int64_t n, const double *__restrict__ pf, const InstDev *__restrict__ inst,
                            int32_t *__restrict__ cell, int32_t *__restrict__ count, int *err) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const InstDev &I = inst[(int)pf[PF_INST * n + p]];
   int c[3] = {0, 0, 0};
   for (int k = 0; k < D; ++k) {
-    const double xi = __ddiv_rn(__dsub_rn(pf[(PF_X + k) * n + p], g.org[k]), g.h);
+    const double xi = __ddiv_rn(__dsub_rn(pf[(PF_X + k) * n + p], I.org[k]), g.h);
     const double cf = floor(xi);
-    if (!(cf >= 0.0) || !(cf <= (double)(g.nc[k] - 1))) {
+    if (!(cf >= 0.0) || !(cf <= (double)(I.nc[k] - 1))) {
       atomicOr(err, DE_OUT_OF_GRID);
       cell[p] = -1;
       return;
     }
-    c[k] = (int)cf;
+    c[k] = (int)cf + I.off[k];
   }
   const int32_t id = (int32_t)cell_index(g, c[0], c[1], c[2]);
   cell[p] = id;
@@ -96,13 +99,14 @@ __global__ void k_permute(int64_t n, int nf, const int32_t *__restrict__ perm,
 // the constant basis of Sec. 4.4 integrates 1/2.  The domain is the point's
 // domain intersected with the grid box, normalised by its length.
 template <int D, bool GIMP>
-__global__ void k_shape(GridP g, int64_t n, const double *__restrict__ pf,
+__global__ void k_shape(GridP g, int64_t n, const double *__restrict__ pf, const InstDev *__restrict__ inst,
                         int32_t *__restrict__ first, int32_t *__restrict__ cnt_packed,
                         double *__restrict__ S, double *__restrict__ dS, double *__restrict__ S0,
                         float *__restrict__ Sf, float *__restrict__ dSf, float *__restrict__ S0f,
                         int *err) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const InstDev &I = inst[(int)pf[PF_INST * n + p]];
   int packed = 0;
   for (int k = 0; k < 3; ++k) {
     double s[MAXS] = {0, 0, 0, 0}, ds[MAXS] = {0, 0, 0, 0}, s0[MAXS] = {0, 0, 0, 0};
@@ -111,10 +115,11 @@ __global__ void k_shape(GridP g, int64_t n, const double *__restrict__ pf,
       s[0] = 1.0;
       s0[0] = 1.0;
     } else {
-      const double dx = __dsub_rn(pf[(PF_X + k) * n + p], g.org[k]);
+      // on the point's own instance grid: its box clips the GIMP domain
+      const double dx = __dsub_rn(pf[(PF_X + k) * n + p], I.org[k]);
       const double h = g.h;
       const double cf = floor(__ddiv_rn(dx, h));
-      if (!(cf >= 0.0) || !(cf <= (double)(g.nc[k] - 1))) {
+      if (!(cf >= 0.0) || !(cf <= (double)(I.nc[k] - 1))) {
         atomicOr(err, DE_OUT_OF_GRID);
         return;
       }
@@ -135,7 +140,7 @@ __global__ void k_shape(GridP g, int64_t n, const double *__restrict__ pf,
           return;
         }
         const double lo = fmax(__ddiv_rn(__dsub_rn(dx, lp), h), 0.0);
-        const double hi = fmin(__ddiv_rn(__dadd_rn(dx, lp), h), (double)g.nc[k]);
+        const double hi = fmin(__ddiv_rn(__dadd_rn(dx, lp), h), (double)I.nc[k]);
         const int i0 = (int)floor(lo), i1 = (int)ceil(hi);
         if (i1 - i0 + 1 > MAXS) {
           atomicOr(err, DE_SUPPORT);
@@ -164,7 +169,7 @@ __global__ void k_shape(GridP g, int64_t n, const double *__restrict__ pf,
         }
       }
     }
-    first[k * n + p] = f0;
+    first[k * n + p] = f0 + (k < D ? I.off[k] : 0);
     packed |= cn << (4 * k);
     for (int q = 0; q < MAXS; ++q) {
       S[(k * MAXS + q) * n + p] = s[q];
@@ -399,9 +404,9 @@ int run_binning(Ctx &c) {
   // points per cell (integer atomics: the counts are exact and order-free)
   cudaMemsetAsync(c.cell_cursor, 0, sizeof(int32_t) * (nc + 1), c.st);
   if (c.d == 2)
-    k_bin_keys<2><<<nblk(n), TPB, 0, c.st>>>(c.g, n, c.pf, c.cell, c.cell_cursor, c.err);
+    k_bin_keys<2><<<nblk(n), TPB, 0, c.st>>>(c.g, n, c.pf, c.inst, c.cell, c.cell_cursor, c.err);
   else
-    k_bin_keys<3><<<nblk(n), TPB, 0, c.st>>>(c.g, n, c.pf, c.cell, c.cell_cursor, c.err);
+    k_bin_keys<3><<<nblk(n), TPB, 0, c.st>>>(c.g, n, c.pf, c.inst, c.cell, c.cell_cursor, c.err);
   UPMPM_LAUNCH(c);
   int rc = read_dev_err(c);
   if (rc) return rc;
@@ -427,14 +432,14 @@ void run_shape(Ctx &c) {
   const int nbk = nblk(n);
   if (c.d == 2) {
     if (c.shape == MPM_SHAPE_GIMP)
-      k_shape<2, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
+      k_shape<2, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.inst, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
     else
-      k_shape<2, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
+      k_shape<2, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.inst, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
   } else {
     if (c.shape == MPM_SHAPE_GIMP)
-      k_shape<3, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
+      k_shape<3, true><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.inst, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
     else
-      k_shape<3, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
+      k_shape<3, false><<<nbk, TPB, 0, c.st>>>(c.g, n, c.pf, c.inst, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS, c.sh_S0, c.sh_Sf, c.sh_dSf, c.sh_S0f, c.err);
   }
   UPMPM_LAUNCH(c);
 }

@@ -591,6 +591,24 @@ void run_scale_system(Ctx &c, LinSys<T> &S, const double *R) {
 }
 
 template <typename T>
+__global__ void k_inst_weight(int64_t N, int nb, const int32_t *__restrict__ node_inst,
+                              const double *__restrict__ w, T *__restrict__ v, int divide) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int inst = node_inst[i / nb];
+  if (inst < 0) return;
+  v[i] = divide ? (T)(v[i] / w[inst]) : (T)(v[i] * w[inst]);
+}
+
+template <typename T>
+void run_inst_weight(Ctx &c, T *v, int divide) {
+  k_inst_weight<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), c.nb, c.node_inst, c.iw, v, divide);
+  UPMPM_LAUNCH(c);
+}
+template void run_inst_weight<double>(Ctx &, double *, int);
+template void run_inst_weight<float>(Ctx &, float *, int);
+
+template <typename T>
 void run_unscale_add(Ctx &c, const LinSys<T> &S, double *X) {
   k_unscale_add<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), X, S.dscale, S.x);
   UPMPM_LAUNCH(c);

@@ -303,3 +303,29 @@ CONFIGS = {
     "footing": lambda: strip_footing(),
     "block3d": lambda: consolidation_block(),
 }
+
+
+def batch_instances(count=256, seed=5, kind="alternate", h=0.1, nx=(16, 128), ny=(32, 64),
+                    logk=(-15.0, -10.0), load=(10e3, 200e3)):
+    """Independent 2D instances of uneven size for batched stepping: grid
+    nx x ny cells drawn uniformly from the ranges, 2 x 2 points per cell,
+    permeability 10^U(logk), load U(load).  kind: "terzaghi" (consolidation
+    under a uniform top load: original MPM, quasi-static, dt = 1 s),
+    "footing" (strip load of half width min(1 m, W/4): GIMP, Newmark,
+    dt = 1e-3 s, ramp 0.1 s) or "alternate" (even i Terzaghi, odd i footing)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        cx = int(rng.integers(nx[0], nx[1] + 1))
+        cy = int(rng.integers(ny[0], ny[1] + 1))
+        k = float(10.0 ** rng.uniform(logk[0], logk[1]))
+        w = float(rng.uniform(load[0], load[1]))
+        kd = kind if kind != "alternate" else ("terzaghi" if i % 2 == 0 else "footing")
+        if kd == "terzaghi":
+            out.append(terzaghi_column(ncell_y=cy, ncell_x=cx, h=h, k=k, load=w, dt=1.0, nsteps=20,
+                                       ppc_axis=(2, 2), shape=ORIG, name=f"terzaghi-{i}-{cx}x{cy}"))
+        else:
+            out.append(strip_footing(body=(cx, cy), pad=2, h=h, seed=seed * 100003 + i, k=k, w_max=w,
+                                     ramp=0.1, dt=1e-3, nsteps=20,
+                                     half_width=min(1.0, 0.25 * cx * h), name=f"footing-{i}-{cx}x{cy}"))
+    return out

@@ -61,7 +61,7 @@ class mpm_options(C.Structure):
                 ("newton_stag", C.c_double), ("krylov_rtol", C.c_double),
                 ("krylov_restart", C.c_int32), ("krylov_max", C.c_int32), ("precond", C.c_int32),
                 ("min_volume_fraction", C.c_double), ("profile", C.c_int32),
-                ("precond_lag", C.c_int32), ("stream", C.c_void_p)]
+                ("precond_lag", C.c_int32), ("schur_approx", C.c_int32), ("stream", C.c_void_p)]
 
 
 class mpm_loads(C.Structure):
@@ -123,6 +123,11 @@ def load(build_if_missing: bool = False):
     lib.mpm_debug_nodal.argtypes = [P, P, P, P]
     lib.mpm_debug_eval.argtypes = [P, P, P, P, C.c_int32]
     lib.mpm_debug_precond.argtypes = [P, P, P, P]
+    lib.mpm_restore.argtypes = [P, C.POINTER(mpm_particles_out), C.c_double, C.c_int64]
+    lib.mpm_batch_pack.argtypes = [C.c_int32, C.POINTER(mpm_grid), P, P]
+    lib.mpm_create_batch.argtypes = [C.c_int32, C.POINTER(mpm_grid), C.POINTER(mpm_particles),
+                                     C.POINTER(mpm_material), P, C.POINTER(mpm_options), C.POINTER(P)]
+    lib.mpm_step_batch.argtypes = [P, C.c_double, P, P]
     _lib = lib
     return lib
 
@@ -144,6 +149,73 @@ def default_options() -> mpm_options:
     return o
 
 
+def _grid(w) -> mpm_grid:
+    g = mpm_grid()
+    g.dim = w.dim
+    for k in range(3):
+        g.ncell[k] = int(w.ncell[k]) if k < w.dim else 0
+        g.origin[k] = float(w.origin[k]) if k < w.dim else 0.0
+    g.h = float(w.h)
+    return g
+
+
+def _point_structs(w):
+    """(arrays kept alive, mpm_particles, mpm_material) of a Workload."""
+    K = {
+        "x": _f64(w.x), "vol": _f64(w.vol), "lp": _f64(w.lp), "p0": _f64(w.p0),
+        "v0": _f64(w.v0), "surf_id": np.ascontiguousarray(w.surf_id, dtype=np.int32),
+        "sn": _f64(w.surf_normal), "sa": _f64(w.surf_area), "E": _f64(w.E), "nu": _f64(w.nu),
+        "k": _f64(w.k),
+    }
+    P = mpm_particles(n=w.n, x=_p(K["x"]), vol=_p(K["vol"]), lp=_p(K["lp"]), p0=_p(K["p0"]),
+                      v0=_p(K["v0"]), surf_id=_p(K["surf_id"]), surf_normal=_p(K["sn"]),
+                      surf_area=_p(K["sa"]), n_surf=w.n_surf)
+    M = mpm_material(E=_p(K["E"]), nu=_p(K["nu"]), rho_s=w.rho_s, rho_f=w.rho_f, phi0=w.phi0,
+                     mu_f=w.mu_f, alpha_vis=w.alpha_vis)
+    for k in range(3):
+        M.g[k] = w.g[k] if k < len(w.g) else 0.0
+    return K, P, M
+
+
+def _options(w, stream, opts) -> mpm_options:
+    o = default_options()
+    o.shape = int(w.shape)
+    o.scheme = MPM_NEWMARK if w.dynamic else MPM_QUASISTATIC
+    o.beta, o.gamma = w.beta, w.gamma
+    o.stabilize = int(bool(w.stabilize))
+    o.tau_scale = w.tau_scale
+    for key, val in opts.items():
+        setattr(o, key, val)
+    if stream is not None:
+        o.stream = stream
+    return o
+
+
+_FIELDS = ("x", "u", "p", "v", "a", "F", "V", "lp", "pd", "pdd")
+
+
+def _read(lib, ctx, n, d, fields, check):
+    comps = {"x": d, "u": d, "p": 1, "v": d, "a": d, "F": d * d, "V": 1, "lp": d, "pd": 1,
+             "pdd": 1}
+    out = {k: np.zeros((n, comps[k])) if comps[k] > 1 else np.zeros(n) for k in fields}
+    o = mpm_particles_out(**{k: _p(v) for k, v in out.items()})
+    check(lib.mpm_read(ctx, C.byref(o)), "mpm_read")
+    return out
+
+
+def batch_pack(grids_of):
+    """mpm_batch_pack for a list of Workloads (host only): (offsets (count, 3),
+    background ncell (3,))."""
+    lib = load()
+    gs = (mpm_grid * len(grids_of))(*[_grid(w) for w in grids_of])
+    offs = np.zeros((len(grids_of), 3), np.int32)
+    nc = np.zeros(3, np.int32)
+    rc = lib.mpm_batch_pack(len(grids_of), gs, _p(offs), _p(nc))
+    if rc != MPM_OK:
+        raise MPMError(rc, "mpm_batch_pack failed")
+    return offs, nc
+
+
 class Simulation:
     """One context for a Workload (see inputs.py).  Host arrays in, host arrays
     out; all computation in the CUDA library."""
@@ -152,37 +224,10 @@ class Simulation:
         lib = load()
         self.w = w
         self.lib = lib
-        d = w.dim
-        g = mpm_grid()
-        g.dim = d
-        for k in range(3):
-            g.ncell[k] = int(w.ncell[k]) if k < d else 0
-            g.origin[k] = float(w.origin[k]) if k < d else 0.0
-        g.h = float(w.h)
-        self._keep = {
-            "x": _f64(w.x), "vol": _f64(w.vol), "lp": _f64(w.lp), "p0": _f64(w.p0),
-            "v0": _f64(w.v0), "surf_id": np.ascontiguousarray(w.surf_id, dtype=np.int32),
-            "sn": _f64(w.surf_normal), "sa": _f64(w.surf_area), "E": _f64(w.E), "nu": _f64(w.nu),
-            "k": _f64(w.k),
-        }
-        K = self._keep
-        P = mpm_particles(n=w.n, x=_p(K["x"]), vol=_p(K["vol"]), lp=_p(K["lp"]), p0=_p(K["p0"]),
-                          v0=_p(K["v0"]), surf_id=_p(K["surf_id"]), surf_normal=_p(K["sn"]),
-                          surf_area=_p(K["sa"]), n_surf=w.n_surf)
-        M = mpm_material(E=_p(K["E"]), nu=_p(K["nu"]), rho_s=w.rho_s, rho_f=w.rho_f, phi0=w.phi0,
-                         mu_f=w.mu_f, alpha_vis=w.alpha_vis)
-        for k in range(3):
-            M.g[k] = w.g[k] if k < len(w.g) else 0.0
-        o = default_options()
-        o.shape = int(w.shape)
-        o.scheme = MPM_NEWMARK if w.dynamic else MPM_QUASISTATIC
-        o.beta, o.gamma = w.beta, w.gamma
-        o.stabilize = int(bool(w.stabilize))
-        o.tau_scale = w.tau_scale
-        for key, val in opts.items():
-            setattr(o, key, val)
-        if stream is not None:
-            o.stream = stream
+        g = _grid(w)
+        K, P, M = _point_structs(w)
+        self._keep = K
+        o = _options(w, stream, opts)
         self.options = o
         ctx = C.c_void_p()
         rc = lib.mpm_create(C.byref(g), C.byref(P), C.byref(M), _p(K["k"]), C.byref(o), C.byref(ctx))
@@ -239,14 +284,20 @@ class Simulation:
         self.t += dt
         return self.stats()
 
-    def read(self, fields=("x", "u", "p", "v", "a", "F", "V", "lp", "pd", "pdd")):
-        n, d = self.w.n, self.w.dim
-        comps = {"x": d, "u": d, "p": 1, "v": d, "a": d, "F": d * d, "V": 1, "lp": d, "pd": 1,
-                 "pdd": 1}
-        out = {k: np.zeros((n, comps[k])) if comps[k] > 1 else np.zeros(n) for k in fields}
-        o = mpm_particles_out(**{k: _p(v) for k, v in out.items()})
-        self._check(self.lib.mpm_read(self.ctx, C.byref(o)), "mpm_read")
-        return out
+    def read(self, fields=_FIELDS):
+        return _read(self.lib, self.ctx, self.w.n, self.w.dim, fields, self._check)
+
+    def checkpoint(self):
+        """The full point state (every field of mpm_read) and the time."""
+        return {"state": self.read(_FIELDS), "t": self.t, "steps": self.stats()["steps"]}
+
+    def restore(self, ck):
+        """mpm_restore of a checkpoint taken from a context of the same workload."""
+        keep = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in ck["state"].items()}
+        o = mpm_particles_out(**{k: _p(v) for k, v in keep.items()})
+        self._check(self.lib.mpm_restore(self.ctx, C.byref(o), C.c_double(ck["t"]),
+                                         C.c_int64(ck["steps"])), "mpm_restore")
+        self.t = ck["t"]
 
     def stats(self):
         s = mpm_stats()
@@ -309,6 +360,98 @@ class Simulation:
         z = np.zeros_like(v)
         self._check(self.lib.mpm_debug_precond(self.ctx, _p(X), _p(v), _p(z)), "mpm_debug_precond")
         return z
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mpm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """One batched context for a list of Workloads that share dim, h, shape,
+    time scheme, time step and material constants (mpm_create_batch): every
+    step advances all of them with one launch per kernel."""
+
+    def __init__(self, ws, stream: Optional[int] = None, **opts):
+        lib = load()
+        self.ws = list(ws)
+        self.lib = lib
+        m = len(self.ws)
+        w0 = self.ws[0]
+        self._keep = []
+        grids = (mpm_grid * m)()
+        parts = (mpm_particles * m)()
+        mats = (mpm_material * m)()
+        perms = (C.c_void_p * m)()
+        for i, w in enumerate(self.ws):
+            K, P, M = _point_structs(w)
+            self._keep.append(K)
+            grids[i], parts[i], mats[i] = _grid(w), P, M
+            perms[i] = K["k"].ctypes.data
+        o = _options(w0, stream, opts)
+        self.options = o
+        ctx = C.c_void_p()
+        rc = lib.mpm_create_batch(m, grids, parts, mats, C.cast(perms, C.c_void_p), C.byref(o),
+                                  C.byref(ctx))
+        if rc != MPM_OK:
+            raise MPMError(rc, "mpm_create_batch failed")
+        self.ctx = ctx
+        self.t = 0.0
+        self._bcs_sent = False
+        self.starts = np.concatenate([[0], np.cumsum([w.n for w in self.ws])])
+
+    def _check(self, rc, what):
+        if rc != MPM_OK:
+            msg = self.lib.mpm_last_error(self.ctx)
+            raise MPMError(rc, f"{what}: {msg.decode() if msg else ''}")
+
+    def step(self, dt=None):
+        """All instances t -> t + dt with each workload's traction at t + dt."""
+        dt = self.ws[0].dt if dt is None else dt
+        m = len(self.ws)
+        loads = (mpm_loads * m)()
+        self._trac = []
+        for i, w in enumerate(self.ws):
+            tr = np.ascontiguousarray(w.trac_full, dtype=np.float64)
+            self._trac.append(tr)
+            loads[i] = mpm_loads(traction=_p(tr) if w.n_surf else None, flux=None,
+                                 scale=w.load_scale(self.t + dt))
+        bp = None
+        if not self._bcs_sent:
+            bcs = (mpm_bcs * m)()
+            self._bc = []
+            for i, w in enumerate(self.ws):
+                b = (np.ascontiguousarray(w.u_fixed, dtype=np.uint8), _f64(w.u_value),
+                     np.ascontiguousarray(w.p_fixed, dtype=np.uint8), _f64(w.p_value))
+                self._bc.append(b)
+                bcs[i] = mpm_bcs(u_fixed=_p(b[0]), u_value=_p(b[1]), p_fixed=_p(b[2]), p_value=_p(b[3]))
+            bp = C.cast(bcs, C.c_void_p)
+        rc = self.lib.mpm_step_batch(self.ctx, C.c_double(dt), C.cast(loads, C.c_void_p), bp)
+        self._check(rc, "mpm_step_batch")
+        self._bcs_sent = True
+        self.t += dt
+        return self.stats()
+
+    def stats(self):
+        s = mpm_stats()
+        self._check(self.lib.mpm_get_stats(self.ctx, C.byref(s)), "mpm_get_stats")
+        k = s.newton_iters
+        return {"newton_iters": k, "krylov_iters": list(s.krylov_iters[:k]),
+                "krylov_total": s.krylov_total, "steps": s.steps, "nnzb": s.nnzb,
+                "kernel_launches": s.kernel_launches}
+
+    def read(self, fields=("x", "u", "p")):
+        """Per-instance dicts of the point fields (each in its own order)."""
+        n = int(self.starts[-1])
+        allf = _read(self.lib, self.ctx, n, self.ws[0].dim, fields, self._check)
+        return [{k: v[self.starts[i]:self.starts[i + 1]] for k, v in allf.items()}
+                for i in range(len(self.ws))]
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -7,7 +7,8 @@ Algorithm (as in the library):
   * scaled system  D J D,  D_ii = |J_ii|^{-1/2} (1 where J_ii = 0);
   * blocks of the unscaled J: A (u-u), B1 (u-p), B2 (p-u), C (p-p);
   * S = C - B2 diag_blocks(A)^{-1} B1 kept on the block sparsity of J, the
-    dropped part of every row added to its diagonal;
+    dropped part of every row added to its diagonal; or (fixed stress) S = C
+    plus a given lumped term fs on the diagonal of the free pressure rows;
   * z_p = V(S) v_p,  z_u = V(A) (v_u - B1 z_p), preconditioner of the scaled
     system  z = D^{-1} M^{-1} (D^{-1} v);
   * V-cycle: factor-2 vertex coarsening per axis ((n + 1) // 2 nodes) while
@@ -97,7 +98,7 @@ class SchurMG:
     """Preconditioner of D J D for the unscaled block-CSR Jacobian J (after
     Dirichlet elimination) with sparsity (row_ptr, col) and fixed-DOF mask."""
 
-    def __init__(self, J, row_ptr, col, fixed, nn, dim):
+    def __init__(self, J, row_ptr, col, fixed, nn, dim, fs=None):
         nb = dim + 1
         J = J.tocsr()
         N = J.shape[0]
@@ -111,12 +112,15 @@ class SchurMG:
         self.B1 = J[iu][:, ip].tocsr()
         B2 = J[ip][:, iu].tocsr()
         C = J[ip][:, ip].tocsr()
-        prod = (B2 @ block_inv(A, dim) @ self.B1).tocsr()
-        rows = np.repeat(np.arange(nnod), np.diff(row_ptr))
-        pat = sps.csr_matrix((np.ones(len(col)), (rows, col)), shape=(nnod, nnod))
-        kept = prod.multiply(pat).tocsr()
-        lump = np.asarray(prod.sum(axis=1)).ravel() - np.asarray(kept.sum(axis=1)).ravel()
-        S = (C - kept - sps.diags(lump)).tocsr()
+        if fs is not None:
+            S = (C + sps.diags(np.where(fixed[ip], 0.0, fs))).tocsr()
+        else:
+            prod = (B2 @ block_inv(A, dim) @ self.B1).tocsr()
+            rows = np.repeat(np.arange(nnod), np.diff(row_ptr))
+            pat = sps.csr_matrix((np.ones(len(col)), (rows, col)), shape=(nnod, nnod))
+            kept = prod.multiply(pat).tocsr()
+            lump = np.asarray(prod.sum(axis=1)).ravel() - np.asarray(kept.sum(axis=1)).ravel()
+            S = (C - kept - sps.diags(lump)).tocsr()
         self.LA = hierarchy(A, nn, dim, dim, ~fixed[iu])
         self.LS = hierarchy(S, nn, dim, 1, ~fixed[ip])
 
@@ -128,3 +132,32 @@ class SchurMG:
         z[self.iu] = zu
         z[self.ip] = zp
         return z / self.D
+
+
+def fixed_stress_diag(w, prep):
+    """Lumped fixed-stress term at the start of the first step (Delta J = 1,
+    J_n = 1): fs_a = sum_p S'_ap V_p / (dt K_p), K = lambda + 2 G / dim, with
+    S' the basis renormalised over the point's active support nodes."""
+    d = w.dim
+    first, count, S, act = prep["first"], prep["count"], prep["S"], prep["active"]
+    nnx = [w.ncell[k] + 1 for k in range(d)] + [1, 1]
+    lam = w.E * w.nu / ((1 + w.nu) * (1 - 2 * w.nu))
+    G = w.E / (2 * (1 + w.nu))
+    coef = w.vol / (w.dt * (lam + 2 * G / d))
+    out = np.zeros(int(np.prod(nnx[:d])))
+    for p in range(w.n):
+        cnt = [count[p, k] if k < d else 1 for k in range(3)]
+        nodes, vals = [], []
+        for o2 in range(cnt[2]):
+            for o1 in range(cnt[1]):
+                for o0 in range(cnt[0]):
+                    o = (o0, o1, o2)
+                    c = [first[p, k] + o[k] if k < d else 0 for k in range(3)]
+                    a = c[0] + nnx[0] * (c[1] + nnx[1] * c[2])
+                    if act[a]:
+                        nodes.append(a)
+                        vals.append(np.prod([S[p, k, o[k]] for k in range(d)]))
+        tot = sum(vals)
+        for a, v in zip(nodes, vals):
+            out[a] += v / tot * coef[p]
+    return out
