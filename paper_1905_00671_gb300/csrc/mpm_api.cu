@@ -320,18 +320,6 @@ int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
     run_scale_system<T>(c, S, c.R);
     run_block_jacobi<T>(c, S);
   }
-  // batched instances: each instance's right-hand side is weighted by the
-  // inverse of its residual norm, so that the one relative Krylov tolerance
-  // applies to every instance alike (the system is block diagonal over the
-  // instances: the weighted solution is the weighted exact one)
-  if (c.ninst > 1) {
-    for (int i = 0; i < c.ninst; ++i) {
-      const double r = sqrt(c.h_inorm[i]);
-      c.h_iw[i] = r > 0.0 ? 1.0 / r : 1.0;
-    }
-    cudaMemcpyAsync(c.iw, c.h_iw, sizeof(double) * c.ninst, cudaMemcpyHostToDevice, c.st);
-    run_inst_weight<T>(c, S.rhs, 0);
-  }
   rc = read_dev_err(c);
   if (rc) return rc;
   const bool inexact = sizeof(T) < sizeof(double);
@@ -343,7 +331,6 @@ int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
     else if (rc == MPM_ERR_NONFINITE) c.last_error = "non-finite value in FGMRES";
     return rc;
   }
-  if (c.ninst > 1) run_inst_weight<T>(c, S.x, 1);
   run_unscale_add<T>(c, S, c.X);
   return MPM_OK;
 }
@@ -450,11 +437,11 @@ void free_all(Ctx &c) {
                   c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.fsd, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
-                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp, c.terms, c.inst, c.inorm, c.iw, c.node_inst};
+                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp, c.terms, c.inst, c.inorm, c.node_inst, c.bk, c.bk_i};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.h_inorm) cudaFreeHost(c.h_inorm);
-  if (c.h_iw) cudaFreeHost(c.h_iw);
+  if (c.h_bk) cudaFreeHost(c.h_bk);
   if (c.h_err) cudaFreeHost(c.h_err);
   if (c.h_scalar) cudaFreeHost(c.h_scalar);
   if (c.h_terms) cudaFreeHost(c.h_terms);
@@ -648,10 +635,13 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
     rc = MPM_ERR_NO_MEMORY;
   A(&c.inst, c.ninst);
   A(&c.inorm, c.ninst);
-  A(&c.iw, c.ninst);
   A(&c.node_inst, nn);
+  // batched FGMRES state: H ((m+1) m), g, cs, sn, y (m+1 each), h1, h2 (PSTR
+  // each), norm, scale, beta, target, residual per instance
+  A(&c.bk, (int64_t)c.ninst * ((int64_t)(m + 1) * m + 5 * (m + 1) + 2 * 129 + 5));
+  A(&c.bk_i, 2 * (int64_t)c.ninst + 1);
   if (!rc && (cudaHostAlloc((void **)&c.h_inorm, sizeof(double) * c.ninst, cudaHostAllocDefault) != cudaSuccess ||
-              cudaHostAlloc((void **)&c.h_iw, sizeof(double) * c.ninst, cudaHostAllocDefault) != cudaSuccess))
+              cudaHostAlloc((void **)&c.h_bk, sizeof(double) * 4, cudaHostAllocDefault) != cudaSuccess))
     rc = MPM_ERR_NO_MEMORY;
   if (rc) {
     free_all(c);

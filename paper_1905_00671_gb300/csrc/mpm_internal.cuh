@@ -198,7 +198,10 @@ struct Ctx {
   double *inorm = nullptr;             // device: per-instance squared residual norms
   double *h_inorm = nullptr;           // pinned copy
   int32_t *node_inst = nullptr;        // device: instance of every node (-1: between instances)
-  double *iw = nullptr, *h_iw = nullptr;  // per-instance weights of the Krylov right-hand side
+  // batched FGMRES: per-instance Krylov state (ninst x ...), see mpm_solver.cu
+  double *bk = nullptr;                // one block of device doubles, carved below
+  int32_t *bk_i = nullptr;             // per-instance flags / column counts
+  double *h_bk = nullptr;              // pinned: active-instance count
   bool capturing = false;    // a CUDA graph capture is in progress on st
   int64_t n = 0;
   int32_t n_surf = 0;
@@ -300,8 +303,7 @@ template <typename T>
 void run_precond(Ctx &c, LinSys<T> &S, const T *v, T *z);  // z = M^{-1} v (scaled system)
 template <typename T>
 void run_unscale_add(Ctx &c, const LinSys<T> &S, double *X);  // X += D x
-template <typename T>
-void run_inst_weight(Ctx &c, T *v, int divide);  // batched: v *= (or /=) instance weight per node
+
 double run_norm(Ctx &c, const double *x);          // synchronises
 
 // Schur-complement multigrid preconditioner

@@ -502,6 +502,150 @@ int fgmres_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
   return converged ? MPM_OK : MPM_ERR_KRYLOV_STAGNATED;
 }
 
+// ------------------------------------------------ batched FGMRES (instances)
+// A batched context solves one block-diagonal system (the instances never
+// couple; the preconditioner keeps that structure), so FGMRES runs per
+// instance: every inner product, Hessenberg column, Givens rotation and
+// convergence test is the instance's own, while each kernel serves all
+// instances at once.  An instance that meets its tolerance is frozen (its next
+// Krylov vectors are zero) until the others finish.
+
+// out[i * ostride + k] = sum over the DOFs of instance i of V_k . w, k < cnt;
+// block (i, k) walks instance i's node box in a fixed order
+template <typename T>
+__global__ void k_inst_dots(GridP g, int nb, const InstDev *__restrict__ inst, const T *__restrict__ V,
+                            int64_t vstride, const T *__restrict__ w, double *__restrict__ out, int ostride) {
+  const InstDev I = inst[blockIdx.x];
+  const int k = blockIdx.y;
+  const T *Vk = V + (int64_t)k * vstride;
+  const int64_t m0 = I.nc[0] + 1, m1 = g.d > 1 ? I.nc[1] + 1 : 1, m2 = g.d > 2 ? I.nc[2] + 1 : 1;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < m0 * m1 * m2; t += blockDim.x) {
+    const int64_t i0 = t % m0, i1 = (t / m0) % m1, i2 = t / (m0 * m1);
+    const int64_t a = (i0 + I.off[0]) + (int64_t)g.nn[0] * ((i1 + I.off[1]) + (int64_t)g.nn[1] * (i2 + I.off[2]));
+    for (int d = 0; d < nb; ++d) acc += (double)Vk[a * nb + d] * (double)w[a * nb + d];
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[(int64_t)blockIdx.x * ostride + k] = acc;
+}
+
+// w -= sum_k h[inst, k] V_k
+template <typename T>
+__global__ void k_inst_orth(int64_t N, int nb, const int32_t *__restrict__ node_inst, T *__restrict__ w,
+                            const T *__restrict__ V, int64_t vstride, const double *__restrict__ h, int cnt) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const int i = node_inst[e / nb];
+  if (i < 0) return;
+  T s = w[e];
+  for (int k = 0; k < cnt; ++k) s -= (T)h[(int64_t)i * PSTR + k] * V[(int64_t)k * vstride + e];
+  w[e] = s;
+}
+
+// out = scale[inst] w (0 between instances)
+template <typename T>
+__global__ void k_inst_scale(int64_t N, int nb, const int32_t *__restrict__ node_inst, const T *__restrict__ w,
+                             const double *__restrict__ scl, T *__restrict__ out) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const int i = node_inst[e / nb];
+  out[e] = i < 0 ? T(0) : (T)(scl[i] * (double)w[e]);
+}
+
+// start of a cycle: beta_i = ||r_i||, g_i = beta_i e_1, scale 1 / beta_i; the
+// tolerance rtol beta_i is fixed at the first start; an instance already
+// within it is frozen
+__global__ void k_inst_init(int ni, int m, const double *__restrict__ nrm, double *__restrict__ g,
+                            double *__restrict__ scl, double *__restrict__ tgt, int32_t *__restrict__ frozen,
+                            int32_t *__restrict__ jc, int32_t *__restrict__ active, double rtol, int set_target) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ni) return;
+  const double beta = sqrt(nrm[i]);
+  if (set_target) tgt[i] = rtol * beta;
+  for (int k = 0; k <= m; ++k) g[(int64_t)i * (m + 1) + k] = 0.0;
+  g[(int64_t)i * (m + 1)] = beta;
+  jc[i] = 0;
+  const bool done = !(beta > tgt[i]);
+  frozen[i] = done ? 1 : 0;
+  scl[i] = (!done && beta > 0.0) ? 1.0 / beta : 0.0;
+  if (!done) atomicAdd(active, 1);
+}
+
+// Arnoldi column j of every active instance: H(:, j) = h1 + h2, previous
+// rotations, new rotation, g update, residual estimate |g_{j+1}|; an instance
+// whose estimate reaches its tolerance (or whose new vector vanishes) freezes
+// with j + 1 columns
+__global__ void k_inst_arnoldi(int ni, int j, int m, const double *__restrict__ h1, const double *__restrict__ h2,
+                               const double *__restrict__ nrm, double *__restrict__ H, double *__restrict__ g,
+                               double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ scl,
+                               const double *__restrict__ tgt, double *__restrict__ res,
+                               int32_t *__restrict__ frozen, int32_t *__restrict__ jc, int32_t *__restrict__ active) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ni) return;
+  if (frozen[i]) {
+    scl[i] = 0.0;
+    return;
+  }
+  double *Hi = H + (int64_t)i * (m + 1) * m, *gi = g + (int64_t)i * (m + 1);
+  double *csi = cs + (int64_t)i * (m + 1), *sni = sn + (int64_t)i * (m + 1);
+  const double hn = sqrt(nrm[i]);
+  double col[PSTR];
+  for (int k = 0; k <= j; ++k) col[k] = h1[(int64_t)i * PSTR + k] + h2[(int64_t)i * PSTR + k];
+  for (int k = 0; k < j; ++k) {
+    const double t = csi[k] * col[k] + sni[k] * col[k + 1];
+    col[k + 1] = -sni[k] * col[k] + csi[k] * col[k + 1];
+    col[k] = t;
+  }
+  const double r = hypot(col[j], hn);
+  double c = 1.0, sv = 0.0;
+  if (r > 0.0) {
+    c = col[j] / r;
+    sv = hn / r;
+  }
+  csi[j] = c;
+  sni[j] = sv;
+  col[j] = r;
+  for (int k = 0; k <= j; ++k) Hi[k * m + j] = col[k];
+  const double gj = gi[j];
+  gi[j + 1] = -sv * gj;
+  gi[j] = c * gj;
+  res[i] = fabs(gi[j + 1]);
+  jc[i] = j + 1;
+  if (res[i] <= tgt[i] || !(hn > 0.0)) {
+    frozen[i] = 1;
+    scl[i] = 0.0;
+  } else {
+    scl[i] = 1.0 / hn;
+    atomicAdd(active, 1);
+  }
+}
+
+__global__ void k_inst_backsolve(int ni, int m, const double *__restrict__ H, const double *__restrict__ g,
+                                 const int32_t *__restrict__ jc, double *__restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ni) return;
+  const double *Hi = H + (int64_t)i * (m + 1) * m, *gi = g + (int64_t)i * (m + 1);
+  double *yi = y + (int64_t)i * (m + 1);
+  for (int k = jc[i] - 1; k >= 0; --k) {
+    double sv = gi[k];
+    for (int l = k + 1; l < jc[i]; ++l) sv -= Hi[k * m + l] * yi[l];
+    yi[k] = Hi[k * m + k] != 0.0 ? sv / Hi[k * m + k] : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void k_inst_update_x(int64_t N, int nb, const int32_t *__restrict__ node_inst, T *__restrict__ x,
+                                const T *__restrict__ Z, int64_t zstride, const double *__restrict__ y, int m,
+                                const int32_t *__restrict__ jc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const int i = node_inst[e / nb];
+  if (i < 0) return;
+  T sv = x[e];
+  for (int k = 0; k < jc[i]; ++k) sv += (T)y[(int64_t)i * (m + 1) + k] * Z[(int64_t)k * zstride + e];
+  x[e] = sv;
+}
+
 template <typename T>
 int dmalloc(T **p, int64_t n) {
   return cudaMalloc((void **)p, sizeof(T) * (size_t)(n > 0 ? n : 1)) == cudaSuccess ? MPM_OK
@@ -591,24 +735,6 @@ void run_scale_system(Ctx &c, LinSys<T> &S, const double *R) {
 }
 
 template <typename T>
-__global__ void k_inst_weight(int64_t N, int nb, const int32_t *__restrict__ node_inst,
-                              const double *__restrict__ w, T *__restrict__ v, int divide) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int inst = node_inst[i / nb];
-  if (inst < 0) return;
-  v[i] = divide ? (T)(v[i] / w[inst]) : (T)(v[i] * w[inst]);
-}
-
-template <typename T>
-void run_inst_weight(Ctx &c, T *v, int divide) {
-  k_inst_weight<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), c.nb, c.node_inst, c.iw, v, divide);
-  UPMPM_LAUNCH(c);
-}
-template void run_inst_weight<double>(Ctx &, double *, int);
-template void run_inst_weight<float>(Ctx &, float *, int);
-
-template <typename T>
 void run_unscale_add(Ctx &c, const LinSys<T> &S, double *X) {
   k_unscale_add<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), X, S.dscale, S.x);
   UPMPM_LAUNCH(c);
@@ -630,8 +756,88 @@ void run_precond(Ctx &c, LinSys<T> &S, const T *v, T *z) {
   else precond<4, T>(c, S, v, z);
 }
 
+int read_active(Ctx &c, const int32_t *dptr) {
+  int32_t *h = reinterpret_cast<int32_t *>(c.h_bk);
+  cudaMemcpyAsync(h, dptr, sizeof(int32_t), cudaMemcpyDeviceToHost, c.st);
+  cudaStreamSynchronize(c.st);
+  return h[0];
+}
+
+template <int NB, typename T>
+int fgmres_batched_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
+  const int64_t N = c.N();
+  const int m = c.m_restart, ni = c.ninst;
+  const int gN = nblk(N);
+  const T *b = S.rhs;
+  T *x = S.x, *w = S.w;
+  double *H = c.bk, *g = H + (int64_t)ni * (m + 1) * m, *cs = g + (int64_t)ni * (m + 1);
+  double *sn = cs + (int64_t)ni * (m + 1), *y = sn + (int64_t)ni * (m + 1);
+  double *h1 = y + (int64_t)ni * (m + 1), *h2 = h1 + (int64_t)ni * PSTR, *nrm = h2 + (int64_t)ni * PSTR;
+  double *scl = nrm + ni, *tgt = scl + ni, *res = tgt + ni;
+  int32_t *frozen = c.bk_i, *jc = frozen + ni, *active = jc + ni;
+  const int ib = nblk(ni, 128);
+  cudaMemsetAsync(x, 0, sizeof(T) * N, c.st);
+  auto start = [&](const T *r, int set_target) {
+    k_inst_dots<T><<<dim3(ni, 1), TPB, 0, c.st>>>(c.g, NB, c.inst, r, N, r, nrm, 1);
+    cudaMemsetAsync(active, 0, sizeof(int32_t), c.st);
+    k_inst_init<<<ib, 128, 0, c.st>>>(ni, m, nrm, g, scl, tgt, frozen, jc, active, rtol, set_target);
+    k_inst_scale<T><<<gN, TPB, 0, c.st>>>(N, NB, c.node_inst, r, scl, S.V);
+    c.launches += 3;
+    return read_active(c, active);
+  };
+  *iters = 0;
+  int nact = start(b, 1);
+  if (nact == 0) return MPM_OK;
+  int total = 0;
+  bool converged = false;
+  while (true) {
+    for (int j = 0; j < m; ++j) {
+      T *Vj = S.V + (int64_t)j * N, *Zj = S.Z + (int64_t)j * N, *Vn = S.V + (int64_t)(j + 1) * N;
+      precond<NB, T>(c, S, Vj, Zj);
+      spmv<NB, T>(c, S, Zj, w);
+      prof_begin(c, MPM_PROF_ORTH);
+      k_inst_dots<T><<<dim3(ni, j + 1), TPB, 0, c.st>>>(c.g, NB, c.inst, S.V, N, w, h1, PSTR);
+      k_inst_orth<T><<<gN, TPB, 0, c.st>>>(N, NB, c.node_inst, w, S.V, N, h1, j + 1);
+      k_inst_dots<T><<<dim3(ni, j + 1), TPB, 0, c.st>>>(c.g, NB, c.inst, S.V, N, w, h2, PSTR);
+      k_inst_orth<T><<<gN, TPB, 0, c.st>>>(N, NB, c.node_inst, w, S.V, N, h2, j + 1);
+      k_inst_dots<T><<<dim3(ni, 1), TPB, 0, c.st>>>(c.g, NB, c.inst, w, N, w, nrm, 1);
+      prof_end(c, MPM_PROF_ORTH);
+      cudaMemsetAsync(active, 0, sizeof(int32_t), c.st);
+      k_inst_arnoldi<<<ib, 128, 0, c.st>>>(ni, j, m, h1, h2, nrm, H, g, cs, sn, scl, tgt, res, frozen, jc,
+                                           active);
+      k_inst_scale<T><<<gN, TPB, 0, c.st>>>(N, NB, c.node_inst, w, scl, Vn);
+      c.launches += 7;
+      ++total;
+      nact = read_active(c, active);
+      if (nact == 0) {
+        converged = true;
+        break;
+      }
+      if (total >= maxit) break;
+    }
+    k_inst_backsolve<<<ib, 128, 0, c.st>>>(ni, m, H, g, jc, y);
+    k_inst_update_x<T><<<gN, TPB, 0, c.st>>>(N, NB, c.node_inst, x, S.Z, N, y, m, jc);
+    c.launches += 2;
+    if (converged || total >= maxit) break;
+    // restart every instance from its true residual r = b - A x
+    spmv<NB, T>(c, S, x, w);
+    k_residual_vec<T><<<gN, TPB, 0, c.st>>>(w, b, N);
+    UPMPM_LAUNCH(c);
+    if (start(w, 0) == 0) {
+      converged = true;
+      break;
+    }
+  }
+  *iters = total;
+  if (check_cuda(c, cudaGetLastError(), "fgmres")) return MPM_ERR_CUDA;
+  return converged ? MPM_OK : MPM_ERR_KRYLOV_STAGNATED;
+}
+
 template <typename T>
 int run_fgmres(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
+  if (c.ninst > 1)
+    return c.nb == 3 ? fgmres_batched_impl<3, T>(c, S, rtol, maxit, iters)
+                     : fgmres_batched_impl<4, T>(c, S, rtol, maxit, iters);
   if (c.nb == 3) return fgmres_impl<3, T>(c, S, rtol, maxit, iters);
   return fgmres_impl<4, T>(c, S, rtol, maxit, iters);
 }
