@@ -302,7 +302,7 @@ struct LevelDev {
   const uint64_t *mask;           // level 0 only: coupling mask of the block sparsity
   // instance of every node (-1 between instances): the transfers connect a
   // fine and a coarse node only within one instance, so the hierarchy of a
-  // batched context never mixes instances (a single instance: all 0)
+  // batched context never mixes instances (null for a single instance)
   const int32_t *inst;
 };
 
@@ -408,6 +408,49 @@ __global__ void k_mg_smooth(LevelDev L, const real *__restrict__ xi, real *__res
     for (int j = 0; j < B; ++j) s = fma(L.dinv[a * B * B + i * B + j], r[j], s);
     xo[a * B + i] = (zero_init ? 0.0 : xi[a * B + i]) + omega * s;
   }
+}
+
+// Fine (block-CSR) level with B <= 2, a group of GS = B * SPL lanes per row:
+// lane (r, part) sums block row r over the row's blocks part, part + SPL, ...
+// (one FMA per stored value, all lanes busy), one shuffle sum over the SPL
+// parts gives (A x)_r, and for a sweep the row's B residuals are exchanged
+// inside the group: out = b - A x (residual) or x + omega Dinv (b - A x).
+template <int B, int SPL, bool SMOOTH>
+__global__ void k_mg_csr_row(LevelDev L, const real *__restrict__ x, real *__restrict__ out,
+                             const real *__restrict__ b, real omega) {
+  constexpr int GS = B * SPL;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / GS;
+  const int lg = (int)(t - a * GS);
+  const int r = lg / SPL, part = lg - r * SPL;
+  const bool valid = a < L.nnodes;
+  real acc = 0;
+  if (valid) {
+    const int e1 = L.row_ptr[a + 1];
+#pragma unroll 4
+    for (int e = L.row_ptr[a] + part; e < e1; e += SPL) {
+      const real *blk = L.val + (int64_t)e * B * B + r * B;
+      const real *xb = x + (int64_t)L.col[e] * B;
+#pragma unroll
+      for (int c = 0; c < B; ++c) acc = fma(blk[c], xb[c], acc);
+    }
+  }
+#pragma unroll
+  for (int o = SPL / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const real res = valid ? b[a * B + r] - acc : real(0);
+  if (!SMOOTH) {
+    if (valid && part == 0) out[a * B + r] = res;
+    return;
+  }
+  const int base = (int)(threadIdx.x & 31) - lg;
+  real rv[B];
+#pragma unroll
+  for (int c = 0; c < B; ++c) rv[c] = __shfl_sync(0xffffffffu, res, base + c * SPL);
+  if (!valid || part != 0) return;
+  real sum = 0;
+#pragma unroll
+  for (int c = 0; c < B; ++c) sum = fma(L.dinv[a * B * B + r * B + c], rv[c], sum);
+  out[a * B + r] = x[a * B + r] + omega * sum;
 }
 
 template <int B, int D, bool ST>
@@ -598,7 +641,7 @@ __global__ void k_mg_restrict(LevelDev F, LevelDev Cl, const real *__restrict__ 
         if (a0 < 0 || a0 >= F.nn[0] || a1 < 0 || a1 >= F.nn[1] || a2 < 0 || a2 >= F.nn[2]) continue;
         const real wgt = pw(a0, Ic[0]) * pw(a1, Ic[1]) * (D == 3 ? pw(a2, Ic[2]) : 1.0);
         const int64_t a = a0 + (int64_t)F.nn[0] * (a1 + (int64_t)F.nn[1] * a2);
-        if (F.inst[a] != Cl.inst[I]) continue;
+        if (F.inst && F.inst[a] != Cl.inst[I]) continue;
         for (int i = 0; i < B; ++i) acc[i] += wgt * free_w(F, a, i) * rf[a * B + i];
       }
   for (int i = 0; i < B; ++i) bc[I * B + i] = acc[i];
@@ -634,7 +677,7 @@ __device__ inline void prolong_at(const LevelDev &Cl, const real *__restrict__ x
     const real wgt = (s0 ? w1[0] : w0[0]) * (s1 ? w1[1] : w0[1]) * (D == 3 ? (s2 ? w1[2] : w0[2]) : 1.0);
     const int64_t I = (s0 ? i1[0] : i0[0]) +
                       (int64_t)Cl.nn[0] * ((s1 ? i1[1] : i0[1]) + (int64_t)Cl.nn[1] * (D == 3 ? (s2 ? i1[2] : i0[2]) : 0));
-    const real w = Cl.inst[I] == inst_a ? wgt : real(0);
+    const real w = (!Cl.inst || Cl.inst[I] == inst_a) ? wgt : real(0);
     for (int i = 0; i < B; ++i) out[i] = fma(w, xc[I * B + i], out[i]);
   }
 }
@@ -648,7 +691,7 @@ __global__ void k_mg_prolong(LevelDev F, LevelDev Cl, real *__restrict__ xf,
   int ac[3];
   grid_xyz(F.nn[0], F.nn[1], (int)a, ac);
   real acc[B];
-  prolong_at<B, D>(Cl, xc, ac, F.inst[a], acc);
+  prolong_at<B, D>(Cl, xc, ac, F.inst ? F.inst[a] : 0, acc);
   for (int i = 0; i < B; ++i) xf[a * B + i] += free_w(F, a, i) * acc[i];
 }
 
@@ -681,7 +724,7 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
             continue;
           const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
           const int64_t a = fa[0] + (int64_t)F.nn[0] * (fa[1] + (int64_t)F.nn[1] * fa[2]);
-          if (F.inst[a] != Cl.inst[I]) continue;
+          if (F.inst && F.inst[a] != Cl.inst[I]) continue;
           for (int b2 = lo2; b2 <= hi2; ++b2)
             for (int b1 = -1; b1 <= 1; ++b1)
               for (int b0 = -1; b0 <= 1; ++b0) {
@@ -692,7 +735,7 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
                 const real wb = pw(fb[0], Jc[0]) * pw(fb[1], Jc[1]) * (D == 3 ? pw(fb[2], Jc[2]) : 1.0);
                 {
                   const int64_t bq = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
-                  if (F.inst[bq] != Cl.inst[Jn]) continue;
+                  if (F.inst && F.inst[bq] != Cl.inst[Jn]) continue;
                 }
                 const real *blk = nullptr;
                 if (!FST) {
@@ -780,9 +823,15 @@ constexpr real MG_OMEGA = 0.6;
 template <int B, int D>
 void sweep(Ctx &c, MGHier<real> &H, int l) {
   LevelDev &L = H.L[l];
-  const Geom g = geom(c, L.nnodes * LN_<D>::v);
-  if (l == 0) k_mg_smooth<B, D, false><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
-  else k_mg_smooth<B, D, true><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+  if (l == 0 && B <= 2) {
+    constexpr int SPL = B <= 2 ? 4 / B : 1;
+    const Geom g = geom(c, L.nnodes * B * SPL);
+    k_mg_csr_row<B, SPL, true><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA);
+  } else {
+    const Geom g = geom(c, L.nnodes * LN_<D>::v);
+    if (l == 0) k_mg_smooth<B, D, false><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+    else k_mg_smooth<B, D, true><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+  }
   UPMPM_LAUNCH(c);
   std::swap(H.x[l], H.x2[l]);
 }
@@ -802,8 +851,15 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
   real *xn_first = l + 1 == H.nlev - 1 ? nullptr : H.x[l + 1];
   sweep<B, D>(c, H, l);  // second pre-smoothing sweep
   const Geom gr = geom(c, L.nnodes * LN_<D>::v), gc = geom(c, Ln.nnodes), gf = geom(c, L.nnodes);
-  if (l == 0) k_mg_resid<B, D, false><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
-  else k_mg_resid<B, D, true><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  if (l == 0 && B <= 2) {
+    constexpr int SPL = B <= 2 ? 4 / B : 1;
+    const Geom g0 = geom(c, L.nnodes * B * SPL);
+    k_mg_csr_row<B, SPL, false><<<g0.blocks, g0.tpb, 0, c.st>>>(L, H.x[l], H.r[l], H.b[l], MG_OMEGA);
+  } else if (l == 0) {
+    k_mg_resid<B, D, false><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  } else {
+    k_mg_resid<B, D, true><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+  }
   k_mg_restrict<B, D><<<gc.blocks, gc.tpb, 0, c.st>>>(L, Ln, H.r[l], H.b[l + 1], xn_first, MG_OMEGA);
   c.launches += 2;
   vcycle_t<B, D>(c, H, l + 1);
@@ -851,8 +907,10 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
       return MPM_ERR_NO_MEMORY;
     if (l > 0 && cudaMalloc(&L.sval, sizeof(real) * L.nnodes * NS * B * B)) return MPM_ERR_NO_MEMORY;
     int32_t *dinst = nullptr;
-    if (cudaMalloc(&dinst, sizeof(int32_t) * L.nnodes) != cudaSuccess) return MPM_ERR_NO_MEMORY;
-    cudaMemcpy(dinst, imap.data(), sizeof(int32_t) * L.nnodes, cudaMemcpyHostToDevice);
+    if (c.ninst > 1) {
+      if (cudaMalloc(&dinst, sizeof(int32_t) * L.nnodes) != cudaSuccess) return MPM_ERR_NO_MEMORY;
+      cudaMemcpy(dinst, imap.data(), sizeof(int32_t) * L.nnodes, cudaMemcpyHostToDevice);
+    }
     L.inst = dinst;
     ++l;
     int mn = 1 << 30;
