@@ -283,18 +283,34 @@ __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
 }
 
 // ---------------------------------------------------------------- FGMRES
-// partial dots of w against V_0..V_{cnt-1}
+// Partial dots of w against V_0..V_{cnt-1}, block (b, i) summing its slice of
+// V_i . w: the cnt products run side by side instead of one after another.
 template <typename T>
-__global__ void k_multidot_partial(const T *__restrict__ V, int cnt, const T *__restrict__ w,
-                                   int64_t n, double *__restrict__ part) {
-  for (int i = 0; i < cnt; ++i) {
-    const T *vi = V + (int64_t)i * n;
-    T acc = 0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x)
-      acc += vi[k] * w[k];
-    const double s = block_sum((double)acc);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = s;
+__global__ void k_multidot2(const T *__restrict__ V, const T *__restrict__ w, int64_t n,
+                            double *__restrict__ part) {
+  const int i = blockIdx.y;
+  const T *vi = V + (int64_t)i * n;
+  T acc = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    acc += vi[k] * w[k];
+  const double s = block_sum((double)acc);
+  if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = s;
+}
+
+// w -= sum_i h_i V_i; with want_norm also the partial sums of |w|^2
+template <typename T>
+__global__ void k_orth_sub(T *__restrict__ w, const T *__restrict__ V, const double *__restrict__ h, int cnt,
+                           int64_t n, double *__restrict__ part, int want_norm) {
+  T nacc = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    T sv = w[k];
+    for (int i = 0; i < cnt; ++i) sv -= (T)h[i] * V[(int64_t)i * n + k];
+    w[k] = sv;
+    nacc += sv * sv;
+  }
+  if (want_norm) {
+    const double sn = block_sum((double)nacc);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR] = sn;
   }
 }
 
@@ -306,36 +322,6 @@ __global__ void k_multidot_reduce(const double *__restrict__ part, int np, int c
   for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * PSTR + i];
   acc = block_sum(acc);
   if (threadIdx.x == 0) h[i] = acc;
-}
-
-// w -= sum_i h_i V_i over the thread's elements, then partial dots of the
-// updated w against V_i (second Gram-Schmidt pass) or with itself (norm).
-template <typename T>
-__global__ void k_orth_update(T *__restrict__ w, const T *__restrict__ V, const double *h, int cnt,
-                              int64_t n, double *__restrict__ part, int want_norm) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    T s = w[k];
-    for (int i = 0; i < cnt; ++i) s -= (T)h[i] * V[(int64_t)i * n + k];
-    w[k] = s;
-  }
-  if (want_norm) {
-    T acc = 0;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-         k += (int64_t)gridDim.x * blockDim.x)
-      acc += w[k] * w[k];
-    const double s = block_sum((double)acc);
-    if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR] = s;
-  } else {
-    for (int i = 0; i < cnt; ++i) {
-      T acc = 0;
-      for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-           k += (int64_t)gridDim.x * blockDim.x)
-        acc += V[(int64_t)i * n + k] * w[k];
-      const double s = block_sum((double)acc);
-      if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = s;
-    }
-  }
 }
 
 // Finish Arnoldi column j: ||w|| from the partials, H(:,j) = h1 + h2, apply
@@ -459,15 +445,20 @@ int fgmres_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
       precond<NB, T>(c, S, Vj, Zj);
       spmv<NB, T>(c, S, Zj, w);
       prof_begin(c, MPM_PROF_ORTH);
-      k_multidot_partial<T><<<NPART, TPB, 0, c.st>>>(S.V, j + 1, w, N, c.part);
-      k_multidot_reduce<<<j + 1, TPB, 0, c.st>>>(c.part, NPART, j + 1, h1);
-      k_orth_update<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h1, j + 1, N, c.part, 0);
-      k_multidot_reduce<<<j + 1, TPB, 0, c.st>>>(c.part, NPART, j + 1, h2);
-      k_orth_update<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h2, j + 1, N, c.part, 1);
+      {  // classical Gram-Schmidt, twice; the j + 1 products of a pass run side by side
+        const int cnt = j + 1;
+        const int nbx = std::min(NPART, std::max(16, NPART / cnt));
+        k_multidot2<T><<<dim3(nbx, cnt), TPB, 0, c.st>>>(S.V, w, N, c.part);
+        k_multidot_reduce<<<cnt, TPB, 0, c.st>>>(c.part, nbx, cnt, h1);
+        k_orth_sub<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h1, cnt, N, c.part, 0);
+        k_multidot2<T><<<dim3(nbx, cnt), TPB, 0, c.st>>>(S.V, w, N, c.part);
+        k_multidot_reduce<<<cnt, TPB, 0, c.st>>>(c.part, nbx, cnt, h2);
+        k_orth_sub<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h2, cnt, N, c.part, 1);
+      }
       prof_end(c, MPM_PROF_ORTH);
       k_arnoldi_finish<<<1, TPB, 0, c.st>>>(c.part, NPART, j, m, h1, h2, c.H, c.gvec, c.cs, c.sn, c.scal);
       k_scale_copy<T><<<gN, TPB, 0, c.st>>>(Vn, w, c.scal + 1, N);
-      c.launches += 7;
+      c.launches += 8;
       ++total;
       jc = j + 1;
       const double res = read_scalar(c, c.scal);
