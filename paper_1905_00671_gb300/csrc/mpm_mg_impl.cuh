@@ -695,6 +695,126 @@ __global__ void k_mg_prolong(LevelDev F, LevelDev Cl, real *__restrict__ xf,
   for (int i = 0; i < B; ++i) xf[a * B + i] += free_w(F, a, i) * acc[i];
 }
 
+// ---- coarse tail of a V-cycle in one thread block (FP32 hierarchies)
+// On the small coarse levels each kernel of a V-cycle is a few microseconds
+// of launch and drain for very little work; one block of 1024 threads runs the
+// whole tail (every level below a size limit down to the dense coarsest
+// solve) with a block barrier between the phases.  Same operations and order
+// of levels as the kernel-per-phase V(2,2) cycle.
+constexpr int TAIL_MAX_LEVELS = 8;
+constexpr int TAIL_MAX_NODES = 128;  // one pass of the block per phase: larger levels are latency-bound here
+constexpr int TAIL_THREADS = 1024;
+
+struct TailLevel {
+  LevelDev L;
+  real *x, *x2, *b, *r;
+};
+struct TailArgs {
+  int nl;  // levels of the tail, the last one the dense coarsest level
+  TailLevel lv[TAIL_MAX_LEVELS];
+  const real *Ai;
+  int ncoarse;
+  real omega;
+};
+
+template <int B, int D, bool SMOOTH>
+__device__ inline void tail_rows(const LevelDev &L, const real *x, real *out, const real *b, real omega) {
+  constexpr int LN = LN_<D>::v;
+  const int64_t total = L.nnodes * LN;
+  for (int64_t base = 0; base < total; base += blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    const int64_t a = t / LN;
+    const int lane = (int)(t % LN);
+    const bool valid = a < L.nnodes;
+    real ax[B];
+    for (int i = 0; i < B; ++i) ax[i] = 0.0;
+    if (valid) row_partial<B, D, true, LN>(L, a, lane, x, ax);
+    lane_reduce<B, LN>(ax);
+    if (!valid || lane != 0) continue;
+    real r[B];
+    for (int i = 0; i < B; ++i) r[i] = b[a * B + i] - ax[i];
+    if (!SMOOTH) {
+      for (int i = 0; i < B; ++i) out[a * B + i] = r[i];
+      continue;
+    }
+    for (int i = 0; i < B; ++i) {
+      real sv = 0.0;
+      for (int j = 0; j < B; ++j) sv = fma(L.dinv[a * B * B + i * B + j], r[j], sv);
+      out[a * B + i] = x[a * B + i] + omega * sv;
+    }
+  }
+}
+
+template <int B, int D>
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs A) {
+  real *xs[TAIL_MAX_LEVELS], *x2s[TAIL_MAX_LEVELS];
+  for (int l = 0; l < A.nl; ++l) {
+    xs[l] = A.lv[l].x;
+    x2s[l] = A.lv[l].x2;
+  }
+  for (int l = 0; l + 1 < A.nl; ++l) {
+    const LevelDev &L = A.lv[l].L, &Ln = A.lv[l + 1].L;
+    tail_rows<B, D, true>(L, xs[l], x2s[l], A.lv[l].b, A.omega);  // second pre-smoothing sweep
+    __syncthreads();
+    real *t = xs[l]; xs[l] = x2s[l]; x2s[l] = t;
+    tail_rows<B, D, false>(L, xs[l], A.lv[l].r, A.lv[l].b, A.omega);
+    __syncthreads();
+    real *xc = l + 2 < A.nl ? xs[l + 1] : nullptr;  // first sweep from zero of the next level
+    for (int64_t I = threadIdx.x; I < Ln.nnodes; I += blockDim.x) {
+      int Ic[3];
+      grid_xyz(Ln.nn[0], Ln.nn[1], (int)I, Ic);
+      real acc[B];
+      for (int i = 0; i < B; ++i) acc[i] = 0.0;
+      const int lo2 = D == 3 ? -1 : 0, hi2 = D == 3 ? 1 : 0;
+      for (int d2 = lo2; d2 <= hi2; ++d2)
+        for (int d1 = -1; d1 <= 1; ++d1)
+          for (int d0 = -1; d0 <= 1; ++d0) {
+            const int a0 = 2 * Ic[0] + d0, a1 = 2 * Ic[1] + d1, a2 = D == 3 ? 2 * Ic[2] + d2 : 0;
+            if (a0 < 0 || a0 >= L.nn[0] || a1 < 0 || a1 >= L.nn[1] || a2 < 0 || a2 >= L.nn[2]) continue;
+            const real wgt = pw(a0, Ic[0]) * pw(a1, Ic[1]) * (D == 3 ? pw(a2, Ic[2]) : 1.0);
+            const int64_t a = a0 + (int64_t)L.nn[0] * (a1 + (int64_t)L.nn[1] * a2);
+            if (L.inst && L.inst[a] != Ln.inst[I]) continue;
+            for (int i = 0; i < B; ++i) acc[i] += wgt * A.lv[l].r[a * B + i];
+          }
+      for (int i = 0; i < B; ++i) A.lv[l + 1].b[I * B + i] = acc[i];
+      if (xc)
+        for (int i = 0; i < B; ++i) {
+          real sv = 0.0;
+          for (int j = 0; j < B; ++j) sv = fma(Ln.dinv[I * B * B + i * B + j], acc[j], sv);
+          xc[I * B + i] = A.omega * sv;
+        }
+    }
+    __syncthreads();
+  }
+  {  // dense coarsest solve, one warp per row
+    const int lc = A.nl - 1;
+    const int lane = threadIdx.x & 31;
+    for (int i = threadIdx.x >> 5; i < A.ncoarse; i += blockDim.x >> 5) {
+      real sv = 0.0;
+      for (int j = lane; j < A.ncoarse; j += 32) sv = fma(A.Ai[(int64_t)i * A.ncoarse + j], A.lv[lc].b[j], sv);
+      for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+      if (lane == 0) xs[lc][i] = sv;
+    }
+    __syncthreads();
+  }
+  for (int l = A.nl - 2; l >= 0; --l) {
+    const LevelDev &L = A.lv[l].L, &Ln = A.lv[l + 1].L;
+    for (int64_t a = threadIdx.x; a < L.nnodes; a += blockDim.x) {
+      int ac[3];
+      grid_xyz(L.nn[0], L.nn[1], (int)a, ac);
+      real acc[B];
+      prolong_at<B, D>(Ln, xs[l + 1], ac, L.inst ? L.inst[a] : 0, acc);
+      for (int i = 0; i < B; ++i) xs[l][a * B + i] += acc[i];
+    }
+    __syncthreads();
+    for (int k = 0; k < 2; ++k) {  // post-smoothing sweeps
+      tail_rows<B, D, true>(L, xs[l], x2s[l], A.lv[l].b, A.omega);
+      __syncthreads();
+      real *t = xs[l]; xs[l] = x2s[l]; x2s[l] = t;
+    }
+  }
+}
+
 // Galerkin coarse operator: one thread per (coarse node I, stencil slot).
 template <int B, int D, bool FST>
 __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
@@ -841,6 +961,20 @@ void sweep(Ctx &c, MGHier<real> &H, int l) {
 // that produced b[l]; on return x[l] holds the result.
 template <int B, int D>
 void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
+  if (sizeof(real) == sizeof(float) && l >= 1 && l < H.nlev - 1 && H.L[l].nnodes <= TAIL_MAX_NODES &&
+      H.nlev - l <= TAIL_MAX_LEVELS) {  // the rest of the cycle in one block
+    TailArgs A{};
+    A.nl = H.nlev - l;
+    for (int k = 0; k < A.nl; ++k) A.lv[k] = TailLevel{H.L[l + k], H.x[l + k], H.x2[l + k], H.b[l + k], H.r[l + k]};
+    A.Ai = H.Ai;
+    A.ncoarse = H.ncoarse;
+    A.omega = MG_OMEGA;
+    k_mg_tail<B, D><<<1, TAIL_THREADS, 0, c.st>>>(A);
+    UPMPM_LAUNCH(c);
+    // three sweeps per level swapped x and x2 (as sweep() does on the host)
+    for (int k = l; k < H.nlev - 1; ++k) std::swap(H.x[k], H.x2[k]);
+    return;
+  }
   if (l == H.nlev - 1) {  // exact solve on the coarsest grid
     const Geom g = geom(c, (int64_t)H.ncoarse * 32);
     k_dense_apply<<<g.blocks, g.tpb, 0, c.st>>>(H.ncoarse, H.Ai, H.b[l], H.x[l]);
