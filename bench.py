@@ -165,10 +165,11 @@ def ncu_traffic(kernel):
 
 # Algorithmic FP64 flops of the Jacobian assembly (Eqs. jacobian-system-
 # stabilized-ppp, newmark-linearization as evaluated per point): F per
-# (point, a, b) term and G per (point, node) term, counted by hand from the
-# formula with the per-(point, node) vectors (g_a = F^-T grad S_a, tau g_a,
-# g_a.w, g_a.grad v, S_a - S0_a) formed once: {(dim, dynamic): (F, G)}.
-JAC_FLOPS = {(2, False): (83, 25), (2, True): (105, 33), (3, False): (158, 53), (3, True): (202, 71)}
+# (point, a, b) term and G per (point, node) term, counted by hand (an FMA is
+# 2 flops) from the formula with the per-(point, node) vectors (g_a = F^-T
+# grad S_a, tau g_a, g_a.w, g_a.grad v, S_a - S0_a) formed once and the point's
+# coefficients of the block terms combined once: {(dim, dynamic): (F, G)}.
+JAC_FLOPS = {(2, False): (62, 25), (2, True): (70, 33), (3, False): (102, 53), (3, True): (112, 71)}
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 

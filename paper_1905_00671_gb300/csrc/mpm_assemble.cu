@@ -478,10 +478,13 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
 //   g_a = F^{-T} grad_n S_a (the spatial gradient), S_a, S_a - S0_a,
 //   (g_a tau')_l, g_a . w, and (Newmark) (g_a grad v)_k,
 // at offsets 0, D, D+1, D+2, 2D+2, 2D+3; the last slot holds the point's
-// coefficients cs, vol, p^h, G - lambda ln J, lambda, kappa vol, m, b2,
-// C_stab factor, grad p.
+// coefficients of the block terms, combined once per point (see k_jacobian):
+//   0: cs, 1: cs (1 + c_v) mu', 2: vol p^h - cs (1 + c_v) lambda,
+//   3: cs (1 + c_v) mu' + vol p^h, 4: m (Newmark), 5: vol, 6: b2,
+//   7: kappa vol, 8: C_stab factor, 9..: grad p
+// with c_v = alpha gamma / (beta dt) the Kelvin factor (0 quasi-static).
 template <int D, bool DYN, typename R>
-__global__ void k_point_nodes(GridP g, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
+__global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                               R *__restrict__ pn) {
   constexpr int NSL = pn_nslot(D);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -491,14 +494,17 @@ __global__ void k_point_nodes(GridP g, DevView v, BasisArrays<R> BA, const R *__
   const int s = (int)(t - q * NSL);
   R *out = pn + t * PN_NPF;
   if (s == NSL - 1) {
-    out[0] = rec[RC_CS * n + q];
-    out[1] = rec[RC_VOL * n + q];
-    out[2] = rec[RC_PH * n + q];
-    out[3] = rec[RC_MUP * n + q];
-    out[4] = rec[RC_LAM * n + q];
-    out[5] = rec[RC_KV * n + q];
-    out[6] = DYN ? rec[RC_MS * n + q] : R(0);
-    out[7] = rec[RC_B2 * n + q];
+    const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
+    const R cv = DYN ? (R)(sp.alpha_vis * sp.gamma / (sp.beta * sp.dt)) : R(0);
+    const R csv = cs * (R(1) + cv);
+    out[0] = cs;
+    out[1] = csv * rec[RC_MUP * n + q];
+    out[2] = vol * ph - csv * rec[RC_LAM * n + q];
+    out[3] = csv * rec[RC_MUP * n + q] + vol * ph;
+    out[4] = DYN ? rec[RC_MS * n + q] : R(0);
+    out[5] = vol;
+    out[6] = rec[RC_B2 * n + q];
+    out[7] = rec[RC_KV * n + q];
     out[8] = rec[RC_CST * n + q];
     for (int k = 0; k < D; ++k) out[9 + k] = rec[(RC_GP + k) * n + q];
     return;
@@ -562,7 +568,6 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   }
   R B[NB * NB];
   for (int i = 0; i < NB * NB; ++i) B[i] = 0;
-  const R cvis = DYN ? (R)(s.alpha_vis * s.gamma / (s.beta * s.dt)) : R(0);
   for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
     for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
       for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
@@ -581,34 +586,39 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
           }
           const R Sa = pa[D], Sb = pb[D], Sta = pa[D + 1], Stb = pb[D + 1];
           const R gaw = pa[2 * D + 2], gbw = pb[2 * D + 2];
-          const R cs = pp[0], vol = pp[1], ph = pp[2], mu = pp[3], lam = pp[4], kv = pp[5];
+          // A_ik = p2 g_a,i g_b,k - p3 g_a,k g_b,i - delta_ik (p0 g_a.tau'.g_b
+          //        + p1 g_a.g_b + m S_a S_b): the stress, geometric, pressure,
+          // Kelvin and inertia terms of the linearization with the point's
+          // coefficients combined once (k_point_nodes)
           R gab = 0, gtg = 0;
           for (int j = 0; j < D; ++j) {
-            gab += ga[j] * gb[j];
-            gtg += pa[D + 2 + j] * gb[j];
+            gab = fma(ga[j], gb[j], gab);
+            gtg = fma(pa[D + 2 + j], gb[j], gtg);
           }
-          const R ms = DYN ? pp[6] * Sa * Sb : R(0);
+          R dg = pp[0] * gtg + pp[1] * gab;
+          if (DYN) dg = fma(pp[4] * Sa, Sb, dg);
+          R tt[3][3];
+          for (int i = 0; i < D; ++i)
+            for (int k = 0; k < D; ++k) tt[i][k] = ga[i] * gb[k];
           for (int i = 0; i < D; ++i)
             for (int k = 0; k < D; ++k) {
-              const R dik = i == k ? R(1) : R(0);
-              const R sym = mu * (dik * gab + ga[k] * gb[i]);
-              R A = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
-              A += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
-              if (DYN) {
-                A -= cs * cvis * (lam * ga[i] * gb[k] + sym);
-                A -= dik * ms;
-              }
-              B[i * NB + k] += A;
+              R acc = fma(pp[2], tt[i][k], B[i * NB + k]);
+              acc = fma(-pp[3], tt[k][i], acc);
+              B[i * NB + k] = i == k ? acc - dg : acc;
             }
-          for (int i = 0; i < D; ++i) B[i * NB + D] += vol * ga[i] * Sb;
-          const R b2 = pp[7];
+          const R vsb = pp[5] * Sb;
+          for (int i = 0; i < D; ++i) B[i * NB + D] = fma(vsb, ga[i], B[i * NB + D]);
+          const R sab2 = Sa * pp[6], kgaw = pp[7] * gaw, kgbw = pp[7] * gbw, kgab = pp[7] * gab;
+          const R svol = DYN ? pp[5] * Sa : R(0);
           for (int k = 0; k < D; ++k) {
-            R tk = Sa * b2 * gb[k];
-            if (DYN) tk -= vol * Sa * pb[2 * D + 3 + k];
-            tk += kv * (gb[k] * gaw - ga[k] * gbw - pp[9 + k] * gab);
+            R tk = sab2 * gb[k];
+            if (DYN) tk = fma(-svol, pb[2 * D + 3 + k], tk);
+            tk = fma(kgaw, gb[k], tk);
+            tk = fma(-kgbw, ga[k], tk);
+            tk = fma(-kgab, pp[9 + k], tk);
             B[D * NB + k] += tk;
           }
-          B[D * NB + D] += kv * gab + pp[8] * Sta * Stb;
+          B[D * NB + D] += kgab + pp[8] * Sta * Stb;
         }
       }
   if (apply_bc) {
@@ -858,11 +868,11 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
   if (staged) {
     const int npb = nblk((int64_t)pn_nslot(c.d) * c.n, TPB);
     if (c.d == 2) {
-      if (c.dyn) k_point_nodes<2, true, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
-      else k_point_nodes<2, false, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
+      if (c.dyn) k_point_nodes<2, true, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
+      else k_point_nodes<2, false, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
     } else {
-      if (c.dyn) k_point_nodes<3, true, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
-      else k_point_nodes<3, false, R><<<npb, TPB, 0, c.st>>>(c.g, v, BA, rec, pn);
+      if (c.dyn) k_point_nodes<3, true, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
+      else k_point_nodes<3, false, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
     }
     UPMPM_LAUNCH(c);
   }
