@@ -325,6 +325,36 @@ int read_dev_err(Ctx &c);   // synchronises; returns MPM_ERR_* or 0
 
 #define UPMPM_LAUNCH(ctx) ((ctx).launches++)
 
+// ---- programmatic dependent launch ------------------------------------------
+// The Krylov iteration is a chain of small dependent kernels.  A kernel launched
+// with launch_pdl may have its blocks scheduled while the kernel before it in
+// the stream is still running, so its launch latency hides behind that kernel.
+// Every kernel launched this way calls pdl_enter() before its first global
+// memory access: it waits until the preceding kernel has completed and its
+// writes are visible, and then lets the next kernel in the stream be scheduled
+// (so at most one kernel waits ahead).  Launched without the attribute, both
+// instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline void launch_pdl(Ctx &c, void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, A... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);  // a failed launch is left in cudaGetLastError
+  c.launches++;
+}
+
 // Event timing of kernel class `kind` around the launches between begin/end.
 void prof_begin(Ctx &c, int kind);
 void prof_end(Ctx &c, int kind);

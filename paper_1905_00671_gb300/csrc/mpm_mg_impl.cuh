@@ -224,6 +224,7 @@ template <int D>
 __global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsc,
                         real *__restrict__ vu, real *__restrict__ bs0, real *__restrict__ xs0,
                         const real *__restrict__ dinvs0, real omega) {
+  pdl_enter();
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
   for (int k = 0; k < D; ++k) vu[a * D + k] = v[a * (D + 1) + k] / dsc[a * (D + 1) + k];
@@ -250,6 +251,7 @@ __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr
                              const real *__restrict__ zp, const real *__restrict__ vu,
                              real *__restrict__ ba0, real *__restrict__ xa0,
                              const real *__restrict__ dinva0, real omega) {
+  pdl_enter();
   constexpr int LN = D == 2 ? 8 : 16;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = t / LN;
@@ -282,6 +284,7 @@ __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr
 template <int D>
 __global__ void k_merge(int64_t nnodes, const real *__restrict__ zu, const real *__restrict__ zp,
                         const real *__restrict__ dsc, real *__restrict__ z) {
+  pdl_enter();
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
   for (int k = 0; k < D; ++k) z[a * (D + 1) + k] = zu[a * D + k] / dsc[a * (D + 1) + k];
@@ -391,6 +394,7 @@ __global__ void k_mg_dinv(LevelDev L, int *err) {
 template <int B, int D, bool ST>
 __global__ void k_mg_smooth(LevelDev L, const real *__restrict__ xi, real *__restrict__ xo,
                             const real *__restrict__ b, real omega, int zero_init) {
+  pdl_enter();
   constexpr int LN = LN_<D>::v;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = t / LN;
@@ -418,6 +422,7 @@ __global__ void k_mg_smooth(LevelDev L, const real *__restrict__ xi, real *__res
 template <int B, int SPL, bool SMOOTH>
 __global__ void k_mg_csr_row(LevelDev L, const real *__restrict__ x, real *__restrict__ out,
                              const real *__restrict__ b, real omega) {
+  pdl_enter();
   constexpr int GS = B * SPL;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = t / GS;
@@ -456,6 +461,7 @@ __global__ void k_mg_csr_row(LevelDev L, const real *__restrict__ x, real *__res
 template <int B, int D, bool ST>
 __global__ void k_mg_resid(LevelDev L, const real *__restrict__ x, const real *__restrict__ b,
                            real *__restrict__ r) {
+  pdl_enter();
   constexpr int LN = LN_<D>::v;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = t / LN;
@@ -606,6 +612,7 @@ constexpr int DENSE_SMEM_MAX_N = 80;
 // one warp per row i; lanes split the row and reduce
 __global__ void k_dense_apply(int n, const real *__restrict__ Ai, const real *__restrict__ b,
                               real *__restrict__ x) {
+  pdl_enter();
   const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   real s = 0.0;
@@ -627,6 +634,7 @@ __device__ inline real pw(int a, int I) {
 template <int B, int D>
 __global__ void k_mg_restrict(LevelDev F, LevelDev Cl, const real *__restrict__ rf,
                               real *__restrict__ bc, real *__restrict__ xc, real omega) {
+  pdl_enter();
   const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= Cl.nnodes) return;
   int Ic[3];
@@ -686,6 +694,7 @@ __device__ inline void prolong_at(const LevelDev &Cl, const real *__restrict__ x
 template <int B, int D>
 __global__ void k_mg_prolong(LevelDev F, LevelDev Cl, real *__restrict__ xf,
                              const real *__restrict__ xc) {
+  pdl_enter();
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= F.nnodes) return;
   int ac[3];
@@ -747,6 +756,7 @@ __device__ inline void tail_rows(const LevelDev &L, const real *x, real *out, co
 
 template <int B, int D>
 __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs A) {
+  pdl_enter();
   real *xs[TAIL_MAX_LEVELS], *x2s[TAIL_MAX_LEVELS];
   for (int l = 0; l < A.nl; ++l) {
     xs[l] = A.lv[l].x;
@@ -946,13 +956,17 @@ void sweep(Ctx &c, MGHier<real> &H, int l) {
   if (l == 0 && B <= 2) {
     constexpr int SPL = B <= 2 ? 4 / B : 1;
     const Geom g = geom(c, L.nnodes * B * SPL);
-    k_mg_csr_row<B, SPL, true><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA);
+    launch_pdl(c, k_mg_csr_row<B, SPL, true>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
+               (const real *)H.b[l], MG_OMEGA);
   } else {
     const Geom g = geom(c, L.nnodes * LN_<D>::v);
-    if (l == 0) k_mg_smooth<B, D, false><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
-    else k_mg_smooth<B, D, true><<<g.blocks, g.tpb, 0, c.st>>>(L, H.x[l], H.x2[l], H.b[l], MG_OMEGA, 0);
+    if (l == 0)
+      launch_pdl(c, k_mg_smooth<B, D, false>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
+                 (const real *)H.b[l], MG_OMEGA, 0);
+    else
+      launch_pdl(c, k_mg_smooth<B, D, true>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
+                 (const real *)H.b[l], MG_OMEGA, 0);
   }
-  UPMPM_LAUNCH(c);
   std::swap(H.x[l], H.x2[l]);
 }
 
@@ -969,16 +983,14 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
     A.Ai = H.Ai;
     A.ncoarse = H.ncoarse;
     A.omega = MG_OMEGA;
-    k_mg_tail<B, D><<<1, TAIL_THREADS, 0, c.st>>>(A);
-    UPMPM_LAUNCH(c);
+    launch_pdl(c, k_mg_tail<B, D>, 1, TAIL_THREADS, 0, A);
     // three sweeps per level swapped x and x2 (as sweep() does on the host)
     for (int k = l; k < H.nlev - 1; ++k) std::swap(H.x[k], H.x2[k]);
     return;
   }
   if (l == H.nlev - 1) {  // exact solve on the coarsest grid
     const Geom g = geom(c, (int64_t)H.ncoarse * 32);
-    k_dense_apply<<<g.blocks, g.tpb, 0, c.st>>>(H.ncoarse, H.Ai, H.b[l], H.x[l]);
-    UPMPM_LAUNCH(c);
+    launch_pdl(c, k_dense_apply, g.blocks, g.tpb, 0, H.ncoarse, (const real *)H.Ai, (const real *)H.b[l], H.x[l]);
     return;
   }
   LevelDev &L = H.L[l], &Ln = H.L[l + 1];
@@ -988,17 +1000,19 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
   if (l == 0 && B <= 2) {
     constexpr int SPL = B <= 2 ? 4 / B : 1;
     const Geom g0 = geom(c, L.nnodes * B * SPL);
-    k_mg_csr_row<B, SPL, false><<<g0.blocks, g0.tpb, 0, c.st>>>(L, H.x[l], H.r[l], H.b[l], MG_OMEGA);
+    launch_pdl(c, k_mg_csr_row<B, SPL, false>, g0.blocks, g0.tpb, 0, L, (const real *)H.x[l], H.r[l],
+               (const real *)H.b[l], MG_OMEGA);
   } else if (l == 0) {
-    k_mg_resid<B, D, false><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+    launch_pdl(c, k_mg_resid<B, D, false>, gr.blocks, gr.tpb, 0, L, (const real *)H.x[l], (const real *)H.b[l],
+               H.r[l]);
   } else {
-    k_mg_resid<B, D, true><<<gr.blocks, gr.tpb, 0, c.st>>>(L, H.x[l], H.b[l], H.r[l]);
+    launch_pdl(c, k_mg_resid<B, D, true>, gr.blocks, gr.tpb, 0, L, (const real *)H.x[l], (const real *)H.b[l],
+               H.r[l]);
   }
-  k_mg_restrict<B, D><<<gc.blocks, gc.tpb, 0, c.st>>>(L, Ln, H.r[l], H.b[l + 1], xn_first, MG_OMEGA);
-  c.launches += 2;
+  launch_pdl(c, k_mg_restrict<B, D>, gc.blocks, gc.tpb, 0, L, Ln, (const real *)H.r[l], H.b[l + 1], xn_first,
+             MG_OMEGA);
   vcycle_t<B, D>(c, H, l + 1);
-  k_mg_prolong<B, D><<<gf.blocks, gf.tpb, 0, c.st>>>(L, Ln, H.x[l], H.x[l + 1]);
-  UPMPM_LAUNCH(c);
+  launch_pdl(c, k_mg_prolong<B, D>, gf.blocks, gf.tpb, 0, L, Ln, H.x[l], (const real *)H.x[l + 1]);
   sweep<B, D>(c, H, l);  // first post-smoothing sweep
   sweep<B, D>(c, H, l);  // second post-smoothing sweep
 }
@@ -1222,9 +1236,9 @@ void schur_split(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *xs0) {
   const int64_t nn = c.g.nnodes;
   MGHier<real> &HS = *S.mgS;
   const Geom g = geom(c, nn);
-  if (c.d == 2) k_split<2><<<g.blocks, g.tpb, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
-  else k_split<3><<<g.blocks, g.tpb, 0, c.st>>>(nn, v, S.dscale, S.vu, HS.b[0], xs0, HS.L[0].dinv, MG_OMEGA);
-  UPMPM_LAUNCH(c);
+  const real *dsc = S.dscale, *dinv = HS.L[0].dinv;
+  if (c.d == 2) launch_pdl(c, k_split<2>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, MG_OMEGA);
+  else launch_pdl(c, k_split<3>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, MG_OMEGA);
 }
 
 void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
@@ -1232,22 +1246,21 @@ void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
   MGHier<real> &HS = *S.mgS, &HA = *S.mgA;
   mg_vcycle(c, HS);
   const Geom g = geom(c, nn * (c.d == 2 ? 8 : 16));
+  const int32_t *rp = c.row_ptr, *cl = c.col;
+  const real *b1 = S.B1c, *zp = HS.x[0], *vu = S.vu, *dinv = HA.L[0].dinv;
   if (c.d == 2)
-    k_b1c_update<2><<<g.blocks, g.tpb, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
-                                                   HA.x[0], HA.L[0].dinv, MG_OMEGA);
+    launch_pdl(c, k_b1c_update<2>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, MG_OMEGA);
   else
-    k_b1c_update<3><<<g.blocks, g.tpb, 0, c.st>>>(nn, c.row_ptr, c.col, S.B1c, HS.x[0], S.vu, HA.b[0],
-                                                   HA.x[0], HA.L[0].dinv, MG_OMEGA);
-  UPMPM_LAUNCH(c);
+    launch_pdl(c, k_b1c_update<3>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, MG_OMEGA);
   mg_vcycle(c, HA);
 }
 
 void schur_merge(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *zu, const MG_REAL *zp, MG_REAL *z) {
   const int64_t nn = c.g.nnodes;
   const Geom g = geom(c, nn);
-  if (c.d == 2) k_merge<2><<<g.blocks, g.tpb, 0, c.st>>>(nn, zu, zp, S.dscale, z);
-  else k_merge<3><<<g.blocks, g.tpb, 0, c.st>>>(nn, zu, zp, S.dscale, z);
-  UPMPM_LAUNCH(c);
+  const real *dsc = S.dscale;
+  if (c.d == 2) launch_pdl(c, k_merge<2>, g.blocks, g.tpb, 0, nn, zu, zp, dsc, z);
+  else launch_pdl(c, k_merge<3>, g.blocks, g.tpb, 0, nn, zu, zp, dsc, z);
 }
 }  // namespace MG_NS
 

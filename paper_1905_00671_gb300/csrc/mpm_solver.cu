@@ -113,6 +113,7 @@ __global__ void k_scan_add(int32_t *__restrict__ out, int64_t n, const int32_t *
 template <typename T>
 __global__ void k_dot_partial(const T *__restrict__ x, const T *__restrict__ y, int64_t n,
                               double *__restrict__ part) {
+  pdl_enter();
   T acc = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -122,6 +123,7 @@ __global__ void k_dot_partial(const T *__restrict__ x, const T *__restrict__ y, 
 }
 
 __global__ void k_reduce(const double *__restrict__ part, int np, double *__restrict__ out) {
+  pdl_enter();
   double acc = 0.0;
   for (int i = threadIdx.x; i < np; i += blockDim.x) acc += part[i];
   acc = block_sum(acc);
@@ -130,12 +132,14 @@ __global__ void k_reduce(const double *__restrict__ part, int np, double *__rest
 
 template <typename T>
 __global__ void k_scale_copy(T *__restrict__ y, const T *__restrict__ x, const double *s, int64_t n) {
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = x[i] * (T)s[0];
 }
 
 template <typename T>
 __global__ void k_residual_vec(T *__restrict__ y, const T *__restrict__ b, int64_t n) {  // y = b - y
+  pdl_enter();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] = b[i] - y[i];
 }
@@ -239,6 +243,7 @@ __global__ void k_block_jacobi(int64_t nnodes, const int32_t *__restrict__ row_p
 template <int NB, typename T>
 __global__ void k_bj_apply(int64_t nnodes, const T *__restrict__ dinv, const T *__restrict__ x,
                            T *__restrict__ y) {
+  pdl_enter();
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
   T xv[NB];
@@ -261,6 +266,7 @@ template <int NB, int SPL, typename T>
 __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, const T *__restrict__ val,
                            const T *__restrict__ x, T *__restrict__ y) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t o = t / SPL;
   const int part = (int)(t - o * SPL);
@@ -288,6 +294,7 @@ __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
 template <typename T>
 __global__ void k_multidot2(const T *__restrict__ V, const T *__restrict__ w, int64_t n,
                             double *__restrict__ part) {
+  pdl_enter();
   const int i = blockIdx.y;
   const T *vi = V + (int64_t)i * n;
   T acc = 0;
@@ -301,6 +308,7 @@ __global__ void k_multidot2(const T *__restrict__ V, const T *__restrict__ w, in
 template <typename T>
 __global__ void k_orth_sub(T *__restrict__ w, const T *__restrict__ V, const double *__restrict__ h, int cnt,
                            int64_t n, double *__restrict__ part, int want_norm) {
+  pdl_enter();
   T nacc = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     T sv = w[k];
@@ -316,6 +324,7 @@ __global__ void k_orth_sub(T *__restrict__ w, const T *__restrict__ V, const dou
 
 __global__ void k_multidot_reduce(const double *__restrict__ part, int np, int cnt,
                                   double *__restrict__ h) {
+  pdl_enter();
   const int i = blockIdx.x;  // one block per coefficient
   if (i >= cnt) return;
   double acc = 0.0;
@@ -331,6 +340,7 @@ __global__ void k_arnoldi_finish(const double *__restrict__ part, int np, int j,
                                  const double *__restrict__ h1, const double *__restrict__ h2,
                                  double *__restrict__ H, double *__restrict__ g, double *__restrict__ cs,
                                  double *__restrict__ sn, double *__restrict__ scal) {
+  pdl_enter();
   double acc = 0.0;
   for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * PSTR];
   acc = block_sum(acc);
@@ -361,6 +371,7 @@ __global__ void k_arnoldi_finish(const double *__restrict__ part, int np, int j,
 }
 
 __global__ void k_gmres_init(double *__restrict__ g, int m, const double *beta_sq, double *scal) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   const double beta = sqrt(beta_sq[0]);
   for (int i = 0; i <= m; ++i) g[i] = 0.0;
@@ -371,6 +382,7 @@ __global__ void k_gmres_init(double *__restrict__ g, int m, const double *beta_s
 
 __global__ void k_backsolve(const double *__restrict__ H, const double *__restrict__ g, int jc, int m,
                             double *__restrict__ y) {
+  pdl_enter();
   if (threadIdx.x != 0) return;
   for (int i = jc - 1; i >= 0; --i) {
     double s = g[i];
@@ -381,6 +393,7 @@ __global__ void k_backsolve(const double *__restrict__ H, const double *__restri
 
 template <typename T>
 __global__ void k_update_x(T *__restrict__ x, const T *__restrict__ Z, const double *y, int jc, int64_t n) {
+  pdl_enter();
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   T s = x[k];
@@ -393,9 +406,10 @@ void spmv(Ctx &c, const LinSys<T> &S, const T *x, T *y) {
   constexpr int SPL = NB == 3 ? 2 : 4;  // 25 (2D) / 125 (3D) blocks per GIMP row
   const int64_t threads = c.g.nnodes * NB * SPL;
   prof_begin(c, MPM_PROF_SPMV);
-  k_bsr_spmv<NB, SPL, T><<<nblk(threads), TPB, 0, c.st>>>(c.g.nnodes, c.row_ptr, c.col, S.val, x, y);
+  const int32_t *rp = c.row_ptr, *cl = c.col;
+  const T *val = S.val;
+  launch_pdl(c, k_bsr_spmv<NB, SPL, T>, nblk(threads), TPB, 0, c.g.nnodes, rp, cl, val, x, y);
   prof_end(c, MPM_PROF_SPMV);
-  UPMPM_LAUNCH(c);
 }
 
 template <int NB, typename T>
@@ -404,8 +418,7 @@ void precond(Ctx &c, LinSys<T> &S, const T *x, T *y) {
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
     schur_apply<T>(c, S, x, y);
   } else {
-    k_bj_apply<NB, T><<<nblk(c.g.nnodes), TPB, 0, c.st>>>(c.g.nnodes, S.dinv, x, y);
-    UPMPM_LAUNCH(c);
+    launch_pdl(c, k_bj_apply<NB, T>, nblk(c.g.nnodes), TPB, 0, c.g.nnodes, (const T *)S.dinv, x, y);
   }
   prof_end(c, MPM_PROF_PRECOND);
 }
@@ -448,17 +461,19 @@ int fgmres_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
       {  // classical Gram-Schmidt, twice; the j + 1 products of a pass run side by side
         const int cnt = j + 1;
         const int nbx = std::min(NPART, std::max(16, NPART / cnt));
-        k_multidot2<T><<<dim3(nbx, cnt), TPB, 0, c.st>>>(S.V, w, N, c.part);
-        k_multidot_reduce<<<cnt, TPB, 0, c.st>>>(c.part, nbx, cnt, h1);
-        k_orth_sub<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h1, cnt, N, c.part, 0);
-        k_multidot2<T><<<dim3(nbx, cnt), TPB, 0, c.st>>>(S.V, w, N, c.part);
-        k_multidot_reduce<<<cnt, TPB, 0, c.st>>>(c.part, nbx, cnt, h2);
-        k_orth_sub<T><<<NPART, TPB, 0, c.st>>>(w, S.V, h2, cnt, N, c.part, 1);
+        const T *V = S.V, *wc = w;
+        const double *ph = c.part;
+        launch_pdl(c, k_multidot2<T>, dim3(nbx, cnt), TPB, 0, V, wc, N, c.part);
+        launch_pdl(c, k_multidot_reduce, cnt, TPB, 0, ph, nbx, cnt, h1);
+        launch_pdl(c, k_orth_sub<T>, NPART, TPB, 0, w, V, (const double *)h1, cnt, N, c.part, 0);
+        launch_pdl(c, k_multidot2<T>, dim3(nbx, cnt), TPB, 0, V, wc, N, c.part);
+        launch_pdl(c, k_multidot_reduce, cnt, TPB, 0, ph, nbx, cnt, h2);
+        launch_pdl(c, k_orth_sub<T>, NPART, TPB, 0, w, V, (const double *)h2, cnt, N, c.part, 1);
       }
       prof_end(c, MPM_PROF_ORTH);
-      k_arnoldi_finish<<<1, TPB, 0, c.st>>>(c.part, NPART, j, m, h1, h2, c.H, c.gvec, c.cs, c.sn, c.scal);
-      k_scale_copy<T><<<gN, TPB, 0, c.st>>>(Vn, w, c.scal + 1, N);
-      c.launches += 8;
+      launch_pdl(c, k_arnoldi_finish, 1, TPB, 0, (const double *)c.part, (int)NPART, j, m, (const double *)h1,
+                 (const double *)h2, c.H, c.gvec, c.cs, c.sn, c.scal);
+      launch_pdl(c, k_scale_copy<T>, gN, TPB, 0, Vn, (const T *)w, (const double *)(c.scal + 1), N);
       ++total;
       jc = j + 1;
       const double res = read_scalar(c, c.scal);
@@ -506,6 +521,7 @@ int fgmres_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
 template <typename T>
 __global__ void k_inst_dots(GridP g, int nb, const InstDev *__restrict__ inst, const T *__restrict__ V,
                             int64_t vstride, const T *__restrict__ w, double *__restrict__ out, int ostride) {
+  pdl_enter();
   const InstDev I = inst[blockIdx.x];
   const int k = blockIdx.y;
   const T *Vk = V + (int64_t)k * vstride;
@@ -524,6 +540,7 @@ __global__ void k_inst_dots(GridP g, int nb, const InstDev *__restrict__ inst, c
 template <typename T>
 __global__ void k_inst_orth(int64_t N, int nb, const int32_t *__restrict__ node_inst, T *__restrict__ w,
                             const T *__restrict__ V, int64_t vstride, const double *__restrict__ h, int cnt) {
+  pdl_enter();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= N) return;
   const int i = node_inst[e / nb];
@@ -537,6 +554,7 @@ __global__ void k_inst_orth(int64_t N, int nb, const int32_t *__restrict__ node_
 template <typename T>
 __global__ void k_inst_scale(int64_t N, int nb, const int32_t *__restrict__ node_inst, const T *__restrict__ w,
                              const double *__restrict__ scl, T *__restrict__ out) {
+  pdl_enter();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= N) return;
   const int i = node_inst[e / nb];
@@ -549,6 +567,7 @@ __global__ void k_inst_scale(int64_t N, int nb, const int32_t *__restrict__ node
 __global__ void k_inst_init(int ni, int m, const double *__restrict__ nrm, double *__restrict__ g,
                             double *__restrict__ scl, double *__restrict__ tgt, int32_t *__restrict__ frozen,
                             int32_t *__restrict__ jc, int32_t *__restrict__ active, double rtol, int set_target) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ni) return;
   const double beta = sqrt(nrm[i]);
@@ -571,6 +590,7 @@ __global__ void k_inst_arnoldi(int ni, int j, int m, const double *__restrict__ 
                                double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ scl,
                                const double *__restrict__ tgt, double *__restrict__ res,
                                int32_t *__restrict__ frozen, int32_t *__restrict__ jc, int32_t *__restrict__ active) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ni) return;
   if (frozen[i]) {
@@ -613,6 +633,7 @@ __global__ void k_inst_arnoldi(int ni, int j, int m, const double *__restrict__ 
 
 __global__ void k_inst_backsolve(int ni, int m, const double *__restrict__ H, const double *__restrict__ g,
                                  const int32_t *__restrict__ jc, double *__restrict__ y) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= ni) return;
   const double *Hi = H + (int64_t)i * (m + 1) * m, *gi = g + (int64_t)i * (m + 1);
@@ -628,6 +649,7 @@ template <typename T>
 __global__ void k_inst_update_x(int64_t N, int nb, const int32_t *__restrict__ node_inst, T *__restrict__ x,
                                 const T *__restrict__ Z, int64_t zstride, const double *__restrict__ y, int m,
                                 const int32_t *__restrict__ jc) {
+  pdl_enter();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= N) return;
   const int i = node_inst[e / nb];
