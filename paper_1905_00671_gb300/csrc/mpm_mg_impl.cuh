@@ -244,7 +244,9 @@ __global__ void k_extract_B1(int64_t nnzb, const real *__restrict__ J, real *__r
 }
 
 // w_u = v_u - B1 z_p with the compact unscaled B1: the A-cycle's level-0 rhs,
-// with its first smoothing sweep from zero (x = omega Dinv w_u).
+// with its first smoothing sweep from zero (x = omega Dinv w_u).  B1C_LANES
+// lanes per row.
+constexpr int B1C_LANES = 8;
 template <int D>
 __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                              const int32_t *__restrict__ col, const real *__restrict__ B1,
@@ -252,7 +254,7 @@ __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr
                              real *__restrict__ ba0, real *__restrict__ xa0,
                              const real *__restrict__ dinva0, real omega) {
   pdl_enter();
-  constexpr int LN = D == 2 ? 8 : 16;
+  constexpr int LN = B1C_LANES;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t a = t / LN;
   const int lane = (int)(t % LN);
@@ -268,17 +270,16 @@ __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr
   }
   for (int o = LN / 2; o > 0; o >>= 1)
     for (int k = 0; k < D; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-  if (!valid || lane != 0) return;
-  real w[D];
-  for (int k = 0; k < D; ++k) {
-    w[k] = vu[a * D + k] - acc[k];
-    ba0[a * D + k] = w[k];
+  if (!valid || lane >= D) return;
+  // lane i < D finishes component i
+  real s = 0.0, wi = 0.0;
+  for (int j = 0; j < D; ++j) {
+    const real wj = vu[a * D + j] - acc[j];
+    wi = lane == j ? wj : wi;
+    s = fma(dinva0[a * D * D + lane * D + j], wj, s);
   }
-  for (int i = 0; i < D; ++i) {
-    real s = 0.0;
-    for (int j = 0; j < D; ++j) s = fma(dinva0[a * D * D + i * D + j], w[j], s);
-    xa0[a * D + i] = omega * s;
-  }
+  ba0[a * D + lane] = wi;
+  xa0[a * D + lane] = omega * s;
 }
 
 template <int D>
@@ -314,11 +315,23 @@ __device__ inline real free_w(const LevelDev &L, int64_t a, int i) {
 }
 
 // Lanes per row of the row kernels (a row is one node: up to 49 blocks of the
-// fine block-CSR in 2D, 5^d slots of a coarse stencil).
+// fine block-CSR in 2D, 125 in 3D, 5^d slots of a coarse stencil).  Eight
+// lanes keep the shuffle reduction (log2 LN steps per block row) small next to
+// the row's FMAs on GB300's narrow FP64 pipe; FP32 3D rows take 16 (latency).
 template <int D>
 struct LN_ {
-  static constexpr int v = D == 2 ? 8 : 16;
+  static constexpr int v = (sizeof(real) == sizeof(double) || D == 2) ? 8 : 16;
 };
+
+// Component `lane` (< B) of a B-vector held in registers, without indexing
+// the register array by a run-time value.
+template <int B>
+__device__ inline real pick(const real v[B], int lane) {
+  real o = v[0];
+#pragma unroll
+  for (int i = 1; i < B; ++i) o = lane == i ? v[i] : o;
+  return o;
+}
 
 // Partial sum over the blocks of row a handled by `lane` (of LN lanes):
 // acc += A_ab x_b, one FMA per matrix value.
@@ -403,15 +416,12 @@ __global__ void k_mg_smooth(LevelDev L, const real *__restrict__ xi, real *__res
   real ax[B];
   for (int i = 0; i < B; ++i) ax[i] = 0.0;
   if (valid && !zero_init) row_partial<B, D, ST, LN>(L, a, lane, xi, ax);
-  lane_reduce<B, LN>(ax);
-  if (!valid || lane != 0) return;
-  real r[B];
-  for (int i = 0; i < B; ++i) r[i] = b[a * B + i] - ax[i];
-  for (int i = 0; i < B; ++i) {
-    real s = 0.0;
-    for (int j = 0; j < B; ++j) s = fma(L.dinv[a * B * B + i * B + j], r[j], s);
-    xo[a * B + i] = (zero_init ? 0.0 : xi[a * B + i]) + omega * s;
-  }
+  lane_reduce<B, LN>(ax);  // every lane of the row now holds (A xi)_a
+  if (!valid || lane >= B) return;
+  // lane i < B finishes component i: B FMAs of row i of Dinv
+  real s = 0.0;
+  for (int j = 0; j < B; ++j) s = fma(L.dinv[a * B * B + lane * B + j], b[a * B + j] - ax[j], s);
+  xo[a * B + lane] = (zero_init ? 0.0 : xi[a * B + lane]) + omega * s;
 }
 
 // Fine (block-CSR) level with B <= 2, a group of GS = B * SPL lanes per row:
@@ -471,8 +481,8 @@ __global__ void k_mg_resid(LevelDev L, const real *__restrict__ x, const real *_
   for (int i = 0; i < B; ++i) ax[i] = 0.0;
   if (valid) row_partial<B, D, ST, LN>(L, a, lane, x, ax);
   lane_reduce<B, LN>(ax);
-  if (!valid || lane != 0) return;
-  for (int i = 0; i < B; ++i) r[a * B + i] = b[a * B + i] - ax[i];
+  if (!valid || lane >= B) return;
+  r[a * B + lane] = b[a * B + lane] - pick<B>(ax, lane);
 }
 
 // ---- coarsest level: exact solve with a dense inverse built at set-up
@@ -1245,7 +1255,7 @@ void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
   const int64_t nn = c.g.nnodes;
   MGHier<real> &HS = *S.mgS, &HA = *S.mgA;
   mg_vcycle(c, HS);
-  const Geom g = geom(c, nn * (c.d == 2 ? 8 : 16));
+  const Geom g = geom(c, nn * B1C_LANES);
   const int32_t *rp = c.row_ptr, *cl = c.col;
   const real *b1 = S.B1c, *zp = HS.x[0], *vu = S.vu, *dinv = HA.L[0].dinv;
   if (c.d == 2)
