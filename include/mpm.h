@@ -84,7 +84,11 @@ enum {
   MPM_PROF_P2G = 5,       /* Stage-1 P2G */
   MPM_PROF_G2P = 6,       /* Stages 3-4 update */
   MPM_PROF_PRECOND = 7,   /* preconditioner application */
-  MPM_PROF_COUNT = 8
+  MPM_PROF_SETUP = 8,     /* preconditioner set-up (Schur complement, multigrid
+                             hierarchy, coarsest inverse) and system scaling */
+  MPM_PROF_PREP = 9,      /* step preparation outside Stage-1 P2G: binning,
+                             shape functions, sparsity pattern, initial guess */
+  MPM_PROF_COUNT = 10
 };
 
 typedef struct mpm_ctx mpm_ctx;

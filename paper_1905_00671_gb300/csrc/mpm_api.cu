@@ -263,13 +263,16 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   if (!rc) rc = upload_bcs(c, B);
   if (rc) return rc;
   c.s.dt = dt;
+  prof_begin(c, MPM_PROF_PREP);
   rc = run_binning(c);
   if (rc) return rc;
   run_shape(c);
   run_mass(c);
   rc = read_dev_err(c);
+  prof_end(c, MPM_PROF_PREP);
   if (rc) return rc;
   run_p2g(c);
+  prof_begin(c, MPM_PROF_PREP);
   rc = run_pattern(c);
   if (!rc) rc = linsys_reserve<double>(c, c.L64);
   if (!rc && c.have32) rc = linsys_reserve<float>(c, c.L32);
@@ -278,6 +281,7 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   run_renorm(c);
   run_count_terms(c);
   rc = read_dev_err(c);
+  prof_end(c, MPM_PROF_PREP);
   if (rc) return rc;
   c.prepared = true;
   return MPM_OK;
@@ -309,6 +313,7 @@ template <typename T>
 int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
   run_jacobian<T>(c, S.val, 1);
   int rc;
+  prof_begin(c, MPM_PROF_SETUP);
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
     const int lag = c.opt.precond_lag > 1 ? c.opt.precond_lag : 1;
     if (k % lag == 0) {
@@ -320,6 +325,7 @@ int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
     run_scale_system<T>(c, S, c.R);
     run_block_jacobi<T>(c, S);
   }
+  prof_end(c, MPM_PROF_SETUP);
   rc = read_dev_err(c);
   if (rc) return rc;
   const bool inexact = sizeof(T) < sizeof(double);

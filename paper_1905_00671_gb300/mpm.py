@@ -24,7 +24,7 @@ MPM_FP64, MPM_MIXED = 0, 1
 MPM_PRECOND_BLOCK_JACOBI, MPM_PRECOND_SCHUR_MG = 0, 1
 MPM_MAX_NEWTON = 64
 PROF = {"spmv": 0, "jacobian": 1, "residual": 2, "point": 3, "orth": 4, "p2g": 5, "g2p": 6,
-        "precond": 7}
+        "precond": 7, "setup": 8, "prep": 9}
 
 EXPORTED = ["mpm_default_options", "mpm_create", "mpm_step", "mpm_read", "mpm_get_stats",
             "mpm_last_error", "mpm_destroy", "mpm_debug_bin", "mpm_debug_prepare",
@@ -81,8 +81,8 @@ class mpm_stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int32), ("krylov_iters", C.c_int32 * MPM_MAX_NEWTON),
                 ("res_norm", C.c_double * (MPM_MAX_NEWTON + 1)), ("krylov_total", C.c_int32),
                 ("steps", C.c_int64), ("t", C.c_double), ("nnzb", C.c_int64),
-                ("kernel_launches", C.c_int64), ("prof_ms", C.c_double * 8),
-                ("prof_launches", C.c_int64 * 8), ("jac_terms", C.c_int64),
+                ("kernel_launches", C.c_int64), ("prof_ms", C.c_double * 10),
+                ("prof_launches", C.c_int64 * 10), ("jac_terms", C.c_int64),
                 ("jac_point_nodes", C.c_int64)]
 
 
