@@ -513,38 +513,41 @@ __global__ void k_dense_fill(LevelDev L, real *__restrict__ Ad) {
   Ad[t] = v;
 }
 
-// In-place Gauss-Jordan inverse of the dense n x n matrix Ad into Ai (one
-// block).  Rows with no usable pivot (singular directions) get a zero row in
-// the inverse, so the coarse correction leaves them alone.
-// Block j inverts job j (the coarsest operators of the two hierarchies are
-// inverted side by side).  With smem set, both matrices are worked on in
-// dynamic shared memory (2 n^2 values) and the inverse is copied out at the end.
+// Inverse of the dense coarsest operator Ad (n x n, row-major) into Ai, for
+// the two hierarchies side by side (job 0, job 1), in two kernels:
+//   k_dense_lu: LU factorisation with partial pivoting, one block per job,
+//     in place in Ad (in dynamic shared memory when n <= DENSE_SMEM_MAX_N),
+//     row interchanges in piv[k] (LAPACK order), n^3 / 3 FMAs;
+//   k_dense_inv_cols: column c of the inverse from P A = L U (forward and
+//     back substitution on e_c), one block per column, so the n^3 FMAs of the
+//     inverse spread over many SMs (GB300's FP64 pipe does 2 FMAs per clock
+//     per SM: one block inverting a 126 x 126 matrix took over a millisecond).
+// Columns with no usable pivot (below 1e-14 of the largest entry: nodes
+// without material on the coarsest grid) are singular directions: their
+// unknowns get zero in every column of the inverse, so the coarse correction
+// leaves them alone.
 struct DenseJob {
   int n;
   real *Ad, *Ai;
+  int *piv;  // n: row interchanged with row k; -1 marks a singular column
 };
 
-__global__ void k_dense_invert(DenseJob j0, DenseJob j1, int smem) {
+constexpr int DENSE_LU_THREADS = 512;
+
+__global__ void __launch_bounds__(DENSE_LU_THREADS) k_dense_lu(DenseJob j0, DenseJob j1, int smem) {
   const DenseJob job = blockIdx.x == 0 ? j0 : j1;
   const int n = job.n;
-  real *__restrict__ Adg = job.Ad;
-  real *__restrict__ Aig = job.Ai;
   __shared__ int piv;
-  __shared__ real pval;
   __shared__ real red_v[32];
   __shared__ int red_i[32];
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  real *Ad = Adg, *Ai = Aig;
-  if (smem) {
-    Ad = reinterpret_cast<real *>(dyn_smem);
-    Ai = Ad + n * n;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ad[t] = Adg[t];
-  }
+  real *M = smem ? reinterpret_cast<real *>(dyn_smem) : job.Ad;
+  if (smem)
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) M[t] = job.Ad[t];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) Ai[t] = (t / n == t % n) ? real(1) : real(0);
-  // largest magnitude (parallel), for the singular-pivot threshold
+  // largest magnitude, for the singular-pivot threshold
   real amax = 0;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) amax = fmax(amax, fabs(Ad[t]));
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) amax = fmax(amax, fabs(M[t]));
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if (lane == 0) red_v[wid] = amax;
   __syncthreads();
@@ -552,11 +555,11 @@ __global__ void k_dense_invert(DenseJob j0, DenseJob j1, int smem) {
   for (int i = 0; i < nw; ++i) amax = fmax(amax, red_v[i]);
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    // pivot: largest |Ad[i][k]| for i >= k (warp-parallel argmax)
+    // pivot: largest |M[i][k]|, i >= k (warp argmax, then across warps)
     real best = -1;
     int bi = k;
     for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-      const real v = fabs(Ad[i * n + k]);
+      const real v = fabs(M[i * n + k]);
       if (v > best) { best = v; bi = i; }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -572,51 +575,72 @@ __global__ void k_dense_invert(DenseJob j0, DenseJob j1, int smem) {
       for (int i = 0; i < nw; ++i)
         if (red_v[i] > b || (red_v[i] == b && red_i[i] < p)) { b = red_v[i]; p = red_i[i]; }
       piv = b > real(1e-14) * amax ? p : -1;
-      pval = piv >= 0 ? Ad[p * n + k] : real(0);
+      job.piv[k] = piv;
     }
     __syncthreads();
-    if (piv < 0) {
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        Ad[k * n + j] = 0;
-        Ai[k * n + j] = 0;
-      }
+    const int p = piv;
+    if (p < 0) {  // singular column: no elimination, zero multipliers
+      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) M[i * n + k] = 0;
       __syncthreads();
       continue;
     }
-    if (piv != k)
+    if (p != k)
       for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        real t1 = Ad[k * n + j]; Ad[k * n + j] = Ad[piv * n + j]; Ad[piv * n + j] = t1;
-        t1 = Ai[k * n + j]; Ai[k * n + j] = Ai[piv * n + j]; Ai[piv * n + j] = t1;
+        const real t1 = M[k * n + j];
+        M[k * n + j] = M[p * n + j];
+        M[p * n + j] = t1;
       }
     __syncthreads();
-    const real inv = real(1) / pval;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      Ad[k * n + j] *= inv;
-      Ai[k * n + j] *= inv;
-    }
+    const real inv = real(1) / M[k * n + k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) M[i * n + k] *= inv;
     __syncthreads();
-    // columns < k of Ad are already reduced (zero in the pivot row), column k
-    // is cleared below: update Ad's columns > k and all of Ai
-    const int wa = n - k - 1, wt = wa + n;
-    for (int t = threadIdx.x; t < n * wt; t += blockDim.x) {
-      const int i = t / wt, jj = t - i * wt;
-      if (i == k) continue;
-      const real f = Ad[i * n + k];
-      if (f == real(0)) continue;
-      if (jj < wa) Ad[i * n + k + 1 + jj] -= f * Ad[k * n + k + 1 + jj];
-      else Ai[i * n + jj - wa] -= f * Ai[k * n + jj - wa];
+    const int w = n - k - 1;
+    for (int t = threadIdx.x; t < w * w; t += blockDim.x) {
+      const int i = k + 1 + t / w, j = k + 1 + t % w;
+      M[i * n + j] = fma(-M[i * n + k], M[k * n + j], M[i * n + j]);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      if (i != k) Ad[i * n + k] = 0;
     __syncthreads();
   }
   if (smem)
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Aig[t] = Ai[t];
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) job.Ad[t] = M[t];
 }
 
-// largest coarsest system whose inverse is built in shared memory
-constexpr int DENSE_SMEM_MAX_N = 80;
+// block (c, job): column c of the job's inverse; dynamic shared memory n values
+__global__ void k_dense_inv_cols(DenseJob j0, DenseJob j1) {
+  const DenseJob job = blockIdx.y == 0 ? j0 : j1;
+  const int n = job.n, c = blockIdx.x;
+  if (c >= n) return;  // block-uniform
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  real *y = reinterpret_cast<real *>(dyn_smem);
+  const real *LU = job.Ad;
+  const int *pv = job.piv;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = i == c ? real(1) : real(0);
+  __syncthreads();
+  if (threadIdx.x == 0)  // y = P e_c (the interchanges in order)
+    for (int k = 0; k < n; ++k) {
+      const int p = pv[k];
+      if (p > k) { const real t = y[k]; y[k] = y[p]; y[p] = t; }
+    }
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {  // L y = P e_c (unit lower triangle)
+    const real yi = y[i];
+    if (yi != real(0))
+      for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) y[k] = fma(-LU[k * n + i], yi, y[k]);
+    __syncthreads();
+  }
+  for (int i = n - 1; i >= 0; --i) {  // U x = y
+    const real xi = pv[i] < 0 ? real(0) : y[i] / LU[i * n + i];
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = xi;
+    if (xi != real(0))
+      for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] = fma(-LU[k * n + i], xi, y[k]);
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < n; k += blockDim.x) job.Ai[(int64_t)k * n + c] = y[k];
+}
+
+// largest coarsest system factorised in shared memory (n^2 values)
+constexpr int DENSE_SMEM_MAX_N = 160;
 
 // x = Ai b
 // one warp per row i; lanes split the row and reduce
@@ -914,7 +938,8 @@ struct MGHier<MG_REAL> {
   int B = 1, nlev = 0;
   MG_NS::LevelDev L[16];
   MG_REAL *x[16], *x2[16], *b[16], *r[16];
-  MG_REAL *Ad = nullptr, *Ai = nullptr;  // dense coarsest operator and its inverse
+  MG_REAL *Ad = nullptr, *Ai = nullptr;  // dense coarsest operator (LU factors after set-up) and its inverse
+  int *piv = nullptr;                    // row interchanges of the LU factorisation
   int ncoarse = 0;                       // unknowns of the coarsest level
 };
 
@@ -949,12 +974,13 @@ void mg_setup_t(Ctx &c, MGHier<real> &H) {
 void dense_invert_pair(Ctx &c, MGHier<real> &H0, MGHier<real> &H1) {
   const int nmax = H0.ncoarse > H1.ncoarse ? H0.ncoarse : H1.ncoarse;
   const int smem = nmax <= DENSE_SMEM_MAX_N;
-  const size_t bytes = smem ? sizeof(real) * 2 * nmax * nmax : 0;
+  const size_t bytes = smem ? sizeof(real) * nmax * nmax : 0;
   if (smem && bytes > 48 * 1024)
-    cudaFuncSetAttribute(k_dense_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  k_dense_invert<<<2, 512, bytes, c.st>>>(DenseJob{H0.ncoarse, H0.Ad, H0.Ai},
-                                          DenseJob{H1.ncoarse, H1.Ad, H1.Ai}, smem);
-  UPMPM_LAUNCH(c);
+    cudaFuncSetAttribute(k_dense_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  const DenseJob a{H0.ncoarse, H0.Ad, H0.Ai, H0.piv}, b{H1.ncoarse, H1.Ad, H1.Ai, H1.piv};
+  k_dense_lu<<<2, DENSE_LU_THREADS, bytes, c.st>>>(a, b, smem);
+  k_dense_inv_cols<<<dim3(nmax, 2), 128, sizeof(real) * nmax, c.st>>>(a, b);
+  c.launches += 2;
 }
 
 constexpr real MG_OMEGA = 0.6;
@@ -1091,7 +1117,7 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
   H.ncoarse = (int)(H.L[l - 1].nnodes * B);
   if (H.ncoarse > 1024) return MPM_ERR_BAD_ARG;
   if (cudaMalloc(&H.Ad, sizeof(real) * H.ncoarse * H.ncoarse) ||
-      cudaMalloc(&H.Ai, sizeof(real) * H.ncoarse * H.ncoarse))
+      cudaMalloc(&H.Ai, sizeof(real) * H.ncoarse * H.ncoarse) || cudaMalloc(&H.piv, sizeof(int) * H.ncoarse))
     return MPM_ERR_NO_MEMORY;
   return MPM_OK;
 }
@@ -1099,7 +1125,9 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
 void mg_free(MGHier<real> &H) {
   cudaFree(H.Ad);
   cudaFree(H.Ai);
+  cudaFree(H.piv);
   H.Ad = H.Ai = nullptr;
+  H.piv = nullptr;
   for (int l = 0; l < H.nlev; ++l) {
     cudaFree(const_cast<int32_t *>(H.L[l].inst));
     H.L[l].inst = nullptr;
