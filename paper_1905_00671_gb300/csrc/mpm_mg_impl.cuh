@@ -930,6 +930,98 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
   for (int i = 0; i < B * B; ++i) Cl.sval[t * B * B + i] = acc[i];
 }
 
+// Galerkin product of the block-CSR finest level in two passes (the fine
+// operator couples nodes up to 3 apart per axis):
+//   k_mg_ap:   T_a(J) = sum_b w_bJ A_ab over the children b of J, for every
+//              fine row a and coarse node J of the 5^d window centred on
+//              floor(a / 2) (the coarse nodes a row can reach); thread per
+//              (a, window slot);
+//   k_mg_rap2: A_c(I, J) = sum_a w_aI T_a(J) over the 3^d children a of I;
+//              thread per (I, stencil slot).
+// Same masks as the one-pass product (Dirichlet DOFs out of the transfers,
+// instances kept apart), grouped as (P^T (A P)): a few lookups and FMAs per
+// coarse entry instead of one per (a, b) pair.
+template <int B, int D>
+__global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
+  constexpr int NS = NS_<D>::v;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= F.nnodes * NS) return;
+  const int64_t a = t / NS;
+  const int s = (int)(t % NS);
+  int fa[3], Jc[3];
+  grid_xyz(F.nn[0], F.nn[1], (int)a, fa);
+  Jc[0] = (fa[0] >> 1) + s % 5 - 2;
+  Jc[1] = (fa[1] >> 1) + (s / 5) % 5 - 2;
+  Jc[2] = D == 3 ? (fa[2] >> 1) + s / 25 - 2 : 0;
+  real acc[B * B];
+  for (int i = 0; i < B * B; ++i) acc[i] = 0.0;
+  if (Jc[0] >= 0 && Jc[0] < Cl.nn[0] && Jc[1] >= 0 && Jc[1] < Cl.nn[1] && Jc[2] >= 0 && Jc[2] < Cl.nn[2]) {
+    const int64_t Jn = Jc[0] + (int64_t)Cl.nn[0] * (Jc[1] + (int64_t)Cl.nn[1] * Jc[2]);
+    int blo[3], bhi[3];  // children of J within reach of a (and inside the grid)
+    for (int k = 0; k < 3; ++k) {
+      const int lo = 2 * Jc[k] - 1 > fa[k] - 3 ? 2 * Jc[k] - 1 : fa[k] - 3;
+      const int hi = 2 * Jc[k] + 1 < fa[k] + 3 ? 2 * Jc[k] + 1 : fa[k] + 3;
+      blo[k] = lo > 0 ? lo : 0;
+      bhi[k] = hi < F.nn[k] - 1 ? hi : F.nn[k] - 1;
+    }
+    if (D == 2) blo[2] = bhi[2] = 0;
+    for (int b2 = blo[2]; b2 <= bhi[2]; ++b2)
+      for (int b1 = blo[1]; b1 <= bhi[1]; ++b1)
+        for (int b0 = blo[0]; b0 <= bhi[0]; ++b0) {
+          const int64_t b = b0 + (int64_t)F.nn[0] * (b1 + (int64_t)F.nn[1] * b2);
+          if (F.inst && F.inst[b] != Cl.inst[Jn]) continue;
+          const int e = mask_block<D>(F.mask, F.row_ptr, (int)a, b0 - fa[0], b1 - fa[1], b2 - fa[2]);
+          if (e < 0) continue;
+          const real w = pw(b0, Jc[0]) * pw(b1, Jc[1]) * (D == 3 ? pw(b2, Jc[2]) : 1.0);
+          const real *blk = F.val + (int64_t)e * B * B;
+          for (int j = 0; j < B; ++j) {
+            const real wj = w * free_w(F, b, j);
+            for (int i = 0; i < B; ++i) acc[i * B + j] = fma(wj, blk[i * B + j], acc[i * B + j]);
+          }
+        }
+  }
+  for (int i = 0; i < B * B; ++i) T[t * B * B + i] = acc[i];
+}
+
+template <int B, int D>
+__global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
+  constexpr int NS = NS_<D>::v;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= Cl.nnodes * NS) return;
+  const int64_t I = t / NS;
+  const int s = (int)(t % NS);
+  int Ic[3], Jc[3];
+  grid_xyz(Cl.nn[0], Cl.nn[1], (int)I, Ic);
+  Jc[0] = Ic[0] + s % 5 - 2;
+  Jc[1] = Ic[1] + (s / 5) % 5 - 2;
+  Jc[2] = D == 3 ? Ic[2] + s / 25 - 2 : 0;
+  real acc[B * B];
+  for (int i = 0; i < B * B; ++i) acc[i] = 0.0;
+  if (Jc[0] >= 0 && Jc[0] < Cl.nn[0] && Jc[1] >= 0 && Jc[1] < Cl.nn[1] && Jc[2] >= 0 && Jc[2] < Cl.nn[2]) {
+    const int lo2 = D == 3 ? -1 : 0, hi2 = D == 3 ? 1 : 0;
+    for (int a2 = lo2; a2 <= hi2; ++a2)
+      for (int a1 = -1; a1 <= 1; ++a1)
+        for (int a0 = -1; a0 <= 1; ++a0) {
+          const int fa[3] = {2 * Ic[0] + a0, 2 * Ic[1] + a1, D == 3 ? 2 * Ic[2] + a2 : 0};
+          if (fa[0] < 0 || fa[0] >= F.nn[0] || fa[1] < 0 || fa[1] >= F.nn[1] || fa[2] < 0 || fa[2] >= F.nn[2])
+            continue;
+          // slot of J in a's window; outside it, T_a(J) is zero (J out of reach)
+          const int d0 = Jc[0] - (fa[0] >> 1), d1 = Jc[1] - (fa[1] >> 1), d2 = D == 3 ? Jc[2] - (fa[2] >> 1) : 0;
+          if (d0 < -2 || d0 > 2 || d1 < -2 || d1 > 2 || d2 < -2 || d2 > 2) continue;
+          const int64_t a = fa[0] + (int64_t)F.nn[0] * (fa[1] + (int64_t)F.nn[1] * fa[2]);
+          if (F.inst && F.inst[a] != Cl.inst[I]) continue;
+          const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
+          const int sl = (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0);
+          const real *ta = T + (a * NS + sl) * B * B;
+          for (int i = 0; i < B; ++i) {
+            const real wi = wa * free_w(F, a, i);
+            for (int j = 0; j < B; ++j) acc[i * B + j] = fma(wi, ta[i * B + j], acc[i * B + j]);
+          }
+        }
+  }
+  for (int i = 0; i < B * B; ++i) Cl.sval[t * B * B + i] = acc[i];
+}
+
 }  // namespace MG_NS
 
 // ============================================================== hierarchy
@@ -940,6 +1032,7 @@ struct MGHier<MG_REAL> {
   MG_REAL *x[16], *x2[16], *b[16], *r[16];
   MG_REAL *Ad = nullptr, *Ai = nullptr;  // dense coarsest operator (LU factors after set-up) and its inverse
   int *piv = nullptr;                    // row interchanges of the LU factorisation
+  MG_REAL *apT = nullptr;                // finest level x 5^d window: A P, first pass of the level-1 product
   int ncoarse = 0;                       // unknowns of the coarsest level
 };
 
@@ -953,8 +1046,13 @@ void mg_setup_t(Ctx &c, MGHier<real> &H) {
     if (l > 0) {
       constexpr int NS = NS_<D>::v;
       const int g2 = nblk(L.nnodes * NS);
-      if (l == 1) k_mg_rap<B, D, false><<<g2, TPB, 0, c.st>>>(H.L[0], L);
-      else k_mg_rap<B, D, true><<<g2, TPB, 0, c.st>>>(H.L[l - 1], L);
+      if (l == 1) {
+        k_mg_ap<B, D><<<nblk(H.L[0].nnodes * NS), TPB, 0, c.st>>>(H.L[0], L, H.apT);
+        k_mg_rap2<B, D><<<g2, TPB, 0, c.st>>>(H.L[0], L, H.apT);
+        UPMPM_LAUNCH(c);
+      } else {
+        k_mg_rap<B, D, true><<<g2, TPB, 0, c.st>>>(H.L[l - 1], L);
+      }
       UPMPM_LAUNCH(c);
       k_mg_dinv<B, D, true><<<nbk, TPB, 0, c.st>>>(L, c.err);
     } else {
@@ -1119,6 +1217,7 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
   if (cudaMalloc(&H.Ad, sizeof(real) * H.ncoarse * H.ncoarse) ||
       cudaMalloc(&H.Ai, sizeof(real) * H.ncoarse * H.ncoarse) || cudaMalloc(&H.piv, sizeof(int) * H.ncoarse))
     return MPM_ERR_NO_MEMORY;
+  if (H.nlev > 1 && cudaMalloc(&H.apT, sizeof(real) * H.L[0].nnodes * NS * B * B)) return MPM_ERR_NO_MEMORY;
   return MPM_OK;
 }
 
@@ -1126,7 +1225,8 @@ void mg_free(MGHier<real> &H) {
   cudaFree(H.Ad);
   cudaFree(H.Ai);
   cudaFree(H.piv);
-  H.Ad = H.Ai = nullptr;
+  cudaFree(H.apT);
+  H.Ad = H.Ai = H.apT = nullptr;
   H.piv = nullptr;
   for (int l = 0; l < H.nlev; ++l) {
     cudaFree(const_cast<int32_t *>(H.L[l].inst));
