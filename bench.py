@@ -169,9 +169,12 @@ def ncu_traffic(kernel):
 # stabilized-ppp, newmark-linearization as evaluated per point): F per
 # (point, a, b) term and G per (point, node) term, counted by hand (an FMA is
 # 2 flops) from the formula with the per-(point, node) vectors (g_a = F^-T
-# grad S_a, tau g_a, g_a.w, g_a.grad v, S_a - S0_a) formed once and the point's
-# coefficients of the block terms combined once: {(dim, dynamic): (F, G)}.
-JAC_FLOPS = {(2, False): (62, 25), (2, True): (70, 33), (3, False): (102, 53), (3, True): (112, 71)}
+# grad S_a, S_a, S_a - S0_a, tau' g_a, g_a.w, g_a.grad v) and their products
+# with the point's coefficients of the block terms formed once per node:
+# per term 2d^2 + 6d + 1 FMAs and d + 1 additions (+ d + 1 FMAs, Newmark);
+# per node the basis, the vectors and 6d + 6 coefficient products (+ 1,
+# Newmark).  {(dim, dynamic): (F, G)}.
+JAC_FLOPS = {(2, False): (45, 43), (2, True): (51, 52), (3, False): (78, 77), (3, True): (86, 96)}
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 

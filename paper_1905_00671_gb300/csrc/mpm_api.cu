@@ -581,7 +581,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   A(&c.sh_S0, 3 * MAXS * n);
   A(&c.m, n);
   A(&c.rec, RC_COUNT * n);
-  A(&c.pn, (int64_t)pn_nslot(c.d) * PN_NPF * n);
+  A(&c.pn, (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn) * n);
   A(&c.M, nn);
   A(&c.Pn, nn);
   A(&c.vn, d * nn);

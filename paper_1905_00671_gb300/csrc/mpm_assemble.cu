@@ -483,29 +483,36 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
 //   3: cs (1 + c_v) mu' + vol p^h, 4: m (Newmark), 5: vol, 6: b2,
 //   7: kappa vol, 8: C_stab factor, 9..: grad p
 // with c_v = alpha gamma / (beta dt) the Kelvin factor (0 quasi-static).
+// Staging of the FP64 Jacobian: one thread per (point, support slot) writes
+// the point's per-node record, so that each (point, a, b) term of the block
+// assembly is a short chain of FMAs.  With g = F^-T grad S (current
+// configuration), St = S - S0 and the point's coefficients
+//   p0 = cs,  p1 = cs (1 + cv) G',
+//   p2 = vol p - cs (1 + cv) lambda,  p3 = cs (1 + cv) G' + vol p,
+//   p4 = m (Newmark),  p5 = vol,  p6 = b2,  p7 = kappa vol,  p8 = C_stab V
+// (cs = V_n / J_n, cv = the Newmark viscous factor, G' = G - lambda ln J), a
+// node record holds (offsets for dimension D):
+//   0        g                       D+2    p2 g
+//   D        S                       2D+2   p3 g
+//   D+1      St                      3D+2   h = p0 (g^T tau') + p1 g
+//   4D+2     p7 g                    5D+2   p6 S + p7 g.w
+//   5D+3     p7 g.w                  5D+4   p5 S
+//   5D+5     p8 St                   5D+6   p4 S, 5D+7 g.grad v (Newmark)
+// and the point's own record (last slot) holds grad p at 9..9+D-1.  (The
+// terms are those of the linearization, Eqs. jacobian-system-stabilized-ppp
+// and newmark-linearization, grouped per node.)
 template <int D, bool DYN, typename R>
 __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                               R *__restrict__ pn) {
   constexpr int NSL = pn_nslot(D);
+  constexpr int NPF = pn_npf(D, DYN);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = v.n;
   if (t >= n * NSL) return;
   const int64_t q = t / NSL;
   const int s = (int)(t - q * NSL);
-  R *out = pn + t * PN_NPF;
+  R *out = pn + t * NPF;
   if (s == NSL - 1) {
-    const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
-    const R cv = DYN ? (R)(sp.alpha_vis * sp.gamma / (sp.beta * sp.dt)) : R(0);
-    const R csv = cs * (R(1) + cv);
-    out[0] = cs;
-    out[1] = csv * rec[RC_MUP * n + q];
-    out[2] = vol * ph - csv * rec[RC_LAM * n + q];
-    out[3] = csv * rec[RC_MUP * n + q] + vol * ph;
-    out[4] = DYN ? rec[RC_MS * n + q] : R(0);
-    out[5] = vol;
-    out[6] = rec[RC_B2 * n + q];
-    out[7] = rec[RC_KV * n + q];
-    out[8] = rec[RC_CST * n + q];
     for (int k = 0; k < D; ++k) out[9 + k] = rec[(RC_GP + k) * n + q];
     return;
   }
@@ -513,6 +520,12 @@ __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, c
   const int packed = v.sh_cnt[q];
   for (int k = 0; k < 3; ++k)
     if (off[k] >= (k < D ? unpack_cnt(packed, k) : 1)) return;
+  const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
+  const R cv = DYN ? (R)(sp.alpha_vis * sp.gamma / (sp.beta * sp.dt)) : R(0);
+  const R csv = cs * (R(1) + cv);
+  const R p0 = cs, p1 = csv * rec[RC_MUP * n + q];
+  const R p2 = vol * ph - csv * rec[RC_LAM * n + q], p3 = csv * rec[RC_MUP * n + q] + vol * ph;
+  const R p5 = vol, p6 = rec[RC_B2 * n + q], p7 = rec[RC_KV * n + q], p8 = rec[RC_CST * n + q];
   int nc[3] = {0, 0, 0};
   for (int k = 0; k < D; ++k) nc[k] = v.sh_first[k * n + q] + off[k];
   const int64_t a = node_index(g, nc);
@@ -523,23 +536,32 @@ __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, c
     for (int k = 0; k < D; ++k) sj += Gn[k] * rec[(RC_FINV + k * D + j) * n + q];
     gs[j] = sj;
   }
-  for (int j = 0; j < D; ++j) out[j] = gs[j];
-  out[D] = Sa;
-  out[D + 1] = Sa - S0a;
   R gw = 0;
   for (int l = 0; l < D; ++l) {
     R tl = 0;
     for (int j = 0; j < D; ++j) tl += gs[j] * rec[(RC_TAU + j * D + l) * n + q];
-    out[D + 2 + l] = tl;
+    out[l] = gs[l];
+    out[D + 2 + l] = p2 * gs[l];
+    out[2 * D + 2 + l] = p3 * gs[l];
+    out[3 * D + 2 + l] = p0 * tl + p1 * gs[l];
+    out[4 * D + 2 + l] = p7 * gs[l];
     gw += gs[l] * rec[(RC_W + l) * n + q];
   }
-  out[2 * D + 2] = gw;
-  if (DYN)
+  const R St = Sa - S0a;
+  out[D] = Sa;
+  out[D + 1] = St;
+  out[5 * D + 2] = p6 * Sa + p7 * gw;
+  out[5 * D + 3] = p7 * gw;
+  out[5 * D + 4] = p5 * Sa;
+  out[5 * D + 5] = p8 * St;
+  if (DYN) {
+    out[5 * D + 6] = rec[RC_MS * n + q] * Sa;
     for (int k = 0; k < D; ++k) {
       R gv = 0;
       for (int j = 0; j < D; ++j) gv += gs[j] * rec[(RC_GV + j * D + k) * n + q];
-      out[2 * D + 3 + k] = gv;
+      out[5 * D + 7 + k] = gv;
     }
+  }
 }
 
 template <int D, bool GIMP, bool DYN, typename T, typename R>
@@ -549,6 +571,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   constexpr int NSLOT = D == 2 ? 49 : 343;
   constexpr int NSL = pn_nslot(D);
+  constexpr int NPF = pn_npf(D, DYN);
   if (t >= NSLOT * g.nnodes) return;
   const int64_t a = t % g.nnodes;
   const int64_t e = block_of_slot<D>(mask, row_ptr, a, (int)(t / g.nnodes));
@@ -575,50 +598,44 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
         for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
           int oa[3], ob[3];
           if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
-          const R *P = pn + (int64_t)q * NSL * PN_NPF;
-          const R *pa = P + (oa[0] + MAXS * (oa[1] + MAXS * oa[2])) * PN_NPF;
-          const R *pb = P + (ob[0] + MAXS * (ob[1] + MAXS * ob[2])) * PN_NPF;
-          const R *pp = P + (NSL - 1) * PN_NPF;
+          const R *P = pn + (int64_t)q * NSL * NPF;
+          const R *pa = P + (oa[0] + MAXS * (oa[1] + MAXS * oa[2])) * NPF;
+          const R *pb = P + (ob[0] + MAXS * (ob[1] + MAXS * ob[2])) * NPF;
+          const R *pp = P + (NSL - 1) * NPF;
           R ga[3], gb[3];
           for (int j = 0; j < D; ++j) {
             ga[j] = pa[j];
             gb[j] = pb[j];
           }
-          const R Sa = pa[D], Sb = pb[D], Sta = pa[D + 1], Stb = pb[D + 1];
-          const R gaw = pa[2 * D + 2], gbw = pb[2 * D + 2];
-          // A_ik = p2 g_a,i g_b,k - p3 g_a,k g_b,i - delta_ik (p0 g_a.tau'.g_b
-          //        + p1 g_a.g_b + m S_a S_b): the stress, geometric, pressure,
-          // Kelvin and inertia terms of the linearization with the point's
-          // coefficients combined once (k_point_nodes)
-          R gab = 0, gtg = 0;
+          // A_ik = g_a,i (p2 g_b)_k - g_b,i (p3 g_a)_k - delta_ik d,
+          // d = h_a.g_b (+ p4 S_a S_b): stress, geometric, pressure, Kelvin
+          // and inertia terms with the point's coefficients staged per node
+          R dg = 0, kgab = 0;
           for (int j = 0; j < D; ++j) {
-            gab = fma(ga[j], gb[j], gab);
-            gtg = fma(pa[D + 2 + j], gb[j], gtg);
+            dg = fma(pa[3 * D + 2 + j], gb[j], dg);
+            kgab = fma(pa[4 * D + 2 + j], gb[j], kgab);  // p7 g_a.g_b
           }
-          R dg = pp[0] * gtg + pp[1] * gab;
-          if (DYN) dg = fma(pp[4] * Sa, Sb, dg);
-          R tt[3][3];
-          for (int i = 0; i < D; ++i)
-            for (int k = 0; k < D; ++k) tt[i][k] = ga[i] * gb[k];
+          if (DYN) dg = fma(pa[5 * D + 6], pb[D], dg);
           for (int i = 0; i < D; ++i)
             for (int k = 0; k < D; ++k) {
-              R acc = fma(pp[2], tt[i][k], B[i * NB + k]);
-              acc = fma(-pp[3], tt[k][i], acc);
+              R acc = fma(ga[i], pb[D + 2 + k], B[i * NB + k]);
+              acc = fma(-gb[i], pa[2 * D + 2 + k], acc);
               B[i * NB + k] = i == k ? acc - dg : acc;
             }
-          const R vsb = pp[5] * Sb;
-          for (int i = 0; i < D; ++i) B[i * NB + D] = fma(vsb, ga[i], B[i * NB + D]);
-          const R sab2 = Sa * pp[6], kgaw = pp[7] * gaw, kgbw = pp[7] * gbw, kgab = pp[7] * gab;
-          const R svol = DYN ? pp[5] * Sa : R(0);
+          // B1 column: (p5 S_b) g_a
+          const R p5Sb = pb[5 * D + 4];
+          for (int i = 0; i < D; ++i) B[i * NB + D] = fma(p5Sb, ga[i], B[i * NB + D]);
+          // B2 row: (p6 S_a + p7 g_a.w) g_b - (p7 g_b.w) g_a - (p7 g_a.g_b) grad p
+          //         (- p5 S_a g_b.grad v, Newmark)
+          const R ca = pa[5 * D + 2], eb = pb[5 * D + 3];
           for (int k = 0; k < D; ++k) {
-            R tk = sab2 * gb[k];
-            if (DYN) tk = fma(-svol, pb[2 * D + 3 + k], tk);
-            tk = fma(kgaw, gb[k], tk);
-            tk = fma(-kgbw, ga[k], tk);
-            tk = fma(-kgab, pp[9 + k], tk);
-            B[D * NB + k] += tk;
+            R tk = fma(ca, gb[k], B[D * NB + k]);
+            if (DYN) tk = fma(-pa[5 * D + 4], pb[5 * D + 7 + k], tk);
+            tk = fma(-eb, ga[k], tk);
+            B[D * NB + k] = fma(-kgab, pp[9 + k], tk);
           }
-          B[D * NB + D] += kgab + pp[8] * Sta * Stb;
+          // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b
+          B[D * NB + D] = fma(pa[5 * D + 5], pb[D + 1], B[D * NB + D] + kgab);
         }
       }
   if (apply_bc) {

@@ -60,8 +60,9 @@ constexpr int PATTERN_MASK_WORDS = 6;
 
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
 // Jacobian staging: per point, one record per support slot (MAXS^d) and one
-// for the point's own coefficients, PN_NPF values each.
-constexpr int PN_NPF = 12;
+// for the point's own coefficients, pn_npf(d, dyn) values each (the layout is
+// in k_point_nodes).
+__host__ __device__ constexpr int pn_npf(int d, bool dyn) { return dyn ? 6 * d + 7 : 5 * d + 6; }
 __host__ __device__ constexpr int pn_nslot(int d) { return (d == 2 ? MAXS * MAXS : MAXS * MAXS * MAXS) + 1; }
 
 // ---- particle fields ------------------------------------------------------
