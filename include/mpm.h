@@ -56,6 +56,20 @@ enum { MPM_SHAPE_ORIG = 0, MPM_SHAPE_GIMP = 1 };     /* Sec. 3.1: FE basis or GI
 enum { MPM_QUASISTATIC = 0, MPM_NEWMARK = 1 };       /* Sec. 3.2: implicit Euler or Newmark */
 enum { MPM_FP64 = 0, MPM_MIXED = 1 };
 
+/* Expression of the PPP stabilization parameter tau (Sec. 3.5), evaluated per
+ * point and step from the point's Lame constants lambda, G and mobility
+ * kappa = k / mu_f, with M = lambda + 2 G (the P-wave modulus K + 4G/3),
+ * c_v = M kappa, the step dt and the grid spacing h:
+ *   WHITE    (Eq. tau-white)     tau = 1 / (2 G)
+ *   SUN      (Eq. tau-sun)       tau = (1 - 3 c_v dt / h^2)
+ *                                      (1 + tanh(2 - 12 c_v dt / h^2)) / M
+ *   MONFORTE (Eq. tau-monforte)  tau = max(2 / M - (beta / gamma) 12 kappa dt / h^2, 0)
+ *                                (2 kappa / c_v written as 2 / M, its value for
+ *                                kappa > 0 and its limit at kappa = 0); Newmark
+ *                                steps only (it uses beta and gamma).
+ * The chosen expression is multiplied by mpm_options.tau_scale. */
+enum { MPM_TAU_WHITE = 0, MPM_TAU_SUN = 1, MPM_TAU_MONFORTE = 2 };
+
 /* Preconditioner of the FGMRES solve of the Newton system: node-block Jacobi,
  * or the Schur-complement block preconditioner of Sec. 3.4 with geometric
  * multigrid V-cycles for the displacement block and the pressure Schur
@@ -138,7 +152,7 @@ typedef struct {
   int32_t scheme;             /* MPM_QUASISTATIC / MPM_NEWMARK */
   double beta, gamma;         /* Newmark parameters (Sec. 3.2: 0.3025, 0.6) */
   int32_t stabilize;          /* PPP on (1) / off (0), Eq. stab-term-ppp */
-  double tau_scale;           /* tau = tau_scale / (2 G), Eq. tau-white */
+  double tau_scale;           /* tau = tau_scale x the expression of tau_kind */
   int32_t precision;          /* MPM_FP64, or MPM_MIXED: Jacobian values, scaling,
                                  preconditioner and Krylov vectors in FP32 inside the
                                  FP64 Newton loop (residual, kinematics, det F,
@@ -170,6 +184,7 @@ typedef struct {
                                  test is on the exact residual. */
   int32_t schur_approx;       /* MPM_SCHUR_* (default AUTO) */
   void *stream;               /* cudaStream_t for all work; NULL = default stream */
+  int32_t tau_kind;           /* MPM_TAU_* (default WHITE) */
 } mpm_options;
 
 /* Neumann data of one step: traction t^ per surface entry (n_surf*dim), and

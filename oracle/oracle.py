@@ -39,6 +39,36 @@ MAXS = 4
 OK, ERR_BAD_ARG, ERR_OUT_OF_GRID, ERR_NEGATIVE_J = 0, -1, -2, -3
 
 
+TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter, Sec. 3.5
+
+
+def stabilization_parameter(w, lam, G, kappa, dt):
+    """PPP parameter tau per point for a step of length dt (Sec. 3.5), times
+    w.tau_scale; zero when unstabilized.  With the P-wave modulus M = K + 4G/3
+    = lambda + 2G and the consolidation coefficient c_v = M kappa:
+      tau_W = 1 / (2 G)                                          (Eq. tau-white)
+      tau_S = (1/M) (1 - 3 c_v dt/h^2) [1 + tanh(2 - 12 c_v dt/h^2)]  (Eq. tau-sun)
+      tau_M = max(2 kappa/c_v - (beta/gamma) 12 kappa dt/h^2, 0)    (Eq. tau-monforte)
+    with 2 kappa / c_v evaluated as 2 / M (equal for kappa > 0, its limit at
+    kappa = 0).  tau_M uses the Newmark parameters: dynamic problems only."""
+    n = len(G)
+    if not w.stabilize:
+        return np.zeros(n)
+    if w.tau_kind == TAU_WHITE:
+        return w.tau_scale / (2.0 * G)
+    M = lam + 2.0 * G
+    h = w.h
+    if w.tau_kind == TAU_SUN:
+        cv = M * kappa
+        r = cv * dt / (h * h)
+        return w.tau_scale * ((1.0 - 3.0 * r) * (1.0 + np.tanh(2.0 - 12.0 * r)) / M)
+    if w.tau_kind == TAU_MONFORTE:
+        if not w.dynamic:
+            raise ValueError("tau_M (Eq. tau-monforte) uses the Newmark parameters: dynamic steps only")
+        return w.tau_scale * np.maximum(2.0 / M - (w.beta / w.gamma) * (12.0 * kappa * dt / (h * h)), 0.0)
+    raise ValueError(f"unknown tau_kind {w.tau_kind}")
+
+
 class OracleError(RuntimeError):
     pass
 
@@ -215,8 +245,7 @@ class Oracle:
         self.pdd = np.zeros(n)
         self.lam, self.G = lame(np.asarray(w.E, float), np.asarray(w.nu, float))
         self.kappa = np.asarray(w.k, float) / w.mu_f
-        # tau_W = 1 / (2 G) (Eq. tau-white); zero when unstabilized
-        self.tau = (w.tau_scale / (2.0 * self.G)) if w.stabilize else np.zeros(n)
+        self.tau = stabilization_parameter(w, self.lam, self.G, self.kappa, w.dt)
         self.surf = np.ascontiguousarray(w.surf_id, dtype=np.int32)
         self.surf_n = np.ascontiguousarray(w.surf_normal, float)
         self.surf_A = np.ascontiguousarray(w.surf_area, float)
@@ -262,6 +291,7 @@ class Oracle:
     # -- Stage 1 + pattern: everything that is fixed over the Newton loop
     def prepare(self, dt):
         d = self.d
+        self.tau = stabilization_parameter(self.w, self.lam, self.G, self.kappa, dt)
         first, count, S, dS, S0 = shape(self.g, self.x, self.lp)
         m = self.mixture_mass()
         fld = [self.p[:, None]]

@@ -161,6 +161,25 @@ __global__ void k_init(int64_t n, double *pf, const double *__restrict__ x, cons
   pid[p] = p;
 }
 
+// PPP parameter of every point for a step of length dt (Sec. 3.5): tau_S
+// (Eq. tau-sun) or tau_M (Eq. tau-monforte, 2 kappa / c_v written as 2 / M),
+// times tau_scale, with M = lambda + 2 G the P-wave modulus and c_v = M kappa.
+// (tau_W of Eq. tau-white does not depend on the step: set once by k_init.)
+__global__ void k_tau(int64_t n, double *pf, int kind, double tau_scale, double dt, double h, double beta,
+                      double gamma) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const double M = pf[PF_LAM * n + p] + 2.0 * pf[PF_G * n + p], kap = pf[PF_KAP * n + p];
+  double tau;
+  if (kind == MPM_TAU_SUN) {
+    const double cv = M * kap, r = cv * dt / (h * h);
+    tau = (1.0 - 3.0 * r) * (1.0 + tanh(2.0 - 12.0 * r)) / M;
+  } else {
+    tau = fmax(2.0 / M - (beta / gamma) * (12.0 * kap * dt / (h * h)), 0.0);
+  }
+  pf[PF_TAU * n + p] = tau_scale * tau;
+}
+
 // Per-instance squared residual norms: block i sums R^2 over the nodes of
 // instance i's grid (a fixed order, so the sums are run-to-run identical).
 __global__ void k_inst_norm(GridP g, int nb, const InstDev *__restrict__ inst, const double *__restrict__ R,
@@ -266,6 +285,11 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   prof_begin(c, MPM_PROF_PREP);
   rc = run_binning(c);
   if (rc) return rc;
+  if (c.stabilize && c.opt.tau_kind != MPM_TAU_WHITE) {  // tau_S, tau_M depend on dt
+    k_tau<<<nblk(c.n), TPB, 0, c.st>>>(c.n, c.pf, c.opt.tau_kind, c.tau_scale, dt, c.g.h, c.opt.beta,
+                                        c.opt.gamma);
+    UPMPM_LAUNCH(c);
+  }
   run_shape(c);
   run_mass(c);
   rc = read_dev_err(c);
@@ -486,6 +510,9 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   if (opt->krylov_restart < 1 || opt->krylov_restart > 128) return MPM_ERR_BAD_ARG;
   if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON) return MPM_ERR_BAD_ARG;
   if (opt->schur_approx < MPM_SCHUR_AUTO || opt->schur_approx > MPM_SCHUR_FIXED_STRESS) return MPM_ERR_BAD_ARG;
+  if (opt->tau_kind < MPM_TAU_WHITE || opt->tau_kind > MPM_TAU_MONFORTE) return MPM_ERR_BAD_ARG;
+  // tau_M uses the Newmark parameters: dynamic steps only (Sec. 3.5)
+  if (opt->stabilize && opt->tau_kind == MPM_TAU_MONFORTE && opt->scheme != MPM_NEWMARK) return MPM_ERR_BAD_ARG;
   if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
     return MPM_ERR_BAD_ARG;
   if (opt->precision != MPM_FP64 && opt->precision != MPM_MIXED) return MPM_ERR_BAD_ARG;
@@ -765,6 +792,7 @@ void mpm_default_options(mpm_options *o) {
   o->profile = 0;
   o->precond_lag = 2;
   o->schur_approx = MPM_SCHUR_AUTO;
+  o->tau_kind = MPM_TAU_WHITE;
   o->stream = nullptr;
 }
 

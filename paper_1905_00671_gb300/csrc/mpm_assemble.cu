@@ -473,16 +473,6 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
   return (int64_t)row_ptr[a] + before;
 }
 
-// Per (point q, support slot) the node vectors the Jacobian terms are built
-// from, formed once per assembly instead of once per (q, a, b) term:
-//   g_a = F^{-T} grad_n S_a (the spatial gradient), S_a, S_a - S0_a,
-//   (g_a tau')_l, g_a . w, and (Newmark) (g_a grad v)_k,
-// at offsets 0, D, D+1, D+2, 2D+2, 2D+3; the last slot holds the point's
-// coefficients of the block terms, combined once per point (see k_jacobian):
-//   0: cs, 1: cs (1 + c_v) mu', 2: vol p^h - cs (1 + c_v) lambda,
-//   3: cs (1 + c_v) mu' + vol p^h, 4: m (Newmark), 5: vol, 6: b2,
-//   7: kappa vol, 8: C_stab factor, 9..: grad p
-// with c_v = alpha gamma / (beta dt) the Kelvin factor (0 quasi-static).
 // Staging of the FP64 Jacobian: one thread per (point, support slot) writes
 // the point's per-node record, so that each (point, a, b) term of the block
 // assembly is a short chain of FMAs.  With g = F^-T grad S (current

@@ -18,6 +18,7 @@ from typing import Optional, Tuple
 import numpy as np
 
 ORIG, GIMP = 0, 1
+TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter (Sec. 3.5)
 
 
 @dataclass
@@ -54,6 +55,7 @@ class Workload:
     gamma: float = 0.6
     stabilize: bool = True
     tau_scale: float = 1.0
+    tau_kind: int = 0               # TAU_WHITE, TAU_SUN or TAU_MONFORTE (Sec. 3.5)
     dt: float = 1.0
     nsteps: int = 1
     ramp_time: float = 0.0          # load scale min(t / ramp_time, 1); 0 = applied at once

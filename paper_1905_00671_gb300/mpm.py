@@ -21,6 +21,7 @@ ERRORS = {-1: "MPM_ERR_BAD_ARG", -2: "MPM_ERR_OUT_OF_GRID", -3: "MPM_ERR_NEGATIV
 MPM_SHAPE_ORIG, MPM_SHAPE_GIMP = 0, 1
 MPM_QUASISTATIC, MPM_NEWMARK = 0, 1
 MPM_FP64, MPM_MIXED = 0, 1
+MPM_TAU_WHITE, MPM_TAU_SUN, MPM_TAU_MONFORTE = 0, 1, 2
 MPM_PRECOND_BLOCK_JACOBI, MPM_PRECOND_SCHUR_MG = 0, 1
 MPM_MAX_NEWTON = 64
 PROF = {"spmv": 0, "jacobian": 1, "residual": 2, "point": 3, "orth": 4, "p2g": 5, "g2p": 6,
@@ -61,7 +62,8 @@ class mpm_options(C.Structure):
                 ("newton_stag", C.c_double), ("krylov_rtol", C.c_double),
                 ("krylov_restart", C.c_int32), ("krylov_max", C.c_int32), ("precond", C.c_int32),
                 ("min_volume_fraction", C.c_double), ("profile", C.c_int32),
-                ("precond_lag", C.c_int32), ("schur_approx", C.c_int32), ("stream", C.c_void_p)]
+                ("precond_lag", C.c_int32), ("schur_approx", C.c_int32), ("stream", C.c_void_p),
+                ("tau_kind", C.c_int32)]
 
 
 class mpm_loads(C.Structure):
@@ -184,6 +186,7 @@ def _options(w, stream, opts) -> mpm_options:
     o.beta, o.gamma = w.beta, w.gamma
     o.stabilize = int(bool(w.stabilize))
     o.tau_scale = w.tau_scale
+    o.tau_kind = int(w.tau_kind)
     for key, val in opts.items():
         setattr(o, key, val)
     if stream is not None:

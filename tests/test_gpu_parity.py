@@ -102,6 +102,11 @@ STEP_CASES = {
     "footing2d-gimp-qs": (CASES["footing2d-gimp-qs"], 3),
     "terzaghi-4x40": (lambda: I.terzaghi_column(), 10),
     "block3d-gimp-qs": (CASES["block3d-gimp-qs"], 2),
+    # the other expressions of the PPP parameter (Sec. 3.5), evaluated per step
+    "paper-terzaghi-40-tau-sun": (lambda: replace(I.paper_terzaghi(40), tau_kind=I.TAU_SUN), 2),
+    "footing2d-gimp-qs-tau-sun": (lambda: replace(CASES["footing2d-gimp-qs"](), tau_kind=I.TAU_SUN), 2),
+    "footing2d-gimp-newmark-tau-monforte": (
+        lambda: replace(CASES["footing2d-gimp-newmark"](), tau_kind=I.TAU_MONFORTE), 3),
 }
 
 
@@ -191,6 +196,14 @@ def test_bad_arguments_are_rejected(mpm):
     sim = mpm.Simulation(w)
     assert sim.lib.mpm_step(sim.ctx, C.c_double(-1.0), None, None) == -1
     sim.close()
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(w, tau_kind=3)
+    assert e.value.code == -1
+    # tau_M uses the Newmark parameters: rejected for a quasi-static context
+    qs = I.small_footing(seed=3, body=(8, 4), pad=1, dynamic=False, dt=1.0)
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(qs, tau_kind=mpm.MPM_TAU_MONFORTE)
+    assert e.value.code == -1
 
 
 def test_deterministic_across_runs(mpm):
