@@ -56,7 +56,7 @@ enum { MPM_SHAPE_ORIG = 0, MPM_SHAPE_GIMP = 1 };     /* Sec. 3.1: FE basis or GI
 enum { MPM_QUASISTATIC = 0, MPM_NEWMARK = 1 };       /* Sec. 3.2: implicit Euler or Newmark */
 enum { MPM_FP64 = 0, MPM_MIXED = 1 };
 
-/* Expression of the PPP stabilization parameter tau (Sec. 3.5), evaluated per
+/* Expression of the PPP stabilization parameter tau (Sec. 4.3), evaluated per
  * point and step from the point's Lame constants lambda, G and mobility
  * kappa = k / mu_f, with M = lambda + 2 G (the P-wave modulus K + 4G/3),
  * c_v = M kappa, the step dt and the grid spacing h:
@@ -69,6 +69,13 @@ enum { MPM_FP64 = 0, MPM_MIXED = 1 };
  *                                steps only (it uses beta and gamma).
  * The chosen expression is multiplied by mpm_options.tau_scale. */
 enum { MPM_TAU_WHITE = 0, MPM_TAU_SUN = 1, MPM_TAU_MONFORTE = 2 };
+
+/* Permeability of a point: CONSTANT (the given k), or KOZENY_CARMAN
+ * (Eq. kozeny-carman): k = k0 (1 - phi0)^2 / phi0^3 * phi^3 / (1 - phi)^2 with
+ * the given k as k0, mpm_material.phi0 and the current porosity
+ * phi = 1 - (1 - phi0) / J (incompressible constituents); k = 0 once
+ * phi <= 0.  The Jacobian carries its derivative with respect to J. */
+enum { MPM_PERM_CONSTANT = 0, MPM_PERM_KOZENY_CARMAN = 1 };
 
 /* Preconditioner of the FGMRES solve of the Newton system: node-block Jacobi,
  * or the Schur-complement block preconditioner of Sec. 3.4 with geometric
@@ -185,6 +192,7 @@ typedef struct {
   int32_t schur_approx;       /* MPM_SCHUR_* (default AUTO) */
   void *stream;               /* cudaStream_t for all work; NULL = default stream */
   int32_t tau_kind;           /* MPM_TAU_* (default WHITE) */
+  int32_t permeability;       /* MPM_PERM_* (default CONSTANT) */
 } mpm_options;
 
 /* Neumann data of one step: traction t^ per surface entry (n_surf*dim), and

@@ -39,11 +39,21 @@ MAXS = 4
 OK, ERR_BAD_ARG, ERR_OUT_OF_GRID, ERR_NEGATIVE_J = 0, -1, -2, -3
 
 
-TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter, Sec. 3.5
+TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter, Sec. 4.3
+PERM_CONSTANT, PERM_KOZENY_CARMAN = 0, 1     # permeability model, Eq. kozeny-carman
+
+
+def kozeny_carman(k0, phi0, J):
+    """Eq. kozeny-carman with the porosity of incompressible constituents,
+    phi = 1 - (1 - phi0) / J: k = k0 (1 - phi0)^2 / phi0^3 * phi^3 / (1 - phi)^2;
+    zero once the pores are closed (phi <= 0)."""
+    phi = 1.0 - (1.0 - phi0) / np.asarray(J, float)
+    k = k0 * ((1.0 - phi0) ** 2 / phi0 ** 3) * (phi ** 3 / (1.0 - phi) ** 2)
+    return np.where(phi > 0.0, k, 0.0)
 
 
 def stabilization_parameter(w, lam, G, kappa, dt):
-    """PPP parameter tau per point for a step of length dt (Sec. 3.5), times
+    """PPP parameter tau per point for a step of length dt (Sec. 4.3), times
     w.tau_scale; zero when unstabilized.  With the P-wave modulus M = K + 4G/3
     = lambda + 2G and the consolidation coefficient c_v = M kappa:
       tau_W = 1 / (2 G)                                          (Eq. tau-white)
@@ -102,7 +112,7 @@ class _Particles(C.Structure):
 class _Step(C.Structure):
     _fields_ = [("dt", C.c_double), ("dynamic", C.c_int32), ("beta", C.c_double),
                 ("gamma", C.c_double), ("rho_f", C.c_double), ("alpha_vis", C.c_double),
-                ("g", C.c_double * 3)]
+                ("g", C.c_double * 3), ("kozeny", C.c_int32), ("phi0", C.c_double)]
 
 
 class _Nodal(C.Structure):
@@ -276,6 +286,7 @@ class Oracle:
         s.rho_f, s.alpha_vis = w.rho_f, (w.alpha_vis if w.dynamic else 0.0)
         for k in range(3):
             s.g[k] = w.g[k]
+        s.kozeny, s.phi0 = int(w.permeability == PERM_KOZENY_CARMAN), w.phi0
         return s
 
     def _particles_struct(self, m):
@@ -291,7 +302,10 @@ class Oracle:
     # -- Stage 1 + pattern: everything that is fixed over the Newton loop
     def prepare(self, dt):
         d = self.d
-        self.tau = stabilization_parameter(self.w, self.lam, self.G, self.kappa, dt)
+        kap_n = self.kappa
+        if self.w.permeability == PERM_KOZENY_CARMAN:   # the mobility at the start of the step
+            kap_n = kozeny_carman(self.kappa, self.w.phi0, det(self.F, d))
+        self.tau = stabilization_parameter(self.w, self.lam, self.G, kap_n, dt)
         first, count, S, dS, S0 = shape(self.g, self.x, self.lp)
         m = self.mixture_mass()
         fld = [self.p[:, None]]

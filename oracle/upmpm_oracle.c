@@ -503,8 +503,25 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
       }
       divv = log(dJ) / dt;
     }
-    /* Darcy: q = -kappa [grad p - rho_f (g - a)] */
-    const double kap = pp->kappa[p];
+    /* Darcy: q = -kappa [grad p - rho_f (g - a)]; with Eq. kozeny-carman the
+     * mobility follows the porosity phi = 1 - (1 - phi0) / J of the iterate:
+     * kappa = kappa_0 (1 - phi0)^2 / phi0^3 * phi^3 / (1 - phi)^2, and
+     * dkappa/dJ by the chain rule (dphi/dJ = (1 - phi0) / J^2); closed pores
+     * (phi <= 0) conduct nothing */
+    double kap = pp->kappa[p], dkap_dJ = 0.0;
+    if (sp->kozeny) {
+      const double phi0 = sp->phi0, phi = 1.0 - (1.0 - phi0) / J;
+      if (phi > 0.0) {
+        const double c0 = (1.0 - phi0) * (1.0 - phi0) / (phi0 * phi0 * phi0);
+        const double k = kap * c0 * phi * phi * phi / ((1.0 - phi) * (1.0 - phi));
+        const double dk_dphi = kap * c0 * (3.0 * phi * phi / ((1.0 - phi) * (1.0 - phi)) +
+                                          2.0 * phi * phi * phi / ((1.0 - phi) * (1.0 - phi) * (1.0 - phi)));
+        dkap_dJ = dk_dphi * (1.0 - phi0) / (J * J);
+        kap = k;
+      } else {
+        kap = 0.0;
+      }
+    }
     double w[3];
     for (int j = 0; j < d; ++j) w[j] = gp[j] - sp->rho_f * (sp->g[j] - ah[j]);
     /* Kelvin viscous stress (v sigma_vis) = (V_n/J_n) alpha (lambda tr D 1 + 2 mu' D) */
@@ -562,6 +579,7 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
 
     /* ---- Jacobian blocks ---- */
     const double kv = vol * kap;
+    const double dkv = vol * J * dkap_dJ; /* delta kappa = kappa'(J) J div(delta u) */
     for (int qa = 0; qa < ns; ++qa) {
       const double *ga = gr[qa];
       const double Sa = su->S[qa], Sda = su->S[qa] - su->S0[qa];
@@ -605,6 +623,7 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
             b2 = vol * Sa * (1.0 + log(dJ)) * gb[k] / dt;
           }
           b2 += kv * (gb[k] * gaw - ga[k] * gbw - gp[k] * gab);
+          b2 += dkv * gaw * gb[k];
           B[d * nb + k] += b2;
         }
         B[d * nb + d] += kv * gab + cstab * Vn * Sda * Sdb; /* C + C_stab */

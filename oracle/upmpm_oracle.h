@@ -59,6 +59,8 @@ typedef struct {
   double rho_f;      /* intrinsic fluid density */
   double alpha_vis;  /* Kelvin damping parameter (dynamic only) */
   double g[3];       /* gravity */
+  int32_t kozeny;    /* 1: permeability from porosity, Eq. kozeny-carman (kappa given = kappa_0) */
+  double phi0;       /* initial porosity (Kozeny-Carman) */
 } orc_step;
 
 typedef struct {

@@ -161,15 +161,22 @@ __global__ void k_init(int64_t n, double *pf, const double *__restrict__ x, cons
   pid[p] = p;
 }
 
-// PPP parameter of every point for a step of length dt (Sec. 3.5): tau_S
+// PPP parameter of every point for a step of length dt (Sec. 4.3): tau_S
 // (Eq. tau-sun) or tau_M (Eq. tau-monforte, 2 kappa / c_v written as 2 / M),
 // times tau_scale, with M = lambda + 2 G the P-wave modulus and c_v = M kappa.
 // (tau_W of Eq. tau-white does not depend on the step: set once by k_init.)
+template <int D>
 __global__ void k_tau(int64_t n, double *pf, int kind, double tau_scale, double dt, double h, double beta,
-                      double gamma) {
+                      double gamma, int kozeny, double phi0) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
-  const double M = pf[PF_LAM * n + p] + 2.0 * pf[PF_G * n + p], kap = pf[PF_KAP * n + p];
+  const double M = pf[PF_LAM * n + p] + 2.0 * pf[PF_G * n + p];
+  double kap = pf[PF_KAP * n + p];
+  if (kozeny) {  // the mobility at the start of the step, J_n = det F_n
+    double Fn[9];
+    for (int i = 0; i < D * D; ++i) Fn[i] = pf[(PF_F + i) * n + p];
+    kap = kozeny_carman(kap, phi0, det_d<D>(Fn), nullptr);
+  }
   double tau;
   if (kind == MPM_TAU_SUN) {
     const double cv = M * kap, r = cv * dt / (h * h);
@@ -286,8 +293,12 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   rc = run_binning(c);
   if (rc) return rc;
   if (c.stabilize && c.opt.tau_kind != MPM_TAU_WHITE) {  // tau_S, tau_M depend on dt
-    k_tau<<<nblk(c.n), TPB, 0, c.st>>>(c.n, c.pf, c.opt.tau_kind, c.tau_scale, dt, c.g.h, c.opt.beta,
-                                        c.opt.gamma);
+    if (c.d == 2)
+      k_tau<2><<<nblk(c.n), TPB, 0, c.st>>>(c.n, c.pf, c.opt.tau_kind, c.tau_scale, dt, c.g.h, c.opt.beta,
+                                           c.opt.gamma, c.s.kozeny, c.s.phi0);
+    else
+      k_tau<3><<<nblk(c.n), TPB, 0, c.st>>>(c.n, c.pf, c.opt.tau_kind, c.tau_scale, dt, c.g.h, c.opt.beta,
+                                           c.opt.gamma, c.s.kozeny, c.s.phi0);
     UPMPM_LAUNCH(c);
   }
   run_shape(c);
@@ -511,7 +522,9 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON) return MPM_ERR_BAD_ARG;
   if (opt->schur_approx < MPM_SCHUR_AUTO || opt->schur_approx > MPM_SCHUR_FIXED_STRESS) return MPM_ERR_BAD_ARG;
   if (opt->tau_kind < MPM_TAU_WHITE || opt->tau_kind > MPM_TAU_MONFORTE) return MPM_ERR_BAD_ARG;
-  // tau_M uses the Newmark parameters: dynamic steps only (Sec. 3.5)
+  if (opt->permeability != MPM_PERM_CONSTANT && opt->permeability != MPM_PERM_KOZENY_CARMAN) return MPM_ERR_BAD_ARG;
+  if (opt->permeability == MPM_PERM_KOZENY_CARMAN && !(mat->phi0 > 0.0 && mat->phi0 < 1.0)) return MPM_ERR_BAD_ARG;
+  // tau_M uses the Newmark parameters: dynamic steps only (Sec. 4.3)
   if (opt->stabilize && opt->tau_kind == MPM_TAU_MONFORTE && opt->scheme != MPM_NEWMARK) return MPM_ERR_BAD_ARG;
   if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
     return MPM_ERR_BAD_ARG;
@@ -578,6 +591,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   s.phi0 = mat->phi0;
   s.alpha_vis = c.dyn ? mat->alpha_vis : 0.0;
   s.phi_min = opt->min_volume_fraction;
+  s.kozeny = opt->permeability == MPM_PERM_KOZENY_CARMAN;
   for (int k = 0; k < 3; ++k) s.g[k] = k < c.d ? mat->g[k] : 0.0;
   c.n = P->n;
   c.n_surf = P->n_surf;
@@ -793,6 +807,7 @@ void mpm_default_options(mpm_options *o) {
   o->precond_lag = 2;
   o->schur_approx = MPM_SCHUR_AUTO;
   o->tau_kind = MPM_TAU_WHITE;
+  o->permeability = MPM_PERM_CONSTANT;
   o->stream = nullptr;
 }
 

@@ -384,7 +384,14 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
   rec[RC_PH * n + p] = ph;
   rec[RC_MUP * n + p] = mu_p;
   rec[RC_LAM * n + p] = lam;
-  rec[RC_KV * n + p] = vol * kap;
+  double kv = vol * kap, dkv = 0.0;
+  if (s.kozeny) {  // mobility at the current porosity, Eq. kozeny-carman
+    double jdk;
+    kv = vol * kozeny_carman(kap, s.phi0, J, &jdk);
+    dkv = vol * jdk;
+  }
+  rec[RC_KV * n + p] = kv;
+  rec[RC_DKV * n + p] = dkv;
   rec[RC_CST * n + p] = (DYN ? tau * gm / (b * dt) : tau / dt) * Vn;
   rec[RC_RST * n + p] = tau * Vn * pdev;
   rec[RC_DIVV * n + p] = vol * divv;
@@ -485,7 +492,7 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
 //   0        g                       D+2    p2 g
 //   D        S                       2D+2   p3 g
 //   D+1      St                      3D+2   h = p0 (g^T tau') + p1 g
-//   4D+2     p7 g                    5D+2   p6 S + p7 g.w
+//   4D+2     p7 g                    5D+2   p6 S + (p7 + J dk/dJ vol) g.w
 //   5D+3     p7 g.w                  5D+4   p5 S
 //   5D+5     p8 St                   5D+6   p4 S, 5D+7 g.grad v (Newmark)
 // and the point's own record (last slot) holds grad p at 9..9+D-1.  (The
@@ -540,7 +547,7 @@ __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, c
   const R St = Sa - S0a;
   out[D] = Sa;
   out[D + 1] = St;
-  out[5 * D + 2] = p6 * Sa + p7 * gw;
+  out[5 * D + 2] = p6 * Sa + (p7 + rec[RC_DKV * n + q]) * gw;
   out[5 * D + 3] = p7 * gw;
   out[5 * D + 4] = p5 * Sa;
   out[5 * D + 5] = p8 * St;
@@ -723,6 +730,7 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
               t -= vol * Sa * gbgv;
             }
             t += kv * (gb[k] * gaw - ga[k] * gbw - rec[(RC_GP + k) * n + q] * gab);
+            t += rec[RC_DKV * n + q] * gb[k] * gaw;  // dk/dJ (Kozeny-Carman)
             B[D * NB + k] += t;
           }
           B[D * NB + D] += kv * gab + rec[RC_CST * n + q] * (Sa - S0a) * (Sb - S0b);

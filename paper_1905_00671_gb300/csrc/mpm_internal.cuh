@@ -118,7 +118,8 @@ enum RField {
   RC_DIVV = 53,    // vol * div v
   RC_B2 = 54,      // B2 divergence coefficient
   RC_MS = 55,      // m (inertia Jacobian)
-  RC_COUNT = 56
+  RC_DKV = 56,     // J dkappa/dJ * vol (Kozeny-Carman; 0 for a constant permeability)
+  RC_COUNT = 57
 };
 
 // error bits raised by kernels (read back at synchronisation points)
@@ -138,6 +139,7 @@ struct StepP {
   double g[3];
   double phi0, rho_s;
   double phi_min;  // minimum nodal volume fraction of an active node
+  int kozeny;      // permeability from porosity by Eq. kozeny-carman (else constant)
 };
 
 // all device pointers the kernels need, passed by value
@@ -364,6 +366,20 @@ void prof_collect(Ctx &c);   // synchronises; adds elapsed times into stats
 // ---- device helpers -------------------------------------------------------
 __host__ __device__ inline int unpack_cnt(int packed, int k) { return (packed >> (4 * k)) & 15; }
 constexpr int RENORM_BIT = 1 << 15;  // in sh_cnt: the point's basis is renormalised
+
+// Eq. kozeny-carman: k(J) from k0 with phi = 1 - (1 - phi0) / J
+// (incompressible constituents); with jdk, also J dk/dJ = k (2 + 3 (1 - phi) / phi).
+// Closed pores (phi <= 0): k = 0.
+__host__ __device__ inline double kozeny_carman(double k0, double phi0, double J, double *jdk) {
+  const double phi = 1.0 - (1.0 - phi0) / J;
+  if (!(phi > 0.0)) {
+    if (jdk) *jdk = 0.0;
+    return 0.0;
+  }
+  const double k = k0 * ((1.0 - phi0) * (1.0 - phi0) / (phi0 * phi0 * phi0)) * (phi * phi * phi / ((1.0 - phi) * (1.0 - phi)));
+  if (jdk) *jdk = k * (2.0 + 3.0 * (1.0 - phi) / phi);
+  return k;
+}
 
 template <int D>
 __device__ inline double det_d(const double *A) {

@@ -18,7 +18,8 @@ from typing import Optional, Tuple
 import numpy as np
 
 ORIG, GIMP = 0, 1
-TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter (Sec. 3.5)
+TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter (Sec. 4.3)
+PERM_CONSTANT, PERM_KOZENY_CARMAN = 0, 1     # permeability model (Eq. kozeny-carman)
 
 
 @dataclass
@@ -55,7 +56,9 @@ class Workload:
     gamma: float = 0.6
     stabilize: bool = True
     tau_scale: float = 1.0
-    tau_kind: int = 0               # TAU_WHITE, TAU_SUN or TAU_MONFORTE (Sec. 3.5)
+    tau_kind: int = 0               # TAU_WHITE, TAU_SUN or TAU_MONFORTE (Sec. 4.3)
+    permeability: int = 0           # PERM_CONSTANT, or PERM_KOZENY_CARMAN (k = k0 at phi0)
+    dt_growth: float = 1.0          # the time step is multiplied by this after each step
     dt: float = 1.0
     nsteps: int = 1
     ramp_time: float = 0.0          # load scale min(t / ramp_time, 1); 0 = applied at once
@@ -88,6 +91,10 @@ class Workload:
 
     def traction(self, t: float) -> np.ndarray:
         return np.ascontiguousarray(self.load_scale(t) * self.trac_full)
+
+    def step_sizes(self, nsteps: int):
+        """dt of steps 0 .. nsteps-1: dt, then multiplied by dt_growth after each step."""
+        return [self.dt * self.dt_growth ** i for i in range(nsteps)]
 
 
 # --------------------------------------------------------------------------
@@ -193,6 +200,43 @@ def paper_terzaghi(n_elem=40, stabilize=True, tau_scale=1.0, shape=ORIG):
     return terzaghi_column(ncell_y=n_elem, ncell_x=1, h=h, E=E, nu=nu, k=k, mu_f=mu_f,
                            load=1.0e3, dt=0.1, nsteps=1, ppc_axis=(1, 2), stabilize=stabilize,
                            tau_scale=tau_scale, shape=shape, name=f"paper-terzaghi-{n_elem}")
+
+
+def self_weight_consolidation(ncell=(16, 16), h=0.125, ppc_axis=5, K=15e3, nu=0.3, k0=1e-14, phi0=0.5,
+                              mu_f=1e-3, rho_s=2600.0, rho_f=1000.0, g=9.81, dt=0.1, dt_growth=1.2,
+                              nsteps=20, shape=ORIG, stabilize=True, name=None):
+    """Self-weight consolidation (Sec. 5.3 set-up): the right half of a soft
+    deposit 4 m wide and 2 m tall (here ncell * h), K = 15 kPa, nu = 0.3,
+    k0 = 1e-14 m^2 with the permeability following the porosity (Eq.
+    kozeny-carman, phi0 = 0.5), mu_f = 1e-6 kPa s, rho_s = 2.6, rho_f = 1.0 Mg/m^3,
+    quasi-static; gravity applied at t = 0 on a stress-free, pressure-free
+    state; dt = 0.1 s multiplied by 1.2 after each step; the paper's two grids
+    are h = 0.125 m with 25 points per cell and h = 0.0625 m with 16.  Drained
+    (p = 0) top and right side, rigid impermeable bottom, the symmetry plane a
+    roller.  The right side is read as a roller too (the paper fixes its
+    pressure only; a free side would let the deposit spread out of the
+    modelled domain)."""
+    dim = 2
+    nc = (int(ncell[0]), int(ncell[1]), 0)
+    x, vol, lp = lattice(dim, nc[:2], h, ppc_axis)
+    n = x.shape[0]
+    G = 3.0 * K * (1.0 - 2.0 * nu) / (2.0 * (1.0 + nu))
+    E = 2.0 * G * (1.0 + nu)
+    uf, uv, pf, pv = empty_bcs(dim, nc)
+    nco = node_coords(dim, nc)
+    uf[nco[:, 0] == 0, 0] = 1              # symmetry plane
+    uf[nco[:, 0] == nc[0], 0] = 1          # right side (roller)
+    uf[nco[:, 1] == 0, :] = 1              # rigid bottom
+    pf[(nco[:, 1] == nc[1]) | (nco[:, 0] == nc[0])] = 1   # drained top and right side
+    return Workload(name=name or f"self-weight-{nc[0]}x{nc[1]}", dim=dim, shape=shape, ncell=nc,
+                    origin=(0.0, 0.0, 0.0), h=h, x=x, vol=vol, lp=lp, p0=np.zeros(n), v0=None,
+                    E=np.full(n, E), nu=np.full(n, nu), k=np.full(n, k0),
+                    surf_id=np.full(n, -1, np.int32), surf_normal=np.zeros((n, dim)),
+                    surf_area=np.zeros(n), trac_full=np.zeros((0, dim)),
+                    rho_s=rho_s, rho_f=rho_f, phi0=phi0, mu_f=mu_f, g=(0.0, -g, 0.0),
+                    dynamic=False, stabilize=stabilize, dt=dt, nsteps=nsteps, dt_growth=dt_growth,
+                    permeability=PERM_KOZENY_CARMAN,
+                    u_fixed=uf, u_value=uv, p_fixed=pf, p_value=pv)
 
 
 def strip_footing(body=(200, 100), pad=2, h=0.1, seed=2, ppc_axis=2, E0=20e6, nu=0.3, k=1e-14,

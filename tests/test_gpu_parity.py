@@ -102,11 +102,18 @@ STEP_CASES = {
     "footing2d-gimp-qs": (CASES["footing2d-gimp-qs"], 3),
     "terzaghi-4x40": (lambda: I.terzaghi_column(), 10),
     "block3d-gimp-qs": (CASES["block3d-gimp-qs"], 2),
-    # the other expressions of the PPP parameter (Sec. 3.5), evaluated per step
+    # the other expressions of the PPP parameter (Sec. 4.3), evaluated per step
     "paper-terzaghi-40-tau-sun": (lambda: replace(I.paper_terzaghi(40), tau_kind=I.TAU_SUN), 2),
     "footing2d-gimp-qs-tau-sun": (lambda: replace(CASES["footing2d-gimp-qs"](), tau_kind=I.TAU_SUN), 2),
     "footing2d-gimp-newmark-tau-monforte": (
         lambda: replace(CASES["footing2d-gimp-newmark"](), tau_kind=I.TAU_MONFORTE), 3),
+    # permeability from porosity (Eq. kozeny-carman); Sec. 5.3 self-weight set-up
+    # with its growing steps (dt x 1.2)
+    "self-weight-paper-16x16": (lambda: I.self_weight_consolidation(), 2),
+    "self-weight-8x8-kozeny": (
+        lambda: I.self_weight_consolidation(ncell=(8, 8), h=0.25, ppc_axis=2, K=1.5e6, k0=1e-10), 4),
+    "footing2d-gimp-newmark-kozeny": (
+        lambda: replace(CASES["footing2d-gimp-newmark"](), permeability=I.PERM_KOZENY_CARMAN), 3),
 }
 
 
@@ -117,9 +124,9 @@ def test_step_trajectory_parity(mpm, name):
     sim = mpm.Simulation(w, **GPU_TIGHT)
     orc = O.Oracle(w, **TIGHT)
     fields = ("x", "u", "p", "F", "V", "lp") + (("v", "a", "pd", "pdd") if w.dynamic else ())
-    for s in range(nsteps):
-        sim.step()
-        orc.step()
+    for s, dt in enumerate(w.step_sizes(nsteps)):
+        sim.step(dt)
+        orc.step(dt)
         got = sim.read(fields)
         ref = orc.state()
         for k in fields:
@@ -204,6 +211,13 @@ def test_bad_arguments_are_rejected(mpm):
     with pytest.raises(mpm.MPMError) as e:
         mpm.Simulation(qs, tau_kind=mpm.MPM_TAU_MONFORTE)
     assert e.value.code == -1
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(w, permeability=2)
+    assert e.value.code == -1
+    # Kozeny-Carman needs an initial porosity in (0, 1)
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(replace(w, phi0=0.0), permeability=mpm.MPM_PERM_KOZENY_CARMAN)
+    assert e.value.code == -1
 
 
 def test_deterministic_across_runs(mpm):
@@ -225,6 +239,8 @@ MIXED_CASES = {
     "footing2d-gimp-qs": (CASES["footing2d-gimp-qs"], 2),
     "terzaghi-4x40": (lambda: I.terzaghi_column(), 4),
     "block3d-gimp-qs": (CASES["block3d-gimp-qs"], 2),
+    "self-weight-8x8-kozeny": (
+        lambda: I.self_weight_consolidation(ncell=(8, 8), h=0.25, ppc_axis=2, K=1.5e6, k0=1e-10), 2),
 }
 
 

@@ -1,4 +1,4 @@
-"""The three expressions of the PPP stabilization parameter (Sec. 3.5) in the
+"""The three expressions of the PPP stabilization parameter (Sec. 4.3) in the
 oracle, pinned to what the paper fixes: the values of Eqs. tau-white, tau-sun
 and tau-monforte at their special points, the Sec. 5.1 checkerboard study with
 tau_S (the oscillation removed, the same solution as tau_W away from the
