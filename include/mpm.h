@@ -77,6 +77,16 @@ enum { MPM_TAU_WHITE = 0, MPM_TAU_SUN = 1, MPM_TAU_MONFORTE = 2 };
  * phi <= 0.  The Jacobian carries its derivative with respect to J. */
 enum { MPM_PERM_CONSTANT = 0, MPM_PERM_KOZENY_CARMAN = 1 };
 
+/* Stage-1 mapping of the point fields to the nodes (Sec. 3.1): LUMPED,
+ * f_i = sum_mp S m f / M_i (Eq. map-from-particles-to-nodes), or CONSISTENT,
+ * sum_j M_ij f_j = sum_mp S_i m f with the consistent mass M_ij = sum_mp S_i S_j m
+ * (Eq. map-from-particles-to-nodes-consistent; the paper's choice for cyclic
+ * loading), solved for the active nodes (those of the Newton system; the
+ * others keep the lumped values) by Jacobi-preconditioned CG to a relative
+ * residual of 1e-14; a step whose mass matrix CG cannot solve to that
+ * tolerance within 1000 iterations fails with MPM_ERR_KRYLOV_STAGNATED. */
+enum { MPM_P2G_LUMPED = 0, MPM_P2G_CONSISTENT = 1 };
+
 /* Preconditioner of the FGMRES solve of the Newton system: node-block Jacobi,
  * or the Schur-complement block preconditioner of Sec. 3.4 with geometric
  * multigrid V-cycles for the displacement block and the pressure Schur
@@ -193,6 +203,7 @@ typedef struct {
   void *stream;               /* cudaStream_t for all work; NULL = default stream */
   int32_t tau_kind;           /* MPM_TAU_* (default WHITE) */
   int32_t permeability;       /* MPM_PERM_* (default CONSTANT) */
+  int32_t p2g_mass;           /* MPM_P2G_* (default LUMPED) */
 } mpm_options;
 
 /* Neumann data of one step: traction t^ per surface entry (n_surf*dim), and

@@ -40,6 +40,7 @@ OK, ERR_BAD_ARG, ERR_OUT_OF_GRID, ERR_NEGATIVE_J = 0, -1, -2, -3
 
 
 TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter, Sec. 4.3
+P2G_LUMPED, P2G_CONSISTENT = 0, 1             # Stage-1 mapping, Eqs. map-from-particles-to-nodes(-consistent)
 PERM_CONSTANT, PERM_KOZENY_CARMAN = 0, 1     # permeability model, Eq. kozeny-carman
 
 
@@ -210,6 +211,28 @@ def p2g(g, first, count, S, m, fld):
     return M, out
 
 
+def consistent_map(g, first, count, S, m, M, active, lumped, row_ptr, col):
+    """Eq. map-from-particles-to-nodes-consistent: sum_j M_ij f_j = sum_mp S_i m f
+    with the consistent mass M_ij = sum_mp S_i S_j m, solved for the active
+    nodes; the other nodes keep the values of the lumped mapping (Eq.
+    map-from-particles-to-nodes), their couplings moved to the right-hand
+    side, whose point sum is taken as M_i f_i of the lumped mapping.  (The
+    consistent mass of nodes that a GIMP domain barely reaches is singular;
+    the active set is the one of the Newton system.)  Solved directly."""
+    nn = M.shape[0]
+    mc = np.zeros(len(col))
+    _check(lib().orc_consistent_mass(C.byref(g), C.c_int64(first.shape[0]), _p(first), _p(count), _p(S),
+                                     _p(np.ascontiguousarray(m)), _p(row_ptr), _p(col), _p(mc)),
+           "consistent mass")
+    A = sps.csr_matrix((mc, col, row_ptr), shape=(nn, nn))
+    ia = np.nonzero(active)[0]
+    ii = np.nonzero(~active)[0]
+    rhs = (M[:, None] * lumped)[ia] - A[ia][:, ii] @ lumped[ii]
+    out = lumped.copy()
+    out[ia] = spla.splu(A[ia][:, ia].tocsc()).solve(np.ascontiguousarray(rhs)).reshape(len(ia), -1)
+    return out
+
+
 # ---------------------------------------------------------------------------
 # material constants from (E, nu), mixture mass (taken by each side itself)
 # ---------------------------------------------------------------------------
@@ -323,6 +346,15 @@ class Oracle:
             nodal["pd"] = np.ascontiguousarray(out[:, 1 + 2 * d])
             nodal["pdd"] = np.ascontiguousarray(out[:, 2 + 2 * d])
         row_ptr, col = pattern(self.g, first, count)
+        if self.w.p2g_mass == P2G_CONSISTENT:
+            act = (M > 0.0) & (phi > self.phi_min)
+            out = consistent_map(self.g, first, count, S, m, M, act, out, row_ptr, col)
+            nodal["P"] = np.ascontiguousarray(out[:, 0])
+            if self.w.dynamic:
+                nodal["v"] = np.ascontiguousarray(out[:, 1:1 + d])
+                nodal["a"] = np.ascontiguousarray(out[:, 1 + d:1 + 2 * d])
+                nodal["pd"] = np.ascontiguousarray(out[:, 1 + 2 * d])
+                nodal["pdd"] = np.ascontiguousarray(out[:, 2 + 2 * d])
         active = (M > 0.0) & (phi > self.phi_min)
         return dict(first=first, count=count, S=S, dS=dS, S0=S0, m=m, M=M, phi=phi,
                     active=active, active_u8=np.ascontiguousarray(active.astype(np.uint8)),

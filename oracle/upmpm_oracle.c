@@ -339,6 +339,31 @@ int orc_p2g(const orc_grid *g, int64_t n, const int32_t *first, const int32_t *c
   return ORC_OK;
 }
 
+static int64_t find_block(const int64_t *row_ptr, const int32_t *col_idx, int64_t a, int64_t b);
+
+int orc_consistent_mass(const orc_grid *g, int64_t n, const int32_t *first, const int32_t *count,
+                        const double *S, const double *m, const int64_t *row_ptr, const int32_t *col_idx,
+                        double *mc) {
+  const int64_t nn = orc_nnodes(g);
+  for (int64_t e = 0; e < row_ptr[nn]; ++e) mc[e] = 0.0;
+  support *sp = (support *)malloc(sizeof(support));
+  int rc = ORC_OK;
+  for (int64_t p = 0; p < n && rc == ORC_OK; ++p) {
+    build_support(g, p, first, count, S, NULL, S, sp);
+    for (int qa = 0; qa < sp->ns; ++qa)
+      for (int qb = 0; qb < sp->ns; ++qb) {
+        const int64_t e = find_block(row_ptr, col_idx, sp->node[qa], sp->node[qb]);
+        if (e < 0) {
+          rc = ORC_ERR_BAD_ARG;
+          break;
+        }
+        mc[e] += sp->S[qa] * sp->S[qb] * m[p];
+      }
+  }
+  free(sp);
+  return rc;
+}
+
 /* ------------------------------------------------------------------------
  * Small dense helpers (d x d, row-major).
  * ---------------------------------------------------------------------- */

@@ -90,6 +90,13 @@ int orc_p2g(const orc_grid *g, int64_t n, const int32_t *first, const int32_t *c
             const double *S, const double *m, int32_t nf, const double *fld,
             double *M, double *out);
 
+/* Consistent mass matrix of Eq. map-from-particles-to-nodes-consistent,
+ * M_ij = sum_mp S_i S_j m, accumulated into the values mc (nnz) of the node
+ * pattern (row_ptr, col_idx) of orc_pattern. */
+int orc_consistent_mass(const orc_grid *g, int64_t n, const int32_t *first, const int32_t *count,
+                        const double *S, const double *m, const int64_t *row_ptr, const int32_t *col_idx,
+                        double *mc);
+
 /* active (nnodes, may be NULL): nodes with active == 0 are removed from the
  * bases of the points whose support box holds them, which are renormalised. */
 int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,

@@ -309,6 +309,7 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   run_p2g(c);
   prof_begin(c, MPM_PROF_PREP);
   rc = run_pattern(c);
+  if (!rc && c.opt.p2g_mass == MPM_P2G_CONSISTENT) rc = run_consistent_p2g(c);
   if (!rc) rc = linsys_reserve<double>(c, c.L64);
   if (!rc && c.have32) rc = linsys_reserve<float>(c, c.L32);
   if (rc) return rc;
@@ -478,7 +479,7 @@ void free_all(Ctx &c) {
                   c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.fsd, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
-                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.scan_tmp, c.terms, c.inst, c.inorm, c.node_inst, c.bk, c.bk_i};
+                  c.cs, c.sn, c.yv, c.hcol, c.part, c.scal, c.mc, c.cm_buf, c.scan_tmp, c.terms, c.inst, c.inorm, c.node_inst, c.bk, c.bk_i};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c.h_inorm) cudaFreeHost(c.h_inorm);
@@ -523,6 +524,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   if (opt->schur_approx < MPM_SCHUR_AUTO || opt->schur_approx > MPM_SCHUR_FIXED_STRESS) return MPM_ERR_BAD_ARG;
   if (opt->tau_kind < MPM_TAU_WHITE || opt->tau_kind > MPM_TAU_MONFORTE) return MPM_ERR_BAD_ARG;
   if (opt->permeability != MPM_PERM_CONSTANT && opt->permeability != MPM_PERM_KOZENY_CARMAN) return MPM_ERR_BAD_ARG;
+  if (opt->p2g_mass != MPM_P2G_LUMPED && opt->p2g_mass != MPM_P2G_CONSISTENT) return MPM_ERR_BAD_ARG;
   if (opt->permeability == MPM_PERM_KOZENY_CARMAN && !(mat->phi0 > 0.0 && mat->phi0 < 1.0)) return MPM_ERR_BAD_ARG;
   // tau_M uses the Newmark parameters: dynamic steps only (Sec. 4.3)
   if (opt->stabilize && opt->tau_kind == MPM_TAU_MONFORTE && opt->scheme != MPM_NEWMARK) return MPM_ERR_BAD_ARG;
@@ -808,6 +810,7 @@ void mpm_default_options(mpm_options *o) {
   o->schur_approx = MPM_SCHUR_AUTO;
   o->tau_kind = MPM_TAU_WHITE;
   o->permeability = MPM_PERM_CONSTANT;
+  o->p2g_mass = MPM_P2G_LUMPED;
   o->stream = nullptr;
 }
 

@@ -750,9 +750,302 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
   for (int i = 0; i < NB * NB; ++i) out[i] = (T)B[i];
 }
 
+// ---------------------------------------------------------------- consistent-mass Stage 1
+// Eq. map-from-particles-to-nodes-consistent: sum_j M_ij f_j = sum_mp S_i m f
+// with M_ij = sum_mp S_i S_j m, for every mapped field f (P; Newmark also v,
+// a, dp/dt, d2p/dt2), solved for the active nodes (mass and volume fraction
+// above phi_min, the active set of the Newton system: the consistent mass of a
+// node that a GIMP domain barely reaches is singular); the other nodes keep
+// the lumped values (Eq. map-from-particles-to-nodes), their couplings moved to
+// the right-hand side, whose point sum is M_i f_i of the lumped mapping.
+// Jacobi-preconditioned CG over all fields at once, per-field scalars on the
+// device.
+
+// M_ij on the node pattern, one thread per block (i = row_of[e], j = col[e]).
+template <int D, bool GIMP>
+__global__ void k_consistent_mass(GridP g, DevView v, int64_t nnzb, const int32_t *__restrict__ row_of,
+                                  const int32_t *__restrict__ col, double *__restrict__ mc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  const int64_t a = row_of[e], b = col[e], n = v.n;
+  int ac[3], bc[3];
+  node_coords(g, a, ac);
+  node_coords(g, b, bc);
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int k = 0; k < D; ++k) {
+    int l1, h1, l2, h2;
+    cand_range<GIMP>(ac[k], g.nc[k], l1, h1);
+    cand_range<GIMP>(bc[k], g.nc[k], l2, h2);
+    lo[k] = max(l1, l2);
+    hi[k] = min(h1, h2);
+  }
+  double acc = 0.0;
+  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
+    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
+      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
+        const int64_t cid = cell_index(g, c0, c1, c2);
+        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
+          int oa[3], ob[3];
+          if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
+          double Sa = 1.0, Sb = 1.0;
+          for (int k = 0; k < D; ++k) {
+            Sa *= v.sh_S[(k * MAXS + oa[k]) * n + q];
+            Sb *= v.sh_S[(k * MAXS + ob[k]) * n + q];
+          }
+          acc += Sa * Sb * v.m[q];
+        }
+      }
+  mc[e] = acc;
+}
+
+constexpr int CM_MAXF = 9;  // mapped fields: 2d + 3 (Newmark) at most
+struct CMFields {
+  double *f[CM_MAXF];
+  int K;
+};
+
+__device__ inline bool cm_active(const DevView &v, int64_t a, double phi_min) {
+  return v.M[a] > 0.0 && v.phi[a] > phi_min;
+}
+
+// x = lumped values; rhs = M_a f_a - sum over inactive columns; dinv = 1 / M_aa
+__global__ void k_cm_setup(int64_t nn, DevView v, double phi_min, const int32_t *__restrict__ row_ptr,
+                           const int32_t *__restrict__ col, const double *__restrict__ mc, CMFields F,
+                           double *__restrict__ x, double *__restrict__ rhs, double *__restrict__ dinv) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nn * F.K) return;
+  const int f = (int)(t / nn);
+  const int64_t a = t - (int64_t)f * nn;
+  const double fa = F.f[f][a];
+  x[t] = fa;
+  if (!cm_active(v, a, phi_min)) {
+    rhs[t] = 0.0;
+    if (f == 0) dinv[a] = 0.0;
+    return;
+  }
+  double r = v.M[a] * fa, diag = 0.0;
+  for (int e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
+    const int64_t b = col[e];
+    if (b == a) diag = mc[e];
+    else if (!cm_active(v, b, phi_min)) r -= mc[e] * F.f[f][b];
+  }
+  rhs[t] = r;
+  if (f == 0) dinv[a] = diag > 0.0 ? 1.0 / diag : 0.0;
+}
+
+// y = A x over the active rows and columns (zero on inactive rows)
+__global__ void k_cm_spmv(int64_t nn, int K, DevView v, double phi_min, const int32_t *__restrict__ row_ptr,
+                          const int32_t *__restrict__ col, const double *__restrict__ mc,
+                          const double *__restrict__ x, double *__restrict__ y) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nn * K) return;
+  const int f = (int)(t / nn);
+  const int64_t a = t - (int64_t)f * nn;
+  double s = 0.0;
+  if (cm_active(v, a, phi_min))
+    for (int e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
+      const int64_t b = col[e];
+      if (cm_active(v, b, phi_min)) s += mc[e] * x[(int64_t)f * nn + b];
+    }
+  y[t] = s;
+}
+
+constexpr int CM_NBLK = 64;  // partial sums per field
+
+// per field f: part[f][blk] = sum of u.w (and, with w2, of u.w2) over its slice
+__global__ void k_cm_dots(int64_t nn, const double *__restrict__ u, const double *__restrict__ w,
+                          const double *__restrict__ w2, double *__restrict__ part, double *__restrict__ part2) {
+  const int f = blockIdx.y;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ui = u[(int64_t)f * nn + i];
+    s += ui * w[(int64_t)f * nn + i];
+    if (w2) s2 += ui * w2[(int64_t)f * nn + i];
+  }
+  __shared__ double sh[2][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][threadIdx.x >> 5] = s;
+    sh[1][threadIdx.x >> 5] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a += sh[0][i];
+      b += sh[1][i];
+    }
+    part[f * CM_NBLK + blockIdx.x] = a;
+    if (part2) part2[f * CM_NBLK + blockIdx.x] = b;
+  }
+}
+
+// out[f] = sum of part[f][:] (and out2 from part2), one thread per field
+__global__ void k_cm_sum(int K, const double *__restrict__ part, const double *__restrict__ part2,
+                         double *__restrict__ out, double *__restrict__ out2) {
+  const int f = threadIdx.x;
+  if (f >= K) return;
+  double a = 0.0, b = 0.0;
+  for (int i = 0; i < CM_NBLK; ++i) {
+    a += part[f * CM_NBLK + i];
+    if (part2) b += part2[f * CM_NBLK + i];
+  }
+  out[f] = a;
+  if (out2) out2[f] = b;
+}
+
+// x += alpha p, r -= alpha q, z = Dinv r with alpha = rz / pq per field
+__global__ void k_cm_step(int64_t nn, int K, const double *__restrict__ rz, const double *__restrict__ pq,
+                          const double *__restrict__ dinv, const double *__restrict__ p,
+                          const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
+                          double *__restrict__ z) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nn * K) return;
+  const int f = (int)(t / nn);
+  const int64_t a = t - (int64_t)f * nn;
+  const double alpha = pq[f] != 0.0 ? rz[f] / pq[f] : 0.0;
+  x[t] += alpha * p[t];
+  r[t] -= alpha * q[t];
+  z[t] = dinv[a] * r[t];
+}
+
+// p = z + beta p with beta = rz_new / rz; rz = rz_new (per field)
+__global__ void k_cm_dir(int64_t nn, int K, double *__restrict__ rz, const double *__restrict__ rzn,
+                         const double *__restrict__ z, double *__restrict__ p) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nn * K) return;
+  const int f = (int)(t / nn);
+  const double beta = rz[f] != 0.0 ? rzn[f] / rz[f] : 0.0;
+  p[t] = z[t] + beta * p[t];
+}
+
+__global__ void k_cm_copy_rz(int K, double *__restrict__ rz, const double *__restrict__ rzn) {
+  if (threadIdx.x < K) rz[threadIdx.x] = rzn[threadIdx.x];
+}
+
+__global__ void k_cm_scatter(int64_t nn, CMFields F, const double *__restrict__ x) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nn * F.K) return;
+  const int f = (int)(t / nn);
+  F.f[f][t - (int64_t)f * nn] = x[t];
+}
+
+// r = rhs - A x, z = Dinv r, p = z (A x in q beforehand)
+__global__ void k_cm_init(int64_t nn, int K, const double *__restrict__ rhs, const double *__restrict__ q,
+                          const double *__restrict__ dinv, double *__restrict__ r, double *__restrict__ z,
+                          double *__restrict__ p) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nn * K) return;
+  const int64_t a = t % nn;
+  const double rv = rhs[t] - q[t];
+  r[t] = rv;
+  z[t] = dinv[a] * rv;
+  p[t] = z[t];
+}
+
 }  // namespace
 
 // ============================================================== launchers
+int run_consistent_p2g(Ctx &c) {
+  const int64_t nn = c.g.nnodes;
+  const int D = c.d, K = c.dyn ? 2 * D + 3 : 1;
+  CMFields F{};
+  F.K = K;
+  if (c.dyn) {
+    for (int k = 0; k < D; ++k) {
+      F.f[k] = c.vn + k * nn;
+      F.f[D + k] = c.an + k * nn;
+    }
+    F.f[2 * D] = c.Pn;
+    F.f[2 * D + 1] = c.pdn;
+    F.f[2 * D + 2] = c.pddn;
+  } else {
+    F.f[0] = c.Pn;
+  }
+  const int64_t need = 6 * (int64_t)K * nn + nn + 4 * (int64_t)CM_NBLK * K + 8 * K;
+  if (need > c.cm_cap) {
+    cudaFree(c.cm_buf);
+    c.cm_buf = nullptr;
+    c.cm_cap = 0;
+    if (cudaMalloc(&c.cm_buf, sizeof(double) * need) != cudaSuccess) {
+      c.last_error = "device allocation of the consistent-mass mapping failed";
+      return MPM_ERR_NO_MEMORY;
+    }
+    c.cm_cap = need;
+  }
+  const int64_t KN = (int64_t)K * nn;
+  double *x = c.cm_buf, *r = x + KN, *z = r + KN, *p = z + KN, *q = p + KN, *rhs = q + KN, *dinv = rhs + KN;
+  double *part = dinv + nn, *part2 = part + 2 * CM_NBLK * K;
+  double *rz = part2 + 2 * CM_NBLK * K, *rzn = rz + K, *pq = rzn + K, *rr = pq + K, *bb = rr + K;
+  if (!c.mc || c.mc_cap < c.nnzb_cap) {
+    cudaFree(c.mc);
+    c.mc = nullptr;
+    c.mc_cap = 0;
+    if (cudaMalloc(&c.mc, sizeof(double) * c.nnzb_cap) != cudaSuccess) {
+      c.last_error = "device allocation of the consistent mass failed";
+      return MPM_ERR_NO_MEMORY;
+    }
+    c.mc_cap = c.nnzb_cap;
+  }
+  const DevView v = c.view();
+  const bool gimp = c.shape == MPM_SHAPE_GIMP;
+  const int ge = nblk(c.nnzb), gk = nblk(KN);
+  if (D == 2) {
+    if (gimp) k_consistent_mass<2, true><<<ge, TPB, 0, c.st>>>(c.g, v, c.nnzb, c.row_of, c.col, c.mc);
+    else k_consistent_mass<2, false><<<ge, TPB, 0, c.st>>>(c.g, v, c.nnzb, c.row_of, c.col, c.mc);
+  } else {
+    if (gimp) k_consistent_mass<3, true><<<ge, TPB, 0, c.st>>>(c.g, v, c.nnzb, c.row_of, c.col, c.mc);
+    else k_consistent_mass<3, false><<<ge, TPB, 0, c.st>>>(c.g, v, c.nnzb, c.row_of, c.col, c.mc);
+  }
+  const double phm = c.s.phi_min;
+  k_cm_setup<<<gk, TPB, 0, c.st>>>(nn, v, phm, c.row_ptr, c.col, c.mc, F, x, rhs, dinv);
+  k_cm_spmv<<<gk, TPB, 0, c.st>>>(nn, K, v, phm, c.row_ptr, c.col, c.mc, x, q);
+  k_cm_init<<<gk, TPB, 0, c.st>>>(nn, K, rhs, q, dinv, r, z, p);
+  k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, r, z, rhs, part, part2);  // r.z and r.rhs (unused)
+  k_cm_sum<<<1, 32, 0, c.st>>>(K, part, nullptr, rz, nullptr);
+  k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, rhs, rhs, nullptr, part, nullptr);
+  k_cm_sum<<<1, 32, 0, c.st>>>(K, part, nullptr, bb, nullptr);
+  c.launches += 8;
+  double hb[CM_MAXF], hr[CM_MAXF];
+  cudaMemcpyAsync(hb, bb, sizeof(double) * K, cudaMemcpyDeviceToHost, c.st);
+  if (check_cuda(c, cudaStreamSynchronize(c.st), "consistent mass")) return MPM_ERR_CUDA;
+  // each field to a relative residual of CM_RTOL (CG on the Jacobi-scaled mass)
+  const double CM_RTOL = 1e-14;
+  const int CM_MAXIT = 1000;
+  bool done = false;
+  for (int it = 0; it < CM_MAXIT && !done; ++it) {
+    k_cm_spmv<<<gk, TPB, 0, c.st>>>(nn, K, v, phm, c.row_ptr, c.col, c.mc, p, q);
+    k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, p, q, nullptr, part, nullptr);
+    k_cm_sum<<<1, 32, 0, c.st>>>(K, part, nullptr, pq, nullptr);
+    k_cm_step<<<gk, TPB, 0, c.st>>>(nn, K, rz, pq, dinv, p, q, x, r, z);
+    k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, r, z, r, part, part2);
+    k_cm_sum<<<1, 32, 0, c.st>>>(K, part, part2, rzn, rr);
+    k_cm_dir<<<gk, TPB, 0, c.st>>>(nn, K, rz, rzn, z, p);
+    k_cm_copy_rz<<<1, 32, 0, c.st>>>(K, rz, rzn);
+    c.launches += 8;
+    cudaMemcpyAsync(hr, rr, sizeof(double) * K, cudaMemcpyDeviceToHost, c.st);
+    if (check_cuda(c, cudaStreamSynchronize(c.st), "consistent mass")) return MPM_ERR_CUDA;
+    done = true;
+    for (int f = 0; f < K; ++f) {
+      if (!isfinite(hr[f])) {
+        c.last_error = "non-finite value in the consistent-mass mapping";
+        return MPM_ERR_NONFINITE;
+      }
+      if (hr[f] > CM_RTOL * CM_RTOL * hb[f]) done = false;
+    }
+  }
+  if (!done) {
+    c.last_error = "consistent-mass mapping: CG did not reach its tolerance (ill-conditioned mass)";
+    return MPM_ERR_KRYLOV_STAGNATED;
+  }
+  k_cm_scatter<<<gk, TPB, 0, c.st>>>(nn, F, x);
+  UPMPM_LAUNCH(c);
+  return check_cuda(c, cudaGetLastError(), "consistent mass");
+}
+
 int run_pattern(Ctx &c) {
   const DevView v = c.view();
   const int nbk = nblk(c.g.nnodes, 128);

@@ -236,6 +236,9 @@ struct Ctx {
   int *h_err = nullptr;                  // pinned
   double *h_scalar = nullptr;            // pinned scratch for scalars read by the host
   unsigned long long *terms = nullptr;   // device: Jacobian term counts (n_p^2, n_p sums)
+  // consistent-mass Stage 1: the mass on the node pattern and the CG workspace
+  double *mc = nullptr, *cm_buf = nullptr;
+  int64_t mc_cap = 0, cm_cap = 0;
   // per-(point, support node) vectors of the FP64 Jacobian (pn_nslot(d)
   // records of PN_NPF values per point)
   double *pn = nullptr;
@@ -281,6 +284,7 @@ void run_p2g(Ctx &c);
 void run_g2p(Ctx &c);
 // assembly
 int run_pattern(Ctx &c);                          // builds row_ptr / col / row_of
+int run_consistent_p2g(Ctx &c);  // Stage-1 fields by the consistent mass (after run_pattern)
 void run_initial_guess(Ctx &c);   // also sets the active flags
 void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
 void run_count_terms(Ctx &c);     // Jacobian term counts into c.terms (device)

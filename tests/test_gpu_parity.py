@@ -114,6 +114,15 @@ STEP_CASES = {
         lambda: I.self_weight_consolidation(ncell=(8, 8), h=0.25, ppc_axis=2, K=1.5e6, k0=1e-10), 4),
     "footing2d-gimp-newmark-kozeny": (
         lambda: replace(CASES["footing2d-gimp-newmark"](), permeability=I.PERM_KOZENY_CARMAN), 3),
+    # Stage 1 by the consistent mass (Eq. map-from-particles-to-nodes-consistent)
+    "footing2d-orig-newmark-consistent": (
+        lambda: replace(CASES["footing2d-orig-newmark"](), p2g_mass=I.P2G_CONSISTENT), 3),
+    "footing2d-gimp-aligned-newmark-consistent": (
+        lambda: replace(I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25, jitter=0.0),
+                        p2g_mass=I.P2G_CONSISTENT), 3),
+    "self-weight-6x6-consistent": (
+        lambda: replace(I.self_weight_consolidation(ncell=(6, 6), h=1.0 / 3.0, ppc_axis=2, K=1.5e6, k0=1e-10),
+                        p2g_mass=I.P2G_CONSISTENT), 2),
 }
 
 
@@ -213,6 +222,9 @@ def test_bad_arguments_are_rejected(mpm):
     assert e.value.code == -1
     with pytest.raises(mpm.MPMError) as e:
         mpm.Simulation(w, permeability=2)
+    assert e.value.code == -1
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(w, p2g_mass=2)
     assert e.value.code == -1
     # Kozeny-Carman needs an initial porosity in (0, 1)
     with pytest.raises(mpm.MPMError) as e:
