@@ -41,6 +41,7 @@ OK, ERR_BAD_ARG, ERR_OUT_OF_GRID, ERR_NEGATIVE_J = 0, -1, -2, -3
 
 TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter, Sec. 4.3
 P2G_LUMPED, P2G_CONSISTENT = 0, 1             # Stage-1 mapping, Eqs. map-from-particles-to-nodes(-consistent)
+MODEL_NEOHOOKE, MODEL_HENCKY = 0, 1           # hyperelastic model of the solid skeleton
 PERM_CONSTANT, PERM_KOZENY_CARMAN = 0, 1     # permeability model, Eq. kozeny-carman
 
 
@@ -113,7 +114,8 @@ class _Particles(C.Structure):
 class _Step(C.Structure):
     _fields_ = [("dt", C.c_double), ("dynamic", C.c_int32), ("beta", C.c_double),
                 ("gamma", C.c_double), ("rho_f", C.c_double), ("alpha_vis", C.c_double),
-                ("g", C.c_double * 3), ("kozeny", C.c_int32), ("phi0", C.c_double)]
+                ("g", C.c_double * 3), ("kozeny", C.c_int32), ("phi0", C.c_double),
+                ("hencky", C.c_int32)]
 
 
 class _Nodal(C.Structure):
@@ -310,6 +312,7 @@ class Oracle:
         for k in range(3):
             s.g[k] = w.g[k]
         s.kozeny, s.phi0 = int(w.permeability == PERM_KOZENY_CARMAN), w.phi0
+        s.hencky = int(w.model == MODEL_HENCKY)
         return s
 
     def _particles_struct(self, m):

@@ -365,6 +365,98 @@ int orc_consistent_mass(const orc_grid *g, int64_t n, const int32_t *first, cons
 }
 
 /* ------------------------------------------------------------------------
+ * Hencky elasticity (Sec. 2.2): Psi = lambda/2 (ln J)^2 + G tr((1/2 ln b)^2),
+ * so tau' = 2 b dPsi/db = lambda ln J 1 + G ln b.  With b = sum_A x_A n_A n_A
+ * (x_A = squared principal stretches), eps_A = ln(x_A)/2 and the principal
+ * Kirchhoff stresses tau_A = lambda sum_B eps_B + 2 G eps_A, the spatial
+ * tangent of tau' (its Lie derivative, L_v tau' = c : d) is, in the principal
+ * basis (m_A = n_A n_A, m_AB = n_A n_B),
+ *   c = sum_AB (lambda + (2G - 2 tau_A) delta_AB) m_A (x) m_B
+ *     + sum_{A != B} theta_AB (m_AB (x) m_AB + m_AB (x) m_BA),
+ *   theta_AB = (tau_A x_B - tau_B x_A) / (x_A - x_B)
+ *            = G log1p(r) / r - tau_B,  r = x_A / x_B - 1,
+ * the second form without cancellation and with its limit G - tau_A at equal
+ * stretches.  (The same formulas give the neo-Hookean tangent lambda 1 (x) 1 +
+ * 2 (G - lambda ln J) I when tau_A = G (x_A - 1) + lambda ln J.)  In plane
+ * strain b is the in-plane 2 x 2 block (the third stretch is 1).
+ * ---------------------------------------------------------------------- */
+static void jacobi_eig(int d, const double *A, double *w, double *Q) {
+  double M[3][3];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      M[i][j] = A[i * d + j];
+      Q[i * d + j] = i == j ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < d; ++i) {
+      diag += M[i][i] * M[i][i];
+      for (int j = i + 1; j < d; ++j) off += M[i][j] * M[i][j];
+    }
+    if (off <= 1e-36 * diag) break;
+    for (int p = 0; p < d; ++p)
+      for (int q = p + 1; q < d; ++q) {
+        if (M[p][q] == 0.0) continue;
+        const double th = 0.5 * atan2(2.0 * M[p][q], M[q][q] - M[p][p]);
+        const double c = cos(th), s = sin(th);
+        for (int k = 0; k < d; ++k) {  /* columns p, q of M */
+          const double mkp = M[k][p], mkq = M[k][q];
+          M[k][p] = c * mkp - s * mkq;
+          M[k][q] = s * mkp + c * mkq;
+        }
+        for (int k = 0; k < d; ++k) {  /* rows p, q */
+          const double mpk = M[p][k], mqk = M[q][k];
+          M[p][k] = c * mpk - s * mqk;
+          M[q][k] = s * mpk + c * mqk;
+        }
+        for (int k = 0; k < d; ++k) {
+          const double qkp = Q[k * d + p], qkq = Q[k * d + q];
+          Q[k * d + p] = c * qkp - s * qkq;
+          Q[k * d + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  for (int i = 0; i < d; ++i) w[i] = M[i][i];
+}
+
+static double log1p_ratio(double r) { return fabs(r) > 1e-6 ? log1p(r) / r : 1.0 - r / 2.0 + r * r / 3.0; }
+
+/* tau' and the tangent c (d^4, index ((i d + j) d + k) d + l) of Hencky elasticity */
+static void hencky(int d, const double *bL, double lam, double G, double *tau, double *c) {
+  double x[3], Q[9], eps[3], tA[3], tr = 0.0;
+  jacobi_eig(d, bL, x, Q);
+  for (int A = 0; A < d; ++A) {
+    eps[A] = 0.5 * log(x[A]);
+    tr += eps[A];
+  }
+  for (int A = 0; A < d; ++A) tA[A] = lam * tr + 2.0 * G * eps[A];
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      double s = 0.0;
+      for (int A = 0; A < d; ++A) s += tA[A] * Q[i * d + A] * Q[j * d + A];
+      tau[i * d + j] = s;
+    }
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      for (int k = 0; k < d; ++k)
+        for (int l = 0; l < d; ++l) {
+          double s = 0.0;
+          for (int A = 0; A < d; ++A)
+            for (int B = 0; B < d; ++B) {
+              const double nAi = Q[i * d + A], nAj = Q[j * d + A];
+              const double nBk = Q[k * d + B], nBl = Q[l * d + B];
+              s += (lam + (A == B ? 2.0 * G - 2.0 * tA[A] : 0.0)) * nAi * nAj * nBk * nBl;
+              if (A != B) {
+                const double th = G * log1p_ratio(x[A] / x[B] - 1.0) - tA[B];
+                /* m_AB (x) m_AB: n_Ai n_Bj n_Ak n_Bl;  m_AB (x) m_BA: n_Ai n_Bj n_Bk n_Al */
+                s += th * (nAi * Q[j * d + B] * Q[k * d + A] * nBl + nAi * Q[j * d + B] * nBk * Q[l * d + A]);
+              }
+            }
+          c[((i * d + j) * d + k) * d + l] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------
  * Small dense helpers (d x d, row-major).
  * ---------------------------------------------------------------------- */
 static double det_d(int d, const double *A) {
@@ -482,11 +574,15 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
       for (int j = 0; j < d; ++j)
         for (int k = 0; k < d; ++k) bL[i * d + j] += F[i * d + k] * F[j * d + k];
     const double lam = pp->lam[p], Gs = pp->G[p];
-    double tau[9];
-    for (int i = 0; i < d; ++i)
-      for (int j = 0; j < d; ++j)
-        tau[i * d + j] = Gs * (bL[i * d + j] - (i == j ? 1.0 : 0.0)) + (i == j ? lam * lnJ : 0.0);
-    const double mu_p = Gs - lam * lnJ; /* shear coefficient of the spatial tangent */
+    double tau[9], ct[81];
+    if (sp->hencky) {
+      hencky(d, bL, lam, Gs, tau, ct);
+    } else {
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+          tau[i * d + j] = Gs * (bL[i * d + j] - (i == j ? 1.0 : 0.0)) + (i == j ? lam * lnJ : 0.0);
+    }
+    const double mu_p = Gs - lam * lnJ; /* shear coefficient of the neo-Hookean spatial tangent */
     const double Vn = pp->V[p];
     const double vol = dJ * Vn;         /* current volume */
     const double cs = Vn / Jn;          /* v sigma = (V_n / J_n) tau */
@@ -559,6 +655,14 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
           const double D = 0.5 * (gv[i * d + j] + gv[j * d + i]);
           svis[i * d + j] = sp->alpha_vis * ((i == j ? lam * trD : 0.0) + 2.0 * mu_p * D);
         }
+      if (sp->hencky) /* sigma_vis = alpha c : grad^s v with the Hencky tangent */
+        for (int i = 0; i < d; ++i)
+          for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k)
+              for (int l = 0; l < d; ++l) s += ct[((i * d + j) * d + k) * d + l] * 0.5 * (gv[k * d + l] + gv[l * d + k]);
+            svis[i * d + j] = sp->alpha_vis * s;
+          }
     }
     const double mp = pp->m[p];
     const double taus = pp->tau[p];
@@ -628,11 +732,20 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
         for (int i = 0; i < d; ++i)
           for (int k = 0; k < d; ++k) {
             const double dik = i == k ? 1.0 : 0.0;
-            double A = -cs * (dik * gtg + mu_p * (dik * gab + ga[k] * gb[i]) + lam * ga[i] * gb[k]);
+            /* material part g_a . c . g_b of the tangent */
+            double mat;
+            if (sp->hencky) {
+              mat = 0.0;
+              for (int j = 0; j < d; ++j)
+                for (int l = 0; l < d; ++l) mat += ga[j] * ct[((i * d + j) * d + k) * d + l] * gb[l];
+            } else {
+              mat = mu_p * (dik * gab + ga[k] * gb[i]) + lam * ga[i] * gb[k];
+            }
+            double A = -cs * (dik * gtg + mat);
             A += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
             if (sp->dynamic) {
               const double cv = sp->alpha_vis * gam / (beta * dt);
-              A -= cs * cv * (lam * ga[i] * gb[k] + mu_p * (dik * gab + ga[k] * gb[i]));
+              A -= cs * cv * mat;
               A -= dik * mp * Sa * Sb / (beta * dt * dt);
             }
             B[i * nb + k] += A;

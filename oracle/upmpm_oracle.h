@@ -61,6 +61,7 @@ typedef struct {
   double g[3];       /* gravity */
   int32_t kozeny;    /* 1: permeability from porosity, Eq. kozeny-carman (kappa given = kappa_0) */
   double phi0;       /* initial porosity (Kozeny-Carman) */
+  int32_t hencky;    /* 1: Hencky elasticity (Sec. 2.2), else compressible neo-Hookean */
 } orc_step;
 
 typedef struct {

@@ -21,6 +21,7 @@ ORIG, GIMP = 0, 1
 TAU_WHITE, TAU_SUN, TAU_MONFORTE = 0, 1, 2   # expressions of the PPP parameter (Sec. 4.3)
 PERM_CONSTANT, PERM_KOZENY_CARMAN = 0, 1     # permeability model (Eq. kozeny-carman)
 P2G_LUMPED, P2G_CONSISTENT = 0, 1             # Stage-1 mapping (Eqs. map-from-particles-to-nodes[-consistent])
+MODEL_NEOHOOKE, MODEL_HENCKY = 0, 1           # hyperelastic model of the solid skeleton
 
 
 @dataclass
@@ -61,6 +62,7 @@ class Workload:
     permeability: int = 0           # PERM_CONSTANT, or PERM_KOZENY_CARMAN (k = k0 at phi0)
     dt_growth: float = 1.0          # the time step is multiplied by this after each step
     p2g_mass: int = 0               # P2G_LUMPED, or P2G_CONSISTENT (Stage-1 mapping)
+    model: int = 0                  # MODEL_NEOHOOKE, or MODEL_HENCKY (Sec. 2.2)
     dt: float = 1.0
     nsteps: int = 1
     ramp_time: float = 0.0          # load scale min(t / ramp_time, 1); 0 = applied at once
