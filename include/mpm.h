@@ -87,6 +87,13 @@ enum { MPM_PERM_CONSTANT = 0, MPM_PERM_KOZENY_CARMAN = 1 };
  * tolerance within 1000 iterations fails with MPM_ERR_KRYLOV_STAGNATED. */
 enum { MPM_P2G_LUMPED = 0, MPM_P2G_CONSISTENT = 1 };
 
+/* Hyperelastic model of the solid skeleton: NEOHOOKE, tau' = G (b - 1) +
+ * lambda ln J 1 (the default), or HENCKY (Sec. 2.2: Psi = lambda/2 (ln J)^2 +
+ * G tr((ln b / 2)^2), tau' = lambda ln J 1 + G ln b), with its spectral
+ * tangent in the Jacobian and in the Kelvin stress; HENCKY runs in FP64
+ * (precision MPM_MIXED is rejected). */
+enum { MPM_MODEL_NEOHOOKE = 0, MPM_MODEL_HENCKY = 1 };
+
 /* Preconditioner of the FGMRES solve of the Newton system: node-block Jacobi,
  * or the Schur-complement block preconditioner of Sec. 3.4 with geometric
  * multigrid V-cycles for the displacement block and the pressure Schur
@@ -204,6 +211,7 @@ typedef struct {
   int32_t tau_kind;           /* MPM_TAU_* (default WHITE) */
   int32_t permeability;       /* MPM_PERM_* (default CONSTANT) */
   int32_t p2g_mass;           /* MPM_P2G_* (default LUMPED) */
+  int32_t model;              /* MPM_MODEL_* (default NEOHOOKE) */
 } mpm_options;
 
 /* Neumann data of one step: traction t^ per surface entry (n_surf*dim), and

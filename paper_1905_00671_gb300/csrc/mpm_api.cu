@@ -525,6 +525,8 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   if (opt->tau_kind < MPM_TAU_WHITE || opt->tau_kind > MPM_TAU_MONFORTE) return MPM_ERR_BAD_ARG;
   if (opt->permeability != MPM_PERM_CONSTANT && opt->permeability != MPM_PERM_KOZENY_CARMAN) return MPM_ERR_BAD_ARG;
   if (opt->p2g_mass != MPM_P2G_LUMPED && opt->p2g_mass != MPM_P2G_CONSISTENT) return MPM_ERR_BAD_ARG;
+  if (opt->model != MPM_MODEL_NEOHOOKE && opt->model != MPM_MODEL_HENCKY) return MPM_ERR_BAD_ARG;
+  if (opt->model == MPM_MODEL_HENCKY && opt->precision != MPM_FP64) return MPM_ERR_BAD_ARG;
   if (opt->permeability == MPM_PERM_KOZENY_CARMAN && !(mat->phi0 > 0.0 && mat->phi0 < 1.0)) return MPM_ERR_BAD_ARG;
   // tau_M uses the Newmark parameters: dynamic steps only (Sec. 4.3)
   if (opt->stabilize && opt->tau_kind == MPM_TAU_MONFORTE && opt->scheme != MPM_NEWMARK) return MPM_ERR_BAD_ARG;
@@ -594,6 +596,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   s.alpha_vis = c.dyn ? mat->alpha_vis : 0.0;
   s.phi_min = opt->min_volume_fraction;
   s.kozeny = opt->permeability == MPM_PERM_KOZENY_CARMAN;
+  s.hencky = opt->model == MPM_MODEL_HENCKY;
   for (int k = 0; k < 3; ++k) s.g[k] = k < c.d ? mat->g[k] : 0.0;
   c.n = P->n;
   c.n_surf = P->n_surf;
@@ -624,7 +627,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   A(&c.sh_S0, 3 * MAXS * n);
   A(&c.m, n);
   A(&c.rec, RC_COUNT * n);
-  A(&c.pn, (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn) * n);
+  A(&c.pn, (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn, opt->model == MPM_MODEL_HENCKY) * n);
   A(&c.M, nn);
   A(&c.Pn, nn);
   A(&c.vn, d * nn);
@@ -811,6 +814,7 @@ void mpm_default_options(mpm_options *o) {
   o->tau_kind = MPM_TAU_WHITE;
   o->permeability = MPM_PERM_CONSTANT;
   o->p2g_mass = MPM_P2G_LUMPED;
+  o->model = MPM_MODEL_NEOHOOKE;
   o->stream = nullptr;
 }
 

@@ -45,6 +45,63 @@ __device__ inline bool in_box(const DevView &v, int64_t q, const int ac[3], int 
   return true;
 }
 
+// ---- Hencky elasticity (Sec. 2.2): tau' = lambda ln J 1 + G ln b.  With
+// b = sum_A x_A n_A n_A, eps_A = ln(x_A) / 2, tau_A = lambda sum_B eps_B +
+// 2 G eps_A, the spatial tangent (L_v tau' = c : d) is
+//   c = sum_AB (lambda + kappa_A delta_AB) m_A (x) m_B
+//     + sum_{A != B} theta_AB (m_AB (x) m_AB + m_AB (x) m_BA),
+// kappa_A = 2G - 2 tau_A, theta_AB = (tau_A x_B - tau_B x_A) / (x_A - x_B)
+// = G log1p(r) / r - tau_B with r = x_A / x_B - 1 (no cancellation, limit
+// G - tau_A at equal stretches); m_A = n_A n_A, m_AB = n_A n_B.  In plane
+// strain b is the in-plane block (third stretch 1).
+// Cyclic Jacobi rotations: A = Q diag(w) Q^T (columns of Q the eigenvectors).
+template <int D>
+__device__ inline void sym_eig(const double *A, double w[3], double Q[9]) {
+  double M[3][3];
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      M[i][j] = A[i * D + j];
+      Q[i * D + j] = i == j ? 1.0 : 0.0;
+    }
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < D; ++i) {
+      diag += M[i][i] * M[i][i];
+      for (int j = i + 1; j < D; ++j) off += M[i][j] * M[i][j];
+    }
+    if (off <= 1e-36 * diag) break;
+    for (int p = 0; p < D; ++p)
+      for (int q = p + 1; q < D; ++q) {
+        if (M[p][q] == 0.0) continue;
+        const double th = 0.5 * atan2(2.0 * M[p][q], M[q][q] - M[p][p]);
+        const double c = cos(th), s = sin(th);
+        for (int k = 0; k < D; ++k) {
+          const double mkp = M[k][p], mkq = M[k][q];
+          M[k][p] = c * mkp - s * mkq;
+          M[k][q] = s * mkp + c * mkq;
+        }
+        for (int k = 0; k < D; ++k) {
+          const double mpk = M[p][k], mqk = M[q][k];
+          M[p][k] = c * mpk - s * mqk;
+          M[q][k] = s * mpk + c * mqk;
+        }
+        for (int k = 0; k < D; ++k) {
+          const double qkp = Q[k * D + p], qkq = Q[k * D + q];
+          Q[k * D + p] = c * qkp - s * qkq;
+          Q[k * D + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  for (int i = 0; i < D; ++i) w[i] = M[i][i];
+}
+
+__device__ inline double log1p_ratio(double r) {
+  return fabs(r) > 1e-6 ? log1p(r) / r : 1.0 - r / 2.0 + r * r / 3.0;
+}
+
+// slot of the pair (A, B), A < B, among (0,1), (0,2), (1,2)
+__device__ inline int pair_index(int A, int B) { return A + B - 1; }
+
 // g = Gn . dF^{-1}
 template <int D>
 __device__ inline void spatial_grad(const DevView &v, int64_t q, const double Gn[3], double g[3]) {
@@ -341,10 +398,35 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
   const double mu_p = G - lam * lnJ;
   const double vol = dJ * Vn;
   double *rec = v.rec;
+  double hq[9], hk[3], ht[3];  // Hencky: principal directions, kappa_A, theta_AB
+  if (s.hencky) {
+    double x[3], eps[3], tA[3], tr = 0.0;
+    sym_eig<D>(bl, x, hq);
+    for (int A = 0; A < D; ++A) {
+      eps[A] = 0.5 * log(x[A]);
+      tr += eps[A];
+    }
+    for (int A = 0; A < D; ++A) {
+      tA[A] = lam * tr + 2.0 * G * eps[A];
+      hk[A] = 2.0 * G - 2.0 * tA[A];
+    }
+    for (int A = 0; A < D; ++A)
+      for (int B = A + 1; B < D; ++B) ht[pair_index(A, B)] = G * log1p_ratio(x[A] / x[B] - 1.0) - tA[B];
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j) {
+        double t = 0.0;
+        for (int A = 0; A < D; ++A) t += tA[A] * hq[i * D + A] * hq[j * D + A];
+        rec[(RC_TAU + i * D + j) * n + p] = t;
+      }
+    for (int i = 0; i < D * D; ++i) rec[(RC_HQ + i) * n + p] = hq[i];
+    for (int A = 0; A < D; ++A) rec[(RC_HK + A) * n + p] = hk[A];
+    for (int k = 0; k < D * (D - 1) / 2; ++k) rec[(RC_HT + k) * n + p] = ht[k];
+  }
   for (int i = 0; i < D; ++i)
     for (int j = 0; j < D; ++j) {
       rec[(RC_FINV + i * D + j) * n + p] = fi[i * D + j];
-      rec[(RC_TAU + i * D + j) * n + p] = G * (bl[i * D + j] - (i == j ? 1.0 : 0.0)) + (i == j ? lam * lnJ : 0.0);
+      if (!s.hencky)
+        rec[(RC_TAU + i * D + j) * n + p] = G * (bl[i * D + j] - (i == j ? 1.0 : 0.0)) + (i == j ? lam * lnJ : 0.0);
     }
   double gp[3] = {0, 0, 0}, gv[9] = {0};
   for (int j = 0; j < D; ++j) {
@@ -370,6 +452,27 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
         rec[(RC_SVIS + i * D + j) * n + p] =
             s.alpha_vis * ((i == j ? lam * trD : 0.0) + 2.0 * mu_p * Dij);
       }
+    if (s.hencky) {  // alpha c : d with the Hencky tangent, in the principal frame
+      double Dh[9], Sh[9];
+      for (int A = 0; A < D; ++A)
+        for (int B = 0; B < D; ++B) {
+          double t = 0.0;
+          for (int i = 0; i < D; ++i)
+            for (int j = 0; j < D; ++j) t += hq[i * D + A] * 0.5 * (gv[i * D + j] + gv[j * D + i]) * hq[j * D + B];
+          Dh[A * D + B] = t;
+        }
+      for (int A = 0; A < D; ++A)
+        for (int B = 0; B < D; ++B)
+          Sh[A * D + B] = A == B ? lam * trD + hk[A] * Dh[A * D + A]
+                                 : 2.0 * ht[pair_index(A < B ? A : B, A < B ? B : A)] * Dh[A * D + B];
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          double t = 0.0;
+          for (int A = 0; A < D; ++A)
+            for (int B = 0; B < D; ++B) t += hq[i * D + A] * Sh[A * D + B] * hq[j * D + B];
+          rec[(RC_SVIS + i * D + j) * n + p] = s.alpha_vis * t;
+        }
+    }
   } else {
     divv = log(dJ) / dt;
   }
@@ -498,11 +601,18 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
 // and the point's own record (last slot) holds grad p at 9..9+D-1.  (The
 // terms are those of the linearization, Eqs. jacobian-system-stabilized-ppp
 // and newmark-linearization, grouped per node.)
-template <int D, bool DYN, typename R>
+// Hencky (HK): the material part of the tangent is not of the lambda / G'
+// form, so p1 = 0, p2 = p3 = vol p, and the record ends with the d^3 values
+// U_ikl = -cs (1 + cv) sum_j g_j c_ijkl at offset pn_npf(D, DYN), so that the
+// term adds sum_l U_a,ikl g_b,l to A_ik; from the principal data of the point
+//   sum_j g_j c_ijkl = lambda g_i delta_kl + sum_A n_Ai (kappa_A gh_A n_Ak n_Al
+//                      + sum_{B != A} theta_AB gh_B (n_Ak n_Bl + n_Bk n_Al)),
+// gh_A = g . n_A.
+template <int D, bool DYN, bool HK, typename R>
 __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                               R *__restrict__ pn) {
   constexpr int NSL = pn_nslot(D);
-  constexpr int NPF = pn_npf(D, DYN);
+  constexpr int NPF = pn_npf(D, DYN, HK);
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = v.n;
   if (t >= n * NSL) return;
@@ -520,8 +630,9 @@ __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, c
   const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
   const R cv = DYN ? (R)(sp.alpha_vis * sp.gamma / (sp.beta * sp.dt)) : R(0);
   const R csv = cs * (R(1) + cv);
-  const R p0 = cs, p1 = csv * rec[RC_MUP * n + q];
-  const R p2 = vol * ph - csv * rec[RC_LAM * n + q], p3 = csv * rec[RC_MUP * n + q] + vol * ph;
+  const R p0 = cs, p1 = HK ? R(0) : csv * rec[RC_MUP * n + q];
+  const R p2 = HK ? vol * ph : vol * ph - csv * rec[RC_LAM * n + q];
+  const R p3 = HK ? vol * ph : csv * rec[RC_MUP * n + q] + vol * ph;
   const R p5 = vol, p6 = rec[RC_B2 * n + q], p7 = rec[RC_KV * n + q], p8 = rec[RC_CST * n + q];
   int nc[3] = {0, 0, 0};
   for (int k = 0; k < D; ++k) nc[k] = v.sh_first[k * n + q] + off[k];
@@ -559,16 +670,44 @@ __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, c
       out[5 * D + 7 + k] = gv;
     }
   }
+  if (HK) {
+    constexpr int UOFF = pn_npf(D, DYN);
+    R nq[9], kap[3], th[3], gh[3];
+    for (int i = 0; i < D * D; ++i) nq[i] = rec[(RC_HQ + i) * n + q];
+    for (int A = 0; A < D; ++A) kap[A] = rec[(RC_HK + A) * n + q];
+    for (int k = 0; k < D * (D - 1) / 2; ++k) th[k] = rec[(RC_HT + k) * n + q];
+    for (int A = 0; A < D; ++A) {
+      R t = 0;
+      for (int j = 0; j < D; ++j) t += gs[j] * nq[j * D + A];
+      gh[A] = t;
+    }
+    const R lam = rec[RC_LAM * n + q];
+    for (int i = 0; i < D; ++i)
+      for (int k = 0; k < D; ++k)
+        for (int l = 0; l < D; ++l) {
+          R u = k == l ? lam * gs[i] : R(0);
+          for (int A = 0; A < D; ++A) {
+            R w = kap[A] * gh[A] * nq[k * D + A] * nq[l * D + A];
+            for (int B = 0; B < D; ++B)
+              if (B != A) {
+                const R tAB = th[pair_index(A < B ? A : B, A < B ? B : A)];
+                w += tAB * gh[B] * (nq[k * D + A] * nq[l * D + B] + nq[k * D + B] * nq[l * D + A]);
+              }
+            u += nq[i * D + A] * w;
+          }
+          out[UOFF + (i * D + k) * D + l] = -csv * u;
+        }
+  }
 }
 
-template <int D, bool GIMP, bool DYN, typename T, typename R>
+template <int D, bool GIMP, bool DYN, bool HK, typename T, typename R>
 __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn,
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   constexpr int NSLOT = D == 2 ? 49 : 343;
   constexpr int NSL = pn_nslot(D);
-  constexpr int NPF = pn_npf(D, DYN);
+  constexpr int NPF = pn_npf(D, DYN, HK);
   if (t >= NSLOT * g.nnodes) return;
   const int64_t a = t % g.nnodes;
   const int64_t e = block_of_slot<D>(mask, row_ptr, a, (int)(t / g.nnodes));
@@ -617,6 +756,8 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
             for (int k = 0; k < D; ++k) {
               R acc = fma(ga[i], pb[D + 2 + k], B[i * NB + k]);
               acc = fma(-gb[i], pa[2 * D + 2 + k], acc);
+              if (HK)  // material part of the Hencky tangent, staged per node
+                for (int l = 0; l < D; ++l) acc = fma(pa[pn_npf(D, DYN) + (i * D + k) * D + l], gb[l], acc);
               B[i * NB + k] = i == k ? acc - dg : acc;
             }
           // B1 column: (p5 S_b) g_a
@@ -1175,20 +1316,26 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
   R *pn = (R *)c.pn;
   if (staged) {
     const int npb = nblk((int64_t)pn_nslot(c.d) * c.n, TPB);
+#define PNODES(D, Y, H) k_point_nodes<D, Y, H, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn)
+    const bool hk = c.s.hencky;
     if (c.d == 2) {
-      if (c.dyn) k_point_nodes<2, true, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
-      else k_point_nodes<2, false, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
+      if (c.dyn) { if (hk) PNODES(2, true, true); else PNODES(2, true, false); }
+      else { if (hk) PNODES(2, false, true); else PNODES(2, false, false); }
     } else {
-      if (c.dyn) k_point_nodes<3, true, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
-      else k_point_nodes<3, false, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn);
+      if (c.dyn) { if (hk) PNODES(3, true, true); else PNODES(3, true, false); }
+      else { if (hk) PNODES(3, false, true); else PNODES(3, false, false); }
     }
+#undef PNODES
     UPMPM_LAUNCH(c);
   }
 #define JAC(D, G, Y)                                                                                         \
   do {                                                                                                       \
-    if (staged)                                                                                              \
-      k_jacobian<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr, c.col, val,   \
-                                                       apply_bc);                                            \
+    if (staged && c.s.hencky)                                                                                \
+      k_jacobian<D, G, Y, true, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr, c.col,  \
+                                                             val, apply_bc);                                 \
+    else if (staged)                                                                                         \
+      k_jacobian<D, G, Y, false, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr, c.col, \
+                                                              val, apply_bc);                                \
     else                                                                                                     \
       k_jacobian_direct<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask, c.row_ptr,   \
                                                               c.col, val, apply_bc);                         \

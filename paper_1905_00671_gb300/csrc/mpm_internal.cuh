@@ -62,7 +62,9 @@ constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
 // Jacobian staging: per point, one record per support slot (MAXS^d) and one
 // for the point's own coefficients, pn_npf(d, dyn) values each (the layout is
 // in k_point_nodes).
-__host__ __device__ constexpr int pn_npf(int d, bool dyn) { return dyn ? 6 * d + 7 : 5 * d + 6; }
+__host__ __device__ constexpr int pn_npf(int d, bool dyn, bool hencky = false) {
+  return (dyn ? 6 * d + 7 : 5 * d + 6) + (hencky ? d * d * d : 0);
+}
 __host__ __device__ constexpr int pn_nslot(int d) { return (d == 2 ? MAXS * MAXS : MAXS * MAXS * MAXS) + 1; }
 
 // ---- particle fields ------------------------------------------------------
@@ -119,7 +121,10 @@ enum RField {
   RC_B2 = 54,      // B2 divergence coefficient
   RC_MS = 55,      // m (inertia Jacobian)
   RC_DKV = 56,     // J dkappa/dJ * vol (Kozeny-Carman; 0 for a constant permeability)
-  RC_COUNT = 57
+  RC_HQ = 57,      // 9  Hencky: principal directions of b (columns, d x d)
+  RC_HK = 66,      // 3  Hencky: kappa_A = 2G - 2 tau_A (diagonal part of the tangent)
+  RC_HT = 69,      // 3  Hencky: theta_AB of the pairs (0,1), (0,2), (1,2)
+  RC_COUNT = 72
 };
 
 // error bits raised by kernels (read back at synchronisation points)
@@ -140,6 +145,7 @@ struct StepP {
   double phi0, rho_s;
   double phi_min;  // minimum nodal volume fraction of an active node
   int kozeny;      // permeability from porosity by Eq. kozeny-carman (else constant)
+  int hencky;      // Hencky elasticity (Sec. 2.2), else compressible neo-Hookean
 };
 
 // all device pointers the kernels need, passed by value

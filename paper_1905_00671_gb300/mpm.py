@@ -24,6 +24,7 @@ MPM_FP64, MPM_MIXED = 0, 1
 MPM_TAU_WHITE, MPM_TAU_SUN, MPM_TAU_MONFORTE = 0, 1, 2
 MPM_PERM_CONSTANT, MPM_PERM_KOZENY_CARMAN = 0, 1
 MPM_P2G_LUMPED, MPM_P2G_CONSISTENT = 0, 1
+MPM_MODEL_NEOHOOKE, MPM_MODEL_HENCKY = 0, 1
 MPM_PRECOND_BLOCK_JACOBI, MPM_PRECOND_SCHUR_MG = 0, 1
 MPM_MAX_NEWTON = 64
 PROF = {"spmv": 0, "jacobian": 1, "residual": 2, "point": 3, "orth": 4, "p2g": 5, "g2p": 6,
@@ -65,7 +66,8 @@ class mpm_options(C.Structure):
                 ("krylov_restart", C.c_int32), ("krylov_max", C.c_int32), ("precond", C.c_int32),
                 ("min_volume_fraction", C.c_double), ("profile", C.c_int32),
                 ("precond_lag", C.c_int32), ("schur_approx", C.c_int32), ("stream", C.c_void_p),
-                ("tau_kind", C.c_int32), ("permeability", C.c_int32), ("p2g_mass", C.c_int32)]
+                ("tau_kind", C.c_int32), ("permeability", C.c_int32), ("p2g_mass", C.c_int32),
+                ("model", C.c_int32)]
 
 
 class mpm_loads(C.Structure):
@@ -191,6 +193,7 @@ def _options(w, stream, opts) -> mpm_options:
     o.tau_kind = int(w.tau_kind)
     o.permeability = int(w.permeability)
     o.p2g_mass = int(w.p2g_mass)
+    o.model = int(w.model)
     for key, val in opts.items():
         setattr(o, key, val)
     if stream is not None:

@@ -44,6 +44,10 @@ CASES = {
                                                  dt=1.0),
     "block3d-gimp-qs": lambda: I.small_block(seed=11, body=(6, 5, 4)),
     "block3d-orig-qs": lambda: I.small_block(seed=12, shape=I.ORIG, body=(5, 4, 4)),
+    # Hencky elasticity (Sec. 2.2), with the Kelvin stress of Sec. 5.2 (alpha_vis = 0.04)
+    "footing2d-gimp-newmark-hencky": lambda: replace(I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25),
+                                                     model=I.MODEL_HENCKY, alpha_vis=0.04),
+    "block3d-gimp-qs-hencky": lambda: replace(I.small_block(seed=11, body=(6, 5, 4)), model=I.MODEL_HENCKY),
 }
 
 
@@ -120,6 +124,9 @@ STEP_CASES = {
     "footing2d-gimp-aligned-newmark-consistent": (
         lambda: replace(I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25, jitter=0.0),
                         p2g_mass=I.P2G_CONSISTENT), 3),
+    "footing2d-gimp-newmark-hencky": (CASES["footing2d-gimp-newmark-hencky"], 3),
+    "block3d-gimp-qs-hencky": (CASES["block3d-gimp-qs-hencky"], 2),
+    "self-weight-paper-16x16-hencky": (lambda: replace(I.self_weight_consolidation(), model=I.MODEL_HENCKY), 2),
     "self-weight-6x6-consistent": (
         lambda: replace(I.self_weight_consolidation(ncell=(6, 6), h=1.0 / 3.0, ppc_axis=2, K=1.5e6, k0=1e-10),
                         p2g_mass=I.P2G_CONSISTENT), 2),
@@ -225,6 +232,13 @@ def test_bad_arguments_are_rejected(mpm):
     assert e.value.code == -1
     with pytest.raises(mpm.MPMError) as e:
         mpm.Simulation(w, p2g_mass=2)
+    assert e.value.code == -1
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(w, model=2)
+    assert e.value.code == -1
+    # Hencky runs in FP64 only
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.Simulation(replace(w, model=I.MODEL_HENCKY), precision=mpm.MPM_MIXED)
     assert e.value.code == -1
     # Kozeny-Carman needs an initial porosity in (0, 1)
     with pytest.raises(mpm.MPMError) as e:
