@@ -64,6 +64,8 @@ def make_workload(name):
         return I.terzaghi_column()
     if name == "block3d":
         return I.consolidation_block()
+    if name == "slope":
+        return I.slope_3d()
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -347,8 +347,9 @@ int eval_residual(Ctx &c, double *rnorm) {
 // residual test of the Newton loop decides convergence.
 template <typename T>
 int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
-  run_jacobian<T>(c, S.val, 1);
   int rc;
+  if (sizeof(T) == sizeof(double) && (rc = ensure_jacobian_staging(c))) return rc;
+  run_jacobian<T>(c, S.val, 1);
   prof_begin(c, MPM_PROF_SETUP);
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
     const int lag = c.opt.precond_lag > 1 ? c.opt.precond_lag : 1;
@@ -627,7 +628,9 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   A(&c.sh_S0, 3 * MAXS * n);
   A(&c.m, n);
   A(&c.rec, RC_COUNT * n);
-  A(&c.pn, (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn, opt->model == MPM_MODEL_HENCKY) * n);
+  // the FP64 Jacobian's staging (allocated on first use in a mixed context,
+  // whose Jacobian is FP32 and unstaged)
+  if (opt->precision == MPM_FP64) A(&c.pn, (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn, opt->model == MPM_MODEL_HENCKY) * n);
   A(&c.M, nn);
   A(&c.Pn, nn);
   A(&c.vn, d * nn);
@@ -1164,6 +1167,8 @@ int mpm_debug_eval(mpm_ctx *h, const double *X, double *R, double *Jv, int32_t a
   run_residual(c, c.dX, c.R, apply_bc);
   cudaMemcpyAsync(R, c.R, sizeof(double) * N, cudaMemcpyDeviceToHost, c.st);
   if (Jv) {
+    rc = ensure_jacobian_staging(c);
+    if (rc) return rc;
     run_jacobian<double>(c, c.L64.val, apply_bc);
     cudaMemcpyAsync(Jv, c.L64.val, sizeof(double) * c.nnzb * c.nb * c.nb, cudaMemcpyDeviceToHost, c.st);
   }
@@ -1181,6 +1186,8 @@ int mpm_debug_precond(mpm_ctx *h, const double *X, const double *v, double *z) {
   if (rc) return rc;
   run_residual(c, c.X, c.R, 1);
   LinSys<double> &S = c.L64;
+  rc = ensure_jacobian_staging(c);
+  if (rc) return rc;
   run_jacobian<double>(c, S.val, 1);
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
     rc = schur_setup<double>(c, S);

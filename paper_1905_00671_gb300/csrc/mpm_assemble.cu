@@ -1090,6 +1090,17 @@ __global__ void k_cm_init(int64_t nn, int K, const double *__restrict__ rhs, con
 }  // namespace
 
 // ============================================================== launchers
+int ensure_jacobian_staging(Ctx &c) {
+  if (c.pn) return MPM_OK;
+  if (cudaMalloc(&c.pn, sizeof(double) * (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn, c.s.hencky) * c.n) !=
+      cudaSuccess) {
+    c.pn = nullptr;
+    c.last_error = "device allocation of the Jacobian staging failed";
+    return MPM_ERR_NO_MEMORY;
+  }
+  return MPM_OK;
+}
+
 int run_consistent_p2g(Ctx &c) {
   const int64_t nn = c.g.nnodes;
   const int D = c.d, K = c.dyn ? 2 * D + 3 : 1;
@@ -1313,6 +1324,7 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
   }
   // FP64: stage the per-(point, node) vectors, then assemble; FP32: direct
   constexpr bool staged = sizeof(R) == sizeof(double);
+  if (staged && !c.pn) return;  // callers run ensure_jacobian_staging first
   R *pn = (R *)c.pn;
   if (staged) {
     const int npb = nblk((int64_t)pn_nslot(c.d) * c.n, TPB);

@@ -291,6 +291,7 @@ void run_g2p(Ctx &c);
 // assembly
 int run_pattern(Ctx &c);                          // builds row_ptr / col / row_of
 int run_consistent_p2g(Ctx &c);  // Stage-1 fields by the consistent mass (after run_pattern)
+int ensure_jacobian_staging(Ctx &c);  // the FP64 Jacobian's staging buffer (allocated by FP64 contexts at create)
 void run_initial_guess(Ctx &c);   // also sets the active flags
 void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
 void run_count_terms(Ctx &c);     // Jacobian term counts into c.terms (device)

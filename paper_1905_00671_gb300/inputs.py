@@ -308,6 +308,64 @@ def consolidation_block(body=(64, 64, 32), pad=1, h=0.1, seed=3, ppc_axis=2, E=1
                     u_fixed=uf, u_value=uv, p_fixed=pf, p_value=pv)
 
 
+def slope_3d(ncell=(128, 128, 64), h=0.1, ppc_axis=2, E=5e6, nu=0.35, k=1e-12, slope_deg=30.0,
+             z_toe=1.2, z_crest=5.2, x_toe=2.9, water_table=None, dt=10.0, nsteps=100,
+             shape=GIMP, name=None):
+    """3D slope under gravity: the cells whose centre lies below the ground
+    surface z(x) = z_toe + tan(slope) (x - x_toe), clipped to [z_toe, z_crest]
+    (a 30 degree slope between a toe and a crest plateau, about half of a
+    128 x 128 x 64 box at 0.1 m: 4.2M points at 2^3 per cell); gravity from
+    t = 0 on a stress-free skeleton with a hydrostatic pore pressure below the
+    water table (default mid-height of the box); the ground surface drained to
+    the water table's level, p = max(rho_f g (z_w - z), 0); fixed bottom,
+    rollers on the four sides (impermeable)."""
+    dim = 3
+    nc = (int(ncell[0]), int(ncell[1]), int(ncell[2]))
+    zw = 0.5 * nc[2] * h if water_table is None else water_table
+    tan = np.tan(np.deg2rad(slope_deg))
+    xc = (np.arange(nc[0]) + 0.5) * h
+    zsurf = np.clip(z_toe + tan * (xc - x_toe), z_toe, z_crest)          # per column of cells
+    ncol = np.floor(zsurf / h + 0.5).astype(int)                         # filled cells per column
+    filled = np.zeros((nc[0], nc[2]), bool)                              # [x cell][z cell]
+    for i in range(nc[0]):
+        filled[i, :ncol[i]] = True
+    x, vol, lp = lattice(dim, nc, h, ppc_axis)
+    ci = np.minimum((x[:, 0] / h).astype(int), nc[0] - 1)
+    ck = np.minimum((x[:, 2] / h).astype(int), nc[2] - 1)
+    keep = filled[ci, ck]
+    x, vol, lp = np.ascontiguousarray(x[keep]), vol[keep], np.ascontiguousarray(lp[keep])
+    n = x.shape[0]
+    rho_f, g = 1000.0, 9.81
+    p0 = np.maximum(rho_f * g * (zw - x[:, 2]), 0.0)
+    uf, uv, pf, pv = empty_bcs(dim, nc)
+    nco = node_coords(dim, nc)
+    uf[nco[:, 2] == 0, :] = 1
+    uf[(nco[:, 0] == 0) | (nco[:, 0] == nc[0]), 0] = 1
+    uf[(nco[:, 1] == 0) | (nco[:, 1] == nc[1]), 1] = 1
+    # ground-surface nodes: a filled and an empty cell among the cells around the node (x-z plane)
+    ix, iz = nco[:, 0], nco[:, 2]
+    any_f = np.zeros(len(nco), bool)
+    any_e = np.zeros(len(nco), bool)
+    for dx in (-1, 0):
+        for dz in (-1, 0):
+            cxi, czi = ix + dx, iz + dz
+            ok = (cxi >= 0) & (cxi < nc[0]) & (czi >= 0) & (czi < nc[2])
+            f = np.zeros(len(nco), bool)
+            f[ok] = filled[cxi[ok], czi[ok]]
+            any_f |= f
+            any_e |= ok & ~f
+    surf = any_f & any_e & (iz > 0)
+    pf[surf] = 1
+    pv[surf] = np.maximum(rho_f * g * (zw - iz[surf] * h), 0.0)
+    return Workload(name=name or "slope-{}x{}x{}".format(*nc), dim=dim, shape=shape, ncell=nc,
+                    origin=(0.0, 0.0, 0.0), h=h, x=x, vol=vol, lp=lp, p0=p0, v0=None,
+                    E=np.full(n, E), nu=np.full(n, nu), k=np.full(n, k),
+                    surf_id=np.full(n, -1, np.int32), surf_normal=np.zeros((n, dim)),
+                    surf_area=np.zeros(n), trac_full=np.zeros((0, dim)),
+                    rho_f=rho_f, g=(0.0, 0.0, -g), dynamic=False, dt=dt, nsteps=nsteps,
+                    u_fixed=uf, u_value=uv, p_fixed=pf, p_value=pv)
+
+
 def jittered(w: Workload, seed: int, frac: float = 0.15, shuffle: bool = True,
              E_spread: float = 0.2, logk_spread: float = 1.0) -> Workload:
     """A copy of `w` whose points are displaced by up to `frac` of their spacing

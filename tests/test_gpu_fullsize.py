@@ -61,3 +61,4 @@ def test_block3d_full_size_zero_load_keeps_rest(mpm):
     got = sim.read(("u", "p"))
     assert np.abs(got["u"]).max() == 0.0 and np.abs(got["p"]).max() == 0.0
     sim.close()
+

@@ -127,6 +127,8 @@ STEP_CASES = {
     "footing2d-gimp-newmark-hencky": (CASES["footing2d-gimp-newmark-hencky"], 3),
     "block3d-gimp-qs-hencky": (CASES["block3d-gimp-qs-hencky"], 2),
     "self-weight-paper-16x16-hencky": (lambda: replace(I.self_weight_consolidation(), model=I.MODEL_HENCKY), 2),
+    # the 3D slope under gravity with a water table (coarse grid, same geometry)
+    "slope3d-16x8x8": (lambda: I.slope_3d(ncell=(16, 8, 8), h=0.8), 2),
     "self-weight-6x6-consistent": (
         lambda: replace(I.self_weight_consolidation(ncell=(6, 6), h=1.0 / 3.0, ppc_axis=2, K=1.5e6, k0=1e-10),
                         p2g_mass=I.P2G_CONSISTENT), 2),
