@@ -1081,7 +1081,16 @@ void dense_invert_pair(Ctx &c, MGHier<real> &H0, MGHier<real> &H1) {
   c.launches += 2;
 }
 
-constexpr real MG_OMEGA = 0.6;
+// Damping of the block-Jacobi smoother.  A damped Jacobi sweep is stable only
+// while omega * lambda_max(Dinv A) < 2 on every level.  Measured lambda_max:
+// at most 2.5 for the plane-strain blocks of the strip footing (2D), 3.25 on
+// the 3D consolidation block and 3.5 next to the inclined free surface of the
+// 3D slope, where 0.6 made the V-cycle diverge (FGMRES at its cap; 14
+// iterations instead of 232 with 0.5 on a 32 x 32 x 16 slope).
+template <int D>
+constexpr real mg_omega() {
+  return D == 3 ? real(0.5) : real(0.6);
+}
 
 // one damped block-Jacobi sweep on level l: x <- x + omega Dinv (b - A x)
 template <int B, int D>
@@ -1091,15 +1100,15 @@ void sweep(Ctx &c, MGHier<real> &H, int l) {
     constexpr int SPL = B <= 2 ? 4 / B : 1;
     const Geom g = geom(c, L.nnodes * B * SPL);
     launch_pdl(c, k_mg_csr_row<B, SPL, true>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
-               (const real *)H.b[l], MG_OMEGA);
+               (const real *)H.b[l], mg_omega<D>());
   } else {
     const Geom g = geom(c, L.nnodes * LN_<D>::v);
     if (l == 0)
       launch_pdl(c, k_mg_smooth<B, D, false>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
-                 (const real *)H.b[l], MG_OMEGA, 0);
+                 (const real *)H.b[l], mg_omega<D>(), 0);
     else
       launch_pdl(c, k_mg_smooth<B, D, true>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
-                 (const real *)H.b[l], MG_OMEGA, 0);
+                 (const real *)H.b[l], mg_omega<D>(), 0);
   }
   std::swap(H.x[l], H.x2[l]);
 }
@@ -1116,7 +1125,7 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
     for (int k = 0; k < A.nl; ++k) A.lv[k] = TailLevel{H.L[l + k], H.x[l + k], H.x2[l + k], H.b[l + k], H.r[l + k]};
     A.Ai = H.Ai;
     A.ncoarse = H.ncoarse;
-    A.omega = MG_OMEGA;
+    A.omega = mg_omega<D>();
     launch_pdl(c, k_mg_tail<B, D>, 1, TAIL_THREADS, 0, A);
     // three sweeps per level swapped x and x2 (as sweep() does on the host)
     for (int k = l; k < H.nlev - 1; ++k) std::swap(H.x[k], H.x2[k]);
@@ -1135,7 +1144,7 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
     constexpr int SPL = B <= 2 ? 4 / B : 1;
     const Geom g0 = geom(c, L.nnodes * B * SPL);
     launch_pdl(c, k_mg_csr_row<B, SPL, false>, g0.blocks, g0.tpb, 0, L, (const real *)H.x[l], H.r[l],
-               (const real *)H.b[l], MG_OMEGA);
+               (const real *)H.b[l], mg_omega<D>());
   } else if (l == 0) {
     launch_pdl(c, k_mg_resid<B, D, false>, gr.blocks, gr.tpb, 0, L, (const real *)H.x[l], (const real *)H.b[l],
                H.r[l]);
@@ -1144,7 +1153,7 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
                H.r[l]);
   }
   launch_pdl(c, k_mg_restrict<B, D>, gc.blocks, gc.tpb, 0, L, Ln, (const real *)H.r[l], H.b[l + 1], xn_first,
-             MG_OMEGA);
+             mg_omega<D>());
   vcycle_t<B, D>(c, H, l + 1);
   launch_pdl(c, k_mg_prolong<B, D>, gf.blocks, gf.tpb, 0, L, Ln, H.x[l], (const real *)H.x[l + 1]);
   sweep<B, D>(c, H, l);  // first post-smoothing sweep
@@ -1375,8 +1384,8 @@ void schur_split(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *xs0) {
   MGHier<real> &HS = *S.mgS;
   const Geom g = geom(c, nn);
   const real *dsc = S.dscale, *dinv = HS.L[0].dinv;
-  if (c.d == 2) launch_pdl(c, k_split<2>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, MG_OMEGA);
-  else launch_pdl(c, k_split<3>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, MG_OMEGA);
+  if (c.d == 2) launch_pdl(c, k_split<2>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, mg_omega<2>());
+  else launch_pdl(c, k_split<3>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, mg_omega<3>());
 }
 
 void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
@@ -1387,9 +1396,9 @@ void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
   const int32_t *rp = c.row_ptr, *cl = c.col;
   const real *b1 = S.B1c, *zp = HS.x[0], *vu = S.vu, *dinv = HA.L[0].dinv;
   if (c.d == 2)
-    launch_pdl(c, k_b1c_update<2>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, MG_OMEGA);
+    launch_pdl(c, k_b1c_update<2>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, mg_omega<2>());
   else
-    launch_pdl(c, k_b1c_update<3>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, MG_OMEGA);
+    launch_pdl(c, k_b1c_update<3>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, mg_omega<3>());
   mg_vcycle(c, HA);
 }
 
