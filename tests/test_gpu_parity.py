@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path through the C-ABI against the CPU oracle.
 
-Bars (spec tolerances): binning order and block sparsity bit-exact;
+Bars: binning order and block sparsity bit-exact;
 Stage-1 nodal values, residual and Jacobian entry-wise to 1e-11 relative to
 each block type's largest entry; whole steps to 1e-10 relative (max abs
 difference over the largest magnitude of each field) with both sides solved to
