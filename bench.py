@@ -29,6 +29,12 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# The oracle legs (cpu_baseline and --impl reference) are reported as one core:
+# keep the BLAS / OpenMP thread pools of numpy and scipy at one thread (set
+# before numpy is imported).
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ[_v] = "1"
+
 METRIC = "implicit u–p MPM steps/s and particle-updates/s at 1e-8 residual, FP64 vs mixed"
 UNIT = "particle-updates/s"
 L2_FLUSH_BYTES = 512 << 20
@@ -480,7 +486,8 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "config": dict(workload_config(w), parallelism="cpu"),
+            "data": "synthetic (seeded)",
+            "config": dict(workload_config(w), parallelism="cpu", l2="host CPU: not applicable"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
