@@ -168,9 +168,10 @@ def kernel_source_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    summary was taken on the current kernel source (else None)."""
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` (its name) from the
+    committed ncu summary, if the summary was taken on that workload and on the
+    current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         lines = open(path).read().splitlines()
@@ -179,8 +180,9 @@ def ncu_traffic(kernel):
     src = kernel_source_hash(kernel)
     for ln in lines:
         parts = ln.split()
-        if len(parts) >= 4 and not ln.startswith("#") and parts[0] == kernel and parts[1] == src:
-            return float(parts[3])
+        if (len(parts) >= 5 and not ln.startswith("#") and parts[0] == kernel and parts[1] == src
+                and parts[2] == workload):
+            return float(parts[4])
     return None
 
 
@@ -398,7 +400,7 @@ def run_ours(args, rank, world, local_rank):
         roofline = {"kernel": "k_jacobian", "bound": "alu", "achieved": round(ach, 4),
                     "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
                     "frac": round(ach / FP64_PEAK_TFLOPS, 4),
-                    "traffic": ncu_traffic("k_jacobian"),
+                    "traffic": ncu_traffic("k_jacobian", w.name),
                     "peak_source": "FP64 from unit counts and clocks (152 SMs x 2 FMA/clk x 2070 MHz)",
                     "algorithmic_flops": int(flops), "jac_terms": int(sum(t for t, _ in terms) / len(terms)),
                     "avg_launch_us": round(avg_ms * 1e3, 3),
@@ -416,7 +418,7 @@ def run_ours(args, rank, world, local_rank):
         peak = float(peaks["hbm_gbs"])
         fl = 2 * avg_nnzb * nb * nb / (avg_ms * 1e-3) / 1e12
         spmv = {"kernel": "k_bsr_spmv", "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic("k_bsr_spmv"),
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": ncu_traffic("k_bsr_spmv", w.name),
                 "algorithmic_bytes": int(bytes_launch), "avg_launch_us": round(avg_ms * 1e3, 3),
                 "peak_source": peak_src + " hbm_gbs",
                 "fp64_tflops": round(fl, 4), "fp64_frac": round(fl / FP64_PEAK_TFLOPS, 4)}
