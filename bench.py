@@ -83,6 +83,8 @@ def make_workload(name):
         return I.consolidation_block()
     if name == "slope":
         return I.slope_3d()
+    if name == "harmonic":
+        return I.harmonic_footing()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -196,6 +198,12 @@ def ncu_traffic(kernel, workload):
 # per node the basis, the vectors and 6d + 6 coefficient products (+ 1,
 # Newmark).  {(dim, dynamic): (F, G)}.
 JAC_FLOPS = {(2, False): (45, 43), (2, True): (51, 52), (3, False): (78, 77), (3, True): (86, 96)}
+# Hencky elasticity adds, per term, the d^3 FMAs of sum_l U_a,ikl g_b,l and,
+# per (point, node), the staged U of its spectral tangent: gh_A = g.n_A (d^2
+# FMAs), w_Akl = kappa_A gh_A n_Ak n_Al + sum_{B != A} theta_AB gh_B (n_Ak n_Bl
+# + n_Bk n_Al) (3 + 6 (d - 1) flops each, d^3 of them) and U_ikl = -cs (1 + cv)
+# (lambda g_i delta_kl + sum_A n_Ai w_Akl) (2 d + 1 flops each, d^3 of them).
+JAC_FLOPS_HENCKY = {2: (16, 120), 3: (54, 612)}
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 
@@ -310,7 +318,9 @@ def run_ours(args, rank, world, local_rank):
     # ---- mixed precision (FP32 Jacobian / preconditioner / Krylov in the FP64
     # Newton loop): same steps, same timing rules, error against the FP64 run
     mixed = None
-    if not args.no_mixed:
+    if not args.no_mixed and w.model == mpm.MPM_MODEL_HENCKY:
+        mixed = {"value": None, "unit": UNIT, "skipped": "Hencky elasticity has no FP32 Jacobian"}
+    elif not args.no_mixed:
         sim_m = mpm.Simulation(w, stream=stream.cuda_stream, precision=mpm.MPM_MIXED,
                                newton_max=60, profile=prof_bits, precond_lag=args.precond_lag)
         sim_r = mpm.Simulation(w, stream=stream.cuda_stream)   # FP64 twin for the error
@@ -394,6 +404,8 @@ def run_ours(args, rank, world, local_rank):
     roofline = None
     if prof_n.get("jacobian", 0) > 0:
         F, G = JAC_FLOPS[(w.dim, w.dynamic)]
+        if w.model == mpm.MPM_MODEL_HENCKY:
+            F, G = F + JAC_FLOPS_HENCKY[w.dim][0], G + JAC_FLOPS_HENCKY[w.dim][1]
         flops = sum(F * t + G * pn for t, pn in terms) / len(terms)   # per assembly
         avg_ms = prof_ms["jacobian"] / prof_n["jacobian"]
         ach = flops / (avg_ms * 1e-3) / 1e12

@@ -66,6 +66,7 @@ class Workload:
     dt: float = 1.0
     nsteps: int = 1
     ramp_time: float = 0.0          # load scale min(t / ramp_time, 1); 0 = applied at once
+    load_omega: float = 0.0         # > 0: harmonic load scale 1 - cos(load_omega t) instead of the ramp
     # Dirichlet data per grid node
     u_fixed: np.ndarray = field(default=None)   # (nnodes, d) uint8
     u_value: np.ndarray = field(default=None)   # (nnodes, d) increment over a step
@@ -89,6 +90,8 @@ class Workload:
         return int(np.prod(self.nn))
 
     def load_scale(self, t: float) -> float:
+        if self.load_omega > 0.0:
+            return 1.0 - float(np.cos(self.load_omega * t))
         if self.ramp_time <= 0.0:
             return 1.0
         return min(t / self.ramp_time, 1.0)
@@ -389,6 +392,44 @@ def jittered(w: Workload, seed: int, frac: float = 0.15, shuffle: bool = True,
                    p0=take(p0), v0=take(v0) if v0 is not None else None, E=take(E), nu=take(w.nu),
                    k=take(k), surf_id=np.ascontiguousarray(surf_id),
                    surf_normal=take(w.surf_normal), surf_area=take(w.surf_area))
+
+
+def harmonic_footing(body=(40, 40), pad=4, h=0.25, ppc_axis=2, lam=8.4e6, G=5.6e6, k=1e-14,
+                     w_amp=3e6, omega=100.0, half_width=1.0, dt=1e-3, nsteps=400, alpha_vis=0.04,
+                     shape=GIMP, model=MODEL_HENCKY, p2g_mass=P2G_CONSISTENT, name=None):
+    """Strip footing under harmonic loading (Sec. 5.2 set-up): the right half of a
+    20 m wide, 10 m deep saturated ground (symmetry plane at x = 0), 1,600
+    cells of h = 0.25 m with 4 points each and 160 empty cells above the
+    surface; a 2 m wide footing at the top centre (here 0 <= x <= 1 m) loaded by
+    w = 3 - 3 cos(100 t) MPa, impermeable, the rest of the top drained; bottom
+    fixed, the symmetry plane and the far side rollers, all impermeable but the
+    top.  lambda = 8.4 MPa, G = 5.6 MPa (Hencky), k = 1e-14 m^2, alpha_vis = 0.04,
+    mu_f = 1e-3 Pa s, rho_s = 2500, rho_f = 1000 kg/m^3, phi0 = 0.33; Newmark,
+    dt = 1e-3 s to t = 0.4 s, consistent-mass mapping (the paper's choice for
+    this cyclic load)."""
+    dim = 2
+    ncell = (body[0], body[1] + pad, 0)
+    x, vol, lp = lattice(dim, body, h, ppc_axis)
+    n = x.shape[0]
+    nu = lam / (2.0 * (lam + G))
+    E = 2.0 * G * (1.0 + nu)
+    H = body[1] * h
+    top = _surface(x, 1, H, h, ppc_axis, lambda q: q[:, 0] <= half_width + 1e-12)
+    surf_id, surf_normal, surf_area, trac = _finish(dim, x, top, 1, h / ppc_axis, (0.0, -w_amp))
+    uf, uv, pf, pv = empty_bcs(dim, ncell)
+    nc = node_coords(dim, ncell)
+    uf[nc[:, 1] == 0, :] = 1
+    uf[nc[:, 0] == 0, 0] = 1
+    uf[nc[:, 0] == ncell[0], 0] = 1
+    strip = int(round(half_width / h))
+    pf[(nc[:, 1] == body[1]) & (nc[:, 0] > strip)] = 1
+    return Workload(name=name or f"harmonic-footing-{body[0]}x{body[1]}", dim=dim, shape=shape,
+                    ncell=ncell, origin=(0.0, 0.0, 0.0), h=h, x=x, vol=vol, lp=lp, p0=np.zeros(n),
+                    v0=np.zeros((n, dim)), E=np.full(n, E), nu=np.full(n, nu), k=np.full(n, k),
+                    surf_id=surf_id, surf_normal=surf_normal, surf_area=surf_area, trac_full=trac,
+                    rho_s=2500.0, rho_f=1000.0, phi0=0.33, mu_f=1e-3, alpha_vis=alpha_vis,
+                    dynamic=True, dt=dt, nsteps=nsteps, load_omega=omega, model=model,
+                    p2g_mass=p2g_mass, u_fixed=uf, u_value=uv, p_fixed=pf, p_value=pv)
 
 
 def small_footing(seed=7, shape=GIMP, dynamic=True, body=(24, 12), pad=2, h=0.25, dt=2e-3,

@@ -1,0 +1,60 @@
+"""The strip footing under harmonic loading of Sec. 5.2 (the paper's own set-up
+of that example) in the inputs and the oracle: the load history w = 3 - 3 cos(100 t)
+MPa and the force it puts on the half footing; the grid, point count and
+boundary conditions the paper states; and the paper's observation on its
+Newton-Krylov table that the relative residual falls below 1e-8 within three
+Newton iterations at a nearly quadratic rate (checked on the first steps, with
+Hencky elasticity and the consistent-mass mapping the paper uses here)."""
+import numpy as np
+
+from oracle import oracle as O
+from paper_1905_00671_gb300 import inputs as I
+
+
+def test_harmonic_load_history():
+    w = I.harmonic_footing()
+    for t in (0.0, 0.004, 0.01, np.pi / 200, np.pi / 100, 0.05, 2 * np.pi / 100, 0.4):
+        total = -np.sum(w.traction(t)[:, 1] * w.surf_area[w.surf_id >= 0])   # N per m of footing length
+        w_mpa = 3.0 - 3.0 * np.cos(100.0 * t)
+        assert abs(total - w_mpa * 1e6 * 1.0) <= 1e-9 * 6e6, t    # half footing: 1 m wide
+    assert w.load_scale(0.0) == 0.0
+    np.testing.assert_allclose(w.load_scale(np.pi / 100), 2.0, rtol=1e-15)   # peak 6 MPa
+
+
+def test_harmonic_footing_setup():
+    w = I.harmonic_footing()
+    assert w.dim == 2 and w.h == 0.25 and w.ncell[:2] == (40, 44)       # 1,600 + 160 empty cells
+    assert w.n == 6400 and w.dynamic and w.nsteps * w.dt == 0.4
+    assert w.model == I.MODEL_HENCKY and w.p2g_mass == I.P2G_CONSISTENT
+    lam = w.E * w.nu / ((1 + w.nu) * (1 - 2 * w.nu))
+    G = w.E / (2 * (1 + w.nu))
+    np.testing.assert_allclose(lam, 8.4e6, rtol=1e-12)
+    np.testing.assert_allclose(G, 5.6e6, rtol=1e-12)
+    assert np.all(w.k == 1e-14) and w.alpha_vis == 0.04 and w.phi0 == 0.33
+    assert (w.rho_s, w.rho_f, w.mu_f) == (2500.0, 1000.0, 1e-3)
+    # loaded points: the top row over 0 <= x <= 1 m
+    sx = w.x[w.surf_id >= 0]
+    assert len(sx) == 8 and np.all(sx[:, 0] < 1.0) and np.allclose(sx[:, 1], 10.0 - 0.0625)
+    nc = I.node_coords(2, w.ncell)
+    x, y = nc[:, 0] * w.h, nc[:, 1] * w.h
+    # drained: the ground surface outside the footing only
+    pf = w.p_fixed.astype(bool)
+    assert np.array_equal(pf, (y == 10.0) & (x > 1.0))
+    uf = w.u_fixed.astype(bool)
+    assert np.all(uf[y == 0.0])                                          # fixed bottom
+    assert np.all(uf[(x == 0.0) | (x == 10.0), 0])                       # rollers
+    assert not np.any(uf[(y > 0.0) & (x > 0.0) & (x < 10.0)])
+
+
+def test_harmonic_footing_newton_converges_like_the_paper():
+    w = I.harmonic_footing()
+    o = O.Oracle(w, newton_rtol=1e-8)
+    for _ in range(5):
+        info = o.step()
+        r = np.array(info.res_hist) / info.res_hist[0]
+        assert info.newton_iters <= 3 and r[-1] <= 1e-8, r
+        assert r[1] < 1e-3 and r[2] < r[1] ** 1.5, r                     # nearly quadratic
+    st = o.state()
+    under = (w.x[:, 0] < 1.0) & (w.x[:, 1] > 9.0)
+    assert st["p"][under].mean() > 0.1 * 3e6 * (1 - np.cos(100 * o.t))   # the footing compresses the fluid
+    assert st["u"][under, 1].mean() < 0.0
