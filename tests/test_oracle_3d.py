@@ -91,5 +91,5 @@ def test_free_fall_3d_matches_newmark_closed_form():
         np.testing.assert_allclose(o.x[:, 2] - x0[:, 2], u, rtol=1e-9)
         # the acceleration is the increment over beta dt^2: it carries the residual's round-off floor
         np.testing.assert_allclose(o.a[:, 2], a, rtol=1e-8)
-        assert np.abs(o.x[:, :2] - x0[:, :2]).max() < 1e-14
+        assert np.abs(o.x[:, :2] - x0[:, :2]).max() < 1e-13        # round-off of 3D sums, x ~ 1 m
         assert np.abs(o.F - np.eye(3).reshape(-1)).max() < 1e-12
