@@ -128,3 +128,54 @@ def test_hencky_jacobian_matches_central_differences(dynamic):
 def test_hencky_jacobian_3d_matches_central_differences():
     w = replace(I.small_block(seed=3, body=(2, 2, 2), pad=1, h=0.25), model=I.MODEL_HENCKY)
     _fd_check(w, 1)
+
+
+def _column_3d(model=I.MODEL_HENCKY):
+    # original MPM, the body filling the grid laterally: bases exactly linear
+    w = I.consolidation_block(body=(3, 3, 4), pad=0, h=0.25, E=E, nu=NU, shape=I.ORIG,
+                              logk=(-10.0, -10.0))
+    return replace(w, model=model, trac_full=np.zeros_like(w.trac_full))
+
+
+def _virtual_work_stress_3d(w, grad):
+    """-sum_a R_a (x) x_a / V0 for the affine increment x -> x + grad x."""
+    o = O.Oracle(w)
+    prep = o.prepare(1.0)
+    nc = I.node_coords(3, w.ncell) * w.h
+    X = np.zeros((o.nn, 4))
+    X[:, :3] = nc @ np.asarray(grad).T
+    R, _ = o.eval(prep, X.reshape(-1), None, want_J=False)
+    Rn = R.reshape(-1, 4)
+    return -np.einsum("ai,aj->ij", Rn[:, :3], nc + X[:, :3]) / w.vol.sum()
+
+
+@pytest.mark.parametrize("s", [0.8, 1.25])
+def test_hencky_3d_uniaxial_stretch(s):
+    tau = _virtual_work_stress_3d(_column_3d(), np.diag([0.0, 0.0, s - 1.0]))
+    scale = (LAM + 2 * G) * abs(np.log(s))
+    expect = np.diag([LAM * np.log(s), LAM * np.log(s), (LAM + 2 * G) * np.log(s)])
+    np.testing.assert_allclose(tau, expect, rtol=0, atol=1e-10 * scale)
+
+
+def test_hencky_3d_simple_shear_is_G_ln_b():
+    """dF = 1 + g e_x (x) e_z + g2 e_y (x) e_x (two shears, J = 1): tau' = G ln b
+    with b = dF dF^T, its logarithm from numpy's symmetric eigensolver."""
+    g1, g2 = 0.3, -0.2
+    grad = np.zeros((3, 3))
+    grad[0, 2], grad[1, 0] = g1, g2
+    tau = _virtual_work_stress_3d(_column_3d(), grad)
+    F = np.eye(3) + grad
+    b = F @ F.T
+    wv, Q = np.linalg.eigh(b)
+    expect = G * (Q @ np.diag(np.log(wv)) @ Q.T)      # lambda ln J = 0: J = 1
+    assert abs(np.linalg.det(F) - 1.0) < 1e-14
+    np.testing.assert_allclose(tau, expect, rtol=0, atol=1e-10 * G * abs(g1))
+
+
+def test_hencky_3d_rigid_rotation_is_stress_free():
+    ax = np.array([1.0, 2.0, 2.0]) / 3.0
+    th = np.deg2rad(40.0)
+    K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+    Rm = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+    tau = _virtual_work_stress_3d(_column_3d(), Rm - np.eye(3))
+    assert np.abs(tau).max() < 1e-8 * G
