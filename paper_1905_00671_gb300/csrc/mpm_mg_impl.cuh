@@ -1222,7 +1222,11 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
   }
   H.nlev = l;
   H.ncoarse = (int)(H.L[l - 1].nnodes * B);
-  if (H.ncoarse > 1024) return MPM_ERR_BAD_ARG;
+  if (H.ncoarse > 1024) {  // an axis of 2 nodes stops the coarsening early (a thin grid)
+    c.last_error = "multigrid: the coarsest level has more than 1024 unknowns (one grid axis of very few "
+                   "cells against a long one)";
+    return MPM_ERR_BAD_ARG;
+  }
   if (cudaMalloc(&H.Ad, sizeof(real) * H.ncoarse * H.ncoarse) ||
       cudaMalloc(&H.Ai, sizeof(real) * H.ncoarse * H.ncoarse) || cudaMalloc(&H.piv, sizeof(int) * H.ncoarse))
     return MPM_ERR_NO_MEMORY;
