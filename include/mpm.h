@@ -25,7 +25,8 @@
  *   - Every pointer argument is a HOST pointer unless stated otherwise; the
  *     library copies what it needs and never keeps a caller pointer.
  *   - Return value: MPM_OK (0) or a negative MPM_ERR_* code.  After an error
- *     mpm_last_error(ctx) describes it.  A failed mpm_step leaves the state at
+ *     mpm_last_error(ctx) describes it; after a failed mpm_create or
+ *     mpm_create_batch (no context), mpm_last_error(NULL) does.  A failed mpm_step leaves the state at
  *     the last completed step.  No call throws.
  *   - A context is used by one host thread at a time.
  */
@@ -298,7 +299,9 @@ int mpm_restore(mpm_ctx *ctx, const mpm_particles_out *state, double t, int64_t 
 
 int mpm_get_stats(const mpm_ctx *ctx, mpm_stats *stats);
 
-/* Human-readable description of the last error on ctx (never NULL). */
+/* Human-readable description of the last error on ctx (never NULL).  With
+ * ctx == NULL: why the calling thread's last mpm_create / mpm_create_batch
+ * failed ("null context" if its last create succeeded or none was made). */
 const char *mpm_last_error(const mpm_ctx *ctx);
 
 /* Frees the context and all its device memory.  NULL is a no-op. */

@@ -508,43 +508,72 @@ namespace {
 // context, P / mat / permeability the points of all instances (instance-major,
 // each in its own grid's coordinates), insts the instance table and pinst the
 // instance of every point (NULL: all instance 0).
+// Why the calling thread's last mpm_create / mpm_create_batch failed (its
+// context is gone by then); empty after a successful create.
+thread_local std::string g_create_error;
+
+int create_fail(int rc, const char *why) {
+  g_create_error = why;
+  return rc;
+}
+
+// a context that failed part-way: keep its message, free it
+int create_abort(mpm_ctx *h, int rc, const char *fallback) {
+  g_create_error = h->c.last_error.empty() ? fallback : h->c.last_error;
+  delete h;
+  return rc;
+}
+
 int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material *mat,
                 const double *permeability, const mpm_options *opt, const std::vector<InstDev> &insts,
                 const int32_t *pinst, mpm_ctx **out) {
-  if (!out) return MPM_ERR_BAD_ARG;
+  constexpr int BAD = MPM_ERR_BAD_ARG;
+  g_create_error.clear();
+  if (!out) return create_fail(BAD, "out is NULL");
   *out = nullptr;
-  if (!grid || !P || !mat || !permeability || !opt) return MPM_ERR_BAD_ARG;
-  if (grid->dim != 2 && grid->dim != 3) return MPM_ERR_BAD_ARG;
-  if (!(grid->h > 0.0) || P->n <= 0 || !P->x || !P->vol || !P->lp || !mat->E || !mat->nu)
-    return MPM_ERR_BAD_ARG;
+  if (!grid || !P || !mat || !permeability || !opt)
+    return create_fail(BAD, "grid, particles, material, permeability and options must not be NULL");
+  if (grid->dim != 2 && grid->dim != 3) return create_fail(BAD, "grid.dim must be 2 or 3");
+  if (!(grid->h > 0.0)) return create_fail(BAD, "grid.h must be positive");
+  if (P->n <= 0 || !P->x || !P->vol || !P->lp || !mat->E || !mat->nu)
+    return create_fail(BAD, "need n > 0 points with x, vol, lp, E and nu");
   for (int k = 0; k < grid->dim; ++k)
-    if (grid->ncell[k] < 1) return MPM_ERR_BAD_ARG;
-  if (P->n > INT32_MAX / 2) return MPM_ERR_BAD_ARG;
-  if (opt->krylov_restart < 1 || opt->krylov_restart > 128) return MPM_ERR_BAD_ARG;
-  if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON) return MPM_ERR_BAD_ARG;
-  if (opt->schur_approx < MPM_SCHUR_AUTO || opt->schur_approx > MPM_SCHUR_FIXED_STRESS) return MPM_ERR_BAD_ARG;
-  if (opt->tau_kind < MPM_TAU_WHITE || opt->tau_kind > MPM_TAU_MONFORTE) return MPM_ERR_BAD_ARG;
-  if (opt->permeability != MPM_PERM_CONSTANT && opt->permeability != MPM_PERM_KOZENY_CARMAN) return MPM_ERR_BAD_ARG;
-  if (opt->p2g_mass != MPM_P2G_LUMPED && opt->p2g_mass != MPM_P2G_CONSISTENT) return MPM_ERR_BAD_ARG;
-  if (opt->model != MPM_MODEL_NEOHOOKE && opt->model != MPM_MODEL_HENCKY) return MPM_ERR_BAD_ARG;
-  if (opt->model == MPM_MODEL_HENCKY && opt->precision != MPM_FP64) return MPM_ERR_BAD_ARG;
-  if (opt->permeability == MPM_PERM_KOZENY_CARMAN && !(mat->phi0 > 0.0 && mat->phi0 < 1.0)) return MPM_ERR_BAD_ARG;
+    if (grid->ncell[k] < 1) return create_fail(BAD, "grid.ncell must be at least 1 on every axis");
+  if (P->n > INT32_MAX / 2) return create_fail(BAD, "more than 2^30 points");
+  if (opt->krylov_restart < 1 || opt->krylov_restart > 128)
+    return create_fail(BAD, "krylov_restart must be in 1..128");
+  if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON)
+    return create_fail(BAD, "precond_lag must be in 0..MPM_MAX_NEWTON");
+  if (opt->schur_approx < MPM_SCHUR_AUTO || opt->schur_approx > MPM_SCHUR_FIXED_STRESS)
+    return create_fail(BAD, "unknown schur_approx");
+  if (opt->tau_kind < MPM_TAU_WHITE || opt->tau_kind > MPM_TAU_MONFORTE) return create_fail(BAD, "unknown tau_kind");
+  if (opt->permeability != MPM_PERM_CONSTANT && opt->permeability != MPM_PERM_KOZENY_CARMAN)
+    return create_fail(BAD, "unknown permeability");
+  if (opt->p2g_mass != MPM_P2G_LUMPED && opt->p2g_mass != MPM_P2G_CONSISTENT)
+    return create_fail(BAD, "unknown p2g_mass");
+  if (opt->model != MPM_MODEL_NEOHOOKE && opt->model != MPM_MODEL_HENCKY) return create_fail(BAD, "unknown model");
+  if (opt->model == MPM_MODEL_HENCKY && opt->precision != MPM_FP64)
+    return create_fail(BAD, "MPM_MODEL_HENCKY needs precision MPM_FP64 (no FP32 Hencky Jacobian)");
+  if (opt->permeability == MPM_PERM_KOZENY_CARMAN && !(mat->phi0 > 0.0 && mat->phi0 < 1.0))
+    return create_fail(BAD, "MPM_PERM_KOZENY_CARMAN needs 0 < material.phi0 < 1");
   // tau_M uses the Newmark parameters: dynamic steps only (Sec. 4.3)
-  if (opt->stabilize && opt->tau_kind == MPM_TAU_MONFORTE && opt->scheme != MPM_NEWMARK) return MPM_ERR_BAD_ARG;
+  if (opt->stabilize && opt->tau_kind == MPM_TAU_MONFORTE && opt->scheme != MPM_NEWMARK)
+    return create_fail(BAD, "MPM_TAU_MONFORTE needs the Newmark scheme");
   if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
-    return MPM_ERR_BAD_ARG;
-  if (opt->precision != MPM_FP64 && opt->precision != MPM_MIXED) return MPM_ERR_BAD_ARG;
+    return create_fail(BAD, "unknown precond");
+  if (opt->precision != MPM_FP64 && opt->precision != MPM_MIXED) return create_fail(BAD, "unknown precision");
   if (P->n_surf < 0 || (P->n_surf > 0 && (!P->surf_id || !P->surf_normal || !P->surf_area)))
-    return MPM_ERR_BAD_ARG;
-  if (!(mat->mu_f > 0.0)) return MPM_ERR_BAD_ARG;
-  if (!(opt->min_volume_fraction >= 0.0)) return MPM_ERR_BAD_ARG;
+    return create_fail(BAD, "n_surf > 0 needs surf_id, surf_normal and surf_area");
+  if (!(mat->mu_f > 0.0)) return create_fail(BAD, "material.mu_f must be positive");
+  if (!(opt->min_volume_fraction >= 0.0)) return create_fail(BAD, "min_volume_fraction must be >= 0");
   // every surface id must address an entry of the load arrays
   if (P->surf_id)
     for (int64_t i = 0; i < P->n; ++i)
-      if (P->surf_id[i] < -1 || P->surf_id[i] >= P->n_surf) return MPM_ERR_BAD_ARG;
+      if (P->surf_id[i] < -1 || P->surf_id[i] >= P->n_surf)
+        return create_fail(BAD, "surf_id outside -1..n_surf-1");
 
   mpm_ctx *h = new (std::nothrow) mpm_ctx();
-  if (!h) return MPM_ERR_NO_MEMORY;
+  if (!h) return create_fail(MPM_ERR_NO_MEMORY, "out of host memory");
   Ctx &c = h->c;
   c.opt = *opt;
   {
@@ -557,10 +586,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   if (!c.st) {
     // a stream of our own (blocking, so it stays ordered with the legacy
     // default stream); needed for CUDA graph capture
-    if (cudaStreamCreate(&c.st) != cudaSuccess) {
-      delete h;
-      return MPM_ERR_CUDA;
-    }
+    if (cudaStreamCreate(&c.st) != cudaSuccess) return create_abort(h, MPM_ERR_CUDA, "cudaStreamCreate failed");
     c.own_stream = true;
   }
   c.d = grid->dim;
@@ -584,10 +610,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
     g.ncells *= g.nc[k];
   }
   g.h = grid->h;
-  if (g.nnodes > INT32_MAX / 16) {
-    delete h;
-    return MPM_ERR_BAD_ARG;
-  }
+  if (g.nnodes > INT32_MAX / 16) return create_abort(h, MPM_ERR_BAD_ARG, "grid has more than 2^27 nodes");
   StepP &s = c.s;
   s.beta = opt->beta;
   s.gamma = opt->gamma;
@@ -700,8 +723,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
     rc = MPM_ERR_NO_MEMORY;
   if (rc) {
     free_all(c);
-    delete h;
-    return rc;
+    return create_abort(h, rc, "device or pinned host memory allocation failed");
   }
   cudaMemcpyAsync(c.inst, c.inst_h.data(), sizeof(InstDev) * c.ninst, cudaMemcpyHostToDevice, c.st);
   {  // instance of every node (node boxes of the instances; -1 between them)
@@ -738,8 +760,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   rc = dalloc(c, &tmp, tcount);
   if (rc) {
     free_all(c);
-    delete h;
-    return rc;
+    return create_abort(h, rc, "device memory allocation failed (point staging)");
   }
   double *dx = tmp, *dvol = dx + n * d, *dlp = dvol + n, *dp0 = dlp + n * d, *dv0 = dp0 + n,
          *dE = dv0 + n * d, *dnu = dE + n, *dk = dnu + n, *dsn = dk + n, *dsa = dsn + n * d;
@@ -780,8 +801,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   if (e != cudaSuccess) {
     rc = check_cuda(c, e, "create");
     free_all(c);
-    delete h;
-    return rc;
+    return create_abort(h, rc, "CUDA error in create");
   }
   *out = h;
   return MPM_OK;
@@ -823,9 +843,10 @@ void mpm_default_options(mpm_options *o) {
 
 int mpm_create(const mpm_grid *grid, const mpm_particles *P, const mpm_material *mat,
                const double *permeability, const mpm_options *opt, mpm_ctx **out) {
-  if (!out) return MPM_ERR_BAD_ARG;
+  g_create_error.clear();
+  if (!out) return create_fail(MPM_ERR_BAD_ARG, "out is NULL");
   *out = nullptr;
-  if (!grid) return MPM_ERR_BAD_ARG;
+  if (!grid) return create_fail(MPM_ERR_BAD_ARG, "grid is NULL");
   InstDev one{};
   for (int k = 0; k < 3; ++k) {
     const bool used = k < grid->dim;
@@ -887,13 +908,16 @@ int mpm_batch_pack(int32_t count, const mpm_grid *grids, int32_t *offsets, int32
 int mpm_create_batch(int32_t count, const mpm_grid *grids, const mpm_particles *parts,
                      const mpm_material *mats, const double *const *permeability, const mpm_options *opt,
                      mpm_ctx **out) {
-  if (!out) return MPM_ERR_BAD_ARG;
+  g_create_error.clear();
+  if (!out) return create_fail(MPM_ERR_BAD_ARG, "out is NULL");
   *out = nullptr;
-  if (count < 1 || !grids || !parts || !mats || !permeability || !opt) return MPM_ERR_BAD_ARG;
+  if (count < 1 || !grids || !parts || !mats || !permeability || !opt)
+    return create_fail(MPM_ERR_BAD_ARG, "need count >= 1 and non-NULL grids, particles, materials, "
+                                        "permeabilities and options");
   std::vector<int32_t> offs(3 * (size_t)count);
   mpm_grid big{};
   int rc = mpm_batch_pack(count, grids, offs.data(), big.ncell);
-  if (rc) return rc;
+  if (rc) return create_fail(rc, "the grids cannot be packed (mixed dim or h, or an axis out of range)");
   const int d = grids[0].dim;
   big.dim = d;
   big.h = grids[0].h;
@@ -903,7 +927,7 @@ int mpm_create_batch(int32_t count, const mpm_grid *grids, const mpm_particles *
     const mpm_material &m = mats[i];
     if (m.rho_s != m0.rho_s || m.rho_f != m0.rho_f || m.phi0 != m0.phi0 || m.mu_f != m0.mu_f ||
         m.alpha_vis != m0.alpha_vis || m.g[0] != m0.g[0] || m.g[1] != m0.g[1] || m.g[2] != m0.g[2])
-      return MPM_ERR_BAD_ARG;
+      return create_fail(MPM_ERR_BAD_ARG, "the instances' material constants differ (only E, nu, k may)");
   }
   int64_t n = 0;
   int32_t nsurf = 0;
@@ -911,19 +935,20 @@ int mpm_create_batch(int32_t count, const mpm_grid *grids, const mpm_particles *
   for (int i = 0; i < count; ++i) {
     const mpm_particles &P = parts[i];
     if (P.n <= 0 || !P.x || !P.vol || !P.lp || !mats[i].E || !mats[i].nu || !permeability[i])
-      return MPM_ERR_BAD_ARG;
+      return create_fail(MPM_ERR_BAD_ARG, "an instance needs n > 0 points with x, vol, lp, E, nu and k");
     if (P.n_surf < 0 || (P.n_surf > 0 && (!P.surf_id || !P.surf_normal || !P.surf_area)))
-      return MPM_ERR_BAD_ARG;
+      return create_fail(MPM_ERR_BAD_ARG, "n_surf > 0 needs surf_id, surf_normal and surf_area");
     if (P.surf_id)
       for (int64_t j = 0; j < P.n; ++j)
-        if (P.surf_id[j] < -1 || P.surf_id[j] >= P.n_surf) return MPM_ERR_BAD_ARG;
+        if (P.surf_id[j] < -1 || P.surf_id[j] >= P.n_surf)
+          return create_fail(MPM_ERR_BAD_ARG, "surf_id outside -1..n_surf-1");
     n += P.n;
     nsurf += P.n_surf;
     any_p0 |= P.p0 != nullptr;
     any_v0 |= P.v0 != nullptr;
     any_surf |= P.n_surf > 0;
   }
-  if (n > INT32_MAX / 2) return MPM_ERR_BAD_ARG;
+  if (n > INT32_MAX / 2) return create_fail(MPM_ERR_BAD_ARG, "more than 2^30 points");
   std::vector<double> x(n * d), vol(n), lp(n * d), p0(any_p0 ? n : 0), v0(any_v0 ? n * d : 0), E(n), nu(n), k(n),
       sn(any_surf ? n * d : 0), sa(any_surf ? n : 0);
   std::vector<int32_t> sid(n, -1), pinst(n);
@@ -1096,7 +1121,7 @@ int mpm_get_stats(const mpm_ctx *h, mpm_stats *s) {
 }
 
 const char *mpm_last_error(const mpm_ctx *h) {
-  if (!h) return "null context";
+  if (!h) return g_create_error.empty() ? "null context" : g_create_error.c_str();
   return h->c.last_error.c_str();
 }
 

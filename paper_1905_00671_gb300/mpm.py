@@ -242,7 +242,7 @@ class Simulation:
         ctx = C.c_void_p()
         rc = lib.mpm_create(C.byref(g), C.byref(P), C.byref(M), _p(K["k"]), C.byref(o), C.byref(ctx))
         if rc != MPM_OK:
-            raise MPMError(rc, "mpm_create failed")
+            raise MPMError(rc, "mpm_create: " + lib.mpm_last_error(None).decode())
         self.ctx = ctx
         self.t = 0.0
         self._bcs_sent = False
@@ -410,7 +410,7 @@ class Batch:
         rc = lib.mpm_create_batch(m, grids, parts, mats, C.cast(perms, C.c_void_p), C.byref(o),
                                   C.byref(ctx))
         if rc != MPM_OK:
-            raise MPMError(rc, "mpm_create_batch failed")
+            raise MPMError(rc, "mpm_create_batch: " + lib.mpm_last_error(None).decode())
         self.ctx = ctx
         self.t = 0.0
         self._bcs_sent = False

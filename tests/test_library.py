@@ -62,3 +62,50 @@ def test_product_path_never_imports_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", src).lower() or f == "inputs.py", f
+
+
+@pytest.mark.parametrize("opts,model,why", [
+    (dict(krylov_restart=200), None, "krylov_restart must be in 1..128"),
+    (dict(precision=1), 1, "needs precision MPM_FP64"),
+    (dict(tau_kind=2), None, "MPM_TAU_MONFORTE needs the Newmark scheme"),
+    (dict(min_volume_fraction=-1.0), None, "min_volume_fraction"),
+])
+def test_rejected_create_names_its_reason_without_gpu(lib, opts, model, why):
+    """Argument checks run on the host before any device call: mpm_create
+    returns MPM_ERR_BAD_ARG and mpm_last_error(NULL) says why."""
+    from dataclasses import replace
+
+    from paper_1905_00671_gb300 import inputs as I
+    from paper_1905_00671_gb300 import mpm
+
+    w = I.terzaghi_column(ncell_y=4, ncell_x=2)          # quasi-static
+    if model is not None:
+        w = replace(w, model=model)
+    with pytest.raises(mpm.MPMError, match=why) as e:
+        mpm.Simulation(w, **opts)
+    assert e.value.code == -1                            # MPM_ERR_BAD_ARG
+
+
+def test_rejected_batch_create_names_its_reason_without_gpu(lib):
+    from dataclasses import replace
+
+    from paper_1905_00671_gb300 import inputs as I
+    from paper_1905_00671_gb300 import mpm
+
+    a = I.terzaghi_column(ncell_y=4, ncell_x=2)
+    b = replace(I.terzaghi_column(ncell_y=6, ncell_x=2), rho_f=900.0)
+    with pytest.raises(mpm.MPMError, match="material constants differ"):
+        mpm.Batch([a, b])
+
+
+def test_last_error_without_a_context_on_a_fresh_thread(lib):
+    import threading
+
+    from paper_1905_00671_gb300 import mpm
+
+    m = mpm.load()
+    out = []
+    t = threading.Thread(target=lambda: out.append(m.mpm_last_error(None)))
+    t.start()
+    t.join()
+    assert out == [b"null context"]
