@@ -1017,7 +1017,10 @@ int mpm_step_batch(mpm_ctx *h, double dt, const mpm_loads *loads, const mpm_bcs 
   if (!h) return MPM_ERR_BAD_ARG;
   Ctx &c = h->c;
   const int d = c.d, ni = c.ninst;
-  if ((int)c.inst_n.size() != ni) return MPM_ERR_BAD_ARG;  // not a batched context
+  if ((int)c.inst_n.size() != ni) {
+    c.last_error = "mpm_step_batch needs a context made by mpm_create_batch";
+    return MPM_ERR_BAD_ARG;
+  }
   mpm_loads L{};
   if (loads) {
     int64_t sb = 0;
@@ -1089,8 +1092,12 @@ int mpm_read(const mpm_ctx *hc, mpm_particles_out *o) {
 }
 
 int mpm_restore(mpm_ctx *h, const mpm_particles_out *st, double t, int64_t steps) {
-  if (!h || !st || !(t >= 0.0) || steps < 0) return MPM_ERR_BAD_ARG;
+  if (!h) return MPM_ERR_BAD_ARG;
   Ctx &c = h->c;
+  if (!st || !(t >= 0.0) || steps < 0) {
+    c.last_error = "mpm_restore needs a state, t >= 0 and steps >= 0";
+    return MPM_ERR_BAD_ARG;
+  }
   const int64_t n = c.n;
   const int d = c.d;
   struct Item {
@@ -1152,7 +1159,10 @@ int mpm_debug_prepare(mpm_ctx *h, double dt, const mpm_loads *loads, const mpm_b
 int64_t mpm_debug_pattern(mpm_ctx *h, int64_t *row_ptr, int32_t *col_idx, int64_t cap) {
   if (!h || !row_ptr) return MPM_ERR_BAD_ARG;
   Ctx &c = h->c;
-  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  if (!c.prepared) {
+    c.last_error = "no step prepared: call mpm_debug_prepare first";
+    return MPM_ERR_BAD_ARG;
+  }
   const int64_t nn = c.g.nnodes;
   int32_t *tmp = new (std::nothrow) int32_t[nn + 1];
   if (!tmp) return MPM_ERR_NO_MEMORY;
@@ -1162,7 +1172,10 @@ int64_t mpm_debug_pattern(mpm_ctx *h, int64_t *row_ptr, int32_t *col_idx, int64_
   delete[] tmp;
   if (e != cudaSuccess) return check_cuda(c, e, "debug_pattern");
   if (col_idx) {
-    if (cap < c.nnzb) return MPM_ERR_BAD_ARG;
+    if (cap < c.nnzb) {
+      c.last_error = "col_idx holds fewer entries than the pattern's block count";
+      return MPM_ERR_BAD_ARG;
+    }
     cudaMemcpyAsync(col_idx, c.col, sizeof(int32_t) * c.nnzb, cudaMemcpyDeviceToHost, c.st);
     e = cudaStreamSynchronize(c.st);
     if (e != cudaSuccess) return check_cuda(c, e, "debug_pattern");
@@ -1173,7 +1186,10 @@ int64_t mpm_debug_pattern(mpm_ctx *h, int64_t *row_ptr, int32_t *col_idx, int64_
 int mpm_debug_nodal(mpm_ctx *h, double *M, double *Pn, double *phi) {
   if (!h) return MPM_ERR_BAD_ARG;
   Ctx &c = h->c;
-  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  if (!c.prepared) {
+    c.last_error = "no step prepared: call mpm_debug_prepare first";
+    return MPM_ERR_BAD_ARG;
+  }
   if (M) cudaMemcpyAsync(M, c.M, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
   if (Pn) cudaMemcpyAsync(Pn, c.Pn, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
   if (phi) cudaMemcpyAsync(phi, c.phi, sizeof(double) * c.g.nnodes, cudaMemcpyDeviceToHost, c.st);
@@ -1183,7 +1199,10 @@ int mpm_debug_nodal(mpm_ctx *h, double *M, double *Pn, double *phi) {
 int mpm_debug_eval(mpm_ctx *h, const double *X, double *R, double *Jv, int32_t apply_bc) {
   if (!h || !X || !R) return MPM_ERR_BAD_ARG;
   Ctx &c = h->c;
-  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  if (!c.prepared) {
+    c.last_error = "no step prepared: call mpm_debug_prepare first";
+    return MPM_ERR_BAD_ARG;
+  }
   const int64_t N = c.N();
   cudaMemcpyAsync(c.dX, X, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
   run_point_eval(c, c.dX);
@@ -1203,7 +1222,10 @@ int mpm_debug_eval(mpm_ctx *h, const double *X, double *R, double *Jv, int32_t a
 int mpm_debug_precond(mpm_ctx *h, const double *X, const double *v, double *z) {
   if (!h || !X || !v || !z) return MPM_ERR_BAD_ARG;
   Ctx &c = h->c;
-  if (!c.prepared) return MPM_ERR_BAD_ARG;
+  if (!c.prepared) {
+    c.last_error = "no step prepared: call mpm_debug_prepare first";
+    return MPM_ERR_BAD_ARG;
+  }
   const int64_t N = c.N();
   cudaMemcpyAsync(c.X, X, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
   run_point_eval(c, c.X);
