@@ -128,3 +128,28 @@ def test_self_weight_consolidation_dissipates():
     exc, settle = np.array(exc), np.array(settle)
     assert np.all(np.diff(exc[1:]) < 0) and exc[-1] < 0.5 * exc[0]
     assert np.all(np.diff(settle) > 0)
+
+
+@pytest.mark.parametrize("model", [I.MODEL_NEOHOOKE, I.MODEL_HENCKY])
+def test_self_weight_paper_setup_consolidates(model):
+    """The paper's own set-up and grid (Sec. 5.3: K = 15 kPa, Kozeny-Carman,
+    h = 0.125 m with 25 points per cell, dt = 0.1 s x 1.2), ten steps: Newton
+    converges in every step; at t = 0.1 s the pore fluid carries the submerged
+    weight (rho - rho_f) g (H - y) at mid-depth (nearly undrained); then the
+    excess pressure dissipates and the top settles, step after step."""
+    w = replace(I.self_weight_consolidation(), model=model)
+    assert w.ncell[:2] == (16, 16) and w.n == 6400
+    o = O.Oracle(w, newton_rtol=1e-8, newton_max=25)
+    mid = (np.abs(w.x[:, 0] - 1.0) < 0.07) & (np.abs(w.x[:, 1] - 1.0) < 0.07)
+    top = w.x[:, 1] > H - 0.1
+    submerged = (RHO - 1000.0) * 9.81 * (H - w.x[mid, 1])
+    exc, settle = [], []
+    for dt in w.step_sizes(10):
+        info = o.step(dt)
+        assert info.newton_iters <= 6
+        st = o.state()
+        exc.append((st["p"][mid] - 1000.0 * 9.81 * (H - w.x[mid, 1])).mean())
+        settle.append(-st["u"][top, 1].mean())
+    assert abs(exc[0] / submerged.mean() - 1.0) < 0.05
+    assert exc[-1] < 0.85 * exc[0]
+    assert np.all(np.diff(settle) > 0) and settle[0] > 0
