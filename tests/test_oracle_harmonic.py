@@ -106,18 +106,41 @@ def _pressure_below_footing(w, steps=20):
     return d2.mean() / np.abs(sub).max(), np.abs(sub).max(), o.t
 
 
+_RUNS = {}
+
+
+def _run(variant):
+    """_pressure_below_footing of the paper's set-up or of one variant of it,
+    computed once per test session."""
+    from dataclasses import replace
+
+    if variant not in _RUNS:
+        w = I.harmonic_footing()
+        w = {"tau_W": w, "standard": replace(w, shape=I.ORIG, stabilize=False),
+             "10 tau_W": replace(w, tau_scale=10.0), "tau_M": replace(w, tau_kind=I.TAU_MONFORTE)}[variant]
+        _RUNS[variant] = _pressure_below_footing(w)
+    return _RUNS[variant]
+
+
 def test_harmonic_footing_stabilization_removes_pressure_oscillations():
     """Sec. 5.2 at t = 0.02 s (the paper's first pressure contours): standard
     (original, unstabilized) MPM gives an oscillating pressure below the
     footing with spurious peaks far above the applied load, while the
     stabilized GIMP solution is smooth and stays below the load
     w(0.02) = 3 - 3 cos 2 = 4.25 MPa."""
-    from dataclasses import replace
-
-    w = I.harmonic_footing()
-    rough_s, peak_s, t = _pressure_below_footing(w)
-    rough_u, peak_u, _ = _pressure_below_footing(replace(w, shape=I.ORIG, stabilize=False))
+    rough_s, peak_s, t = _run("tau_W")
+    rough_u, peak_u, _ = _run("standard")
     load = 3e6 * (1.0 - np.cos(100.0 * t))
     assert abs(t - 0.02) < 1e-12
     assert rough_u > 5.0 * rough_s
     assert peak_s < load < peak_u
+
+
+def test_harmonic_footing_stabilization_parameter():
+    """Sec. 5.2: tau_M and tau_W give nearly the same pressures, and too large
+    a tau (10 tau_W) over-smooths and lowers the peak pressure."""
+    _, peak_w, _ = _run("tau_W")
+    _, peak_m, _ = _run("tau_M")
+    _, peak_10, _ = _run("10 tau_W")
+    assert abs(peak_m / peak_w - 1.0) < 0.03
+    assert peak_10 < 0.85 * peak_w
