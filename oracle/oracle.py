@@ -25,7 +25,6 @@ import ctypes as C
 import os
 import subprocess
 from dataclasses import dataclass
-from typing import Optional
 
 import numpy as np
 import scipy.sparse as sps

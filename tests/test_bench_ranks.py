@@ -2,11 +2,9 @@
 gloo on the CPU): every rank steps its own replica, and the whole job is timed
 as its slowest rank, so the reported time is the maximum over the ranks and
 the throughput is all ranks' work over that time."""
-import os
 import socket
 
 import pytest
-import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 

@@ -1,6 +1,5 @@
 """The oracle still reproduces its committed Terzaghi trajectory (guards the
 oracle's arithmetic against unintended change)."""
-import os
 
 import numpy as np
 
