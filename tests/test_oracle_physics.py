@@ -314,3 +314,37 @@ def test_newton_converges_quadratically_on_terzaghi():
     h = info.res_hist
     assert info.newton_iters <= 4
     assert h[2] / h[0] < (h[1] / h[0]) ** 1.5
+
+
+def test_p2g_conserves_momentum_and_maps_constants_exactly():
+    """Lumped Stage-1 mapping (Eq. map-from-particles-to-nodes): sum_i M_i v_i =
+    sum_p m_p v_p, and a field constant over the points is mapped to that
+    constant at every node with mass."""
+    w = I.small_footing(seed=2)
+    o = O.Oracle(w)
+    prep = o.prepare(w.dt)
+    first, count, S, m = prep["first"], prep["count"], prep["S"], prep["m"]
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal((w.n, 2))
+    M, out = O.p2g(o.g, first, count, S, m, np.concatenate([v, np.full((w.n, 1), 7.25)], axis=1))
+    np.testing.assert_allclose((M[:, None] * out[:, :2]).sum(axis=0), (m[:, None] * v).sum(axis=0),
+                               rtol=1e-12)
+    has = M > 0
+    np.testing.assert_allclose(out[has, 2], 7.25, rtol=1e-13)
+
+
+def test_mixture_mass_keeps_the_solid_mass():
+    """Reading R11 (incompressible constituents, phi = 1 - (1 - phi0) / J): after
+    any volume change the solid mass of a point is still (1 - phi0) rho_s V0 and
+    the fluid mass is rho_f (J - 1 + phi0) V0."""
+    w = I.small_footing(seed=2)
+    o = O.Oracle(w)
+    rng = np.random.default_rng(1)
+    Fs = np.eye(2) + 0.1 * rng.standard_normal((w.n, 2, 2))
+    J = np.linalg.det(Fs)
+    assert J.min() > 0.5
+    V0 = o.V.copy()
+    o.F = Fs.reshape(w.n, 4).copy()
+    o.V = J * V0
+    m = o.mixture_mass()
+    np.testing.assert_allclose(m, (1 - w.phi0) * w.rho_s * V0 + w.rho_f * (J - 1 + w.phi0) * V0, rtol=1e-13)
