@@ -59,3 +59,34 @@ def test_g2p_affine_update_3d():
     K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
     R = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
     _check_affine_update(w, R - np.eye(3))
+
+
+def test_g2p_newmark_from_rest_with_affine_fields():
+    """Newmark step from rest (v_n = a_n = 0, p_n = 0): for an affine increment
+    the nodal acceleration a = dU / (beta dt^2) is affine, so every point gets
+    a_p = grad x_p / (beta dt^2) (PIC) and v_p = gamma dt a_p (FLIP,
+    v = v_n + dt sum S ((1 - gamma) a_n + gamma a)); a linear nodal pressure
+    gives p_p at the point (PIC) and its Newmark rate gamma / (beta dt) p_p."""
+    from dataclasses import replace
+
+    w = I.terzaghi_column(ncell_y=6, ncell_x=3, h=0.25, shape=I.GIMP)
+    w = replace(w, dynamic=True, dt=2e-3, v0=np.zeros((w.n, 2)))
+    o = O.Oracle(w)
+    prep = o.prepare(w.dt)
+    assert np.all(prep["active"])
+    grad = np.array([[0.002, -0.001], [0.0015, 0.003]])
+    cp = np.array([3e3, -5e3])
+    nc = I.node_coords(2, w.ncell) * w.h
+    X = np.zeros((o.nn, 3))
+    X[:, :2] = nc @ grad.T
+    X[:, 2] = nc @ cp
+    x0 = o.x.copy()
+    o.update(prep, X.reshape(-1))
+    b, gm, dt = w.beta, w.gamma, w.dt
+    a = (x0 @ grad.T) / (b * dt * dt)
+    scale = np.abs(a).max()
+    np.testing.assert_allclose(o.a, a, rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(o.v, gm * dt * a, rtol=0, atol=1e-11 * gm * dt * scale)
+    p = x0 @ cp
+    np.testing.assert_allclose(o.p, p, rtol=0, atol=1e-12 * np.abs(p).max())
+    np.testing.assert_allclose(o.pd, gm / (b * dt) * p, rtol=0, atol=1e-11 * gm / (b * dt) * np.abs(p).max())
