@@ -153,3 +153,21 @@ def test_self_weight_paper_setup_consolidates(model):
     assert abs(exc[0] / submerged.mean() - 1.0) < 0.05
     assert exc[-1] < 0.85 * exc[0]
     assert np.all(np.diff(settle) > 0) and settle[0] > 0
+
+
+def test_self_weight_first_step_on_both_paper_grids():
+    """Sec. 5.3 names two discretisations: h = 0.125 m with 25 points per cell
+    (6,400 points) and h = 0.0625 m with 16 (16,384).  After the first 0.1 s
+    the mid-depth excess pressure is within 2% of the submerged weight on both,
+    and closer on the finer grid."""
+    gaps = []
+    for ncell, h, ppc, n in (((16, 16), 0.125, 5, 6400), ((32, 32), 0.0625, 4, 16384)):
+        w = replace(I.self_weight_consolidation(ncell=ncell, h=h, ppc_axis=ppc), model=I.MODEL_HENCKY)
+        assert w.n == n
+        o = O.Oracle(w, newton_rtol=1e-8, newton_max=25)
+        info = o.step(w.dt)
+        assert info.newton_iters <= 6
+        mid = (np.abs(w.x[:, 0] - 1.0) < 0.07) & (np.abs(w.x[:, 1] - 1.0) < 0.07)
+        exc = (o.state()["p"][mid] - 1000.0 * 9.81 * (H - w.x[mid, 1])).mean()
+        gaps.append(abs(exc / ((RHO - 1000.0) * 9.81 * (H - w.x[mid, 1])).mean() - 1.0))
+    assert max(gaps) < 0.02 and gaps[1] < gaps[0]
