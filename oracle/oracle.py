@@ -200,6 +200,23 @@ def pattern(g, first, count):
     return row_ptr, col[:nnz]
 
 
+def point_basis(g, p, first, count, S, dS, S0, active=None):
+    """Basis of point p as the residual and the update use it (reading R7):
+    node ids of its support box, S, the t_n gradient (nodes x d) and S0, with
+    inactive nodes removed and the rest renormalised."""
+    d = g.dim
+    cap = MAXS ** d
+    node = np.zeros(cap, np.int64)
+    Sv, S0v = np.zeros(cap), np.zeros(cap)
+    Gv = np.zeros(cap * d)
+    act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+    ns = lib().orc_point_basis(C.byref(g), C.c_int64(p), _p(first), _p(count), _p(S), _p(dS),
+                               _p(S0), _p(act), _p(node), _p(Sv), _p(Gv), _p(S0v))
+    if ns < 0:
+        _check(ns, "point_basis")
+    return node[:ns].copy(), Sv[:ns].copy(), Gv[:ns * d].reshape(ns, d).copy(), S0v[:ns].copy()
+
+
 def p2g(g, first, count, S, m, fld):
     n = first.shape[0]
     nn = lib().orc_nnodes(C.byref(g))

@@ -251,6 +251,30 @@ static void build_support_active(const orc_grid *g, int64_t p, const int32_t *fi
   }
 }
 
+/* The basis of one point as orc_eval and orc_g2p use it: the nodes of its
+ * support box with S, S0 and the t_n gradient, inactive nodes removed and the
+ * rest renormalised (reading R7).  Exposed for the pins of that rule; returns
+ * the number of box nodes written (at most MAXS^d) or ORC_ERR_BAD_ARG. */
+int orc_point_basis(const orc_grid *g, int64_t p, const int32_t *first, const int32_t *count,
+                    const double *S, const double *dS, const double *S0, const uint8_t *active,
+                    int64_t *node, double *Sv, double *Gv, double *S0v) {
+  if (!g || p < 0 || !first || !count || !S || !dS || !S0 || !node || !Sv || !Gv || !S0v)
+    return ORC_ERR_BAD_ARG;
+  const int d = g->dim;
+  support *sp = (support *)malloc(sizeof(support));
+  if (!sp) return ORC_ERR_BAD_ARG;
+  build_support_active(g, p, first, count, S, dS, S0, active, sp);
+  const int ns = sp->ns;
+  for (int q = 0; q < ns; ++q) {
+    node[q] = sp->node[q];
+    Sv[q] = sp->S[q];
+    S0v[q] = sp->S0[q];
+    for (int k = 0; k < d; ++k) Gv[q * d + k] = sp->Gn[q][k];
+  }
+  free(sp);
+  return ns;
+}
+
 /* ------------------------------------------------------------------------
  * Sparsity: node b couples with node a iff some material point has both in
  * its support; every node couples with itself.  Rows over all grid nodes,

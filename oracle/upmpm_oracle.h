@@ -98,6 +98,13 @@ int orc_consistent_mass(const orc_grid *g, int64_t n, const int32_t *first, cons
                         const double *S, const double *m, const int64_t *row_ptr, const int32_t *col_idx,
                         double *mc);
 
+/* Basis of point p over its support box (node ids, S, t_n gradient d per
+ * node, S0), with the inactive nodes removed and the rest renormalised as in
+ * orc_eval (active may be NULL).  Returns the node count (<= 4^d). */
+int orc_point_basis(const orc_grid *g, int64_t p, const int32_t *first, const int32_t *count,
+                    const double *S, const double *dS, const double *S0, const uint8_t *active,
+                    int64_t *node, double *Sv, double *Gv, double *S0v);
+
 /* active (nnodes, may be NULL): nodes with active == 0 are removed from the
  * bases of the points whose support box holds them, which are renormalised. */
 int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
