@@ -3,11 +3,16 @@
 
 One "step" is one load step of the whole hot path (bin + sort, shape
 functions, Stage-1 P2G, sparsity, Newton with residual / Jacobian assembly and
-FGMRES to the paper's 1e-8 residual test, G2P + convection) on the 2D dynamic
-strip footing: 200 x 100 cells at h = 0.1 m (+2 empty rows), 80,000 points,
-GIMP, Newmark, k = 1e-14 m^2, seeded lognormal stiffness, strip load ramped to
-200 kPa over 0.1 s, dt = 1e-3 s.  Inputs are synthetic (seeded), resident in
-HBM for `value`; `e2e` goes through the C-ABI with host buffers.
+FGMRES to the paper's 1e-8 residual test, G2P + convection).  The default
+workload is the largest single-GPU one, the 3D slope: a 12.8 x 12.8 x 6.4 m box
+of 128 x 128 x 64 cells at h = 0.1 m, the cells below a 30 degree ground
+surface filled with 2 x 2 x 2 points (4,208,640), GIMP, quasi-static implicit
+Euler, dt = 10 s, gravity from t = 0 with a hydrostatic pore pressure below a
+water table at mid-height, k = 1e-12 m^2.  `value` is FP64; `mixed` is the
+same steps in the mixed-precision mode with its error against the FP64 run.
+Inputs are synthetic (seeded), resident in HBM for `value`; `e2e` goes
+through the C-ABI with host buffers.  --workload footing | block3d |
+terzaghi | harmonic | batch select the other configurations.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -57,7 +62,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="footing")
+    ap.add_argument("--workload", default="slope")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
@@ -88,9 +93,16 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def workload_label(w):
+    if w.name.startswith("slope-") and not w.name.startswith("slope-piece"):
+        return f"{w.name}: 3D slope under gravity (30 degrees, water table at mid-height)"
+    if w.name.startswith("footing-"):
+        return f"{w.name}: 2D plane-strain dynamic strip footing"
+    return w.name
+
+
 def workload_config(w):
-    return {"workload": f"{w.name}: 2D plane-strain dynamic strip footing" if w.dim == 2 and w.dynamic
-            else w.name,
+    return {"workload": workload_label(w),
             "grid_cells": list(w.ncell[:w.dim]), "h_m": w.h, "points": w.n,
             "shape": "GIMP" if w.shape == 1 else "original MPM",
             "scheme": "Newmark" if w.dynamic else "quasi-static implicit Euler",
@@ -452,58 +464,88 @@ def run_ours(args, rank, world, local_rank):
 
 
 # --------------------------------------------------------------- oracle
-def oracle_sample_step(w, dt):
-    from oracle import oracle as O
-
-    o = O.Oracle(w, newton_rtol=1e-8)
-    t0 = time.perf_counter()
-    info = o.step(dt)
-    return time.perf_counter() - t0, info.newton_iters
+# largest workload the oracle steps whole in bounded time (a direct sparse solve)
+CPU_BASELINE_MAX_POINTS = 100_000
+# the slope piece: 24 x 16 x 12 cells at the same h, the slope geometry (toe,
+# crest, water table) scaled by 24/128 so that the 30 degree face is kept
+SLOPE_PIECE_CELLS = (24, 16, 12)
 
 
-def reference_sample():
-    """A bounded piece of the footing workload for the oracle: same h, material,
-    loading and time step, 140 x 70 cells of body (39,200 points)."""
+def oracle_piece(w):
+    """(workload, description) of the bounded piece of workload `w` that the
+    oracle legs time: the workload itself when it is small, else a piece of
+    the same kind at the same h, material, loading and time step."""
     from paper_1905_00671_gb300 import inputs as I
 
-    return I.strip_footing(body=(140, 70), seed=2)
+    if w.name.startswith("slope-"):
+        s = 128.0 / SLOPE_PIECE_CELLS[0]
+        nc = SLOPE_PIECE_CELLS
+        p = I.slope_3d(ncell=nc, z_toe=1.2 / s, z_crest=5.2 / s, x_toe=2.9 / s,
+                       name="slope-piece-{}x{}x{}".format(*nc))
+        return p, (f"a {nc[0]}x{nc[1]}x{nc[2]}-cell, {p.n}-point piece of the slope (same h, "
+                   "material, gravity, dt and 30 degree face; toe, crest and water table scaled "
+                   f"by {nc[0]}/128)")
+    if w.name.startswith("block-") and w.n > CPU_BASELINE_MAX_POINTS:
+        p = I.consolidation_block(body=(16, 16, 8), name="block-piece-16x16x8")
+        return p, f"a 16x16x8-cell, {p.n}-point piece of the 3D block (same h, material, load, dt)"
+    if w.name.startswith("footing-") and w.n > 40_000:
+        p = I.strip_footing(body=(140, 70), seed=2)
+        return p, (f"a 140x70-cell, {p.n}-point piece of the footing (same h, material, load, dt)")
+    return w, f"the full {w.n}-point {w.name}"
 
 
-# largest workload the oracle steps in bounded time (a direct sparse solve)
-CPU_BASELINE_MAX_POINTS = 100_000
+def run_cpu_baseline(w, min_seconds=10.0, max_steps=3):
+    """The oracle as it stands on one host core: consecutive load steps from
+    t = 0 of the full workload (when small) or of its piece, until about
+    min_seconds of CPU work (at most max_steps steps)."""
+    from oracle import oracle as O
 
-
-def run_cpu_baseline(w):
-    if w.n > CPU_BASELINE_MAX_POINTS:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"not run: one oracle step of the {w.n}-point {w.name} needs a direct "
-                          f"sparse solve of {w.nnodes * (w.dim + 1)} unknowns"}
-    sec, its = oracle_sample_step(w, w.dt)
-    return {"value": w.n / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one load step (t = 0 -> dt, {its} Newton iterations) of the full "
-                      f"{w.n}-point {w.name}, C loops + SuperLU, single thread",
+    if w.n <= CPU_BASELINE_MAX_POINTS:
+        piece, desc = w, f"the full {w.n}-point {w.name}"
+        max_steps = 1
+    else:
+        piece, desc = oracle_piece(w)
+    o = O.Oracle(piece, newton_rtol=1e-8)
+    sec, steps, its = 0.0, 0, []
+    while steps < max_steps and (steps == 0 or sec < min_seconds):
+        t0 = time.perf_counter()
+        info = o.step()
+        sec += time.perf_counter() - t0
+        steps += 1
+        its.append(info.newton_iters)
+    return {"value": piece.n * steps / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} oracle load step(s) from t = 0 ({sum(its)} Newton iterations) of "
+                      f"{desc}, C loops + SuperLU, single thread",
             "seconds": round(sec, 2)}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (this project's reference is a paper; its
+    CPU restatement is the oracle) on one host core, each step one oracle load
+    step of the workload's bounded piece, stepped on from t = 0; the warm-up
+    steps are stepped but not timed."""
     if rank != 0:
         return None
+    from oracle import oracle as O
+
     w = make_workload(args.workload)
-    s = reference_sample()
+    piece, desc = oracle_piece(w)
+    o = O.Oracle(piece, newton_rtol=1e-8)
     secs = []
     for i in range(args.warmup + args.steps):
-        sec, _ = oracle_sample_step(s, s.dt)
+        t0 = time.perf_counter()
+        o.step()
         if i >= args.warmup:
-            secs.append(sec)
+            secs.append(time.perf_counter() - t0)
     total = sum(secs)
-    value = s.n * args.steps / total
-    sample = (f"each step: one oracle load step of a {s.ncell[0]}x{s.ncell[1] - 2}-cell, "
-              f"{s.n}-point piece of the footing (same h, material, load, dt)")
+    value = piece.n * args.steps / total
+    sample = f"each step: one oracle load step of {desc}, continuing from t = 0"
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": dict(workload_config(w), parallelism="cpu", l2="host CPU: not applicable"),
+            "config": dict(workload_config(piece), parallelism="cpu", l2="host CPU: not applicable",
+                           sample_of=workload_label(w)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -549,6 +591,8 @@ def run_batch(args, rank, world, local_rank):
         e1 = torch.cuda.Event(enable_timing=True)
         ms = 0.0
         newton = []
+        clocks = ClockSampler(local_rank)
+        clocks.start()
         for _ in range(args.steps):
             flush.zero_()
             e0.record(stream)
@@ -557,13 +601,14 @@ def run_batch(args, rank, world, local_rank):
             e1.record(stream)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
+        clk = clocks.stop()
         out = [b.read(("u", "p")) for b in bs]
         for b in bs:
             b.close()
-        return max_over_ranks(ms, world, "cuda"), newton, out
+        return max_over_ranks(ms, world, "cuda"), newton, out, clk
 
-    ms_mixed, newton_mixed, res_mixed = timed(mpm.MPM_MIXED)
-    ms_fp64, newton_fp64, res_fp64 = timed(mpm.MPM_FP64)
+    ms_mixed, newton_mixed, res_mixed, clk_mixed = timed(mpm.MPM_MIXED)
+    ms_fp64, newton_fp64, res_fp64, clk_fp64 = timed(mpm.MPM_FP64)
     # one at a time, FP64: a sample of each kind, same number of steps
     sample = {k: v[:args.batch_sample] for k, v in kinds.items() if v}
     per_kind_ms = {}
@@ -603,8 +648,9 @@ def run_batch(args, rank, world, local_rank):
                        "instances": len(ws), "points": npts, "contexts": len(sample),
                        "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
             "newton_iters_per_context_step": float(np.mean(newton_mixed)),
+            "clocks": clk_mixed,
             "fp64_batched": {"value": world * npts * args.steps / (ms_fp64 * 1e-3), "unit": UNIT,
-                             "ms_per_step": ms_fp64 / args.steps,
+                             "ms_per_step": ms_fp64 / args.steps, "clocks": clk_fp64,
                              "newton_iters_per_context_step": float(np.mean(newton_fp64))},
             "one_by_one_fp64": {"value": world * npts * args.steps / (one_ms * 1e-3), "unit": UNIT,
                                 "ms_per_step": one_ms / args.steps,

@@ -274,7 +274,11 @@ void mpm_default_options(mpm_options *o);
  * points, per-point E, nu and intrinsic permeability k (permeability, n
  * values, m^2).  Allocates all device memory the run needs except what
  * depends on the evolving sparsity.  *out receives the context, or NULL on
- * error (the code says why). */
+ * error (the code says why).  Rejected with MPM_ERR_BAD_ARG before any device
+ * call: a non-finite position, a volume that is not positive and finite, an E
+ * that is not positive and finite, nu outside (-1, 1/2), a negative or
+ * non-finite permeability.  A non-finite p0, load or boundary value is not
+ * checked here; the step that meets it fails with MPM_ERR_NONFINITE. */
 int mpm_create(const mpm_grid *grid, const mpm_particles *particles, const mpm_material *material,
                const double *permeability, const mpm_options *options, mpm_ctx **out);
 
@@ -397,11 +401,13 @@ int mpm_debug_precond(mpm_ctx *ctx, const double *X, const double *v, double *z)
  * owned by the caller; stream is a cudaStream_t (NULL = default stream).  The
  * per-cell counters live in a fixed device array of this library (about 3 MiB
  * on every GPU that loads it, held until exit), so the grid may have at most
- * 262,144 cells; larger grids return MPM_ERR_TOO_LARGE.  A point outside the
+ * 262,144 cells (also per axis, checked before the cell count is formed);
+ * larger grids return MPM_ERR_TOO_LARGE.  A point outside the
  * grid returns MPM_ERR_OUT_OF_GRID (cell_dev then holds -1 for it and
- * order_dev is not written).  The call returns when the work is done.  The
- * first call on a device looks up the array's device address and should come
- * before any stream capture.  All calls on a device share the array and the
+ * order_dev is not written).  Every call copies an error word to the host
+ * and waits for `stream`, so it returns when the work is done.  The first call
+ * on a device also looks up the array's device address and should come before
+ * any stream capture.  All calls on a device share the array and the
  * call clears what it needs at zero; calls that overlap on the GPU race on it
  * and must be ordered by the caller. */
 int mpm_bin_noalloc(const mpm_grid *grid, int64_t n, const double *x_dev, int32_t *cell_dev,

@@ -566,6 +566,19 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
     return create_fail(BAD, "n_surf > 0 needs surf_id, surf_normal and surf_area");
   if (!(mat->mu_f > 0.0)) return create_fail(BAD, "material.mu_f must be positive");
   if (!(opt->min_volume_fraction >= 0.0)) return create_fail(BAD, "min_volume_fraction must be >= 0");
+  // the points' own data: finite positions, positive volumes, a positive
+  // Young's modulus with -1 < nu < 1/2, a non-negative permeability (the
+  // initial pressure and the loads are not checked here: a non-finite value
+  // there surfaces as MPM_ERR_NONFINITE at the first residual of a step)
+  for (int64_t i = 0; i < P->n; ++i) {
+    for (int k = 0; k < grid->dim; ++k)
+      if (!isfinite(P->x[i * grid->dim + k])) return create_fail(BAD, "non-finite point position");
+    if (!(P->vol[i] > 0.0) || !isfinite(P->vol[i])) return create_fail(BAD, "point volume must be positive and finite");
+    if (!(mat->E[i] > 0.0) || !isfinite(mat->E[i])) return create_fail(BAD, "E must be positive and finite");
+    if (!(mat->nu[i] > -1.0 && mat->nu[i] < 0.5)) return create_fail(BAD, "nu must lie in (-1, 1/2)");
+    if (!(permeability[i] >= 0.0) || !isfinite(permeability[i]))
+      return create_fail(BAD, "permeability must be non-negative and finite");
+  }
   // every surface id must address an entry of the load arrays
   if (P->surf_id)
     for (int64_t i = 0; i < P->n; ++i)

@@ -10,16 +10,18 @@
 // physical blocks (Galerkin coarse operators then weigh every node by its
 // physical stiffness / mass); the Krylov solver sees the preconditioner of its
 // symmetrically scaled system as D^-1 M^-1 D^-1.  Dirichlet and inactive DOFs
-// are masked out of the finest restriction, prolongation and Galerkin product.  S is assembled on the sparsity of J (the fill
-// of B2 diag(A)^-1 B1 outside it is lumped onto the diagonal, which keeps the
+// are masked out of the finest restriction, prolongation and Galerkin
+// product.  S is assembled on the sparsity of J (the fill of
+// B2 diag(A)^-1 B1 outside it is lumped onto the diagonal, which keeps the
 // row sums of S).
 //
 // Multigrid: vertex-centred factor-2 coarsening of the node lattice, bilinear
 // (trilinear) prolongation P, Galerkin coarse operators P^T A P stored as
 // dense 5^d-point block stencils (the Galerkin product of a stencil of radius
 // <= 3 with bilinear P has radius <= 2 and stays at 2), damped block-Jacobi
-// smoothing, and Jacobi sweeps on the coarsest grid.  Every kernel is a
-// gather with a fixed summation order (deterministic, no atomics).
+// smoothing, and an exact solve on the coarsest grid (a dense inverse formed
+// at set-up by LU with partial pivoting).  Every kernel is a gather with a
+// fixed summation order (deterministic, no atomics).
 #include <math.h>
 
 #include <utility>

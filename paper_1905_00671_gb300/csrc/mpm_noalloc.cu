@@ -14,9 +14,11 @@
 // address; the first call on each device looks the address up with
 // cudaGetSymbolAddress (with that device current) and keeps it.  Because that
 // first call does this set-up (and synchronises), it should be made before any
-// stream capture.  The counters a call needs at zero are cleared by the call;
-// two calls that overlap on the GPU (different streams, or host threads that
-// do not order them) race on the shared array and give wrong results.
+// stream capture.  Every call, not only the first, copies an error word to the
+// host and waits for its stream before it returns.  The counters a call needs
+// at zero are cleared by the call; two calls that overlap on the GPU
+// (different streams, or host threads that do not order them) race on the
+// shared array and give wrong results.
 #include <math.h>
 #include <string.h>
 
@@ -129,18 +131,20 @@ extern "C" int mpm_bin_noalloc(const mpm_grid *grid, int64_t n, const double *x_
   if (!grid || n < 0 || (n > 0 && (!x_dev || !cell_dev || !order_dev))) return MPM_ERR_BAD_ARG;
   if (grid->dim != 2 && grid->dim != 3) return MPM_ERR_BAD_ARG;
   if (!(grid->h > 0.0) || n > INT32_MAX) return MPM_ERR_BAD_ARG;
+  // Each axis is bounded before the product is formed, so the product of at
+  // most three factors <= 2^18 cannot overflow int64 and a grid whose cell
+  // count would wrap is rejected rather than indexed.  Only the cell fields
+  // of GridP are used here.
   GridP g{};
   g.d = grid->dim;
-  g.nnodes = 1;
   g.ncells = 1;
   for (int k = 0; k < 3; ++k) {
     const bool used = k < g.d;
     if (used && grid->ncell[k] < 1) return MPM_ERR_BAD_ARG;
+    if (used && grid->ncell[k] > NOALLOC_MAX_CELLS) return MPM_ERR_TOO_LARGE;
     g.nc[k] = used ? grid->ncell[k] : 1;
-    g.nn[k] = used ? grid->ncell[k] + 1 : 1;
     g.org[k] = used ? grid->origin[k] : 0.0;
     g.ncells *= g.nc[k];
-    g.nnodes *= g.nn[k];
   }
   g.h = grid->h;
   if (g.ncells > NOALLOC_MAX_CELLS) return MPM_ERR_TOO_LARGE;

@@ -25,7 +25,10 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["unit"] == "particle-updates/s"
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["ms_per_step"] > 0 and d["n_gpus"] == 1
-    assert d["config"]["workload"].startswith("footing-200x100")
+    # a bounded piece of the default workload (the 3D slope), labelled as such
+    assert d["config"]["workload"].startswith("slope-piece-24x16x12")
+    assert d["config"]["sample_of"].startswith("slope-128x128x64")
+    assert d["config"]["points"] < 100_000
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,

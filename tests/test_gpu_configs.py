@@ -1,0 +1,206 @@
+"""GPU parity of the configurations the other parity files leave out, and the
+host-made failures of a step.
+
+  * the unstabilized switch (Eq. stab-term-ppp off) on the Sec. 5.1 column and
+    on a GIMP footing;
+  * the strip footing under harmonic loading as the paper sets it up (Sec.
+    5.2: Hencky, consistent mass, w = 3 - 3 cos(100 t) MPa) at full size, step
+    by step against the oracle, and at the paper's tolerances through the
+    steps of its Newton-Krylov table;
+  * batched instances against the oracle directly (not only against the
+    GPU's own one-by-one runs);
+  * MPM_ERR_NEGATIVE_J and MPM_ERR_NONFINITE from bad inputs made on the host
+    (an absurd load, a NaN initial pressure, a NaN traction), with the state
+    kept at the last completed step and the context usable afterwards.
+Parity bar as in test_gpu_parity: 1e-10 relative per field and step with both
+sides at their round-off floor.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1905_00671_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(newton_rtol=1e-13, newton_stag=1e-6, newton_max=12)
+GPU_TIGHT = dict(TIGHT, krylov_rtol=1e-13, krylov_max=20000)
+
+
+@pytest.fixture(scope="module")
+def mpm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1905_00671_gb300 import mpm as m
+
+    m.load()
+    return m
+
+
+def rel(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / scale
+
+
+def _compare(w, got, ref, fields, where):
+    for k in fields:
+        r = ref[k].reshape(got[k].shape)
+        if k in ("x", "F", "V", "lp"):       # the change over the run, not the offset
+            base = {"x": w.x, "F": np.tile(np.eye(w.dim).reshape(-1), (w.n, 1)),
+                    "V": w.vol, "lp": w.lp}[k].reshape(got[k].shape)
+            err = rel(got[k] - base, r - base)
+        else:
+            err = rel(got[k], r)
+        assert err <= 1e-10, (where, k, err)
+
+
+def _fields(w):
+    return ("x", "u", "p", "F", "V", "lp") + (("v", "a", "pd", "pdd") if w.dynamic else ())
+
+
+UNSTAB = {
+    # Sec. 5.1: 40 elements, 2 points per element, undrained first step
+    "paper-terzaghi-40-unstabilized": (lambda: I.paper_terzaghi(40, stabilize=False), 2),
+    "footing2d-gimp-qs-unstabilized": (
+        lambda: replace(I.small_footing(seed=9, dynamic=False, body=(20, 10), pad=2, dt=1.0),
+                        stabilize=False), 2),
+    "footing2d-gimp-newmark-unstabilized": (
+        lambda: replace(I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25), stabilize=False), 2),
+}
+
+
+@pytest.mark.parametrize("name", list(UNSTAB))
+def test_unstabilized_step_parity(mpm, name):
+    make, nsteps = UNSTAB[name]
+    w = make()
+    assert not w.stabilize
+    sim = mpm.Simulation(w, **GPU_TIGHT)
+    orc = O.Oracle(w, **TIGHT)
+    for s in range(nsteps):
+        sim.step()
+        orc.step()
+        _compare(w, sim.read(_fields(w)), orc.state(), _fields(w), (name, s))
+    sim.close()
+
+
+def test_harmonic_footing_step_parity(mpm):
+    """The Sec. 5.2 set-up at full size (6,400 points, 40 x 44 cells of
+    0.25 m): Hencky, consistent-mass Stage 1, Newmark, the harmonic load."""
+    w = I.harmonic_footing()
+    sim = mpm.Simulation(w, **GPU_TIGHT)
+    orc = O.Oracle(w, **TIGHT)
+    for s in range(3):
+        sim.step()
+        orc.step()
+        _compare(w, sim.read(_fields(w)), orc.state(), _fields(w), ("harmonic", s))
+    sim.close()
+
+
+def test_harmonic_footing_newton_history_at_paper_tolerances(mpm):
+    """At the paper's tolerances (Newton 1e-8, Krylov 1e-8 of the current
+    residual) the GPU steps the harmonic footing to its 100th step (t =
+    0.1 s, the first row of the paper's Newton-Krylov table), every step
+    converging; at step 100 it takes three Newton iterations, as the table
+    reports, each reducing the residual."""
+    w = I.harmonic_footing()
+    sim = mpm.Simulation(w, newton_rtol=1e-8, krylov_rtol=1e-8)
+    for s in range(1, 101):
+        st = sim.step()
+        assert st["res_norm"][-1] <= 1e-8 * st["res_norm"][0]
+    assert 2 <= st["newton_iters"] <= 4, st
+    r = st["res_norm"]
+    assert all(r[i + 1] < r[i] for i in range(len(r) - 1)), r
+    assert all(k >= 1 for k in st["krylov_iters"]), st
+    sim.close()
+
+
+def _terzaghi_set():
+    return [I.terzaghi_column(ncell_y=12, ncell_x=3, h=0.25, k=1e-10, load=10e3),
+            I.terzaghi_column(ncell_y=8, ncell_x=5, h=0.25, k=1e-11, load=50e3)]
+
+
+def _footing_set():
+    return [I.small_footing(seed=21, body=(24, 12), pad=2, k=1e-12),
+            I.small_footing(seed=23, body=(28, 8), pad=2, k=3e-12)]
+
+
+@pytest.mark.parametrize("maker", [_terzaghi_set, _footing_set])
+def test_batch_instances_against_the_oracle(mpm, maker):
+    """Each instance of a batched context against the oracle stepping that
+    instance alone (Sec. 3.1 per instance; batching changes no equation)."""
+    ws = maker()
+    batch = mpm.Batch(ws, **GPU_TIGHT)
+    orcs = [O.Oracle(w, **TIGHT) for w in ws]
+    for s in range(2):
+        batch.step()
+        for o in orcs:
+            o.step()
+        got = batch.read(("x", "u", "p"))
+        for i, (w, o) in enumerate(zip(ws, orcs)):
+            _compare(w, got[i], o.state(), ("x", "u", "p"), (w.name, s))
+    batch.close()
+
+
+# ---------------------------------------------------------------- host-made failures
+def test_negative_jacobian_is_reported_state_kept_and_context_usable(mpm):
+    """A load a thousand times the footing's crushes the first Newton iterate
+    (det F <= 0 at some point): MPM_ERR_NEGATIVE_J, the state of the last
+    completed step kept, and the next step with the regular load matches the
+    oracle's first step."""
+    w = I.small_footing(seed=3, body=(8, 4), pad=1, dynamic=False, dt=1.0)
+    with pytest.raises(O.OracleError, match="non-positive Jacobian"):
+        O.Oracle(w).step(traction=w.traction(w.dt) * 1000.0)
+    sim = mpm.Simulation(w, **GPU_TIGHT)
+    before = sim.read(("x", "u", "p", "F"))
+    with pytest.raises(mpm.MPMError) as e:
+        sim.step(traction=w.traction(w.dt) * 1000.0)
+    assert e.value.code == -3
+    after = sim.read(("x", "u", "p", "F"))
+    for k in before:
+        np.testing.assert_array_equal(before[k], after[k])
+    assert sim.stats()["steps"] == 0
+    sim.step(traction=w.traction(w.dt))
+    orc = O.Oracle(w, **TIGHT)
+    orc.step()
+    _compare(w, sim.read(("x", "u", "p")), orc.state(), ("x", "u", "p"), "after NEGATIVE_J")
+    sim.close()
+
+
+def test_nan_initial_pressure_is_nonfinite(mpm):
+    w = I.small_footing(seed=3, body=(8, 4), pad=1, dynamic=False, dt=1.0)
+    p0 = w.p0.copy()
+    p0[7] = np.nan
+    sim = mpm.Simulation(replace(w, p0=p0))
+    before = sim.read(("x", "u"))
+    with pytest.raises(mpm.MPMError) as e:
+        sim.step()
+    assert e.value.code == -4
+    after = sim.read(("x", "u"))
+    for k in before:
+        np.testing.assert_array_equal(before[k], after[k])
+    sim.close()
+
+
+def test_nan_traction_is_nonfinite_and_the_state_stays_at_the_last_step(mpm):
+    w = I.small_footing(seed=3, body=(8, 4), pad=1)              # Newmark
+    sim = mpm.Simulation(w, **GPU_TIGHT)
+    orc = O.Oracle(w, **TIGHT)
+    sim.step()
+    orc.step()
+    keep = sim.read(_fields(w))
+    bad = w.traction(sim.t + w.dt).copy()
+    bad[0, 1] = np.nan
+    with pytest.raises(mpm.MPMError) as e:
+        sim.step(traction=bad)
+    assert e.value.code == -4
+    now = sim.read(_fields(w))
+    for k in keep:
+        np.testing.assert_array_equal(keep[k], now[k])
+    sim.step(traction=w.traction(sim.t + w.dt))
+    orc.step()
+    _compare(w, sim.read(_fields(w)), orc.state(), _fields(w), "after NONFINITE")
+    sim.close()

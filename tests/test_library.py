@@ -86,6 +86,34 @@ def test_rejected_create_names_its_reason_without_gpu(lib, opts, model, why):
     assert e.value.code == -1                            # MPM_ERR_BAD_ARG
 
 
+@pytest.mark.parametrize("field,value,why", [
+    ("vol", -1e-3, "point volume must be positive"),
+    ("vol", float("nan"), "point volume must be positive"),
+    ("x", float("inf"), "non-finite point position"),
+    ("E", float("nan"), "E must be positive and finite"),
+    ("E", 0.0, "E must be positive and finite"),
+    ("nu", 0.5, "nu must lie in"),
+    ("k", -1e-12, "permeability must be non-negative"),
+])
+def test_bad_point_data_is_rejected_at_create_without_gpu(lib, field, value, why):
+    """Host-made faults in the points' own data (a negative or NaN volume, an
+    infinite position, a NaN or zero modulus, an incompressible nu, a negative
+    permeability) are rejected by mpm_create before any device call."""
+    from dataclasses import replace
+
+    import numpy as np
+
+    from paper_1905_00671_gb300 import inputs as I
+    from paper_1905_00671_gb300 import mpm
+
+    w = I.terzaghi_column(ncell_y=4, ncell_x=2)
+    a = getattr(w, field).copy()
+    a.reshape(-1)[3] = value
+    with pytest.raises(mpm.MPMError, match=why) as e:
+        mpm.Simulation(replace(w, **{field: np.ascontiguousarray(a)}))
+    assert e.value.code == -1
+
+
 def test_rejected_batch_create_names_its_reason_without_gpu(lib):
     from dataclasses import replace
 

@@ -9,6 +9,7 @@ two calls in a row (the second on a different grid, so that counters left over
 from the first call would show).  This file is collected last on purpose.
 """
 import ctypes as C
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -73,3 +74,35 @@ def test_noalloc_rejects_grids_beyond_its_scratch(env):
     out_o = torch.zeros(4, dtype=torch.int64, device="cuda")
     rc = lib.mpm_bin_noalloc(C.byref(g), 4, x.data_ptr(), out_c.data_ptr(), out_o.data_ptr(), None)
     assert rc == -10
+
+
+def test_noalloc_rejects_cell_counts_that_would_overflow(env):
+    """Per-axis counts whose product wraps (2^21 x 2^21 x 2^22 = 2^64) are
+    rejected before any kernel runs; with n = 0 nothing touches the array."""
+    torch, mpm, lib = env
+    g = mpm.mpm_grid()
+    g.dim = 3
+    g.ncell[0], g.ncell[1], g.ncell[2] = 1 << 21, 1 << 21, 1 << 22
+    g.h = 1.0
+    assert lib.mpm_bin_noalloc(C.byref(g), 0, None, None, None, None) == -10
+
+
+def test_noalloc_point_outside_grid_then_valid_call(env):
+    """A point outside the grid: MPM_ERR_OUT_OF_GRID and cell -1 for it; the
+    next valid call starts from a cleared error word and matches the regular
+    path exactly."""
+    torch, mpm, lib = env
+    w = I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25)
+    bad = replace(w, x=w.x.copy())
+    j = 5
+    bad.x[j, 0] = -0.3                     # left of the grid's origin
+    rc, cell, _ = noalloc_bin(torch, mpm, lib, bad)
+    assert rc == -2
+    assert cell[j] == -1
+    sim = mpm.Simulation(w)
+    ref_cell, ref_order = sim.debug_bin()
+    sim.close()
+    rc, cell, order = noalloc_bin(torch, mpm, lib, w)
+    assert rc == 0
+    np.testing.assert_array_equal(cell, ref_cell)
+    np.testing.assert_array_equal(order, ref_order)
