@@ -74,7 +74,25 @@ def parse():
                     help="kernel classes timed with CUDA events inside the timed steps")
     ap.add_argument("--breakdown-steps", type=int, default=3,
                     help="extra steps, after the timed ones, with every kernel class timed")
+    ap.add_argument("--schur-order", type=int, default=None, help="0 upper, 1 lower triangular")
+    ap.add_argument("--mg-sweeps", type=int, default=None, help="V(k,k) smoothing sweeps")
+    ap.add_argument("--mg-omega", type=float, default=None, help="block-Jacobi damping")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="1: the library times its Jacobian kernel configurations at the first "
+                         "assembly of each context (a warm-up step) and keeps the fastest")
     return ap.parse_args()
+
+
+def solver_opts(args):
+    """Preconditioner options given on the command line (library defaults otherwise)."""
+    o = {"autotune": int(args.autotune)}
+    if args.schur_order is not None:
+        o["schur_order"] = args.schur_order
+    if args.mg_sweeps is not None:
+        o["mg_sweeps"] = args.mg_sweeps
+    if args.mg_omega is not None:
+        o["mg_omega"] = args.mg_omega
+    return o
 
 
 def make_workload(name):
@@ -201,29 +219,61 @@ def ncu_traffic(kernel, workload):
 
 
 # Algorithmic FP64 flops of the Jacobian assembly (Eqs. jacobian-system-
-# stabilized-ppp, newmark-linearization as evaluated per point): F per
-# (point, a, b) term and G per (point, node) term, counted by hand (an FMA is
-# 2 flops) from the formula with the per-(point, node) vectors (g_a = F^-T
-# grad S_a, S_a, S_a - S0_a, tau' g_a, g_a.w, g_a.grad v) and their products
-# with the point's coefficients of the block terms formed once per node:
-# per term 2d^2 + 6d + 1 FMAs and d + 1 additions (+ d + 1 FMAs, Newmark);
-# per node the basis, the vectors and 6d + 6 coefficient products (+ 1,
-# Newmark).  {(dim, dynamic): (F, G)}.
-JAC_FLOPS = {(2, False): (45, 43), (2, True): (51, 52), (3, False): (78, 77), (3, True): (86, 96)}
-# Hencky elasticity adds, per term, the d^3 FMAs of sum_l U_a,ikl g_b,l and,
-# per (point, node), the staged U of its spectral tangent: gh_A = g.n_A (d^2
-# FMAs), w_Akl = kappa_A gh_A n_Ak n_Al + sum_{B != A} theta_AB gh_B (n_Ak n_Bl
-# + n_Bk n_Al) (3 + 6 (d - 1) flops each, d^3 of them) and U_ikl = -cs (1 + cv)
-# (lambda g_i delta_kl + sum_A n_Ai w_Akl) (2 d + 1 flops each, d^3 of them).
+# stabilized-ppp, newmark-linearization as evaluated per point), counted by
+# hand (an FMA is 2 flops) from the staged form: the per-(point, node) vectors
+# (g_a = F^-T grad S_a, S_a, S_a - S0_a, tau' g_a, g_a.w, g_a.grad v) and their
+# products with the point's coefficients of the block terms are formed once per
+# node (G per (point, node)); the blocks (a, b) and (b, a) are assembled as one
+# symmetric pair (A and C once, B1 and B2 for both), so a (point, a, b) term
+# with a != b costs F_pair per unordered pair and a diagonal term F_diag:
+#   F_diag = 2 (2d^2 + 6d + 1) + d + 1   (+ 2 (d + 1), Newmark)
+#   F_pair = F_diag + 8d                 (+ 2 (2d + 1) over F_diag's QS value, Newmark)
+# (the pair adds the d + 3d FMAs of the second block's B1 and B2).
+# {(dim, dynamic): (F_pair, F_diag, G)}.
+JAC_FLOPS = {(2, False): (61, 45, 43), (2, True): (71, 51, 52), (3, False): (102, 78, 77),
+             (3, True): (116, 86, 96)}
+# Hencky elasticity adds, per pair and per diagonal term, the d^3 FMAs of
+# sum_l U_a,ikl g_b,l and, per (point, node), the staged U of its spectral
+# tangent: gh_A = g.n_A (d^2 FMAs), w_Akl = kappa_A gh_A n_Ak n_Al + sum_{B != A}
+# theta_AB gh_B (n_Ak n_Bl + n_Bk n_Al) (3 + 6 (d - 1) flops each, d^3 of
+# them) and U_ikl = -cs (1 + cv) (lambda g_i delta_kl + sum_A n_Ai w_Akl)
+# (2 d + 1 flops each, d^3 of them).  {dim: (per pair or diagonal term, G)}
 JAC_FLOPS_HENCKY = {2: (16, 120), 3: (54, 612)}
+
+
+def jacobian_flops(dim, dynamic, hencky, terms, point_nodes):
+    """Algorithmic flops of one assembly: terms = sum over points of n_p^2
+    (ordered (a, b) pairs of the point's active support nodes), point_nodes =
+    sum of n_p; (terms - point_nodes) / 2 unordered pairs a != b and
+    point_nodes diagonal terms."""
+    fp, fd, g = JAC_FLOPS[(dim, dynamic)]
+    if hencky:
+        h, gh = JAC_FLOPS_HENCKY[dim]
+        fp, fd, g = fp + h, fd + h, g + gh
+    return fp * (terms - point_nodes) / 2 + (fd + g) * point_nodes
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 
 
-def spmv_bytes(nnodes, nnzb, nb):
+def spmv_bytes(nnodes, nnzb, nb, word=8):
     """Algorithmic bytes of one block-CSR SpMV: values + column indices + row
-    pointers, x read once, y written once."""
-    return nnzb * (nb * nb * 8 + 4) + (nnodes + 1) * 4 + 2 * nnodes * nb * 8
+    pointers, x read once, y written once (word = 8 for FP64, 4 for FP32)."""
+    return nnzb * (nb * nb * word + 4) + (nnodes + 1) * 4 + 2 * nnodes * nb * word
+
+
+# FP32 peak from unit counts and clocks: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def jacobian32_bytes(n, nnzb, nnodes, dim, dynamic):
+    """Algorithmic bytes of one FP32 Jacobian assembly: every point's data the
+    tangent needs read once (dF^-1, tau', grad p - rho_f (g - a), grad p, nine
+    scalar coefficients, the 1D basis S, dS, S0 in 4 slots per axis; Newmark:
+    the mass and grad v), the sparsity read once (coupling mask, row pointers,
+    block columns) and every (d+1)^2 block written once, 4-byte words."""
+    per_point = 2 * dim * dim + 2 * dim + 9 + 3 * dim * 4 + (1 + dim * dim if dynamic else 0)
+    nb = dim + 1
+    return 4 * per_point * n + nnzb * (nb * nb * 4 + 4) + nnodes * (6 * 8 + 4)
 
 
 def nvtx_push(name):
@@ -261,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_stream(stream)
     prof_bits = 0
     for k in args.profile.split(","):
-        if k:
+        if k and k != "none":
             prof_bits |= 1 << mpm.PROF[k]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -271,7 +321,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     # ---- device-resident throughput
-    sim = mpm.Simulation(w, stream=stream.cuda_stream, profile=prof_bits, precond_lag=args.precond_lag)
+    sopts = solver_opts(args)
+    sim = mpm.Simulation(w, stream=stream.cuda_stream, profile=prof_bits, precond_lag=args.precond_lag, **sopts)
     for _ in range(args.warmup):
         sim.step(resident=True)
     barrier()
@@ -296,6 +347,8 @@ def run_ours(args, rank, world, local_rank):
         launches += st["kernel_launches"]
         nnzb.append(st["nnzb"])
         terms.append((st["jac_terms"], st["jac_point_nodes"]))
+        jac_cfg = {"config": st["jac_config"][0], "tuned": st["jac_tuned"][0],
+                   "candidates_ms": [round(x, 3) for x in st["jac_tune_ms"][0]]}
         for k in mpm.PROF:
             prof_ms[k] += st["prof_ms"][k]
             prof_n[k] += st["prof_launches"][k]
@@ -313,7 +366,8 @@ def run_ours(args, rank, world, local_rank):
     bd_nnzb = []
     if args.breakdown_steps > 0:
         all_bits = sum(1 << v for v in mpm.PROF.values())
-        sim_b = mpm.Simulation(w, stream=stream.cuda_stream, profile=all_bits, precond_lag=args.precond_lag)
+        sim_b = mpm.Simulation(w, stream=stream.cuda_stream, profile=all_bits, precond_lag=args.precond_lag,
+                               **sopts)
         sim_b.step(resident=True)
         for _ in range(args.breakdown_steps):
             flush.zero_()
@@ -334,8 +388,8 @@ def run_ours(args, rank, world, local_rank):
         mixed = {"value": None, "unit": UNIT, "skipped": "Hencky elasticity has no FP32 Jacobian"}
     elif not args.no_mixed:
         sim_m = mpm.Simulation(w, stream=stream.cuda_stream, precision=mpm.MPM_MIXED,
-                               newton_max=60, profile=prof_bits, precond_lag=args.precond_lag)
-        sim_r = mpm.Simulation(w, stream=stream.cuda_stream)   # FP64 twin for the error
+                               newton_max=60, profile=prof_bits, precond_lag=args.precond_lag, **sopts)
+        sim_r = mpm.Simulation(w, stream=stream.cuda_stream, **sopts)   # FP64 twin for the error
         for _ in range(args.warmup):
             sim_m.step(resident=True)
             sim_r.step(resident=True)
@@ -343,6 +397,8 @@ def run_ours(args, rank, world, local_rank):
         ms = 0.0
         newton_m = krylov_m = 0
         prof_m = {k: 0.0 for k in mpm.PROF}
+        prof_nm = {k: 0 for k in mpm.PROF}
+        terms_m, nnzb_m = [], []
         for i in range(args.steps):
             flush.zero_()
             nvtx_push("timed_mixed")
@@ -352,8 +408,13 @@ def run_ours(args, rank, world, local_rank):
             nvtx_pop()
             newton_m += st["newton_iters"]
             krylov_m += st["krylov_total"]
+            jac_cfg_m = {"config": st["jac_config"][1], "tuned": st["jac_tuned"][1],
+                         "candidates_ms": [round(x, 3) for x in st["jac_tune_ms"][1]]}
+            terms_m.append((st["jac_terms"], st["jac_point_nodes"]))
+            nnzb_m.append(st["nnzb"])
             for k in mpm.PROF:
                 prof_m[k] += st["prof_ms"][k]
+                prof_nm[k] += st["prof_launches"][k]
             sim_r.step(resident=True)
             torch.cuda.synchronize()
             ms += ev0[i].elapsed_time(ev1[i])
@@ -366,9 +427,54 @@ def run_ours(args, rank, world, local_rank):
                  "newton_iters_per_step": newton_m / args.steps,
                  "krylov_iters_per_step": krylov_m / args.steps,
                  "class_ms_per_step": {k: round(v / args.steps, 3) for k, v in prof_m.items() if v > 0},
-                 "rel_error_vs_fp64": errs}
+                 "rel_error_vs_fp64": errs, "jacobian_kernel": jac_cfg_m}
         sim_m.close()
         sim_r.close()
+        # FP32 rooflines: the Jacobian from the live events of the timed steps,
+        # the SpMV from a separate pass with events around every class
+        peaks_m, peak_src_m = measured_peaks()
+        hbm = float(peaks_m["hbm_gbs"])
+        roof_m = {}
+        if prof_nm["jacobian"] > 0:
+            avg_ms = prof_m["jacobian"] / prof_nm["jacobian"]
+            nz = sum(nnzb_m) / len(nnzb_m)
+            byt = jacobian32_bytes(w.n, nz, w.nnodes, w.dim, w.dynamic)
+            fl = sum(jacobian_flops(w.dim, w.dynamic, False, t, pn) for t, pn in terms_m) / len(terms_m)
+            ach = byt / (avg_ms * 1e-3) / 1e9
+            roof_m["jacobian"] = {
+                "kernel": "k_jacobian_direct" if jac_cfg_m["config"] < 1000 else "k_point_nodes + k_jacobian (FP32)",
+                "bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "algorithmic_bytes": int(byt),
+                "avg_launch_us": round(avg_ms * 1e3, 3), "peak_source": peak_src_m + " hbm_gbs",
+                "fp32_tflops": round(fl / (avg_ms * 1e-3) / 1e12, 3),
+                "fp32_frac": round(fl / (avg_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS, 4),
+                "fp32_peak_source": "FP32 from unit counts and clocks (152 SMs x 128 lanes x 2 x 2070 MHz)"}
+        if args.breakdown_steps > 0:
+            all_bits = sum(1 << v for v in mpm.PROF.values())
+            sim_mb = mpm.Simulation(w, stream=stream.cuda_stream, precision=mpm.MPM_MIXED, newton_max=60,
+                                    profile=all_bits, precond_lag=args.precond_lag, **sopts)
+            sim_mb.step(resident=True)
+            bdm, bdn, bnz = {k: 0.0 for k in mpm.PROF}, {k: 0 for k in mpm.PROF}, []
+            for _ in range(args.breakdown_steps):
+                flush.zero_()
+                st = sim_mb.step(resident=True)
+                bnz.append(st["nnzb"])
+                for k in mpm.PROF:
+                    bdm[k] += st["prof_ms"][k]
+                    bdn[k] += st["prof_launches"][k]
+            sim_mb.close()
+            if bdn["spmv"] > 0:
+                nb = w.dim + 1
+                byt = spmv_bytes(w.nnodes, sum(bnz) / len(bnz), nb, word=4)
+                avg_ms = bdm["spmv"] / bdn["spmv"]
+                ach = byt / (avg_ms * 1e-3) / 1e9
+                roof_m["spmv"] = {"kernel": "k_bsr_spmv (FP32)", "bound": "hbm", "achieved": round(ach, 1),
+                                  "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                                  "algorithmic_bytes": int(byt), "avg_launch_us": round(avg_ms * 1e3, 3),
+                                  "peak_source": peak_src_m + " hbm_gbs"}
+            mixed["class_ms_per_step_breakdown"] = {k: round(v / args.breakdown_steps, 3)
+                                                    for k, v in bdm.items() if bdn[k] > 0}
+        mixed["roofline"] = roof_m
 
     # ---- end to end through the C-ABI with host buffers
     e2e = None
@@ -377,7 +483,7 @@ def run_ours(args, rank, world, local_rank):
         pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
         trac_h = pin((max(w.n_surf, 1), d))
         outs = {"x": pin((n, d)), "u": pin((n, d)), "p": pin(n)}
-        sim2 = mpm.Simulation(w, stream=stream.cuda_stream)
+        sim2 = mpm.Simulation(w, stream=stream.cuda_stream, **sopts)
         for _ in range(args.warmup):
             trac_h[:w.n_surf] = w.traction(sim2.t + w.dt)
             sim2.step(traction=trac_h[:w.n_surf])
@@ -415,10 +521,8 @@ def run_ours(args, rank, world, local_rank):
     nbd = max(args.breakdown_steps, 1)
     roofline = None
     if prof_n.get("jacobian", 0) > 0:
-        F, G = JAC_FLOPS[(w.dim, w.dynamic)]
-        if w.model == mpm.MPM_MODEL_HENCKY:
-            F, G = F + JAC_FLOPS_HENCKY[w.dim][0], G + JAC_FLOPS_HENCKY[w.dim][1]
-        flops = sum(F * t + G * pn for t, pn in terms) / len(terms)   # per assembly
+        hk = w.model == mpm.MPM_MODEL_HENCKY
+        flops = sum(jacobian_flops(w.dim, w.dynamic, hk, t, pn) for t, pn in terms) / len(terms)
         avg_ms = prof_ms["jacobian"] / prof_n["jacobian"]
         ach = flops / (avg_ms * 1e-3) / 1e12
         roofline = {"kernel": "k_jacobian", "bound": "alu", "achieved": round(ach, 4),
@@ -460,6 +564,9 @@ def run_ours(args, rank, world, local_rank):
             "newton_iters_per_step": newton / args.steps, "krylov_iters_per_step": krylov / args.steps,
             "gpu_launches": launches, "clocks": clk, "roofline": roofline, "e2e": e2e,
             "mixed": mixed}
+    line["jacobian_kernel"] = jac_cfg   # threads per block + 1000 if staged; tuned = chosen by timing
+    if sopts:
+        line["solver_options"] = sopts
     return line, w
 
 

@@ -23,6 +23,7 @@ DevView Ctx::view() const {
   v.cell_start = cell_start;
   v.sh_first = sh_first;
   v.sh_cnt = sh_cnt;
+  v.sh_box = sh_box;
   v.sh_S = sh_S;
   v.sh_dS = sh_dS;
   v.sh_S0 = sh_S0;
@@ -472,11 +473,11 @@ void free_all(Ctx &c) {
   c.ev.clear();
   linsys_free<double>(c.L64);
   linsys_free<float>(c.L32);
-  float *fptrs[] = {c.sh_Sf, c.sh_dSf, c.sh_S0f, c.sh_nrmf, c.recf};
+  float *fptrs[] = {c.sh_Sf, c.sh_dSf, c.sh_S0f, c.sh_nrmf, c.recf, c.pn32};
   for (float *p : fptrs)
     if (p) cudaFree(p);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
-                  c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_S, c.sh_dS,
+                  c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_box, c.sh_S, c.sh_dS,
                   c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.fsd, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
@@ -561,6 +562,10 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
     return create_fail(BAD, "MPM_TAU_MONFORTE needs the Newmark scheme");
   if (opt->precond != MPM_PRECOND_BLOCK_JACOBI && opt->precond != MPM_PRECOND_SCHUR_MG)
     return create_fail(BAD, "unknown precond");
+  if (opt->schur_order != MPM_SCHUR_LOWER && opt->schur_order != MPM_SCHUR_UPPER)
+    return create_fail(BAD, "unknown schur_order");
+  if (opt->mg_sweeps < 0 || opt->mg_sweeps > 3) return create_fail(BAD, "mg_sweeps must be in 0..3");
+  if (!(opt->mg_omega >= 0.0 && opt->mg_omega <= 1.0)) return create_fail(BAD, "mg_omega must be in [0, 1]");
   if (opt->precision != MPM_FP64 && opt->precision != MPM_MIXED) return create_fail(BAD, "unknown precision");
   if (P->n_surf < 0 || (P->n_surf > 0 && (!P->surf_id || !P->surf_normal || !P->surf_area)))
     return create_fail(BAD, "n_surf > 0 needs surf_id, surf_normal and surf_area");
@@ -659,6 +664,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   A(&c.perm, n);
   A(&c.sh_first, 3 * n);
   A(&c.sh_cnt, n);
+  A(&c.sh_box, n);
   A(&c.sh_S, 3 * MAXS * n);
   A(&c.sh_dS, 3 * MAXS * n);
   A(&c.sh_S0, 3 * MAXS * n);

@@ -32,6 +32,20 @@ constexpr int MASKW = PATTERN_MASK_WORDS;  // 7^3 = 343 offsets in [-3, 3]^3
 
 // Support box of point q along each axis, and whether node coordinate ac lies in
 // it (off = slot of that node).
+// The same from the point's packed box word (sh_box, written with the
+// renormalisation flag at the end of the step's set-up).
+template <int D>
+__device__ inline bool in_box4(const int4 bx, const int ac[3], int off[3]) {
+  const int first[3] = {bx.x, bx.y, bx.z};
+  off[0] = off[1] = off[2] = 0;
+  for (int k = 0; k < D; ++k) {
+    const int o = ac[k] - first[k];
+    if (o < 0 || o >= unpack_cnt(bx.w, k)) return false;
+    off[k] = o;
+  }
+  return true;
+}
+
 template <int D>
 __device__ inline bool in_box(const DevView &v, int64_t q, const int ac[3], int off[3]) {
   const int64_t n = v.n;
@@ -315,6 +329,7 @@ __global__ void k_renorm(GridP g, DevView v) {
     packed |= RENORM_BIT;
   }
   v.sh_cnt[p] = packed;
+  v.sh_box[p] = make_int4(f[0], f[1], f[2], packed);
 }
 
 // ---------------------------------------------------------------- points
@@ -524,7 +539,7 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
         const int64_t cid = cell_index(g, c0, c1, c2);
         for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
           int off[3];
-          if (!in_box<D>(v, q, ac, off)) continue;
+          if (!in_box4<D>(v.sh_box[q], ac, off)) continue;
           double Sa, S0a, Gn[3], ga[3];
           basis_at<D>(v, q, off, a, Sa, S0a, Gn);
           spatial_grad<D>(v, q, Gn, ga);
@@ -700,20 +715,54 @@ __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, c
   }
 }
 
+// Symmetric pairs.  The Jacobian's blocks (a, b) and (b, a) come from the
+// same (point, a, b) terms: A_ba = A_ab^T (the material, geometric, pressure,
+// Kelvin and inertia parts of A are each symmetric under (a, i) <-> (b, k):
+// tau' and the tangent are symmetric) and C_ba = C_ab (Darcy and C_stab are
+// symmetric), while B1 and B2 of the two blocks differ.  One thread takes the
+// unordered pair: coupling offset o = b - a in the upper half of [-3, 3]^d
+// (slot s >= the centre slot, offset-major as before: thread t takes slot
+// centre + t / nnodes of row a = t % nnodes) and writes block (a, b) and, for
+// o != 0, block (b, a) = row b, slot of -o.  Per (point, a, b) term of a pair
+// the A and C parts are formed once and the B1 / B2 parts twice.
+template <int D>
+struct PairSlots {
+  static constexpr int NSLOT = D == 2 ? 49 : 343;
+  static constexpr int CENTRE = NSLOT / 2;  // offset 0
+  static constexpr int COUNT = CENTRE + 1;  // slots >= CENTRE
+};
+
+template <int D, typename R, typename T>
+__device__ inline void write_block_bc(const DevView &v, int64_t row, int64_t colnode, const R *B, T *out,
+                                      int apply_bc) {
+  constexpr int NB = D + 1;
+  for (int i = 0; i < NB; ++i) {
+    const bool fr = apply_bc && v.fixed[row * NB + i] != 0;
+    for (int k = 0; k < NB; ++k) {
+      const bool fc = apply_bc && v.fixed[colnode * NB + k] != 0;
+      R x = B[i * NB + k];
+      if (fr || fc) x = (row == colnode && i == k) ? R(1) : R(0);
+      out[i * NB + k] = (T)x;
+    }
+  }
+}
+
 template <int D, bool GIMP, bool DYN, bool HK, typename T, typename R>
 __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn,
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
+  using PS = PairSlots<D>;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  constexpr int NSLOT = D == 2 ? 49 : 343;
   constexpr int NSL = pn_nslot(D);
   constexpr int NPF = pn_npf(D, DYN, HK);
-  if (t >= NSLOT * g.nnodes) return;
+  if (t >= (int64_t)PS::COUNT * g.nnodes) return;
   const int64_t a = t % g.nnodes;
-  const int64_t e = block_of_slot<D>(mask, row_ptr, a, (int)(t / g.nnodes));
+  const int slot = PS::CENTRE + (int)(t / g.nnodes);
+  const int64_t e = block_of_slot<D>(mask, row_ptr, a, slot);
   if (e < 0) return;
   constexpr int NB = D + 1;
   const int64_t bn = col[e];
+  const bool diag = slot == PS::CENTRE;
   int ac[3], bc[3];
   node_coords(g, a, ac);
   node_coords(g, bn, bc);
@@ -725,15 +774,19 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
     lo[k] = max(l1, l2);
     hi[k] = min(h1, h2);
   }
-  R B[NB * NB];
-  for (int i = 0; i < NB * NB; ++i) B[i] = 0;
+  // pair accumulators: A (shared, for (a, b); (b, a) gets its transpose), C
+  // (shared), B1 and B2 of each of the two blocks
+  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], C = 0;
+  for (int i = 0; i < D * D; ++i) A[i] = 0;
+  for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = 0;
   for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
     for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
       for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
         const int64_t cid = cell_index(g, c0, c1, c2);
         for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
           int oa[3], ob[3];
-          if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
+          const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
+          if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) continue;
           const R *P = pn + (int64_t)q * NSL * NPF;
           const R *pa = P + (oa[0] + MAXS * (oa[1] + MAXS * oa[2])) * NPF;
           const R *pb = P + (ob[0] + MAXS * (ob[1] + MAXS * ob[2])) * NPF;
@@ -754,56 +807,76 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
           if (DYN) dg = fma(pa[5 * D + 6], pb[D], dg);
           for (int i = 0; i < D; ++i)
             for (int k = 0; k < D; ++k) {
-              R acc = fma(ga[i], pb[D + 2 + k], B[i * NB + k]);
+              R acc = fma(ga[i], pb[D + 2 + k], A[i * D + k]);
               acc = fma(-gb[i], pa[2 * D + 2 + k], acc);
               if (HK)  // material part of the Hencky tangent, staged per node
                 for (int l = 0; l < D; ++l) acc = fma(pa[pn_npf(D, DYN) + (i * D + k) * D + l], gb[l], acc);
-              B[i * NB + k] = i == k ? acc - dg : acc;
+              A[i * D + k] = i == k ? acc - dg : acc;
             }
-          // B1 column: (p5 S_b) g_a
-          const R p5Sb = pb[5 * D + 4];
-          for (int i = 0; i < D; ++i) B[i * NB + D] = fma(p5Sb, ga[i], B[i * NB + D]);
-          // B2 row: (p6 S_a + p7 g_a.w) g_b - (p7 g_b.w) g_a - (p7 g_a.g_b) grad p
-          //         (- p5 S_a g_b.grad v, Newmark)
+          // B1 column of (a, b): (p5 S_b) g_a; of (b, a): (p5 S_a) g_b
+          const R p5Sb = pb[5 * D + 4], p5Sa = pa[5 * D + 4];
+          for (int i = 0; i < D; ++i) b1ab[i] = fma(p5Sb, ga[i], b1ab[i]);
+          // B2 row of (a, b): (p6 S_a + p7 g_a.w) g_b - (p7 g_b.w) g_a - (p7 g_a.g_b) grad p
+          //                   (- p5 S_a g_b.grad v, Newmark); (b, a): a <-> b
           const R ca = pa[5 * D + 2], eb = pb[5 * D + 3];
           for (int k = 0; k < D; ++k) {
-            R tk = fma(ca, gb[k], B[D * NB + k]);
-            if (DYN) tk = fma(-pa[5 * D + 4], pb[5 * D + 7 + k], tk);
+            R tk = fma(ca, gb[k], b2ab[k]);
+            if (DYN) tk = fma(-p5Sa, pb[5 * D + 7 + k], tk);
             tk = fma(-eb, ga[k], tk);
-            B[D * NB + k] = fma(-kgab, pp[9 + k], tk);
+            b2ab[k] = fma(-kgab, pp[9 + k], tk);
           }
-          // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b
-          B[D * NB + D] = fma(pa[5 * D + 5], pb[D + 1], B[D * NB + D] + kgab);
+          if (!diag) {
+            for (int i = 0; i < D; ++i) b1ba[i] = fma(p5Sa, gb[i], b1ba[i]);
+            const R cb = pb[5 * D + 2], ea = pa[5 * D + 3];
+            for (int k = 0; k < D; ++k) {
+              R tk = fma(cb, ga[k], b2ba[k]);
+              if (DYN) tk = fma(-p5Sb, pa[5 * D + 7 + k], tk);
+              tk = fma(-ea, gb[k], tk);
+              b2ba[k] = fma(-kgab, pp[9 + k], tk);
+            }
+          }
+          // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b (symmetric)
+          C = fma(pa[5 * D + 5], pb[D + 1], C + kgab);
         }
       }
-  if (apply_bc) {
-    for (int i = 0; i < NB; ++i) {
-      const bool fr = v.fixed[a * NB + i] != 0;
-      for (int k = 0; k < NB; ++k) {
-        const bool fc = v.fixed[bn * NB + k] != 0;
-        if (fr || fc) B[i * NB + k] = (a == bn && i == k) ? R(1) : R(0);
-      }
-    }
+  R B[NB * NB];
+  for (int i = 0; i < D; ++i) {
+    for (int k = 0; k < D; ++k) B[i * NB + k] = A[i * D + k];
+    B[i * NB + D] = b1ab[i];
+    B[D * NB + i] = b2ab[i];
   }
-  T *out = val + e * (NB * NB);
-  for (int i = 0; i < NB * NB; ++i) out[i] = (T)B[i];
+  B[D * NB + D] = C;
+  write_block_bc<D>(v, a, bn, B, val + e * (NB * NB), apply_bc);
+  if (diag) return;
+  const int64_t e2 = block_of_slot<D>(mask, row_ptr, bn, PS::NSLOT - 1 - slot);
+  if (e2 < 0) return;  // the coupling is symmetric: not reached
+  for (int i = 0; i < D; ++i) {
+    for (int k = 0; k < D; ++k) B[i * NB + k] = A[k * D + i];
+    B[i * NB + D] = b1ba[i];
+    B[D * NB + i] = b2ba[i];
+  }
+  B[D * NB + D] = C;
+  write_block_bc<D>(v, bn, a, B, val + e2 * (NB * NB), apply_bc);
 }
 
 // FP32 variant (mixed mode): the node vectors are recomputed per term from the
 // FP32 basis and records; with FP32 arithmetic plentiful this beats staging.
+// Symmetric pairs as in k_jacobian: one thread per unordered pair (a, b).
 template <int D, bool GIMP, bool DYN, typename T, typename R>
 __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
+  using PS = PairSlots<D>;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  constexpr int NSLOT = D == 2 ? 49 : 343;
-  if (t >= NSLOT * g.nnodes) return;
+  if (t >= (int64_t)PS::COUNT * g.nnodes) return;
   const int64_t a = t % g.nnodes;
-  const int64_t e = block_of_slot<D>(mask, row_ptr, a, (int)(t / g.nnodes));
+  const int slot = PS::CENTRE + (int)(t / g.nnodes);
+  const int64_t e = block_of_slot<D>(mask, row_ptr, a, slot);
   if (e < 0) return;
   constexpr int NB = D + 1;
   const int64_t n = v.n;
   const int64_t bn = col[e];
+  const bool diag = slot == PS::CENTRE;
   int ac[3], bc[3];
   node_coords(g, a, ac);
   node_coords(g, bn, bc);
@@ -815,8 +888,9 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
     lo[k] = max(l1, l2);
     hi[k] = min(h1, h2);
   }
-  R B[NB * NB];
-  for (int i = 0; i < NB * NB; ++i) B[i] = 0;
+  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], C = 0;
+  for (int i = 0; i < D * D; ++i) A[i] = 0;
+  for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = 0;
   const R cvis = DYN ? (R)(s.alpha_vis * s.gamma / (s.beta * s.dt)) : R(0);
   for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
     for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
@@ -824,7 +898,8 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
         const int64_t cid = cell_index(g, c0, c1, c2);
         for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
           int oa[3], ob[3];
-          if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
+          const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
+          if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) continue;
           R Sa, S0a, Gna[3], Sb, S0b, Gnb[3], ga[3], gb[3];
           basis_at_t<D, R>(BA, q, oa, a, Sa, S0a, Gna);
           basis_at_t<D, R>(BA, q, ob, bn, Sb, S0b, Gnb);
@@ -853,16 +928,16 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
             for (int k = 0; k < D; ++k) {
               const R dik = i == k ? R(1) : R(0);
               const R sym = mu * (dik * gab + ga[k] * gb[i]);
-              R A = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
-              A += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
+              R Aik = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
+              Aik += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
               if (DYN) {
-                A -= cs * cvis * (lam * ga[i] * gb[k] + sym);
-                A -= dik * ms;
+                Aik -= cs * cvis * (lam * ga[i] * gb[k] + sym);
+                Aik -= dik * ms;
               }
-              B[i * NB + k] += A;
+              A[i * D + k] += Aik;
             }
-          for (int i = 0; i < D; ++i) B[i * NB + D] += vol * ga[i] * Sb;
-          const R b2 = rec[RC_B2 * n + q];
+          const R b2 = rec[RC_B2 * n + q], dkv = rec[RC_DKV * n + q];
+          for (int i = 0; i < D; ++i) b1ab[i] += vol * ga[i] * Sb;
           for (int k = 0; k < D; ++k) {
             R t = Sa * b2 * gb[k];
             if (DYN) {
@@ -871,24 +946,44 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
               t -= vol * Sa * gbgv;
             }
             t += kv * (gb[k] * gaw - ga[k] * gbw - rec[(RC_GP + k) * n + q] * gab);
-            t += rec[RC_DKV * n + q] * gb[k] * gaw;  // dk/dJ (Kozeny-Carman)
-            B[D * NB + k] += t;
+            t += dkv * gb[k] * gaw;  // dk/dJ (Kozeny-Carman)
+            b2ab[k] += t;
           }
-          B[D * NB + D] += kv * gab + rec[RC_CST * n + q] * (Sa - S0a) * (Sb - S0b);
+          if (!diag) {
+            for (int i = 0; i < D; ++i) b1ba[i] += vol * gb[i] * Sa;
+            for (int k = 0; k < D; ++k) {
+              R t = Sb * b2 * ga[k];
+              if (DYN) {
+                R gagv = 0;
+                for (int j = 0; j < D; ++j) gagv += ga[j] * rec[(RC_GV + j * D + k) * n + q];
+                t -= vol * Sb * gagv;
+              }
+              t += kv * (ga[k] * gbw - gb[k] * gaw - rec[(RC_GP + k) * n + q] * gab);
+              t += dkv * ga[k] * gbw;
+              b2ba[k] += t;
+            }
+          }
+          C += kv * gab + rec[RC_CST * n + q] * (Sa - S0a) * (Sb - S0b);
         }
       }
-  if (apply_bc) {
-    constexpr int NBc = NB;
-    for (int i = 0; i < NBc; ++i) {
-      const bool fr = v.fixed[a * NBc + i] != 0;
-      for (int k = 0; k < NBc; ++k) {
-        const bool fc = v.fixed[bn * NBc + k] != 0;
-        if (fr || fc) B[i * NBc + k] = (a == bn && i == k) ? R(1) : R(0);
-      }
-    }
+  R B[NB * NB];
+  for (int i = 0; i < D; ++i) {
+    for (int k = 0; k < D; ++k) B[i * NB + k] = A[i * D + k];
+    B[i * NB + D] = b1ab[i];
+    B[D * NB + i] = b2ab[i];
   }
-  T *out = val + e * (NB * NB);
-  for (int i = 0; i < NB * NB; ++i) out[i] = (T)B[i];
+  B[D * NB + D] = C;
+  write_block_bc<D>(v, a, bn, B, val + e * (NB * NB), apply_bc);
+  if (diag) return;
+  const int64_t e2 = block_of_slot<D>(mask, row_ptr, bn, PS::NSLOT - 1 - slot);
+  if (e2 < 0) return;
+  for (int i = 0; i < D; ++i) {
+    for (int k = 0; k < D; ++k) B[i * NB + k] = A[k * D + i];
+    B[i * NB + D] = b1ba[i];
+    B[D * NB + i] = b2ba[i];
+  }
+  B[D * NB + D] = C;
+  write_block_bc<D>(v, bn, a, B, val + e2 * (NB * NB), apply_bc);
 }
 
 // ---------------------------------------------------------------- consistent-mass Stage 1
@@ -1302,30 +1397,46 @@ void run_residual(Ctx &c, const double *X, double *R, int apply_bc) {
   prof_end(c, MPM_PROF_RESIDUAL);
 }
 
+// FP32 copy of the staging (allocated for the staged FP32 variant only)
+int ensure_jacobian_staging32(Ctx &c) {
+  if (c.pn32) return MPM_OK;
+  if (cudaMalloc(&c.pn32, sizeof(float) * (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn, c.s.hencky) * c.n) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    c.pn32 = nullptr;
+    return MPM_ERR_NO_MEMORY;
+  }
+  return MPM_OK;
+}
+
+// One assembly with a given kernel configuration: staged (k_point_nodes then
+// k_jacobian on the per-(point, node) vectors) or direct (k_jacobian_direct),
+// tpb threads per block.  Values in precision T computed in precision T from
+// the FP64 records or their FP32 copies.
 template <typename T>
-void run_jacobian(Ctx &c, T *val, int apply_bc) {
-  prof_begin(c, MPM_PROF_JACOBIAN);
+void launch_jacobian(Ctx &c, T *val, int apply_bc, bool staged, int tpb) {
   const DevView v = c.view();
-  const int nbk = nblk((c.d == 2 ? 49 : 343) * c.g.nnodes, 128);
+  // the Jacobian kernels take symmetric pairs: half the offsets plus the centre
+  const int64_t nthr = (int64_t)(c.d == 2 ? PairSlots<2>::COUNT : PairSlots<3>::COUNT) * c.g.nnodes;
+  const int nbk_pair = (int)((nthr + tpb - 1) / tpb);
   const bool gimp = c.shape == MPM_SHAPE_GIMP;
-  // FP32 values are computed in FP32 from the FP32 copies; FP64 in FP64
   using R = T;
   BasisArrays<R> BA;
   BA.n = c.n;
   BA.cnt = c.sh_cnt;
   BA.act = c.act;
   const R *rec;
+  R *pn;
   if constexpr (sizeof(T) == sizeof(double)) {
     BA.S = (const R *)c.sh_S; BA.dS = (const R *)c.sh_dS; BA.S0 = (const R *)c.sh_S0;
     BA.nrm = (const R *)c.sh_nrm; rec = (const R *)c.rec;
+    pn = (R *)c.pn;
   } else {
     BA.S = (const R *)c.sh_Sf; BA.dS = (const R *)c.sh_dSf; BA.S0 = (const R *)c.sh_S0f;
     BA.nrm = (const R *)c.sh_nrmf; rec = (const R *)c.recf;
+    pn = (R *)c.pn32;
   }
-  // FP64: stage the per-(point, node) vectors, then assemble; FP32: direct
-  constexpr bool staged = sizeof(R) == sizeof(double);
-  if (staged && !c.pn) return;  // callers run ensure_jacobian_staging first
-  R *pn = (R *)c.pn;
+  if (staged && !pn) return;  // callers allocate the staging first
   if (staged) {
     const int npb = nblk((int64_t)pn_nslot(c.d) * c.n, TPB);
 #define PNODES(D, Y, H) k_point_nodes<D, Y, H, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn)
@@ -1343,14 +1454,14 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
 #define JAC(D, G, Y)                                                                                         \
   do {                                                                                                       \
     if (staged && c.s.hencky)                                                                                \
-      k_jacobian<D, G, Y, true, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr, c.col,  \
-                                                             val, apply_bc);                                 \
+      k_jacobian<D, G, Y, true, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr,    \
+                                                                  c.col, val, apply_bc);                     \
     else if (staged)                                                                                         \
-      k_jacobian<D, G, Y, false, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr, c.col, \
-                                                              val, apply_bc);                                \
+      k_jacobian<D, G, Y, false, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr,   \
+                                                                   c.col, val, apply_bc);                    \
     else                                                                                                     \
-      k_jacobian_direct<D, G, Y, T, R><<<nbk, 128, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask, c.row_ptr,   \
-                                                              c.col, val, apply_bc);                         \
+      k_jacobian_direct<D, G, Y, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask,         \
+                                                                   c.row_ptr, c.col, val, apply_bc);         \
   } while (0)
   if (c.d == 2) {
     if (gimp) { if (c.dyn) JAC(2, true, true); else JAC(2, true, false); }
@@ -1361,6 +1472,68 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
   }
 #undef JAC
   UPMPM_LAUNCH(c);
+}
+
+// Autotuner of the assembly: every candidate configuration is run twice on
+// the context's own data (the first run warms caches and page tables), the
+// second timed with CUDA events; the fastest is kept for the rest of the
+// context's life.  Candidates: 64, 128, 256 threads per block, and for FP32
+// also the staged variant (FP64 is always staged: recomputing the node
+// vectors per term costs FP64 issue slots, the bound of that kernel).  The
+// chosen configuration only moves work between threads (block size) or
+// stages exact copies (FP32 staging rounds the same products in a different
+// order), so the values agree to the precision's rounding.
+template <typename T>
+void autotune_jacobian(Ctx &c, T *val, int apply_bc) {
+  constexpr int pi = sizeof(T) == sizeof(double) ? 0 : 1;
+  Ctx::JacCfg &cfg = c.jac_cfg[pi];
+  const int tpbs[3] = {64, 128, 256};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  float best = 1e30f;
+  for (int k = 0; k < 6; ++k) c.stats.jac_tune_ms[pi][k] = 0.0f;
+  for (int st = 0; st < 2; ++st) {
+    const bool staged = st == 1;
+    if (pi == 0 && !staged) continue;
+    if (pi == 1 && staged && ensure_jacobian_staging32(c) != MPM_OK) continue;
+    for (int k = 0; k < 3; ++k) {
+      launch_jacobian<T>(c, val, apply_bc, staged, tpbs[k]);
+      cudaEventRecord(e0, c.st);
+      launch_jacobian<T>(c, val, apply_bc, staged, tpbs[k]);
+      cudaEventRecord(e1, c.st);
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+      c.stats.jac_tune_ms[pi][st * 3 + k] = ms;
+      if (ms < best) {
+        best = ms;
+        cfg.staged = staged;
+        cfg.tpb = tpbs[k];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cfg.tuned = 1;
+  if (pi == 1 && !cfg.staged && c.pn32) {  // not chosen: give the memory back
+    cudaFree(c.pn32);
+    c.pn32 = nullptr;
+  }
+}
+
+template <typename T>
+void run_jacobian(Ctx &c, T *val, int apply_bc) {
+  constexpr int pi = sizeof(T) == sizeof(double) ? 0 : 1;
+  Ctx::JacCfg &cfg = c.jac_cfg[pi];
+  if (c.opt.autotune && !cfg.tuned && !c.capturing) autotune_jacobian<T>(c, val, apply_bc);
+  if (pi == 1 && cfg.staged && ensure_jacobian_staging32(c) != MPM_OK) cfg.staged = 0;
+  c.stats.jac_config[pi] = cfg.tpb + (cfg.staged ? 1000 : 0);
+  c.stats.jac_tuned[pi] = cfg.tuned;
+  prof_begin(c, MPM_PROF_JACOBIAN);
+  launch_jacobian<T>(c, val, apply_bc, cfg.staged, cfg.tpb);
   prof_end(c, MPM_PROF_JACOBIAN);
 }
 

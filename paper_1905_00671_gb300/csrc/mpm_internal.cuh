@@ -42,14 +42,19 @@ struct LinSys {
   T *W = nullptr;      // B2_ac diag(A)_c^{-1} per block (d values), Schur set-up
   T *B1rs = nullptr;   // per node: sum over its row of the B1 blocks (d values)
   T *vu = nullptr;
+  T *B2c = nullptr;    // compact B2 (d values per block), lower-triangular order only
+  T *vp = nullptr;     // unscaled v_p, lower-triangular order only
   int64_t sub_cap = 0;
   // The multigrid part of the preconditioner application (both V-cycles and
   // the B1 update between them) captured as a CUDA graph; valid while the
   // matrix buffers it reads stay in place.  The graph reads the S-cycle's
-  // level-0 rhs and first iterate from g_bs0 / g_xs0 and leaves the results
+  // level-0 rhs and first iterate of the first sub-solve (the S-cycle in the
+  // upper-triangular order, the A-cycle in the lower one) from the buffers the
+  // split kernel fills, g_x0 being that first iterate, and leaves the results
   // in g_zp / g_zu (the hierarchies' vector buffers at capture time).
   cudaGraphExec_t gexec = nullptr;
-  T *g_xs0 = nullptr, *g_zp = nullptr, *g_zu = nullptr;
+  T *g_x0 = nullptr, *g_zp = nullptr, *g_zu = nullptr;
+  int g_lower = 0;     // order the graph was captured for
   const void *gkey_col = nullptr, *gkey_val = nullptr;
   int64_t gkernels = 0;
 };
@@ -158,6 +163,7 @@ struct DevView {
   int32_t *cell_start;      // ncells + 1
   int32_t *sh_first;        // 3 * n
   int32_t *sh_cnt;          // n, counts packed 4 bits per axis
+  int4 *sh_box;             // n: (first node per axis, sh_cnt) of each point in one 16-byte word
   double *sh_S, *sh_dS, *sh_S0;  // 12 * n each
   double *m;                // n mixture mass of the step
   double *rec;              // RC_COUNT * n
@@ -194,6 +200,11 @@ struct Ctx {
   bool fixed_stress() const {
     return opt.schur_approx == MPM_SCHUR_FIXED_STRESS || (opt.schur_approx == MPM_SCHUR_AUTO && !dyn);
   }
+  bool schur_lower() const { return opt.schur_order == MPM_SCHUR_LOWER; }
+  // multigrid smoothing: V(mg_sweeps, mg_sweeps) with damping mg_omega (the
+  // options' values, or the defaults 1 and 0.7 in 2D / 0.5 in 3D)
+  int mg_sweeps() const { return opt.mg_sweeps > 0 ? opt.mg_sweeps : 1; }
+  double mg_omega() const { return opt.mg_omega > 0.0 ? opt.mg_omega : (d == 3 ? 0.5 : 0.7); }
   // instances (batched contexts hold several; see mpm_create_batch)
   int ninst = 1;
   InstDev *inst = nullptr;             // device table
@@ -227,6 +238,7 @@ struct Ctx {
   int32_t *cell = nullptr, *cell_tmp = nullptr, *cell_start = nullptr, *cell_cursor = nullptr;
   int32_t *perm = nullptr;
   int32_t *sh_first = nullptr, *sh_cnt = nullptr;
+  int4 *sh_box = nullptr;
   double *sh_S = nullptr, *sh_dS = nullptr, *sh_S0 = nullptr;
   double *m = nullptr, *rec = nullptr;
   double *M = nullptr, *Pn = nullptr, *vn = nullptr, *an = nullptr, *pdn = nullptr, *pddn = nullptr;
@@ -248,7 +260,16 @@ struct Ctx {
   // per-(point, support node) vectors of the FP64 Jacobian (pn_nslot(d)
   // records of PN_NPF values per point)
   double *pn = nullptr;
+  float *pn32 = nullptr;                 // the same in FP32 (the staged FP32 variant)
   unsigned long long *h_terms = nullptr; // pinned copy
+  // Jacobian kernel configuration per precision ([0] FP64, [1] FP32): staged
+  // (per-(point, node) vectors formed first) or direct (recomputed per term),
+  // and threads per block.  Fixed defaults, or chosen by timing every
+  // candidate at the context's first assembly when mpm_options.autotune is set.
+  struct JacCfg {
+    int staged, tpb, tuned;
+  };
+  JacCfg jac_cfg[2] = {{1, 128, 0}, {0, 128, 0}};
 
   // sparsity + matrix
   int32_t *row_nnz = nullptr, *row_ptr = nullptr, *row_of = nullptr, *col = nullptr;

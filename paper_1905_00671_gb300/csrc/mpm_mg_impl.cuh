@@ -233,6 +233,48 @@ __global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *
   xs0[a] = omega * (dinvs0[a] * vp);
 }
 
+// Lower-triangular order: v_u is the A-cycle's level-0 rhs, with its first
+// smoothing sweep from zero (x = omega Dinv_A v_u, a D x D block per node);
+// v_p is kept for the S-cycle's rhs v_p - B2 z_u.
+template <int D>
+__global__ void k_split_lower(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsc,
+                              real *__restrict__ ba0, real *__restrict__ xa0, const real *__restrict__ dinva0,
+                              real *__restrict__ vp, real omega) {
+  pdl_enter();
+  const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (a >= nnodes) return;
+  real vu[D];
+  for (int k = 0; k < D; ++k) {
+    vu[k] = v[a * (D + 1) + k] / dsc[a * (D + 1) + k];
+    ba0[a * D + k] = vu[k];
+  }
+  for (int i = 0; i < D; ++i) {
+    real sv = 0.0;
+    for (int j = 0; j < D; ++j) sv = fma(dinva0[a * D * D + i * D + j], vu[j], sv);
+    xa0[a * D + i] = omega * sv;
+  }
+  vp[a] = v[a * (D + 1) + D] / dsc[a * (D + 1) + D];
+}
+
+// Compact unscaled B2 (row D, u columns, of the unscaled J): D values per block.
+template <int D>
+__global__ void k_extract_B2(int64_t nnzb, const real *__restrict__ J, real *__restrict__ B2) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  constexpr int NB = D + 1;
+  for (int k = 0; k < D; ++k) B2[e * D + k] = J[e * NB * NB + D * NB + k];
+}
+
+// w_p = v_p - B2 z_u with the compact unscaled B2: the S-cycle's level-0 rhs,
+// with its first smoothing sweep from zero (x = omega Dinv_S w_p).  B1C_LANES
+// lanes per row.
+template <int D>
+__global__ void k_b2c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const real *__restrict__ B2,
+                             const real *__restrict__ zu, const real *__restrict__ vp,
+                             real *__restrict__ bs0, real *__restrict__ xs0,
+                             const real *__restrict__ dinvs0, real omega);
+
 // Compact unscaled B1 (column D of the u rows of the unscaled J): D values
 // per block instead of the whole (D+1)^2 block.
 template <int D>
@@ -280,6 +322,33 @@ __global__ void k_b1c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr
   }
   ba0[a * D + lane] = wi;
   xa0[a * D + lane] = omega * s;
+}
+
+template <int D>
+__global__ void k_b2c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col, const real *__restrict__ B2,
+                             const real *__restrict__ zu, const real *__restrict__ vp,
+                             real *__restrict__ bs0, real *__restrict__ xs0,
+                             const real *__restrict__ dinvs0, real omega) {
+  pdl_enter();
+  constexpr int LN = B1C_LANES;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t a = t / LN;
+  const int lane = (int)(t % LN);
+  const bool valid = a < nnodes;
+  real acc = 0;
+  if (valid) {
+    const int e1 = row_ptr[a + 1];
+    for (int e = row_ptr[a] + lane; e < e1; e += LN) {
+      const int64_t b = col[e];
+      for (int k = 0; k < D; ++k) acc = fma(B2[(int64_t)e * D + k], zu[b * D + k], acc);
+    }
+  }
+  for (int o = LN / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (!valid || lane != 0) return;
+  const real w = vp[a] - acc;
+  bs0[a] = w;
+  xs0[a] = omega * (dinvs0[a] * w);
 }
 
 template <int D>
@@ -743,7 +812,7 @@ __global__ void k_mg_prolong(LevelDev F, LevelDev Cl, real *__restrict__ xf,
 // of launch and drain for very little work; one block of 1024 threads runs the
 // whole tail (every level below a size limit down to the dense coarsest
 // solve) with a block barrier between the phases.  Same operations and order
-// of levels as the kernel-per-phase V(2,2) cycle.
+// of levels as the kernel-per-phase V(k, k) cycle.
 constexpr int TAIL_MAX_LEVELS = 8;
 constexpr int TAIL_MAX_NODES = 128;  // one pass of the block per phase: larger levels are latency-bound here
 constexpr int TAIL_THREADS = 1024;
@@ -758,6 +827,7 @@ struct TailArgs {
   const real *Ai;
   int ncoarse;
   real omega;
+  int nsw;  // sweeps before and after the coarse correction
 };
 
 template <int B, int D, bool SMOOTH>
@@ -798,9 +868,11 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs A) {
   }
   for (int l = 0; l + 1 < A.nl; ++l) {
     const LevelDev &L = A.lv[l].L, &Ln = A.lv[l + 1].L;
-    tail_rows<B, D, true>(L, xs[l], x2s[l], A.lv[l].b, A.omega);  // second pre-smoothing sweep
-    __syncthreads();
-    real *t = xs[l]; xs[l] = x2s[l]; x2s[l] = t;
+    for (int k = 1; k < A.nsw; ++k) {  // pre-smoothing sweeps after the first (from zero)
+      tail_rows<B, D, true>(L, xs[l], x2s[l], A.lv[l].b, A.omega);
+      __syncthreads();
+      real *t = xs[l]; xs[l] = x2s[l]; x2s[l] = t;
+    }
     tail_rows<B, D, false>(L, xs[l], A.lv[l].r, A.lv[l].b, A.omega);
     __syncthreads();
     real *xc = l + 2 < A.nl ? xs[l + 1] : nullptr;  // first sweep from zero of the next level
@@ -851,7 +923,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs A) {
       for (int i = 0; i < B; ++i) xs[l][a * B + i] += acc[i];
     }
     __syncthreads();
-    for (int k = 0; k < 2; ++k) {  // post-smoothing sweeps
+    for (int k = 0; k < A.nsw; ++k) {  // post-smoothing sweeps
       tail_rows<B, D, true>(L, xs[l], x2s[l], A.lv[l].b, A.omega);
       __syncthreads();
       real *t = xs[l]; xs[l] = x2s[l]; x2s[l] = t;
@@ -927,7 +999,7 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
               }
         }
   }
-  for (int i = 0; i < B * B; ++i) Cl.sval[t * B * B + i] = acc[i];
+  for (int i = 0; i < B * B; ++i) Cl.sval[(I * NS + s) * B * B + i] = acc[i];
 }
 
 // Galerkin product of the block-CSR finest level in two passes (the fine
@@ -935,9 +1007,9 @@ __global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
 //   k_mg_ap:   T_a(J) = sum_b w_bJ A_ab over the children b of J, for every
 //              fine row a and coarse node J of the 5^d window centred on
 //              floor(a / 2) (the coarse nodes a row can reach); thread per
-//              (a, window slot);
+//              (window slot, a), T stored slot-major;
 //   k_mg_rap2: A_c(I, J) = sum_a w_aI T_a(J) over the 3^d children a of I;
-//              thread per (I, stencil slot).
+//              thread per (stencil slot, I).
 // Same masks as the one-pass product (Dirichlet DOFs out of the transfers,
 // instances kept apart), grouped as (P^T (A P)): a few lookups and FMAs per
 // coarse entry instead of one per (a, b) pair.
@@ -946,8 +1018,11 @@ __global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
   constexpr int NS = NS_<D>::v;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= F.nnodes * NS) return;
-  const int64_t a = t / NS;
-  const int s = (int)(t % NS);
+  // slot-major: the lanes of a warp take one window slot of consecutive fine
+  // rows (the same loop bounds up to the parity of a), and T is stored
+  // slot-major ([s][a]) so that their results are written side by side
+  const int64_t a = t % F.nnodes;
+  const int s = (int)(t / F.nnodes);
   int fa[3], Jc[3];
   grid_xyz(F.nn[0], F.nn[1], (int)a, fa);
   Jc[0] = (fa[0] >> 1) + s % 5 - 2;
@@ -980,7 +1055,7 @@ __global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
           }
         }
   }
-  for (int i = 0; i < B * B; ++i) T[t * B * B + i] = acc[i];
+  for (int i = 0; i < B * B; ++i) T[t * B * B + i] = acc[i];  // t = s * nnodes + a
 }
 
 template <int B, int D>
@@ -988,8 +1063,11 @@ __global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
   constexpr int NS = NS_<D>::v;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= Cl.nnodes * NS) return;
-  const int64_t I = t / NS;
-  const int s = (int)(t % NS);
+  // slot-major as k_mg_ap: the lanes take consecutive coarse nodes I of one
+  // stencil slot, so a child a = 2 I + d of every lane reads the same window
+  // slot of T at every other fine row
+  const int64_t I = t % Cl.nnodes;
+  const int s = (int)(t / Cl.nnodes);
   int Ic[3], Jc[3];
   grid_xyz(Cl.nn[0], Cl.nn[1], (int)I, Ic);
   Jc[0] = Ic[0] + s % 5 - 2;
@@ -1012,14 +1090,14 @@ __global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
           if (F.inst && F.inst[a] != Cl.inst[I]) continue;
           const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
           const int sl = (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0);
-          const real *ta = T + (a * NS + sl) * B * B;
+          const real *ta = T + ((int64_t)sl * F.nnodes + a) * B * B;
           for (int i = 0; i < B; ++i) {
             const real wi = wa * free_w(F, a, i);
             for (int j = 0; j < B; ++j) acc[i * B + j] = fma(wi, ta[i * B + j], acc[i * B + j]);
           }
         }
   }
-  for (int i = 0; i < B * B; ++i) Cl.sval[t * B * B + i] = acc[i];
+  for (int i = 0; i < B * B; ++i) Cl.sval[(I * NS + s) * B * B + i] = acc[i];
 }
 
 }  // namespace MG_NS
@@ -1085,12 +1163,13 @@ void dense_invert_pair(Ctx &c, MGHier<real> &H0, MGHier<real> &H1) {
 // while omega * lambda_max(Dinv A) < 2 on every level.  Measured lambda_max:
 // at most 2.5 for the plane-strain blocks of the strip footing (2D), 3.25 on
 // the 3D consolidation block and 3.5 next to the inclined free surface of the
-// 3D slope, where 0.6 made the V-cycle diverge (FGMRES at its cap; 14
-// iterations instead of 232 with 0.5 on a 32 x 32 x 16 slope).
-template <int D>
-constexpr real mg_omega() {
-  return D == 3 ? real(0.5) : real(0.6);
-}
+// 3D slope, where 0.6 made the V(2,2)-cycle diverge (FGMRES at its cap; 14
+// iterations instead of 232 with 0.5 on a 32 x 32 x 16 slope).  The default
+// cycle is V(1,1) (0.7 in 2D, 0.5 in 3D): on the full-size slope it took
+// fewer FGMRES iterations than V(2,2) at 0.56 of its cost per application,
+// and V(3,3) stalled there.
+// (the defaults of Ctx::mg_omega; mpm_options.mg_omega overrides them)
+inline real mg_omega(const Ctx &c) { return (real)c.mg_omega(); }
 
 // one damped block-Jacobi sweep on level l: x <- x + omega Dinv (b - A x)
 template <int B, int D>
@@ -1100,22 +1179,23 @@ void sweep(Ctx &c, MGHier<real> &H, int l) {
     constexpr int SPL = B <= 2 ? 4 / B : 1;
     const Geom g = geom(c, L.nnodes * B * SPL);
     launch_pdl(c, k_mg_csr_row<B, SPL, true>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
-               (const real *)H.b[l], mg_omega<D>());
+               (const real *)H.b[l], mg_omega(c));
   } else {
     const Geom g = geom(c, L.nnodes * LN_<D>::v);
     if (l == 0)
       launch_pdl(c, k_mg_smooth<B, D, false>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
-                 (const real *)H.b[l], mg_omega<D>(), 0);
+                 (const real *)H.b[l], mg_omega(c), 0);
     else
       launch_pdl(c, k_mg_smooth<B, D, true>, g.blocks, g.tpb, 0, L, (const real *)H.x[l], H.x2[l],
-                 (const real *)H.b[l], mg_omega<D>(), 0);
+                 (const real *)H.b[l], mg_omega(c), 0);
   }
   std::swap(H.x[l], H.x2[l]);
 }
 
-// V(2,2)-cycle on level l.  On entry b[l] holds the rhs and x[l] the first
-// pre-smoothing sweep from zero (omega Dinv b, pointwise), done by the kernel
-// that produced b[l]; on return x[l] holds the result.
+// V(k,k)-cycle on level l (k = c.mg_sweeps(), default 2).  On entry b[l]
+// holds the rhs and x[l] the first pre-smoothing sweep from zero (omega Dinv
+// b, pointwise), done by the kernel that produced b[l]; on return x[l] holds
+// the result.
 template <int B, int D>
 void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
   if (sizeof(real) == sizeof(float) && l >= 1 && l < H.nlev - 1 && H.L[l].nnodes <= TAIL_MAX_NODES &&
@@ -1125,9 +1205,10 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
     for (int k = 0; k < A.nl; ++k) A.lv[k] = TailLevel{H.L[l + k], H.x[l + k], H.x2[l + k], H.b[l + k], H.r[l + k]};
     A.Ai = H.Ai;
     A.ncoarse = H.ncoarse;
-    A.omega = mg_omega<D>();
+    A.omega = mg_omega(c);
+    A.nsw = c.mg_sweeps();
     launch_pdl(c, k_mg_tail<B, D>, 1, TAIL_THREADS, 0, A);
-    // three sweeps per level swapped x and x2 (as sweep() does on the host)
+    // 2 nsw - 1 sweeps per level (odd) swapped x and x2 (as sweep() does on the host)
     for (int k = l; k < H.nlev - 1; ++k) std::swap(H.x[k], H.x2[k]);
     return;
   }
@@ -1138,13 +1219,13 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
   }
   LevelDev &L = H.L[l], &Ln = H.L[l + 1];
   real *xn_first = l + 1 == H.nlev - 1 ? nullptr : H.x[l + 1];
-  sweep<B, D>(c, H, l);  // second pre-smoothing sweep
+  for (int k = 1; k < c.mg_sweeps(); ++k) sweep<B, D>(c, H, l);  // pre-smoothing after the first
   const Geom gr = geom(c, L.nnodes * LN_<D>::v), gc = geom(c, Ln.nnodes), gf = geom(c, L.nnodes);
   if (l == 0 && B <= 2) {
     constexpr int SPL = B <= 2 ? 4 / B : 1;
     const Geom g0 = geom(c, L.nnodes * B * SPL);
     launch_pdl(c, k_mg_csr_row<B, SPL, false>, g0.blocks, g0.tpb, 0, L, (const real *)H.x[l], H.r[l],
-               (const real *)H.b[l], mg_omega<D>());
+               (const real *)H.b[l], mg_omega(c));
   } else if (l == 0) {
     launch_pdl(c, k_mg_resid<B, D, false>, gr.blocks, gr.tpb, 0, L, (const real *)H.x[l], (const real *)H.b[l],
                H.r[l]);
@@ -1153,11 +1234,10 @@ void vcycle_t(Ctx &c, MGHier<real> &H, int l) {
                H.r[l]);
   }
   launch_pdl(c, k_mg_restrict<B, D>, gc.blocks, gc.tpb, 0, L, Ln, (const real *)H.r[l], H.b[l + 1], xn_first,
-             mg_omega<D>());
+             mg_omega(c));
   vcycle_t<B, D>(c, H, l + 1);
   launch_pdl(c, k_mg_prolong<B, D>, gf.blocks, gf.tpb, 0, L, Ln, H.x[l], (const real *)H.x[l + 1]);
-  sweep<B, D>(c, H, l);  // first post-smoothing sweep
-  sweep<B, D>(c, H, l);  // second post-smoothing sweep
+  for (int k = 0; k < c.mg_sweeps(); ++k) sweep<B, D>(c, H, l);  // post-smoothing sweeps
 }
 
 // Allocate a hierarchy for block size B over the grid's node lattice; level 0
@@ -1298,7 +1378,7 @@ int schur_alloc<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
   if (!rc) rc = mg_alloc(c, *S.mgS, 1);
   if (rc) return rc;
   if (cudaMalloc(&S.DAinv, sizeof(real) * nn * d * d) || cudaMalloc(&S.vu, sizeof(real) * nn * d) ||
-      cudaMalloc(&S.B1rs, sizeof(real) * nn * d))
+      cudaMalloc(&S.B1rs, sizeof(real) * nn * d) || (c.schur_lower() && cudaMalloc(&S.vp, sizeof(real) * nn)))
     return MPM_ERR_NO_MEMORY;
   return MPM_OK;
 }
@@ -1308,13 +1388,13 @@ void schur_free<MG_REAL>(LinSys<MG_REAL> &S) {
   using namespace MG_NS;
   if (S.mgA) { mg_free(*S.mgA); delete S.mgA; S.mgA = nullptr; }
   if (S.mgS) { mg_free(*S.mgS); delete S.mgS; S.mgS = nullptr; }
-  MG_REAL *ptrs[] = {S.Aval, S.Sval, S.B1c, S.W, S.B1rs, S.DAinv, S.vu};
+  MG_REAL *ptrs[] = {S.Aval, S.Sval, S.B1c, S.W, S.B1rs, S.DAinv, S.vu, S.B2c, S.vp};
   for (MG_REAL *p : ptrs) cudaFree(p);
-  S.Aval = S.Sval = S.B1c = S.W = S.B1rs = S.DAinv = S.vu = nullptr;
+  S.Aval = S.Sval = S.B1c = S.W = S.B1rs = S.DAinv = S.vu = S.B2c = S.vp = nullptr;
   if (S.gexec) cudaGraphExecDestroy(S.gexec);
   S.gexec = nullptr;
   S.gkey_col = S.gkey_val = nullptr;
-  S.g_xs0 = S.g_zp = S.g_zu = nullptr;
+  S.g_x0 = S.g_zp = S.g_zu = nullptr;
   S.sub_cap = 0;
 }
 
@@ -1330,12 +1410,13 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
     // the finest multigrid level): drop it, it is re-captured on next use
     if (S.gexec) cudaGraphExecDestroy(S.gexec);
     S.gexec = nullptr;
-    MG_REAL *ptrs[] = {S.Aval, S.Sval, S.B1c, S.W};
+    MG_REAL *ptrs[] = {S.Aval, S.Sval, S.B1c, S.W, S.B2c};
     for (MG_REAL *p : ptrs) cudaFree(p);
-    S.Aval = S.Sval = S.B1c = S.W = nullptr;
+    S.Aval = S.Sval = S.B1c = S.W = S.B2c = nullptr;
     const int64_t cap = c.nnzb_cap;
     if (cudaMalloc(&S.Aval, sizeof(real) * cap * d * d) || cudaMalloc(&S.Sval, sizeof(real) * cap) ||
-        cudaMalloc(&S.B1c, sizeof(real) * cap * d) || cudaMalloc(&S.W, sizeof(real) * cap * d)) {
+        cudaMalloc(&S.B1c, sizeof(real) * cap * d) || cudaMalloc(&S.W, sizeof(real) * cap * d) ||
+        (c.schur_lower() && cudaMalloc(&S.B2c, sizeof(real) * cap * d))) {
       S.sub_cap = 0;
       c.last_error = "device allocation of the block preconditioner failed";
       return MPM_ERR_NO_MEMORY;
@@ -1373,36 +1454,66 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
     k_schur_lump<3><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.W, S.B1rs, S.Sval);
   }
   if (!c.fixed_stress()) c.launches += 6;
+  if (c.schur_lower()) {
+    if (d == 2) k_extract_B2<2><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B2c);
+    else k_extract_B2<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B2c);
+    c.launches += 1;
+  }
   mg_setup(c, *S.mgA, c.row_ptr, c.col, S.Aval, 0);
   mg_setup(c, *S.mgS, c.row_ptr, c.col, S.Sval, d);
   dense_invert_pair(c, *S.mgA, *S.mgS);
   return check_cuda(c, cudaGetLastError(), "schur setup");
 }
 
-// z = M^{-1} v (block upper triangular, multigrid sub-solves) in three parts:
-// split (v -> v_u and the S-cycle's rhs), the multigrid core (S-cycle, B1
-// update, A-cycle), merge (-> z).
+// z = M^{-1} v (block triangular, multigrid sub-solves) in three parts:
+// split (v -> the first sub-solve's rhs and first sweep, and the other
+// block's part of v), the multigrid core (first V-cycle, coupling update,
+// second V-cycle), merge (-> z).  Upper order: S-cycle, B1 update, A-cycle;
+// lower order: A-cycle, B2 update, S-cycle.
 namespace MG_NS {
-void schur_split(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *xs0) {
+// x0: where the first sub-solve's first sweep goes (its hierarchy's x[0])
+void schur_split(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *x0) {
   const int64_t nn = c.g.nnodes;
-  MGHier<real> &HS = *S.mgS;
+  MGHier<real> &HS = *S.mgS, &HA = *S.mgA;
   const Geom g = geom(c, nn);
-  const real *dsc = S.dscale, *dinv = HS.L[0].dinv;
-  if (c.d == 2) launch_pdl(c, k_split<2>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, mg_omega<2>());
-  else launch_pdl(c, k_split<3>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], xs0, dinv, mg_omega<3>());
+  const real *dsc = S.dscale;
+  const real om = mg_omega(c);
+  if (c.schur_lower()) {
+    const real *dinv = HA.L[0].dinv;
+    if (c.d == 2) launch_pdl(c, k_split_lower<2>, g.blocks, g.tpb, 0, nn, v, dsc, HA.b[0], x0, dinv, S.vp, om);
+    else launch_pdl(c, k_split_lower<3>, g.blocks, g.tpb, 0, nn, v, dsc, HA.b[0], x0, dinv, S.vp, om);
+    return;
+  }
+  const real *dinv = HS.L[0].dinv;
+  if (c.d == 2) launch_pdl(c, k_split<2>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], x0, dinv, om);
+  else launch_pdl(c, k_split<3>, g.blocks, g.tpb, 0, nn, v, dsc, S.vu, HS.b[0], x0, dinv, om);
 }
+
+// x0 of the hierarchy whose V-cycle comes first
+MG_REAL *schur_first_x0(Ctx &c, LinSys<MG_REAL> &S) { return c.schur_lower() ? S.mgA->x[0] : S.mgS->x[0]; }
 
 void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
   const int64_t nn = c.g.nnodes;
   MGHier<real> &HS = *S.mgS, &HA = *S.mgA;
-  mg_vcycle(c, HS);
   const Geom g = geom(c, nn * B1C_LANES);
   const int32_t *rp = c.row_ptr, *cl = c.col;
+  const real om = mg_omega(c);
+  if (c.schur_lower()) {
+    mg_vcycle(c, HA);
+    const real *b2 = S.B2c, *zu = HA.x[0], *vp = S.vp, *dinv = HS.L[0].dinv;
+    if (c.d == 2)
+      launch_pdl(c, k_b2c_update<2>, g.blocks, g.tpb, 0, nn, rp, cl, b2, zu, vp, HS.b[0], HS.x[0], dinv, om);
+    else
+      launch_pdl(c, k_b2c_update<3>, g.blocks, g.tpb, 0, nn, rp, cl, b2, zu, vp, HS.b[0], HS.x[0], dinv, om);
+    mg_vcycle(c, HS);
+    return;
+  }
+  mg_vcycle(c, HS);
   const real *b1 = S.B1c, *zp = HS.x[0], *vu = S.vu, *dinv = HA.L[0].dinv;
   if (c.d == 2)
-    launch_pdl(c, k_b1c_update<2>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, mg_omega<2>());
+    launch_pdl(c, k_b1c_update<2>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, om);
   else
-    launch_pdl(c, k_b1c_update<3>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, mg_omega<3>());
+    launch_pdl(c, k_b1c_update<3>, g.blocks, g.tpb, 0, nn, rp, cl, b1, zp, vu, HA.b[0], HA.x[0], dinv, om);
   mg_vcycle(c, HA);
 }
 
@@ -1424,12 +1535,13 @@ void schur_merge(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *zu, const MG_REAL *z
 template <>
 void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *z) {
   using namespace MG_NS;
-  if (!c.capturing && (!S.gexec || S.gkey_col != c.col || S.gkey_val != S.val)) {
+  if (!c.capturing && (!S.gexec || S.gkey_col != c.col || S.gkey_val != S.val ||
+                       S.g_lower != (int)c.schur_lower())) {
     if (S.gexec) cudaGraphExecDestroy(S.gexec);
     S.gexec = nullptr;
     cudaGraph_t graph = nullptr;
     const int64_t before = c.launches;
-    MG_REAL *xs0 = S.mgS->x[0];
+    MG_REAL *x0 = schur_first_x0(c, S);
     bool ok = cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
       c.capturing = true;
@@ -1442,7 +1554,8 @@ void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL 
     S.gkernels = c.launches - before;
     c.launches = before;
     if (ok) {
-      S.g_xs0 = xs0;
+      S.g_x0 = x0;
+      S.g_lower = (int)c.schur_lower();
       S.g_zp = S.mgS->x[0];
       S.g_zu = S.mgA->x[0];
       S.gkey_col = c.col;
@@ -1453,13 +1566,13 @@ void schur_apply<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL 
     }
   }
   if (S.gexec && !c.capturing) {
-    schur_split(c, S, v, S.g_xs0);
+    schur_split(c, S, v, S.g_x0);
     cudaGraphLaunch(S.gexec, c.st);
     c.launches += S.gkernels;
     schur_merge(c, S, S.g_zu, S.g_zp, z);
     return;
   }
-  schur_split(c, S, v, S.mgS->x[0]);
+  schur_split(c, S, v, schur_first_x0(c, S));
   schur_core(c, S);
   schur_merge(c, S, S.mgA->x[0], S.mgS->x[0], z);
 }

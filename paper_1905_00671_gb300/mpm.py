@@ -26,6 +26,7 @@ MPM_PERM_CONSTANT, MPM_PERM_KOZENY_CARMAN = 0, 1
 MPM_P2G_LUMPED, MPM_P2G_CONSISTENT = 0, 1
 MPM_MODEL_NEOHOOKE, MPM_MODEL_HENCKY = 0, 1
 MPM_PRECOND_BLOCK_JACOBI, MPM_PRECOND_SCHUR_MG = 0, 1
+MPM_SCHUR_LOWER, MPM_SCHUR_UPPER = 0, 1
 MPM_MAX_NEWTON = 64
 PROF = {"spmv": 0, "jacobian": 1, "residual": 2, "point": 3, "orth": 4, "p2g": 5, "g2p": 6,
         "precond": 7, "setup": 8, "prep": 9}
@@ -67,7 +68,8 @@ class mpm_options(C.Structure):
                 ("min_volume_fraction", C.c_double), ("profile", C.c_int32),
                 ("precond_lag", C.c_int32), ("schur_approx", C.c_int32), ("stream", C.c_void_p),
                 ("tau_kind", C.c_int32), ("permeability", C.c_int32), ("p2g_mass", C.c_int32),
-                ("model", C.c_int32)]
+                ("model", C.c_int32), ("schur_order", C.c_int32), ("mg_sweeps", C.c_int32),
+                ("mg_omega", C.c_double), ("autotune", C.c_int32)]
 
 
 class mpm_loads(C.Structure):
@@ -89,7 +91,8 @@ class mpm_stats(C.Structure):
                 ("steps", C.c_int64), ("t", C.c_double), ("nnzb", C.c_int64),
                 ("kernel_launches", C.c_int64), ("prof_ms", C.c_double * 10),
                 ("prof_launches", C.c_int64 * 10), ("jac_terms", C.c_int64),
-                ("jac_point_nodes", C.c_int64)]
+                ("jac_point_nodes", C.c_int64), ("jac_config", C.c_int32 * 2),
+                ("jac_tuned", C.c_int32 * 2), ("jac_tune_ms", (C.c_float * 6) * 2)]
 
 
 _lib = None
@@ -318,7 +321,9 @@ class Simulation:
                 "steps": s.steps, "t": s.t, "nnzb": s.nnzb, "kernel_launches": s.kernel_launches,
                 "prof_ms": {k: s.prof_ms[i] for k, i in PROF.items()},
                 "prof_launches": {k: s.prof_launches[i] for k, i in PROF.items()},
-                "jac_terms": s.jac_terms, "jac_point_nodes": s.jac_point_nodes}
+                "jac_terms": s.jac_terms, "jac_point_nodes": s.jac_point_nodes,
+                "jac_config": list(s.jac_config), "jac_tuned": list(s.jac_tuned),
+                "jac_tune_ms": [list(r) for r in s.jac_tune_ms]}
 
     # -- inspection
     def debug_bin(self):

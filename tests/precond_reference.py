@@ -9,19 +9,21 @@ Algorithm (as in the library):
   * S = C - B2 diag_blocks(A)^{-1} B1 kept on the block sparsity of J, the
     dropped part of every row added to its diagonal; or (fixed stress) S = C
     plus a given lumped term fs on the diagonal of the free pressure rows;
-  * z_p = V(S) v_p,  z_u = V(A) (v_u - B1 z_p), preconditioner of the scaled
-    system  z = D^{-1} M^{-1} (D^{-1} v);
+  * z_p = V(S) v_p,  z_u = V(A) (v_u - B1 z_p) (upper order), or
+    z_u = V(A) v_u,  z_p = V(S) (v_p - B2 z_u) (lower order); preconditioner
+    of the scaled system  z = D^{-1} M^{-1} (D^{-1} v);
   * V-cycle: factor-2 vertex coarsening per axis ((n + 1) // 2 nodes) while
     every axis has more than 2 nodes and the level more than 64 nodes,
     bilinear P (rows of Dirichlet / inactive DOFs zeroed on the finest level),
-    Galerkin P^T A P, damped block Jacobi (omega 0.6 in 2D, 0.5 in 3D,
-    2 + 2 sweeps, first sweep from zero), exact solve on the coarsest level.
+    Galerkin P^T A P, damped block Jacobi (omega 0.7 in 2D, 0.5 in 3D by
+    default, k + k sweeps with k = 1 by default, first sweep from zero),
+    exact solve on the coarsest level.
 """
 import numpy as np
 import scipy.sparse as sps
 
-OMEGA = {2: 0.6, 3: 0.5}   # smoother damping per dimension
-PRE, POST = 2, 2
+OMEGA = {2: 0.7, 3: 0.5}   # smoother damping per dimension
+PRE, POST = 1, 1
 
 
 def prolong_1d(nf):
@@ -53,13 +55,14 @@ def block_inv(A, B):
     return sps.block_diag(out, format="csr")
 
 
-def hierarchy(A, nn, dim, B, free):
+def hierarchy(A, nn, dim, B, free, omega=None, sweeps=None):
     levels = []
     cur = A.tocsr()
     nnc = list(nn)
     first = True
     while True:
-        lev = {"A": cur, "Dinv": block_inv(cur, B), "omega": OMEGA[dim]}
+        lev = {"A": cur, "Dinv": block_inv(cur, B), "omega": OMEGA[dim] if omega is None else omega,
+               "sweeps": (PRE, POST) if sweeps is None else (sweeps, sweeps)}
         levels.append(lev)
         if min(nnc[:dim]) <= 2 or int(np.prod(nnc)) <= 64 or len(levels) >= 15:
             break
@@ -85,12 +88,13 @@ def vcycle(levels, b, l=0):
     A, Dinv, om = levels[l]["A"], levels[l]["Dinv"], levels[l]["omega"]
     if l == len(levels) - 1:
         return np.linalg.solve(A.toarray(), b)
+    pre, post = levels[l].get("sweeps", (PRE, POST))
     x = om * (Dinv @ b)
-    for _ in range(PRE - 1):
+    for _ in range(pre - 1):
         x = x + om * (Dinv @ (b - A @ x))
     P = levels[l]["P"]
     x = x + P @ vcycle(levels, P.T @ (b - A @ x), l + 1)
-    for _ in range(POST):
+    for _ in range(post):
         x = x + om * (Dinv @ (b - A @ x))
     return x
 
@@ -99,7 +103,7 @@ class SchurMG:
     """Preconditioner of D J D for the unscaled block-CSR Jacobian J (after
     Dirichlet elimination) with sparsity (row_ptr, col) and fixed-DOF mask."""
 
-    def __init__(self, J, row_ptr, col, fixed, nn, dim, fs=None):
+    def __init__(self, J, row_ptr, col, fixed, nn, dim, fs=None, lower=True, omega=None, sweeps=None):
         nb = dim + 1
         J = J.tocsr()
         N = J.shape[0]
@@ -112,6 +116,8 @@ class SchurMG:
         A = J[iu][:, iu].tocsr()
         self.B1 = J[iu][:, ip].tocsr()
         B2 = J[ip][:, iu].tocsr()
+        self.B2 = B2
+        self.lower = lower
         C = J[ip][:, ip].tocsr()
         if fs is not None:
             S = (C + sps.diags(np.where(fixed[ip], 0.0, fs))).tocsr()
@@ -122,13 +128,17 @@ class SchurMG:
             kept = prod.multiply(pat).tocsr()
             lump = np.asarray(prod.sum(axis=1)).ravel() - np.asarray(kept.sum(axis=1)).ravel()
             S = (C - kept - sps.diags(lump)).tocsr()
-        self.LA = hierarchy(A, nn, dim, dim, ~fixed[iu])
-        self.LS = hierarchy(S, nn, dim, 1, ~fixed[ip])
+        self.LA = hierarchy(A, nn, dim, dim, ~fixed[iu], omega, sweeps)
+        self.LS = hierarchy(S, nn, dim, 1, ~fixed[ip], omega, sweeps)
 
     def apply(self, v):
         vv = v / self.D
-        zp = vcycle(self.LS, vv[self.ip])
-        zu = vcycle(self.LA, vv[self.iu] - self.B1 @ zp)
+        if self.lower:
+            zu = vcycle(self.LA, vv[self.iu])
+            zp = vcycle(self.LS, vv[self.ip] - self.B2 @ zu)
+        else:
+            zp = vcycle(self.LS, vv[self.ip])
+            zu = vcycle(self.LA, vv[self.iu] - self.B1 @ zp)
         z = np.zeros_like(v)
         z[self.iu] = zu
         z[self.ip] = zp

@@ -1,8 +1,8 @@
 """GPU parity of the configurations the other parity files leave out, and the
 host-made failures of a step.
 
-  * the unstabilized switch (Eq. stab-term-ppp off) on the Sec. 5.1 column and
-    on a GIMP footing;
+  * the unstabilized switch (Eq. stab-term-ppp off) on a consolidation column
+    and on GIMP footings;
   * the strip footing under harmonic loading as the paper sets it up (Sec.
     5.2: Hencky, consistent mass, w = 3 - 3 cos(100 t) MPa) at full size, step
     by step against the oracle, and at the paper's tolerances through the
@@ -47,15 +47,21 @@ def rel(a, b):
 
 
 def _compare(w, got, ref, fields, where):
+    """1e-10 of each field's largest magnitude; for the fields stored as totals
+    (x, F, V, lp) 1e-10 of the largest change over the run, plus the rounding
+    of the stored totals themselves (8 ulp of their largest value): a change
+    smaller than that cannot be resolved in a stored total."""
+    eps = np.finfo(np.float64).eps
     for k in fields:
         r = ref[k].reshape(got[k].shape)
         if k in ("x", "F", "V", "lp"):       # the change over the run, not the offset
             base = {"x": w.x, "F": np.tile(np.eye(w.dim).reshape(-1), (w.n, 1)),
                     "V": w.vol, "lp": w.lp}[k].reshape(got[k].shape)
-            err = rel(got[k] - base, r - base)
+            bound = 1e-10 * np.abs(r - base).max() + 8 * eps * np.abs(base).max()
+            diff = np.abs(got[k] - r).max()
+            assert diff <= bound, (where, k, diff, bound)
         else:
-            err = rel(got[k], r)
-        assert err <= 1e-10, (where, k, err)
+            assert rel(got[k], r) <= 1e-10, (where, k, rel(got[k], r))
 
 
 def _fields(w):
@@ -63,8 +69,13 @@ def _fields(w):
 
 
 UNSTAB = {
-    # Sec. 5.1: 40 elements, 2 points per element, undrained first step
-    "paper-terzaghi-40-unstabilized": (lambda: I.paper_terzaghi(40, stabilize=False), 2),
+    # the 4 x 40 consolidation column (k = 1e-10 m^2, dt = 1 s): drained enough
+    # that the unstabilized equal-order system stays well posed.  (The Sec. 5.1
+    # column in its undrained first step is not a parity case: without the
+    # stabilization its checkerboard pressure mode is singular to round-off,
+    # which is the paper's point, so two correct solvers differ there by more
+    # than 1e-10.)
+    "terzaghi-4x40-unstabilized": (lambda: I.terzaghi_column(stabilize=False), 3),
     "footing2d-gimp-qs-unstabilized": (
         lambda: replace(I.small_footing(seed=9, dynamic=False, body=(20, 10), pad=2, dt=1.0),
                         stabilize=False), 2),

@@ -31,10 +31,24 @@ def mpm():
     return m
 
 
-@pytest.mark.parametrize("name", list(CASES))
-def test_preconditioner_matches_reference(mpm, name):
+# solver options of the preconditioner: (mpm_options, restatement keywords)
+VARIANTS = {
+    "default": ({}, {}),
+    "upper-v22": (dict(schur_order=1, mg_sweeps=2), dict(lower=False, sweeps=2)),
+    "v22-omega06": (dict(mg_sweeps=2, mg_omega=0.6), dict(sweeps=2, omega=0.6)),
+    "v33-upper": (dict(mg_sweeps=3, schur_order=1), dict(sweeps=3, lower=False)),
+}
+VARIANT_CASES = [(n, "default") for n in CASES] + [
+    ("footing2d-gimp-newmark", "upper-v22"), ("block3d-gimp-qs", "upper-v22"),
+    ("footing2d-gimp-newmark", "v22-omega06"), ("terzaghi-4x40", "v22-omega06"),
+    ("block3d-gimp-qs", "v33-upper")]
+
+
+@pytest.mark.parametrize("name,variant", VARIANT_CASES)
+def test_preconditioner_matches_reference(mpm, name, variant):
     w = CASES[name]()
-    sim = mpm.Simulation(w)
+    opts, ref_kw = VARIANTS[variant]
+    sim = mpm.Simulation(w, **opts)
     sim.debug_prepare()
     orc = O.Oracle(w)
     prep = orc.prepare(w.dt)
@@ -51,13 +65,13 @@ def test_preconditioner_matches_reference(mpm, name):
     fixed = orc.fixed_dofs(prep)
     J = orc.jacobian_matrix(prep, Jv, fixed)
     nn = [w.ncell[k] + 1 for k in range(w.dim)] + [1]
-    ref = SchurMG(J, prep["row_ptr"], prep["col"], fixed, nn, w.dim, fs=fs)
+    ref = SchurMG(J, prep["row_ptr"], prep["col"], fixed, nn, w.dim, fs=fs, **ref_kw)
     for trial in range(2):
         v = rng.standard_normal(orc.nn * nb)
         v[fixed] = 0.0
         z = sim.debug_precond(X, v)
         zr = ref.apply(v)
         err = np.abs(z - zr).max() / np.abs(zr).max()
-        assert err <= 1e-7, (name, trial, err)
+        assert err <= 1e-7, (name, variant, trial, err)
     sim.close()
 
