@@ -598,9 +598,10 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
   return (int64_t)row_ptr[a] + before;
 }
 
-// Staging of the FP64 Jacobian: one thread per (point, support slot) writes
-// the point's per-node record, so that each (point, a, b) term of the block
-// assembly is a short chain of FMAs.  With g = F^-T grad S (current
+// Staging of the Jacobian (FP64, and FP32 in the staged mixed form): the
+// point's per-node records (k_point_nodes below: PN_LANES lanes per point),
+// so that each (point, a, b) term of the block assembly is a short chain of
+// FMAs.  With g = F^-T grad S (current
 // configuration), St = S - S0 and the point's coefficients
 //   p0 = cs,  p1 = cs (1 + cv) G',
 //   p2 = vol p - cs (1 + cv) lambda,  p3 = cs (1 + cv) G' + vol p,
@@ -624,24 +625,10 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
 //                      + sum_{B != A} theta_AB gh_B (n_Ak n_Bl + n_Bk n_Al)),
 // gh_A = g . n_A.
 template <int D, bool DYN, bool HK, typename R>
-__global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
-                              R *__restrict__ pn) {
-  constexpr int NSL = pn_nslot(D);
-  constexpr int NPF = pn_npf(D, DYN, HK);
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__device__ inline void point_node_record(const GridP &g, const StepP &sp, const DevView &v,
+                                         const BasisArrays<R> &BA, const R *__restrict__ rec, int64_t q,
+                                         const int off[3], R *__restrict__ out) {
   const int64_t n = v.n;
-  if (t >= n * NSL) return;
-  const int64_t q = t / NSL;
-  const int s = (int)(t - q * NSL);
-  R *out = pn + t * NPF;
-  if (s == NSL - 1) {
-    for (int k = 0; k < D; ++k) out[9 + k] = rec[(RC_GP + k) * n + q];
-    return;
-  }
-  const int off[3] = {s % MAXS, (s / MAXS) % MAXS, s / (MAXS * MAXS)};
-  const int packed = v.sh_cnt[q];
-  for (int k = 0; k < 3; ++k)
-    if (off[k] >= (k < D ? unpack_cnt(packed, k) : 1)) return;
   const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
   const R cv = DYN ? (R)(sp.alpha_vis * sp.gamma / (sp.beta * sp.dt)) : R(0);
   const R csv = cs * (R(1) + cv);
@@ -747,6 +734,65 @@ __device__ inline void write_block_bc(const DevView &v, int64_t row, int64_t col
   }
 }
 
+// PNL lanes per point, each taking the point's support nodes PNL apart (the
+// box's own nodes only, not the 4^d slots of the record array), so that the
+// lanes of a warp are busy with the nodes that exist; lane 0 also writes the
+// point's own record (grad p, last slot).
+constexpr int PN_LANES = 16;
+template <int D, bool DYN, bool HK, typename R>
+__global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
+                              R *__restrict__ pn) {
+  constexpr int NSL = pn_nslot(D);
+  constexpr int NPS = pn_stride(D, DYN, HK, (int)sizeof(R));
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = v.n;
+  if (t >= n * PN_LANES) return;
+  const int64_t q = t / PN_LANES;
+  const int j = (int)(t - q * PN_LANES);
+  R *P = pn + q * NSL * NPS;
+  if (j == 0)
+    for (int k = 0; k < D; ++k) P[(NSL - 1) * NPS + 9 + k] = rec[(RC_GP + k) * n + q];
+  const int packed = v.sh_cnt[q];
+  const int c0 = unpack_cnt(packed, 0), c1 = D > 1 ? unpack_cnt(packed, 1) : 1,
+            c2 = D > 2 ? unpack_cnt(packed, 2) : 1;
+  const int nq = c0 * c1 * c2;
+  for (int sc = j; sc < nq; sc += PN_LANES) {
+    const int off[3] = {sc % c0, (sc / c0) % c1, sc / (c0 * c1)};
+    point_node_record<D, DYN, HK, R>(g, sp, v, BA, rec, q, off, P + (off[0] + MAXS * (off[1] + MAXS * off[2])) * NPS);
+  }
+}
+
+// One staged (point, node) record as the pair kernel reads it: in FP32 the
+// whole record is brought into registers with 16-byte vector loads (the FP32
+// kernel is bound by the load path, and a record read value by value costs a
+// memory transaction per value and lane); in FP64 (bound by the FP64 pipe) the
+// values are read where they are used.
+template <typename R, int NPS>
+struct PnRec {
+  static constexpr bool VEC = sizeof(R) == 4;
+  R v[VEC ? NPS : 1];
+  const R *p;
+  __device__ __forceinline__ void load(const R *__restrict__ src) {
+    if constexpr (VEC) {
+      static_assert(NPS % 4 == 0, "FP32 records are padded to 16 bytes");
+#pragma unroll
+      for (int i = 0; i < NPS / 4; ++i) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(src) + i);
+        v[4 * i] = x.x;
+        v[4 * i + 1] = x.y;
+        v[4 * i + 2] = x.z;
+        v[4 * i + 3] = x.w;
+      }
+    } else {
+      p = src;
+    }
+  }
+  __device__ __forceinline__ R operator[](int i) const {
+    if constexpr (VEC) return v[i];
+    else return p[i];
+  }
+};
+
 template <int D, bool GIMP, bool DYN, bool HK, typename T, typename R>
 __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn,
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
@@ -754,7 +800,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   using PS = PairSlots<D>;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   constexpr int NSL = pn_nslot(D);
-  constexpr int NPF = pn_npf(D, DYN, HK);
+  constexpr int NPS = pn_stride(D, DYN, HK, (int)sizeof(R));
   if (t >= (int64_t)PS::COUNT * g.nnodes) return;
   const int64_t a = t % g.nnodes;
   const int slot = PS::CENTRE + (int)(t / g.nnodes);
@@ -787,10 +833,11 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
           int oa[3], ob[3];
           const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
           if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) continue;
-          const R *P = pn + (int64_t)q * NSL * NPF;
-          const R *pa = P + (oa[0] + MAXS * (oa[1] + MAXS * oa[2])) * NPF;
-          const R *pb = P + (ob[0] + MAXS * (ob[1] + MAXS * ob[2])) * NPF;
-          const R *pp = P + (NSL - 1) * NPF;
+          const R *P = pn + (int64_t)q * NSL * NPS;
+          PnRec<R, NPS> pa, pb;
+          pa.load(P + (oa[0] + MAXS * (oa[1] + MAXS * oa[2])) * NPS);
+          pb.load(P + (ob[0] + MAXS * (ob[1] + MAXS * ob[2])) * NPS);
+          const R *pp = P + (NSL - 1) * NPS;
           R ga[3], gb[3];
           for (int j = 0; j < D; ++j) {
             ga[j] = pa[j];
@@ -1187,7 +1234,7 @@ __global__ void k_cm_init(int64_t nn, int K, const double *__restrict__ rhs, con
 // ============================================================== launchers
 int ensure_jacobian_staging(Ctx &c) {
   if (c.pn) return MPM_OK;
-  if (cudaMalloc(&c.pn, sizeof(double) * (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn, c.s.hencky) * c.n) !=
+  if (cudaMalloc(&c.pn, sizeof(double) * (int64_t)pn_nslot(c.d) * pn_stride(c.d, c.dyn, c.s.hencky, 8) * c.n) !=
       cudaSuccess) {
     c.pn = nullptr;
     c.last_error = "device allocation of the Jacobian staging failed";
@@ -1400,7 +1447,7 @@ void run_residual(Ctx &c, const double *X, double *R, int apply_bc) {
 // FP32 copy of the staging (allocated for the staged FP32 variant only)
 int ensure_jacobian_staging32(Ctx &c) {
   if (c.pn32) return MPM_OK;
-  if (cudaMalloc(&c.pn32, sizeof(float) * (int64_t)pn_nslot(c.d) * pn_npf(c.d, c.dyn, c.s.hencky) * c.n) !=
+  if (cudaMalloc(&c.pn32, sizeof(float) * (int64_t)pn_nslot(c.d) * pn_stride(c.d, c.dyn, c.s.hencky, 4) * c.n) !=
       cudaSuccess) {
     cudaGetLastError();
     c.pn32 = nullptr;
@@ -1438,7 +1485,7 @@ void launch_jacobian(Ctx &c, T *val, int apply_bc, bool staged, int tpb) {
   }
   if (staged && !pn) return;  // callers allocate the staging first
   if (staged) {
-    const int npb = nblk((int64_t)pn_nslot(c.d) * c.n, TPB);
+    const int npb = nblk((int64_t)PN_LANES * c.n, TPB);
 #define PNODES(D, Y, H) k_point_nodes<D, Y, H, R><<<npb, TPB, 0, c.st>>>(c.g, c.s, v, BA, rec, pn)
     const bool hk = c.s.hencky;
     if (c.d == 2) {

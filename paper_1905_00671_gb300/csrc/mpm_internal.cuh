@@ -71,6 +71,12 @@ __host__ __device__ constexpr int pn_npf(int d, bool dyn, bool hencky = false) {
   return (dyn ? 6 * d + 7 : 5 * d + 6) + (hencky ? d * d * d : 0);
 }
 __host__ __device__ constexpr int pn_nslot(int d) { return (d == 2 ? MAXS * MAXS : MAXS * MAXS * MAXS) + 1; }
+// Values per record as stored: pn_npf rounded up to 16 bytes (a multiple of 2
+// doubles or 4 floats), so that every record starts on a 16-byte boundary and
+// can be read with vector loads.
+__host__ __device__ constexpr int pn_stride(int d, bool dyn, bool hencky, int word) {
+  return (pn_npf(d, dyn, hencky) * word + 15) / 16 * 16 / word;
+}
 
 // ---- particle fields ------------------------------------------------------
 enum PField {
