@@ -96,8 +96,13 @@ def solver_opts(args):
 
 
 def make_workload(name):
+    """A named configuration; 'block3d-jit:AxBxC' is the 3D block on A x B x C
+    cells with its points jittered (the small case of the profiles)."""
     from paper_1905_00671_gb300 import inputs as I
 
+    if name.startswith("block3d-jit:"):
+        body = tuple(int(x) for x in name.split(":", 1)[1].split("x"))
+        return I.jittered(I.consolidation_block(body=body), seed=5, frac=0.15, shuffle=False, logk_spread=0.0)
     if name == "footing":
         return I.strip_footing()
     if name == "terzaghi":
@@ -227,11 +232,12 @@ def ncu_traffic(kernel, workload):
 # symmetric pair (A and C once, B1 and B2 for both), so a (point, a, b) term
 # with a != b costs F_pair per unordered pair and a diagonal term F_diag:
 #   F_diag = 2 (2d^2 + 6d + 1) + d + 1   (+ 2 (d + 1), Newmark)
-#   F_pair = F_diag + 8d                 (+ 2 (2d + 1) over F_diag's QS value, Newmark)
-# (the pair adds the d + 3d FMAs of the second block's B1 and B2).
+#   F_pair = F_diag + 6d                 (+ 2 (2d + 1) over F_pair's QS value, Newmark)
+# (the pair adds the d + 2d FMAs of the second block's B1 and B2; the grad p
+# part of B2, (p7 g_a.g_b) grad p, is accumulated once for both blocks).
 # {(dim, dynamic): (F_pair, F_diag, G)}.
-JAC_FLOPS = {(2, False): (61, 45, 43), (2, True): (71, 51, 52), (3, False): (102, 78, 77),
-             (3, True): (116, 86, 96)}
+JAC_FLOPS = {(2, False): (57, 45, 43), (2, True): (67, 51, 52), (3, False): (96, 78, 77),
+             (3, True): (110, 86, 96)}
 # Hencky elasticity adds, per pair and per diagonal term, the d^3 FMAs of
 # sum_l U_a,ikl g_b,l and, per (point, node), the staged U of its spectral
 # tangent: gh_A = g.n_A (d^2 FMAs), w_Akl = kappa_A gh_A n_Ak n_Al + sum_{B != A}

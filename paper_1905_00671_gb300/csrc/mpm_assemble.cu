@@ -582,10 +582,10 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
 // ---------------------------------------------------------------- Jacobian
 // Block values are written in precision T and computed in precision R: FP64
 // from the FP64 records, or FP32 from their FP32 copies in the mixed mode.
-// One thread per block (a, b), mapped offset-major: thread t takes coupling
-// offset slot s = t / nnodes (b - a in [-3, 3]^d) of row a = t % nnodes, so the
-// 32 lanes of a warp hold the same offset in 32 consecutive rows and walk the
-// same number of candidate cells; a slot absent from the row's pattern exits.
+// One thread per block (a, b) (per symmetric pair of blocks, below), mapped
+// so that the 32 lanes of a warp hold the same coupling offset (b - a in
+// [-3, 3]^d) in 32 consecutive rows and walk the same number of candidate
+// cells; a slot absent from the row's pattern exits.
 template <int D>
 __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                                         int64_t a, int s) {
@@ -719,6 +719,29 @@ struct PairSlots {
   static constexpr int COUNT = CENTRE + 1;  // slots >= CENTRE
 };
 
+// Thread -> (row a, pair slot), tiled: a tile of PAIR_ROWS consecutive rows
+// takes all the pair slots before the next tile, and the lanes of a warp hold
+// one slot in PAIR_ROWS consecutive rows.  The warps of a block and their
+// neighbours then walk the same candidate points for different offsets, so a
+// point's records are reused from L1 and L2 instead of being read again from
+// DRAM for every offset (slot-major over the whole grid, each offset swept the
+// whole point set).  Returns false past the last row.
+constexpr int PAIR_ROWS = 32;
+template <int D>
+__device__ inline bool pair_of_thread(const GridP &g, int64_t t, int64_t &a, int &slot) {
+  using PS = PairSlots<D>;
+  constexpr int64_t PER_TILE = (int64_t)PAIR_ROWS * PS::COUNT;
+  const int64_t tile = t / PER_TILE;
+  const int rem = (int)(t - tile * PER_TILE);
+  slot = PS::CENTRE + rem / PAIR_ROWS;
+  a = tile * PAIR_ROWS + rem % PAIR_ROWS;
+  return a < g.nnodes;
+}
+inline int64_t pair_threads(int d, int64_t nnodes) {
+  const int64_t tiles = (nnodes + PAIR_ROWS - 1) / PAIR_ROWS;
+  return tiles * PAIR_ROWS * (d == 2 ? PairSlots<2>::COUNT : PairSlots<3>::COUNT);
+}
+
 template <int D, typename R, typename T>
 __device__ inline void write_block_bc(const DevView &v, int64_t row, int64_t colnode, const R *B, T *out,
                                       int apply_bc) {
@@ -798,12 +821,11 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
   using PS = PairSlots<D>;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   constexpr int NSL = pn_nslot(D);
   constexpr int NPS = pn_stride(D, DYN, HK, (int)sizeof(R));
-  if (t >= (int64_t)PS::COUNT * g.nnodes) return;
-  const int64_t a = t % g.nnodes;
-  const int slot = PS::CENTRE + (int)(t / g.nnodes);
+  int64_t a;
+  int slot;
+  if (!pair_of_thread<D>(g, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, a, slot)) return;
   const int64_t e = block_of_slot<D>(mask, row_ptr, a, slot);
   if (e < 0) return;
   constexpr int NB = D + 1;
@@ -822,9 +844,10 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   }
   // pair accumulators: A (shared, for (a, b); (b, a) gets its transpose), C
   // (shared), B1 and B2 of each of the two blocks
-  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], C = 0;
+  // kgp: the grad p part of B2, (p7 g_a.g_b) grad p, the same for both blocks
+  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], kgp[D], C = 0;
   for (int i = 0; i < D * D; ++i) A[i] = 0;
-  for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = 0;
+  for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = kgp[i] = 0;
   for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
     for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
       for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
@@ -869,8 +892,8 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
           for (int k = 0; k < D; ++k) {
             R tk = fma(ca, gb[k], b2ab[k]);
             if (DYN) tk = fma(-p5Sa, pb[5 * D + 7 + k], tk);
-            tk = fma(-eb, ga[k], tk);
-            b2ab[k] = fma(-kgab, pp[9 + k], tk);
+            b2ab[k] = fma(-eb, ga[k], tk);
+            kgp[k] = fma(kgab, pp[9 + k], kgp[k]);
           }
           if (!diag) {
             for (int i = 0; i < D; ++i) b1ba[i] = fma(p5Sa, gb[i], b1ba[i]);
@@ -878,8 +901,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
             for (int k = 0; k < D; ++k) {
               R tk = fma(cb, ga[k], b2ba[k]);
               if (DYN) tk = fma(-p5Sb, pa[5 * D + 7 + k], tk);
-              tk = fma(-ea, gb[k], tk);
-              b2ba[k] = fma(-kgab, pp[9 + k], tk);
+              b2ba[k] = fma(-ea, gb[k], tk);
             }
           }
           // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b (symmetric)
@@ -890,7 +912,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   for (int i = 0; i < D; ++i) {
     for (int k = 0; k < D; ++k) B[i * NB + k] = A[i * D + k];
     B[i * NB + D] = b1ab[i];
-    B[D * NB + i] = b2ab[i];
+    B[D * NB + i] = b2ab[i] - kgp[i];
   }
   B[D * NB + D] = C;
   write_block_bc<D>(v, a, bn, B, val + e * (NB * NB), apply_bc);
@@ -900,7 +922,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   for (int i = 0; i < D; ++i) {
     for (int k = 0; k < D; ++k) B[i * NB + k] = A[k * D + i];
     B[i * NB + D] = b1ba[i];
-    B[D * NB + i] = b2ba[i];
+    B[D * NB + i] = b2ba[i] - kgp[i];
   }
   B[D * NB + D] = C;
   write_block_bc<D>(v, bn, a, B, val + e2 * (NB * NB), apply_bc);
@@ -914,10 +936,9 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
   using PS = PairSlots<D>;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= (int64_t)PS::COUNT * g.nnodes) return;
-  const int64_t a = t % g.nnodes;
-  const int slot = PS::CENTRE + (int)(t / g.nnodes);
+  int64_t a;
+  int slot;
+  if (!pair_of_thread<D>(g, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, a, slot)) return;
   const int64_t e = block_of_slot<D>(mask, row_ptr, a, slot);
   if (e < 0) return;
   constexpr int NB = D + 1;
@@ -935,9 +956,9 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
     lo[k] = max(l1, l2);
     hi[k] = min(h1, h2);
   }
-  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], C = 0;
+  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], kgp[D], C = 0;
   for (int i = 0; i < D * D; ++i) A[i] = 0;
-  for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = 0;
+  for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = kgp[i] = 0;
   const R cvis = DYN ? (R)(s.alpha_vis * s.gamma / (s.beta * s.dt)) : R(0);
   for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
     for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
@@ -992,9 +1013,10 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
               for (int j = 0; j < D; ++j) gbgv += gb[j] * rec[(RC_GV + j * D + k) * n + q];
               t -= vol * Sa * gbgv;
             }
-            t += kv * (gb[k] * gaw - ga[k] * gbw - rec[(RC_GP + k) * n + q] * gab);
+            t += kv * (gb[k] * gaw - ga[k] * gbw);
             t += dkv * gb[k] * gaw;  // dk/dJ (Kozeny-Carman)
             b2ab[k] += t;
+            kgp[k] += kv * gab * rec[(RC_GP + k) * n + q];  // grad p part, the same for both blocks
           }
           if (!diag) {
             for (int i = 0; i < D; ++i) b1ba[i] += vol * gb[i] * Sa;
@@ -1005,7 +1027,7 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
                 for (int j = 0; j < D; ++j) gagv += ga[j] * rec[(RC_GV + j * D + k) * n + q];
                 t -= vol * Sb * gagv;
               }
-              t += kv * (ga[k] * gbw - gb[k] * gaw - rec[(RC_GP + k) * n + q] * gab);
+              t += kv * (ga[k] * gbw - gb[k] * gaw);
               t += dkv * ga[k] * gbw;
               b2ba[k] += t;
             }
@@ -1017,7 +1039,7 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
   for (int i = 0; i < D; ++i) {
     for (int k = 0; k < D; ++k) B[i * NB + k] = A[i * D + k];
     B[i * NB + D] = b1ab[i];
-    B[D * NB + i] = b2ab[i];
+    B[D * NB + i] = b2ab[i] - kgp[i];
   }
   B[D * NB + D] = C;
   write_block_bc<D>(v, a, bn, B, val + e * (NB * NB), apply_bc);
@@ -1027,7 +1049,7 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
   for (int i = 0; i < D; ++i) {
     for (int k = 0; k < D; ++k) B[i * NB + k] = A[k * D + i];
     B[i * NB + D] = b1ba[i];
-    B[D * NB + i] = b2ba[i];
+    B[D * NB + i] = b2ba[i] - kgp[i];
   }
   B[D * NB + D] = C;
   write_block_bc<D>(v, bn, a, B, val + e2 * (NB * NB), apply_bc);
@@ -1464,7 +1486,7 @@ template <typename T>
 void launch_jacobian(Ctx &c, T *val, int apply_bc, bool staged, int tpb) {
   const DevView v = c.view();
   // the Jacobian kernels take symmetric pairs: half the offsets plus the centre
-  const int64_t nthr = (int64_t)(c.d == 2 ? PairSlots<2>::COUNT : PairSlots<3>::COUNT) * c.g.nnodes;
+  const int64_t nthr = pair_threads(c.d, c.g.nnodes);
   const int nbk_pair = (int)((nthr + tpb - 1) / tpb);
   const bool gimp = c.shape == MPM_SHAPE_GIMP;
   using R = T;

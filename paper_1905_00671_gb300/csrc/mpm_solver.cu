@@ -22,6 +22,8 @@ namespace {
 constexpr int TPB = 256;
 constexpr int NPART = 304;  // partial sums per reduction (2 x 152 SMs)
 constexpr int PSTR = 129;   // stride of the per-block partial sums (restart <= 128)
+constexpr int ORTH_TPB = 1024;     // threads per block of the Gram-Schmidt update ...
+constexpr int64_t ORTH_BIG = 1 << 20;  // ... on systems of at least this many unknowns
 inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
 
 __device__ inline double block_sum(double v) {
@@ -459,16 +461,24 @@ int fgmres_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
       spmv<NB, T>(c, S, Zj, w);
       prof_begin(c, MPM_PROF_ORTH);
       {  // classical Gram-Schmidt, twice; the j + 1 products of a pass run side by side
+        // slices per vector: enough blocks to stream the vectors at HBM speed
+        // on large systems (about 8 elements per thread, up to NPART slices),
+        // at least NPART / cnt on small ones; the update uses 1024-thread
+        // blocks on large systems for the same reason (measured: slope
+        // Gram-Schmidt 70 -> 46 ms per step; on the 62k-unknown footing the
+        // larger blocks cost more than they gave, 1.4 -> 1.7 ms)
         const int cnt = j + 1;
-        const int nbx = std::min(NPART, std::max(16, NPART / cnt));
+        const int64_t by_size = N >= ORTH_BIG ? N / (TPB * 8) : 0;
+        const int nbx = (int)std::min<int64_t>(NPART, std::max<int64_t>(std::max(16, NPART / cnt), by_size));
         const T *V = S.V, *wc = w;
         const double *ph = c.part;
         launch_pdl(c, k_multidot2<T>, dim3(nbx, cnt), TPB, 0, V, wc, N, c.part);
         launch_pdl(c, k_multidot_reduce, cnt, TPB, 0, ph, nbx, cnt, h1);
-        launch_pdl(c, k_orth_sub<T>, NPART, TPB, 0, w, V, (const double *)h1, cnt, N, c.part, 0);
+        const int otpb = N >= ORTH_BIG ? ORTH_TPB : TPB;
+        launch_pdl(c, k_orth_sub<T>, NPART, otpb, 0, w, V, (const double *)h1, cnt, N, c.part, 0);
         launch_pdl(c, k_multidot2<T>, dim3(nbx, cnt), TPB, 0, V, wc, N, c.part);
         launch_pdl(c, k_multidot_reduce, cnt, TPB, 0, ph, nbx, cnt, h2);
-        launch_pdl(c, k_orth_sub<T>, NPART, TPB, 0, w, V, (const double *)h2, cnt, N, c.part, 1);
+        launch_pdl(c, k_orth_sub<T>, NPART, otpb, 0, w, V, (const double *)h2, cnt, N, c.part, 1);
       }
       prof_end(c, MPM_PROF_ORTH);
       launch_pdl(c, k_arnoldi_finish, 1, TPB, 0, (const double *)c.part, (int)NPART, j, m, (const double *)h1,
