@@ -24,6 +24,7 @@ DevView Ctx::view() const {
   v.sh_first = sh_first;
   v.sh_cnt = sh_cnt;
   v.sh_box = sh_box;
+  v.pn_base = pn_base;
   v.sh_S = sh_S;
   v.sh_dS = sh_dS;
   v.sh_S0 = sh_S0;
@@ -316,6 +317,8 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   if (rc) return rc;
   run_initial_guess(c);
   run_renorm(c);
+  rc = run_pn_layout(c);
+  if (rc) return rc;
   run_count_terms(c);
   rc = read_dev_err(c);
   prof_end(c, MPM_PROF_PREP);
@@ -477,7 +480,7 @@ void free_all(Ctx &c) {
   for (float *p : fptrs)
     if (p) cudaFree(p);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
-                  c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_box, c.sh_S, c.sh_dS,
+                  c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_box, c.pn_cnt, c.pn_base, c.sh_S, c.sh_dS,
                   c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.fsd, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
@@ -541,6 +544,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   for (int k = 0; k < grid->dim; ++k)
     if (grid->ncell[k] < 1) return create_fail(BAD, "grid.ncell must be at least 1 on every axis");
   if (P->n > INT32_MAX / 2) return create_fail(BAD, "more than 2^30 points");
+  if (P->n > INT32_MAX / pn_nslot(grid->dim)) return create_fail(BAD, "too many points for the Jacobian staging");
   if (opt->krylov_restart < 1 || opt->krylov_restart > 128)
     return create_fail(BAD, "krylov_restart must be in 1..128");
   if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON)
@@ -665,6 +669,8 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   A(&c.sh_first, 3 * n);
   A(&c.sh_cnt, n);
   A(&c.sh_box, n);
+  A(&c.pn_cnt, n + 1);
+  A(&c.pn_base, n + 1);
   A(&c.sh_S, 3 * MAXS * n);
   A(&c.sh_dS, 3 * MAXS * n);
   A(&c.sh_S0, 3 * MAXS * n);

@@ -765,23 +765,22 @@ constexpr int PN_LANES = 16;
 template <int D, bool DYN, bool HK, typename R>
 __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                               R *__restrict__ pn) {
-  constexpr int NSL = pn_nslot(D);
   constexpr int NPS = pn_stride(D, DYN, HK, (int)sizeof(R));
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = v.n;
   if (t >= n * PN_LANES) return;
   const int64_t q = t / PN_LANES;
   const int j = (int)(t - q * PN_LANES);
-  R *P = pn + q * NSL * NPS;
-  if (j == 0)
-    for (int k = 0; k < D; ++k) P[(NSL - 1) * NPS + 9 + k] = rec[(RC_GP + k) * n + q];
+  R *P = pn + (int64_t)v.pn_base[q] * NPS;  // the point's records: box nodes x-fastest, then its own
   const int packed = v.sh_cnt[q];
   const int c0 = unpack_cnt(packed, 0), c1 = D > 1 ? unpack_cnt(packed, 1) : 1,
             c2 = D > 2 ? unpack_cnt(packed, 2) : 1;
   const int nq = c0 * c1 * c2;
+  if (j == 0)
+    for (int k = 0; k < D; ++k) P[nq * NPS + 9 + k] = rec[(RC_GP + k) * n + q];
   for (int sc = j; sc < nq; sc += PN_LANES) {
     const int off[3] = {sc % c0, (sc / c0) % c1, sc / (c0 * c1)};
-    point_node_record<D, DYN, HK, R>(g, sp, v, BA, rec, q, off, P + (off[0] + MAXS * (off[1] + MAXS * off[2])) * NPS);
+    point_node_record<D, DYN, HK, R>(g, sp, v, BA, rec, q, off, P + sc * NPS);
   }
 }
 
@@ -856,11 +855,14 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
           int oa[3], ob[3];
           const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
           if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) continue;
-          const R *P = pn + (int64_t)q * NSL * NPS;
+          // the point's records: its box nodes x-fastest, then its own
+          const R *P = pn + (int64_t)v.pn_base[q] * NPS;
+          const int c0 = unpack_cnt(bx.w, 0), c1 = D > 1 ? unpack_cnt(bx.w, 1) : 1,
+                    c2 = D > 2 ? unpack_cnt(bx.w, 2) : 1;
           PnRec<R, NPS> pa, pb;
-          pa.load(P + (oa[0] + MAXS * (oa[1] + MAXS * oa[2])) * NPS);
-          pb.load(P + (ob[0] + MAXS * (ob[1] + MAXS * ob[2])) * NPS);
-          const R *pp = P + (NSL - 1) * NPS;
+          pa.load(P + (oa[0] + c0 * (oa[1] + c1 * oa[2])) * NPS);
+          pb.load(P + (ob[0] + c0 * (ob[1] + c1 * ob[2])) * NPS);
+          const R *pp = P + (c0 * c1 * c2) * NPS;
           R ga[3], gb[3];
           for (int j = 0; j < D; ++j) {
             ga[j] = pa[j];
@@ -1423,6 +1425,29 @@ void run_count_terms(Ctx &c) {
   if (c.d == 2) k_count_terms<2><<<nblk(c.n), TPB, 0, c.st>>>(c.g, v, c.terms);
   else k_count_terms<3><<<nblk(c.n), TPB, 0, c.st>>>(c.g, v, c.terms);
   UPMPM_LAUNCH(c);
+}
+
+// n_q + 1 records of point q (its support box's nodes and its own), 0 at q = n
+__global__ void k_pn_count(int64_t n, const int32_t *__restrict__ cnt, int32_t *__restrict__ out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p > n) return;
+  if (p == n) {
+    out[p] = 0;
+    return;
+  }
+  const int packed = cnt[p];
+  out[p] = unpack_cnt(packed, 0) * unpack_cnt(packed, 1) * max(unpack_cnt(packed, 2), 1) + 1;
+}
+
+int run_pn_layout(Ctx &c) {
+  k_pn_count<<<nblk(c.n + 1), TPB, 0, c.st>>>(c.n, c.sh_cnt, c.pn_cnt);
+  UPMPM_LAUNCH(c);
+  const int64_t total = scan_exclusive(c, c.pn_cnt, c.pn_base, c.n + 1);
+  if (total < 0 || total > (int64_t)pn_nslot(c.d) * c.n) {
+    if (c.last_error.empty()) c.last_error = "Jacobian staging layout";
+    return MPM_ERR_CUDA;
+  }
+  return MPM_OK;
 }
 
 void run_renorm(Ctx &c) {

@@ -64,9 +64,10 @@ struct LinSys {
 constexpr int PATTERN_MASK_WORDS = 6;
 
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
-// Jacobian staging: per point, one record per support slot (MAXS^d) and one
-// for the point's own coefficients, pn_npf(d, dyn) values each (the layout is
-// in k_point_nodes).
+// Jacobian staging: per point, one record per node of its support box (at
+// most MAXS^d) and one for the point's own coefficients, pn_npf(d, dyn)
+// values each (the layout is in k_point_nodes); pn_nslot bounds the records
+// of a point.
 __host__ __device__ constexpr int pn_npf(int d, bool dyn, bool hencky = false) {
   return (dyn ? 6 * d + 7 : 5 * d + 6) + (hencky ? d * d * d : 0);
 }
@@ -170,6 +171,7 @@ struct DevView {
   int32_t *sh_first;        // 3 * n
   int32_t *sh_cnt;          // n, counts packed 4 bits per axis
   int4 *sh_box;             // n: (first node per axis, sh_cnt) of each point in one 16-byte word
+  const int32_t *pn_base;   // n + 1: first staged Jacobian record of each point
   double *sh_S, *sh_dS, *sh_S0;  // 12 * n each
   double *m;                // n mixture mass of the step
   double *rec;              // RC_COUNT * n
@@ -267,6 +269,11 @@ struct Ctx {
   // records of PN_NPF values per point)
   double *pn = nullptr;
   float *pn32 = nullptr;                 // the same in FP32 (the staged FP32 variant)
+  // record layout of the staging: point q's records (one per node of its
+  // support box, then its own) start at record pn_base[q]; packed in point
+  // order (an exclusive scan of n_q + 1) so that a point's records are
+  // contiguous and the staged region is only as large as the supports
+  int32_t *pn_cnt = nullptr, *pn_base = nullptr;
   unsigned long long *h_terms = nullptr; // pinned copy
   // Jacobian kernel configuration per precision ([0] FP64, [1] FP32): staged
   // (per-(point, node) vectors formed first) or direct (recomputed per term),
@@ -321,6 +328,7 @@ int run_consistent_p2g(Ctx &c);  // Stage-1 fields by the consistent mass (after
 int ensure_jacobian_staging(Ctx &c);  // the FP64 Jacobian's staging buffer (allocated by FP64 contexts at create)
 void run_initial_guess(Ctx &c);   // also sets the active flags
 void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
+int run_pn_layout(Ctx &c);        // first staged Jacobian record of each point (pn_base)
 void run_count_terms(Ctx &c);     // Jacobian term counts into c.terms (device)
 void run_fs_diag(Ctx &c);         // c.fsd = sum_p S_ip b2 vol / (cs K) (current records)
 void run_point_eval(Ctx &c, const double *X);
