@@ -299,7 +299,9 @@ void mpm_default_options(mpm_options *o);
 /* Creates a context and uploads the problem (Sec. 2.4 "given u0, p0"): the
  * points, per-point E, nu and intrinsic permeability k (permeability, n
  * values, m^2).  Allocates all device memory the run needs except what
- * depends on the evolving sparsity.  *out receives the context, or NULL on
+ * depends on the evolving sparsity and supports (the block matrix, the
+ * preconditioner's coupling blocks and the Jacobian's staged per-(point,
+ * node) vectors), which a step grows when it needs more.  *out receives the context, or NULL on
  * error (the code says why).  Rejected with MPM_ERR_BAD_ARG before any device
  * call: a non-finite position, a volume that is not positive and finite, an E
  * that is not positive and finite, nu outside (-1, 1/2), a negative or

@@ -678,8 +678,6 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   A(&c.rec, RC_COUNT * n);
   // the FP64 Jacobian's staging (allocated on first use in a mixed context,
   // whose Jacobian is FP32 and unstaged)
-  if (opt->precision == MPM_FP64)
-    A(&c.pn, (int64_t)pn_nslot(c.d) * pn_stride(c.d, c.dyn, opt->model == MPM_MODEL_HENCKY, 8) * n);
   A(&c.M, nn);
   A(&c.Pn, nn);
   A(&c.vn, d * nn);

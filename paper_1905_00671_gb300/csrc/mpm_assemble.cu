@@ -601,26 +601,24 @@ __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const
 // Staging of the Jacobian (FP64, and FP32 in the staged mixed form): the
 // point's per-node records (k_point_nodes below: PN_LANES lanes per point),
 // so that each (point, a, b) term of the block assembly is a short chain of
-// FMAs.  With g = F^-T grad S (current
-// configuration), St = S - S0 and the point's coefficients
+// FMAs.  With g = F^-T grad S (current configuration), St = S - S0 and the
+// point's coefficients
 //   p0 = cs,  p1 = cs (1 + cv) G',
 //   p2 = vol p - cs (1 + cv) lambda,  p3 = cs (1 + cv) G' + vol p,
 //   p4 = m (Newmark),  p5 = vol,  p6 = b2,  p7 = kappa vol,  p8 = C_stab V
 // (cs = V_n / J_n, cv = the Newmark viscous factor, G' = G - lambda ln J), a
-// node record holds (offsets for dimension D):
-//   0        g                       D+2    p2 g
-//   D        S                       2D+2   p3 g
-//   D+1      St                      3D+2   h = p0 (g^T tau') + p1 g
-//   4D+2     p7 g                    5D+2   p6 S + (p7 + J dk/dJ vol) g.w
-//   5D+3     p7 g.w                  5D+4   p5 S
-//   5D+5     p8 St                   5D+6   p4 S, 5D+7 g.grad v (Newmark)
-// and the point's own record (last slot) holds grad p at 9..9+D-1.  (The
+// node record holds (PnLay: first the fields a pair term reads at both of its
+// nodes, then those it reads at the row node only)
+//   g, S, St, p2 g, c = p6 S + (p7 + J dk/dJ vol) g.w, e = p7 g.w, p5 S,
+//   g.grad v (Newmark); then p3 g, h = p0 (g^T tau') + p1 g, p7 g, p8 St,
+//   p4 S (Newmark),
+// and the point's own record (after its node records) holds grad p.  (The
 // terms are those of the linearization, Eqs. jacobian-system-stabilized-ppp
 // and newmark-linearization, grouped per node.)
 // Hencky (HK): the material part of the tangent is not of the lambda / G'
 // form, so p1 = 0, p2 = p3 = vol p, and the record ends with the d^3 values
-// U_ikl = -cs (1 + cv) sum_j g_j c_ijkl at offset pn_npf(D, DYN), so that the
-// term adds sum_l U_a,ikl g_b,l to A_ik; from the principal data of the point
+// U_ikl = -cs (1 + cv) sum_j g_j c_ijkl (PnLay::U), so that the term adds
+// sum_l U_a,ikl g_b,l to A_ik; from the principal data of the point
 //   sum_j g_j c_ijkl = lambda g_i delta_kl + sum_A n_Ai (kappa_A gh_A n_Ak n_Al
 //                      + sum_{B != A} theta_AB gh_B (n_Ak n_Bl + n_Bk n_Al)),
 // gh_A = g . n_A.
@@ -628,6 +626,7 @@ template <int D, bool DYN, bool HK, typename R>
 __device__ inline void point_node_record(const GridP &g, const StepP &sp, const DevView &v,
                                          const BasisArrays<R> &BA, const R *__restrict__ rec, int64_t q,
                                          const int off[3], R *__restrict__ out) {
+  using L = PnLay<D, DYN, HK, (int)sizeof(R)>;
   const int64_t n = v.n;
   const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
   const R cv = DYN ? (R)(sp.alpha_vis * sp.gamma / (sp.beta * sp.dt)) : R(0);
@@ -650,30 +649,29 @@ __device__ inline void point_node_record(const GridP &g, const StepP &sp, const 
   for (int l = 0; l < D; ++l) {
     R tl = 0;
     for (int j = 0; j < D; ++j) tl += gs[j] * rec[(RC_TAU + j * D + l) * n + q];
-    out[l] = gs[l];
-    out[D + 2 + l] = p2 * gs[l];
-    out[2 * D + 2 + l] = p3 * gs[l];
-    out[3 * D + 2 + l] = p0 * tl + p1 * gs[l];
-    out[4 * D + 2 + l] = p7 * gs[l];
+    out[L::G + l] = gs[l];
+    out[L::P2G + l] = p2 * gs[l];
+    out[L::P3G + l] = p3 * gs[l];
+    out[L::H + l] = p0 * tl + p1 * gs[l];
+    out[L::P7G + l] = p7 * gs[l];
     gw += gs[l] * rec[(RC_W + l) * n + q];
   }
   const R St = Sa - S0a;
-  out[D] = Sa;
-  out[D + 1] = St;
-  out[5 * D + 2] = p6 * Sa + (p7 + rec[RC_DKV * n + q]) * gw;
-  out[5 * D + 3] = p7 * gw;
-  out[5 * D + 4] = p5 * Sa;
-  out[5 * D + 5] = p8 * St;
+  out[L::S] = Sa;
+  out[L::ST] = St;
+  out[L::C] = p6 * Sa + (p7 + rec[RC_DKV * n + q]) * gw;
+  out[L::E] = p7 * gw;
+  out[L::P5S] = p5 * Sa;
+  out[L::P8ST] = p8 * St;
   if (DYN) {
-    out[5 * D + 6] = rec[RC_MS * n + q] * Sa;
+    out[L::MS] = rec[RC_MS * n + q] * Sa;
     for (int k = 0; k < D; ++k) {
       R gv = 0;
       for (int j = 0; j < D; ++j) gv += gs[j] * rec[(RC_GV + j * D + k) * n + q];
-      out[5 * D + 7 + k] = gv;
+      out[L::GV + k] = gv;
     }
   }
   if (HK) {
-    constexpr int UOFF = pn_npf(D, DYN);
     R nq[9], kap[3], th[3], gh[3];
     for (int i = 0; i < D * D; ++i) nq[i] = rec[(RC_HQ + i) * n + q];
     for (int A = 0; A < D; ++A) kap[A] = rec[(RC_HK + A) * n + q];
@@ -697,7 +695,7 @@ __device__ inline void point_node_record(const GridP &g, const StepP &sp, const 
               }
             u += nq[i * D + A] * w;
           }
-          out[UOFF + (i * D + k) * D + l] = -csv * u;
+          out[L::U + (i * D + k) * D + l] = -csv * u;
         }
   }
 }
@@ -708,10 +706,10 @@ __device__ inline void point_node_record(const GridP &g, const StepP &sp, const 
 // tau' and the tangent are symmetric) and C_ba = C_ab (Darcy and C_stab are
 // symmetric), while B1 and B2 of the two blocks differ.  One thread takes the
 // unordered pair: coupling offset o = b - a in the upper half of [-3, 3]^d
-// (slot s >= the centre slot, offset-major as before: thread t takes slot
-// centre + t / nnodes of row a = t % nnodes) and writes block (a, b) and, for
-// o != 0, block (b, a) = row b, slot of -o.  Per (point, a, b) term of a pair
-// the A and C parts are formed once and the B1 / B2 parts twice.
+// (slot s >= the centre slot; threads mapped by pair_of_thread) and writes
+// block (a, b) and, for o != 0, block (b, a) = row b, slot of -o.  Per
+// (point, a, b) term of a pair the A and C parts are formed once and the
+// B1 / B2 parts twice.
 template <int D>
 struct PairSlots {
   static constexpr int NSLOT = D == 2 ? 49 : 343;
@@ -765,7 +763,8 @@ constexpr int PN_LANES = 16;
 template <int D, bool DYN, bool HK, typename R>
 __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                               R *__restrict__ pn) {
-  constexpr int NPS = pn_stride(D, DYN, HK, (int)sizeof(R));
+  using L = PnLay<D, DYN, HK, (int)sizeof(R)>;
+  constexpr int NPS = L::STRIDE;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = v.n;
   if (t >= n * PN_LANES) return;
@@ -777,7 +776,7 @@ __global__ void k_point_nodes(GridP g, StepP sp, DevView v, BasisArrays<R> BA, c
             c2 = D > 2 ? unpack_cnt(packed, 2) : 1;
   const int nq = c0 * c1 * c2;
   if (j == 0)
-    for (int k = 0; k < D; ++k) P[nq * NPS + 9 + k] = rec[(RC_GP + k) * n + q];
+    for (int k = 0; k < D; ++k) P[nq * NPS + L::GP + k] = rec[(RC_GP + k) * n + q];
   for (int sc = j; sc < nq; sc += PN_LANES) {
     const int off[3] = {sc % c0, (sc / c0) % c1, sc / (c0 * c1)};
     point_node_record<D, DYN, HK, R>(g, sp, v, BA, rec, q, off, P + sc * NPS);
@@ -820,8 +819,8 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
   using PS = PairSlots<D>;
-  constexpr int NSL = pn_nslot(D);
-  constexpr int NPS = pn_stride(D, DYN, HK, (int)sizeof(R));
+  using L = PnLay<D, DYN, HK, (int)sizeof(R)>;
+  constexpr int NPS = L::STRIDE;
   int64_t a;
   int slot;
   if (!pair_of_thread<D>(g, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, a, slot)) return;
@@ -859,55 +858,56 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
           const R *P = pn + (int64_t)v.pn_base[q] * NPS;
           const int c0 = unpack_cnt(bx.w, 0), c1 = D > 1 ? unpack_cnt(bx.w, 1) : 1,
                     c2 = D > 2 ? unpack_cnt(bx.w, 2) : 1;
-          PnRec<R, NPS> pa, pb;
+          PnRec<R, NPS> pa;        // the row node's record: all of it
+          PnRec<R, L::BPART> pb;   // the column node's: the fields read for both nodes
           pa.load(P + (oa[0] + c0 * (oa[1] + c1 * oa[2])) * NPS);
           pb.load(P + (ob[0] + c0 * (ob[1] + c1 * ob[2])) * NPS);
           const R *pp = P + (c0 * c1 * c2) * NPS;
           R ga[3], gb[3];
           for (int j = 0; j < D; ++j) {
-            ga[j] = pa[j];
-            gb[j] = pb[j];
+            ga[j] = pa[L::G + j];
+            gb[j] = pb[L::G + j];
           }
           // A_ik = g_a,i (p2 g_b)_k - g_b,i (p3 g_a)_k - delta_ik d,
           // d = h_a.g_b (+ p4 S_a S_b): stress, geometric, pressure, Kelvin
           // and inertia terms with the point's coefficients staged per node
           R dg = 0, kgab = 0;
           for (int j = 0; j < D; ++j) {
-            dg = fma(pa[3 * D + 2 + j], gb[j], dg);
-            kgab = fma(pa[4 * D + 2 + j], gb[j], kgab);  // p7 g_a.g_b
+            dg = fma(pa[L::H + j], gb[j], dg);
+            kgab = fma(pa[L::P7G + j], gb[j], kgab);  // p7 g_a.g_b
           }
-          if (DYN) dg = fma(pa[5 * D + 6], pb[D], dg);
+          if (DYN) dg = fma(pa[L::MS], pb[L::S], dg);
           for (int i = 0; i < D; ++i)
             for (int k = 0; k < D; ++k) {
-              R acc = fma(ga[i], pb[D + 2 + k], A[i * D + k]);
-              acc = fma(-gb[i], pa[2 * D + 2 + k], acc);
+              R acc = fma(ga[i], pb[L::P2G + k], A[i * D + k]);
+              acc = fma(-gb[i], pa[L::P3G + k], acc);
               if (HK)  // material part of the Hencky tangent, staged per node
-                for (int l = 0; l < D; ++l) acc = fma(pa[pn_npf(D, DYN) + (i * D + k) * D + l], gb[l], acc);
+                for (int l = 0; l < D; ++l) acc = fma(pa[L::U + (i * D + k) * D + l], gb[l], acc);
               A[i * D + k] = i == k ? acc - dg : acc;
             }
           // B1 column of (a, b): (p5 S_b) g_a; of (b, a): (p5 S_a) g_b
-          const R p5Sb = pb[5 * D + 4], p5Sa = pa[5 * D + 4];
+          const R p5Sb = pb[L::P5S], p5Sa = pa[L::P5S];
           for (int i = 0; i < D; ++i) b1ab[i] = fma(p5Sb, ga[i], b1ab[i]);
           // B2 row of (a, b): (p6 S_a + p7 g_a.w) g_b - (p7 g_b.w) g_a - (p7 g_a.g_b) grad p
           //                   (- p5 S_a g_b.grad v, Newmark); (b, a): a <-> b
-          const R ca = pa[5 * D + 2], eb = pb[5 * D + 3];
+          const R ca = pa[L::C], eb = pb[L::E];
           for (int k = 0; k < D; ++k) {
             R tk = fma(ca, gb[k], b2ab[k]);
-            if (DYN) tk = fma(-p5Sa, pb[5 * D + 7 + k], tk);
+            if (DYN) tk = fma(-p5Sa, pb[L::GV + k], tk);
             b2ab[k] = fma(-eb, ga[k], tk);
-            kgp[k] = fma(kgab, pp[9 + k], kgp[k]);
+            kgp[k] = fma(kgab, pp[L::GP + k], kgp[k]);
           }
           if (!diag) {
             for (int i = 0; i < D; ++i) b1ba[i] = fma(p5Sa, gb[i], b1ba[i]);
-            const R cb = pb[5 * D + 2], ea = pa[5 * D + 3];
+            const R cb = pb[L::C], ea = pa[L::E];
             for (int k = 0; k < D; ++k) {
               R tk = fma(cb, ga[k], b2ba[k]);
-              if (DYN) tk = fma(-p5Sb, pa[5 * D + 7 + k], tk);
+              if (DYN) tk = fma(-p5Sb, pa[L::GV + k], tk);
               b2ba[k] = fma(-ea, gb[k], tk);
             }
           }
           // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b (symmetric)
-          C = fma(pa[5 * D + 5], pb[D + 1], C + kgab);
+          C = fma(pa[L::P8ST], pb[L::ST], C + kgab);
         }
       }
   R B[NB * NB];
@@ -1256,15 +1256,29 @@ __global__ void k_cm_init(int64_t nn, int K, const double *__restrict__ rhs, con
 }  // namespace
 
 // ============================================================== launchers
-int ensure_jacobian_staging(Ctx &c) {
-  if (c.pn) return MPM_OK;
-  if (cudaMalloc(&c.pn, sizeof(double) * (int64_t)pn_nslot(c.d) * pn_stride(c.d, c.dyn, c.s.hencky, 8) * c.n) !=
-      cudaSuccess) {
-    c.pn = nullptr;
-    c.last_error = "device allocation of the Jacobian staging failed";
+// Staging buffer of at least c.pn_total records of `stride` values: kept
+// while large enough, else reallocated with a quarter of headroom (the supports
+// grow and shrink a little from step to step as the points move).
+template <typename R>
+static int grow_staging(R **buf, int64_t *cap, int64_t total, int stride) {
+  if (*buf && *cap >= total) return MPM_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  const int64_t want = total + total / 4 + 1024;
+  if (cudaMalloc(buf, sizeof(R) * want * stride) != cudaSuccess) {
+    cudaGetLastError();
+    *buf = nullptr;
     return MPM_ERR_NO_MEMORY;
   }
+  *cap = want;
   return MPM_OK;
+}
+
+int ensure_jacobian_staging(Ctx &c) {
+  const int rc = grow_staging(&c.pn, &c.pn_cap, c.pn_total, pn_stride(c.d, c.dyn, c.s.hencky, 8));
+  if (rc) c.last_error = "device allocation of the Jacobian staging failed";
+  return rc;
 }
 
 int run_consistent_p2g(Ctx &c) {
@@ -1447,8 +1461,11 @@ int run_pn_layout(Ctx &c) {
     if (c.last_error.empty()) c.last_error = "Jacobian staging layout";
     return MPM_ERR_CUDA;
   }
+  c.pn_total = total;
   return MPM_OK;
 }
+
+
 
 void run_renorm(Ctx &c) {
   const DevView v = c.view();
@@ -1493,14 +1510,7 @@ void run_residual(Ctx &c, const double *X, double *R, int apply_bc) {
 
 // FP32 copy of the staging (allocated for the staged FP32 variant only)
 int ensure_jacobian_staging32(Ctx &c) {
-  if (c.pn32) return MPM_OK;
-  if (cudaMalloc(&c.pn32, sizeof(float) * (int64_t)pn_nslot(c.d) * pn_stride(c.d, c.dyn, c.s.hencky, 4) * c.n) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    c.pn32 = nullptr;
-    return MPM_ERR_NO_MEMORY;
-  }
-  return MPM_OK;
+  return grow_staging(&c.pn32, &c.pn32_cap, c.pn_total, pn_stride(c.d, c.dyn, c.s.hencky, 4));
 }
 
 // One assembly with a given kernel configuration: staged (k_point_nodes then
@@ -1615,6 +1625,7 @@ void autotune_jacobian(Ctx &c, T *val, int apply_bc) {
   if (pi == 1 && !cfg.staged && c.pn32) {  // not chosen: give the memory back
     cudaFree(c.pn32);
     c.pn32 = nullptr;
+    c.pn32_cap = 0;
   }
 }
 

@@ -33,6 +33,7 @@ struct LinSys {
   T *val = nullptr;            // nnzb_cap * nb * nb block values (scaled in place)
   int64_t cap = 0;             // blocks val can hold
   T *dscale = nullptr;         // nb * nnodes, D = |diag J|^{-1/2}
+  T *dscinv = nullptr;         // nb * nnodes, D^{-1} = |diag J|^{1/2} (multiplied, not divided by D)
   T *dinv = nullptr;           // nnodes * nb * nb block-Jacobi inverse
   T *rhs = nullptr, *x = nullptr, *w = nullptr;  // N each
   T *V = nullptr, *Z = nullptr;                  // (m + 1) * N and m * N
@@ -65,19 +66,45 @@ constexpr int PATTERN_MASK_WORDS = 6;
 
 constexpr int MAXS = 4;  // nodes per axis in one support (GIMP half length < h)
 // Jacobian staging: per point, one record per node of its support box (at
-// most MAXS^d) and one for the point's own coefficients, pn_npf(d, dyn)
-// values each (the layout is in k_point_nodes); pn_nslot bounds the records
-// of a point.
-__host__ __device__ constexpr int pn_npf(int d, bool dyn, bool hencky = false) {
-  return (dyn ? 6 * d + 7 : 5 * d + 6) + (hencky ? d * d * d : 0);
-}
+// most MAXS^d) and one for the point's own coefficients (PnLay below; the
+// values are written by k_point_nodes); pn_nslot bounds the records of a
+// point.
 __host__ __device__ constexpr int pn_nslot(int d) { return (d == 2 ? MAXS * MAXS : MAXS * MAXS * MAXS) + 1; }
-// Values per record as stored: pn_npf rounded up to 16 bytes (a multiple of 2
-// doubles or 4 floats), so that every record starts on a 16-byte boundary and
-// can be read with vector loads.
-__host__ __device__ constexpr int pn_stride(int d, bool dyn, bool hencky, int word) {
-  return (pn_npf(d, dyn, hencky) * word + 15) / 16 * 16 / word;
+
+// Field offsets of a staged (point, node) record of WORD-byte values.  The
+// fields a pair term reads from both of its nodes come first, padded to 16
+// bytes, so that the column node's record is read with about half the loads;
+// the fields read for the row node only follow; the record is padded to 16
+// bytes.  A point's own record holds grad p at GP.
+__host__ __device__ constexpr int pn_bpart(int d, bool dyn, int word) {
+  return (2 * d + 5 + (dyn ? d : 0) + 16 / word - 1) / (16 / word) * (16 / word);
 }
+__host__ __device__ constexpr int pn_npf(int d, bool dyn, bool hencky, int word) {
+  return pn_bpart(d, dyn, word) + 3 * d + 1 + (dyn ? 1 : 0) + (hencky ? d * d * d : 0);
+}
+__host__ __device__ constexpr int pn_stride(int d, bool dyn, bool hencky, int word) {
+  return (pn_npf(d, dyn, hencky, word) + 16 / word - 1) / (16 / word) * (16 / word);
+}
+template <int D, bool DYN, bool HK, int WORD>
+struct PnLay {
+  static constexpr int G = 0;                 // g = F^-T grad S (D values)
+  static constexpr int S = D;                 // S
+  static constexpr int ST = D + 1;            // S - S0
+  static constexpr int P2G = D + 2;           // p2 g (D)
+  static constexpr int C = 2 * D + 2;         // p6 S + (p7 + J dk/dJ vol) g.w
+  static constexpr int E = 2 * D + 3;         // p7 g.w
+  static constexpr int P5S = 2 * D + 4;       // p5 S
+  static constexpr int GV = 2 * D + 5;        // g.grad v (D, Newmark)
+  static constexpr int BPART = pn_bpart(D, DYN, WORD);  // values read for the column node
+  static constexpr int P3G = BPART;           // p3 g (D)
+  static constexpr int H = BPART + D;         // p0 g^T tau' + p1 g (D)
+  static constexpr int P7G = BPART + 2 * D;   // p7 g (D)
+  static constexpr int P8ST = BPART + 3 * D;  // p8 (S - S0)
+  static constexpr int MS = P8ST + 1;         // m S (Newmark)
+  static constexpr int U = MS + (DYN ? 1 : 0);  // Hencky: staged tangent (D^3)
+  static constexpr int STRIDE = pn_stride(D, DYN, HK, WORD);
+  static constexpr int GP = 0;                // own record: grad p (D)
+};
 
 // ---- particle fields ------------------------------------------------------
 enum PField {
@@ -274,6 +301,8 @@ struct Ctx {
   // order (an exclusive scan of n_q + 1) so that a point's records are
   // contiguous and the staged region is only as large as the supports
   int32_t *pn_cnt = nullptr, *pn_base = nullptr;
+  int64_t pn_total = 0;                  // records of the current step
+  int64_t pn_cap = 0, pn32_cap = 0;      // records pn / pn32 can hold
   unsigned long long *h_terms = nullptr; // pinned copy
   // Jacobian kernel configuration per precision ([0] FP64, [1] FP32): staged
   // (per-(point, node) vectors formed first) or direct (recomputed per term),

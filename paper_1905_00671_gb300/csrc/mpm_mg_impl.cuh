@@ -217,18 +217,20 @@ __global__ void k_schur_lump(int64_t nnodes, const int32_t *__restrict__ row_ptr
 
 // ------------------------------------------------------------ Schur apply
 // The Krylov solver works on D J D (D = dsc); the blocks below are the
-// unscaled physical ones, so the preconditioner of D J D is D^-1 M^-1 D^-1.
+// unscaled physical ones, so the preconditioner of D J D is D^-1 M^-1 D^-1,
+// applied with the stored D^-1 (dsi = |diag J|^{1/2}: products instead of
+// FP64 divisions, which run long on the narrow FP64 pipe).
 // v_u, v_p of the unscaled system; v_p is the S-cycle's level-0 rhs, whose
 // first smoothing sweep from zero (x = omega Dinv b, pointwise) is done here.
 template <int D>
-__global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsc,
+__global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsi,
                         real *__restrict__ vu, real *__restrict__ bs0, real *__restrict__ xs0,
                         const real *__restrict__ dinvs0, real omega) {
   pdl_enter();
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
-  for (int k = 0; k < D; ++k) vu[a * D + k] = v[a * (D + 1) + k] / dsc[a * (D + 1) + k];
-  const real vp = v[a * (D + 1) + D] / dsc[a * (D + 1) + D];
+  for (int k = 0; k < D; ++k) vu[a * D + k] = v[a * (D + 1) + k] * dsi[a * (D + 1) + k];
+  const real vp = v[a * (D + 1) + D] * dsi[a * (D + 1) + D];
   bs0[a] = vp;
   xs0[a] = omega * (dinvs0[a] * vp);
 }
@@ -237,7 +239,7 @@ __global__ void k_split(int64_t nnodes, const real *__restrict__ v, const real *
 // smoothing sweep from zero (x = omega Dinv_A v_u, a D x D block per node);
 // v_p is kept for the S-cycle's rhs v_p - B2 z_u.
 template <int D>
-__global__ void k_split_lower(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsc,
+__global__ void k_split_lower(int64_t nnodes, const real *__restrict__ v, const real *__restrict__ dsi,
                               real *__restrict__ ba0, real *__restrict__ xa0, const real *__restrict__ dinva0,
                               real *__restrict__ vp, real omega) {
   pdl_enter();
@@ -245,7 +247,7 @@ __global__ void k_split_lower(int64_t nnodes, const real *__restrict__ v, const 
   if (a >= nnodes) return;
   real vu[D];
   for (int k = 0; k < D; ++k) {
-    vu[k] = v[a * (D + 1) + k] / dsc[a * (D + 1) + k];
+    vu[k] = v[a * (D + 1) + k] * dsi[a * (D + 1) + k];
     ba0[a * D + k] = vu[k];
   }
   for (int i = 0; i < D; ++i) {
@@ -253,7 +255,7 @@ __global__ void k_split_lower(int64_t nnodes, const real *__restrict__ v, const 
     for (int j = 0; j < D; ++j) sv = fma(dinva0[a * D * D + i * D + j], vu[j], sv);
     xa0[a * D + i] = omega * sv;
   }
-  vp[a] = v[a * (D + 1) + D] / dsc[a * (D + 1) + D];
+  vp[a] = v[a * (D + 1) + D] * dsi[a * (D + 1) + D];
 }
 
 // Compact unscaled B2 (row D, u columns, of the unscaled J): D values per block.
@@ -353,12 +355,12 @@ __global__ void k_b2c_update(int64_t nnodes, const int32_t *__restrict__ row_ptr
 
 template <int D>
 __global__ void k_merge(int64_t nnodes, const real *__restrict__ zu, const real *__restrict__ zp,
-                        const real *__restrict__ dsc, real *__restrict__ z) {
+                        const real *__restrict__ dsi, real *__restrict__ z) {
   pdl_enter();
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
-  for (int k = 0; k < D; ++k) z[a * (D + 1) + k] = zu[a * D + k] / dsc[a * (D + 1) + k];
-  z[a * (D + 1) + D] = zp[a] / dsc[a * (D + 1) + D];
+  for (int k = 0; k < D; ++k) z[a * (D + 1) + k] = zu[a * D + k] * dsi[a * (D + 1) + k];
+  z[a * (D + 1) + D] = zp[a] * dsi[a * (D + 1) + D];
 }
 
 // ------------------------------------------------------------ multigrid
@@ -931,89 +933,20 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs A) {
   }
 }
 
-// Galerkin coarse operator: one thread per (coarse node I, stencil slot).
-template <int B, int D, bool FST>
-__global__ void k_mg_rap(LevelDev F, LevelDev Cl) {
-  constexpr int NS = NS_<D>::v;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= Cl.nnodes * NS) return;
-  const int64_t I = t / NS;
-  const int s = (int)(t % NS);
-  const int o0 = s % 5 - 2, o1 = (s / 5) % 5 - 2, o2 = D == 3 ? s / 25 - 2 : 0;
-  int Ic[3], Jc[3];
-  grid_xyz(Cl.nn[0], Cl.nn[1], (int)I, Ic);
-  Jc[0] = Ic[0] + o0;
-  Jc[1] = Ic[1] + o1;
-  Jc[2] = Ic[2] + o2;
-  real acc[B * B];
-  for (int i = 0; i < B * B; ++i) acc[i] = 0.0;
-  const bool Jin = Jc[0] >= 0 && Jc[0] < Cl.nn[0] && Jc[1] >= 0 && Jc[1] < Cl.nn[1] && Jc[2] >= 0 &&
-                   Jc[2] < Cl.nn[2];
-  if (Jin) {
-    const int64_t Jn = Jc[0] + (int64_t)Cl.nn[0] * (Jc[1] + (int64_t)Cl.nn[1] * Jc[2]);
-    const int lo2 = D == 3 ? -1 : 0, hi2 = D == 3 ? 1 : 0;
-    for (int a2 = lo2; a2 <= hi2; ++a2)
-      for (int a1 = -1; a1 <= 1; ++a1)
-        for (int a0 = -1; a0 <= 1; ++a0) {
-          const int fa[3] = {2 * Ic[0] + a0, 2 * Ic[1] + a1, D == 3 ? 2 * Ic[2] + a2 : 0};
-          if (fa[0] < 0 || fa[0] >= F.nn[0] || fa[1] < 0 || fa[1] >= F.nn[1] || fa[2] < 0 || fa[2] >= F.nn[2])
-            continue;
-          const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
-          const int64_t a = fa[0] + (int64_t)F.nn[0] * (fa[1] + (int64_t)F.nn[1] * fa[2]);
-          if (F.inst && F.inst[a] != Cl.inst[I]) continue;
-          for (int b2 = lo2; b2 <= hi2; ++b2)
-            for (int b1 = -1; b1 <= 1; ++b1)
-              for (int b0 = -1; b0 <= 1; ++b0) {
-                const int fb[3] = {2 * Jc[0] + b0, 2 * Jc[1] + b1, D == 3 ? 2 * Jc[2] + b2 : 0};
-                if (fb[0] < 0 || fb[0] >= F.nn[0] || fb[1] < 0 || fb[1] >= F.nn[1] || fb[2] < 0 ||
-                    fb[2] >= F.nn[2])
-                  continue;
-                const real wb = pw(fb[0], Jc[0]) * pw(fb[1], Jc[1]) * (D == 3 ? pw(fb[2], Jc[2]) : 1.0);
-                {
-                  const int64_t bq = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
-                  if (F.inst && F.inst[bq] != Cl.inst[Jn]) continue;
-                }
-                const real *blk = nullptr;
-                if (!FST) {
-                  const int e = mask_block<D>(F.mask, F.row_ptr, (int)a, fb[0] - fa[0], fb[1] - fa[1],
-                                              fb[2] - fa[2]);
-                  if (e < 0) continue;
-                  blk = F.val + (int64_t)e * B * B;
-                } else {
-                  const int d0 = fb[0] - fa[0], d1 = fb[1] - fa[1], d2 = fb[2] - fa[2];
-                  if (d0 < -2 || d0 > 2 || d1 < -2 || d1 > 2 || d2 < -2 || d2 > 2) continue;
-                  const int sl = (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0);
-                  blk = F.sval + (a * NS + sl) * B * B;
-                }
-                const real w = wa * wb;
-                if (!FST) {
-                  const int64_t b = fb[0] + (int64_t)F.nn[0] * (fb[1] + (int64_t)F.nn[1] * fb[2]);
-                  for (int i = 0; i < B; ++i) {
-                    if (free_w(F, a, i) == 0.0) continue;
-                    for (int j = 0; j < B; ++j)
-                      if (free_w(F, b, j) != 0.0) acc[i * B + j] = fma(w, blk[i * B + j], acc[i * B + j]);
-                  }
-                } else {
-                  for (int i = 0; i < B * B; ++i) acc[i] = fma(w, blk[i], acc[i]);
-                }
-              }
-        }
-  }
-  for (int i = 0; i < B * B; ++i) Cl.sval[(I * NS + s) * B * B + i] = acc[i];
-}
-
-// Galerkin product of the block-CSR finest level in two passes (the fine
-// operator couples nodes up to 3 apart per axis):
+// Galerkin product P^T A P in two passes, from the block-CSR finest level
+// (couplings up to 3 apart per axis) or a stencil level (up to 2 apart):
 //   k_mg_ap:   T_a(J) = sum_b w_bJ A_ab over the children b of J, for every
 //              fine row a and coarse node J of the 5^d window centred on
 //              floor(a / 2) (the coarse nodes a row can reach); thread per
 //              (window slot, a), T stored slot-major;
 //   k_mg_rap2: A_c(I, J) = sum_a w_aI T_a(J) over the 3^d children a of I;
 //              thread per (stencil slot, I).
-// Same masks as the one-pass product (Dirichlet DOFs out of the transfers,
-// instances kept apart), grouped as (P^T (A P)): a few lookups and FMAs per
-// coarse entry instead of one per (a, b) pair.
-template <int B, int D>
+// Dirichlet DOFs are masked out of the finest level's transfers only, and
+// instances are kept apart on every level; grouped as (P^T (A P)), a coarse
+// entry costs a few lookups and 3^d FMA blocks instead of one per (a, b) pair
+// (measured on the slope's stencil levels: the one-pass product took 20 ms
+// per set-up).
+template <int B, int D, bool FST>
 __global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
   constexpr int NS = NS_<D>::v;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1045,12 +978,19 @@ __global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
         for (int b0 = blo[0]; b0 <= bhi[0]; ++b0) {
           const int64_t b = b0 + (int64_t)F.nn[0] * (b1 + (int64_t)F.nn[1] * b2);
           if (F.inst && F.inst[b] != Cl.inst[Jn]) continue;
-          const int e = mask_block<D>(F.mask, F.row_ptr, (int)a, b0 - fa[0], b1 - fa[1], b2 - fa[2]);
-          if (e < 0) continue;
+          const real *blk;
+          if (!FST) {  // finest level: block-CSR, found by the coupling mask
+            const int e = mask_block<D>(F.mask, F.row_ptr, (int)a, b0 - fa[0], b1 - fa[1], b2 - fa[2]);
+            if (e < 0) continue;
+            blk = F.val + (int64_t)e * B * B;
+          } else {     // stencil level: the 5^d slot of b - a
+            const int d0 = b0 - fa[0], d1 = b1 - fa[1], d2 = b2 - fa[2];
+            if (d0 < -2 || d0 > 2 || d1 < -2 || d1 > 2 || d2 < -2 || d2 > 2) continue;
+            blk = F.sval + (a * NS + (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0)) * B * B;
+          }
           const real w = pw(b0, Jc[0]) * pw(b1, Jc[1]) * (D == 3 ? pw(b2, Jc[2]) : 1.0);
-          const real *blk = F.val + (int64_t)e * B * B;
           for (int j = 0; j < B; ++j) {
-            const real wj = w * free_w(F, b, j);
+            const real wj = FST ? w : w * free_w(F, b, j);  // Dirichlet masks: finest transfers only
             for (int i = 0; i < B; ++i) acc[i * B + j] = fma(wj, blk[i * B + j], acc[i * B + j]);
           }
         }
@@ -1058,7 +998,7 @@ __global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
   for (int i = 0; i < B * B; ++i) T[t * B * B + i] = acc[i];  // t = s * nnodes + a
 }
 
-template <int B, int D>
+template <int B, int D, bool FST>
 __global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
   constexpr int NS = NS_<D>::v;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1092,7 +1032,7 @@ __global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
           const int sl = (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0);
           const real *ta = T + ((int64_t)sl * F.nnodes + a) * B * B;
           for (int i = 0; i < B; ++i) {
-            const real wi = wa * free_w(F, a, i);
+            const real wi = FST ? wa : wa * free_w(F, a, i);
             for (int j = 0; j < B; ++j) acc[i * B + j] = fma(wi, ta[i * B + j], acc[i * B + j]);
           }
         }
@@ -1110,7 +1050,7 @@ struct MGHier<MG_REAL> {
   MG_REAL *x[16], *x2[16], *b[16], *r[16];
   MG_REAL *Ad = nullptr, *Ai = nullptr;  // dense coarsest operator (LU factors after set-up) and its inverse
   int *piv = nullptr;                    // row interchanges of the LU factorisation
-  MG_REAL *apT = nullptr;                // finest level x 5^d window: A P, first pass of the level-1 product
+  MG_REAL *apT = nullptr;                // finest level x 5^d window: A P, first pass of a level's product
   int ncoarse = 0;                       // unknowns of the coarsest level
 };
 
@@ -1124,13 +1064,17 @@ void mg_setup_t(Ctx &c, MGHier<real> &H) {
     if (l > 0) {
       constexpr int NS = NS_<D>::v;
       const int g2 = nblk(L.nnodes * NS);
+      // two passes, P^T (A P), on every level (the intermediate of the finest
+      // level is the largest): on the stencil levels a few lookups and 3^d
+      // FMA blocks per coarse entry instead of 3^d x 3^d in one pass
       if (l == 1) {
-        k_mg_ap<B, D><<<nblk(H.L[0].nnodes * NS), TPB, 0, c.st>>>(H.L[0], L, H.apT);
-        k_mg_rap2<B, D><<<g2, TPB, 0, c.st>>>(H.L[0], L, H.apT);
-        UPMPM_LAUNCH(c);
+        k_mg_ap<B, D, false><<<nblk(H.L[0].nnodes * NS), TPB, 0, c.st>>>(H.L[0], L, H.apT);
+        k_mg_rap2<B, D, false><<<g2, TPB, 0, c.st>>>(H.L[0], L, H.apT);
       } else {
-        k_mg_rap<B, D, true><<<g2, TPB, 0, c.st>>>(H.L[l - 1], L);
+        k_mg_ap<B, D, true><<<nblk(H.L[l - 1].nnodes * NS), TPB, 0, c.st>>>(H.L[l - 1], L, H.apT);
+        k_mg_rap2<B, D, true><<<g2, TPB, 0, c.st>>>(H.L[l - 1], L, H.apT);
       }
+      UPMPM_LAUNCH(c);
       UPMPM_LAUNCH(c);
       k_mg_dinv<B, D, true><<<nbk, TPB, 0, c.st>>>(L, c.err);
     } else {
@@ -1476,7 +1420,7 @@ void schur_split(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *v, MG_REAL *x0) {
   const int64_t nn = c.g.nnodes;
   MGHier<real> &HS = *S.mgS, &HA = *S.mgA;
   const Geom g = geom(c, nn);
-  const real *dsc = S.dscale;
+  const real *dsc = S.dscinv;  // D^-1: the unscaled v is D^-1 times the scaled one
   const real om = mg_omega(c);
   if (c.schur_lower()) {
     const real *dinv = HA.L[0].dinv;
@@ -1520,7 +1464,7 @@ void schur_core(Ctx &c, LinSys<MG_REAL> &S) {
 void schur_merge(Ctx &c, LinSys<MG_REAL> &S, const MG_REAL *zu, const MG_REAL *zp, MG_REAL *z) {
   const int64_t nn = c.g.nnodes;
   const Geom g = geom(c, nn);
-  const real *dsc = S.dscale;
+  const real *dsc = S.dscinv;  // D^-1: the unscaled v is D^-1 times the scaled one
   if (c.d == 2) launch_pdl(c, k_merge<2>, g.blocks, g.tpb, 0, nn, zu, zp, dsc, z);
   else launch_pdl(c, k_merge<3>, g.blocks, g.tpb, 0, nn, zu, zp, dsc, z);
 }

@@ -162,13 +162,14 @@ __device__ inline int find_diag(const int32_t *__restrict__ row_ptr, const int32
 template <int NB, typename T>
 __global__ void k_diag_scale(int64_t nnodes, const int32_t *__restrict__ row_ptr,
                              const int32_t *__restrict__ col, const T *__restrict__ val,
-                             T *__restrict__ dsc) {
+                             T *__restrict__ dsc, T *__restrict__ dsci) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (a >= nnodes) return;
   const int e = find_diag(row_ptr, col, a);
   for (int r = 0; r < NB; ++r) {
     const double d = e >= 0 ? fabs((double)val[(int64_t)e * NB * NB + r * NB + r]) : 0.0;
     dsc[a * NB + r] = (T)(d > 0.0 ? 1.0 / sqrt(d) : 1.0);
+    dsci[a * NB + r] = (T)(d > 0.0 ? sqrt(d) : 1.0);
   }
 }
 
@@ -707,6 +708,7 @@ int linsys_alloc(Ctx &c, LinSys<T> &S, bool krylov) {
     if (!rc) rc = dmalloc(p, n);
   };
   A(&S.dscale, N);
+  A(&S.dscinv, N);
   A(&S.dinv, nn * nb * nb);
   A(&S.rhs, N);
   A(&S.x, N);
@@ -722,10 +724,10 @@ int linsys_alloc(Ctx &c, LinSys<T> &S, bool krylov) {
 template <typename T>
 void linsys_free(LinSys<T> &S) {
   schur_free<T>(S);
-  T *ptrs[] = {S.val, S.dscale, S.dinv, S.rhs, S.x, S.w, S.V, S.Z};
+  T *ptrs[] = {S.val, S.dscale, S.dscinv, S.dinv, S.rhs, S.x, S.w, S.V, S.Z};
   for (T *p : ptrs)
     if (p) cudaFree(p);
-  S.val = S.dscale = S.dinv = S.rhs = S.x = S.w = S.V = S.Z = nullptr;
+  S.val = S.dscale = S.dscinv = S.dinv = S.rhs = S.x = S.w = S.V = S.Z = nullptr;
   S.cap = 0;
 }
 
@@ -747,10 +749,10 @@ template <typename T>
 void run_scale_system(Ctx &c, LinSys<T> &S, const double *R) {
   const int64_t nn = c.g.nnodes;
   if (c.nb == 3) {
-    k_diag_scale<3, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale);
+    k_diag_scale<3, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.dscinv);
     k_scale_matrix<3, T><<<nblk(c.nnzb * 9), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
   } else {
-    k_diag_scale<4, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale);
+    k_diag_scale<4, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.dscinv);
     k_scale_matrix<4, T><<<nblk(c.nnzb * 16), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
   }
   k_scale_rhs<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), R, S.dscale, S.rhs);
