@@ -415,6 +415,19 @@ int mpm_debug_eval(mpm_ctx *ctx, const double *X, double *R, double *Jv, int32_t
  * is the preconditioner of that scaled system.  X, v, z: nnodes*(dim+1). */
 int mpm_debug_precond(mpm_ctx *ctx, const double *X, const double *v, double *z);
 
+/* The FP32 Jacobian of the mixed mode (Eq. jacobian-system-stabilized-ppp
+ * evaluated in FP32 from FP32 copies of the point records, as the mixed
+ * Newton step assembles it) at the nodal unknowns X (FP64, as in
+ * mpm_debug_eval) of the prepared step, assembled by one given kernel
+ * configuration: form 0 per-term, 1 staged per-(point, node) vectors; tpb 64,
+ * 128 or 256 threads per block (the candidates of mpm_options.autotune).  Jv: nnzb blocks of
+ * (dim+1)^2 floats in the pattern's order, before (apply_bc = 0) or after
+ * (apply_bc = 1) Dirichlet elimination.  MPM_ERR_BAD_ARG for a context that
+ * is not mixed-precision, a form or block size outside these sets, or no
+ * prepared step. */
+int mpm_debug_jacobian32(mpm_ctx *ctx, const double *X, int32_t form, int32_t tpb, float *Jv,
+                         int32_t apply_bc);
+
 /* ------------------------------------------------------------------------
  * Allocation-free binning.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory where they bin points

@@ -24,6 +24,9 @@ DevView Ctx::view() const {
   v.sh_first = sh_first;
   v.sh_cnt = sh_cnt;
   v.sh_box = sh_box;
+  v.fb_start = fb_start;
+  v.fb_perm = fb_perm;
+  v.fb_cmax = fb_cmax;
   v.pn_base = pn_base;
   v.sh_S = sh_S;
   v.sh_dS = sh_dS;
@@ -306,6 +309,7 @@ int prepare_step(Ctx &c, double dt, const mpm_loads *L, const mpm_bcs *B) {
   run_shape(c);
   run_mass(c);
   rc = read_dev_err(c);
+  if (!rc) rc = run_first_bins(c);
   prof_end(c, MPM_PROF_PREP);
   if (rc) return rc;
   run_p2g(c);
@@ -480,7 +484,7 @@ void free_all(Ctx &c) {
   for (float *p : fptrs)
     if (p) cudaFree(p);
   void *ptrs[] = {c.pf, c.pf_alt, c.pid, c.pid_alt, c.surf, c.surf_alt, c.cell, c.cell_tmp,
-                  c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_box, c.pn_cnt, c.pn_base, c.sh_S, c.sh_dS,
+                  c.cell_start, c.cell_cursor, c.perm, c.sh_first, c.sh_cnt, c.sh_box, c.fb_key, c.fb_start, c.fb_cursor, c.fb_perm, c.fb_cmax, c.pn_cnt, c.pn_base, c.sh_S, c.sh_dS,
                   c.sh_S0, c.m, c.rec, c.pn, c.M, c.Pn, c.vn, c.an, c.pdn, c.pddn, c.phi, c.act, c.fsd, c.sh_nrm, c.fixed, c.u_fixed,
                   c.p_fixed, c.u_value, c.p_value, c.trac, c.trac_raw, c.flux, c.err, c.row_nnz,
                   c.row_ptr, c.row_of, c.col, c.row_mask, c.X, c.R, c.dX, c.stage, c.H, c.gvec,
@@ -669,6 +673,11 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   A(&c.sh_first, 3 * n);
   A(&c.sh_cnt, n);
   A(&c.sh_box, n);
+  A(&c.fb_key, n);
+  A(&c.fb_perm, n);
+  A(&c.fb_start, nn + 1);
+  A(&c.fb_cursor, nn + 1);
+  A(&c.fb_cmax, 4);
   A(&c.pn_cnt, n + 1);
   A(&c.pn_base, n + 1);
   A(&c.sh_S, 3 * MAXS * n);
@@ -1241,6 +1250,32 @@ int mpm_debug_eval(mpm_ctx *h, const double *X, double *R, double *Jv, int32_t a
     cudaMemcpyAsync(Jv, c.L64.val, sizeof(double) * c.nnzb * c.nb * c.nb, cudaMemcpyDeviceToHost, c.st);
   }
   return check_cuda(c, cudaStreamSynchronize(c.st), "debug_eval");
+}
+
+int mpm_debug_jacobian32(mpm_ctx *h, const double *X, int32_t form, int32_t tpb, float *Jv, int32_t apply_bc) {
+  if (!h || !X || !Jv) return MPM_ERR_BAD_ARG;
+  Ctx &c = h->c;
+  if (!c.prepared) {
+    c.last_error = "no step prepared: call mpm_debug_prepare first";
+    return MPM_ERR_BAD_ARG;
+  }
+  if (!c.have32) {
+    c.last_error = "the FP32 Jacobian exists in mixed-precision contexts only";
+    return MPM_ERR_BAD_ARG;
+  }
+  if (form < 0 || form >= Ctx::JAC_FORMS || (tpb != 64 && tpb != 128 && tpb != 256)) {
+    c.last_error = "form must be 0 or 1 and tpb 64, 128 or 256";
+    return MPM_ERR_BAD_ARG;
+  }
+  const int64_t N = c.N();
+  cudaMemcpyAsync(c.dX, X, sizeof(double) * N, cudaMemcpyHostToDevice, c.st);
+  run_point_eval(c, c.dX);
+  int rc = read_dev_err(c);
+  if (rc) return rc;
+  rc = run_jacobian32_form(c, c.L32.val, apply_bc, form, tpb);
+  if (rc) return rc;
+  cudaMemcpyAsync(Jv, c.L32.val, sizeof(float) * c.nnzb * c.nb * c.nb, cudaMemcpyDeviceToHost, c.st);
+  return check_cuda(c, cudaStreamSynchronize(c.st), "debug_jacobian32");
 }
 
 int mpm_debug_precond(mpm_ctx *h, const double *X, const double *v, double *z) {

@@ -10,7 +10,13 @@
 //   newmark-linearization and delta ln J = div u for the quasi-static form.
 //
 // Design: gather, not scatter.  Points are cell-sorted, so the points that
-// can touch node a live in a small box of cells around it.  The residual is
+// can touch node a live in a small box of cells around it; the pattern, the
+// consistent mass and the Jacobian walk instead the first-node bins (the
+// points indexed by the first node of their support box, built per step),
+// whose box around a node (or a pair of nodes) is one narrower per axis,
+// fewer candidates for the kernels that read little per point or stage their
+// reads (the residual, which reads many record fields of each point, keeps the
+// cells' contiguous runs of points).  The residual is
 // computed by one thread per node row and each Jacobian block by one thread,
 // each summing its points in a fixed order: no floating-point atomics, results
 // are deterministic, and every (point, a, b) block term is computed exactly
@@ -140,30 +146,31 @@ __global__ void k_pattern_count(GridP g, DevView v, uint64_t *__restrict__ mask,
     const int bit = 3 + 7 * (D > 1 ? 3 : 0) + 49 * (D > 2 ? 3 : 0);
     mk[bit >> 6] |= 1ull << (bit & 63);
   }
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) cand_range<GIMP>(ac[k], g.nc[k], lo[k], hi[k]);
+  int lo[3], hi[3];
+  fb_window<D>(v.fb_cmax, ac, ac, lo, hi);
   const int64_t n = v.n;
-  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
-    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
-      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
-        const int64_t cid = cell_index(g, c0, c1, c2);
-        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
-          int off[3];
-          if (!in_box<D>(v, q, ac, off)) continue;
-          const int packed = v.sh_cnt[q];
-          int ob[3] = {0, 0, 0}, oe[3] = {0, 0, 0};
-          for (int k = 0; k < D; ++k) {
-            ob[k] = v.sh_first[k * n + q] - ac[k];
-            oe[k] = ob[k] + unpack_cnt(packed, k) - 1;
-          }
-          for (int o2 = ob[2]; o2 <= oe[2]; ++o2)
-            for (int o1 = ob[1]; o1 <= oe[1]; ++o1)
-              for (int o0 = ob[0]; o0 <= oe[0]; ++o0) {
-                const int bit = (o0 + 3) + 7 * (D > 1 ? o1 + 3 : 0) + 49 * (D > 2 ? o2 + 3 : 0);
-                mk[bit >> 6] |= 1ull << (bit & 63);
-              }
+  for (int f2 = lo[2]; f2 <= hi[2]; ++f2)
+    for (int f1 = lo[1]; f1 <= hi[1]; ++f1) {
+      int32_t ib, ie;
+      fb_run(g, v.fb_start, lo[0], hi[0], f1, f2, ib, ie);
+      for (int32_t i = ib; i < ie; ++i) {
+        const int32_t q = v.fb_perm[i];
+        int off[3];
+        if (!in_box<D>(v, q, ac, off)) continue;
+        const int packed = v.sh_cnt[q];
+        int ob[3] = {0, 0, 0}, oe[3] = {0, 0, 0};
+        for (int k = 0; k < D; ++k) {
+          ob[k] = v.sh_first[k * n + q] - ac[k];
+          oe[k] = ob[k] + unpack_cnt(packed, k) - 1;
         }
+        for (int o2 = ob[2]; o2 <= oe[2]; ++o2)
+          for (int o1 = ob[1]; o1 <= oe[1]; ++o1)
+            for (int o0 = ob[0]; o0 <= oe[0]; ++o0) {
+              const int bit = (o0 + 3) + 7 * (D > 1 ? o1 + 3 : 0) + 49 * (D > 2 ? o2 + 3 : 0);
+              mk[bit >> 6] |= 1ull << (bit & 63);
+            }
       }
+    }
   int cnt = 0;
   for (int w = 0; w < MASKW; ++w) {
     mask[a * MASKW + w] = mk[w];
@@ -225,7 +232,8 @@ __global__ void k_initial_guess(GridP g, double phi_min, DevView v, double *__re
 // Fixed-stress term of the pressure Schur complement, lumped per node:
 // fsd_a = sum_p S_ap b2_p vol_p / (cs_p K_p), K = lambda + 2 (G - lambda ln J) / d
 // (the drained bulk modulus of the current records).  Node-centric gather in
-// (cell, id) order.
+// (cell, id) order: these gathers read many record fields per point, and the
+// cells' contiguous runs of points serve them better than the first-node bins.
 template <int D, bool GIMP>
 __global__ void k_fs_diag(GridP g, DevView v, double *__restrict__ out) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -585,7 +593,7 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
 // One thread per block (a, b) (per symmetric pair of blocks, below), mapped
 // so that the 32 lanes of a warp hold the same coupling offset (b - a in
 // [-3, 3]^d) in 32 consecutive rows and walk the same number of candidate
-// cells; a slot absent from the row's pattern exits.
+// bins; a slot absent from the row's pattern exits.
 template <int D>
 __device__ inline int64_t block_of_slot(const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                                         int64_t a, int s) {
@@ -814,7 +822,44 @@ struct PnRec {
   }
 };
 
-template <int D, bool GIMP, bool DYN, bool HK, typename T, typename R>
+// Every candidate point q of the node pair (ac, bc), in a fixed order: the
+// points of the first-node bins that can hold both nodes (FB), or those of the
+// cells around both (each x-run of cells is one contiguous run of the
+// cell-sorted points).  The bins visit fewer candidates; the cells visit them
+// in storage order, whose locality serves the FP64 staged kernel better (its
+// records are read in point order), while the FP32 kernels gain from the
+// bins.
+template <int D, bool GIMP, bool FB, typename F>
+__device__ __forceinline__ void for_pair_candidates(const GridP &g, const DevView &v, const int ac[3],
+                                                    const int bc[3], F &&f) {
+  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  if constexpr (FB) {
+    fb_window<D>(v.fb_cmax, ac, bc, lo, hi);
+    for (int f2 = lo[2]; f2 <= hi[2]; ++f2)
+      for (int f1 = lo[1]; f1 <= hi[1]; ++f1) {
+        int32_t ib, ie;
+        fb_run(g, v.fb_start, lo[0], hi[0], f1, f2, ib, ie);
+        for (int32_t i = ib; i < ie; ++i) f(v.fb_perm[i]);
+      }
+  } else {
+    for (int k = 0; k < D; ++k) {
+      int l1, h1, l2, h2;
+      cand_range<GIMP>(ac[k], g.nc[k], l1, h1);
+      cand_range<GIMP>(bc[k], g.nc[k], l2, h2);
+      lo[k] = max(l1, l2);
+      hi[k] = min(h1, h2);
+    }
+    if (lo[0] > hi[0]) return;
+    for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
+      for (int c1 = lo[1]; c1 <= hi[1]; ++c1) {
+        const int64_t c0 = cell_index(g, lo[0], c1, c2);
+        const int32_t qb = v.cell_start[c0], qe = v.cell_start[c0 + (hi[0] - lo[0]) + 1];
+        for (int32_t q = qb; q < qe; ++q) f(q);
+      }
+  }
+}
+
+template <int D, bool GIMP, bool DYN, bool HK, bool FB, typename T, typename R>
 __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn,
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
@@ -832,84 +877,71 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   int ac[3], bc[3];
   node_coords(g, a, ac);
   node_coords(g, bn, bc);
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) {
-    int l1, h1, l2, h2;
-    cand_range<GIMP>(ac[k], g.nc[k], l1, h1);
-    cand_range<GIMP>(bc[k], g.nc[k], l2, h2);
-    lo[k] = max(l1, l2);
-    hi[k] = min(h1, h2);
-  }
   // pair accumulators: A (shared, for (a, b); (b, a) gets its transpose), C
   // (shared), B1 and B2 of each of the two blocks
   // kgp: the grad p part of B2, (p7 g_a.g_b) grad p, the same for both blocks
   R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], kgp[D], C = 0;
   for (int i = 0; i < D * D; ++i) A[i] = 0;
   for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = kgp[i] = 0;
-  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
-    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
-      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
-        const int64_t cid = cell_index(g, c0, c1, c2);
-        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
-          int oa[3], ob[3];
-          const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
-          if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) continue;
-          // the point's records: its box nodes x-fastest, then its own
-          const R *P = pn + (int64_t)v.pn_base[q] * NPS;
-          const int c0 = unpack_cnt(bx.w, 0), c1 = D > 1 ? unpack_cnt(bx.w, 1) : 1,
-                    c2 = D > 2 ? unpack_cnt(bx.w, 2) : 1;
-          PnRec<R, NPS> pa;        // the row node's record: all of it
-          PnRec<R, L::BPART> pb;   // the column node's: the fields read for both nodes
-          pa.load(P + (oa[0] + c0 * (oa[1] + c1 * oa[2])) * NPS);
-          pb.load(P + (ob[0] + c0 * (ob[1] + c1 * ob[2])) * NPS);
-          const R *pp = P + (c0 * c1 * c2) * NPS;
-          R ga[3], gb[3];
-          for (int j = 0; j < D; ++j) {
-            ga[j] = pa[L::G + j];
-            gb[j] = pb[L::G + j];
-          }
-          // A_ik = g_a,i (p2 g_b)_k - g_b,i (p3 g_a)_k - delta_ik d,
-          // d = h_a.g_b (+ p4 S_a S_b): stress, geometric, pressure, Kelvin
-          // and inertia terms with the point's coefficients staged per node
-          R dg = 0, kgab = 0;
-          for (int j = 0; j < D; ++j) {
-            dg = fma(pa[L::H + j], gb[j], dg);
-            kgab = fma(pa[L::P7G + j], gb[j], kgab);  // p7 g_a.g_b
-          }
-          if (DYN) dg = fma(pa[L::MS], pb[L::S], dg);
-          for (int i = 0; i < D; ++i)
-            for (int k = 0; k < D; ++k) {
-              R acc = fma(ga[i], pb[L::P2G + k], A[i * D + k]);
-              acc = fma(-gb[i], pa[L::P3G + k], acc);
-              if (HK)  // material part of the Hencky tangent, staged per node
-                for (int l = 0; l < D; ++l) acc = fma(pa[L::U + (i * D + k) * D + l], gb[l], acc);
-              A[i * D + k] = i == k ? acc - dg : acc;
-            }
-          // B1 column of (a, b): (p5 S_b) g_a; of (b, a): (p5 S_a) g_b
-          const R p5Sb = pb[L::P5S], p5Sa = pa[L::P5S];
-          for (int i = 0; i < D; ++i) b1ab[i] = fma(p5Sb, ga[i], b1ab[i]);
-          // B2 row of (a, b): (p6 S_a + p7 g_a.w) g_b - (p7 g_b.w) g_a - (p7 g_a.g_b) grad p
-          //                   (- p5 S_a g_b.grad v, Newmark); (b, a): a <-> b
-          const R ca = pa[L::C], eb = pb[L::E];
-          for (int k = 0; k < D; ++k) {
-            R tk = fma(ca, gb[k], b2ab[k]);
-            if (DYN) tk = fma(-p5Sa, pb[L::GV + k], tk);
-            b2ab[k] = fma(-eb, ga[k], tk);
-            kgp[k] = fma(kgab, pp[L::GP + k], kgp[k]);
-          }
-          if (!diag) {
-            for (int i = 0; i < D; ++i) b1ba[i] = fma(p5Sa, gb[i], b1ba[i]);
-            const R cb = pb[L::C], ea = pa[L::E];
-            for (int k = 0; k < D; ++k) {
-              R tk = fma(cb, ga[k], b2ba[k]);
-              if (DYN) tk = fma(-p5Sb, pa[L::GV + k], tk);
-              b2ba[k] = fma(-ea, gb[k], tk);
-            }
-          }
-          // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b (symmetric)
-          C = fma(pa[L::P8ST], pb[L::ST], C + kgab);
-        }
+  for_pair_candidates<D, GIMP, FB>(g, v, ac, bc, [&](const int32_t q) {
+    int oa[3], ob[3];
+    const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
+    if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) return;
+    // the point's records: its box nodes x-fastest, then its own
+    const R *P = pn + (int64_t)v.pn_base[q] * NPS;
+    const int c0 = unpack_cnt(bx.w, 0), c1 = D > 1 ? unpack_cnt(bx.w, 1) : 1,
+              c2 = D > 2 ? unpack_cnt(bx.w, 2) : 1;
+    PnRec<R, NPS> pa;        // the row node's record: all of it
+    PnRec<R, L::BPART> pb;   // the column node's: the fields read for both nodes
+    pa.load(P + (oa[0] + c0 * (oa[1] + c1 * oa[2])) * NPS);
+    pb.load(P + (ob[0] + c0 * (ob[1] + c1 * ob[2])) * NPS);
+    const R *pp = P + (c0 * c1 * c2) * NPS;
+    R ga[3], gb[3];
+    for (int j = 0; j < D; ++j) {
+      ga[j] = pa[L::G + j];
+      gb[j] = pb[L::G + j];
+    }
+    // A_ik = g_a,i (p2 g_b)_k - g_b,i (p3 g_a)_k - delta_ik d,
+    // d = h_a.g_b (+ p4 S_a S_b): stress, geometric, pressure, Kelvin
+    // and inertia terms with the point's coefficients staged per node
+    R dg = 0, kgab = 0;
+    for (int j = 0; j < D; ++j) {
+      dg = fma(pa[L::H + j], gb[j], dg);
+      kgab = fma(pa[L::P7G + j], gb[j], kgab);  // p7 g_a.g_b
+    }
+    if (DYN) dg = fma(pa[L::MS], pb[L::S], dg);
+    for (int i = 0; i < D; ++i)
+      for (int k = 0; k < D; ++k) {
+        R acc = fma(ga[i], pb[L::P2G + k], A[i * D + k]);
+        acc = fma(-gb[i], pa[L::P3G + k], acc);
+        if (HK)  // material part of the Hencky tangent, staged per node
+          for (int l = 0; l < D; ++l) acc = fma(pa[L::U + (i * D + k) * D + l], gb[l], acc);
+        A[i * D + k] = i == k ? acc - dg : acc;
       }
+    // B1 column of (a, b): (p5 S_b) g_a; of (b, a): (p5 S_a) g_b
+    const R p5Sb = pb[L::P5S], p5Sa = pa[L::P5S];
+    for (int i = 0; i < D; ++i) b1ab[i] = fma(p5Sb, ga[i], b1ab[i]);
+    // B2 row of (a, b): (p6 S_a + p7 g_a.w) g_b - (p7 g_b.w) g_a - (p7 g_a.g_b) grad p
+    //                   (- p5 S_a g_b.grad v, Newmark); (b, a): a <-> b
+    const R ca = pa[L::C], eb = pb[L::E];
+    for (int k = 0; k < D; ++k) {
+      R tk = fma(ca, gb[k], b2ab[k]);
+      if (DYN) tk = fma(-p5Sa, pb[L::GV + k], tk);
+      b2ab[k] = fma(-eb, ga[k], tk);
+      kgp[k] = fma(kgab, pp[L::GP + k], kgp[k]);
+    }
+    if (!diag) {
+      for (int i = 0; i < D; ++i) b1ba[i] = fma(p5Sa, gb[i], b1ba[i]);
+      const R cb = pb[L::C], ea = pa[L::E];
+      for (int k = 0; k < D; ++k) {
+        R tk = fma(cb, ga[k], b2ba[k]);
+        if (DYN) tk = fma(-p5Sb, pa[L::GV + k], tk);
+        b2ba[k] = fma(-ea, gb[k], tk);
+      }
+    }
+    // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b (symmetric)
+    C = fma(pa[L::P8ST], pb[L::ST], C + kgab);
+  });
   R B[NB * NB];
   for (int i = 0; i < D; ++i) {
     for (int k = 0; k < D; ++k) B[i * NB + k] = A[i * D + k];
@@ -933,7 +965,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
 // FP32 variant (mixed mode): the node vectors are recomputed per term from the
 // FP32 basis and records; with FP32 arithmetic plentiful this beats staging.
 // Symmetric pairs as in k_jacobian: one thread per unordered pair (a, b).
-template <int D, bool GIMP, bool DYN, typename T, typename R>
+template <int D, bool GIMP, bool DYN, bool FB, typename T, typename R>
 __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
                            const uint64_t *__restrict__ mask, const int32_t *__restrict__ row_ptr,
                            const int32_t *__restrict__ col, T *__restrict__ val, int apply_bc) {
@@ -950,93 +982,80 @@ __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA
   int ac[3], bc[3];
   node_coords(g, a, ac);
   node_coords(g, bn, bc);
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) {
-    int l1, h1, l2, h2;
-    cand_range<GIMP>(ac[k], g.nc[k], l1, h1);
-    cand_range<GIMP>(bc[k], g.nc[k], l2, h2);
-    lo[k] = max(l1, l2);
-    hi[k] = min(h1, h2);
-  }
   R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], kgp[D], C = 0;
   for (int i = 0; i < D * D; ++i) A[i] = 0;
   for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = kgp[i] = 0;
   const R cvis = DYN ? (R)(s.alpha_vis * s.gamma / (s.beta * s.dt)) : R(0);
-  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
-    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
-      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
-        const int64_t cid = cell_index(g, c0, c1, c2);
-        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
-          int oa[3], ob[3];
-          const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
-          if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) continue;
-          R Sa, S0a, Gna[3], Sb, S0b, Gnb[3], ga[3], gb[3];
-          basis_at_t<D, R>(BA, q, oa, a, Sa, S0a, Gna);
-          basis_at_t<D, R>(BA, q, ob, bn, Sb, S0b, Gnb);
-          for (int j = 0; j < D; ++j) {
-            R sa = 0, sb = 0;
-            for (int k = 0; k < D; ++k) {
-              const R fkj = rec[(RC_FINV + k * D + j) * n + q];
-              sa += Gna[k] * fkj;
-              sb += Gnb[k] * fkj;
-            }
-            ga[j] = sa;
-            gb[j] = sb;
-          }
-          const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
-          const R mu = rec[RC_MUP * n + q], lam = rec[RC_LAM * n + q], kv = rec[RC_KV * n + q];
-          R gab = 0, gtg = 0, gaw = 0, gbw = 0;
-          for (int j = 0; j < D; ++j) {
-            gab += ga[j] * gb[j];
-            const R wj = rec[(RC_W + j) * n + q];
-            gaw += ga[j] * wj;
-            gbw += gb[j] * wj;
-            for (int l = 0; l < D; ++l) gtg += ga[j] * rec[(RC_TAU + j * D + l) * n + q] * gb[l];
-          }
-          const R ms = DYN ? rec[RC_MS * n + q] * Sa * Sb : R(0);
-          for (int i = 0; i < D; ++i)
-            for (int k = 0; k < D; ++k) {
-              const R dik = i == k ? R(1) : R(0);
-              const R sym = mu * (dik * gab + ga[k] * gb[i]);
-              R Aik = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
-              Aik += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
-              if (DYN) {
-                Aik -= cs * cvis * (lam * ga[i] * gb[k] + sym);
-                Aik -= dik * ms;
-              }
-              A[i * D + k] += Aik;
-            }
-          const R b2 = rec[RC_B2 * n + q], dkv = rec[RC_DKV * n + q];
-          for (int i = 0; i < D; ++i) b1ab[i] += vol * ga[i] * Sb;
-          for (int k = 0; k < D; ++k) {
-            R t = Sa * b2 * gb[k];
-            if (DYN) {
-              R gbgv = 0;
-              for (int j = 0; j < D; ++j) gbgv += gb[j] * rec[(RC_GV + j * D + k) * n + q];
-              t -= vol * Sa * gbgv;
-            }
-            t += kv * (gb[k] * gaw - ga[k] * gbw);
-            t += dkv * gb[k] * gaw;  // dk/dJ (Kozeny-Carman)
-            b2ab[k] += t;
-            kgp[k] += kv * gab * rec[(RC_GP + k) * n + q];  // grad p part, the same for both blocks
-          }
-          if (!diag) {
-            for (int i = 0; i < D; ++i) b1ba[i] += vol * gb[i] * Sa;
-            for (int k = 0; k < D; ++k) {
-              R t = Sb * b2 * ga[k];
-              if (DYN) {
-                R gagv = 0;
-                for (int j = 0; j < D; ++j) gagv += ga[j] * rec[(RC_GV + j * D + k) * n + q];
-                t -= vol * Sb * gagv;
-              }
-              t += kv * (ga[k] * gbw - gb[k] * gaw);
-              t += dkv * ga[k] * gbw;
-              b2ba[k] += t;
-            }
-          }
-          C += kv * gab + rec[RC_CST * n + q] * (Sa - S0a) * (Sb - S0b);
-        }
+  for_pair_candidates<D, GIMP, FB>(g, v, ac, bc, [&](const int32_t q) {
+    int oa[3], ob[3];
+    const int4 bx = v.sh_box[q];  // one 16-byte load per visited point
+    if (!in_box4<D>(bx, ac, oa) || !in_box4<D>(bx, bc, ob)) return;
+    R Sa, S0a, Gna[3], Sb, S0b, Gnb[3], ga[3], gb[3];
+    basis_at_t<D, R>(BA, q, oa, a, Sa, S0a, Gna);
+    basis_at_t<D, R>(BA, q, ob, bn, Sb, S0b, Gnb);
+    for (int j = 0; j < D; ++j) {
+      R sa = 0, sb = 0;
+      for (int k = 0; k < D; ++k) {
+        const R fkj = rec[(RC_FINV + k * D + j) * n + q];
+        sa += Gna[k] * fkj;
+        sb += Gnb[k] * fkj;
       }
+      ga[j] = sa;
+      gb[j] = sb;
+    }
+    const R cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
+    const R mu = rec[RC_MUP * n + q], lam = rec[RC_LAM * n + q], kv = rec[RC_KV * n + q];
+    R gab = 0, gtg = 0, gaw = 0, gbw = 0;
+    for (int j = 0; j < D; ++j) {
+      gab += ga[j] * gb[j];
+      const R wj = rec[(RC_W + j) * n + q];
+      gaw += ga[j] * wj;
+      gbw += gb[j] * wj;
+      for (int l = 0; l < D; ++l) gtg += ga[j] * rec[(RC_TAU + j * D + l) * n + q] * gb[l];
+    }
+    const R ms = DYN ? rec[RC_MS * n + q] * Sa * Sb : R(0);
+    for (int i = 0; i < D; ++i)
+      for (int k = 0; k < D; ++k) {
+        const R dik = i == k ? R(1) : R(0);
+        const R sym = mu * (dik * gab + ga[k] * gb[i]);
+        R Aik = -cs * (dik * gtg + sym + lam * ga[i] * gb[k]);
+        Aik += vol * ph * (ga[i] * gb[k] - ga[k] * gb[i]);
+        if (DYN) {
+          Aik -= cs * cvis * (lam * ga[i] * gb[k] + sym);
+          Aik -= dik * ms;
+        }
+        A[i * D + k] += Aik;
+      }
+    const R b2 = rec[RC_B2 * n + q], dkv = rec[RC_DKV * n + q];
+    for (int i = 0; i < D; ++i) b1ab[i] += vol * ga[i] * Sb;
+    for (int k = 0; k < D; ++k) {
+      R t = Sa * b2 * gb[k];
+      if (DYN) {
+        R gbgv = 0;
+        for (int j = 0; j < D; ++j) gbgv += gb[j] * rec[(RC_GV + j * D + k) * n + q];
+        t -= vol * Sa * gbgv;
+      }
+      t += kv * (gb[k] * gaw - ga[k] * gbw);
+      t += dkv * gb[k] * gaw;  // dk/dJ (Kozeny-Carman)
+      b2ab[k] += t;
+      kgp[k] += kv * gab * rec[(RC_GP + k) * n + q];  // grad p part, the same for both blocks
+    }
+    if (!diag) {
+      for (int i = 0; i < D; ++i) b1ba[i] += vol * gb[i] * Sa;
+      for (int k = 0; k < D; ++k) {
+        R t = Sb * b2 * ga[k];
+        if (DYN) {
+          R gagv = 0;
+          for (int j = 0; j < D; ++j) gagv += ga[j] * rec[(RC_GV + j * D + k) * n + q];
+          t -= vol * Sb * gagv;
+        }
+        t += kv * (ga[k] * gbw - gb[k] * gaw);
+        t += dkv * ga[k] * gbw;
+        b2ba[k] += t;
+      }
+    }
+    C += kv * gab + rec[RC_CST * n + q] * (Sa - S0a) * (Sb - S0b);
+  });
   R B[NB * NB];
   for (int i = 0; i < D; ++i) {
     for (int k = 0; k < D; ++k) B[i * NB + k] = A[i * D + k];
@@ -1078,30 +1097,25 @@ __global__ void k_consistent_mass(GridP g, DevView v, int64_t nnzb, const int32_
   int ac[3], bc[3];
   node_coords(g, a, ac);
   node_coords(g, b, bc);
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) {
-    int l1, h1, l2, h2;
-    cand_range<GIMP>(ac[k], g.nc[k], l1, h1);
-    cand_range<GIMP>(bc[k], g.nc[k], l2, h2);
-    lo[k] = max(l1, l2);
-    hi[k] = min(h1, h2);
-  }
+  int lo[3], hi[3];
+  fb_window<D>(v.fb_cmax, ac, bc, lo, hi);
   double acc = 0.0;
-  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
-    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
-      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
-        const int64_t cid = cell_index(g, c0, c1, c2);
-        for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
-          int oa[3], ob[3];
-          if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
-          double Sa = 1.0, Sb = 1.0;
-          for (int k = 0; k < D; ++k) {
-            Sa *= v.sh_S[(k * MAXS + oa[k]) * n + q];
-            Sb *= v.sh_S[(k * MAXS + ob[k]) * n + q];
-          }
-          acc += Sa * Sb * v.m[q];
+  for (int f2 = lo[2]; f2 <= hi[2]; ++f2)
+    for (int f1 = lo[1]; f1 <= hi[1]; ++f1) {
+      int32_t ib, ie;
+      fb_run(g, v.fb_start, lo[0], hi[0], f1, f2, ib, ie);
+      for (int32_t i = ib; i < ie; ++i) {
+        const int32_t q = v.fb_perm[i];
+        int oa[3], ob[3];
+        if (!in_box<D>(v, q, ac, oa) || !in_box<D>(v, q, bc, ob)) continue;
+        double Sa = 1.0, Sb = 1.0;
+        for (int k = 0; k < D; ++k) {
+          Sa *= v.sh_S[(k * MAXS + oa[k]) * n + q];
+          Sb *= v.sh_S[(k * MAXS + ob[k]) * n + q];
         }
+        acc += Sa * Sb * v.m[q];
       }
+    }
   mc[e] = acc;
 }
 
@@ -1515,16 +1529,19 @@ int ensure_jacobian_staging32(Ctx &c) {
 
 // One assembly with a given kernel configuration: staged (k_point_nodes then
 // k_jacobian on the per-(point, node) vectors) or direct (k_jacobian_direct),
-// tpb threads per block.  Values in precision T computed in precision T from
-// the FP64 records or their FP32 copies.
+// tpb threads per block.  Values in precision T computed
+// in precision T from the FP64 records or their FP32 copies.
 template <typename T>
-void launch_jacobian(Ctx &c, T *val, int apply_bc, bool staged, int tpb) {
+void launch_jacobian(Ctx &c, T *val, int apply_bc, int form, int tpb) {
   const DevView v = c.view();
+  const bool staged = form == Ctx::JAC_STAGED;
   // the Jacobian kernels take symmetric pairs: half the offsets plus the centre
   const int64_t nthr = pair_threads(c.d, c.g.nnodes);
   const int nbk_pair = (int)((nthr + tpb - 1) / tpb);
   const bool gimp = c.shape == MPM_SHAPE_GIMP;
   using R = T;
+  // candidates from the first-node bins in FP32, from the cells in FP64
+  constexpr bool FB = sizeof(T) == sizeof(float);
   BasisArrays<R> BA;
   BA.n = c.n;
   BA.cnt = c.sh_cnt;
@@ -1558,14 +1575,14 @@ void launch_jacobian(Ctx &c, T *val, int apply_bc, bool staged, int tpb) {
 #define JAC(D, G, Y)                                                                                         \
   do {                                                                                                       \
     if (staged && c.s.hencky)                                                                                \
-      k_jacobian<D, G, Y, true, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr,    \
-                                                                  c.col, val, apply_bc);                     \
+      k_jacobian<D, G, Y, true, FB, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask,           \
+                                                                      c.row_ptr, c.col, val, apply_bc);      \
     else if (staged)                                                                                         \
-      k_jacobian<D, G, Y, false, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask, c.row_ptr,   \
-                                                                   c.col, val, apply_bc);                    \
+      k_jacobian<D, G, Y, false, FB, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, pn, c.row_mask,          \
+                                                                       c.row_ptr, c.col, val, apply_bc);     \
     else                                                                                                     \
-      k_jacobian_direct<D, G, Y, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask,         \
-                                                                   c.row_ptr, c.col, val, apply_bc);         \
+      k_jacobian_direct<D, G, Y, FB, T, R><<<nbk_pair, tpb, 0, c.st>>>(c.g, c.s, v, BA, rec, c.row_mask,     \
+                                                                       c.row_ptr, c.col, val, apply_bc);     \
   } while (0)
   if (c.d == 2) {
     if (gimp) { if (c.dyn) JAC(2, true, true); else JAC(2, true, false); }
@@ -1581,12 +1598,12 @@ void launch_jacobian(Ctx &c, T *val, int apply_bc, bool staged, int tpb) {
 // Autotuner of the assembly: every candidate configuration is run twice on
 // the context's own data (the first run warms caches and page tables), the
 // second timed with CUDA events; the fastest is kept for the rest of the
-// context's life.  Candidates: 64, 128, 256 threads per block, and for FP32
-// also the staged variant (FP64 is always staged: recomputing the node
-// vectors per term costs FP64 issue slots, the bound of that kernel).  The
-// chosen configuration only moves work between threads (block size) or
-// stages exact copies (FP32 staging rounds the same products in a different
-// order), so the values agree to the precision's rounding.
+// context's life.  Candidates: 64, 128, 256 threads per block of each form;
+// FP64 is always staged (recomputing the node vectors per term costs FP64
+// issue slots, the bound of that kernel), FP32 tries the direct and the
+// staged form.  The chosen configuration only moves work between threads or
+// stages exact copies (a different summation order), so the values agree to
+// the precision's rounding.
 template <typename T>
 void autotune_jacobian(Ctx &c, T *val, int apply_bc) {
   constexpr int pi = sizeof(T) == sizeof(double) ? 0 : 1;
@@ -1599,22 +1616,21 @@ void autotune_jacobian(Ctx &c, T *val, int apply_bc) {
     return;
   }
   float best = 1e30f;
-  for (int k = 0; k < 6; ++k) c.stats.jac_tune_ms[pi][k] = 0.0f;
-  for (int st = 0; st < 2; ++st) {
-    const bool staged = st == 1;
-    if (pi == 0 && !staged) continue;
-    if (pi == 1 && staged && ensure_jacobian_staging32(c) != MPM_OK) continue;
+  for (int k = 0; k < 3 * Ctx::JAC_FORMS; ++k) c.stats.jac_tune_ms[pi][k] = 0.0f;
+  for (int form = 0; form < Ctx::JAC_FORMS; ++form) {
+    if (pi == 0 && form != Ctx::JAC_STAGED) continue;
+    if (pi == 1 && form != Ctx::JAC_DIRECT && ensure_jacobian_staging32(c) != MPM_OK) continue;
     for (int k = 0; k < 3; ++k) {
-      launch_jacobian<T>(c, val, apply_bc, staged, tpbs[k]);
+      launch_jacobian<T>(c, val, apply_bc, form, tpbs[k]);
       cudaEventRecord(e0, c.st);
-      launch_jacobian<T>(c, val, apply_bc, staged, tpbs[k]);
+      launch_jacobian<T>(c, val, apply_bc, form, tpbs[k]);
       cudaEventRecord(e1, c.st);
       float ms = 0.0f;
       if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
-      c.stats.jac_tune_ms[pi][st * 3 + k] = ms;
+      c.stats.jac_tune_ms[pi][form * 3 + k] = ms;
       if (ms < best) {
         best = ms;
-        cfg.staged = staged;
+        cfg.form = form;
         cfg.tpb = tpbs[k];
       }
     }
@@ -1622,7 +1638,7 @@ void autotune_jacobian(Ctx &c, T *val, int apply_bc) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cfg.tuned = 1;
-  if (pi == 1 && !cfg.staged && c.pn32) {  // not chosen: give the memory back
+  if (pi == 1 && cfg.form == Ctx::JAC_DIRECT && c.pn32) {  // not chosen: give the memory back
     cudaFree(c.pn32);
     c.pn32 = nullptr;
     c.pn32_cap = 0;
@@ -1634,12 +1650,23 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
   constexpr int pi = sizeof(T) == sizeof(double) ? 0 : 1;
   Ctx::JacCfg &cfg = c.jac_cfg[pi];
   if (c.opt.autotune && !cfg.tuned && !c.capturing) autotune_jacobian<T>(c, val, apply_bc);
-  if (pi == 1 && cfg.staged && ensure_jacobian_staging32(c) != MPM_OK) cfg.staged = 0;
-  c.stats.jac_config[pi] = cfg.tpb + (cfg.staged ? 1000 : 0);
+  if (pi == 1 && cfg.form != Ctx::JAC_DIRECT && ensure_jacobian_staging32(c) != MPM_OK) cfg.form = Ctx::JAC_DIRECT;
+  c.stats.jac_config[pi] = cfg.tpb + 1000 * cfg.form;
   c.stats.jac_tuned[pi] = cfg.tuned;
   prof_begin(c, MPM_PROF_JACOBIAN);
-  launch_jacobian<T>(c, val, apply_bc, cfg.staged, cfg.tpb);
+  launch_jacobian<T>(c, val, apply_bc, cfg.form, cfg.tpb);
   prof_end(c, MPM_PROF_JACOBIAN);
+}
+
+// One FP32 assembly by a given form and block size (inspection of every
+// candidate of the autotuner).
+int run_jacobian32_form(Ctx &c, float *val, int apply_bc, int form, int tpb) {
+  if (form != Ctx::JAC_DIRECT) {
+    const int rc = ensure_jacobian_staging32(c);
+    if (rc) return rc;
+  }
+  launch_jacobian<float>(c, val, apply_bc, form, tpb);
+  return check_cuda(c, cudaGetLastError(), "jacobian32");
 }
 
 template void run_jacobian<double>(Ctx &, double *, int);

@@ -198,6 +198,11 @@ struct DevView {
   int32_t *sh_first;        // 3 * n
   int32_t *sh_cnt;          // n, counts packed 4 bits per axis
   int4 *sh_box;             // n: (first node per axis, sh_cnt) of each point in one 16-byte word
+  // first-node bins: the points by the first node of their support box
+  // (fb_perm, ascending point index within a bin; bin f is fb_perm[fb_start[f]
+  // .. fb_start[f + 1])), and the largest box extent per axis of the step
+  const int32_t *fb_start, *fb_perm;
+  const int *fb_cmax;
   const int32_t *pn_base;   // n + 1: first staged Jacobian record of each point
   double *sh_S, *sh_dS, *sh_S0;  // 12 * n each
   double *m;                // n mixture mass of the step
@@ -274,6 +279,8 @@ struct Ctx {
   int32_t *perm = nullptr;
   int32_t *sh_first = nullptr, *sh_cnt = nullptr;
   int4 *sh_box = nullptr;
+  int32_t *fb_key = nullptr, *fb_start = nullptr, *fb_cursor = nullptr, *fb_perm = nullptr;
+  int *fb_cmax = nullptr;
   double *sh_S = nullptr, *sh_dS = nullptr, *sh_S0 = nullptr;
   double *m = nullptr, *rec = nullptr;
   double *M = nullptr, *Pn = nullptr, *vn = nullptr, *an = nullptr, *pdn = nullptr, *pddn = nullptr;
@@ -304,14 +311,16 @@ struct Ctx {
   int64_t pn_total = 0;                  // records of the current step
   int64_t pn_cap = 0, pn32_cap = 0;      // records pn / pn32 can hold
   unsigned long long *h_terms = nullptr; // pinned copy
-  // Jacobian kernel configuration per precision ([0] FP64, [1] FP32): staged
-  // (per-(point, node) vectors formed first) or direct (recomputed per term),
-  // and threads per block.  Fixed defaults, or chosen by timing every
-  // candidate at the context's first assembly when mpm_options.autotune is set.
+  // Jacobian kernel configuration per precision ([0] FP64, [1] FP32): the
+  // form (JAC_DIRECT: node vectors recomputed per term; JAC_STAGED:
+  // per-(point, node) vectors formed first) and threads per block.  Fixed
+  // defaults, or chosen by timing every candidate at the context's first
+  // assembly when mpm_options.autotune is set.
+  enum { JAC_DIRECT = 0, JAC_STAGED = 1, JAC_FORMS = 2 };
   struct JacCfg {
-    int staged, tpb, tuned;
+    int form, tpb, tuned;
   };
-  JacCfg jac_cfg[2] = {{1, 128, 0}, {0, 128, 0}};
+  JacCfg jac_cfg[2] = {{JAC_STAGED, 128, 0}, {JAC_DIRECT, 128, 0}};
 
   // sparsity + matrix
   int32_t *row_nnz = nullptr, *row_ptr = nullptr, *row_of = nullptr, *col = nullptr;
@@ -348,6 +357,7 @@ struct Ctx {
 // particles: binning, shape, Stage 1, Stage 3/4
 int run_binning(Ctx &c);                          // keys, counting sort, (cell, id) order, permute
 void run_shape(Ctx &c);
+int run_first_bins(Ctx &c);        // the first-node bins (after run_shape)
 void run_mass(Ctx &c);
 void run_p2g(Ctx &c);
 void run_g2p(Ctx &c);
@@ -364,6 +374,7 @@ void run_point_eval(Ctx &c, const double *X);
 void run_residual(Ctx &c, const double *X, double *R, int apply_bc);
 template <typename T>
 void run_jacobian(Ctx &c, T *val, int apply_bc);  // block values in precision T
+int run_jacobian32_form(Ctx &c, float *val, int apply_bc, int form, int tpb);  // one given FP32 configuration
 // linear algebra
 template <typename T>
 int linsys_alloc(Ctx &c, LinSys<T> &S, bool krylov);  // vectors; matrix on demand
@@ -576,6 +587,29 @@ __device__ inline void cand_range(int a, int nc, int &lo, int &hi) {
   hi = GIMP ? a + 1 : a;
   if (lo < 0) lo = 0;
   if (hi > nc - 1) hi = nc - 1;
+}
+
+// First-node bins holding every point whose support box contains both nodes
+// ac and bc (ac == bc for one node): along each axis the box origin f has
+// f <= min(a, b) and f + extent - 1 >= max(a, b) with extent <= cmax, the
+// step's largest extent (3 for GIMP domains narrower than a cell, against the
+// 4 cells around a node that can hold such a point).
+template <int D>
+__device__ inline void fb_window(const int *__restrict__ cmax, const int ac[3], const int bc[3], int lo[3],
+                                 int hi[3]) {
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = k < D ? max(max(ac[k], bc[k]) - cmax[k] + 1, 0) : 0;
+    hi[k] = k < D ? min(ac[k], bc[k]) : 0;
+  }
+}
+
+// The points of bins lo0 .. hi0 along x at (f1, f2) are one contiguous run of
+// fb_perm (bins are numbered like nodes, x fastest): [b, e).
+__device__ inline void fb_run(const GridP &g, const int32_t *__restrict__ fb_start, int lo0, int hi0, int f1,
+                              int f2, int32_t &b, int32_t &e) {
+  const int64_t r = (int64_t)g.nn[0] * (f1 + (int64_t)g.nn[1] * f2);
+  b = fb_start[r + lo0];
+  e = fb_start[r + hi0 + 1];
 }
 
 }  // namespace upmpm

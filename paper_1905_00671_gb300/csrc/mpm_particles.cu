@@ -79,6 +79,57 @@ __global__ void k_bin_sort_cells(int64_t ncells, const int32_t *__restrict__ sta
   }
 }
 
+// First-node bins (a second index of the cell-sorted points, for the
+// node-centric gathers): key = node index of the point's box origin, and the
+// largest box extent per axis (a warp maximum, then one atomic per warp).
+template <int D>
+__global__ void k_fb_count(GridP g, int64_t n, const int32_t *__restrict__ first,
+                           const int32_t *__restrict__ cnt_packed, int32_t *__restrict__ key,
+                           int32_t *__restrict__ count, int *__restrict__ cmax, int *err) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int ext[3] = {0, 0, 0};
+  if (p < n) {
+    const int packed = cnt_packed[p];
+    int f[3] = {0, 0, 0};
+    bool in = true;
+    for (int k = 0; k < D; ++k) {
+      f[k] = first[k * n + p];
+      ext[k] = unpack_cnt(packed, k);
+      if (f[k] < 0 || ext[k] < 1 || f[k] + ext[k] > g.nn[k]) in = false;
+    }
+    if (in) {
+      const int32_t id = (int32_t)node_index(g, f);
+      key[p] = id;
+      atomicAdd(&count[id], 1);
+    } else {  // not reached: k_shape clips the box to the grid
+      atomicOr(err, DE_SUPPORT);
+      key[p] = -1;
+      ext[0] = ext[1] = ext[2] = 0;
+    }
+  }
+  for (int k = 0; k < D; ++k) {
+    const int m = __reduce_max_sync(0xffffffffu, ext[k]);
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&cmax[k], m);
+  }
+}
+
+// Within each bin, ascending point index (insertion sort of a short run), so
+// that the gathers sum in an order independent of the scatter's atomics.
+__global__ void k_fb_sort(int64_t nbins, const int32_t *__restrict__ start, int32_t *__restrict__ perm) {
+  const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nbins) return;
+  const int32_t b = start[f], e = start[f + 1];
+  for (int32_t i = b + 1; i < e; ++i) {
+    const int32_t v = perm[i];
+    int32_t j = i - 1;
+    while (j >= b && perm[j] > v) {
+      perm[j + 1] = perm[j];
+      --j;
+    }
+    perm[j + 1] = v;
+  }
+}
+
 __global__ void k_permute(int64_t n, int nf, const int32_t *__restrict__ perm,
                           const double *__restrict__ src, double *__restrict__ dst,
                           const int64_t *__restrict__ pid, int64_t *__restrict__ pid_dst,
@@ -203,7 +254,7 @@ __global__ void k_mass(int64_t n, StepP s, const double *__restrict__ pf, double
 
 // ---------------------------------------------------------------- Stage 1
 // Node-centric gather: each thread owns one node and sums S m f over the
-// points of the candidate cells, in cell-sorted order.
+// points of the first-node bins that can hold it, in (bin, index) order.
 template <int D, bool GIMP, bool DYN>
 __global__ void k_p2g(GridP g, DevView v) {
   const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -211,41 +262,41 @@ __global__ void k_p2g(GridP g, DevView v) {
   const int64_t n = v.n;
   int ac[3];
   node_coords(g, a, ac);
-  int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) cand_range<GIMP>(ac[k], g.nc[k], lo[k], hi[k]);
+  int lo[3], hi[3];
+  fb_window<D>(v.fb_cmax, ac, ac, lo, hi);
   double Msum = 0.0, Vsum = 0.0, mp = 0.0, mv[3] = {0, 0, 0}, ma[3] = {0, 0, 0}, mpd = 0.0, mpdd = 0.0;
-  for (int c2 = lo[2]; c2 <= hi[2]; ++c2)
-    for (int c1 = lo[1]; c1 <= hi[1]; ++c1)
-      for (int c0 = lo[0]; c0 <= hi[0]; ++c0) {
-        const int64_t cid = cell_index(g, c0, c1, c2);
-        const int32_t qb = v.cell_start[cid], qe = v.cell_start[cid + 1];
-        for (int32_t q = qb; q < qe; ++q) {
-          const int packed = v.sh_cnt[q];
-          double S = 1.0;
-          bool in = true;
+  for (int f2 = lo[2]; f2 <= hi[2]; ++f2)
+    for (int f1 = lo[1]; f1 <= hi[1]; ++f1) {
+      int32_t ib, ie;
+      fb_run(g, v.fb_start, lo[0], hi[0], f1, f2, ib, ie);
+      for (int32_t i = ib; i < ie; ++i) {
+        const int32_t q = v.fb_perm[i];
+        const int packed = v.sh_cnt[q];
+        double S = 1.0;
+        bool in = true;
+        for (int k = 0; k < D; ++k) {
+          const int off = ac[k] - v.sh_first[k * n + q];
+          if (off < 0 || off >= unpack_cnt(packed, k)) {
+            in = false;
+            break;
+          }
+          S *= v.sh_S[(k * MAXS + off) * n + q];
+        }
+        if (!in) continue;
+        const double w = S * v.m[q];
+        Msum += w;
+        Vsum += S * v.pf[PF_V * n + q];
+        mp += w * v.pf[PF_P * n + q];
+        if (DYN) {
           for (int k = 0; k < D; ++k) {
-            const int off = ac[k] - v.sh_first[k * n + q];
-            if (off < 0 || off >= unpack_cnt(packed, k)) {
-              in = false;
-              break;
-            }
-            S *= v.sh_S[(k * MAXS + off) * n + q];
+            mv[k] += w * v.pf[(PF_VEL + k) * n + q];
+            ma[k] += w * v.pf[(PF_ACC + k) * n + q];
           }
-          if (!in) continue;
-          const double w = S * v.m[q];
-          Msum += w;
-          Vsum += S * v.pf[PF_V * n + q];
-          mp += w * v.pf[PF_P * n + q];
-          if (DYN) {
-            for (int k = 0; k < D; ++k) {
-              mv[k] += w * v.pf[(PF_VEL + k) * n + q];
-              ma[k] += w * v.pf[(PF_ACC + k) * n + q];
-            }
-            mpd += w * v.pf[PF_PD * n + q];
-            mpdd += w * v.pf[PF_PDD * n + q];
-          }
+          mpd += w * v.pf[PF_PD * n + q];
+          mpdd += w * v.pf[PF_PDD * n + q];
         }
       }
+    }
   const int64_t nn = g.nnodes;
   v.M[a] = Msum;
   double hd = g.h;
@@ -425,6 +476,31 @@ int run_binning(Ctx &c) {
   std::swap(c.surf, c.surf_alt);
   std::swap(c.cell, c.cell_tmp);
   return check_cuda(c, cudaGetLastError(), "binning");
+}
+
+// First-node bins of the step (after run_shape; the box origins and extents
+// are fixed over the step): counts and the largest extents, an exclusive scan,
+// the scatter, and the per-bin sort.
+int run_first_bins(Ctx &c) {
+  const int64_t n = c.n, nn = c.g.nnodes;
+  cudaMemsetAsync(c.fb_cursor, 0, sizeof(int32_t) * (nn + 1), c.st);
+  cudaMemsetAsync(c.fb_cmax, 0, sizeof(int) * 4, c.st);
+  if (c.d == 2)
+    k_fb_count<2><<<nblk(n), TPB, 0, c.st>>>(c.g, n, c.sh_first, c.sh_cnt, c.fb_key, c.fb_cursor, c.fb_cmax, c.err);
+  else
+    k_fb_count<3><<<nblk(n), TPB, 0, c.st>>>(c.g, n, c.sh_first, c.sh_cnt, c.fb_key, c.fb_cursor, c.fb_cmax, c.err);
+  UPMPM_LAUNCH(c);
+  if (scan_exclusive(c, c.fb_cursor, c.fb_start, nn + 1) != n) {
+    int rc = read_dev_err(c);
+    if (rc) return rc;
+    c.last_error = "first-node bins lost points";
+    return MPM_ERR_CUDA;
+  }
+  cudaMemsetAsync(c.fb_cursor, 0, sizeof(int32_t) * nn, c.st);
+  k_bin_scatter<<<nblk(n), TPB, 0, c.st>>>(n, c.fb_key, c.fb_start, c.fb_cursor, c.fb_perm);
+  k_fb_sort<<<nblk(nn), TPB, 0, c.st>>>(nn, c.fb_start, c.fb_perm);
+  c.launches += 2;
+  return check_cuda(c, cudaGetLastError(), "first-node bins");
 }
 
 void run_shape(Ctx &c) {

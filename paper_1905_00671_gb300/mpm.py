@@ -33,7 +33,8 @@ PROF = {"spmv": 0, "jacobian": 1, "residual": 2, "point": 3, "orth": 4, "p2g": 5
 
 EXPORTED = ["mpm_default_options", "mpm_create", "mpm_step", "mpm_read", "mpm_get_stats",
             "mpm_last_error", "mpm_destroy", "mpm_debug_bin", "mpm_debug_prepare",
-            "mpm_debug_pattern", "mpm_debug_nodal", "mpm_debug_eval", "mpm_debug_precond"]
+            "mpm_debug_pattern", "mpm_debug_nodal", "mpm_debug_eval", "mpm_debug_precond",
+            "mpm_debug_jacobian32"]
 
 
 class MPMError(RuntimeError):
@@ -132,6 +133,7 @@ def load(build_if_missing: bool = False):
     lib.mpm_debug_nodal.argtypes = [P, P, P, P]
     lib.mpm_debug_eval.argtypes = [P, P, P, P, C.c_int32]
     lib.mpm_debug_precond.argtypes = [P, P, P, P]
+    lib.mpm_debug_jacobian32.argtypes = [P, P, C.c_int32, C.c_int32, P, C.c_int32]
     lib.mpm_restore.argtypes = [P, C.POINTER(mpm_particles_out), C.c_double, C.c_int64]
     lib.mpm_batch_pack.argtypes = [C.c_int32, C.POINTER(mpm_grid), P, P]
     lib.mpm_create_batch.argtypes = [C.c_int32, C.POINTER(mpm_grid), C.POINTER(mpm_particles),
@@ -368,6 +370,15 @@ class Simulation:
         self._check(self.lib.mpm_debug_eval(self.ctx, _p(X), _p(R), _p(Jv), int(apply_bc)),
                     "mpm_debug_eval")
         return R, Jv
+
+    def debug_jacobian32(self, X, nnzb, form, tpb=128, apply_bc=False):
+        """The mixed mode's FP32 Jacobian at X by one kernel configuration."""
+        nb = self.w.dim + 1
+        X = _f64(X).reshape(-1)
+        Jv = np.zeros(nnzb * nb * nb, dtype=np.float32)
+        self._check(self.lib.mpm_debug_jacobian32(self.ctx, _p(X), int(form), int(tpb), _p(Jv), int(apply_bc)),
+                    "mpm_debug_jacobian32")
+        return Jv
 
     def debug_precond(self, X, v):
         X = _f64(X).reshape(-1)
