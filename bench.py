@@ -231,13 +231,14 @@ def ncu_traffic(kernel, workload):
 # node (G per (point, node)); the blocks (a, b) and (b, a) are assembled as one
 # symmetric pair (A and C once, B1 and B2 for both), so a (point, a, b) term
 # with a != b costs F_pair per unordered pair and a diagonal term F_diag:
-#   F_diag = 2 (2d^2 + 6d + 1) + d + 1   (+ 2 (d + 1), Newmark)
+#   F_diag = 2 (2d^2 + 6d + 1) + 1       (+ 2 (d + 1), Newmark)
 #   F_pair = F_diag + 6d                 (+ 2 (2d + 1) over F_pair's QS value, Newmark)
 # (the pair adds the d + 2d FMAs of the second block's B1 and B2; the grad p
-# part of B2, (p7 g_a.g_b) grad p, is accumulated once for both blocks).
+# part of B2, (p7 g_a.g_b) grad p, is accumulated once for both blocks, and the
+# d = h_a.g_b part of A's diagonal into one sum subtracted once per pair).
 # {(dim, dynamic): (F_pair, F_diag, G)}.
-JAC_FLOPS = {(2, False): (57, 45, 43), (2, True): (67, 51, 52), (3, False): (96, 78, 77),
-             (3, True): (110, 86, 96)}
+JAC_FLOPS = {(2, False): (55, 43, 43), (2, True): (65, 49, 52), (3, False): (93, 75, 77),
+             (3, True): (107, 83, 96)}
 # Hencky elasticity adds, per pair and per diagonal term, the d^3 FMAs of
 # sum_l U_a,ikl g_b,l and, per (point, node), the staged U of its spectral
 # tangent: gh_A = g.n_A (d^2 FMAs), w_Akl = kappa_A gh_A n_Ak n_Al + sum_{B != A}

@@ -880,7 +880,8 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
   // pair accumulators: A (shared, for (a, b); (b, a) gets its transpose), C
   // (shared), B1 and B2 of each of the two blocks
   // kgp: the grad p part of B2, (p7 g_a.g_b) grad p, the same for both blocks
-  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], kgp[D], C = 0;
+  // Dg: the sum of the terms' d (A_ii - d per term, subtracted once at the end)
+  R A[D * D], b1ab[D], b1ba[D], b2ab[D], b2ba[D], kgp[D], C = 0, Dg = 0;
   for (int i = 0; i < D * D; ++i) A[i] = 0;
   for (int i = 0; i < D; ++i) b1ab[i] = b1ba[i] = b2ab[i] = b2ba[i] = kgp[i] = 0;
   for_pair_candidates<D, GIMP, FB>(g, v, ac, bc, [&](const int32_t q) {
@@ -904,19 +905,19 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
     // A_ik = g_a,i (p2 g_b)_k - g_b,i (p3 g_a)_k - delta_ik d,
     // d = h_a.g_b (+ p4 S_a S_b): stress, geometric, pressure, Kelvin
     // and inertia terms with the point's coefficients staged per node
-    R dg = 0, kgab = 0;
+    R kgab = 0;
     for (int j = 0; j < D; ++j) {
-      dg = fma(pa[L::H + j], gb[j], dg);
+      Dg = fma(pa[L::H + j], gb[j], Dg);
       kgab = fma(pa[L::P7G + j], gb[j], kgab);  // p7 g_a.g_b
     }
-    if (DYN) dg = fma(pa[L::MS], pb[L::S], dg);
+    if (DYN) Dg = fma(pa[L::MS], pb[L::S], Dg);
     for (int i = 0; i < D; ++i)
       for (int k = 0; k < D; ++k) {
         R acc = fma(ga[i], pb[L::P2G + k], A[i * D + k]);
         acc = fma(-gb[i], pa[L::P3G + k], acc);
         if (HK)  // material part of the Hencky tangent, staged per node
           for (int l = 0; l < D; ++l) acc = fma(pa[L::U + (i * D + k) * D + l], gb[l], acc);
-        A[i * D + k] = i == k ? acc - dg : acc;
+        A[i * D + k] = acc;
       }
     // B1 column of (a, b): (p5 S_b) g_a; of (b, a): (p5 S_a) g_b
     const R p5Sb = pb[L::P5S], p5Sa = pa[L::P5S];
@@ -942,6 +943,7 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
     // C + C_stab: p7 g_a.g_b + (p8 St_a) St_b (symmetric)
     C = fma(pa[L::P8ST], pb[L::ST], C + kgab);
   });
+  for (int i = 0; i < D; ++i) A[i * D + i] -= Dg;
   R B[NB * NB];
   for (int i = 0; i < D; ++i) {
     for (int k = 0; k < D; ++k) B[i * NB + k] = A[i * D + k];
