@@ -732,7 +732,7 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
     F(&c.sh_dSf, 3 * MAXS * n);
     F(&c.sh_S0f, 3 * MAXS * n);
     F(&c.sh_nrmf, 5 * n);
-    F(&c.recf, RC_COUNT * n);
+    F(&c.recf, RC_F32 * n);
   }
   if (!rc) rc = linsys_alloc<double>(c, c.L64, !c.have32);
   if (!rc && c.have32) rc = linsys_alloc<float>(c, c.L32, true);

@@ -122,17 +122,6 @@ __device__ inline double log1p_ratio(double r) {
 // slot of the pair (A, B), A < B, among (0,1), (0,2), (1,2)
 __device__ inline int pair_index(int A, int B) { return A + B - 1; }
 
-// g = Gn . dF^{-1}
-template <int D>
-__device__ inline void spatial_grad(const DevView &v, int64_t q, const double Gn[3], double g[3]) {
-  const int64_t n = v.n;
-  for (int j = 0; j < D; ++j) {
-    double s = 0.0;
-    for (int k = 0; k < D; ++k) s += Gn[k] * v.rec[(RC_FINV + k * D + j) * n + q];
-    g[j] = s;
-  }
-}
-
 // ---------------------------------------------------------------- pattern
 template <int D, bool GIMP>
 __global__ void k_pattern_count(GridP g, DevView v, uint64_t *__restrict__ mask,
@@ -523,8 +512,28 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
   rec[RC_DIVV * n + p] = vol * divv;
   rec[RC_B2 * n + p] = DYN ? vol * (gm / (b * dt) + divv) : vol * (1.0 + log(dJ)) / dt;
   rec[RC_MS * n + p] = DYN ? m / (b * dt * dt) : 0.0;
+  // The residual's per-point factors.  With g = Gn dF^-1 (Gn the gradient of
+  // the basis in the configuration of t_n), the momentum term of a node,
+  // -cs g.(tau' + s_vis) + vol p^h g, is Gn.RU, and the Darcy term
+  // kappa vol g.w is Gn.KW: the residual's node sums then spend d^2 + d FMAs
+  // per (point, node) on them instead of forming g first.
+  for (int i = 0; i < D; ++i)
+    for (int k = 0; k < D; ++k) {
+      double acc = vol * ph * fi[k * D + i];
+      for (int j = 0; j < D; ++j) {
+        double sij = rec[(RC_TAU + i * D + j) * n + p];
+        if (DYN) sij += rec[(RC_SVIS + i * D + j) * n + p];
+        acc -= (Vn / Jn) * sij * fi[k * D + j];
+      }
+      rec[(RC_RU + i * D + k) * n + p] = acc;
+    }
+  for (int k = 0; k < D; ++k) {
+    double acc = 0.0;
+    for (int j = 0; j < D; ++j) acc += fi[k * D + j] * rec[(RC_W + j) * n + p];
+    rec[(RC_KW + k) * n + p] = kv * acc;
+  }
   if (v.recf)
-    for (int f = 0; f < RC_COUNT; ++f) v.recf[f * n + p] = (float)rec[f * n + p];
+    for (int f = 0; f < RC_F32; ++f) v.recf[f * n + p] = (float)rec[f * n + p];
 }
 
 // ---------------------------------------------------------------- residual
@@ -548,24 +557,16 @@ __global__ void k_residual(GridP g, DevView v, double *__restrict__ R, int apply
         for (int32_t q = v.cell_start[cid]; q < v.cell_start[cid + 1]; ++q) {
           int off[3];
           if (!in_box4<D>(v.sh_box[q], ac, off)) continue;
-          double Sa, S0a, Gn[3], ga[3];
+          double Sa, S0a, Gn[3];
           basis_at<D>(v, q, off, a, Sa, S0a, Gn);
-          spatial_grad<D>(v, q, Gn, ga);
-          const double cs = rec[RC_CS * n + q], vol = rec[RC_VOL * n + q], ph = rec[RC_PH * n + q];
-          for (int i = 0; i < D; ++i) {
-            double acc = 0.0;
-            for (int j = 0; j < D; ++j) {
-              double sij = rec[(RC_TAU + i * D + j) * n + q];
-              if (DYN) sij += rec[(RC_SVIS + i * D + j) * n + q];
-              acc -= cs * ga[j] * sij;
-            }
-            acc += vol * ga[i] * ph;
-            acc += Sa * rec[(RC_FRC + i) * n + q];
+          for (int i = 0; i < D; ++i) {  // Gn.RU + S_a m (g - a)
+            double acc = Sa * rec[(RC_FRC + i) * n + q];
+            for (int k = 0; k < D; ++k) acc = fma(Gn[k], rec[(RC_RU + i * D + k) * n + q], acc);
             r[i] += acc;
           }
-          double gw = 0.0;
-          for (int j = 0; j < D; ++j) gw += ga[j] * rec[(RC_W + j) * n + q];
-          r[D] += Sa * rec[RC_DIVV * n + q] + rec[RC_KV * n + q] * gw + (Sa - S0a) * rec[RC_RST * n + q];
+          double rp = fma(Sa, rec[RC_DIVV * n + q], (Sa - S0a) * rec[RC_RST * n + q]);
+          for (int k = 0; k < D; ++k) rp = fma(Gn[k], rec[(RC_KW + k) * n + q], rp);  // Gn.KW
+          r[D] += rp;
           const int32_t e = v.surf[q];
           if (e >= 0) {  // Neumann data at the surface point x + lp.n (hat basis)
             const InstDev &I = v.inst[(int)v.pf[PF_INST * n + q]];

@@ -163,7 +163,10 @@ enum RField {
   RC_HQ = 57,      // 9  Hencky: principal directions of b (columns, d x d)
   RC_HK = 66,      // 3  Hencky: kappa_A = 2G - 2 tau_A (diagonal part of the tangent)
   RC_HT = 69,      // 3  Hencky: theta_AB of the pairs (0,1), (0,2), (1,2)
-  RC_COUNT = 72
+  RC_F32 = 72,     // fields above have FP32 copies (mixed mode); those below are FP64 only
+  RC_RU = 72,      // 9  residual factor -cs (tau' + s_vis) dF^-T + vol p^h dF^-T (rows i, cols k)
+  RC_KW = 81,      // 3  residual factor kappa vol dF^-1 w
+  RC_COUNT = 84
 };
 
 // error bits raised by kernels (read back at synchronisation points)
