@@ -370,6 +370,7 @@ struct LevelDev {
   const int32_t *row_ptr, *col;  // level 0 only
   const real *val;              // level 0: block-CSR values
   real *sval;                   // coarse levels: dense 5^d stencil values
+  uint8_t *nslot;               // coarse levels: nonzero blocks of each row (0: a node without coupling)
   real *dinv;
   // level 0 only: Dirichlet / inactive DOFs are left out of the transfers
   const uint8_t *fixed;           // fixed[a * mstride + moff + i] != 0: DOF fixed
@@ -424,6 +425,9 @@ __device__ inline void row_partial(const LevelDev &L, int64_t a, int lane, const
     grid_xyz(L.nn[0], L.nn[1], (int)a, ac);
     constexpr int NS = NS_<D>::v;
     const real *base = L.sval + a * NS * B * B;
+    // rows without coupling (grid nodes outside the material: half of the
+    // slope's coarse grids) are skipped whole
+    if (L.nslot[a] == 0) return;
 #pragma unroll
     for (int k = 0; k < (NS + LN - 1) / LN; ++k) {
       const int s = lane + k * LN;
@@ -1040,6 +1044,24 @@ __global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
   for (int i = 0; i < B * B; ++i) Cl.sval[(I * NS + s) * B * B + i] = acc[i];
 }
 
+// Nonzero blocks of each coarse row (a block is zero when the product never
+// reached it: the coupling is absent), so that the row kernels skip the rows
+// of nodes without coupling.  Thread per row.
+template <int B, int D>
+__global__ void k_mg_rowcount(LevelDev Cl) {
+  constexpr int NS = NS_<D>::v;
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= Cl.nnodes) return;
+  const real *row = Cl.sval + I * NS * B * B;
+  int cnt = 0;
+  for (int s = 0; s < NS; ++s) {
+    bool nz = false;
+    for (int e = 0; e < B * B; ++e) nz |= row[s * B * B + e] != real(0);
+    cnt += nz ? 1 : 0;
+  }
+  Cl.nslot[I] = (uint8_t)cnt;
+}
+
 }  // namespace MG_NS
 
 // ============================================================== hierarchy
@@ -1074,6 +1096,8 @@ void mg_setup_t(Ctx &c, MGHier<real> &H) {
         k_mg_ap<B, D, true><<<nblk(H.L[l - 1].nnodes * NS), TPB, 0, c.st>>>(H.L[l - 1], L, H.apT);
         k_mg_rap2<B, D, true><<<g2, TPB, 0, c.st>>>(H.L[l - 1], L, H.apT);
       }
+      k_mg_rowcount<B, D><<<nbk, TPB, 0, c.st>>>(L);
+      UPMPM_LAUNCH(c);
       UPMPM_LAUNCH(c);
       UPMPM_LAUNCH(c);
       k_mg_dinv<B, D, true><<<nbk, TPB, 0, c.st>>>(L, c.err);
@@ -1211,6 +1235,7 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
     L.col = nullptr;
     L.val = nullptr;
     L.sval = nullptr;
+    L.nslot = nullptr;
     L.fixed = nullptr;
     L.mask = nullptr;
     L.mstride = 1;
@@ -1220,7 +1245,8 @@ int mg_alloc(Ctx &c, MGHier<real> &H, int B) {
         cudaMalloc(&H.x[l], sizeof(real) * vb) || cudaMalloc(&H.x2[l], sizeof(real) * vb) ||
         cudaMalloc(&H.b[l], sizeof(real) * vb) || cudaMalloc(&H.r[l], sizeof(real) * vb))
       return MPM_ERR_NO_MEMORY;
-    if (l > 0 && cudaMalloc(&L.sval, sizeof(real) * L.nnodes * NS * B * B)) return MPM_ERR_NO_MEMORY;
+    if (l > 0 && (cudaMalloc(&L.sval, sizeof(real) * L.nnodes * NS * B * B) || cudaMalloc(&L.nslot, L.nnodes)))
+      return MPM_ERR_NO_MEMORY;
     int32_t *dinst = nullptr;
     if (c.ninst > 1) {
       if (cudaMalloc(&dinst, sizeof(int32_t) * L.nnodes) != cudaSuccess) return MPM_ERR_NO_MEMORY;
@@ -1270,6 +1296,7 @@ void mg_free(MGHier<real> &H) {
     H.L[l].inst = nullptr;
     cudaFree(H.L[l].dinv);
     cudaFree(H.L[l].sval);
+    cudaFree(H.L[l].nslot);
     cudaFree(H.x[l]);
     cudaFree(H.x2[l]);
     cudaFree(H.b[l]);
