@@ -950,6 +950,19 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailArgs A) {
 // entry costs a few lookups and 3^d FMA blocks instead of one per (a, b) pair
 // (measured on the slope's stencil levels: the one-pass product took 20 ms
 // per set-up).
+// A fine row that contributes nothing to the Galerkin product: a stencil row
+// without coupling, or a finest-level row whose DOFs are all fixed (its
+// transfers are masked).  k_mg_ap leaves such a row's T unwritten and
+// k_mg_rap2 skips it (on the slope, the grid nodes outside the material).
+template <int B, bool FST>
+__device__ inline bool row_void(const LevelDev &F, int64_t a) {
+  if (FST) return F.nslot[a] == 0;
+  if (!F.fixed) return false;
+  for (int i = 0; i < B; ++i)
+    if (!F.fixed[a * F.mstride + F.moff + i]) return false;
+  return true;
+}
+
 template <int B, int D, bool FST>
 __global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
   constexpr int NS = NS_<D>::v;
@@ -960,6 +973,7 @@ __global__ void k_mg_ap(LevelDev F, LevelDev Cl, real *__restrict__ T) {
   // slot-major ([s][a]) so that their results are written side by side
   const int64_t a = t % F.nnodes;
   const int s = (int)(t / F.nnodes);
+  if (row_void<B, FST>(F, a)) return;
   int fa[3], Jc[3];
   grid_xyz(F.nn[0], F.nn[1], (int)a, fa);
   Jc[0] = (fa[0] >> 1) + s % 5 - 2;
@@ -1032,6 +1046,7 @@ __global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
           if (d0 < -2 || d0 > 2 || d1 < -2 || d1 > 2 || d2 < -2 || d2 > 2) continue;
           const int64_t a = fa[0] + (int64_t)F.nn[0] * (fa[1] + (int64_t)F.nn[1] * fa[2]);
           if (F.inst && F.inst[a] != Cl.inst[I]) continue;
+          if (row_void<B, FST>(F, a)) continue;  // T_a not written: no contribution
           const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
           const int sl = (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0);
           const real *ta = T + ((int64_t)sl * F.nnodes + a) * B * B;
