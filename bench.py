@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--schur-order", type=int, default=None, help="0 upper, 1 lower triangular")
     ap.add_argument("--mg-sweeps", type=int, default=None, help="V(k,k) smoothing sweeps")
     ap.add_argument("--mg-omega", type=float, default=None, help="block-Jacobi damping")
+    ap.add_argument("--precond-reuse", type=int, default=None,
+                    help="steps served by one Galerkin product of the multigrid coarse levels")
     ap.add_argument("--autotune", type=int, default=1,
                     help="1: the library times its Jacobian kernel configurations at the first "
                          "assembly of each context (a warm-up step) and keeps the fastest")
@@ -92,6 +94,8 @@ def solver_opts(args):
         o["mg_sweeps"] = args.mg_sweeps
     if args.mg_omega is not None:
         o["mg_omega"] = args.mg_omega
+    if args.precond_reuse is not None:
+        o["precond_reuse"] = args.precond_reuse
     return o
 
 

@@ -234,6 +234,12 @@ typedef struct {
                                  own data and keep the fastest (reported in
                                  mpm_stats.jac_config); 0 (default): fixed
                                  configuration (FP64 staged, FP32 per-term, 128) */
+  int32_t precond_reuse;      /* steps served by one Galerkin product of the multigrid
+                                 hierarchies' coarse levels (0 or 1, default: rebuilt
+                                 at every step's first set-up; k > 1: rebuilt at every
+                                 k-th step, the other steps refreshing only the finest
+                                 levels' values and block-Jacobi inverses).  Changes
+                                 Krylov iteration counts only. */
 } mpm_options;
 
 /* Neumann data of one step: traction t^ per surface entry (n_surf*dim), and

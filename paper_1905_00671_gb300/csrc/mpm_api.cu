@@ -362,7 +362,11 @@ int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
     const int lag = c.opt.precond_lag > 1 ? c.opt.precond_lag : 1;
     if (k % lag == 0) {
-      rc = schur_setup<T>(c, S);  // on the unscaled blocks
+      // a step's first set-up rebuilds the coarse levels once per
+      // precond_reuse steps (default: every step)
+      const int reuse = c.opt.precond_reuse > 1 ? c.opt.precond_reuse : 1;
+      const bool coarse = k > 0 || S.coarse_step < 0 || c.steps - S.coarse_step >= reuse;
+      rc = schur_setup<T>(c, S, coarse);  // on the unscaled blocks
       if (rc) return rc;
     }
     run_scale_system<T>(c, S, c.R);
@@ -553,6 +557,8 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
     return create_fail(BAD, "krylov_restart must be in 1..128");
   if (opt->precond_lag < 0 || opt->precond_lag > MPM_MAX_NEWTON)
     return create_fail(BAD, "precond_lag must be in 0..MPM_MAX_NEWTON");
+  if (opt->precond_reuse < 0 || opt->precond_reuse > 1000000)
+    return create_fail(BAD, "precond_reuse must be in 0..1000000");
   if (opt->schur_approx < MPM_SCHUR_AUTO || opt->schur_approx > MPM_SCHUR_FIXED_STRESS)
     return create_fail(BAD, "unknown schur_approx");
   if (opt->tau_kind < MPM_TAU_WHITE || opt->tau_kind > MPM_TAU_MONFORTE) return create_fail(BAD, "unknown tau_kind");
@@ -866,6 +872,7 @@ void mpm_default_options(mpm_options *o) {
   o->min_volume_fraction = 1e-4;
   o->profile = 0;
   o->precond_lag = 2;
+  o->precond_reuse = 0;
   o->schur_approx = MPM_SCHUR_AUTO;
   o->tau_kind = MPM_TAU_WHITE;
   o->permeability = MPM_PERM_CONSTANT;

@@ -46,6 +46,8 @@ struct LinSys {
   T *B2c = nullptr;    // compact B2 (d values per block), lower-triangular order only
   T *vp = nullptr;     // unscaled v_p, lower-triangular order only
   int64_t sub_cap = 0;
+  bool coarse_built = false;  // the hierarchies' coarse levels hold a Galerkin product
+  int64_t coarse_step = -1;   // the step (Ctx::steps) of that product
   // The multigrid part of the preconditioner application (both V-cycles and
   // the B1 update between them) captured as a CUDA graph; valid while the
   // matrix buffers it reads stay in place.  The graph reads the S-cycle's
@@ -404,7 +406,8 @@ int schur_alloc(Ctx &c, LinSys<T> &S);
 template <typename T>
 void schur_free(LinSys<T> &S);
 template <typename T>
-int schur_setup(Ctx &c, LinSys<T> &S);                 // before run_scale_system (unscaled val)
+int schur_setup(Ctx &c, LinSys<T> &S, bool coarse = true);  // before run_scale_system (unscaled val);
+                                                             // coarse = false: the finest levels only
 template <typename T>
 void schur_apply(Ctx &c, LinSys<T> &S, const T *v, T *z);  // z = M^{-1} v
 

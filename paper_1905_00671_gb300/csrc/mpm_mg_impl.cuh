@@ -1320,8 +1320,16 @@ void mg_free(MGHier<real> &H) {
   H.nlev = 0;
 }
 
+// The finest level's block-Jacobi inverses only: the coarse levels keep the
+// Galerkin product of an earlier set-up (mpm_options.precond_reuse).
+template <int B, int D>
+void mg_refresh_t(Ctx &c, MGHier<real> &H) {
+  k_mg_dinv<B, D, false><<<nblk(H.L[0].nnodes), TPB, 0, c.st>>>(H.L[0], c.err);
+  UPMPM_LAUNCH(c);
+}
+
 void mg_setup(Ctx &c, MGHier<real> &H, const int32_t *row_ptr, const int32_t *col, const real *val,
-              int moff) {
+              int moff, bool coarse) {
   H.L[0].row_ptr = row_ptr;
   H.L[0].col = col;
   H.L[0].val = val;
@@ -1330,11 +1338,11 @@ void mg_setup(Ctx &c, MGHier<real> &H, const int32_t *row_ptr, const int32_t *co
   H.L[0].moff = moff;
   H.L[0].mask = c.row_mask;
   if (c.d == 2) {
-    if (H.B == 1) mg_setup_t<1, 2>(c, H);
-    else mg_setup_t<2, 2>(c, H);
+    if (H.B == 1) coarse ? mg_setup_t<1, 2>(c, H) : mg_refresh_t<1, 2>(c, H);
+    else coarse ? mg_setup_t<2, 2>(c, H) : mg_refresh_t<2, 2>(c, H);
   } else {
-    if (H.B == 1) mg_setup_t<1, 3>(c, H);
-    else mg_setup_t<3, 3>(c, H);
+    if (H.B == 1) coarse ? mg_setup_t<1, 3>(c, H) : mg_refresh_t<1, 3>(c, H);
+    else coarse ? mg_setup_t<3, 3>(c, H) : mg_refresh_t<3, 3>(c, H);
   }
 }
 
@@ -1387,7 +1395,7 @@ void schur_free<MG_REAL>(LinSys<MG_REAL> &S) {
 // Split the unscaled Jacobian (after Dirichlet elimination) into A and S and
 // build both hierarchies.
 template <>
-int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
+int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S, bool coarse) {
   using namespace MG_NS;
   const int64_t nn = c.g.nnodes, nnzb = c.nnzb;
   const int d = c.d;
@@ -1445,9 +1453,17 @@ int schur_setup<MG_REAL>(Ctx &c, LinSys<MG_REAL> &S) {
     else k_extract_B2<3><<<nblk(nnzb), TPB, 0, c.st>>>(nnzb, S.val, S.B2c);
     c.launches += 1;
   }
-  mg_setup(c, *S.mgA, c.row_ptr, c.col, S.Aval, 0);
-  mg_setup(c, *S.mgS, c.row_ptr, c.col, S.Sval, d);
-  dense_invert_pair(c, *S.mgA, *S.mgS);
+  // the coarse levels and the coarsest inverses: a new Galerkin product, or
+  // (coarse = false, after one exists) the product of an earlier set-up kept,
+  // the finest levels' values and block-Jacobi inverses refreshed
+  const bool full = coarse || !S.coarse_built;
+  mg_setup(c, *S.mgA, c.row_ptr, c.col, S.Aval, 0, full);
+  mg_setup(c, *S.mgS, c.row_ptr, c.col, S.Sval, d, full);
+  if (full) {
+    dense_invert_pair(c, *S.mgA, *S.mgS);
+    S.coarse_built = true;
+    S.coarse_step = c.steps;
+  }
   return check_cuda(c, cudaGetLastError(), "schur setup");
 }
 

@@ -70,7 +70,8 @@ class mpm_options(C.Structure):
                 ("precond_lag", C.c_int32), ("schur_approx", C.c_int32), ("stream", C.c_void_p),
                 ("tau_kind", C.c_int32), ("permeability", C.c_int32), ("p2g_mass", C.c_int32),
                 ("model", C.c_int32), ("schur_order", C.c_int32), ("mg_sweeps", C.c_int32),
-                ("mg_omega", C.c_double), ("autotune", C.c_int32)]
+                ("mg_omega", C.c_double), ("autotune", C.c_int32),
+                ("precond_reuse", C.c_int32)]
 
 
 class mpm_loads(C.Structure):
