@@ -1046,14 +1046,19 @@ __global__ void k_mg_rap2(LevelDev F, LevelDev Cl, const real *__restrict__ T) {
           if (d0 < -2 || d0 > 2 || d1 < -2 || d1 > 2 || d2 < -2 || d2 > 2) continue;
           const int64_t a = fa[0] + (int64_t)F.nn[0] * (fa[1] + (int64_t)F.nn[1] * fa[2]);
           if (F.inst && F.inst[a] != Cl.inst[I]) continue;
-          if (row_void<B, FST>(F, a)) continue;  // T_a not written: no contribution
           const real wa = pw(fa[0], Ic[0]) * pw(fa[1], Ic[1]) * (D == 3 ? pw(fa[2], Ic[2]) : 1.0);
+          real wi[B];
+          bool any = false;
+          for (int i = 0; i < B; ++i) {
+            wi[i] = FST ? wa : wa * free_w(F, a, i);
+            any |= wi[i] != real(0);
+          }
+          // a row without contribution (row_void): T_a was not written
+          if (FST ? F.nslot[a] == 0 : !any) continue;
           const int sl = (d0 + 2) + 5 * (d1 + 2) + (D == 3 ? 25 * (d2 + 2) : 0);
           const real *ta = T + ((int64_t)sl * F.nnodes + a) * B * B;
-          for (int i = 0; i < B; ++i) {
-            const real wi = FST ? wa : wa * free_w(F, a, i);
-            for (int j = 0; j < B; ++j) acc[i * B + j] = fma(wi, ta[i * B + j], acc[i * B + j]);
-          }
+          for (int i = 0; i < B; ++i)
+            for (int j = 0; j < B; ++j) acc[i * B + j] = fma(wi[i], ta[i * B + j], acc[i * B + j]);
         }
   }
   for (int i = 0; i < B * B; ++i) Cl.sval[(I * NS + s) * B * B + i] = acc[i];
