@@ -24,6 +24,13 @@ constexpr int NPART = 304;  // partial sums per reduction (2 x 152 SMs)
 constexpr int PSTR = 129;   // stride of the per-block partial sums (restart <= 128)
 constexpr int ORTH_TPB = 1024;     // threads per block of the Gram-Schmidt update ...
 constexpr int64_t ORTH_BIG = 1 << 20;  // ... on systems of at least this many unknowns
+// FP64 Gram-Schmidt: the second pass of classical Gram-Schmidt runs when the
+// first left less than this fraction of the new vector's norm (it then lost
+// more digits than a second pass needs to restore; otherwise one pass keeps
+// the basis orthogonal to round-off: on the oracle's Jacobian of a slope piece
+// the first pass left 0.2-0.5 of the norm and the basis orthogonal to 4e-15
+// with one pass).  FP32 keeps both passes always.
+constexpr double REORTH_THETA = 0.01;
 inline int nblk(int64_t n, int tpb = TPB) { return (int)((n + tpb - 1) / tpb); }
 
 __device__ inline double block_sum(double v) {
@@ -294,12 +301,16 @@ __global__ void k_bsr_spmv(int64_t nnodes, const int32_t *__restrict__ row_ptr,
 // ---------------------------------------------------------------- FGMRES
 // Partial dots of w against V_0..V_{cnt-1}, block (b, i) summing its slice of
 // V_i . w: the cnt products run side by side instead of one after another.
+// A row i = cnt of blocks (grid y = cnt + 1) sums w . w.  With skip set, the
+// kernel does nothing unless *skip is nonzero (a second Gram-Schmidt pass
+// that the first pass's norms made unnecessary).
 template <typename T>
-__global__ void k_multidot2(const T *__restrict__ V, const T *__restrict__ w, int64_t n,
-                            double *__restrict__ part) {
+__global__ void k_multidot2(const T *__restrict__ V, const T *__restrict__ w, int64_t n, int cnt,
+                            double *__restrict__ part, const double *__restrict__ skip) {
   pdl_enter();
+  if (skip && *skip == 0.0) return;
   const int i = blockIdx.y;
-  const T *vi = V + (int64_t)i * n;
+  const T *vi = i < cnt ? V + (int64_t)i * n : w;
   T acc = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     acc += vi[k] * w[k];
@@ -307,11 +318,13 @@ __global__ void k_multidot2(const T *__restrict__ V, const T *__restrict__ w, in
   if (threadIdx.x == 0) part[(int64_t)blockIdx.x * PSTR + i] = s;
 }
 
-// w -= sum_i h_i V_i; with want_norm also the partial sums of |w|^2
+// w -= sum_i h_i V_i; with want_norm also the partial sums of |w|^2; with
+// skip set, nothing unless *skip is nonzero (as k_multidot2)
 template <typename T>
 __global__ void k_orth_sub(T *__restrict__ w, const T *__restrict__ V, const double *__restrict__ h, int cnt,
-                           int64_t n, double *__restrict__ part, int want_norm) {
+                           int64_t n, double *__restrict__ part, int want_norm, const double *__restrict__ skip) {
   pdl_enter();
+  if (skip && *skip == 0.0) return;
   T nacc = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     T sv = w[k];
@@ -326,14 +339,31 @@ __global__ void k_orth_sub(T *__restrict__ w, const T *__restrict__ V, const dou
 }
 
 __global__ void k_multidot_reduce(const double *__restrict__ part, int np, int cnt,
-                                  double *__restrict__ h) {
+                                  double *__restrict__ h, const double *__restrict__ skip) {
   pdl_enter();
   const int i = blockIdx.x;  // one block per coefficient
   if (i >= cnt) return;
+  if (skip && *skip == 0.0) {  // the pass is skipped: its coefficients are zero
+    if (threadIdx.x == 0) h[i] = 0.0;
+    return;
+  }
   double acc = 0.0;
   for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * PSTR + i];
   acc = block_sum(acc);
   if (threadIdx.x == 0) h[i] = acc;
+}
+
+// Whether classical Gram-Schmidt needs its second pass: after the first, w
+// has lost most of its norm to the basis (|w1|^2 < theta^2 |w0|^2, |w0|^2 in
+// h1[cnt] from the first pass's products, |w1|^2 from the first update's
+// partials).  Writes 1 (second pass) or 0 into *flag.
+__global__ void k_reorth_test(const double *__restrict__ part, int np, const double *__restrict__ h1, int cnt,
+                              double theta, double *__restrict__ flag) {
+  pdl_enter();
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < np; b += blockDim.x) acc += part[(int64_t)b * PSTR];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *flag = acc < theta * theta * h1[cnt] ? 1.0 : 0.0;
 }
 
 // Finish Arnoldi column j: ||w|| from the partials, H(:,j) = h1 + h2, apply
@@ -473,13 +503,22 @@ int fgmres_impl(Ctx &c, LinSys<T> &S, double rtol, int maxit, int *iters) {
         const int nbx = (int)std::min<int64_t>(NPART, std::max<int64_t>(std::max(16, NPART / cnt), by_size));
         const T *V = S.V, *wc = w;
         const double *ph = c.part;
-        launch_pdl(c, k_multidot2<T>, dim3(nbx, cnt), TPB, 0, V, wc, N, c.part);
-        launch_pdl(c, k_multidot_reduce, cnt, TPB, 0, ph, nbx, cnt, h1);
         const int otpb = N >= ORTH_BIG ? ORTH_TPB : TPB;
-        launch_pdl(c, k_orth_sub<T>, NPART, otpb, 0, w, V, (const double *)h1, cnt, N, c.part, 0);
-        launch_pdl(c, k_multidot2<T>, dim3(nbx, cnt), TPB, 0, V, wc, N, c.part);
-        launch_pdl(c, k_multidot_reduce, cnt, TPB, 0, ph, nbx, cnt, h2);
-        launch_pdl(c, k_orth_sub<T>, NPART, otpb, 0, w, V, (const double *)h2, cnt, N, c.part, 1);
+        // FP64: the second pass only where the first lost the new direction's
+        // digits (REORTH_THETA); FP32 always takes both passes
+        const bool sel = sizeof(T) == sizeof(double);
+        const double *skip = sel ? (const double *)(c.scal + 6) : nullptr;
+        const int c1 = sel ? cnt + 1 : cnt;  // FP64: |w|^2 beside the products
+        launch_pdl(c, k_multidot2<T>, dim3(nbx, c1), TPB, 0, V, wc, N, cnt, c.part, (const double *)nullptr);
+        launch_pdl(c, k_multidot_reduce, c1, TPB, 0, ph, nbx, c1, h1, (const double *)nullptr);
+        launch_pdl(c, k_orth_sub<T>, NPART, otpb, 0, w, V, (const double *)h1, cnt, N, c.part, sel ? 1 : 0,
+                   (const double *)nullptr);
+        if (sel)
+          launch_pdl(c, k_reorth_test, 1, TPB, 0, ph, (int)NPART, (const double *)h1, cnt, REORTH_THETA,
+                     c.scal + 6);
+        launch_pdl(c, k_multidot2<T>, dim3(nbx, cnt), TPB, 0, V, wc, N, cnt, c.part, skip);
+        launch_pdl(c, k_multidot_reduce, cnt, TPB, 0, ph, nbx, cnt, h2, skip);
+        launch_pdl(c, k_orth_sub<T>, NPART, otpb, 0, w, V, (const double *)h2, cnt, N, c.part, 1, skip);
       }
       prof_end(c, MPM_PROF_ORTH);
       launch_pdl(c, k_arnoldi_finish, 1, TPB, 0, (const double *)c.part, (int)NPART, j, m, (const double *)h1,
