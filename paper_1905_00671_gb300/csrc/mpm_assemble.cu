@@ -410,6 +410,11 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
   const double mu_p = G - lam * lnJ;
   const double vol = dJ * Vn;
   double *rec = v.rec;
+  float *recf = v.recf;  // FP32 copies (mixed mode), written with the FP64 values
+  auto put = [&](int f, double val) {
+    rec[f * n + p] = val;
+    if (recf) recf[f * n + p] = (float)val;
+  };
   double hq[9], hk[3], ht[3];  // Hencky: principal directions, kappa_A, theta_AB
   if (s.hencky) {
     double x[3], eps[3], tA[3], tr = 0.0;
@@ -428,17 +433,17 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
       for (int j = 0; j < D; ++j) {
         double t = 0.0;
         for (int A = 0; A < D; ++A) t += tA[A] * hq[i * D + A] * hq[j * D + A];
-        rec[(RC_TAU + i * D + j) * n + p] = t;
+        put(RC_TAU + i * D + j, t);
       }
-    for (int i = 0; i < D * D; ++i) rec[(RC_HQ + i) * n + p] = hq[i];
-    for (int A = 0; A < D; ++A) rec[(RC_HK + A) * n + p] = hk[A];
-    for (int k = 0; k < D * (D - 1) / 2; ++k) rec[(RC_HT + k) * n + p] = ht[k];
+    for (int i = 0; i < D * D; ++i) put(RC_HQ + i, hq[i]);
+    for (int A = 0; A < D; ++A) put(RC_HK + A, hk[A]);
+    for (int k = 0; k < D * (D - 1) / 2; ++k) put(RC_HT + k, ht[k]);
   }
   for (int i = 0; i < D; ++i)
     for (int j = 0; j < D; ++j) {
-      rec[(RC_FINV + i * D + j) * n + p] = fi[i * D + j];
+      put(RC_FINV + i * D + j, fi[i * D + j]);
       if (!s.hencky)
-        rec[(RC_TAU + i * D + j) * n + p] = G * (bl[i * D + j] - (i == j ? 1.0 : 0.0)) + (i == j ? lam * lnJ : 0.0);
+        put(RC_TAU + i * D + j, G * (bl[i * D + j] - (i == j ? 1.0 : 0.0)) + (i == j ? lam * lnJ : 0.0));
     }
   double gp[3] = {0, 0, 0}, gv[9] = {0};
   for (int j = 0; j < D; ++j) {
@@ -459,10 +464,9 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
     double trD = divv;
     for (int i = 0; i < D; ++i)
       for (int j = 0; j < D; ++j) {
-        rec[(RC_GV + i * D + j) * n + p] = gv[i * D + j];
+        put(RC_GV + i * D + j, gv[i * D + j]);
         const double Dij = 0.5 * (gv[i * D + j] + gv[j * D + i]);
-        rec[(RC_SVIS + i * D + j) * n + p] =
-            s.alpha_vis * ((i == j ? lam * trD : 0.0) + 2.0 * mu_p * Dij);
+        put(RC_SVIS + i * D + j, s.alpha_vis * ((i == j ? lam * trD : 0.0) + 2.0 * mu_p * Dij));
       }
     if (s.hencky) {  // alpha c : d with the Hencky tangent, in the principal frame
       double Dh[9], Sh[9];
@@ -482,7 +486,7 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
           double t = 0.0;
           for (int A = 0; A < D; ++A)
             for (int B = 0; B < D; ++B) t += hq[i * D + A] * Sh[A * D + B] * hq[j * D + B];
-          rec[(RC_SVIS + i * D + j) * n + p] = s.alpha_vis * t;
+          put(RC_SVIS + i * D + j, s.alpha_vis * t);
         }
     }
   } else {
@@ -490,28 +494,28 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
   }
   const double m = v.m[p];
   for (int j = 0; j < D; ++j) {
-    rec[(RC_GP + j) * n + p] = gp[j];
-    rec[(RC_W + j) * n + p] = gp[j] - s.rho_f * (s.g[j] - ah[j]);
-    rec[(RC_FRC + j) * n + p] = m * (s.g[j] - ah[j]);
+    put(RC_GP + j, gp[j]);
+    put(RC_W + j, gp[j] - s.rho_f * (s.g[j] - ah[j]));
+    put(RC_FRC + j, m * (s.g[j] - ah[j]));
   }
-  rec[RC_CS * n + p] = Vn / Jn;
-  rec[RC_VOL * n + p] = vol;
-  rec[RC_PH * n + p] = ph;
-  rec[RC_MUP * n + p] = mu_p;
-  rec[RC_LAM * n + p] = lam;
+  put(RC_CS, Vn / Jn);
+  put(RC_VOL, vol);
+  put(RC_PH, ph);
+  put(RC_MUP, mu_p);
+  put(RC_LAM, lam);
   double kv = vol * kap, dkv = 0.0;
   if (s.kozeny) {  // mobility at the current porosity, Eq. kozeny-carman
     double jdk;
     kv = vol * kozeny_carman(kap, s.phi0, J, &jdk);
     dkv = vol * jdk;
   }
-  rec[RC_KV * n + p] = kv;
-  rec[RC_DKV * n + p] = dkv;
-  rec[RC_CST * n + p] = (DYN ? tau * gm / (b * dt) : tau / dt) * Vn;
-  rec[RC_RST * n + p] = tau * Vn * pdev;
-  rec[RC_DIVV * n + p] = vol * divv;
-  rec[RC_B2 * n + p] = DYN ? vol * (gm / (b * dt) + divv) : vol * (1.0 + log(dJ)) / dt;
-  rec[RC_MS * n + p] = DYN ? m / (b * dt * dt) : 0.0;
+  put(RC_KV, kv);
+  put(RC_DKV, dkv);
+  put(RC_CST, (DYN ? tau * gm / (b * dt) : tau / dt) * Vn);
+  put(RC_RST, tau * Vn * pdev);
+  put(RC_DIVV, vol * divv);
+  put(RC_B2, DYN ? vol * (gm / (b * dt) + divv) : vol * (1.0 + log(dJ)) / dt);
+  put(RC_MS, DYN ? m / (b * dt * dt) : 0.0);
   // The residual's per-point factors.  With g = Gn dF^-1 (Gn the gradient of
   // the basis in the configuration of t_n), the momentum term of a node,
   // -cs g.(tau' + s_vis) + vol p^h g, is Gn.RU, and the Darcy term
@@ -532,8 +536,6 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
     for (int j = 0; j < D; ++j) acc += fi[k * D + j] * rec[(RC_W + j) * n + p];
     rec[(RC_KW + k) * n + p] = kv * acc;
   }
-  if (v.recf)
-    for (int f = 0; f < RC_F32; ++f) v.recf[f * n + p] = (float)rec[f * n + p];
 }
 
 // ---------------------------------------------------------------- residual
