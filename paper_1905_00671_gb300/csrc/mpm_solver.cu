@@ -180,16 +180,53 @@ __global__ void k_diag_scale(int64_t nnodes, const int32_t *__restrict__ row_ptr
   }
 }
 
+// D J D in place, FP64: one thread per value (the two multiplications of
+// each value are the kernel's FP64 work; one thread per block was slower).
 template <int NB, typename T>
-__global__ void k_scale_matrix(int64_t nnzb, const int32_t *__restrict__ row_of,
-                               const int32_t *__restrict__ col, T *__restrict__ val,
-                               const T *__restrict__ dsc) {
+__global__ void k_scale_matrix_v(int64_t nnzb, const int32_t *__restrict__ row_of,
+                                 const int32_t *__restrict__ col, T *__restrict__ val,
+                                 const T *__restrict__ dsc) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= nnzb * NB * NB) return;
   const int64_t e = t / (NB * NB);
   const int rc = (int)(t % (NB * NB));
   const int r = rc / NB, cc = rc % NB;
   val[t] *= dsc[(int64_t)row_of[e] * NB + r] * dsc[(int64_t)col[e] * NB + cc];
+}
+
+// D J D in place, FP32 (bound by memory): one thread per block, the block's
+// NB row and NB column scales read once, its NB^2 values in 16-byte words.
+template <int NB, typename T>
+__global__ void k_scale_matrix(int64_t nnzb, const int32_t *__restrict__ row_of,
+                               const int32_t *__restrict__ col, T *__restrict__ val,
+                               const T *__restrict__ dsc) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nnzb) return;
+  const int64_t ra = (int64_t)row_of[e] * NB, cb = (int64_t)col[e] * NB;
+  T rs[NB], cs[NB];
+#pragma unroll
+  for (int i = 0; i < NB; ++i) {
+    rs[i] = dsc[ra + i];
+    cs[i] = dsc[cb + i];
+  }
+  T *blk = val + e * NB * NB;
+  if constexpr (NB == 4 && sizeof(T) == sizeof(float)) {  // a block row is one 16-byte word
+    float4 *b4 = reinterpret_cast<float4 *>(blk);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float4 v = b4[i];
+      v.x *= rs[i] * cs[0];
+      v.y *= rs[i] * cs[1];
+      v.z *= rs[i] * cs[2];
+      v.w *= rs[i] * cs[3];
+      b4[i] = v;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NB; ++i)
+#pragma unroll
+      for (int j = 0; j < NB; ++j) blk[i * NB + j] *= rs[i] * cs[j];
+  }
 }
 
 template <typename T>
@@ -789,10 +826,16 @@ void run_scale_system(Ctx &c, LinSys<T> &S, const double *R) {
   const int64_t nn = c.g.nnodes;
   if (c.nb == 3) {
     k_diag_scale<3, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.dscinv);
-    k_scale_matrix<3, T><<<nblk(c.nnzb * 9), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
+    if (sizeof(T) == sizeof(float))
+      k_scale_matrix<3, T><<<nblk(c.nnzb), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
+    else
+      k_scale_matrix_v<3, T><<<nblk(c.nnzb * 9), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
   } else {
     k_diag_scale<4, T><<<nblk(nn), TPB, 0, c.st>>>(nn, c.row_ptr, c.col, S.val, S.dscale, S.dscinv);
-    k_scale_matrix<4, T><<<nblk(c.nnzb * 16), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
+    if (sizeof(T) == sizeof(float))
+      k_scale_matrix<4, T><<<nblk(c.nnzb), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
+    else
+      k_scale_matrix_v<4, T><<<nblk(c.nnzb * 16), TPB, 0, c.st>>>(c.nnzb, c.row_of, c.col, S.val, S.dscale);
   }
   k_scale_rhs<T><<<nblk(c.N()), TPB, 0, c.st>>>(c.N(), R, S.dscale, S.rhs);
   c.launches += 3;
