@@ -41,6 +41,7 @@ def test_default_options_without_gpu(lib):
     o = mpm.default_options()
     assert o.shape == mpm.MPM_SHAPE_GIMP and o.newton_rtol == 1e-8 and o.krylov_restart == 120
     assert o.precond_lag == 2
+    assert o.precond_reuse == 0  # the coarse levels rebuilt at every step
     assert o.precond == mpm.MPM_PRECOND_SCHUR_MG
 
 
@@ -69,6 +70,7 @@ def test_product_path_never_imports_the_oracle():
     (dict(precision=1), 1, "needs precision MPM_FP64"),
     (dict(tau_kind=2), None, "MPM_TAU_MONFORTE needs the Newmark scheme"),
     (dict(min_volume_fraction=-1.0), None, "min_volume_fraction"),
+    (dict(precond_reuse=-1), None, "precond_reuse must be in"),
 ])
 def test_rejected_create_names_its_reason_without_gpu(lib, opts, model, why):
     """Argument checks run on the host before any device call: mpm_create
