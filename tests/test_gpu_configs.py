@@ -215,3 +215,19 @@ def test_nan_traction_is_nonfinite_and_the_state_stays_at_the_last_step(mpm):
     orc.step()
     _compare(w, sim.read(_fields(w)), orc.state(), _fields(w), "after NONFINITE")
     sim.close()
+
+
+def test_coarse_levels_kept_over_steps_leave_the_steps_unchanged(mpm):
+    """mpm_options.precond_reuse keeps the multigrid coarse levels of one
+    Galerkin product for several steps (the finest levels refreshed): the
+    preconditioner changes, the solution does not (steps against the oracle at
+    the parity bar, on a Newmark footing and a quasi-static 3D block)."""
+    for w, nsteps in ((I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25), 4),
+                      (I.small_block(seed=11, body=(6, 5, 4)), 3)):
+        sim = mpm.Simulation(w, precond_reuse=3, **GPU_TIGHT)
+        orc = O.Oracle(w, **TIGHT)
+        for s in range(nsteps):
+            sim.step()
+            orc.step()
+            _compare(w, sim.read(_fields(w)), orc.state(), _fields(w), ("reuse", w.name, s))
+        sim.close()
