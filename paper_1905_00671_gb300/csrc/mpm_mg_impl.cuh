@@ -26,10 +26,6 @@ struct NS_ {
   static constexpr int v = D == 2 ? 25 : 125;
 };
 
-__host__ __device__ inline int slot_of(int o0, int o1, int o2) {
-  return (o0 + 2) + 5 * (o1 + 2) + 25 * (o2 + 2);
-}
-
 // Small dense inverse with partial pivoting (B <= 4); identity on failure.
 template <int B>
 __device__ inline bool invert_small(real A[B][B], real Inv[B][B]) {
