@@ -702,8 +702,10 @@ def run_batch(args, rank, world, local_rank):
     npts = sum(w.n for w in ws)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    sopts = solver_opts(args)
+
     def timed(precision):
-        bs = [mpm.Batch(v, stream=stream.cuda_stream, precision=precision, newton_max=60)
+        bs = [mpm.Batch(v, stream=stream.cuda_stream, precision=precision, newton_max=60, **sopts)
               for v in kinds.values() if v]
         for _ in range(args.warmup):
             for b in bs:
@@ -715,24 +717,34 @@ def run_batch(args, rank, world, local_rank):
         e1 = torch.cuda.Event(enable_timing=True)
         ms = 0.0
         newton = []
+        launches = 0
         clocks = ClockSampler(local_rank)
         clocks.start()
         for _ in range(args.steps):
             flush.zero_()
             e0.record(stream)
             for b in bs:
-                newton.append(b.step()["newton_iters"])
+                st = b.step()
+                newton.append(st["newton_iters"])
+                launches += st["kernel_launches"]
             e1.record(stream)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
         clk = clocks.stop()
         out = [b.read(("u", "p")) for b in bs]
+        pi = 0 if precision == mpm.MPM_FP64 else 1
+        jac = []
+        for name, b in zip([k for k, v in kinds.items() if v], bs):
+            st = b.stats()
+            jac.append({"context": name, "config": st["jac_config"][pi], "tuned": st["jac_tuned"][pi],
+                        "candidates_ms": [round(x, 3) for x in st["jac_tune_ms"][pi]]})
         for b in bs:
             b.close()
-        return max_over_ranks(ms, world, "cuda"), newton, out, clk
+        info = {"kernel_launches_per_step": launches / args.steps, "jacobian_kernel": jac}
+        return max_over_ranks(ms, world, "cuda"), newton, out, clk, info
 
-    ms_mixed, newton_mixed, res_mixed, clk_mixed = timed(mpm.MPM_MIXED)
-    ms_fp64, newton_fp64, res_fp64, clk_fp64 = timed(mpm.MPM_FP64)
+    ms_mixed, newton_mixed, res_mixed, clk_mixed, info_mixed = timed(mpm.MPM_MIXED)
+    ms_fp64, newton_fp64, res_fp64, clk_fp64, info_fp64 = timed(mpm.MPM_FP64)
     # one at a time, FP64: a sample of each kind, same number of steps
     sample = {k: v[:args.batch_sample] for k, v in kinds.items() if v}
     per_kind_ms = {}
@@ -773,9 +785,15 @@ def run_batch(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
             "newton_iters_per_context_step": float(np.mean(newton_mixed)),
             "clocks": clk_mixed,
+            "gpu_launches": int(info_mixed["kernel_launches_per_step"] * args.steps),
+            "kernel_launches_per_step": info_mixed["kernel_launches_per_step"],
+            "jacobian_kernel": info_mixed["jacobian_kernel"],
+            "solver_options": sopts,
             "fp64_batched": {"value": world * npts * args.steps / (ms_fp64 * 1e-3), "unit": UNIT,
                              "ms_per_step": ms_fp64 / args.steps, "clocks": clk_fp64,
-                             "newton_iters_per_context_step": float(np.mean(newton_fp64))},
+                             "newton_iters_per_context_step": float(np.mean(newton_fp64)),
+                             "kernel_launches_per_step": info_fp64["kernel_launches_per_step"],
+                             "jacobian_kernel": info_fp64["jacobian_kernel"]},
             "one_by_one_fp64": {"value": world * npts * args.steps / (one_ms * 1e-3), "unit": UNIT,
                                 "ms_per_step": one_ms / args.steps,
                                 "sample": f"{sum(len(v) for v in sample.values())} instances stepped alone "

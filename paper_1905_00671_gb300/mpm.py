@@ -471,7 +471,9 @@ class Batch:
         k = s.newton_iters
         return {"newton_iters": k, "krylov_iters": list(s.krylov_iters[:k]),
                 "krylov_total": s.krylov_total, "steps": s.steps, "nnzb": s.nnzb,
-                "kernel_launches": s.kernel_launches}
+                "kernel_launches": s.kernel_launches,
+                "jac_config": list(s.jac_config), "jac_tuned": list(s.jac_tuned),
+                "jac_tune_ms": [list(r) for r in s.jac_tune_ms]}
 
     def read(self, fields=("x", "u", "p")):
         """Per-instance dicts of the point fields (each in its own order)."""
