@@ -521,19 +521,27 @@ __global__ void k_point_eval(GridP g, StepP s, DevView v, const double *__restri
   // -cs g.(tau' + s_vis) + vol p^h g, is Gn.RU, and the Darcy term
   // kappa vol g.w is Gn.KW: the residual's node sums then spend d^2 + d FMAs
   // per (point, node) on them instead of forming g first.
+  // (the stress and w read back once into registers: the stores below could
+  // alias them for the compiler)
+  const double cs = Vn / Jn;
+  double sg[9], wv[3];
+  for (int i = 0; i < D; ++i) {
+    for (int j = 0; j < D; ++j) {
+      double sij = rec[(RC_TAU + i * D + j) * n + p];
+      if (DYN) sij += rec[(RC_SVIS + i * D + j) * n + p];
+      sg[i * D + j] = sij;
+    }
+    wv[i] = rec[(RC_W + i) * n + p];
+  }
   for (int i = 0; i < D; ++i)
     for (int k = 0; k < D; ++k) {
       double acc = vol * ph * fi[k * D + i];
-      for (int j = 0; j < D; ++j) {
-        double sij = rec[(RC_TAU + i * D + j) * n + p];
-        if (DYN) sij += rec[(RC_SVIS + i * D + j) * n + p];
-        acc -= (Vn / Jn) * sij * fi[k * D + j];
-      }
+      for (int j = 0; j < D; ++j) acc -= cs * sg[i * D + j] * fi[k * D + j];
       rec[(RC_RU + i * D + k) * n + p] = acc;
     }
   for (int k = 0; k < D; ++k) {
     double acc = 0.0;
-    for (int j = 0; j < D; ++j) acc += fi[k * D + j] * rec[(RC_W + j) * n + p];
+    for (int j = 0; j < D; ++j) acc += fi[k * D + j] * wv[j];
     rec[(RC_KW + k) * n + p] = kv * acc;
   }
 }
