@@ -231,3 +231,60 @@ def test_coarse_levels_kept_over_steps_leave_the_steps_unchanged(mpm):
             orc.step()
             _compare(w, sim.read(_fields(w)), orc.state(), _fields(w), ("reuse", w.name, s))
         sim.close()
+
+
+WIDE = {
+    # GIMP domains of 0.7 h (two points per cell and axis overlap): supports of
+    # four nodes along an axis, the widest the first-node bins (and the
+    # candidate cells) handle
+    "footing2d-gimp-qs-wide": lambda: I.small_footing(seed=9, dynamic=False, body=(20, 10), pad=2, dt=1.0),
+    "footing2d-gimp-newmark-wide": lambda: I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25),
+    "block3d-gimp-qs-wide": lambda: I.small_block(seed=11, body=(6, 5, 4)),
+}
+
+
+@pytest.mark.parametrize("name", list(WIDE))
+def test_four_node_supports(mpm, name):
+    """Pattern bit-exact, residual and Jacobian entry-wise (FP64 and every FP32
+    configuration) and two steps against the oracle on GIMP domains wide enough
+    that supports span four nodes along an axis."""
+    w = WIDE[name]()
+    w = replace(w, lp=np.ascontiguousarray(w.lp * 2.8), name=w.name + "-wide")
+    orc = O.Oracle(w, **TIGHT)
+    prep = orc.prepare(w.dt)
+    assert (prep["count"] == 4).any()
+    nb = w.dim + 1
+    rng = np.random.default_rng(3)
+    X = orc.initial_guess(prep).reshape(-1, nb)
+    X[:, :w.dim] += 1e-4 * rng.standard_normal((orc.nn, w.dim))
+    X[:, w.dim] += 1e3 * rng.standard_normal(orc.nn)
+    X = X.reshape(-1)
+    Ro, Jo = orc.eval(prep, X, w.traction(w.dt))
+    Jo = Jo.reshape(-1, nb, nb)
+    for precision in (mpm.MPM_FP64, mpm.MPM_MIXED):
+        sim = mpm.Simulation(w, precision=precision)
+        sim.debug_prepare()
+        row_ptr, col = sim.debug_pattern()
+        np.testing.assert_array_equal(row_ptr, prep["row_ptr"])
+        np.testing.assert_array_equal(col, prep["col"])
+        Rg, Jg = sim.debug_eval(X, nnzb=len(col), apply_bc=False)
+        for r in range(nb):
+            assert rel(Rg[r::nb], Ro[r::nb]) <= 1e-11, ("R", r)
+        Jg = Jg.reshape(-1, nb, nb)
+        for r in range(nb):
+            for c in range(nb):
+                assert rel(Jg[:, r, c], Jo[:, r, c]) <= 1e-11, ("J", r, c)
+        if precision == mpm.MPM_MIXED:
+            for form in (0, 1):
+                J32 = sim.debug_jacobian32(X, len(col), form, 128).reshape(-1, nb, nb)
+                for r in range(nb):
+                    for c in range(nb):
+                        assert rel(J32[:, r, c], Jo[:, r, c]) <= 2e-5, ("J32", form, r, c)
+        sim.close()
+    sim = mpm.Simulation(w, **GPU_TIGHT)
+    orc = O.Oracle(w, **TIGHT)
+    for s in range(2):
+        sim.step()
+        orc.step()
+        _compare(w, sim.read(_fields(w)), orc.state(), _fields(w), (name, s))
+    sim.close()
