@@ -276,13 +276,16 @@ def spmv_bytes(nnodes, nnzb, nb, word=8):
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
 
 
-def jacobian32_bytes(n, nnzb, nnodes, dim, dynamic):
+def jacobian32_bytes(n, nnzb, nnodes, dim, dynamic, hencky=False):
     """Algorithmic bytes of one FP32 Jacobian assembly: every point's data the
     tangent needs read once (dF^-1, tau', grad p - rho_f (g - a), grad p, nine
     scalar coefficients, the 1D basis S, dS, S0 in 4 slots per axis; Newmark:
-    the mass and grad v), the sparsity read once (coupling mask, row pointers,
-    block columns) and every (d+1)^2 block written once, 4-byte words."""
+    the mass and grad v; Hencky: the principal directions, kappa_A and
+    theta_AB), the sparsity read once (coupling mask, row pointers, block
+    columns) and every (d+1)^2 block written once, 4-byte words."""
     per_point = 2 * dim * dim + 2 * dim + 9 + 3 * dim * 4 + (1 + dim * dim if dynamic else 0)
+    if hencky:
+        per_point += dim * dim + dim + dim * (dim - 1) // 2
     nb = dim + 1
     return 4 * per_point * n + nnzb * (nb * nb * 4 + 4) + nnodes * (6 * 8 + 4)
 
@@ -395,9 +398,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- mixed precision (FP32 Jacobian / preconditioner / Krylov in the FP64
     # Newton loop): same steps, same timing rules, error against the FP64 run
     mixed = None
-    if not args.no_mixed and w.model == mpm.MPM_MODEL_HENCKY:
-        mixed = {"value": None, "unit": UNIT, "skipped": "Hencky elasticity has no FP32 Jacobian"}
-    elif not args.no_mixed:
+    if not args.no_mixed:
         sim_m = mpm.Simulation(w, stream=stream.cuda_stream, precision=mpm.MPM_MIXED,
                                newton_max=60, profile=prof_bits, precond_lag=args.precond_lag, **sopts)
         sim_r = mpm.Simulation(w, stream=stream.cuda_stream, **sopts)   # FP64 twin for the error
@@ -449,8 +450,9 @@ def run_ours(args, rank, world, local_rank):
         if prof_nm["jacobian"] > 0:
             avg_ms = prof_m["jacobian"] / prof_nm["jacobian"]
             nz = sum(nnzb_m) / len(nnzb_m)
-            byt = jacobian32_bytes(w.n, nz, w.nnodes, w.dim, w.dynamic)
-            fl = sum(jacobian_flops(w.dim, w.dynamic, False, t, pn) for t, pn in terms_m) / len(terms_m)
+            hk = w.model == mpm.MPM_MODEL_HENCKY
+            byt = jacobian32_bytes(w.n, nz, w.nnodes, w.dim, w.dynamic, hk)
+            fl = sum(jacobian_flops(w.dim, w.dynamic, hk, t, pn) for t, pn in terms_m) / len(terms_m)
             ach = byt / (avg_ms * 1e-3) / 1e9
             roof_m["jacobian"] = {
                 "kernel": "k_jacobian_direct" if jac_cfg_m["config"] < 1000 else "k_point_nodes + k_jacobian (FP32)",

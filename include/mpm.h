@@ -91,8 +91,9 @@ enum { MPM_P2G_LUMPED = 0, MPM_P2G_CONSISTENT = 1 };
 /* Hyperelastic model of the solid skeleton: NEOHOOKE, tau' = G (b - 1) +
  * lambda ln J 1 (the default), or HENCKY (Sec. 2.2: Psi = lambda/2 (ln J)^2 +
  * G tr((ln b / 2)^2), tau' = lambda ln J 1 + G ln b), with its spectral
- * tangent in the Jacobian and in the Kelvin stress; HENCKY runs in FP64
- * (precision MPM_MIXED is rejected). */
+ * tangent in the Jacobian and in the Kelvin stress; in precision MPM_MIXED
+ * the FP32 Jacobian of HENCKY stages that tangent per (point, node) (the
+ * per-term form is neo-Hookean only). */
 enum { MPM_MODEL_NEOHOOKE = 0, MPM_MODEL_HENCKY = 1 };
 
 /* Preconditioner of the FGMRES solve of the Newton system: node-block Jacobi,
@@ -232,8 +233,9 @@ typedef struct {
                                  per-term or staged per-(point, node) vectors; both:
                                  64, 128 or 256 threads per block) on the context's
                                  own data and keep the fastest (reported in
-                                 mpm_stats.jac_config); 0 (default): fixed
-                                 configuration (FP64 staged, FP32 per-term, 128) */
+                                 mpm_stats.jac_config; FP32 Hencky: staged only);
+                                 0 (default): fixed configuration (FP64 staged,
+                                 FP32 per-term (Hencky: staged), 128) */
   int32_t precond_reuse;      /* steps served by one Galerkin product of the multigrid
                                  hierarchies' coarse levels (0 or 1, default: rebuilt
                                  at every step's first set-up; k > 1: rebuilt at every
@@ -429,8 +431,8 @@ int mpm_debug_precond(mpm_ctx *ctx, const double *X, const double *v, double *z)
  * 128 or 256 threads per block (the candidates of mpm_options.autotune).  Jv: nnzb blocks of
  * (dim+1)^2 floats in the pattern's order, before (apply_bc = 0) or after
  * (apply_bc = 1) Dirichlet elimination.  MPM_ERR_BAD_ARG for a context that
- * is not mixed-precision, a form or block size outside these sets, or no
- * prepared step. */
+ * is not mixed-precision, a form or block size outside these sets, form 0 in
+ * a Hencky context, or no prepared step. */
 int mpm_debug_jacobian32(mpm_ctx *ctx, const double *X, int32_t form, int32_t tpb, float *Jv,
                          int32_t apply_bc);
 

@@ -357,6 +357,7 @@ template <typename T>
 int newton_correction(Ctx &c, LinSys<T> &S, int k, int *its) {
   int rc;
   if (sizeof(T) == sizeof(double) && (rc = ensure_jacobian_staging(c))) return rc;
+  if (sizeof(T) == sizeof(float) && c.s.hencky && (rc = ensure_jacobian_staging32(c))) return rc;
   run_jacobian<T>(c, S.val, 1);
   prof_begin(c, MPM_PROF_SETUP);
   if (c.opt.precond == MPM_PRECOND_SCHUR_MG) {
@@ -567,8 +568,6 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   if (opt->p2g_mass != MPM_P2G_LUMPED && opt->p2g_mass != MPM_P2G_CONSISTENT)
     return create_fail(BAD, "unknown p2g_mass");
   if (opt->model != MPM_MODEL_NEOHOOKE && opt->model != MPM_MODEL_HENCKY) return create_fail(BAD, "unknown model");
-  if (opt->model == MPM_MODEL_HENCKY && opt->precision != MPM_FP64)
-    return create_fail(BAD, "MPM_MODEL_HENCKY needs precision MPM_FP64 (no FP32 Hencky Jacobian)");
   if (opt->permeability == MPM_PERM_KOZENY_CARMAN && !(mat->phi0 > 0.0 && mat->phi0 < 1.0))
     return create_fail(BAD, "MPM_PERM_KOZENY_CARMAN needs 0 < material.phi0 < 1");
   // tau_M uses the Newmark parameters: dynamic steps only (Sec. 4.3)
@@ -653,6 +652,8 @@ int create_impl(const mpm_grid *grid, const mpm_particles *P, const mpm_material
   s.phi_min = opt->min_volume_fraction;
   s.kozeny = opt->permeability == MPM_PERM_KOZENY_CARMAN;
   s.hencky = opt->model == MPM_MODEL_HENCKY;
+  // the FP32 Jacobian's direct form has no Hencky tangent: staged only
+  if (s.hencky) c.jac_cfg[1].form = Ctx::JAC_STAGED;
   for (int k = 0; k < 3; ++k) s.g[k] = k < c.d ? mat->g[k] : 0.0;
   c.n = P->n;
   c.n_surf = P->n_surf;
@@ -1272,6 +1273,10 @@ int mpm_debug_jacobian32(mpm_ctx *h, const double *X, int32_t form, int32_t tpb,
   }
   if (form < 0 || form >= Ctx::JAC_FORMS || (tpb != 64 && tpb != 128 && tpb != 256)) {
     c.last_error = "form must be 0 or 1 and tpb 64, 128 or 256";
+    return MPM_ERR_BAD_ARG;
+  }
+  if (c.s.hencky && form == Ctx::JAC_DIRECT) {
+    c.last_error = "the direct FP32 Jacobian has no Hencky tangent: form 1 only";
     return MPM_ERR_BAD_ARG;
   }
   const int64_t N = c.N();

@@ -976,7 +976,8 @@ __global__ void k_jacobian(GridP g, StepP s, DevView v, const R *__restrict__ pn
 }
 
 // FP32 variant (mixed mode): the node vectors are recomputed per term from the
-// FP32 basis and records; with FP32 arithmetic plentiful this beats staging.
+// FP32 basis and records; with FP32 arithmetic plentiful this can beat staging.
+// Neo-Hookean only: the Hencky tangent (d^3 values per node) is staged.
 // Symmetric pairs as in k_jacobian: one thread per unordered pair (a, b).
 template <int D, bool GIMP, bool DYN, bool FB, typename T, typename R>
 __global__ void k_jacobian_direct(GridP g, StepP s, DevView v, BasisArrays<R> BA, const R *__restrict__ rec,
@@ -1186,16 +1187,9 @@ __global__ void k_cm_spmv(int64_t nn, int K, DevView v, double phi_min, const in
 
 constexpr int CM_NBLK = 64;  // partial sums per field
 
-// per field f: part[f][blk] = sum of u.w (and, with w2, of u.w2) over its slice
-__global__ void k_cm_dots(int64_t nn, const double *__restrict__ u, const double *__restrict__ w,
-                          const double *__restrict__ w2, double *__restrict__ part, double *__restrict__ part2) {
-  const int f = blockIdx.y;
-  double s = 0.0, s2 = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
-    const double ui = u[(int64_t)f * nn + i];
-    s += ui * w[(int64_t)f * nn + i];
-    if (w2) s2 += ui * w2[(int64_t)f * nn + i];
-  }
+// Block sums of s and s2 (every thread's), left in thread 0's s and s2: warp
+// butterflies, then warp 0's lane 0 adds the warps' sums in warp order.
+__device__ inline void cm_block_sum2(double &s, double &s2) {
   __shared__ double sh[2][32];
   for (int o = 16; o > 0; o >>= 1) {
     s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -1212,8 +1206,25 @@ __global__ void k_cm_dots(int64_t nn, const double *__restrict__ u, const double
       a += sh[0][i];
       b += sh[1][i];
     }
-    part[f * CM_NBLK + blockIdx.x] = a;
-    if (part2) part2[f * CM_NBLK + blockIdx.x] = b;
+    s = a;
+    s2 = b;
+  }
+}
+
+// per field f: part[f][blk] = sum of u.w (and, with w2, of u.w2) over its slice
+__global__ void k_cm_dots(int64_t nn, const double *__restrict__ u, const double *__restrict__ w,
+                          const double *__restrict__ w2, double *__restrict__ part, double *__restrict__ part2) {
+  const int f = blockIdx.y;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ui = u[(int64_t)f * nn + i];
+    s += ui * w[(int64_t)f * nn + i];
+    if (w2) s2 += ui * w2[(int64_t)f * nn + i];
+  }
+  cm_block_sum2(s, s2);
+  if (threadIdx.x == 0) {
+    part[f * CM_NBLK + blockIdx.x] = s;
+    if (part2) part2[f * CM_NBLK + blockIdx.x] = s2;
   }
 }
 
@@ -1231,33 +1242,123 @@ __global__ void k_cm_sum(int K, const double *__restrict__ part, const double *_
   if (out2) out2[f] = b;
 }
 
-// x += alpha p, r -= alpha q, z = Dinv r with alpha = rz / pq per field
-__global__ void k_cm_step(int64_t nn, int K, const double *__restrict__ rz, const double *__restrict__ pq,
-                          const double *__restrict__ dinv, const double *__restrict__ p,
-                          const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
-                          double *__restrict__ z) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nn * K) return;
-  const int f = (int)(t / nn);
-  const int64_t a = t - (int64_t)f * nn;
-  const double alpha = pq[f] != 0.0 ? rz[f] / pq[f] : 0.0;
-  x[t] += alpha * p[t];
-  r[t] -= alpha * q[t];
-  z[t] = dinv[a] * r[t];
+// One CG iteration on the Jacobi-scaled consistent mass is three kernels on a
+// (CM_NBLK, K) grid (a block per slice of one field, the slices of k_cm_dots,
+// so the partial sums are those of separate product and dot kernels).  The
+// convergence test runs on the device: k_cm_next sets *flag to 1 when every
+// field's r.r is within rtol^2 of its rhs.rhs (2 for a non-finite r.r), and
+// k_cm_qdot and k_cm_update do nothing once it is set, so iterations launched
+// past convergence leave x as the converged iteration wrote it and the host
+// reads the flag only every few iterations.  rz alternates between two
+// buffers (k_cm_next writes the next iteration's while its blocks read the
+// current one).
+
+// q = A p over the active rows and columns (zero on inactive rows); part[f][blk] = p.q over the slice
+__global__ void k_cm_qdot(int64_t nn, DevView v, double phi_min, const int32_t *__restrict__ row_ptr,
+                          const int32_t *__restrict__ col, const double *__restrict__ mc,
+                          const double *__restrict__ p, double *__restrict__ q, double *__restrict__ part,
+                          const double *__restrict__ flag) {
+  pdl_enter();
+  if (*flag != 0.0) return;
+  const int f = blockIdx.y;
+  const double *pf = p + (int64_t)f * nn;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nn; a += (int64_t)gridDim.x * blockDim.x) {
+    double y = 0.0;
+    if (cm_active(v, a, phi_min))
+      for (int e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
+        const int64_t b = col[e];
+        if (cm_active(v, b, phi_min)) y += mc[e] * pf[b];
+      }
+    q[(int64_t)f * nn + a] = y;
+    s += pf[a] * y;
+  }
+  cm_block_sum2(s, s2);
+  if (threadIdx.x == 0) part[f * CM_NBLK + blockIdx.x] = s;
 }
 
-// p = z + beta p with beta = rz_new / rz; rz = rz_new (per field)
-__global__ void k_cm_dir(int64_t nn, int K, double *__restrict__ rz, const double *__restrict__ rzn,
-                         const double *__restrict__ z, double *__restrict__ p) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= nn * K) return;
-  const int f = (int)(t / nn);
-  const double beta = rz[f] != 0.0 ? rzn[f] / rz[f] : 0.0;
-  p[t] = z[t] + beta * p[t];
+// Sum of one field's CM_NBLK partial sums by a whole warp (two per lane, then
+// a butterfly): every lane gets the sum, and every block forms it in the same
+// order.  (One thread walking them would chain CM_NBLK dependent loads.)
+static_assert(CM_NBLK == 64, "two partial sums per lane");
+__device__ inline double cm_warp_sum_parts(const double *__restrict__ part) {
+  const int lane = threadIdx.x & 31;
+  double s = part[lane] + part[lane + 32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
 }
 
-__global__ void k_cm_copy_rz(int K, double *__restrict__ rz, const double *__restrict__ rzn) {
-  if (threadIdx.x < K) rz[threadIdx.x] = rzn[threadIdx.x];
+// alpha = rz / p.q; x += alpha p, r -= alpha q, z = Dinv r; part_rz / part_rr = r.z / r.r over the slice
+__global__ void k_cm_update(int64_t nn, const double *__restrict__ rz, const double *__restrict__ part_pq,
+                            const double *__restrict__ dinv, const double *__restrict__ p,
+                            const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r,
+                            double *__restrict__ z, double *__restrict__ part_rz, double *__restrict__ part_rr,
+                            const double *__restrict__ flag) {
+  pdl_enter();
+  if (*flag != 0.0) return;
+  const int f = blockIdx.y;
+  __shared__ double s_alpha;
+  if (threadIdx.x < 32) {
+    const double pq = cm_warp_sum_parts(part_pq + f * CM_NBLK);
+    if (threadIdx.x == 0) s_alpha = pq != 0.0 ? rz[f] / pq : 0.0;
+  }
+  __syncthreads();
+  const double alpha = s_alpha;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nn; a += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = (int64_t)f * nn + a;
+    x[t] += alpha * p[t];
+    const double rv = r[t] - alpha * q[t];
+    r[t] = rv;
+    const double zv = dinv[a] * rv;
+    z[t] = zv;
+    s += rv * zv;
+    s2 += rv * rv;
+  }
+  cm_block_sum2(s, s2);
+  if (threadIdx.x == 0) {
+    part_rz[f * CM_NBLK + blockIdx.x] = s;
+    part_rr[f * CM_NBLK + blockIdx.x] = s2;
+  }
+}
+
+// beta = rz_new / rz; p = z + beta p; rz_next = rz_new; the convergence flag
+// (block (0, 0), a warp per field's r.r).  Not skipped after convergence: it
+// then recomputes the same values from partial sums nothing changes.
+__global__ void k_cm_next(int64_t nn, int K, const double *__restrict__ rz, double *__restrict__ rz_next,
+                          const double *__restrict__ part_rz, const double *__restrict__ part_rr,
+                          const double *__restrict__ bb, double rtol2, const double *__restrict__ z,
+                          double *__restrict__ p, double *__restrict__ flag) {
+  pdl_enter();
+  const int f = blockIdx.y;
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  __shared__ double s_rzn, s_st[CM_MAXF];
+  if (warp == 0) {
+    const double v = cm_warp_sum_parts(part_rz + f * CM_NBLK);
+    if (threadIdx.x == 0) s_rzn = v;
+  }
+  const bool lead = blockIdx.x == 0 && blockIdx.y == 0;
+  if (lead)
+    for (int g = warp; g < K; g += nwarp) {
+      const double rr = cm_warp_sum_parts(part_rr + g * CM_NBLK);
+      if ((threadIdx.x & 31) == 0) s_st[g] = !isfinite(rr) ? 2.0 : (rr > rtol2 * bb[g] ? 0.0 : 1.0);
+    }
+  __syncthreads();
+  const double rzn = s_rzn;
+  const double beta = rz[f] != 0.0 ? rzn / rz[f] : 0.0;
+  for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nn; a += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = (int64_t)f * nn + a;
+    p[t] = z[t] + beta * p[t];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rz_next[f] = rzn;
+  if (lead && threadIdx.x == 0) {
+    double st = 1.0;  // 1 converged, 0 not yet, 2 non-finite
+    for (int g = 0; g < K; ++g) {
+      if (s_st[g] == 2.0) st = 2.0;
+      else if (s_st[g] == 0.0 && st == 1.0) st = 0.0;
+    }
+    *flag = st;
+  }
 }
 
 __global__ void k_cm_scatter(int64_t nn, CMFields F, const double *__restrict__ x) {
@@ -1337,8 +1438,8 @@ int run_consistent_p2g(Ctx &c) {
   }
   const int64_t KN = (int64_t)K * nn;
   double *x = c.cm_buf, *r = x + KN, *z = r + KN, *p = z + KN, *q = p + KN, *rhs = q + KN, *dinv = rhs + KN;
-  double *part = dinv + nn, *part2 = part + 2 * CM_NBLK * K;
-  double *rz = part2 + 2 * CM_NBLK * K, *rzn = rz + K, *pq = rzn + K, *rr = pq + K, *bb = rr + K;
+  double *part = dinv + nn, *part_rz = part + CM_NBLK * K, *part_rr = part_rz + CM_NBLK * K;
+  double *rz = part_rr + 2 * CM_NBLK * K, *rz2 = rz + K, *bb = rz2 + K, *flag = bb + K;
   if (!c.mc || c.mc_cap < c.nnzb_cap) {
     cudaFree(c.mc);
     c.mc = nullptr;
@@ -1363,40 +1464,38 @@ int run_consistent_p2g(Ctx &c) {
   k_cm_setup<<<gk, TPB, 0, c.st>>>(nn, v, phm, c.row_ptr, c.col, c.mc, F, x, rhs, dinv);
   k_cm_spmv<<<gk, TPB, 0, c.st>>>(nn, K, v, phm, c.row_ptr, c.col, c.mc, x, q);
   k_cm_init<<<gk, TPB, 0, c.st>>>(nn, K, rhs, q, dinv, r, z, p);
-  k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, r, z, rhs, part, part2);  // r.z and r.rhs (unused)
+  k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, r, z, nullptr, part, nullptr);  // r.z
   k_cm_sum<<<1, 32, 0, c.st>>>(K, part, nullptr, rz, nullptr);
   k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, rhs, rhs, nullptr, part, nullptr);
   k_cm_sum<<<1, 32, 0, c.st>>>(K, part, nullptr, bb, nullptr);
   c.launches += 8;
-  double hb[CM_MAXF], hr[CM_MAXF];
-  cudaMemcpyAsync(hb, bb, sizeof(double) * K, cudaMemcpyDeviceToHost, c.st);
-  if (check_cuda(c, cudaStreamSynchronize(c.st), "consistent mass")) return MPM_ERR_CUDA;
-  // each field to a relative residual of CM_RTOL (CG on the Jacobi-scaled mass)
+  // each field to a relative residual of CM_RTOL (CG on the Jacobi-scaled
+  // mass), tested on the device; the host reads the flag every CM_CHECK
+  // iterations
   const double CM_RTOL = 1e-14;
-  const int CM_MAXIT = 1000;
-  bool done = false;
-  for (int it = 0; it < CM_MAXIT && !done; ++it) {
-    k_cm_spmv<<<gk, TPB, 0, c.st>>>(nn, K, v, phm, c.row_ptr, c.col, c.mc, p, q);
-    k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, p, q, nullptr, part, nullptr);
-    k_cm_sum<<<1, 32, 0, c.st>>>(K, part, nullptr, pq, nullptr);
-    k_cm_step<<<gk, TPB, 0, c.st>>>(nn, K, rz, pq, dinv, p, q, x, r, z);
-    k_cm_dots<<<dim3(CM_NBLK, K), TPB, 0, c.st>>>(nn, r, z, r, part, part2);
-    k_cm_sum<<<1, 32, 0, c.st>>>(K, part, part2, rzn, rr);
-    k_cm_dir<<<gk, TPB, 0, c.st>>>(nn, K, rz, rzn, z, p);
-    k_cm_copy_rz<<<1, 32, 0, c.st>>>(K, rz, rzn);
-    c.launches += 8;
-    cudaMemcpyAsync(hr, rr, sizeof(double) * K, cudaMemcpyDeviceToHost, c.st);
-    if (check_cuda(c, cudaStreamSynchronize(c.st), "consistent mass")) return MPM_ERR_CUDA;
-    done = true;
-    for (int f = 0; f < K; ++f) {
-      if (!isfinite(hr[f])) {
-        c.last_error = "non-finite value in the consistent-mass mapping";
-        return MPM_ERR_NONFINITE;
-      }
-      if (hr[f] > CM_RTOL * CM_RTOL * hb[f]) done = false;
+  const int CM_MAXIT = 1000, CM_CHECK = 8;
+  cudaMemsetAsync(flag, 0, sizeof(double), c.st);
+  double hflag = 0.0;
+  const dim3 gcm(CM_NBLK, K);
+  for (int it = 0; it < CM_MAXIT && hflag == 0.0;) {
+    for (int k = 0; k < CM_CHECK && it < CM_MAXIT; ++k, ++it) {
+      double *rzc = (it & 1) ? rz2 : rz, *rzx = (it & 1) ? rz : rz2;
+      launch_pdl(c, k_cm_qdot, gcm, TPB, 0, nn, v, phm, (const int32_t *)c.row_ptr, (const int32_t *)c.col,
+                 (const double *)c.mc, (const double *)p, q, part, (const double *)flag);
+      launch_pdl(c, k_cm_update, gcm, TPB, 0, nn, (const double *)rzc, (const double *)part,
+                 (const double *)dinv, (const double *)p, (const double *)q, x, r, z, part_rz, part_rr,
+                 (const double *)flag);
+      launch_pdl(c, k_cm_next, gcm, TPB, 0, nn, K, (const double *)rzc, rzx, (const double *)part_rz,
+                 (const double *)part_rr, (const double *)bb, CM_RTOL * CM_RTOL, (const double *)z, p, flag);
     }
+    cudaMemcpyAsync(&hflag, flag, sizeof(double), cudaMemcpyDeviceToHost, c.st);
+    if (check_cuda(c, cudaStreamSynchronize(c.st), "consistent mass")) return MPM_ERR_CUDA;
   }
-  if (!done) {
+  if (hflag == 2.0) {
+    c.last_error = "non-finite value in the consistent-mass mapping";
+    return MPM_ERR_NONFINITE;
+  }
+  if (hflag != 1.0) {
     c.last_error = "consistent-mass mapping: CG did not reach its tolerance (ill-conditioned mass)";
     return MPM_ERR_KRYLOV_STAGNATED;
   }
@@ -1632,6 +1731,7 @@ void autotune_jacobian(Ctx &c, T *val, int apply_bc) {
   for (int k = 0; k < 3 * Ctx::JAC_FORMS; ++k) c.stats.jac_tune_ms[pi][k] = 0.0f;
   for (int form = 0; form < Ctx::JAC_FORMS; ++form) {
     if (pi == 0 && form != Ctx::JAC_STAGED) continue;
+    if (pi == 1 && form == Ctx::JAC_DIRECT && c.s.hencky) continue;  // no Hencky tangent there
     if (pi == 1 && form != Ctx::JAC_DIRECT && ensure_jacobian_staging32(c) != MPM_OK) continue;
     for (int k = 0; k < 3; ++k) {
       launch_jacobian<T>(c, val, apply_bc, form, tpbs[k]);
@@ -1663,7 +1763,10 @@ void run_jacobian(Ctx &c, T *val, int apply_bc) {
   constexpr int pi = sizeof(T) == sizeof(double) ? 0 : 1;
   Ctx::JacCfg &cfg = c.jac_cfg[pi];
   if (c.opt.autotune && !cfg.tuned && !c.capturing) autotune_jacobian<T>(c, val, apply_bc);
-  if (pi == 1 && cfg.form != Ctx::JAC_DIRECT && ensure_jacobian_staging32(c) != MPM_OK) cfg.form = Ctx::JAC_DIRECT;
+  // without room for the FP32 staging the direct form serves, except for
+  // Hencky (whose Newton loop allocates the staging first and stops on failure)
+  if (pi == 1 && cfg.form != Ctx::JAC_DIRECT && !c.s.hencky && ensure_jacobian_staging32(c) != MPM_OK)
+    cfg.form = Ctx::JAC_DIRECT;
   c.stats.jac_config[pi] = cfg.tpb + 1000 * cfg.form;
   c.stats.jac_tuned[pi] = cfg.tuned;
   prof_begin(c, MPM_PROF_JACOBIAN);

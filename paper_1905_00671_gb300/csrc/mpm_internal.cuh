@@ -370,6 +370,7 @@ void run_g2p(Ctx &c);
 int run_pattern(Ctx &c);                          // builds row_ptr / col / row_of
 int run_consistent_p2g(Ctx &c);  // Stage-1 fields by the consistent mass (after run_pattern)
 int ensure_jacobian_staging(Ctx &c);  // the FP64 Jacobian's staging buffer (allocated by FP64 contexts at create)
+int ensure_jacobian_staging32(Ctx &c);  // the FP32 staged Jacobian's buffer (mixed mode; Hencky always, else when chosen)
 void run_initial_guess(Ctx &c);   // also sets the active flags
 void run_renorm(Ctx &c);          // per-point renormalisation over active box nodes
 int run_pn_layout(Ctx &c);        // first staged Jacobian record of each point (pn_base)

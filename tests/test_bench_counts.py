@@ -48,3 +48,14 @@ def test_traffic_lookup_by_hash_and_workload(tmp_path, monkeypatch):
     assert bench.ncu_traffic("k_bsr_spmv", "footing-200x100") is None   # another source
     assert bench.ncu_traffic("k_jacobian", "slope-128x128x64") is None  # no line
     assert bench.ncu_traffic("k_bsr_spmv", "slope-64x64x32") is None    # another workload
+
+
+def test_fp32_jacobian_bytes():
+    # 3D quasi-static: 2 d^2 + 2 d + 9 + 12 d words per point; Hencky adds
+    # the principal directions (d^2), kappa_A (d) and theta_AB (d (d - 1) / 2)
+    n, nnzb, nnodes = 100, 2000, 50
+    base = 4 * (18 + 6 + 9 + 36) * n + nnzb * (16 * 4 + 4) + nnodes * 52
+    assert bench.jacobian32_bytes(n, nnzb, nnodes, 3, False) == base
+    assert bench.jacobian32_bytes(n, nnzb, nnodes, 3, False, True) == base + 4 * (9 + 3 + 3) * n
+    assert bench.jacobian32_bytes(n, nnzb, nnodes, 2, True, True) - bench.jacobian32_bytes(
+        n, nnzb, nnodes, 2, True) == 4 * (4 + 2 + 1) * n

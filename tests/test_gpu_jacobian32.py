@@ -1,6 +1,6 @@
 """The FP32 Jacobian of the mixed mode (Eq. jacobian-system-stabilized-ppp in
 FP32) by every kernel configuration the autotuner chooses from (per-term and
-staged; 64, 128, 256 threads),
+staged; 64, 128, 256 threads; Hencky elasticity staged only),
 against the oracle's FP64 Jacobian at a perturbed iterate and against one
 another.
 
@@ -9,6 +9,8 @@ Bars: each block type entry-wise within 2e-5 of that type's largest entry
 configurations within 2e-6 of one another (the same FP32 products summed in
 different orders).  Sparsity, Dirichlet rows and columns exact.
 """
+
+from dataclasses import replace
 
 import numpy as np
 import pytest
@@ -46,7 +48,15 @@ CASES = {
     "block3d-gimp-qs": lambda: I.small_block(seed=11, body=(6, 5, 4)),
     "block3d-orig-qs": lambda: I.small_block(seed=12, shape=I.ORIG, body=(5, 4, 4)),
     "block3d-gimp-lattice": lambda: I.small_block(seed=13, body=(6, 6, 4), jitter=0.0),
+    # Hencky (Sec. 2.2) with the Kelvin stress of Sec. 5.2
+    "footing2d-gimp-newmark-hencky": lambda: replace(I.small_footing(seed=7, body=(24, 12), pad=2, h=0.25),
+                                                     model=I.MODEL_HENCKY, alpha_vis=0.04),
+    "block3d-gimp-qs-hencky": lambda: replace(I.small_block(seed=11, body=(6, 5, 4)), model=I.MODEL_HENCKY),
 }
+
+
+def forms_of(w):
+    return (1,) if w.model == I.MODEL_HENCKY else FORMS
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -67,7 +77,7 @@ def test_fp32_jacobian_every_configuration(mpm, name):
     _, Jo = orc.eval(prep, X, w.traction(w.dt))
     Jo = Jo.reshape(-1, nb, nb)
     first = None
-    for form in FORMS:
+    for form in forms_of(w):
         for tpb in TPBS:
             Jg = sim.debug_jacobian32(X, len(col), form, tpb, apply_bc=False).reshape(-1, nb, nb)
             for r in range(nb):
@@ -83,13 +93,13 @@ def test_fp32_jacobian_every_configuration(mpm, name):
     # fixed rows and columns, by every form
     fixed = np.asarray(orc.fixed_dofs(prep), dtype=bool).reshape(-1, nb)
     rows = np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
-    for form in FORMS:
+    for form in forms_of(w):
         Jb = sim.debug_jacobian32(X, len(col), form, 128, apply_bc=True).reshape(-1, nb, nb)
         fr = fixed[rows][:, :, None] | fixed[col][:, None, :]
         eye = (rows == col)[:, None, None] & np.eye(nb, dtype=bool)[None]
         np.testing.assert_array_equal(Jb[fr & eye], 1.0)
         np.testing.assert_array_equal(Jb[fr & ~eye], 0.0)
-        if form == 0:  # the same form and kernel: the free entries bit for bit
+        if form == forms_of(w)[0]:  # the same form and kernel: the free entries bit for bit
             np.testing.assert_array_equal(Jb[~fr], first[~fr])
     sim.close()
 
@@ -108,4 +118,28 @@ def test_fp32_jacobian_rejects_a_fp64_context_and_bad_configurations(mpm):
     for form, tpb in ((2, 128), (-1, 128), (0, 96)):
         with pytest.raises(mpm.MPMError):
             sim.debug_jacobian32(X, len(col), form, tpb)
+    sim.close()
+    # the per-term form has no Hencky tangent
+    sim = mpm.Simulation(replace(w, model=I.MODEL_HENCKY), precision=mpm.MPM_MIXED)
+    sim.debug_prepare()
+    with pytest.raises(mpm.MPMError) as e:
+        sim.debug_jacobian32(X, len(col), 0)
+    assert e.value.code == -1
+    sim.close()
+
+
+@pytest.mark.parametrize("autotune", [0, 1])
+def test_hencky_mixed_step_uses_the_staged_form(mpm, autotune):
+    """A mixed-precision Hencky context assembles by the staged form, fixed or
+    tuned: the autotuner times only the staged candidates (the per-term
+    candidates' times stay 0)."""
+    w = CASES["footing2d-gimp-newmark-hencky"]()
+    sim = mpm.Simulation(w, precision=mpm.MPM_MIXED, autotune=autotune, newton_max=40)
+    sim.step()
+    st = sim.stats()
+    assert st["jac_config"][1] // 1000 == 1, st["jac_config"]
+    assert st["jac_tuned"][1] == autotune
+    assert all(t == 0.0 for t in st["jac_tune_ms"][1][:3])
+    if autotune:
+        assert all(t > 0.0 for t in st["jac_tune_ms"][1][3:])
     sim.close()

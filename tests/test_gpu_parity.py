@@ -238,10 +238,6 @@ def test_bad_arguments_are_rejected(mpm):
     with pytest.raises(mpm.MPMError) as e:
         mpm.Simulation(w, model=2)
     assert e.value.code == -1
-    # Hencky runs in FP64 only
-    with pytest.raises(mpm.MPMError) as e:
-        mpm.Simulation(replace(w, model=I.MODEL_HENCKY), precision=mpm.MPM_MIXED)
-    assert e.value.code == -1
     # Kozeny-Carman needs an initial porosity in (0, 1)
     with pytest.raises(mpm.MPMError) as e:
         mpm.Simulation(replace(w, phi0=0.0), permeability=mpm.MPM_PERM_KOZENY_CARMAN)
@@ -269,6 +265,12 @@ MIXED_CASES = {
     "block3d-gimp-qs": (CASES["block3d-gimp-qs"], 2),
     "self-weight-8x8-kozeny": (
         lambda: I.self_weight_consolidation(ncell=(8, 8), h=0.25, ppc_axis=2, K=1.5e6, k0=1e-10), 2),
+    # Hencky: the FP32 Jacobian stages the spectral tangent per (point, node)
+    "footing2d-gimp-newmark-hencky": (CASES["footing2d-gimp-newmark-hencky"], 3),
+    "block3d-gimp-qs-hencky": (CASES["block3d-gimp-qs-hencky"], 2),
+    "self-weight-paper-16x16-hencky": (lambda: replace(I.self_weight_consolidation(), model=I.MODEL_HENCKY), 2),
+    # the Sec. 5.2 set-up at full size: Hencky, consistent mass, Newmark, harmonic load
+    "harmonic-footing-40x44": (lambda: I.harmonic_footing(), 2),
 }
 
 

@@ -67,7 +67,7 @@ def test_product_path_never_imports_the_oracle():
 
 @pytest.mark.parametrize("opts,model,why", [
     (dict(krylov_restart=200), None, "krylov_restart must be in 1..128"),
-    (dict(precision=1), 1, "needs precision MPM_FP64"),
+    (dict(model=2), None, "unknown model"),
     (dict(tau_kind=2), None, "MPM_TAU_MONFORTE needs the Newmark scheme"),
     (dict(min_volume_fraction=-1.0), None, "min_volume_fraction"),
     (dict(precond_reuse=-1), None, "precond_reuse must be in"),
