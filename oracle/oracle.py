@@ -15,9 +15,9 @@ One load step follows the four stages of Sec. 3.1:
   3./4. update the points from the nodes, convect them, update the GIMP
      domains (Sec. 3.5).
 
-Functions with no independent pin: the dynamic terms whose linearization the
-paper leaves out (Kelvin damping geometry, Darcy acceleration) are checked only
-against the CUDA path, not against the paper: parity unpinned for those terms.
+The dynamic terms whose linearization the paper leaves out (Kelvin damping
+geometry, Darcy acceleration) are pinned through eval_frozen: the Jacobian
+matches central differences of the residual with exactly those terms frozen.
 """
 from __future__ import annotations
 
@@ -407,6 +407,27 @@ class Oracle:
                             _p(prep["row_ptr"]), _p(prep["col"]), _p(R), _p(Jv))
         _check(rc, "eval")
         return R, Jv
+
+    def eval_frozen(self, prep, X, Xf, traction, flux=None):
+        """Residual with the terms the Jacobian leaves unlinearized (Sec. 3.4:
+        the Kelvin stress's geometry, Darcy's acceleration) frozen at the
+        iterate Xf; its derivative at X = Xf is the Jacobian of eval."""
+        d, nb = self.d, self.d + 1
+        X = np.ascontiguousarray(X, float).reshape(-1)
+        Xf = np.ascontiguousarray(Xf, float).reshape(-1)
+        R = np.zeros(self.nn * nb)
+        sp = self._step_struct(prep["dt"])
+        pp = self._particles_struct(prep["m"])
+        nd = self._nodal_struct(prep["nodal"])
+        trac = np.ascontiguousarray(traction, float).reshape(-1) if traction is not None \
+            else np.zeros(max(1, self.w.n_surf * d))
+        flx = None if flux is None else np.ascontiguousarray(flux, float)
+        rc = lib().orc_eval_frozen(C.byref(self.g), C.byref(sp), C.byref(pp), _p(prep["first"]),
+                                   _p(prep["count"]), _p(prep["S"]), _p(prep["dS"]), _p(prep["S0"]),
+                                   _p(prep["active_u8"]), C.byref(nd), _p(trac), _p(flx), _p(X), _p(Xf),
+                                   _p(R))
+        _check(rc, "eval_frozen")
+        return R
 
     def fixed_dofs(self, prep):
         """Dirichlet DOFs plus every DOF of an inactive node: a node whose

@@ -551,13 +551,22 @@ static void newmark_node(const orc_step *sp, int d, const orc_nodal *nd, int64_t
  * geometric dependence of the viscous term, the acceleration inside Darcy's
  * law; the mixture mass is frozen over the step.
  * Pinned: central finite differences (quasi-static; dynamic with
- * alpha_vis = 0 and rho_f = 0), C_stab symmetric PSD, Terzaghi series.
+ * alpha_vis = 0 and rho_f = 0; dynamic with both, of the residual whose
+ * unlinearized terms are frozen, orc_eval_frozen), C_stab symmetric PSD,
+ * Terzaghi series.
+ *
+ * Xf (NULL for the residual itself): the frozen variant.  The terms left
+ * unlinearized take their geometry from the iterate Xf instead of X: the
+ * Kelvin stress its spatial gradients (in D = grad^s v and in the contraction
+ * with grad S_a), its mu' (or the Hencky tangent), and Darcy's law its
+ * acceleration; the nodal velocities stay those of X.  The derivative of that
+ * residual at X = Xf is what the analytic Jacobian holds.
  * ---------------------------------------------------------------------- */
-int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
-             const int32_t *first, const int32_t *count, const double *S, const double *dS,
-             const double *S0, const uint8_t *active, const orc_nodal *nd, const double *trac,
-             const double *flux, const double *X, const int64_t *row_ptr, const int32_t *col_idx,
-             double *R, double *Jv) {
+static int eval_impl(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
+                     const int32_t *first, const int32_t *count, const double *S, const double *dS,
+                     const double *S0, const uint8_t *active, const orc_nodal *nd, const double *trac,
+                     const double *flux, const double *X, const double *Xf, const int64_t *row_ptr,
+                     const int32_t *col_idx, double *R, double *Jv) {
   const int d = g->dim, nb = d + 1, nb2 = nb * nb;
   const int64_t nn = orc_nnodes(g);
   const double dt = sp->dt, beta = sp->beta, gam = sp->gamma;
@@ -667,24 +676,72 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
         kap = 0.0;
       }
     }
+    /* the frozen variant's geometry of the unlinearized terms (see above):
+     * gradients grk, mu' muk, Hencky tangent ctk and acceleration ahk at Xf */
+    double grf[MAXS * MAXS * MAXS][MAXD], ctf[81], ahf[3] = {0, 0, 0}, muf = 0.0;
+    const double(*grk)[MAXD] = gr;
+    const double *ctk = ct, *ahk = ah;
+    double muk = mu_p;
+    if (Xf && sp->dynamic) {
+      double dFf[9] = {0}, ff[9], Ff[9] = {0}, bf[9] = {0}, tauf[9];
+      for (int i = 0; i < d; ++i) dFf[i * d + i] = 1.0;
+      for (int q = 0; q < ns; ++q)
+        for (int i = 0; i < d; ++i)
+          for (int k = 0; k < d; ++k) dFf[i * d + k] += Xf[su->node[q] * nb + i] * su->Gn[q][k];
+      if (!(det_d(d, dFf) > 0.0)) {
+        rc = ORC_ERR_NEGATIVE_J;
+        break;
+      }
+      inv_d(d, dFf, ff);
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+          for (int k = 0; k < d; ++k) Ff[i * d + j] += dFf[i * d + k] * Fn[k * d + j];
+      for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+          for (int k = 0; k < d; ++k) bf[i * d + j] += Ff[i * d + k] * Ff[j * d + k];
+      if (sp->hencky) hencky(d, bf, lam, Gs, tauf, ctf);
+      muf = Gs - lam * log(det_d(d, Ff));
+      for (int q = 0; q < ns; ++q) {
+        for (int j = 0; j < d; ++j) {
+          double s = 0.0;
+          for (int k = 0; k < d; ++k) s += su->Gn[q][k] * ff[k * d + j];
+          grf[q][j] = s;
+        }
+        double vf[3], af[3], pdf, pddf;
+        newmark_node(sp, d, nd, su->node[q], Xf, vf, af, &pdf, &pddf);
+        for (int i = 0; i < d; ++i) ahf[i] += su->S[q] * af[i];
+      }
+      grk = (const double(*)[MAXD])grf;
+      ctk = ctf;
+      ahk = ahf;
+      muk = muf;
+    }
     double w[3];
-    for (int j = 0; j < d; ++j) w[j] = gp[j] - sp->rho_f * (sp->g[j] - ah[j]);
+    for (int j = 0; j < d; ++j) w[j] = gp[j] - sp->rho_f * (sp->g[j] - ahk[j]);
     /* Kelvin viscous stress (v sigma_vis) = (V_n/J_n) alpha (lambda tr D 1 + 2 mu' D) */
     double svis[9] = {0};
     if (sp->dynamic && sp->alpha_vis != 0.0) {
+      double gvk[9] = {0}; /* grad v: the velocities of X at the gradients grk */
+      if (grk == (const double(*)[MAXD])gr) {
+        for (int i = 0; i < d * d; ++i) gvk[i] = gv[i];
+      } else {
+        for (int q = 0; q < ns; ++q)
+          for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) gvk[i * d + j] += nva[q][i] * grk[q][j];
+      }
       double trD = 0.0;
-      for (int i = 0; i < d; ++i) trD += gv[i * d + i];
+      for (int i = 0; i < d; ++i) trD += gvk[i * d + i];
       for (int i = 0; i < d; ++i)
         for (int j = 0; j < d; ++j) {
-          const double D = 0.5 * (gv[i * d + j] + gv[j * d + i]);
-          svis[i * d + j] = sp->alpha_vis * ((i == j ? lam * trD : 0.0) + 2.0 * mu_p * D);
+          const double D = 0.5 * (gvk[i * d + j] + gvk[j * d + i]);
+          svis[i * d + j] = sp->alpha_vis * ((i == j ? lam * trD : 0.0) + 2.0 * muk * D);
         }
       if (sp->hencky) /* sigma_vis = alpha c : grad^s v with the Hencky tangent */
         for (int i = 0; i < d; ++i)
           for (int j = 0; j < d; ++j) {
             double s = 0.0;
             for (int k = 0; k < d; ++k)
-              for (int l = 0; l < d; ++l) s += ct[((i * d + j) * d + k) * d + l] * 0.5 * (gv[k * d + l] + gv[l * d + k]);
+              for (int l = 0; l < d; ++l) s += ctk[((i * d + j) * d + k) * d + l] * 0.5 * (gvk[k * d + l] + gvk[l * d + k]);
             svis[i * d + j] = sp->alpha_vis * s;
           }
     }
@@ -699,7 +756,7 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
         double r = 0.0;
         for (int j = 0; j < d; ++j) r -= cs * gr[q][j] * tau[i * d + j];   /* -grad^s S : sigma' dv */
         r += vol * gr[q][i] * ph;                                          /* +div S p dv          */
-        for (int j = 0; j < d; ++j) r -= cs * gr[q][j] * svis[i * d + j]; /* -grad^s S : sigma_vis */
+        for (int j = 0; j < d; ++j) r -= cs * grk[q][j] * svis[i * d + j]; /* -grad^s S : sigma_vis */
         r -= su->S[q] * mp * ah[i];                                        /* -S rho a dv          */
         r += su->S[q] * mp * sp->g[i];                                     /* +S rho g dv          */
         R[a * nb + i] += r;
@@ -795,6 +852,23 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
 done:
   free(su);
   return rc;
+}
+
+int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
+             const int32_t *first, const int32_t *count, const double *S, const double *dS,
+             const double *S0, const uint8_t *active, const orc_nodal *nd, const double *trac,
+             const double *flux, const double *X, const int64_t *row_ptr, const int32_t *col_idx,
+             double *R, double *Jv) {
+  return eval_impl(g, sp, pp, first, count, S, dS, S0, active, nd, trac, flux, X, NULL, row_ptr, col_idx,
+                   R, Jv);
+}
+
+int orc_eval_frozen(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
+                    const int32_t *first, const int32_t *count, const double *S, const double *dS,
+                    const double *S0, const uint8_t *active, const orc_nodal *nd, const double *trac,
+                    const double *flux, const double *X, const double *Xf, double *R) {
+  if (!Xf) return ORC_ERR_BAD_ARG;
+  return eval_impl(g, sp, pp, first, count, S, dS, S0, active, nd, trac, flux, X, Xf, NULL, NULL, R, NULL);
 }
 
 /* ------------------------------------------------------------------------

@@ -113,6 +113,16 @@ int orc_eval(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
              const double *flux, const double *X, const int64_t *row_ptr, const int32_t *col_idx,
              double *R, double *Jv);
 
+/* The residual of orc_eval with the terms it leaves unlinearized frozen at
+ * the iterate Xf (the Kelvin stress's geometry and mu' or Hencky tangent,
+ * Darcy's acceleration; the nodal velocities still from X): its derivative at
+ * X = Xf is the analytic Jacobian of orc_eval (Sec. 3.4: some inertia and
+ * damping terms are not linearized).  R only. */
+int orc_eval_frozen(const orc_grid *g, const orc_step *sp, const orc_particles *pp,
+                    const int32_t *first, const int32_t *count, const double *S, const double *dS,
+                    const double *S0, const uint8_t *active, const orc_nodal *nd, const double *trac,
+                    const double *flux, const double *X, const double *Xf, double *R);
+
 int orc_g2p(const orc_grid *g, const orc_step *sp, int64_t n, const int32_t *first,
             const int32_t *count, const double *S, const double *dS, const double *S0,
             const uint8_t *active, const orc_nodal *nd, const double *X, double *x, double *u,

@@ -10,7 +10,12 @@ leaves out of the linearization (Sec. 3.3), pinned by closed forms:
   change by exactly rho_f kappa V a by virtual work;
 * the Jacobian at rest with the Kelvin stress against central differences: D
   vanishes at rest, so the geometric dependence the Jacobian omits does too and
-  the viscous tangent gamma / (beta dt) alpha c is all that remains.
+  the viscous tangent gamma / (beta dt) alpha c is all that remains;
+* away from rest (Kelvin stress and fluid density on, velocities and
+  accelerations nonzero), the Jacobian against central differences of the
+  residual with exactly the unlinearized terms frozen at the iterate (the
+  Kelvin stress's geometry, Darcy's acceleration): every other term of the
+  Jacobian is the exact derivative, and what it leaves out is only those terms.
 """
 from dataclasses import replace
 
@@ -19,7 +24,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_1905_00671_gb300 import inputs as I
-from tests.test_oracle_physics import dense_J
+from tests.test_oracle_physics import dense_J, perturbed_X
 
 E, NU = 12e6, 0.3
 LAM = E * NU / ((1 + NU) * (1 - 2 * NU))
@@ -133,3 +138,63 @@ def test_jacobian_with_kelvin_stress_at_rest_matches_central_differences():
     _, J0 = o0.eval(o0.prepare(w.dt), X, trac)
     A0 = dense_J(o0, prep, J0)[0::nb, 0::nb]
     assert np.abs(A0 - J[0::nb, 0::nb]).max() > 1e-3 * np.abs(J[0::nb, 0::nb]).max()
+
+
+def _fd_columns(o, prep, X, fn):
+    nb = o.d + 1
+    Jfd = np.zeros((o.nn * nb, o.nn * nb))
+    for j in range(o.nn * nb):
+        hstep = 1e-5 * (1e-3 if j % nb < o.d else 1e3)
+        Xp, Xm = X.copy(), X.copy()
+        Xp[j] += hstep
+        Xm[j] -= hstep
+        Jfd[:, j] = (fn(Xp) - fn(Xm)) / (2 * hstep)
+    return Jfd
+
+
+# a permeable soil (k = 1e-9 m^2), so that the Darcy terms weigh in the mass
+# rows as much as the Newmark divergence does
+def _permeable(w):
+    return replace(w, k=np.full_like(w.k, 1e-9))
+
+
+FROZEN_CASES = {
+    "footing2d-neohookean": lambda: _permeable(replace(
+        I.small_footing(seed=4, body=(4, 3), pad=1, h=0.25, dynamic=True), alpha_vis=0.2, rho_f=1000.0)),
+    "footing2d-hencky": lambda: _permeable(replace(
+        I.small_footing(seed=5, body=(4, 3), pad=1, h=0.25, dynamic=True), alpha_vis=0.2, rho_f=1000.0,
+        model=I.MODEL_HENCKY)),
+    "block3d-neohookean": lambda: _permeable(replace(
+        I.small_block(seed=6, body=(2, 2, 2)), dynamic=True, alpha_vis=0.2, rho_f=1000.0, dt=1e-3)),
+}
+
+
+@pytest.mark.parametrize("name", list(FROZEN_CASES))
+def test_jacobian_away_from_rest_is_the_derivative_of_the_frozen_residual(name):
+    w = FROZEN_CASES[name]()
+    o = O.Oracle(w)
+    prep = o.prepare(w.dt)
+    X0 = perturbed_X(o, prep, seed=3, amp_u=2e-4, amp_p=1e3)
+    trac = w.traction(w.dt)
+    R0, Jv = o.eval(prep, X0, trac)
+    # frozen at the iterate itself, the variant is the residual
+    np.testing.assert_array_equal(o.eval_frozen(prep, X0, X0, trac), R0)
+    J = dense_J(o, prep, Jv)
+    nb = o.d + 1
+    Jfz = _fd_columns(o, prep, X0, lambda X: o.eval_frozen(prep, X, X0, trac))
+    Jfull = _fd_columns(o, prep, X0, lambda X: o.eval(prep, X, trac, want_J=False)[0])
+    # displacement columns to 1e-9 of each block type's largest entry (the
+    # central differences reach about 1e-11 there, so that terms a thousandth
+    # of the dominant inertia and stiffness still count); the pressure
+    # columns, differenced with steps of 10 Pa, to 1e-6
+    left_out = 0.0
+    for r in range(nb):
+        for cc in range(nb):
+            A, B, Cf = J[r::nb, cc::nb], Jfz[r::nb, cc::nb], Jfull[r::nb, cc::nb]
+            scale = max(np.abs(A).max(), np.abs(B).max())
+            tol = 1e-9 if cc < o.d else 1e-6
+            assert np.abs(A - B).max() <= tol * scale, (name, r, cc, np.abs(A - B).max() / scale)
+            left_out = max(left_out, np.abs(A - Cf).max() / scale)
+    # the frozen terms matter at this iterate: the full residual's differences
+    # are not the Jacobian
+    assert left_out > 1e-4, left_out
