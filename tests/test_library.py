@@ -139,3 +139,51 @@ def test_last_error_without_a_context_on_a_fresh_thread(lib):
     t.start()
     t.join()
     assert out == [b"null context"]
+
+
+def _empty_points(w):
+    import numpy as np
+    d = w.dim
+    return dict(x=np.zeros((0, d)), vol=np.zeros(0), lp=np.zeros((0, d)), p0=np.zeros(0), v0=None,
+                E=np.zeros(0), nu=np.zeros(0), k=np.zeros(0), surf_id=np.zeros(0, np.int32),
+                surf_normal=np.zeros((0, d)), surf_area=np.zeros(0), trac_full=np.zeros((0, d)))
+
+
+@pytest.mark.parametrize("case,why", [
+    ("no points", "need n > 0 points"),
+    ("dim 4", "grid.dim must be 2 or 3"),
+    ("zero cells", "grid.ncell must be at least 1"),
+    ("zero spacing", "grid.h must be positive"),
+    ("surface id out of range", "surf_id outside"),
+    ("zero fluid viscosity", "material.mu_f must be positive"),
+])
+def test_degenerate_inputs_are_rejected_at_create_without_gpu(lib, case, why):
+    """Degenerate problems (an empty point set, a grid of another dimension,
+    of no cells or of zero spacing, a surface id past the surface count, no
+    fluid viscosity) return MPM_ERR_BAD_ARG from mpm_create before any device
+    call, with the reason in mpm_last_error."""
+    from dataclasses import replace
+
+    import numpy as np
+
+    from paper_1905_00671_gb300 import inputs as I
+    from paper_1905_00671_gb300 import mpm
+
+    w = I.terzaghi_column(ncell_y=4, ncell_x=2)
+    if case == "no points":
+        w = replace(w, **_empty_points(w))
+    elif case == "dim 4":
+        w = replace(w, dim=4)
+    elif case == "zero cells":
+        w = replace(w, ncell=(2, 0, 0))
+    elif case == "zero spacing":
+        w = replace(w, h=0.0)
+    elif case == "surface id out of range":
+        sid = w.surf_id.copy()
+        sid[np.nonzero(sid >= 0)[0][0]] = w.n_surf
+        w = replace(w, surf_id=sid)
+    elif case == "zero fluid viscosity":
+        w = replace(w, mu_f=0.0)
+    with pytest.raises(mpm.MPMError, match=why) as e:
+        mpm.Simulation(w)
+    assert e.value.code == -1
