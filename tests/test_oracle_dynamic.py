@@ -166,6 +166,13 @@ FROZEN_CASES = {
         model=I.MODEL_HENCKY)),
     "block3d-neohookean": lambda: _permeable(replace(
         I.small_block(seed=6, body=(2, 2, 2)), dynamic=True, alpha_vis=0.2, rho_f=1000.0, dt=1e-3)),
+    "block3d-hencky": lambda: _permeable(replace(
+        I.small_block(seed=7, body=(2, 2, 2)), dynamic=True, alpha_vis=0.2, rho_f=1000.0, dt=1e-3,
+        model=I.MODEL_HENCKY)),
+    # Kozeny-Carman: the mobility follows the iterate's porosity (Eq. kozeny-carman)
+    "footing2d-kozeny": lambda: _permeable(replace(
+        I.small_footing(seed=8, body=(4, 3), pad=1, h=0.25, dynamic=True), alpha_vis=0.2, rho_f=1000.0,
+        permeability=I.PERM_KOZENY_CARMAN, phi0=0.4)),
 }
 
 
